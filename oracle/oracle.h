@@ -1,0 +1,101 @@
+/* Oracle for the explicit-implicit domain-splitting scheme (May & Thein, arXiv 2211.00705).
+ *
+ * TEST INFRASTRUCTURE ONLY. This is a plain, slow FP64 CPU implementation of the scheme,
+ * written from the paper, that the tests, the smoke check and the CPU baseline of the
+ * benchmark compare the CUDA library against. Nothing in the product library links it,
+ * includes it or calls it, and it shares no code with the CUDA path.
+ *
+ * Conventions (shared in meaning, not in code, with the product C-ABI):
+ *   phase 0 = vapour, phase 1 = liquid.
+ *   [[X]] = X_right - X_left at any discontinuity (Sec. 2.1).
+ *   A state is (rho, m = rho*u) per cell; cells carry a width and a phase label.
+ */
+#ifndef IMEXDS_ORACLE_H
+#define IMEXDS_ORACLE_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int kind;    /* 0: ideal gas p = a2*rho (Eq. eos:isoT_idgas); 1: linear Tait p = p0 + a2*(rho - rho0) (Eq. eos:isoT_lintait) */
+  double a2;   /* squared isothermal sound speed (k T0 / m for the vapour, K0/rho0 for the liquid) */
+  double p0;   /* Tait reference pressure (saturation pressure); unused for kind 0 */
+  double rho0; /* Tait reference density (saturation liquid density); unused for kind 0 */
+} orc_eos;
+
+typedef struct {
+  orc_eos ph[2];   /* [0] vapour, [1] liquid */
+  double p_sat;    /* saturation pressure: common zero of both Gibbs energies */
+  double p_min;    /* minimum liquid pressure (cavitation threshold, App. B) */
+  double p_tilde;  /* maximum vapour pressure (nucleation threshold, App. B) */
+} orc_fluid;
+
+typedef struct {
+  double cfl;          /* C_CFL of Eq. cfl_cond:unif */
+  double theta_nb;     /* theta of the regular neighbours in Alg. 2 (0.9 in Sec. 4) */
+  double tol_nb, tol_k;/* stop tolerances of Sec. 4 (1e-3 neighbours, 1e-1 tiny cells) */
+  int res_mode;        /* 0: residual as printed in Sec. 4 (1/s); 1: residual times dt (dimensionless) */
+  int l_max;           /* cap on dual-time iterations per block */
+  double newton_tol;   /* relative step tolerance of the phase-boundary Newton iteration */
+  int newton_itmax;    /* cap on Newton iterations */
+  double alpha_min;    /* merge floor: a cell predicted below alpha_min*h is merged */
+  double split_ratio;  /* a phase-boundary cell wider than split_ratio*h is split (2 in Sec. 3.4) */
+  int creation;        /* 1: detect cavitation/nucleation at same-phase faces (App. B) */
+} orc_opts;
+
+/* statuses (same numbering as the product library) */
+enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_NONPHYSICAL = 3, ORC_ERR_PB_NOCONV = 4,
+       ORC_ERR_VANISH = 6, ORC_ERR_CAPACITY = 9 };
+
+void orc_default_opts(orc_opts* o);
+
+/* ---- pointwise pieces (unit tests and pins) ---- */
+/* HLL flux (Toro) at a same-phase face; F[2] = (mass, momentum) flux. */
+void orc_hll(const orc_fluid* fl, int ph, double rl, double ml, double rr, double mr, double F[2]);
+/* Evaluate the phase-boundary system G of Eq. 2p_RP:ex_sys at given star pressures (pl, pr) of
+ * the left and right side. out[0..1] = G, out[2] = z (kinetic relation), out[3..6] = DG row-major. */
+void orc_pb_system(const orc_fluid* fl, double tau, int phl, double rl, double ul, int phr, double rr,
+                   double ur, double pls, double prs, double out[7]);
+/* Solve the phase-boundary Riemann problem (App. A). out: [0] p_l*, [1] p_r*, [2] rho_l*, [3] rho_r*,
+ * [4] u_l*, [5] u_r*, [6] z, [7] w, [8] F_mass, [9] F_mom, [10] newton iterations. Returns status. */
+int orc_pb_solve(const orc_fluid* fl, const orc_opts* o, double tau, int phl, double rl, double ul,
+                 int phr, double rr, double ur, double out[11]);
+/* Star pressure of the same-phase Riemann problem without phase transition. */
+double orc_nopt_star(const orc_fluid* fl, int ph, double rl, double ul, double rr, double ur);
+/* Single-phase Riemann problem with phase creation (App. B): parent phase ph, created phase 1-ph.
+ * out: [0] p_parent_left*, [1] p_created*, [2] p_parent_right*, [3] rho_created, [4] u_created,
+ * [5] z_left_PB, [6] z_right_PB, [7] w_left, [8] w_right, [9] u_parent_left*, [10] u_parent_right*,
+ * [11] newton iterations. Returns status. */
+int orc_creation_solve(const orc_fluid* fl, const orc_opts* o, double tau, int ph, double rl, double ul,
+                       double rr, double ur, double out[12]);
+/* Exact solution of the two-phase Riemann problem sampled at n similarity coordinates xi = x/t. */
+int orc_exact_sample(const orc_fluid* fl, const orc_opts* o, double tau, int phl, double rl, double ul,
+                     int phr, double rr, double ur, int n, const double* xi, double* rho, double* u, int* ph);
+
+/* ---- batched instances ---- */
+void* orc_create(int n_inst, const int* n_lattice, const double* x_left, const double* x_right,
+                 const double* tau, const orc_fluid* fl, const orc_opts* o);
+void orc_destroy(void* H);
+/* Cell lists per instance, concatenated; cell_offsets has n_inst+1 entries. */
+int orc_set_states(void* H, const int* cell_offsets, const double* widths, const double* rho,
+                   const double* m, const unsigned char* phase, double t0);
+int orc_n_cells(void* H, int* cell_counts);
+int orc_get_states(void* H, int* cell_offsets, double* widths, double* rho, double* m,
+                   unsigned char* phase, double* t, int* status);
+/* Phase-boundary positions of every instance (n_pb per instance, concatenated). */
+int orc_get_pbs(void* H, int* pb_offsets, double* x_pb);
+/* per instance 10 counters: steps, dts_iters, dts_max, newton, merges, splits, creations,
+ * maxiter_warnings, pb_solves, last_dt_bits(unused=0) */
+int orc_get_stats(void* H, long long* stats);
+int orc_run_to(void* H, double t_end, int n_threads);
+int orc_step(void* H, int n_steps, int n_threads);
+/* Fully explicit reference (brute force): every cell explicit, dt limited by the smallest cell. */
+int orc_explicit_run_to(void* H, double t_end, int n_threads);
+/* Residual of the implicit system G(W) = 0 (Sec. 3.3) of the last step's blocks, max over blocks;
+ * recorded when the dual-time loop ends (diagnostic for tests). */
+double orc_last_implicit_residual(void* H, int inst);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,204 @@
+"""Scheme-level pins of the CPU oracle (no GPU): conservation, preserved states, mirror symmetry,
+convergence to the exact Riemann solution, agreement with a fully explicit run on the same grid, and
+the converged dual-time iterate solving the implicit system of Sec. 3.3."""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+from oracle import pyoracle as P
+from paper_2211_00705_gb300 import inputs as I
+
+
+def riemann(N, alpha, rl, ul, rv, uv, tau, jfrac=0.5, opts=None, t_end=1e-4, fluid=None):
+    """One liquid | vapour instance on [0, 1] with chosen states (layout of the input module)."""
+    b = I.riemann_batch(0, 1, n_range=(N, N), alpha_range=(alpha, alpha), coef_range=(1, 1),
+                        rho_liq=(rl, rl), rho_vap=(rv, rv), u_range=(0, 0), pb_range=(jfrac, jfrac),
+                        options=opts or I.Options(), t_end=t_end, fluid=fluid)
+    b.m[:] = np.where(b.phase == 1, b.rho * ul, b.rho * uv)
+    b.tau[:] = tau
+    return b
+
+
+def run(b, **kw):
+    o = P.Oracle(b, **kw)
+    assert o.set_rc == 0
+    if b.t_end > 0:
+        o.run_to(b.t_end)
+    else:
+        o.step(b.n_steps)
+    return o, o.states()
+
+
+def totals(widths, rho, m):
+    return np.sum(widths * rho), np.sum(widths * m)
+
+
+@pytest.mark.parametrize("wid", [0, 1])
+def test_conservation_with_phase_boundary_fluxes(wid):
+    """Sum of h_i U_i changes only by the boundary fluxes (Sec. 3.2: the mixed scheme is conservative,
+    Part 2 of Alg. 2 restores conservation); waves stay inside the domain, so the boundary cells keep
+    their states and the boundary fluxes are those of the initial data."""
+    b = I.workload(wid, scale=8 / 4096) if wid == 1 else I.workload(0)
+    # t_end such that the numerical domain of dependence (one cell per step) stays off the boundary
+    b.t_end = 8e-5 if wid == 1 else 5e-5
+    o, s = run(b)
+    assert (s["status"] == 0).all()
+    fl = b.fluid
+    for k in range(b.n_inst):
+        a0, a1 = b.cell_offsets[k], b.cell_offsets[k + 1]
+        c0, c1 = s["offsets"][k], s["offsets"][k + 1]
+        M0, P0 = totals(b.widths[a0:a1], b.rho[a0:a1], b.m[a0:a1])
+        M1, P1 = totals(s["widths"][c0:c1], s["rho"][c0:c1], s["m"][c0:c1])
+        rl, ml, rr, mr = b.rho[a0], b.m[a0], b.rho[a1 - 1], b.m[a1 - 1]
+        pl = fl.p_sat + fl.a2_liq * (rl - fl.rho0_liq)
+        pr = fl.a2_vap * rr
+        T = s["t"][k]
+        dM = -T * (mr - ml)
+        dP = -T * ((mr * mr / rr + pr) - (ml * ml / rl + pl))
+        assert o.stats()["steps"][k] < 0.34 * b.n_lattice[k]
+        assert abs(M1 - M0 - dM) <= 1e-13 * (abs(M0) + abs(dM))
+        assert abs(P1 - P0 - dP) <= 1e-13 * (abs(P0) + abs(T * pl))
+
+
+def test_uniform_state_is_preserved():
+    """A uniform single-phase state is a fixed point of every flux (consistency of HLL)."""
+    fl = I.workload_fluid()
+    b = riemann(64, 1e-2, 970.0, 3.0, 0.6, 3.0, I.tau_paper())
+    b.phase[:] = 1
+    b.rho[:] = 970.0
+    b.m[:] = 970.0 * 3.0
+    b.widths[:] = 1.0 / 64
+    b.widths = b.widths[:64]
+    b.rho, b.m, b.phase = b.rho[:64], b.m[:64], b.phase[:64]
+    b.cell_offsets[1] = 64
+    o, s = run(b)
+    assert s["status"][0] == 0
+    np.testing.assert_allclose(s["rho"], 970.0, rtol=1e-14)
+    np.testing.assert_allclose(s["m"], 970.0 * 3.0, rtol=1e-13)
+
+
+def test_saturation_equilibrium_moves_without_change():
+    """Liquid at rho0 and vapour at p_sat/a_V^2 with a common velocity: equal Gibbs energies, no mass
+    transfer (z = 0), the boundary is a contact moving with the flow; all states stay exact while the
+    grid follows the boundary (merges and splits included)."""
+    fl = I.workload_fluid()
+    rv = fl.p_sat / fl.a2_vap
+    u = 30.0
+    b = riemann(100, 1e-3, fl.rho0_liq, u, rv, u, I.tau_paper(), t_end=1e-3)
+    o, s = run(b)
+    assert s["status"][0] == 0
+    liq = s["phase"] == 1
+    np.testing.assert_allclose(s["rho"][liq], fl.rho0_liq, rtol=1e-12)
+    np.testing.assert_allclose(s["rho"][~liq], rv, rtol=1e-10)
+    np.testing.assert_allclose(s["m"] / s["rho"], u, rtol=1e-9)
+    x_pb = o.pbs()[1][0]
+    x0 = 0.5 + 1.0 / 100 * (1 - 1e-3)
+    assert x_pb == pytest.approx(x0 + u * s["t"][0], rel=1e-12)
+    st = o.stats()
+    assert st["merges"][0] + st["splits"][0] >= 1   # the boundary crossed background faces
+
+
+def test_mirror_symmetry_of_a_run():
+    """x -> 1 - x, u -> -u: the mirrored run is the mirror image of the run."""
+    fl = I.workload_fluid()
+    b = riemann(80, 1e-2, 975.0, -8.0, 0.45, 6.0, 1e-3 * I.tau_paper(), jfrac=0.4, t_end=1.5e-4)
+    o, s = run(b)
+    bm = dataclasses.replace(b, widths=b.widths[::-1].copy(), rho=b.rho[::-1].copy(), m=-b.m[::-1].copy(),
+                             phase=b.phase[::-1].copy())
+    om, sm = run(bm)
+    assert s["status"][0] == 0 and sm["status"][0] == 0
+    assert len(s["rho"]) == len(sm["rho"])
+    np.testing.assert_allclose(sm["rho"][::-1], s["rho"], rtol=1e-9)
+    np.testing.assert_allclose(-sm["m"][::-1], s["m"], rtol=1e-8, atol=1e-8 * np.abs(s["m"]).max())
+    np.testing.assert_allclose(sm["widths"][::-1], s["widths"], rtol=1e-9, atol=1e-15)
+
+
+def _l1_error(b, s, t):
+    """L1 distance of the cell averages from the exact solution (App. A) averaged on 16 sub-points."""
+    fl = b.fluid
+    i = np.where(b.phase[:-1] != b.phase[1:])[0][0]
+    x_pb0 = np.sum(b.widths[: i + 1])
+    rl, ul = b.rho[0], b.m[0] / b.rho[0]
+    rr, ur = b.rho[-1], b.m[-1] / b.rho[-1]
+    edges = np.concatenate([[0.0], np.cumsum(s["widths"])])
+    sub = (np.arange(16) + 0.5) / 16
+    xs = (edges[:-1, None] + sub[None, :] * s["widths"][:, None]).ravel()
+    rho_ex, u_ex, ph_ex = P.exact_sample(fl, b.options, b.tau[0], 1, rl, ul, 0, rr, ur, (xs - x_pb0) / t)
+    rho_avg = rho_ex.reshape(-1, 16).mean(axis=1)
+    liq = s["phase"] == 1
+    err_l = np.sum(s["widths"][liq] * np.abs(s["rho"][liq] - rho_avg[liq])) / rl
+    err_v = np.sum(s["widths"][~liq] * np.abs(s["rho"][~liq] - rho_avg[~liq])) / rr
+    return err_l, err_v
+
+
+def test_convergence_to_exact_riemann_solution():
+    """The first-order scheme converges to the exact two-phase Riemann solution (App. A) under grid
+    refinement: L1 errors of both phases fall by at least 2^0.4 per doubling of N."""
+    errs = []
+    for N in (100, 200, 400, 800):
+        b = riemann(N, 1e-3, 972.0, -6.0, 0.40, 4.0, 1e-2 * I.tau_paper(), t_end=1.2e-4)
+        o, s = run(b)
+        assert s["status"][0] == 0
+        errs.append(_l1_error(b, s, s["t"][0]))
+    errs = np.array(errs)
+    rates = np.log2(errs[:-1] / errs[1:])
+    assert (rates > 0.4).all(), (errs, rates)
+
+
+def test_agrees_with_fully_explicit_run():
+    """The mixed scheme and a fully explicit moving-grid run (dt limited by the tiny cell) approximate
+    the same solution: their difference is far below either one's distance to the exact solution."""
+    # liquid near saturation pressure moving away: the boundary moves left and the tiny vapour cell
+    # grows, so the explicit run's smallest cell (and its time step) does not shrink to zero
+    rl = I.workload_fluid().rho0_liq + 0.002
+    b = riemann(200, 1e-2, rl, -6.0, 0.40, 4.0, 1e-2 * I.tau_paper(), t_end=1.0e-4)
+    o, s = run(b)
+    oe = P.Oracle(b)
+    oe.explicit_run_to(b.t_end)
+    se = oe.states()
+    assert s["status"][0] == 0 and se["status"][0] == 0
+    # compare on the background lattice (piecewise-constant sampling at background centres)
+    xc = (np.arange(200) + 0.5) / 200
+
+    def sample(st):
+        edges = np.concatenate([[0.0], np.cumsum(st["widths"])])
+        k = np.clip(np.searchsorted(edges, xc) - 1, 0, len(st["rho"]) - 1)
+        return st["rho"][k]
+
+    d = np.abs(sample(s) - sample(se))
+    liq = sample(s) > 100
+    el, ev = _l1_error(b, s, b.t_end)
+    print("split-explicit", np.mean(d[liq]) / rl, np.mean(d[~liq]) / 0.40, "exact", el, ev)
+    assert np.mean(d[liq]) / rl < 0.2 * el / 0.5 + 1e-7
+    assert np.mean(d[~liq]) / 0.40 < 0.2 * ev / 0.5 + 1e-7
+    assert abs(o.pbs()[1][0] - oe.pbs()[1][0]) < 1e-2 / 200
+
+
+def test_dual_time_solution_solves_the_implicit_system():
+    """With tight tolerances the dual-time iterate U^{n,*} satisfies the implicit update
+    (G(W) = 0 of Sec. 3.3 with the moving widths of Sec. 3.4) to near round-off."""
+    opts = I.scaled_options(tol_nb=1e-15, tol_k=1e-13)
+    b = riemann(100, 1e-3, 972.0, -6.0, 0.40, 4.0, 1e-2 * I.tau_paper(), opts=opts, t_end=0.0)
+    b.n_steps = 3
+    o, s = run(b)
+    assert s["status"][0] == 0
+    assert o.stats()["maxiter"][0] == 0
+    assert o.implicit_defect(0) < 1e-12
+
+
+def test_dts_iterations_grow_mildly_with_smaller_alpha():
+    """Sec. 4.1: with theta_{k+-1} = 0.9 and theta_k = alpha the dual-time iteration count grows only
+    mildly as alpha falls (far below 1/alpha)."""
+    counts = []
+    for alpha in (1e-2, 1e-4, 1e-6):
+        b = riemann(100, alpha, 972.0, -6.0, 0.40, 4.0, 1e-2 * I.tau_paper(), opts=I.scaled_options(),
+                    t_end=0.0)
+        b.n_steps = 5
+        o, s = run(b)
+        assert s["status"][0] == 0
+        st = o.stats()
+        counts.append(st["dts_iters"][0] / st["steps"][0])
+    assert counts[-1] < 1e3
+    assert counts[-1] < 100 * counts[0]
