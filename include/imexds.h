@@ -1,0 +1,137 @@
+/* imexds: explicit-implicit domain splitting for 1-D isothermal two-phase flow with phase transition
+ * (May & Thein, arXiv 2211.00705), on one NVIDIA GB300 (sm_103a), FP64 throughout.
+ *
+ * One time step (Algorithm 1) is: the CFL time step (Eq. cfl_cond:unif); an explicit HLL sweep over
+ * every cell away from the tiny cells (Algorithm 1, Step 1); and, on the neighbourhood {k-1, k, k+1}
+ * of every tiny cell k next to a phase boundary, dual time stepping (Algorithm 2, Eq. dual time tau
+ * diff) with the phase-boundary Riemann solver of App. A at the implicit faces, followed by the
+ * conservative re-flux of Algorithm 2 Part 2 on the moving grid (Eq. godunov_meth:nonunif, Sec. 3.4).
+ * Grid management (merge/split of cells next to a boundary, Sec. 2.3/3.4) and phase creation
+ * (App. B) run inside the step.
+ *
+ * Units: SI. Phase labels: 0 = vapour, 1 = liquid. A state is (rho, m = rho u) per cell.
+ *
+ * Conventions of every call:
+ *   - every function returns an imexds_status; nothing throws across this interface;
+ *   - host pointers belong to the caller and are only read/written during the call;
+ *   - device memory is owned by the context (allocated in imexds_create, freed in imexds_destroy);
+ *   - the library works on the CUDA stream given to imexds_create (0 = the legacy default stream)
+ *     and returns after the work is complete unless a function says otherwise;
+ *   - a context is used by one host thread at a time.
+ */
+#ifndef IMEXDS_H
+#define IMEXDS_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct imexds_ctx imexds_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  IMEXDS_OK = 0,
+  IMEXDS_ERR_ARG = 1,          /* invalid argument (sizes, a fixed face off the lattice, NULL) */
+  IMEXDS_ERR_CUDA = 2,         /* a CUDA call failed; imexds_last_error_string() has the text */
+  IMEXDS_ERR_NONPHYSICAL = 3,  /* rho <= 0, width <= 0 or a non-finite state after a step */
+  IMEXDS_ERR_PB_NOCONV = 4,    /* the phase-boundary (or phase-creation) Newton iteration failed */
+  IMEXDS_WARN_DTS_MAXITER = 5, /* dual time stepping hit l_max (the last iterate was used) */
+  IMEXDS_ERR_VANISH = 6,       /* a cell between two phase boundaries would vanish (not treated) */
+  IMEXDS_ERR_TIMEOUT = 7,      /* a bounded device wait gave up */
+  IMEXDS_ERR_STATE = 8,        /* call order (e.g. step before set_states) */
+  IMEXDS_ERR_CAPACITY = 9      /* a zone or the zone pool of an instance is full */
+} imexds_status;
+
+/* Equation of state of one phase (Sec. 4, Eq. eos:isoT_idgas and eos:isoT_lintait):
+ *   kind 0 (ideal gas):   p = a2 * rho
+ *   kind 1 (linear Tait): p = p0 + a2 * (rho - rho0)       (a2 = K0 / rho0)
+ * a2 is the squared isothermal sound speed. */
+typedef struct {
+  int kind;
+  double a2, p0, rho0;
+} imexds_eos;
+
+/* Two-phase fluid. p_sat is the saturation pressure, where both Gibbs energies g = a2 ln(rho/rho_sat)
+ * vanish (Sec. 2.1: the Maxwell construction makes them equal there). p_min / p_tilde are the
+ * cavitation / nucleation thresholds of App. B (Table tab:max_vap_lintait363). */
+typedef struct {
+  imexds_eos vapour, liquid;
+  double p_sat, p_min, p_tilde;
+} imexds_fluid;
+
+/* Scheme options. NULL in imexds_create selects the defaults listed. */
+typedef struct {
+  double cfl;          /* C_CFL of Eq. cfl_cond:unif (0.5) */
+  double theta_nb;     /* theta of Alg. 2 for cells of width h; theta_i = min(theta_nb, h_i/h) (0.9, Sec. 4) */
+  double tol_nb, tol_k;/* dual-time stop tolerances of Sec. 4 for neighbours / tiny cells (1e-3, 1e-1) */
+  int res_mode;        /* 0: residual as printed in Sec. 4 (1/s); 1: residual times dt (0) */
+  int l_max;           /* cap on dual-time iterations per block and step (10000) */
+  double newton_tol;   /* relative step tolerance of the phase-boundary Newton iteration (1e-12) */
+  int newton_itmax;    /* cap on Newton iterations (50) */
+  double alpha_min;    /* a boundary cell predicted below max(alpha_min h, h_i/2) is merged (1e-8) */
+  double split_ratio;  /* a boundary cell wider than split_ratio * h is split (2) */
+  int creation;        /* 1: detect cavitation / nucleation at same-phase faces (App. B) (0) */
+  int zone_capacity;   /* zone records per instance (0 = automatic: 4 + 2 * phase boundaries) */
+} imexds_options;
+
+/* A batch of independent 1-D problems on [x_left[i], x_right[i]] with n_lattice[i] background
+ * cells of width h_i = (x_right - x_left)/n_lattice and kinetic coefficient tau[i] > 0 of the kinetic
+ * relation z = tau p_V [[g + e_kin]] (Eq. isoT:kin_rel1). Arrays have n_inst entries. */
+typedef struct {
+  int32_t n_inst;
+  const int32_t* n_lattice;
+  const double* x_left;
+  const double* x_right;
+  const double* tau;
+  imexds_fluid fluid;
+} imexds_problem;
+
+/* Create a context on the current CUDA device. `stream` is a cudaStream_t (NULL = default stream).
+ * Copies everything it needs from `prob`/`opts`. On error *out is NULL. */
+imexds_status imexds_create(const imexds_problem* prob, const imexds_options* opts, void* stream,
+                            imexds_ctx** out);
+
+/* Load the initial cell lists (host arrays). Instance i owns cells [cell_offsets[i], cell_offsets[i+1])
+ * of widths/rho/m/phase. A face between cells of different phase is a phase boundary (Sec. 2.3); every
+ * other face must lie on the background lattice (face positions accumulate the widths from the last
+ * fixed face; tolerance 1e-9 h), and a cell with two fixed faces must be one background cell.
+ * Sets t = t0 for all instances and resets statistics. IMEXDS_ERR_ARG on a malformed list. */
+imexds_status imexds_set_states(imexds_ctx* ctx, const int32_t* cell_offsets, const double* widths,
+                                const double* rho, const double* m, const uint8_t* phase, double t0);
+
+/* Number of cells of every instance now (host array of n_inst entries). */
+imexds_status imexds_cell_counts(imexds_ctx* ctx, int32_t* counts);
+
+/* Copy the cell lists back (host arrays sized from imexds_cell_counts; cell_offsets has n_inst+1
+ * entries). t and inst_status have n_inst entries; inst_status holds an imexds_status per instance. */
+imexds_status imexds_get_states(imexds_ctx* ctx, int32_t* cell_offsets, double* widths, double* rho,
+                                double* m, uint8_t* phase, double* t, int32_t* inst_status);
+
+/* Advance every instance by n_steps time steps (no clipping to an end time). */
+imexds_status imexds_step(imexds_ctx* ctx, int32_t n_steps);
+
+/* Advance every instance until t = t_end (the last step of each instance is shortened to land on
+ * t_end). Finished instances idle. */
+imexds_status imexds_run_to(imexds_ctx* ctx, double t_end);
+
+/* Per-instance counters (n_inst x 10, int64, row-major): steps, dual-time iterations, max dual-time
+ * iterations in one step, Newton iterations, merges, splits, creations, l_max warnings, boundary
+ * solves, kernel launches of the last call (same value in every row). */
+imexds_status imexds_get_stats(imexds_ctx* ctx, int64_t* stats);
+
+/* Device-resident variant of imexds_set_states / imexds_get_states for callers that keep the cell
+ * lists in GPU memory: the same arguments as device pointers (cell_offsets stays a host array). The
+ * copies run on the context's stream. */
+imexds_status imexds_set_states_device(imexds_ctx* ctx, const int32_t* cell_offsets_host,
+                                       const double* widths_d, const double* rho_d, const double* m_d,
+                                       const uint8_t* phase_d, double t0);
+
+void imexds_destroy(imexds_ctx* ctx);
+const char* imexds_status_string(imexds_status s);
+/* Text of the last CUDA error seen by any context of this process (thread-unsafe, static storage). */
+const char* imexds_last_error_string(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

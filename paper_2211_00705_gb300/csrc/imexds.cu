@@ -1,0 +1,1448 @@
+// imexds: CUDA kernels and C-ABI of the explicit-implicit domain-splitting scheme for 1-D isothermal
+// two-phase flow with phase transition (May & Thein, arXiv 2211.00705), FP64, sm_103a.
+//
+// Device layout (per instance, batched):
+//   * background lattice: rho[], m[] (double buffered, parity per instance), phase[] (uint8),
+//     own[] (int32: zone slot that currently owns the lattice cell, -1 if it is an explicit cell);
+//   * zones: fixed-capacity records holding the irregular cells next to phase boundaries (a maximal
+//     run of cells whose faces are not all on the lattice) with their widths, phases, face kinds and
+//     boundary positions. Zones are kept at least ZONE_GAP lattice cells apart (closer zones are
+//     joined), so every step's work on a zone touches no other zone.
+//
+// One time step = five kernels (captured in a CUDA graph by the host loop):
+//   k_pre    (thread per zone)  phase-boundary solves at U^n -> predicted widths -> merge marks (Sec. 3.4)
+//   k_plan   (thread per zone)  merges, tiny cells, implicit blocks {k-1,k,k+1} (Sec. 3.2), owned range
+//   k_sweep  (tile per CTA)     Algorithm 1 Step 1: HLL fluxes and explicit update of every free lattice
+//                               cell; phase-creation detection at free same-phase faces (App. B)
+//   k_dts    (thread per zone)  Algorithm 2 (dual time stepping + Part 2) on the zone's blocks with the
+//                               App. A boundary solver at the implicit faces and the moving widths
+//   k_post   (thread per instance) splits, release of regular cells, creation, t += dt, next dt
+// k_sweep and k_dts read U^n only and write disjoint cells of U^{n+1}.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/imexds.h"
+#include "physics.cuh"
+
+using namespace imexds;
+
+namespace {
+
+constexpr int ZC = 16;            // max cells per zone
+constexpr int ZB = ZC + 2;        // block index space: zone cells plus one pulled lattice cell per side
+constexpr int MAXBLK = ZC;        // max blocks per zone
+constexpr int ZONE_GAP = 4;       // minimum number of lattice cells between two zones
+constexpr int EV_CAP = 4;         // creation events per instance and step
+constexpr int TILE = 256;         // lattice cells per sweep CTA
+constexpr int N_STATS = 9;
+constexpr long long kRunToMaxSteps = 20000000;  // run_to gives up (IMEXDS_ERR_TIMEOUT) after this many steps
+
+struct Zone {
+  int alive, inst, A, B, nc;
+  int merge_mask;
+  int pullL, pullR, oA, oB;
+  int nblk;
+  int blo[MAXBLK], bhi[MAXBLK];  // block ranges in the extended index space (-1 .. nc)
+  unsigned tiny_mask;            // bit (e + 1) set for a tiny extended index e
+  int ph[ZC];
+  int fpb[ZC + 1];               // face k between cells k-1 and k: 1 = phase boundary
+  int fj[ZC + 1];                // lattice index of a fixed face
+  double w[ZC], r[ZC], m[ZC];
+  double fx[ZC + 1];             // position of a phase-boundary face
+  double eL0, eL1, eR0, eR1;     // U^n of the first / last owned cell (read by neighbouring sweep cells)
+};
+
+struct Inst {
+  int N, lat_off, zone_off, zone_cap;
+  double xL, h, tau;
+  double t, dt;
+  int status, active, parity, clipped;
+  unsigned long long smax_bits;
+  int n_ev;
+  long long stats[N_STATS];  // steps, dts_iters, dts_max, newton, merges, splits, creations, maxiter, pb_solves
+};
+
+struct Event {
+  int face;
+  double w1, w2, rhoC, mC, hl, hr;
+  int phC;
+};
+
+struct Ctrl {
+  double t_end;
+  int clip;
+  int n_active;
+};
+
+struct Dev {
+  double* rho[2];
+  double* m[2];
+  unsigned char* phase;
+  int* own;
+  Zone* zones;
+  Inst* inst;
+  Event* ev;
+  int2* tiles;  // (instance, first lattice cell)
+  Ctrl* ctrl;
+};
+
+__constant__ Fluid c_fluid;
+__constant__ Opts c_opts;
+
+__device__ inline void set_status(Inst& I, int code) { atomicCAS(&I.status, 0, code); }
+
+__device__ inline unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+// ------------------------------------------------------------------------------------------ k_pre
+// Phase-boundary solves at U^n predict the widths of the cells next to each boundary; a cell that would
+// fall below max(alpha_min h, h_i / 2) is marked for merging (Sec. 2.3, Sec. 3.4).
+__global__ void k_pre(Dev d, int n_zone_slots) {
+  int zi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (zi >= n_zone_slots) return;
+  Zone& Z = d.zones[zi];
+  Z.merge_mask = 0;
+  if (!Z.alive) return;
+  Inst& I = d.inst[Z.inst];
+  if (!I.active || I.status) return;
+  double dt = I.dt;
+  double wf[ZC + 1];
+  for (int k = 0; k <= Z.nc; ++k) wf[k] = 0.0;
+  long long newton = 0, solves = 0;
+  for (int k = 1; k < Z.nc; ++k) {
+    if (!Z.fpb[k]) continue;
+    PBOut R = pb_solve(c_fluid, c_opts, I.tau, Z.ph[k - 1], Z.r[k - 1], Z.m[k - 1], Z.ph[k], Z.r[k], Z.m[k]);
+    newton += R.iters;
+    solves++;
+    if (!R.ok) {
+      set_status(I, IMEXDS_ERR_PB_NOCONV);
+      return;
+    }
+    wf[k] = R.w;
+  }
+  int mask = 0;
+  for (int i = 0; i < Z.nc; ++i) {
+    if (!(Z.fpb[i] || Z.fpb[i + 1])) continue;
+    double hp = Z.w[i] + (wf[i + 1] - wf[i]) * dt;
+    if (hp < fmax(c_opts.alpha_min * I.h, 0.5 * Z.w[i])) mask |= 1 << i;
+  }
+  Z.merge_mask = mask;
+  atomicAdd((unsigned long long*)&I.stats[3], (unsigned long long)newton);
+  atomicAdd((unsigned long long*)&I.stats[8], (unsigned long long)solves);
+}
+
+// remove cell index b of a zone (faces shift down; face b is removed)
+__device__ inline void zone_erase_cell(Zone& Z, int b) {
+  for (int i = b; i + 1 < Z.nc; ++i) {
+    Z.w[i] = Z.w[i + 1];
+    Z.r[i] = Z.r[i + 1];
+    Z.m[i] = Z.m[i + 1];
+    Z.ph[i] = Z.ph[i + 1];
+  }
+  for (int k = b; k < Z.nc; ++k) {
+    Z.fpb[k] = Z.fpb[k + 1];
+    Z.fj[k] = Z.fj[k + 1];
+    Z.fx[k] = Z.fx[k + 1];
+  }
+  Z.nc--;
+}
+
+// ------------------------------------------------------------------------------------------ k_plan
+// Merges (left to right, a marked cell joins its neighbour across its fixed face), then the implicit
+// neighbourhoods: at every boundary the smaller adjacent cell is the tiny cell k; {k-1, k, k+1} are
+// joined where they overlap. Cells outside the zone taking part (one lattice cell per side) are
+// "pulled": the sweep skips them and k_dts updates them.
+__global__ void k_plan(Dev d, int n_zone_slots) {
+  int zi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (zi >= n_zone_slots) return;
+  Zone& Z = d.zones[zi];
+  if (!Z.alive) return;
+  Inst& I = d.inst[Z.inst];
+  if (!I.active || I.status) return;
+  const int cur = I.parity;
+  const double* lr = d.rho[cur] + I.lat_off;
+  const double* lm = d.m[cur] + I.lat_off;
+  int mark[ZC];
+  for (int i = 0; i < Z.nc; ++i) mark[i] = (Z.merge_mask >> i) & 1;
+  long long merges = 0;
+  for (int i = 0; i < Z.nc; ++i) {
+    if (!mark[i]) continue;
+    bool left_fixed = !Z.fpb[i] && !(i == 0 && Z.A == 0);
+    bool right_fixed = !Z.fpb[i + 1] && !(i == Z.nc - 1 && Z.B == I.N);
+    if (left_fixed) {
+      if (i == 0) {  // join the lattice cell A-1 (free: zones are ZONE_GAP apart)
+        int j = Z.A - 1;
+        double wl = I.h, rl = lr[j], ml = lm[j];
+        double wm = wl + Z.w[0];
+        double rm = (wl * rl + Z.w[0] * Z.r[0]) / wm;
+        double mm = (wl * ml + Z.w[0] * Z.m[0]) / wm;
+        Z.w[0] = wm;
+        Z.r[0] = rm;
+        Z.m[0] = mm;
+        Z.A = j;
+        Z.fj[0] = j;
+        mark[0] = 0;
+      } else {
+        int a = i - 1;
+        double wm = Z.w[a] + Z.w[i];
+        double rm = (Z.w[a] * Z.r[a] + Z.w[i] * Z.r[i]) / wm;
+        double mm = (Z.w[a] * Z.m[a] + Z.w[i] * Z.m[i]) / wm;
+        Z.w[a] = wm;
+        Z.r[a] = rm;
+        Z.m[a] = mm;
+        zone_erase_cell(Z, i);
+        for (int q = i; q < Z.nc; ++q) mark[q] = mark[q + 1];
+        mark[a] = 0;
+        --i;
+      }
+    } else if (right_fixed) {
+      if (i == Z.nc - 1) {  // join the lattice cell B
+        int j = Z.B;
+        double wr = I.h, rr = lr[j], mr = lm[j];
+        double wm = Z.w[i] + wr;
+        double rm = (Z.w[i] * Z.r[i] + wr * rr) / wm;
+        double mm = (Z.w[i] * Z.m[i] + wr * mr) / wm;
+        Z.w[i] = wm;
+        Z.r[i] = rm;
+        Z.m[i] = mm;
+        Z.B = j + 1;
+        Z.fj[Z.nc] = j + 1;
+      } else {
+        int b = i + 1;
+        double wm = Z.w[i] + Z.w[b];
+        double rm = (Z.w[i] * Z.r[i] + Z.w[b] * Z.r[b]) / wm;
+        double mm = (Z.w[i] * Z.m[i] + Z.w[b] * Z.m[b]) / wm;
+        Z.w[i] = wm;
+        Z.r[i] = rm;
+        Z.m[i] = mm;
+        zone_erase_cell(Z, b);
+        for (int q = b; q < Z.nc; ++q) mark[q] = mark[q + 1];
+      }
+      mark[i] = 0;
+    } else {
+      set_status(I, IMEXDS_ERR_VANISH);
+      return;
+    }
+    merges++;
+  }
+  if (merges) atomicAdd((unsigned long long*)&I.stats[4], (unsigned long long)merges);
+  // implicit neighbourhoods in the extended index space
+  int emin = (Z.A > 0) ? -1 : 0;
+  int emax = (Z.B < I.N) ? Z.nc : Z.nc - 1;
+  int nblk = 0;
+  unsigned tiny = 0;
+  for (int k = 1; k < Z.nc; ++k) {
+    if (!Z.fpb[k]) continue;
+    int kt = (Z.w[k - 1] < Z.w[k]) ? k - 1 : k;
+    tiny |= 1u << (kt + 1);
+    int lo = max(kt - 1, emin), hi = min(kt + 1, emax);
+    if (nblk > 0 && lo <= Z.bhi[nblk - 1]) {
+      Z.bhi[nblk - 1] = max(Z.bhi[nblk - 1], hi);
+    } else {
+      if (nblk == MAXBLK) {
+        set_status(I, IMEXDS_ERR_CAPACITY);
+        return;
+      }
+      Z.blo[nblk] = lo;
+      Z.bhi[nblk] = hi;
+      nblk++;
+    }
+  }
+  Z.nblk = nblk;
+  Z.tiny_mask = tiny;
+  Z.pullL = (nblk > 0 && Z.blo[0] == -1) ? 1 : 0;
+  Z.pullR = (nblk > 0 && Z.bhi[nblk - 1] == Z.nc) ? 1 : 0;
+  Z.oA = Z.A - Z.pullL;
+  Z.oB = Z.B + Z.pullR;
+  if (Z.pullL) {
+    Z.eL0 = lr[Z.A - 1];
+    Z.eL1 = lm[Z.A - 1];
+  } else {
+    Z.eL0 = Z.r[0];
+    Z.eL1 = Z.m[0];
+  }
+  if (Z.pullR) {
+    Z.eR0 = lr[Z.B];
+    Z.eR1 = lm[Z.B];
+  } else {
+    Z.eR0 = Z.r[Z.nc - 1];
+    Z.eR1 = Z.m[Z.nc - 1];
+  }
+  int* own = d.own + I.lat_off;
+  for (int j = Z.oA; j < Z.oB; ++j) own[j] = zi;
+}
+
+// ------------------------------------------------------------------------------------------ k_sweep
+// Algorithm 1, Step 1 on one tile of free lattice cells: HLL fluxes from U^n, the explicit update of
+// Eq. update expl time (Eq. godunov_meth:nonunif next to a creation face), and the next step's
+// wave-speed maximum. Faces next to a zone see the zone's edge state.
+__global__ void __launch_bounds__(TILE) k_sweep(Dev d) {
+  __shared__ double sr[TILE + 3], sm[TILE + 3];
+  __shared__ int sown[TILE + 3];
+  __shared__ unsigned char sph[TILE + 3];
+  __shared__ double F0L[TILE + 1], F1L[TILE + 1], F0R[TILE + 1], F1R[TILE + 1], WL[TILE + 1], WR[TILE + 1];
+  __shared__ int sdet[TILE + 2];
+  __shared__ double red[TILE / 32];
+  const int2 tile = d.tiles[blockIdx.x];
+  Inst& I = d.inst[tile.x];
+  if (!I.active || I.status) return;
+  const int N = I.N, j0 = tile.y, cur = I.parity;
+  const int nt = min(TILE, N - j0);
+  const double* lr = d.rho[cur] + I.lat_off;
+  const double* lm = d.m[cur] + I.lat_off;
+  double* nr = d.rho[cur ^ 1] + I.lat_off;
+  double* nm = d.m[cur ^ 1] + I.lat_off;
+  const unsigned char* lph = d.phase + I.lat_off;
+  const int* lown = d.own + I.lat_off;
+  const double h = I.h, dt = I.dt;
+  // cells j0-2 .. j0+nt (index q = j - j0 + 2)
+  for (int q = threadIdx.x; q < nt + 3; q += blockDim.x) {
+    int j = j0 - 2 + q;
+    if (j >= 0 && j < N) {
+      sown[q] = lown[j];
+      sph[q] = lph[j];
+      if (sown[q] < 0) {
+        sr[q] = lr[j];
+        sm[q] = lm[j];
+      }
+    } else {
+      sown[q] = -2;  // outside the domain
+    }
+  }
+  __syncthreads();
+  const bool creation = c_opts.creation != 0;
+  // detection at faces f = j0-1 .. j0+nt (index t = f - j0 + 1), only between two free cells
+  if (creation) {
+    for (int t = threadIdx.x; t < nt + 2; t += blockDim.x) {
+      int q = t + 1;  // right cell of face f has index q = f - j0 + 2 = t + 1
+      int det = 0;
+      if (q >= 1 && q < nt + 3 && sown[q - 1] == -1 && sown[q] == -1) {
+        int P = sph[q];
+        double ps = nopt_star(c_fluid.ph[P], sr[q - 1], sm[q - 1] / sr[q - 1], sr[q], sm[q] / sr[q]);
+        det = (P == LIQ) ? (ps < c_fluid.p_min) : (ps > c_fluid.p_tilde);
+      }
+      sdet[t] = det;
+    }
+    __syncthreads();
+  }
+  // fluxes at faces f = j0 .. j0+nt (index t = f - j0)
+  for (int t = threadIdx.x; t <= nt; t += blockDim.x) {
+    int f = j0 + t;
+    int ql = t + 1, qr = t + 2;  // left / right cell indices in shared memory
+    double a0, a1;
+    bool need = (t < nt && sown[qr] == -1) || (t > 0 && sown[ql] == -1) || (t == 0 && sown[qr] == -1) ||
+                (t == nt && sown[ql] == -1);
+    WL[t] = 0.0;
+    WR[t] = 0.0;
+    if (!need) {
+      F0L[t] = F1L[t] = F0R[t] = F1R[t] = 0.0;
+      continue;
+    }
+    if (f == 0) {
+      phys_flux(c_fluid.ph[sph[qr]], sr[qr], sm[qr], a0, a1);
+    } else if (f == N) {
+      phys_flux(c_fluid.ph[sph[ql]], sr[ql], sm[ql], a0, a1);
+    } else {
+      double rl, ml, rr, mr;
+      int P;
+      if (sown[ql] >= 0) {
+        const Zone& Z = d.zones[sown[ql]];
+        rl = Z.eR0;
+        ml = Z.eR1;
+        P = sph[qr];
+      } else {
+        rl = sr[ql];
+        ml = sm[ql];
+        P = sph[ql];
+      }
+      if (sown[qr] >= 0) {
+        const Zone& Z = d.zones[sown[qr]];
+        rr = Z.eL0;
+        mr = Z.eL1;
+      } else {
+        rr = sr[qr];
+        mr = sm[qr];
+      }
+      if (creation && sdet[t + 1] && !sdet[t]) {
+        // App. B: create a cell of the other phase at this face (fluxes of Eq. flux:cavitation /
+        // flux:nucleation with each boundary's own mass flux)
+        CreateOut C = creation_solve(c_fluid, c_opts, I.tau, P, rl, ml, rr, mr);
+        atomicAdd((unsigned long long*)&I.stats[3], (unsigned long long)C.iters);
+        if (!C.ok) {
+          set_status(I, IMEXDS_ERR_PB_NOCONV);
+          F0L[t] = F1L[t] = F0R[t] = F1R[t] = 0.0;
+          continue;
+        }
+        F0L[t] = -C.z1;
+        F1L[t] = -C.z1 * C.uC + C.pC;
+        F0R[t] = -C.z2;
+        F1R[t] = -C.z2 * C.uC + C.pC;
+        WL[t] = C.w1;
+        WR[t] = C.w2;
+        if (t < nt) {  // the tile owning the right cell records the event
+          int k = atomicAdd(&I.n_ev, 1);
+          if (k < EV_CAP) {
+            Event& E = d.ev[tile.x * EV_CAP + k];
+            E.face = f;
+            E.w1 = C.w1;
+            E.w2 = C.w2;
+            E.rhoC = C.rhoC;
+            E.mC = C.rhoC * C.uC;
+            E.phC = 1 - P;
+            E.hl = h + (C.w1 - 0.0) * dt;
+            E.hr = h + (0.0 - C.w2) * dt;
+          } else {
+            set_status(I, IMEXDS_ERR_CAPACITY);
+          }
+        }
+        continue;
+      }
+      hll(c_fluid.ph[P], rl, ml, rr, mr, a0, a1);
+    }
+    F0L[t] = F0R[t] = a0;
+    F1L[t] = F1R[t] = a1;
+  }
+  __syncthreads();
+  double smax = 0.0;
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+    int q = t + 2;
+    if (sown[q] != -1) continue;
+    int j = j0 + t;
+    double hnp1 = h + (WL[t + 1] - WR[t]) * dt;
+    double r1 = (h * sr[q] - dt * (F0L[t + 1] - F0R[t])) / hnp1;
+    double m1 = (h * sm[q] - dt * (F1L[t + 1] - F1R[t])) / hnp1;
+    nr[j] = r1;
+    nm[j] = m1;
+    if (!(r1 > 0.0) || !isfinite(r1) || !isfinite(m1)) set_status(I, IMEXDS_ERR_NONPHYSICAL);
+    smax = fmax(smax, fabs(m1 / r1) + c_fluid.ph[sph[q]].a);
+  }
+  for (int off = 16; off > 0; off >>= 1) smax = fmax(smax, __shfl_down_sync(0xffffffffu, smax, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = smax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = fmax(s, red[w]);
+    if (s > 0.0) atomicMax(&I.smax_bits, dbits(s));
+  }
+}
+
+// ------------------------------------------------------------------------------------------ k_dts
+// Algorithm 2 on the blocks of one zone: dual time stepping (Eq. dual time tau diff) with local
+// pseudo steps dtau_i = theta_i dt, theta_i = min(theta_nb, h_i^n/h), fluxes at the implicit faces from
+// the App. A solver and width iterates h_i^{n,l+1} = h_i^n + (w_{i+1/2} - w_{i-1/2}) dt (Sec. 3.4); stop
+// test of Sec. 4; Part 2 re-flux with F_left/F_right from U^n. Zone cells outside every block take the
+// explicit update.
+struct BlockCtx {
+  double r[ZB], m[ZB], w[ZB];
+  int ph[ZB];
+  int fpb[ZB + 1];  // face q between local cells q-1 and q
+};
+
+__device__ inline bool block_fluxes(const BlockCtx& B, int lo, int hi, const double* Wr, const double* Wm,
+                                    double FL0, double FL1, double FR0, double FR1, double tau, double dt,
+                                    double* F0, double* F1, double* wc, double* hl, long long& newton,
+                                    long long& solves, bool& nonconv) {
+  F0[lo] = FL0;
+  F1[lo] = FL1;
+  F0[hi + 1] = FR0;
+  F1[hi + 1] = FR1;
+  wc[lo] = 0.0;
+  wc[hi + 1] = 0.0;
+  for (int g = lo + 1; g <= hi; ++g) {
+    if (B.fpb[g]) {
+      PBOut R = pb_solve(c_fluid, c_opts, tau, B.ph[g - 1], Wr[g - 1], Wm[g - 1], B.ph[g], Wr[g], Wm[g]);
+      newton += R.iters;
+      solves++;
+      if (!R.ok) {
+        nonconv = true;
+        return false;
+      }
+      F0[g] = R.F0;
+      F1[g] = R.F1;
+      wc[g] = R.w;
+    } else {
+      hll(c_fluid.ph[B.ph[g]], Wr[g - 1], Wm[g - 1], Wr[g], Wm[g], F0[g], F1[g]);
+      wc[g] = 0.0;
+    }
+  }
+  for (int i = lo; i <= hi; ++i) hl[i] = B.w[i] + (wc[i + 1] - wc[i]) * dt;
+  for (int i = lo; i <= hi; ++i)
+    if (!(hl[i] > 0.0)) return false;
+  return true;
+}
+
+__global__ void k_dts(Dev d, int n_zone_slots) {
+  int zi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (zi >= n_zone_slots) return;
+  Zone& Z = d.zones[zi];
+  if (!Z.alive) return;
+  Inst& I = d.inst[Z.inst];
+  if (!I.active || I.status) return;
+  const int cur = I.parity;
+  const double* lr = d.rho[cur] + I.lat_off;
+  const double* lm = d.m[cur] + I.lat_off;
+  double* nr = d.rho[cur ^ 1] + I.lat_off;
+  double* nm = d.m[cur ^ 1] + I.lat_off;
+  const unsigned char* lph = d.phase + I.lat_off;
+  const double dt = I.dt, h = I.h, tau = I.tau;
+  const int N = I.N;
+  BlockCtx B;
+  const int e0 = -Z.pullL;              // first extended index
+  const int nq = Z.nc + Z.pullL + Z.pullR;
+  // local cells q = e - e0
+  for (int q = 0; q < nq; ++q) {
+    int e = q + e0;
+    if (e < 0) {
+      B.r[q] = lr[Z.A - 1];
+      B.m[q] = lm[Z.A - 1];
+      B.w[q] = h;
+      B.ph[q] = lph[Z.A - 1];
+    } else if (e >= Z.nc) {
+      B.r[q] = lr[Z.B];
+      B.m[q] = lm[Z.B];
+      B.w[q] = h;
+      B.ph[q] = lph[Z.B];
+    } else {
+      B.r[q] = Z.r[e];
+      B.m[q] = Z.m[e];
+      B.w[q] = Z.w[e];
+      B.ph[q] = Z.ph[e];
+    }
+  }
+  for (int q = 0; q <= nq; ++q) {
+    int e = q + e0;  // face between extended cells e-1 and e
+    B.fpb[q] = (e >= 1 && e <= Z.nc - 1) ? Z.fpb[e] : 0;
+  }
+  // explicit fluxes at U^n on every face that is not a phase boundary (block outer faces and the faces
+  // of zone cells outside the blocks)
+  double Fx0[ZB + 1], Fx1[ZB + 1];
+  for (int q = 0; q <= nq; ++q) {
+    if (B.fpb[q]) {
+      Fx0[q] = Fx1[q] = 0.0;
+      continue;
+    }
+    if (q == 0) {
+      if (Z.oA > 0)
+        hll(c_fluid.ph[B.ph[0]], lr[Z.oA - 1], lm[Z.oA - 1], B.r[0], B.m[0], Fx0[q], Fx1[q]);
+      else
+        phys_flux(c_fluid.ph[B.ph[0]], B.r[0], B.m[0], Fx0[q], Fx1[q]);
+    } else if (q == nq) {
+      if (Z.oB < N)
+        hll(c_fluid.ph[B.ph[nq - 1]], B.r[nq - 1], B.m[nq - 1], lr[Z.oB], lm[Z.oB], Fx0[q], Fx1[q]);
+      else
+        phys_flux(c_fluid.ph[B.ph[nq - 1]], B.r[nq - 1], B.m[nq - 1], Fx0[q], Fx1[q]);
+    } else {
+      hll(c_fluid.ph[B.ph[q]], B.r[q - 1], B.m[q - 1], B.r[q], B.m[q], Fx0[q], Fx1[q]);
+    }
+  }
+  int inblk[ZB];
+  for (int q = 0; q < nq; ++q) inblk[q] = 0;
+  for (int b = 0; b < Z.nblk; ++b)
+    for (int q = Z.blo[b] - e0; q <= Z.bhi[b] - e0; ++q) inblk[q] = 1;
+  double out_r[ZB], out_m[ZB], out_w[ZB];
+  for (int q = 0; q < nq; ++q) {
+    out_w[q] = B.w[q];
+    if (inblk[q]) continue;
+    double hnp1 = B.w[q] + (0.0 - 0.0) * dt;
+    out_r[q] = (B.w[q] * B.r[q] - dt * (Fx0[q + 1] - Fx0[q])) / hnp1;
+    out_m[q] = (B.w[q] * B.m[q] - dt * (Fx1[q + 1] - Fx1[q])) / hnp1;
+  }
+  long long newton = 0, solves = 0, iters_sum = 0, iters_max = 0, maxiter = 0;
+  double xpb_new[ZB + 1];
+  int moved[ZB + 1];
+  for (int q = 0; q <= nq; ++q) moved[q] = 0;
+  for (int b = 0; b < Z.nblk; ++b) {
+    const int lo = Z.blo[b] - e0, hi = Z.bhi[b] - e0;
+    const double FL0 = Fx0[lo], FL1 = Fx1[lo], FR0 = Fx0[hi + 1], FR1 = Fx1[hi + 1];
+    double Wr[ZB], Wm[ZB], Nr[ZB], Nm[ZB], theta[ZB], F0[ZB + 1], F1[ZB + 1], wc[ZB + 1], hl[ZB];
+    for (int q = 0; q < nq; ++q) {
+      Wr[q] = B.r[q];
+      Wm[q] = B.m[q];
+    }
+    for (int q = lo; q <= hi; ++q) theta[q] = fmin(c_opts.theta_nb, B.w[q] / h);
+    bool stop = false, nonconv = false;
+    int l;
+    for (l = 0; l < c_opts.l_max && !stop; ++l) {
+      if (!block_fluxes(B, lo, hi, Wr, Wm, FL0, FL1, FR0, FR1, tau, dt, F0, F1, wc, hl, newton, solves, nonconv)) {
+        set_status(I, nonconv ? IMEXDS_ERR_PB_NOCONV : IMEXDS_ERR_VANISH);
+        return;
+      }
+      double res_nb = 0.0, res_k = 0.0;
+      for (int q = lo; q <= hi; ++q) {
+        double th = theta[q];
+        double tr = B.w[q] / hl[q] * B.r[q] - dt / hl[q] * (F0[q + 1] - F0[q]);
+        double tm = B.w[q] / hl[q] * B.m[q] - dt / hl[q] * (F1[q + 1] - F1[q]);
+        Nr[q] = (Wr[q] + th * tr) / (1.0 + th);
+        Nm[q] = (Wm[q] + th * tm) / (1.0 + th);
+        double dtau = th * dt;
+        double e0r = (1.0 + th) * fabs(Nr[q] - Wr[q]) / (dtau * fmax(fabs(Wr[q]), 1.0));
+        double e1m = (1.0 + th) * fabs(Nm[q] - Wm[q]) / (dtau * fmax(fabs(Wm[q]), 1.0));
+        double res = fmax(e0r, e1m);
+        if (c_opts.res_mode == 1) res *= dt;
+        if ((Z.tiny_mask >> (q + e0 + 1)) & 1u)
+          res_k = fmax(res_k, res);
+        else
+          res_nb = fmax(res_nb, res);
+      }
+      for (int q = lo; q <= hi; ++q) {
+        Wr[q] = Nr[q];
+        Wm[q] = Nm[q];
+      }
+      if (res_nb < c_opts.tol_nb && res_k < c_opts.tol_k) stop = true;
+    }
+    if (!stop) maxiter++;
+    iters_sum += l;
+    iters_max = max(iters_max, (long long)l);
+    if (!block_fluxes(B, lo, hi, Wr, Wm, FL0, FL1, FR0, FR1, tau, dt, F0, F1, wc, hl, newton, solves, nonconv)) {
+      set_status(I, nonconv ? IMEXDS_ERR_PB_NOCONV : IMEXDS_ERR_VANISH);
+      return;
+    }
+    for (int q = lo; q <= hi; ++q) {
+      out_r[q] = (B.w[q] * B.r[q] - dt * (F0[q + 1] - F0[q])) / hl[q];
+      out_m[q] = (B.w[q] * B.m[q] - dt * (F1[q + 1] - F1[q])) / hl[q];
+      out_w[q] = hl[q];
+    }
+    for (int g = lo + 1; g <= hi; ++g)
+      if (B.fpb[g]) {
+        int e = g + e0;
+        moved[g] = 1;
+        xpb_new[g] = Z.fx[e] + wc[g] * dt;
+      }
+  }
+  double smax = 0.0;
+  for (int q = 0; q < nq; ++q) {
+    int e = q + e0;
+    double r1 = out_r[q], m1 = out_m[q];
+    if (!(r1 > 0.0) || !isfinite(r1) || !isfinite(m1) || !(out_w[q] > 0.0)) set_status(I, IMEXDS_ERR_NONPHYSICAL);
+    smax = fmax(smax, fabs(m1 / r1) + c_fluid.ph[B.ph[q]].a);
+    if (e < 0) {
+      nr[Z.A - 1] = r1;
+      nm[Z.A - 1] = m1;
+    } else if (e >= Z.nc) {
+      nr[Z.B] = r1;
+      nm[Z.B] = m1;
+    } else {
+      Z.r[e] = r1;
+      Z.m[e] = m1;
+      Z.w[e] = out_w[q];
+    }
+  }
+  for (int q = 1; q < nq; ++q)
+    if (moved[q]) Z.fx[q + e0] = xpb_new[q];
+  if (smax > 0.0) atomicMax(&I.smax_bits, dbits(smax));
+  atomicAdd((unsigned long long*)&I.stats[1], (unsigned long long)iters_sum);
+  atomicMax((unsigned long long*)&I.stats[2], (unsigned long long)iters_max);
+  atomicAdd((unsigned long long*)&I.stats[3], (unsigned long long)newton);
+  atomicAdd((unsigned long long*)&I.stats[7], (unsigned long long)maxiter);
+  atomicAdd((unsigned long long*)&I.stats[8], (unsigned long long)solves);
+}
+
+// ------------------------------------------------------------------------------------------ k_post
+// Grid management after the step (Sec. 2.3, 3.4) and phase creation (App. B), one thread per instance:
+// split boundary cells wider than split_ratio*h (keeping fixed faces on the lattice), return regular
+// cells at the zone ends to the lattice, turn creation events into zones, join zones closer than
+// ZONE_GAP, then advance t and set the next dt from the wave-speed maximum.
+__device__ inline int zone_insert_cell(Zone& Z, int pos) {
+  if (Z.nc >= ZC) return 0;
+  for (int i = Z.nc; i > pos; --i) {
+    Z.w[i] = Z.w[i - 1];
+    Z.r[i] = Z.r[i - 1];
+    Z.m[i] = Z.m[i - 1];
+    Z.ph[i] = Z.ph[i - 1];
+  }
+  for (int k = Z.nc + 1; k > pos; --k) {
+    Z.fpb[k] = Z.fpb[k - 1];
+    Z.fj[k] = Z.fj[k - 1];
+    Z.fx[k] = Z.fx[k - 1];
+  }
+  Z.nc++;
+  return 1;
+}
+
+__global__ void k_post(Dev d, int n_inst) {
+  int ii = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ii >= n_inst) return;
+  Inst& I = d.inst[ii];
+  if (!I.active) return;
+  const double h = I.h;
+  int* own = d.own + I.lat_off;
+  const int nxt = I.parity ^ 1;
+  double* nr = d.rho[nxt] + I.lat_off;
+  double* nm = d.m[nxt] + I.lat_off;
+  unsigned char* lph = d.phase + I.lat_off;
+  Zone* zones = d.zones + I.zone_off;
+  for (int z = 0; z < I.zone_cap; ++z) {
+    Zone& Z = zones[z];
+    if (!Z.alive) continue;
+    for (int j = Z.oA; j < Z.oB; ++j) own[j] = -1;
+    Z.oA = Z.oB = 0;
+  }
+  if (I.status) {
+    I.active = 0;
+    I.n_ev = 0;
+    return;
+  }
+  long long splits = 0, creations = 0;
+  // splits
+  for (int z = 0; z < I.zone_cap; ++z) {
+    Zone& Z = zones[z];
+    if (!Z.alive) continue;
+    for (int i = 0; i < Z.nc; ++i) {
+      bool lpb = Z.fpb[i], rpb = Z.fpb[i + 1];
+      if (!(lpb || rpb) || !(Z.w[i] > c_opts.split_ratio * h)) continue;
+      double w1, w2;
+      int jc;
+      if (!lpb) {
+        jc = Z.fj[i] + 1;
+        w1 = h;
+        w2 = Z.w[i] - h;
+      } else if (!rpb) {
+        jc = Z.fj[i + 1] - 1;
+        w2 = h;
+        w1 = Z.w[i] - h;
+      } else {
+        double xm = 0.5 * (Z.fx[i] + Z.fx[i + 1]);
+        jc = (int)llround((xm - I.xL) / h);
+        w1 = (I.xL + (double)jc * h) - Z.fx[i];
+        w2 = Z.w[i] - w1;
+        if (!(w1 > 0.0) || !(w2 > 0.0)) continue;
+      }
+      if (!zone_insert_cell(Z, i + 1)) {
+        set_status(I, IMEXDS_ERR_CAPACITY);
+        break;
+      }
+      // insert_cell shifted faces >= i+1 up; the new face i+1 is the split face
+      Z.fpb[i + 1] = 0;
+      Z.fj[i + 1] = jc;
+      Z.fx[i + 1] = 0.0;
+      Z.w[i] = w1;
+      Z.w[i + 1] = w2;
+      Z.r[i + 1] = Z.r[i];
+      Z.m[i + 1] = Z.m[i];
+      Z.ph[i + 1] = Z.ph[i];
+      splits++;
+      ++i;
+    }
+  }
+  // release regular cells at the zone ends back to the lattice (a pure change of representation)
+  for (int z = 0; z < I.zone_cap; ++z) {
+    Zone& Z = zones[z];
+    if (!Z.alive) continue;
+    while (Z.nc > 1 && !Z.fpb[1] && Z.fj[1] == Z.A + 1 && Z.w[0] == h) {
+      nr[Z.A] = Z.r[0];
+      nm[Z.A] = Z.m[0];
+      lph[Z.A] = (unsigned char)Z.ph[0];
+      zone_erase_cell(Z, 0);
+      Z.A += 1;
+      Z.fj[0] = Z.A;
+      Z.fpb[0] = 0;
+    }
+    while (Z.nc > 1 && !Z.fpb[Z.nc - 1] && Z.fj[Z.nc - 1] == Z.B - 1 && Z.w[Z.nc - 1] == h) {
+      nr[Z.B - 1] = Z.r[Z.nc - 1];
+      nm[Z.B - 1] = Z.m[Z.nc - 1];
+      lph[Z.B - 1] = (unsigned char)Z.ph[Z.nc - 1];
+      Z.nc--;
+      Z.B -= 1;
+      Z.fj[Z.nc] = Z.B;
+      Z.fpb[Z.nc] = 0;
+    }
+  }
+  double smax = __longlong_as_double((long long)I.smax_bits);
+  // creation events -> new zones
+  int nev = min(I.n_ev, EV_CAP);
+  for (int k = 0; k < nev; ++k) {
+    const Event& E = d.ev[ii * EV_CAP + k];
+    int slot = -1;
+    for (int z = 0; z < I.zone_cap; ++z)
+      if (!zones[z].alive) {
+        slot = z;
+        break;
+      }
+    if (slot < 0) {
+      set_status(I, IMEXDS_ERR_CAPACITY);
+      break;
+    }
+    Zone& Z = zones[slot];
+    int f = E.face;
+    double xf = I.xL + (double)f * h;
+    Z.alive = 1;
+    Z.inst = ii;
+    Z.A = f - 1;
+    Z.B = f + 1;
+    Z.nc = 3;
+    Z.ph[0] = lph[f - 1];
+    Z.ph[1] = E.phC;
+    Z.ph[2] = lph[f];
+    Z.w[0] = E.hl;
+    Z.w[1] = (E.w2 - E.w1) * I.dt;
+    Z.w[2] = E.hr;
+    Z.r[0] = nr[f - 1];
+    Z.m[0] = nm[f - 1];
+    Z.r[1] = E.rhoC;
+    Z.m[1] = E.mC;
+    Z.r[2] = nr[f];
+    Z.m[2] = nm[f];
+    Z.fpb[0] = 0;
+    Z.fj[0] = f - 1;
+    Z.fpb[1] = 1;
+    Z.fx[1] = xf + E.w1 * I.dt;
+    Z.fpb[2] = 1;
+    Z.fx[2] = xf + E.w2 * I.dt;
+    Z.fpb[3] = 0;
+    Z.fj[3] = f + 1;
+    Z.oA = Z.oB = 0;
+    Z.merge_mask = 0;
+    smax = fmax(smax, fabs(E.mC / E.rhoC) + c_fluid.ph[E.phC].a);
+    creations++;
+  }
+  I.n_ev = 0;
+  // join zones closer than ZONE_GAP lattice cells (insertion sort by A, then sweep)
+  for (bool again = true; again;) {
+    again = false;
+    for (int a = 0; a < I.zone_cap && !again; ++a) {
+      Zone& Za = zones[a];
+      if (!Za.alive) continue;
+      int best = -1;
+      for (int b = 0; b < I.zone_cap; ++b) {
+        if (b == a || !zones[b].alive || zones[b].A < Za.B) continue;
+        if (best < 0 || zones[b].A < zones[best].A) best = b;
+      }
+      if (best < 0) continue;
+      Zone& Zb = zones[best];
+      int gap = Zb.A - Za.B;
+      if (gap >= ZONE_GAP) continue;
+      if (Za.nc + gap + Zb.nc > ZC) {
+        set_status(I, IMEXDS_ERR_CAPACITY);
+        break;
+      }
+      for (int j = Za.B; j < Zb.A; ++j) {  // absorb the regular lattice cells in between
+        int i = Za.nc;
+        Za.w[i] = h;
+        Za.r[i] = nr[j];
+        Za.m[i] = nm[j];
+        Za.ph[i] = lph[j];
+        Za.fpb[i] = 0;
+        Za.fj[i] = j;
+        Za.nc++;
+      }
+      for (int i = 0; i < Zb.nc; ++i) {
+        int k = Za.nc;
+        Za.w[k] = Zb.w[i];
+        Za.r[k] = Zb.r[i];
+        Za.m[k] = Zb.m[i];
+        Za.ph[k] = Zb.ph[i];
+        Za.fpb[k] = Zb.fpb[i];
+        Za.fj[k] = Zb.fj[i];
+        Za.fx[k] = Zb.fx[i];
+        Za.nc++;
+      }
+      Za.fpb[Za.nc] = 0;
+      Za.fj[Za.nc] = Zb.B;
+      Za.B = Zb.B;
+      Zb.alive = 0;
+      again = true;
+    }
+  }
+  if (splits) I.stats[5] += splits;
+  if (creations) I.stats[6] += creations;
+  // time and next step
+  const Ctrl& C = *d.ctrl;
+  I.t = I.clipped ? C.t_end : I.t + I.dt;
+  I.stats[0] += 1;
+  I.parity = nxt;
+  I.smax_bits = 0ull;
+  if (I.status) {
+    I.active = 0;
+    return;
+  }
+  double dtn = c_opts.cfl * h / smax;
+  I.clipped = 0;
+  if (C.clip) {
+    if (!(I.t < C.t_end)) {
+      I.active = 0;
+      return;
+    }
+    if (C.t_end - I.t <= dtn) {
+      dtn = C.t_end - I.t;
+      I.clipped = 1;
+    }
+  }
+  I.dt = dtn;
+}
+
+// Wave-speed maximum over all cells of every instance and the first dt (before the first step).
+__global__ void k_init_dt(Dev d, int n_inst) {
+  int ii = blockIdx.x;
+  if (ii >= n_inst) return;
+  Inst& I = d.inst[ii];
+  if (I.status) {
+    if (threadIdx.x == 0) I.active = 0;
+    return;
+  }
+  const int cur = I.parity;
+  const double* lr = d.rho[cur] + I.lat_off;
+  const double* lm = d.m[cur] + I.lat_off;
+  const unsigned char* lph = d.phase + I.lat_off;
+  const int* own = d.own + I.lat_off;
+  double s = 0.0;
+  for (int j = threadIdx.x; j < I.N; j += blockDim.x)
+    if (own[j] < 0) s = fmax(s, fabs(lm[j] / lr[j]) + c_fluid.ph[lph[j]].a);
+  for (int z = threadIdx.x; z < I.zone_cap; z += blockDim.x) {
+    const Zone& Z = d.zones[I.zone_off + z];
+    if (!Z.alive) continue;
+    for (int i = 0; i < Z.nc; ++i) s = fmax(s, fabs(Z.m[i] / Z.r[i]) + c_fluid.ph[Z.ph[i]].a);
+  }
+  __shared__ double red[32];
+  for (int off = 16; off > 0; off >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double S = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) S = fmax(S, red[w]);
+    const Ctrl& C = *d.ctrl;
+    double dt = c_opts.cfl * I.h / S;
+    I.clipped = 0;
+    I.active = 1;
+    if (C.clip) {
+      if (!(I.t < C.t_end)) {
+        I.active = 0;
+      } else if (C.t_end - I.t <= dt) {
+        dt = C.t_end - I.t;
+        I.clipped = 1;
+      }
+    }
+    I.dt = dt;
+    I.smax_bits = 0ull;
+  }
+}
+
+__global__ void k_count_active(Dev d, int n_inst) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  int c = 0;
+  for (int i = threadIdx.x; i < n_inst; i += blockDim.x) c += (d.inst[i].active && !d.inst[i].status) ? 1 : 0;
+  atomicAdd(&cnt, c);
+  __syncthreads();
+  if (threadIdx.x == 0) d.ctrl->n_active = cnt;
+}
+
+// ---------------------------------------------------------------------------------------- host side
+std::string g_last_error;
+
+}  // namespace
+
+struct imexds_ctx {
+  int n_inst = 0;
+  std::vector<int> N;
+  std::vector<double> xL, xR, tau;
+  Fluid fluid;
+  Opts opts;
+  int zone_cap_opt = 0;
+  cudaStream_t stream = nullptr;
+  Dev d{};
+  int n_lat = 0, n_zone_slots = 0, n_tiles = 0;
+  std::vector<int> lat_off, zone_off, zone_cap;
+  bool loaded = false;
+  int* h_active = nullptr;  // pinned
+  long long launches = 0;
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+};
+
+namespace {
+
+imexds_status cuda_fail(cudaError_t e) {
+  g_last_error = cudaGetErrorString(e);
+  return IMEXDS_ERR_CUDA;
+}
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+Phase make_phase(const imexds_eos& e, double p_sat) {
+  Phase P;
+  P.kind = e.kind;
+  P.a2 = e.a2;
+  P.a = std::sqrt(e.a2);
+  P.p0 = e.p0;
+  P.rho0 = e.rho0;
+  P.rho_sat = (e.kind == 0) ? p_sat / e.a2 : e.rho0 + (p_sat - e.p0) / e.a2;
+  return P;
+}
+
+void free_dev(imexds_ctx* c) {
+  Dev& d = c->d;
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(d.rho[k]);
+    cudaFree(d.m[k]);
+  }
+  cudaFree(d.phase);
+  cudaFree(d.own);
+  cudaFree(d.zones);
+  cudaFree(d.inst);
+  cudaFree(d.ev);
+  cudaFree(d.tiles);
+  cudaFree(d.ctrl);
+  d = Dev{};
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+}
+
+// one time step: five kernel launches on the context stream
+void launch_step(imexds_ctx* c) {
+  const int zt = 64;
+  int zb = (c->n_zone_slots + zt - 1) / zt;
+  int ib = (c->n_inst + zt - 1) / zt;
+  k_pre<<<zb, zt, 0, c->stream>>>(c->d, c->n_zone_slots);
+  k_plan<<<zb, zt, 0, c->stream>>>(c->d, c->n_zone_slots);
+  k_sweep<<<c->n_tiles, TILE, 0, c->stream>>>(c->d);
+  k_dts<<<zb, zt, 0, c->stream>>>(c->d, c->n_zone_slots);
+  k_post<<<ib, zt, 0, c->stream>>>(c->d, c->n_inst);
+  c->launches += 5;
+}
+
+imexds_status set_ctrl(imexds_ctx* c, double t_end, int clip) {
+  Ctrl C{t_end, clip, 0};
+  CK(cudaMemcpyAsync(c->d.ctrl, &C, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream));
+  return IMEXDS_OK;
+}
+
+imexds_status run_steps(imexds_ctx* c, long long max_steps, bool until_done) {
+  // Steps are replayed from a CUDA graph of S steps; the host checks the number of active instances
+  // after each replay.
+  const int S = 8;
+  if (!c->graph || c->graph_steps != S) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaStream_t saved = c->stream;
+    c->stream = cs;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    long long l0 = c->launches;
+    for (int s = 0; s < S; ++s) launch_step(c);
+    k_count_active<<<1, 256, 0, cs>>>(c->d, c->n_inst);
+    cudaGraph_t g;
+    CK(cudaStreamEndCapture(cs, &g));
+    c->launches = l0;
+    CK(cudaGraphInstantiate(&c->graph, g, 0));
+    cudaGraphDestroy(g);
+    c->stream = saved;
+    cudaStreamDestroy(cs);
+    c->graph_steps = S;
+  }
+  long long done = 0;
+  while (done < max_steps) {
+    if (!until_done && max_steps - done < S) {
+      for (long long s = done; s < max_steps; ++s) launch_step(c);
+      k_count_active<<<1, 256, 0, c->stream>>>(c->d, c->n_inst);
+      CK(cudaGetLastError());
+      done = max_steps;
+      break;
+    }
+    CK(cudaGraphLaunch(c->graph, c->stream));
+    c->launches += 5 * S;
+    done += S;
+    if (until_done) {
+      CK(cudaMemcpyAsync(c->h_active, &c->d.ctrl->n_active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      if (*c->h_active == 0) break;
+    }
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaGetLastError());
+  return IMEXDS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* imexds_status_string(imexds_status s) {
+  switch (s) {
+    case IMEXDS_OK: return "ok";
+    case IMEXDS_ERR_ARG: return "invalid argument";
+    case IMEXDS_ERR_CUDA: return "CUDA error";
+    case IMEXDS_ERR_NONPHYSICAL: return "non-physical state";
+    case IMEXDS_ERR_PB_NOCONV: return "phase-boundary Newton iteration did not converge";
+    case IMEXDS_WARN_DTS_MAXITER: return "dual time stepping reached l_max";
+    case IMEXDS_ERR_VANISH: return "a phase would vanish";
+    case IMEXDS_ERR_TIMEOUT: return "device wait timed out";
+    case IMEXDS_ERR_STATE: return "call order";
+    case IMEXDS_ERR_CAPACITY: return "zone capacity exceeded";
+  }
+  return "unknown status";
+}
+
+const char* imexds_last_error_string(void) { return g_last_error.c_str(); }
+
+imexds_status imexds_create(const imexds_problem* prob, const imexds_options* opts, void* stream,
+                            imexds_ctx** out) {
+  if (!out) return IMEXDS_ERR_ARG;
+  *out = nullptr;
+  if (!prob || prob->n_inst <= 0 || !prob->n_lattice || !prob->x_left || !prob->x_right || !prob->tau)
+    return IMEXDS_ERR_ARG;
+  imexds_ctx* c = new imexds_ctx();
+  c->n_inst = prob->n_inst;
+  for (int i = 0; i < prob->n_inst; ++i) {
+    if (prob->n_lattice[i] < 2 || !(prob->x_right[i] > prob->x_left[i]) || !(prob->tau[i] >= 0.0)) {
+      delete c;
+      return IMEXDS_ERR_ARG;
+    }
+    c->N.push_back(prob->n_lattice[i]);
+    c->xL.push_back(prob->x_left[i]);
+    c->xR.push_back(prob->x_right[i]);
+    c->tau.push_back(prob->tau[i]);
+  }
+  const imexds_fluid& f = prob->fluid;
+  c->fluid.ph[VAP] = make_phase(f.vapour, f.p_sat);
+  c->fluid.ph[LIQ] = make_phase(f.liquid, f.p_sat);
+  c->fluid.p_sat = f.p_sat;
+  c->fluid.p_min = f.p_min;
+  c->fluid.p_tilde = f.p_tilde;
+  imexds_options o;
+  if (opts) {
+    o = *opts;
+  } else {
+    o.cfl = 0.5;
+    o.theta_nb = 0.9;
+    o.tol_nb = 1e-3;
+    o.tol_k = 1e-1;
+    o.res_mode = 0;
+    o.l_max = 10000;
+    o.newton_tol = 1e-12;
+    o.newton_itmax = 50;
+    o.alpha_min = 1e-8;
+    o.split_ratio = 2.0;
+    o.creation = 0;
+    o.zone_capacity = 0;
+  }
+  if (!(o.cfl > 0.0) || o.l_max < 1 || o.newton_itmax < 1 || !(o.split_ratio > 1.0)) {
+    delete c;
+    return IMEXDS_ERR_ARG;
+  }
+  c->opts = Opts{o.cfl, o.theta_nb, o.tol_nb, o.tol_k, o.res_mode, o.l_max, o.newton_tol, o.newton_itmax,
+                 o.alpha_min, o.split_ratio, o.creation};
+  c->zone_cap_opt = o.zone_capacity;
+  c->stream = (cudaStream_t)stream;
+  cudaError_t e = cudaMallocHost(&c->h_active, sizeof(int));
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e);
+  }
+  *out = c;
+  return IMEXDS_OK;
+}
+
+void imexds_destroy(imexds_ctx* c) {
+  if (!c) return;
+  free_dev(c);
+  if (c->h_active) cudaFreeHost(c->h_active);
+  delete c;
+}
+
+imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double* widths, const double* rho,
+                                const double* m, const uint8_t* phase, double t0) {
+  if (!c || !off || !widths || !rho || !m || !phase) return IMEXDS_ERR_ARG;
+  const int n = c->n_inst;
+  // host-side parse into lattice + zones
+  std::vector<int> lat_off(n + 1, 0);
+  for (int i = 0; i < n; ++i) lat_off[i + 1] = lat_off[i] + c->N[i];
+  const int n_lat = lat_off[n];
+  std::vector<double> hr(n_lat, 1.0), hm(n_lat, 0.0);
+  std::vector<unsigned char> hph(n_lat, 1);
+  std::vector<std::vector<Zone>> inst_zones(n);
+  std::vector<int> status(n, 0);
+  for (int i = 0; i < n; ++i) {
+    const int a = off[i], b = off[i + 1], M = b - a, N = c->N[i];
+    const double xL = c->xL[i], h = (c->xR[i] - c->xL[i]) / (double)N;
+    if (M < 1) return IMEXDS_ERR_ARG;
+    // faces: positions accumulate the widths from the last fixed face
+    std::vector<int> fpb(M + 1, 0), fj(M + 1, 0);
+    std::vector<double> fx(M + 1, 0.0);
+    long jfix = 0;
+    double part = 0.0;
+    bool bad = false;
+    for (int k = 0; k < M; ++k) {
+      part += widths[a + k];
+      if (k + 1 < M && phase[a + k + 1] != phase[a + k]) {
+        fpb[k + 1] = 1;
+        fx[k + 1] = xL + (double)jfix * h + part;
+      } else {
+        double units = part / h;
+        long j = jfix + std::lround(units);
+        if (std::fabs(units - std::round(units)) > 1e-9 || j <= jfix || j > N) bad = true;
+        fj[k + 1] = (int)j;
+        jfix = j;
+        part = 0.0;
+      }
+    }
+    if (fpb[M] || fj[M] != N) bad = true;
+    if (bad) return IMEXDS_ERR_ARG;
+    for (int k = 0; k < M; ++k)
+      if (phase[a + k] > 1 || !(rho[a + k] > 0.0) || !(widths[a + k] > 0.0)) return IMEXDS_ERR_ARG;
+    // cells with two fixed faces spanning one lattice cell are lattice cells; every other cell is part of
+    // a zone (runs of such cells, joined when closer than ZONE_GAP)
+    std::vector<int> special(M, 0);
+    for (int k = 0; k < M; ++k) {
+      bool lat = !fpb[k] && !fpb[k + 1] && fj[k + 1] == fj[k] + 1;
+      special[k] = !lat;
+      if (!fpb[k] && !fpb[k + 1] && !lat) return IMEXDS_ERR_ARG;  // a regular cell spanning several lattice cells
+    }
+    // group special cells into runs with their lattice footprints
+    std::vector<std::pair<int, int>> runs;  // [k0, k1) in cell indices
+    for (int k = 0; k < M;) {
+      if (!special[k]) {
+        ++k;
+        continue;
+      }
+      int k1 = k;
+      while (k1 < M && special[k1]) ++k1;
+      runs.push_back({k, k1});
+      k = k1;
+    }
+    // join runs whose footprints are closer than ZONE_GAP lattice cells
+    std::vector<std::pair<int, int>> joined;
+    for (auto& r : runs) {
+      if (!joined.empty() && fj[r.first] - fj[joined.back().second] < ZONE_GAP)
+        joined.back().second = r.second;
+      else
+        joined.push_back(r);
+    }
+    for (auto& r : joined) {
+      Zone Z;
+      std::memset(&Z, 0, sizeof(Z));
+      Z.alive = 1;
+      Z.inst = i;
+      Z.nc = r.second - r.first;
+      if (Z.nc > ZC) return IMEXDS_ERR_CAPACITY;
+      Z.A = fj[r.first];
+      Z.B = fj[r.second];
+      for (int q = 0; q < Z.nc; ++q) {
+        int k = r.first + q;
+        bool lat = !special[k];
+        Z.w[q] = lat ? h : widths[a + k];
+        Z.r[q] = rho[a + k];
+        Z.m[q] = m[a + k];
+        Z.ph[q] = phase[a + k];
+      }
+      for (int q = 0; q <= Z.nc; ++q) {
+        int k = r.first + q;
+        Z.fpb[q] = fpb[k];
+        Z.fj[q] = fj[k];
+        Z.fx[q] = fx[k];
+      }
+      inst_zones[i].push_back(Z);
+    }
+    for (int k = 0; k < M; ++k) {
+      if (special[k]) continue;
+      int j = fj[k];
+      hr[lat_off[i] + j] = rho[a + k];
+      hm[lat_off[i] + j] = m[a + k];
+      hph[lat_off[i] + j] = phase[a + k];
+    }
+    // lattice phase under zones: the phase of the zone cell covering it (kept for released cells)
+    for (auto& Z : inst_zones[i])
+      for (int j = Z.A; j < Z.B; ++j) hph[lat_off[i] + j] = (unsigned char)Z.ph[0];
+  }
+  std::vector<int> zone_off(n + 1, 0), zone_cap(n, 0);
+  for (int i = 0; i < n; ++i) {
+    int npb = 0;
+    for (auto& Z : inst_zones[i])
+      for (int q = 1; q < Z.nc; ++q) npb += Z.fpb[q];
+    int cap = c->zone_cap_opt > 0 ? c->zone_cap_opt : 4 + 2 * npb;
+    cap = std::max<int>(cap, (int)inst_zones[i].size());
+    zone_cap[i] = cap;
+    zone_off[i + 1] = zone_off[i] + cap;
+  }
+  const int n_zone = zone_off[n];
+  std::vector<Zone> hz(n_zone);
+  std::memset(hz.data(), 0, sizeof(Zone) * hz.size());
+  for (int i = 0; i < n; ++i)
+    for (size_t q = 0; q < inst_zones[i].size(); ++q) hz[zone_off[i] + q] = inst_zones[i][q];
+  std::vector<Inst> hi(n);
+  std::memset(hi.data(), 0, sizeof(Inst) * n);
+  for (int i = 0; i < n; ++i) {
+    Inst& I = hi[i];
+    I.N = c->N[i];
+    I.lat_off = lat_off[i];
+    I.zone_off = zone_off[i];
+    I.zone_cap = zone_cap[i];
+    I.xL = c->xL[i];
+    I.h = (c->xR[i] - c->xL[i]) / (double)c->N[i];
+    I.tau = c->tau[i];
+    I.t = t0;
+    I.status = status[i];
+    I.active = 1;
+  }
+  std::vector<int2> tiles;
+  for (int i = 0; i < n; ++i)
+    for (int j0 = 0; j0 < c->N[i]; j0 += TILE) tiles.push_back(make_int2(i, j0));
+  free_dev(c);
+  Dev& d = c->d;
+  for (int k = 0; k < 2; ++k) {
+    CK(cudaMalloc(&d.rho[k], sizeof(double) * n_lat));
+    CK(cudaMalloc(&d.m[k], sizeof(double) * n_lat));
+    CK(cudaMemcpyAsync(d.rho[k], hr.data(), sizeof(double) * n_lat, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(d.m[k], hm.data(), sizeof(double) * n_lat, cudaMemcpyHostToDevice, c->stream));
+  }
+  CK(cudaMalloc(&d.phase, n_lat));
+  CK(cudaMemcpyAsync(d.phase, hph.data(), n_lat, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMalloc(&d.own, sizeof(int) * n_lat));
+  CK(cudaMemsetAsync(d.own, 0xff, sizeof(int) * n_lat, c->stream));
+  CK(cudaMalloc(&d.zones, sizeof(Zone) * std::max(1, n_zone)));
+  CK(cudaMemcpyAsync(d.zones, hz.data(), sizeof(Zone) * n_zone, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMalloc(&d.inst, sizeof(Inst) * n));
+  CK(cudaMemcpyAsync(d.inst, hi.data(), sizeof(Inst) * n, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMalloc(&d.ev, sizeof(Event) * EV_CAP * n));
+  CK(cudaMalloc(&d.tiles, sizeof(int2) * tiles.size()));
+  CK(cudaMemcpyAsync(d.tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMalloc(&d.ctrl, sizeof(Ctrl)));
+  CK(cudaMemcpyToSymbolAsync(c_fluid, &c->fluid, sizeof(Fluid), 0, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyToSymbolAsync(c_opts, &c->opts, sizeof(Opts), 0, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->n_lat = n_lat;
+  c->n_zone_slots = n_zone;
+  c->n_tiles = (int)tiles.size();
+  c->lat_off = lat_off;
+  c->zone_off = zone_off;
+  c->zone_cap = zone_cap;
+  c->loaded = true;
+  return IMEXDS_OK;
+}
+
+imexds_status imexds_set_states_device(imexds_ctx* c, const int32_t* off, const double* w_d, const double* r_d,
+                                       const double* m_d, const uint8_t* ph_d, double t0) {
+  if (!c || !off) return IMEXDS_ERR_ARG;
+  int n = off[c->n_inst];
+  std::vector<double> w(n), r(n), m(n);
+  std::vector<uint8_t> ph(n);
+  CK(cudaMemcpyAsync(w.data(), w_d, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(r.data(), r_d, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(m.data(), m_d, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(ph.data(), ph_d, n, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return imexds_set_states(c, off, w.data(), r.data(), m.data(), ph.data(), t0);
+}
+
+imexds_status imexds_step(imexds_ctx* c, int32_t n_steps) {
+  if (!c || n_steps < 0) return IMEXDS_ERR_ARG;
+  if (!c->loaded) return IMEXDS_ERR_STATE;
+  c->launches = 0;
+  imexds_status s = set_ctrl(c, 0.0, 0);
+  if (s) return s;
+  int gb = c->n_inst;
+  k_init_dt<<<gb, 256, 0, c->stream>>>(c->d, c->n_inst);
+  c->launches += 1;
+  return run_steps(c, n_steps, false);
+}
+
+imexds_status imexds_run_to(imexds_ctx* c, double t_end) {
+  if (!c) return IMEXDS_ERR_ARG;
+  if (!c->loaded) return IMEXDS_ERR_STATE;
+  c->launches = 0;
+  imexds_status s = set_ctrl(c, t_end, 1);
+  if (s) return s;
+  k_init_dt<<<c->n_inst, 256, 0, c->stream>>>(c->d, c->n_inst);
+  c->launches += 1;
+  imexds_status st = run_steps(c, kRunToMaxSteps, true);
+  if (st == IMEXDS_OK && *c->h_active != 0) return IMEXDS_ERR_TIMEOUT;
+  return st;
+}
+
+imexds_status imexds_cell_counts(imexds_ctx* c, int32_t* counts) {
+  if (!c || !counts) return IMEXDS_ERR_ARG;
+  if (!c->loaded) return IMEXDS_ERR_STATE;
+  std::vector<Zone> hz(c->n_zone_slots);
+  CK(cudaMemcpyAsync(hz.data(), c->d.zones, sizeof(Zone) * hz.size(), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < c->n_inst; ++i) {
+    int cnt = c->N[i];
+    for (int z = 0; z < c->zone_cap[i]; ++z) {
+      const Zone& Z = hz[c->zone_off[i] + z];
+      if (Z.alive) cnt += Z.nc - (Z.B - Z.A);
+    }
+    counts[i] = cnt;
+  }
+  return IMEXDS_OK;
+}
+
+imexds_status imexds_get_states(imexds_ctx* c, int32_t* off, double* widths, double* rho, double* m,
+                                uint8_t* phase, double* t, int32_t* inst_status) {
+  if (!c || !off || !widths || !rho || !m || !phase || !t || !inst_status) return IMEXDS_ERR_ARG;
+  if (!c->loaded) return IMEXDS_ERR_STATE;
+  const int n = c->n_inst;
+  std::vector<double> r[2], mm[2];
+  for (int k = 0; k < 2; ++k) {
+    r[k].resize(c->n_lat);
+    mm[k].resize(c->n_lat);
+    CK(cudaMemcpyAsync(r[k].data(), c->d.rho[k], sizeof(double) * c->n_lat, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(mm[k].data(), c->d.m[k], sizeof(double) * c->n_lat, cudaMemcpyDeviceToHost, c->stream));
+  }
+  std::vector<unsigned char> ph(c->n_lat);
+  CK(cudaMemcpyAsync(ph.data(), c->d.phase, c->n_lat, cudaMemcpyDeviceToHost, c->stream));
+  std::vector<Zone> hz(c->n_zone_slots);
+  CK(cudaMemcpyAsync(hz.data(), c->d.zones, sizeof(Zone) * hz.size(), cudaMemcpyDeviceToHost, c->stream));
+  std::vector<Inst> hi(n);
+  CK(cudaMemcpyAsync(hi.data(), c->d.inst, sizeof(Inst) * n, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  int o = 0;
+  for (int i = 0; i < n; ++i) {
+    off[i] = o;
+    const Inst& I = hi[i];
+    const int p = I.parity;
+    std::vector<const Zone*> zs;
+    for (int z = 0; z < c->zone_cap[i]; ++z)
+      if (hz[c->zone_off[i] + z].alive) zs.push_back(&hz[c->zone_off[i] + z]);
+    std::sort(zs.begin(), zs.end(), [](const Zone* a, const Zone* b) { return a->A < b->A; });
+    size_t zk = 0;
+    for (int j = 0; j < c->N[i];) {
+      if (zk < zs.size() && zs[zk]->A == j) {
+        const Zone& Z = *zs[zk];
+        for (int q = 0; q < Z.nc; ++q, ++o) {
+          widths[o] = Z.w[q];
+          rho[o] = Z.r[q];
+          m[o] = Z.m[q];
+          phase[o] = (uint8_t)Z.ph[q];
+        }
+        j = Z.B;
+        ++zk;
+        continue;
+      }
+      int g = c->lat_off[i] + j;
+      widths[o] = I.h;
+      rho[o] = r[p][g];
+      m[o] = mm[p][g];
+      phase[o] = ph[g];
+      ++o;
+      ++j;
+    }
+    t[i] = I.t;
+    inst_status[i] = I.status;
+  }
+  off[n] = o;
+  return IMEXDS_OK;
+}
+
+imexds_status imexds_get_stats(imexds_ctx* c, int64_t* stats) {
+  if (!c || !stats) return IMEXDS_ERR_ARG;
+  if (!c->loaded) return IMEXDS_ERR_STATE;
+  std::vector<Inst> hi(c->n_inst);
+  CK(cudaMemcpyAsync(hi.data(), c->d.inst, sizeof(Inst) * c->n_inst, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < c->n_inst; ++i) {
+    for (int k = 0; k < N_STATS; ++k) stats[10 * i + k] = hi[i].stats[k];
+    stats[10 * i + 9] = c->launches;
+  }
+  return IMEXDS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,394 @@
+// Device physics of the explicit-implicit splitting scheme (arXiv 2211.00705): equations of state,
+// HLL fluxes, the phase-boundary Riemann solver of App. A (Newton with the Armijo rule), the
+// same-phase star pressure without transition and the phase-creation solve of App. B.
+// Every routine runs in registers of one thread; FP64 throughout.
+#pragma once
+#include <cstdint>
+
+namespace imexds {
+
+constexpr int VAP = 0;
+constexpr int LIQ = 1;
+
+struct Phase {
+  int kind;       // 0: p = a2 rho; 1: p = p0 + a2 (rho - rho0)
+  double a2, a;   // squared sound speed, sound speed
+  double p0, rho0;
+  double rho_sat; // density at the saturation pressure (zero of g)
+};
+
+struct Fluid {
+  Phase ph[2];
+  double p_sat, p_min, p_tilde;
+};
+
+struct Opts {
+  double cfl, theta_nb, tol_nb, tol_k;
+  int res_mode, l_max;
+  double newton_tol;
+  int newton_itmax;
+  double alpha_min, split_ratio;
+  int creation;
+};
+
+__host__ __device__ inline double pressure(const Phase& e, double rho) {
+  return e.kind == 0 ? e.a2 * rho : e.p0 + e.a2 * (rho - e.rho0);
+}
+__host__ __device__ inline double density(const Phase& e, double p) {
+  return e.kind == 0 ? p / e.a2 : e.rho0 + (p - e.p0) / e.a2;
+}
+__device__ inline bool valid_pressure(const Phase& e, double p) { return isfinite(p) && density(e, p) > 0.0; }
+// Gibbs energy with dg = v dp: g = a2 ln(rho / rho_sat), zero at the saturation pressure (Sec. 2.1).
+__device__ inline double gibbs(const Phase& e, double rho) { return e.a2 * log(rho / e.rho_sat); }
+
+// Physical flux (rho u, rho u^2 + p) of the isothermal Euler equations (Eq. eeq:isoT both).
+__device__ inline void phys_flux(const Phase& e, double r, double m, double& F0, double& F1) {
+  double u = m / r;
+  F0 = m;
+  F1 = m * u + pressure(e, r);
+}
+
+// HLL flux at a same-phase face (Toro), Davis wave speeds S_L = min(u_l, u_r) - a, S_R = max + a.
+__device__ inline void hll(const Phase& e, double rl, double ml, double rr, double mr, double& F0, double& F1) {
+  double ul = ml / rl, ur = mr / rr;
+  double Fl0 = ml, Fl1 = ml * ul + pressure(e, rl);
+  double Fr0 = mr, Fr1 = mr * ur + pressure(e, rr);
+  double SL = fmin(ul - e.a, ur - e.a);
+  double SR = fmax(ul + e.a, ur + e.a);
+  if (SL >= 0.0) {
+    F0 = Fl0;
+    F1 = Fl1;
+  } else if (SR <= 0.0) {
+    F0 = Fr0;
+    F1 = Fr1;
+  } else {
+    F0 = (SR * Fl0 - SL * Fr0 + SL * SR * (rr - rl)) / (SR - SL);
+    F1 = (SR * Fl1 - SL * Fr1 + SL * SR * (mr - ml)) / (SR - SL);
+  }
+}
+
+// Outer-wave function f_K of App. A for an isothermal linear EOS: shock sqrt((p* - p_K)(v_K - v*)),
+// rarefaction a ln(rho*/rho_K); derivative in dfdp.
+__device__ inline double wave_f(const Phase& e, double pstar, double rhoK, double& dfdp) {
+  double pK = pressure(e, rhoK);
+  double rs = density(e, pstar);
+  double vs = 1.0 / rs;
+  if (pstar > pK) {
+    double dv = 1.0 / rhoK - vs;
+    double q = (pstar - pK) * dv;
+    double f = sqrt(q);
+    double dq = dv + (pstar - pK) * vs * vs / e.a2;
+    dfdp = (f > 0.0) ? 0.5 * dq / f : vs / e.a;
+    return f;
+  }
+  dfdp = vs / e.a;
+  return e.a * log(rs / rhoK);
+}
+
+struct Side {
+  double p, rho, v, g, dv;
+};
+
+__device__ inline Side side_at(const Phase& e, double p) {
+  Side s;
+  s.p = p;
+  s.rho = density(e, p);
+  s.v = 1.0 / s.rho;
+  s.g = gibbs(e, s.rho);
+  s.dv = -s.v * s.v / e.a2;
+  return s;
+}
+
+// Kinetic relation z = tau p_V [[g + e_kin]] (Eq. isoT:kin_rel1) with e_kin relative to the moving
+// boundary and z^2 = -[[p]]/[[v]], i.e. [[e_kin]] = -[[p]] (v_L + v_R) / 2; returns dz/dp per side.
+__device__ inline double kinetic_z(double tau, bool left_is_vapour, const Side& L, const Side& R, double& dzl,
+                                   double& dzr) {
+  double pV = left_is_vapour ? L.p : R.p;
+  double jp = R.p - L.p;
+  double Q = (R.g - L.g) - 0.5 * jp * (L.v + R.v);
+  double dQl = -L.v + 0.5 * (L.v + R.v) - 0.5 * jp * L.dv;
+  double dQr = R.v - 0.5 * (L.v + R.v) - 0.5 * jp * R.dv;
+  dzl = tau * ((left_is_vapour ? Q : 0.0) + pV * dQl);
+  dzr = tau * ((left_is_vapour ? 0.0 : Q) + pV * dQr);
+  return tau * pV * Q;
+}
+
+struct PBSys {
+  double G0, G1, J00, J01, J10, J11, z;
+  Side L, R;
+  double fl, fr;
+};
+
+// G(p_l*, p_r*) of Eq. 2p_RP:ex_sys with left/right orientation and its Jacobian (Eq. jacobian:ex_sys).
+__device__ inline bool pb_eval(const Fluid& F, double tau, int phl, double rl, double ul, int phr, double rr,
+                               double ur, double pls, double prs, PBSys& S) {
+  const Phase& El = F.ph[phl];
+  const Phase& Er = F.ph[phr];
+  if (!valid_pressure(El, pls) || !valid_pressure(Er, prs)) return false;
+  S.L = side_at(El, pls);
+  S.R = side_at(Er, prs);
+  double dzl, dzr;
+  double z = kinetic_z(tau, phl == VAP, S.L, S.R, dzl, dzr);
+  double dfl, dfr;
+  S.fl = wave_f(El, pls, rl, dfl);
+  S.fr = wave_f(Er, prs, rr, dfr);
+  double jp = prs - pls, jv = S.R.v - S.L.v;
+  S.z = z;
+  S.G0 = jp + z * z * jv;
+  S.G1 = S.fl + S.fr + z * jv + (ur - ul);
+  S.J00 = -1.0 + 2.0 * z * dzl * jv - z * z * S.L.dv;
+  S.J01 = 1.0 + 2.0 * z * dzr * jv + z * z * S.R.dv;
+  S.J10 = dfl + dzl * jv - z * S.L.dv;
+  S.J11 = dfr + dzr * jv + z * S.R.dv;
+  return isfinite(S.G0) && isfinite(S.G1);
+}
+
+struct PBOut {
+  double F0, F1, w, z, pl, pr;
+  int iters;
+  int ok;
+};
+
+// HLLC-based starting pressure of App. A (Eq. HLLC:2p_nopt), with a fallback when it is not positive.
+__device__ inline void pb_initial_guess(const Fluid& F, int phl, double rl, double ul, int phr, double rr,
+                                        double ur, double& pl0, double& pr0) {
+  const Phase& El = F.ph[phl];
+  const Phase& Er = F.ph[phr];
+  double pl = pressure(El, rl), pr = pressure(Er, rr);
+  double Sl = ul - El.a, Sr = ur + Er.a;
+  double w = (pr - pl + rl * ul * (Sl - ul) - rr * ur * (Sr - ur)) / (rl * (Sl - ul) - rr * (Sr - ur));
+  double rls = (phl == LIQ) ? rl * (Sl - ul) / (Sl - w) : rr * (Sr - ur) / (Sr - w);
+  double p = pressure(F.ph[LIQ], rls);
+  if (isfinite(p) && p > 0.0) {
+    pl0 = p;
+    pr0 = p;
+    return;
+  }
+  double pv = (phl == VAP) ? pl : pr;
+  double pliq = (phl == LIQ) ? pl : pr;
+  double pvg = fmax(pv, 1e-3 * F.p_sat);
+  pl0 = (phl == VAP) ? pvg : pliq;
+  pr0 = (phr == VAP) ? pvg : pliq;
+}
+
+// Phase-boundary Riemann problem (App. A): Newton's method with the Armijo rule on the 2x2 system;
+// flux F_PB = (-z, -z u_V* + p_V*) (Eq. pb_flux:pt) through the boundary moving at w = u_V* + z v_V*.
+__device__ inline PBOut pb_solve(const Fluid& F, const Opts& o, double tau, int phl, double rl, double ml, int phr,
+                                 double rr, double mr) {
+  PBOut R;
+  R.ok = 0;
+  R.iters = 0;
+  R.F0 = R.F1 = R.w = R.z = R.pl = R.pr = 0.0;
+  double ul = ml / rl, ur = mr / rr;
+  double imp = rl * F.ph[phl].a + rr * F.ph[phr].a;
+  double x0, x1;
+  pb_initial_guess(F, phl, rl, ul, phr, rr, ur, x0, x1);
+  PBSys S;
+  if (!pb_eval(F, tau, phl, rl, ul, phr, rr, ur, x0, x1, S)) return R;
+  double nrm = hypot(S.G0 / imp, S.G1);
+  bool conv = (nrm == 0.0);
+  int it = 0;
+  while (!conv && it < o.newton_itmax) {
+    ++it;
+    double det = S.J00 * S.J11 - S.J01 * S.J10;
+    if (!isfinite(det) || det == 0.0) break;
+    double d0 = -(S.J11 * S.G0 - S.J01 * S.G1) / det;
+    double d1 = -(-S.J10 * S.G0 + S.J00 * S.G1) / det;
+    double lam = 1.0;
+    bool acc = false;
+    PBSys T;
+    for (int ls = 0; ls <= 20; ++ls) {
+      if (pb_eval(F, tau, phl, rl, ul, phr, rr, ur, x0 + lam * d0, x1 + lam * d1, T)) {
+        double nt = hypot(T.G0 / imp, T.G1);
+        if (nt <= (1.0 - 1e-4 * lam) * nrm) {
+          acc = true;
+          nrm = nt;
+          break;
+        }
+      }
+      lam *= 0.5;
+    }
+    double s0 = fabs(d0) / fmax(fabs(x0), F.p_sat);
+    double s1 = fabs(d1) / fmax(fabs(x1), F.p_sat);
+    if (!acc) {
+      if (fmax(s0, s1) <= 1e-9) conv = true;
+      break;
+    }
+    x0 += lam * d0;
+    x1 += lam * d1;
+    S = T;
+    if (lam * fmax(s0, s1) <= o.newton_tol || nrm == 0.0) conv = true;
+  }
+  R.iters = it;
+  if (!conv) return R;
+  double ulS = ul - S.fl, urS = ur + S.fr;
+  double uV = (phl == VAP) ? ulS : urS;
+  double vV = (phl == VAP) ? S.L.v : S.R.v;
+  double pV = (phl == VAP) ? x0 : x1;
+  R.z = S.z;
+  R.w = uV + R.z * vV;
+  R.F0 = -R.z;
+  R.F1 = -R.z * uV + pV;
+  R.pl = x0;
+  R.pr = x1;
+  R.ok = 1;
+  return R;
+}
+
+// Star pressure of the same-phase Riemann problem without transition: closed form for two
+// rarefactions, otherwise bisection on [min(p_l, p_r), p_TR] (the shock curve lies above the
+// rarefaction curve).
+__device__ inline double nopt_star(const Phase& e, double rl, double ul, double rr, double ur) {
+  double pl = pressure(e, rl), pr = pressure(e, rr);
+  double pm = fmin(pl, pr);
+  double rs = sqrt(rl * rr) * exp((ul - ur) / (2.0 * e.a));
+  double ptr = pressure(e, rs);
+  if (ptr <= pm) return ptr;
+  double lo = pm, hi = ptr, d;
+  for (int i = 0; i < 200; ++i) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    double phi = wave_f(e, mid, rl, d) + wave_f(e, mid, rr, d) + (ur - ul);
+    if (phi > 0.0)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+struct CreateOut {
+  double pC, rhoC, uC, z1, z2, w1, w2;
+  int iters;
+  int ok;
+};
+
+struct CrSys {
+  double E[3], J[3][3];
+  Side Pl, C, Pr;
+  double z1, z2, fl, fr;
+};
+
+__device__ inline bool cr_eval(const Fluid& F, double tau, int P, double rl, double ul, double rr, double ur,
+                               const double x[3], CrSys& S) {
+  int Cph = 1 - P;
+  const Phase& EP = F.ph[P];
+  const Phase& EC = F.ph[Cph];
+  if (!valid_pressure(EP, x[0]) || !valid_pressure(EC, x[1]) || !valid_pressure(EP, x[2])) return false;
+  S.Pl = side_at(EP, x[0]);
+  S.C = side_at(EC, x[1]);
+  S.Pr = side_at(EP, x[2]);
+  double dz1a, dz1b, dz2a, dz2b;
+  S.z1 = kinetic_z(tau, P == VAP, S.Pl, S.C, dz1a, dz1b);
+  S.z2 = kinetic_z(tau, Cph == VAP, S.C, S.Pr, dz2a, dz2b);
+  double dfl, dfr;
+  S.fl = wave_f(EP, x[0], rl, dfl);
+  S.fr = wave_f(EP, x[2], rr, dfr);
+  double jv1 = S.C.v - S.Pl.v, jv2 = S.Pr.v - S.C.v;
+  double z1 = S.z1, z2 = S.z2;
+  S.E[0] = (x[1] - x[0]) + z1 * z1 * jv1;
+  S.E[1] = (x[2] - x[1]) + z2 * z2 * jv2;
+  S.E[2] = S.fl + S.fr + z1 * jv1 + z2 * jv2 + (ur - ul);
+  S.J[0][0] = -1.0 + 2.0 * z1 * dz1a * jv1 - z1 * z1 * S.Pl.dv;
+  S.J[0][1] = 1.0 + 2.0 * z1 * dz1b * jv1 + z1 * z1 * S.C.dv;
+  S.J[0][2] = 0.0;
+  S.J[1][0] = 0.0;
+  S.J[1][1] = -1.0 + 2.0 * z2 * dz2a * jv2 - z2 * z2 * S.C.dv;
+  S.J[1][2] = 1.0 + 2.0 * z2 * dz2b * jv2 + z2 * z2 * S.Pr.dv;
+  S.J[2][0] = dfl + dz1a * jv1 - z1 * S.Pl.dv;
+  S.J[2][1] = dz1b * jv1 + z1 * S.C.dv + dz2a * jv2 - z2 * S.C.dv;
+  S.J[2][2] = dfr + dz2b * jv2 + z2 * S.Pr.dv;
+  return isfinite(S.E[0]) && isfinite(S.E[1]) && isfinite(S.E[2]);
+}
+
+// 3x3 solve by elimination with partial pivoting.
+__device__ inline bool solve3(const double A[3][3], const double b[3], double x[3]) {
+  double M[3][4];
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) M[i][j] = A[i][j];
+    M[i][3] = b[i];
+  }
+  for (int c = 0; c < 3; ++c) {
+    int p = c;
+    for (int r = c + 1; r < 3; ++r)
+      if (fabs(M[r][c]) > fabs(M[p][c])) p = r;
+    if (M[p][c] == 0.0 || !isfinite(M[p][c])) return false;
+    if (p != c)
+      for (int j = 0; j < 4; ++j) {
+        double t = M[p][j];
+        M[p][j] = M[c][j];
+        M[c][j] = t;
+      }
+    for (int r = c + 1; r < 3; ++r) {
+      double f = M[r][c] / M[c][c];
+      for (int j = c; j < 4; ++j) M[r][j] -= f * M[c][j];
+    }
+  }
+  for (int i = 2; i >= 0; --i) {
+    double s = M[i][3];
+    for (int j = i + 1; j < 3; ++j) s -= M[i][j] * x[j];
+    x[i] = s / M[i][i];
+  }
+  return true;
+}
+
+// Single-phase Riemann problem with creation of the other phase (App. B): unknowns
+// (p_parent-, p_created, p_parent+), two boundary momentum jumps and the chained velocity balance,
+// solved by Newton with the Armijo rule from the saturation pressure.
+__device__ inline CreateOut creation_solve(const Fluid& F, const Opts& o, double tau, int P, double rl, double ml,
+                                           double rr, double mr) {
+  CreateOut R;
+  R.ok = 0;
+  R.iters = 0;
+  double ul = ml / rl, ur = mr / rr;
+  double imp = (rl + rr) * F.ph[P].a;
+  double x[3] = {F.p_sat, F.p_sat, F.p_sat};
+  CrSys S;
+  if (!cr_eval(F, tau, P, rl, ul, rr, ur, x, S)) return R;
+  double nrm = sqrt((S.E[0] / imp) * (S.E[0] / imp) + (S.E[1] / imp) * (S.E[1] / imp) + S.E[2] * S.E[2]);
+  bool conv = (nrm == 0.0);
+  int it = 0;
+  while (!conv && it < o.newton_itmax) {
+    ++it;
+    double b[3] = {-S.E[0], -S.E[1], -S.E[2]}, d[3];
+    if (!solve3(S.J, b, d)) break;
+    double lam = 1.0;
+    bool acc = false;
+    CrSys T;
+    for (int ls = 0; ls <= 20; ++ls) {
+      double xt[3] = {x[0] + lam * d[0], x[1] + lam * d[1], x[2] + lam * d[2]};
+      if (cr_eval(F, tau, P, rl, ul, rr, ur, xt, T)) {
+        double nt = sqrt((T.E[0] / imp) * (T.E[0] / imp) + (T.E[1] / imp) * (T.E[1] / imp) + T.E[2] * T.E[2]);
+        if (nt <= (1.0 - 1e-4 * lam) * nrm) {
+          acc = true;
+          nrm = nt;
+          break;
+        }
+      }
+      lam *= 0.5;
+    }
+    double s = 0.0;
+    for (int i = 0; i < 3; ++i) s = fmax(s, fabs(d[i]) / fmax(fabs(x[i]), F.p_sat));
+    if (!acc) {
+      if (s <= 1e-9) conv = true;
+      break;
+    }
+    for (int i = 0; i < 3; ++i) x[i] += lam * d[i];
+    S = T;
+    if (lam * s <= o.newton_tol || nrm == 0.0) conv = true;
+  }
+  R.iters = it;
+  if (!conv) return R;
+  R.pC = x[1];
+  R.rhoC = S.C.rho;
+  R.z1 = S.z1;
+  R.z2 = S.z2;
+  double uPl = ul - S.fl;
+  R.uC = uPl - S.z1 * (S.C.v - S.Pl.v);
+  R.w1 = R.uC + S.z1 * S.C.v;
+  R.w2 = R.uC + S.z2 * S.C.v;
+  R.ok = (R.w2 > R.w1) ? 1 : 0;
+  return R;
+}
+
+}  // namespace imexds

@@ -1,0 +1,181 @@
+"""Python binding of the imexds C-ABI (include/imexds.h): argument marshalling only.
+
+Every step of the scheme runs in the CUDA library libimexds.so built in this package directory;
+importing this module without that library (or without a CUDA device when a call needs one) raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libimexds.so")
+
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_NONPHYSICAL", 4: "ERR_PB_NOCONV", 5: "WARN_DTS_MAXITER",
+          6: "ERR_VANISH", 7: "ERR_TIMEOUT", 8: "ERR_STATE", 9: "ERR_CAPACITY"}
+
+EXPORTED = ["imexds_create", "imexds_set_states", "imexds_set_states_device", "imexds_cell_counts",
+            "imexds_get_states", "imexds_step", "imexds_run_to", "imexds_get_stats", "imexds_destroy",
+            "imexds_status_string", "imexds_last_error_string"]
+
+
+class ImexdsError(RuntimeError):
+    pass
+
+
+class Eos(C.Structure):
+    _fields_ = [("kind", C.c_int), ("a2", C.c_double), ("p0", C.c_double), ("rho0", C.c_double)]
+
+
+class FluidS(C.Structure):
+    _fields_ = [("vapour", Eos), ("liquid", Eos), ("p_sat", C.c_double), ("p_min", C.c_double),
+                ("p_tilde", C.c_double)]
+
+
+class OptionsS(C.Structure):
+    _fields_ = [("cfl", C.c_double), ("theta_nb", C.c_double), ("tol_nb", C.c_double), ("tol_k", C.c_double),
+                ("res_mode", C.c_int), ("l_max", C.c_int), ("newton_tol", C.c_double),
+                ("newton_itmax", C.c_int), ("alpha_min", C.c_double), ("split_ratio", C.c_double),
+                ("creation", C.c_int), ("zone_capacity", C.c_int)]
+
+
+class ProblemS(C.Structure):
+    _fields_ = [("n_inst", C.c_int32), ("n_lattice", C.POINTER(C.c_int32)), ("x_left", C.POINTER(C.c_double)),
+                ("x_right", C.POINTER(C.c_double)), ("tau", C.POINTER(C.c_double)), ("fluid", FluidS)]
+
+
+_lib = None
+
+
+def load():
+    """Load libimexds.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImexdsError(f"CUDA library missing: {LIB_PATH} (run __graft_entry__.build())")
+        L = C.CDLL(LIB_PATH)
+        dp, ip, vp = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_void_p
+        u8p = C.POINTER(C.c_uint8)
+        L.imexds_create.argtypes = [C.POINTER(ProblemS), C.POINTER(OptionsS), vp, C.POINTER(vp)]
+        L.imexds_set_states.argtypes = [vp, ip, dp, dp, dp, u8p, C.c_double]
+        L.imexds_set_states_device.argtypes = [vp, ip, vp, vp, vp, vp, C.c_double]
+        L.imexds_cell_counts.argtypes = [vp, ip]
+        L.imexds_get_states.argtypes = [vp, ip, dp, dp, dp, u8p, dp, ip]
+        L.imexds_step.argtypes = [vp, C.c_int32]
+        L.imexds_run_to.argtypes = [vp, C.c_double]
+        L.imexds_get_stats.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.imexds_destroy.argtypes = [vp]
+        L.imexds_status_string.restype = C.c_char_p
+        L.imexds_status_string.argtypes = [C.c_int]
+        L.imexds_last_error_string.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        L = load()
+        msg = L.imexds_status_string(rc).decode()
+        if rc == 2:
+            msg += ": " + L.imexds_last_error_string().decode()
+        raise ImexdsError(f"imexds status {rc} ({msg})")
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def make_fluid(f) -> FluidS:
+    """From an inputs.Fluid."""
+    return FluidS(Eos(0, f.a2_vap, 0.0, 0.0), Eos(1, f.a2_liq, f.p_sat, f.rho0_liq), f.p_sat, f.p_min, f.p_tilde)
+
+
+def make_options(o, zone_capacity: int = 0) -> OptionsS:
+    return OptionsS(o.cfl, o.theta_nb, o.tol_nb, o.tol_k, o.res_mode, o.l_max, o.newton_tol, o.newton_itmax,
+                    o.alpha_min, o.split_ratio, o.creation, zone_capacity)
+
+
+class Imexds:
+    """A context of the CUDA library holding a batch of instances (see include/imexds.h)."""
+
+    def __init__(self, n_lattice, x_left, x_right, tau, fluid, options, stream: int = 0, zone_capacity: int = 0):
+        L = load()
+        self._keep = [np.ascontiguousarray(n_lattice, dtype=np.int32), np.ascontiguousarray(x_left, dtype=np.float64),
+                      np.ascontiguousarray(x_right, dtype=np.float64), np.ascontiguousarray(tau, dtype=np.float64)]
+        nl, xl, xr, tau_ = self._keep
+        self.n_inst = int(nl.shape[0])
+        prob = ProblemS(self.n_inst, _ip(nl), _dp(xl), _dp(xr), _dp(tau_), make_fluid(fluid))
+        opts = make_options(options, zone_capacity)
+        h = C.c_void_p()
+        _check(L.imexds_create(C.byref(prob), C.byref(opts), C.c_void_p(stream), C.byref(h)))
+        self.h = h
+
+    @classmethod
+    def from_batch(cls, batch, options=None, stream: int = 0, zone_capacity: int = 0) -> "Imexds":
+        ctx = cls(batch.n_lattice, batch.x_left, batch.x_right, batch.tau, batch.fluid, options or batch.options,
+                  stream=stream, zone_capacity=zone_capacity)
+        ctx.set_states(batch.cell_offsets, batch.widths, batch.rho, batch.m, batch.phase)
+        return ctx
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().imexds_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_states(self, offsets, widths, rho, m, phase, t0: float = 0.0):
+        off = np.ascontiguousarray(offsets, dtype=np.int32)
+        w = np.ascontiguousarray(widths, dtype=np.float64)
+        r = np.ascontiguousarray(rho, dtype=np.float64)
+        mm = np.ascontiguousarray(m, dtype=np.float64)
+        ph = np.ascontiguousarray(phase, dtype=np.uint8)
+        _check(load().imexds_set_states(self.h, _ip(off), _dp(w), _dp(r), _dp(mm),
+                                        ph.ctypes.data_as(C.POINTER(C.c_uint8)), t0))
+
+    def set_states_device(self, offsets, widths_d, rho_d, m_d, phase_d, t0: float = 0.0):
+        """Device-pointer variant: widths_d/rho_d/m_d (float64) and phase_d (uint8) are CUDA tensors."""
+        off = np.ascontiguousarray(offsets, dtype=np.int32)
+        _check(load().imexds_set_states_device(self.h, _ip(off), C.c_void_p(widths_d.data_ptr()),
+                                               C.c_void_p(rho_d.data_ptr()), C.c_void_p(m_d.data_ptr()),
+                                               C.c_void_p(phase_d.data_ptr()), t0))
+
+    def step(self, n_steps: int):
+        _check(load().imexds_step(self.h, int(n_steps)))
+
+    def run_to(self, t_end: float):
+        _check(load().imexds_run_to(self.h, float(t_end)))
+
+    def cell_counts(self) -> np.ndarray:
+        c = np.zeros(self.n_inst, dtype=np.int32)
+        _check(load().imexds_cell_counts(self.h, _ip(c)))
+        return c
+
+    def get_states(self) -> dict:
+        counts = self.cell_counts()
+        tot = int(counts.sum())
+        off = np.zeros(self.n_inst + 1, dtype=np.int32)
+        w, r, m = np.zeros(tot), np.zeros(tot), np.zeros(tot)
+        ph = np.zeros(tot, dtype=np.uint8)
+        t = np.zeros(self.n_inst)
+        st = np.zeros(self.n_inst, dtype=np.int32)
+        _check(load().imexds_get_states(self.h, _ip(off), _dp(w), _dp(r), _dp(m),
+                                        ph.ctypes.data_as(C.POINTER(C.c_uint8)), _dp(t), _ip(st)))
+        return {"offsets": off, "widths": w, "rho": r, "m": m, "phase": ph, "t": t, "status": st}
+
+    def stats(self) -> dict:
+        s = np.zeros((self.n_inst, 10), dtype=np.int64)
+        _check(load().imexds_get_stats(self.h, s.ctypes.data_as(C.POINTER(C.c_int64))))
+        keys = ["steps", "dts_iters", "dts_max", "newton", "merges", "splits", "creations", "maxiter", "pb_solves",
+                "launches"]
+        return {k: s[:, i].copy() for i, k in enumerate(keys)}
