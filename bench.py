@@ -1,0 +1,309 @@
+"""Benchmark: batched FP64 cell-steps/s of the explicit-implicit splitting scheme on GB300.
+
+Workload (one bench step = one whole run): 4096 independent liquid|vapour Riemann instances with
+N uniform in [200, 2000] background cells, cut fractions alpha log-uniform in [1e-6, 1e-1] and kinetic
+coefficients c log-uniform in [1e-4, 1e-2] (tau = c * tau_paper), all advanced to t_end = 2e-4 s
+(every instance takes 0.6 N .. 0.7 N time steps). Synthetic seeded data (no dataset exists).
+cell-steps = sum over instances of (cells at the end of the run x time steps taken).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs its own full batch (weak scaling, no collective on the data
+path); value = cell-steps of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "batched FP64 cell-steps/s (fwd, adjoint) vs plain GPU step at ≤1e-9 rel err; %HBM"
+UNIT = "cell-steps/s"
+# algorithmic FP64 operations of one explicit cell-step (HLL face + cell update, counted in the design doc)
+SWEEP_FLOP_PER_CELL = 33
+FP64_PEAK_TFLOPS = 1.25   # GB300 dense FP64 (nominal; no FP64 figure in MEASURED_PEAKS.json)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(scale=1.0):
+    from paper_2211_00705_gb300 import inputs as I
+    return I.workload(1, scale=scale)
+
+
+def cell_steps(stats, counts):
+    return float(np.sum(stats["steps"].astype(np.float64) * counts.astype(np.float64)))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(batch, target_s=15.0):
+    """The oracle on the host cores on a bounded sample of the workload: instances taken in a fixed
+    stride until their estimated work (0.62 N^2 cell-steps each) fills about target_s seconds."""
+    from oracle import pyoracle as P
+    cores = os.cpu_count() or 1
+    # calibrate on one mid-size instance
+    order = np.argsort(batch.n_lattice)
+    probe = batch.subset([order[len(order) // 2]])
+    o = P.Oracle(probe)
+    t0 = time.perf_counter()
+    o.run_to(probe.t_end, 1)
+    dt1 = time.perf_counter() - t0
+    st = o.stats()
+    rate1 = cell_steps(st, np.array([len(o.states()["rho"])])) / max(dt1, 1e-9)
+    budget = target_s * rate1 * cores
+    est = 0.62 * batch.n_lattice.astype(np.float64) ** 2
+    stride = max(1, int(round(len(est) * 1.0 / max(1.0, budget / est.mean()))))
+    idx = np.arange(0, batch.n_inst, stride)
+    sample = batch.subset(idx)
+    o = P.Oracle(sample)
+    t0 = time.perf_counter()
+    o.run_to(sample.t_end, cores)
+    wall = time.perf_counter() - t0
+    s = o.states()
+    counts = np.diff(s["offsets"])
+    cs = cell_steps(o.stats(), counts)
+    return {"value": cs / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(idx)} of {batch.n_inst} instances (every {stride}th), run to t_end on {cores} "
+                      f"threads: {cs:.3e} cell-steps in {wall:.1f} s"}
+
+
+def run_reference(args, ws, rank):
+    """The oracle as the reference arm: each step is a bounded sample of the workload on host cores."""
+    if rank != 0:
+        return 0
+    batch = workload()
+    from oracle import pyoracle as P
+    cores = os.cpu_count() or 1
+    idx = np.arange(0, batch.n_inst, 64)
+    sample = batch.subset(idx)
+    times, css = [], []
+    for k in range(args.warmup + args.steps):
+        o = P.Oracle(sample)
+        t0 = time.perf_counter()
+        o.run_to(sample.t_end, cores)
+        wall = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(wall)
+            css.append(cell_steps(o.stats(), np.diff(o.states()["offsets"])))
+    value = sum(css) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)",
+            "config": {"workload": batch.name, "sample": f"{len(idx)} of {batch.n_inst} instances per step",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{len(idx)} of {batch.n_inst} instances (every 64th) per step, {cores} threads"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="fraction of the 4096 instances (smaller cases for profiling only)")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    import torch.distributed as dist
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2211_00705_gb300.imexds import Imexds
+
+    batch = workload(args.scale)
+    ctx = Imexds.from_batch(batch)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (also builds the step graph)
+    for _ in range(max(args.warmup, 3)):
+        ctx.reset()
+        ctx.run_to(batch.t_end)
+    torch.cuda.synchronize()
+    counts = ctx.cell_counts()
+    st = ctx.stats()
+    cs_run = cell_steps(st, counts)
+    status = ctx.get_states()["status"]
+
+    # timed region: K whole runs with inputs resident in HBM; L2 flushed between runs (outside the events)
+    sampler = ClockSampler(dev.index) if rank == 0 else None
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches = 0
+    barrier()
+    if sampler:
+        sampler.start()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ctx.reset()
+        barrier()
+        ev0[k].record()
+        ctx.run_to(batch.t_end)
+        ev1[k].record()
+        barrier()
+        launches += int(ctx.stats()["launches"][0])
+    clocks = sampler.stop() if sampler else None
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in zip(ev0, ev1))
+    t_local = ms / 1e3
+    if ws > 1:
+        t = torch.tensor([t_local], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    value = cs_run * args.steps * ws / t_max
+
+    # per-kernel durations over one instrumented run (events captured in the step graph)
+    ctx.set_kernel_timing(True)
+    ctx.reset()
+    ctx.run_to(batch.t_end)
+    kt = ctx.kernel_times()
+    ctx.set_kernel_timing(False)
+    tot = sum(v[0] for v in kt.values())
+    dominant = max(kt, key=lambda k: kt[k][0])
+
+    # end to end through the public API with host buffers: upload, run, download every step
+    h2d = int(batch.widths.nbytes + batch.rho.nbytes + batch.m.nbytes + batch.phase.nbytes
+              + batch.cell_offsets.nbytes)
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    d2h = 0
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        barrier()
+        e0[k].record()
+        ctx.set_states(batch.cell_offsets, batch.widths, batch.rho, batch.m, batch.phase)
+        ctx.run_to(batch.t_end)
+        out = ctx.get_states()
+        e1[k].record()
+        barrier()
+        d2h = int(out["widths"].nbytes + out["rho"].nbytes + out["m"].nbytes + out["phase"].nbytes
+                  + out["offsets"].nbytes + out["t"].nbytes + out["status"].nbytes)
+    e2e_s = sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / 1e3
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": cs_run * args.steps * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+
+    # roofline of the dominant kernel
+    if dominant == "k_sweep":
+        sweep_cells = float(np.sum(st["steps"] * batch.n_lattice))   # lattice cells swept per run (upper bound)
+        flops = SWEEP_FLOP_PER_CELL * sweep_cells / max(kt["k_sweep"][1], 1)
+        per_launch_s = kt["k_sweep"][0] / 1e3 / max(kt["k_sweep"][1], 1)
+        achieved = flops / per_launch_s / 1e12
+        roof = {"bound": "alu", "kernel": "k_sweep", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table; measured DFMA 0.50 G/s x 2)"}
+    else:
+        # latency-bound dual-time chain: report the FP64 pipe use implied by its duration
+        roof = {"bound": "alu", "kernel": dominant, "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "note": "latency-bound dual-time chain"}
+    roof["kernel_share"] = {k: round(v[0] / tot, 4) if tot else None for k, v in kt.items()}
+    roof["kernel_ms_per_launch"] = {k: (v[0] / v[1] if v[1] else None) for k, v in kt.items()}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+                "config": {"workload": batch.name, "instances": batch.n_inst, "cells": int(batch.rho.shape[0]),
+                           "cell_steps_per_step": cs_run, "l2": "flushed (256 MB write) between timed runs",
+                           "instance_status_nonzero": int(np.count_nonzero(status))},
+                "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(batch)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

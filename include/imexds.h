@@ -126,6 +126,17 @@ imexds_status imexds_set_states_device(imexds_ctx* ctx, const int32_t* cell_offs
                                        const double* widths_d, const double* rho_d, const double* m_d,
                                        const uint8_t* phase_d, double t0);
 
+/* Restore the states (and t0) given to the last imexds_set_states, on the device (device-to-device
+ * copies only). */
+imexds_status imexds_reset(imexds_ctx* ctx);
+
+/* Measurement: with on != 0, the step graph records CUDA events around each of the five kernels of a
+ * step; imexds_get_kernel_times returns, per kernel (0 pre-solve, 1 plan, 2 sweep, 3 dual time,
+ * 4 post), the summed duration in ms and the number of timed launches since timing was switched on.
+ * Arrays have 5 entries. Switching timing on or off rebuilds the step graph. */
+imexds_status imexds_set_kernel_timing(imexds_ctx* ctx, int32_t on);
+imexds_status imexds_get_kernel_times(imexds_ctx* ctx, double* total_ms, int64_t* launches);
+
 void imexds_destroy(imexds_ctx* ctx);
 const char* imexds_status_string(imexds_status s);
 /* Text of the last CUDA error seen by any context of this process (thread-unsafe, static storage). */

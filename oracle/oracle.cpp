@@ -553,6 +553,7 @@ void step_instance(Ctx& C, Inst& I, double t_end) {
   // (2) Grid management before the step (Sec. 2.3, Sec. 3.4): phase-boundary speeds at U^n predict
   //     the widths; a cell next to a phase boundary that would fall below max(alpha_min h, h_i/2)
   //     is merged with its neighbour across its fixed face (possible only within one phase).
+  std::vector<double> hpred;  // predicted widths at t^{n+1} after the merges (Sec. 3.1: the model mesh is the mesh at t^{n+1})
   {
     int M = I.M();
     std::vector<double> wf(M + 1, 0.0);
@@ -591,6 +592,21 @@ void step_instance(Ctx& C, Inst& I, double t_end) {
     }
   }
   const int M = I.M();
+  {
+    // predicted widths on the merged grid: boundary speeds from U^n of the (possibly merged) cells
+    hpred.assign(I.w.begin(), I.w.end());
+    std::vector<double> wf(M + 1, 0.0);
+    for (int g = 1; g < M; ++g) {
+      if (!I.f[g].pb) continue;
+      PBResult R = solve_face(C, I, I.ph[g - 1], I.r[g - 1], I.m[g - 1], I.ph[g], I.r[g], I.m[g]);
+      if (!R.ok) {
+        I.status = ORC_ERR_PB_NOCONV;
+        return;
+      }
+      wf[g] = R.w;
+    }
+    for (int i = 0; i < M; ++i) hpred[i] = I.w[i] + (wf[i + 1] - wf[i]) * dt;
+  }
   // (3) Implicit neighbourhoods (Sec. 3.2): at every phase boundary the smaller adjacent cell is the
   //     tiny cell k; {k-1, k, k+1} is treated implicitly. Overlapping neighbourhoods are joined.
   std::vector<int> blk(M, -1), tiny(M, 0);
@@ -678,7 +694,10 @@ void step_instance(Ctx& C, Inst& I, double t_end) {
     double FR[2] = {Fl0[hi + 1], Fl1[hi + 1]}; // F_right = flux at face hi+1 from U^n
     std::vector<double> Wr = rn, Wm = mn;      // dual-time iterate, indexed like the cells
     std::vector<double> theta(M, 0.0);
-    for (int i = lo; i <= hi; ++i) theta[i] = std::min(o.theta_nb, wn[i] / I.h);  // Delta tau_i = theta_i dt
+    // Delta tau_i = theta_i dt with theta_i <= h_i/h for stability (Sec. 3.3). Reading: the widths are
+    // those of the mesh at t^{n+1} (Sec. 3.1 treats the model mesh as the mesh at t^{n+1}), predicted
+    // with the boundary speeds at U^n.
+    for (int i = lo; i <= hi; ++i) theta[i] = std::min(o.theta_nb, hpred[i] / I.h);
     std::vector<double> Fc0(M + 1), Fc1(M + 1), wc(M + 1, 0.0), hl(M);
     auto fluxes = [&](const std::vector<double>& Ar, const std::vector<double>& Am) -> bool {
       Fc0[lo] = FL[0];

@@ -56,6 +56,8 @@ struct Zone {
   double w[ZC], r[ZC], m[ZC];
   double fx[ZC + 1];             // position of a phase-boundary face
   double eL0, eL1, eR0, eR1;     // U^n of the first / last owned cell (read by neighbouring sweep cells)
+  double wpre[ZC + 1];           // boundary speeds from the solves at U^n (k_pre)
+  double hp[ZC];                 // widths predicted for t^{n+1} on the merged grid (theta of Alg. 2)
 };
 
 struct Inst {
@@ -125,6 +127,7 @@ __global__ void k_pre(Dev d, int n_zone_slots) {
     }
     wf[k] = R.w;
   }
+  for (int k = 0; k <= Z.nc; ++k) Z.wpre[k] = wf[k];
   int mask = 0;
   for (int i = 0; i < Z.nc; ++i) {
     if (!(Z.fpb[i] || Z.fpb[i + 1])) continue;
@@ -231,6 +234,27 @@ __global__ void k_plan(Dev d, int n_zone_slots) {
     merges++;
   }
   if (merges) atomicAdd((unsigned long long*)&I.stats[4], (unsigned long long)merges);
+  // widths predicted for t^{n+1} (Sec. 3.1 treats the implicit neighbourhood on the mesh at t^{n+1});
+  // after a merge the boundary speeds are solved again from the merged states
+  {
+    double wf[ZC + 1];
+    for (int k = 0; k <= Z.nc; ++k) wf[k] = 0.0;
+    for (int k = 1; k < Z.nc; ++k) {
+      if (!Z.fpb[k]) continue;
+      if (merges) {
+        PBOut R = pb_solve(c_fluid, c_opts, I.tau, Z.ph[k - 1], Z.r[k - 1], Z.m[k - 1], Z.ph[k], Z.r[k], Z.m[k]);
+        atomicAdd((unsigned long long*)&I.stats[3], (unsigned long long)R.iters);
+        if (!R.ok) {
+          set_status(I, IMEXDS_ERR_PB_NOCONV);
+          return;
+        }
+        wf[k] = R.w;
+      } else {
+        wf[k] = Z.wpre[k];
+      }
+    }
+    for (int i = 0; i < Z.nc; ++i) Z.hp[i] = Z.w[i] + (wf[i + 1] - wf[i]) * I.dt;
+  }
   // implicit neighbourhoods in the extended index space
   int emin = (Z.A > 0) ? -1 : 0;
   int emax = (Z.B < I.N) ? Z.nc : Z.nc - 1;
@@ -564,7 +588,11 @@ __global__ void k_dts(Dev d, int n_zone_slots) {
       Wr[q] = B.r[q];
       Wm[q] = B.m[q];
     }
-    for (int q = lo; q <= hi; ++q) theta[q] = fmin(c_opts.theta_nb, B.w[q] / h);
+    for (int q = lo; q <= hi; ++q) {
+      int e = q + e0;
+      double hp = (e < 0 || e >= Z.nc) ? h : Z.hp[e];
+      theta[q] = fmin(c_opts.theta_nb, hp / h);
+    }
     bool stop = false, nonconv = false;
     int l;
     for (l = 0; l < c_opts.l_max && !stop; ++l) {
@@ -953,6 +981,13 @@ struct imexds_ctx {
   long long launches = 0;
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+  // device copy of the state loaded by the last set_states (imexds_reset)
+  Dev saved{};
+  // optional per-kernel timing with events captured in the step graph
+  int timing = 0;
+  std::vector<cudaEvent_t> tev;  // 6 events per step of the graph
+  double kt_ms[6] = {0, 0, 0, 0, 0, 0};
+  long long kt_n[6] = {0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -992,21 +1027,49 @@ void free_dev(imexds_ctx* c) {
   cudaFree(d.tiles);
   cudaFree(d.ctrl);
   d = Dev{};
+  Dev& sv = c->saved;
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(sv.rho[k]);
+    cudaFree(sv.m[k]);
+  }
+  cudaFree(sv.phase);
+  cudaFree(sv.zones);
+  cudaFree(sv.inst);
+  sv = Dev{};
   if (c->graph) cudaGraphExecDestroy(c->graph);
   c->graph = nullptr;
+  for (auto e : c->tev) cudaEventDestroy(e);
+  c->tev.clear();
 }
 
 // one time step: five kernel launches on the context stream
-void launch_step(imexds_ctx* c) {
+void launch_step(imexds_ctx* c, cudaEvent_t* ev = nullptr) {
   const int zt = 64;
   int zb = (c->n_zone_slots + zt - 1) / zt;
   int ib = (c->n_inst + zt - 1) / zt;
+  if (ev) cudaEventRecord(ev[0], c->stream);
   k_pre<<<zb, zt, 0, c->stream>>>(c->d, c->n_zone_slots);
+  if (ev) cudaEventRecord(ev[1], c->stream);
   k_plan<<<zb, zt, 0, c->stream>>>(c->d, c->n_zone_slots);
+  if (ev) cudaEventRecord(ev[2], c->stream);
   k_sweep<<<c->n_tiles, TILE, 0, c->stream>>>(c->d);
+  if (ev) cudaEventRecord(ev[3], c->stream);
   k_dts<<<zb, zt, 0, c->stream>>>(c->d, c->n_zone_slots);
+  if (ev) cudaEventRecord(ev[4], c->stream);
   k_post<<<ib, zt, 0, c->stream>>>(c->d, c->n_inst);
+  if (ev) cudaEventRecord(ev[5], c->stream);
   c->launches += 5;
+}
+
+void accumulate_times(imexds_ctx* c, int steps) {
+  for (int s = 0; s < steps; ++s)
+    for (int k = 0; k < 5; ++k) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, c->tev[6 * s + k], c->tev[6 * s + k + 1]) == cudaSuccess) {
+        c->kt_ms[k] += ms;
+        c->kt_n[k] += 1;
+      }
+    }
 }
 
 imexds_status set_ctrl(imexds_ctx* c, double t_end, int clip) {
@@ -1019,6 +1082,13 @@ imexds_status run_steps(imexds_ctx* c, long long max_steps, bool until_done) {
   // Steps are replayed from a CUDA graph of S steps; the host checks the number of active instances
   // after each replay.
   const int S = 8;
+  if (c->timing && (int)c->tev.size() < 6 * S) {
+    for (int k = (int)c->tev.size(); k < 6 * S; ++k) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      c->tev.push_back(e);
+    }
+  }
   if (!c->graph || c->graph_steps != S) {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
@@ -1028,7 +1098,7 @@ imexds_status run_steps(imexds_ctx* c, long long max_steps, bool until_done) {
     c->stream = cs;
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     long long l0 = c->launches;
-    for (int s = 0; s < S; ++s) launch_step(c);
+    for (int s = 0; s < S; ++s) launch_step(c, c->timing ? &c->tev[6 * s] : nullptr);
     k_count_active<<<1, 256, 0, cs>>>(c->d, c->n_inst);
     cudaGraph_t g;
     CK(cudaStreamEndCapture(cs, &g));
@@ -1044,17 +1114,19 @@ imexds_status run_steps(imexds_ctx* c, long long max_steps, bool until_done) {
     if (!until_done && max_steps - done < S) {
       for (long long s = done; s < max_steps; ++s) launch_step(c);
       k_count_active<<<1, 256, 0, c->stream>>>(c->d, c->n_inst);
+      c->launches += 1;
       CK(cudaGetLastError());
       done = max_steps;
       break;
     }
     CK(cudaGraphLaunch(c->graph, c->stream));
-    c->launches += 5 * S;
+    c->launches += 5 * S + 1;
     done += S;
-    if (until_done) {
+    if (until_done || c->timing) {
       CK(cudaMemcpyAsync(c->h_active, &c->d.ctrl->n_active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
       CK(cudaStreamSynchronize(c->stream));
-      if (*c->h_active == 0) break;
+      if (c->timing) accumulate_times(c, S);
+      if (until_done && *c->h_active == 0) break;
     }
   }
   CK(cudaStreamSynchronize(c->stream));
@@ -1308,6 +1380,21 @@ imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double*
   CK(cudaMalloc(&d.ctrl, sizeof(Ctrl)));
   CK(cudaMemcpyToSymbolAsync(c_fluid, &c->fluid, sizeof(Fluid), 0, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyToSymbolAsync(c_opts, &c->opts, sizeof(Opts), 0, cudaMemcpyHostToDevice, c->stream));
+  {
+    Dev& sv = c->saved;
+    for (int k = 0; k < 2; ++k) {
+      CK(cudaMalloc(&sv.rho[k], sizeof(double) * n_lat));
+      CK(cudaMalloc(&sv.m[k], sizeof(double) * n_lat));
+      CK(cudaMemcpyAsync(sv.rho[k], d.rho[k], sizeof(double) * n_lat, cudaMemcpyDeviceToDevice, c->stream));
+      CK(cudaMemcpyAsync(sv.m[k], d.m[k], sizeof(double) * n_lat, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    CK(cudaMalloc(&sv.phase, n_lat));
+    CK(cudaMemcpyAsync(sv.phase, d.phase, n_lat, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMalloc(&sv.zones, sizeof(Zone) * std::max(1, n_zone)));
+    CK(cudaMemcpyAsync(sv.zones, d.zones, sizeof(Zone) * n_zone, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMalloc(&sv.inst, sizeof(Inst) * n));
+    CK(cudaMemcpyAsync(sv.inst, d.inst, sizeof(Inst) * n, cudaMemcpyDeviceToDevice, c->stream));
+  }
   CK(cudaStreamSynchronize(c->stream));
   c->n_lat = n_lat;
   c->n_zone_slots = n_zone;
@@ -1429,6 +1516,46 @@ imexds_status imexds_get_states(imexds_ctx* c, int32_t* off, double* widths, dou
     inst_status[i] = I.status;
   }
   off[n] = o;
+  return IMEXDS_OK;
+}
+
+imexds_status imexds_reset(imexds_ctx* c) {
+  if (!c) return IMEXDS_ERR_ARG;
+  if (!c->loaded) return IMEXDS_ERR_STATE;
+  Dev& d = c->d;
+  Dev& sv = c->saved;
+  for (int k = 0; k < 2; ++k) {
+    CK(cudaMemcpyAsync(d.rho[k], sv.rho[k], sizeof(double) * c->n_lat, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(d.m[k], sv.m[k], sizeof(double) * c->n_lat, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  CK(cudaMemcpyAsync(d.phase, sv.phase, c->n_lat, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemsetAsync(d.own, 0xff, sizeof(int) * c->n_lat, c->stream));
+  CK(cudaMemcpyAsync(d.zones, sv.zones, sizeof(Zone) * c->n_zone_slots, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(d.inst, sv.inst, sizeof(Inst) * c->n_inst, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return IMEXDS_OK;
+}
+
+imexds_status imexds_set_kernel_timing(imexds_ctx* c, int32_t on) {
+  if (!c) return IMEXDS_ERR_ARG;
+  if ((on != 0) != (c->timing != 0)) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->timing = on ? 1 : 0;
+  for (int k = 0; k < 6; ++k) {
+    c->kt_ms[k] = 0.0;
+    c->kt_n[k] = 0;
+  }
+  return IMEXDS_OK;
+}
+
+imexds_status imexds_get_kernel_times(imexds_ctx* c, double* total_ms, int64_t* launches) {
+  if (!c || !total_ms || !launches) return IMEXDS_ERR_ARG;
+  for (int k = 0; k < 5; ++k) {
+    total_ms[k] = c->kt_ms[k];
+    launches[k] = c->kt_n[k];
+  }
   return IMEXDS_OK;
 }
 

@@ -18,7 +18,8 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_NONPHYSICAL", 4: "ERR_PB
 
 EXPORTED = ["imexds_create", "imexds_set_states", "imexds_set_states_device", "imexds_cell_counts",
             "imexds_get_states", "imexds_step", "imexds_run_to", "imexds_get_stats", "imexds_destroy",
-            "imexds_status_string", "imexds_last_error_string"]
+            "imexds_status_string", "imexds_last_error_string", "imexds_reset", "imexds_set_kernel_timing",
+            "imexds_get_kernel_times"]
 
 
 class ImexdsError(RuntimeError):
@@ -67,6 +68,9 @@ def load():
         L.imexds_run_to.argtypes = [vp, C.c_double]
         L.imexds_get_stats.argtypes = [vp, C.POINTER(C.c_int64)]
         L.imexds_destroy.argtypes = [vp]
+        L.imexds_reset.argtypes = [vp]
+        L.imexds_set_kernel_timing.argtypes = [vp, C.c_int32]
+        L.imexds_get_kernel_times.argtypes = [vp, dp, C.POINTER(C.c_int64)]
         L.imexds_status_string.restype = C.c_char_p
         L.imexds_status_string.argtypes = [C.c_int]
         L.imexds_last_error_string.restype = C.c_char_p
@@ -172,6 +176,21 @@ class Imexds:
         _check(load().imexds_get_states(self.h, _ip(off), _dp(w), _dp(r), _dp(m),
                                         ph.ctypes.data_as(C.POINTER(C.c_uint8)), _dp(t), _ip(st)))
         return {"offsets": off, "widths": w, "rho": r, "m": m, "phase": ph, "t": t, "status": st}
+
+    def reset(self):
+        """Restore the states given to the last set_states (device-to-device)."""
+        _check(load().imexds_reset(self.h))
+
+    def set_kernel_timing(self, on: bool):
+        _check(load().imexds_set_kernel_timing(self.h, 1 if on else 0))
+
+    KERNELS = ["k_pre", "k_plan", "k_sweep", "k_dts", "k_post"]
+
+    def kernel_times(self) -> dict:
+        ms = np.zeros(5)
+        n = np.zeros(5, dtype=np.int64)
+        _check(load().imexds_get_kernel_times(self.h, _dp(ms), n.ctypes.data_as(C.POINTER(C.c_int64))))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.KERNELS)}
 
     def stats(self) -> dict:
         s = np.zeros((self.n_inst, 10), dtype=np.int64)
