@@ -130,10 +130,10 @@ imexds_status imexds_set_states_device(imexds_ctx* ctx, const int32_t* cell_offs
  * copies only). */
 imexds_status imexds_reset(imexds_ctx* ctx);
 
-/* Measurement: with on != 0, the step graph records CUDA events around each of the five kernels of a
- * step; imexds_get_kernel_times returns, per kernel (0 pre-solve, 1 plan, 2 sweep, 3 dual time,
- * 4 post), the summed duration in ms and the number of timed launches since timing was switched on.
- * Arrays have 5 entries. Switching timing on or off rebuilds the step graph. */
+/* Measurement: with on != 0, steps are launched without the step graph and CUDA events are recorded
+ * around each of the five kernels of a step; imexds_get_kernel_times returns, per kernel (0 pre-solve,
+ * 1 plan, 2 sweep, 3 dual time, 4 post), the summed duration in ms and the number of timed launches
+ * since timing was switched on. Arrays have 5 entries. */
 imexds_status imexds_set_kernel_timing(imexds_ctx* ctx, int32_t on);
 imexds_status imexds_get_kernel_times(imexds_ctx* ctx, double* total_ms, int64_t* launches);
 

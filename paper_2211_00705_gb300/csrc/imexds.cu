@@ -57,6 +57,7 @@ struct Zone {
   double fx[ZC + 1];             // position of a phase-boundary face
   double eL0, eL1, eR0, eR1;     // U^n of the first / last owned cell (read by neighbouring sweep cells)
   double wpre[ZC + 1];           // boundary speeds from the solves at U^n (k_pre)
+  double pwl[ZC + 1], pwr[ZC + 1]; // last converged star pressures at a boundary face (Newton start)
   double hp[ZC];                 // widths predicted for t^{n+1} on the merged grid (theta of Alg. 2)
 };
 
@@ -118,7 +119,8 @@ __global__ void k_pre(Dev d, int n_zone_slots) {
   long long newton = 0, solves = 0;
   for (int k = 1; k < Z.nc; ++k) {
     if (!Z.fpb[k]) continue;
-    PBOut R = pb_solve(c_fluid, c_opts, I.tau, Z.ph[k - 1], Z.r[k - 1], Z.m[k - 1], Z.ph[k], Z.r[k], Z.m[k]);
+    PBOut R = pb_solve_warm(c_fluid, c_opts, I.tau, Z.ph[k - 1], Z.r[k - 1], Z.m[k - 1], Z.ph[k], Z.r[k], Z.m[k],
+                            Z.pwl[k], Z.pwr[k]);
     newton += R.iters;
     solves++;
     if (!R.ok) {
@@ -151,6 +153,8 @@ __device__ inline void zone_erase_cell(Zone& Z, int b) {
     Z.fpb[k] = Z.fpb[k + 1];
     Z.fj[k] = Z.fj[k + 1];
     Z.fx[k] = Z.fx[k + 1];
+    Z.pwl[k] = Z.pwl[k + 1];
+    Z.pwr[k] = Z.pwr[k + 1];
   }
   Z.nc--;
 }
@@ -242,7 +246,8 @@ __global__ void k_plan(Dev d, int n_zone_slots) {
     for (int k = 1; k < Z.nc; ++k) {
       if (!Z.fpb[k]) continue;
       if (merges) {
-        PBOut R = pb_solve(c_fluid, c_opts, I.tau, Z.ph[k - 1], Z.r[k - 1], Z.m[k - 1], Z.ph[k], Z.r[k], Z.m[k]);
+        PBOut R = pb_solve_warm(c_fluid, c_opts, I.tau, Z.ph[k - 1], Z.r[k - 1], Z.m[k - 1], Z.ph[k], Z.r[k], Z.m[k],
+                                Z.pwl[k], Z.pwr[k]);
         atomicAdd((unsigned long long*)&I.stats[3], (unsigned long long)R.iters);
         if (!R.ok) {
           set_status(I, IMEXDS_ERR_PB_NOCONV);
@@ -304,13 +309,17 @@ __global__ void k_plan(Dev d, int n_zone_slots) {
 // ------------------------------------------------------------------------------------------ k_sweep
 // Algorithm 1, Step 1 on one tile of free lattice cells: HLL fluxes from U^n, the explicit update of
 // Eq. update expl time (Eq. godunov_meth:nonunif next to a creation face), and the next step's
-// wave-speed maximum. Faces next to a zone see the zone's edge state.
+// wave-speed maximum. u = m/rho and the momentum flux are formed once per cell and staged in shared
+// memory; a face next to a zone sees the zone's edge state. CREATION adds the detection and the
+// creation solve of App. B at faces between two free cells.
+template <bool CREATION>
 __global__ void __launch_bounds__(TILE) k_sweep(Dev d) {
-  __shared__ double sr[TILE + 3], sm[TILE + 3];
+  __shared__ double sr[TILE + 3], sm[TILE + 3], su[TILE + 3], sf[TILE + 3];
   __shared__ int sown[TILE + 3];
   __shared__ unsigned char sph[TILE + 3];
-  __shared__ double F0L[TILE + 1], F1L[TILE + 1], F0R[TILE + 1], F1R[TILE + 1], WL[TILE + 1], WR[TILE + 1];
-  __shared__ int sdet[TILE + 2];
+  __shared__ double F0L[TILE + 1], F1L[TILE + 1], F0R[TILE + 1], F1R[TILE + 1];
+  __shared__ double WL[CREATION ? TILE + 1 : 1], WR[CREATION ? TILE + 1 : 1];
+  __shared__ int sdet[CREATION ? TILE + 2 : 1];
   __shared__ double red[TILE / 32];
   const int2 tile = d.tiles[blockIdx.x];
   Inst& I = d.inst[tile.x];
@@ -323,110 +332,120 @@ __global__ void __launch_bounds__(TILE) k_sweep(Dev d) {
   double* nm = d.m[cur ^ 1] + I.lat_off;
   const unsigned char* lph = d.phase + I.lat_off;
   const int* lown = d.own + I.lat_off;
-  const double h = I.h, dt = I.dt;
-  // cells j0-2 .. j0+nt (index q = j - j0 + 2)
+  const double h = I.h, dt = I.dt, lam = dt / h;
+  // cells j0-2 .. j0+nt (shared index q = j - j0 + 2)
   for (int q = threadIdx.x; q < nt + 3; q += blockDim.x) {
     int j = j0 - 2 + q;
+    int ow = -2;  // outside the domain
     if (j >= 0 && j < N) {
-      sown[q] = lown[j];
-      sph[q] = lph[j];
-      if (sown[q] < 0) {
-        sr[q] = lr[j];
-        sm[q] = lm[j];
+      ow = lown[j];
+      int ph = lph[j];
+      sph[q] = (unsigned char)ph;
+      if (ow < 0) {
+        double r = lr[j], m = lm[j];
+        double u = m / r;
+        sr[q] = r;
+        sm[q] = m;
+        su[q] = u;
+        sf[q] = __fma_rn(m, u, pressure_fma(c_fluid.ph[ph], r));
       }
-    } else {
-      sown[q] = -2;  // outside the domain
     }
+    sown[q] = ow;
   }
   __syncthreads();
-  const bool creation = c_opts.creation != 0;
-  // detection at faces f = j0-1 .. j0+nt (index t = f - j0 + 1), only between two free cells
-  if (creation) {
+  if (CREATION) {
+    // detection at faces f = j0-1 .. j0+nt (index t = f - j0 + 1), only between two free cells
     for (int t = threadIdx.x; t < nt + 2; t += blockDim.x) {
-      int q = t + 1;  // right cell of face f has index q = f - j0 + 2 = t + 1
+      int q = t + 1;
       int det = 0;
-      if (q >= 1 && q < nt + 3 && sown[q - 1] == -1 && sown[q] == -1) {
+      if (sown[q - 1] == -1 && sown[q] == -1) {
         int P = sph[q];
-        double ps = nopt_star(c_fluid.ph[P], sr[q - 1], sm[q - 1] / sr[q - 1], sr[q], sm[q] / sr[q]);
+        double ps = nopt_star(c_fluid.ph[P], sr[q - 1], su[q - 1], sr[q], su[q]);
         det = (P == LIQ) ? (ps < c_fluid.p_min) : (ps > c_fluid.p_tilde);
       }
       sdet[t] = det;
     }
     __syncthreads();
   }
-  // fluxes at faces f = j0 .. j0+nt (index t = f - j0)
+  // fluxes at faces f = j0 .. j0+nt (index t = f - j0); cells left/right of face t: q = t+1, t+2
   for (int t = threadIdx.x; t <= nt; t += blockDim.x) {
-    int f = j0 + t;
-    int ql = t + 1, qr = t + 2;  // left / right cell indices in shared memory
-    double a0, a1;
-    bool need = (t < nt && sown[qr] == -1) || (t > 0 && sown[ql] == -1) || (t == 0 && sown[qr] == -1) ||
-                (t == nt && sown[ql] == -1);
-    WL[t] = 0.0;
-    WR[t] = 0.0;
-    if (!need) {
-      F0L[t] = F1L[t] = F0R[t] = F1R[t] = 0.0;
-      continue;
+    const int f = j0 + t, ql = t + 1, qr = t + 2;
+    if (CREATION) {
+      WL[t] = 0.0;
+      WR[t] = 0.0;
     }
+    const bool need = (t < nt && sown[qr] == -1) || (t > 0 && sown[ql] == -1);
+    if (!need) continue;
+    double a0, a1;
     if (f == 0) {
-      phys_flux(c_fluid.ph[sph[qr]], sr[qr], sm[qr], a0, a1);
+      a0 = sm[qr];
+      a1 = sf[qr];
     } else if (f == N) {
-      phys_flux(c_fluid.ph[sph[ql]], sr[ql], sm[ql], a0, a1);
+      a0 = sm[ql];
+      a1 = sf[ql];
     } else {
-      double rl, ml, rr, mr;
-      int P;
+      const int P = (sown[ql] == -1) ? sph[ql] : sph[qr];
+      const Phase& E = c_fluid.ph[P];
+      double rl, ml, ul, fl1, rr, mr, ur, fr1;
       if (sown[ql] >= 0) {
         const Zone& Z = d.zones[sown[ql]];
         rl = Z.eR0;
         ml = Z.eR1;
-        P = sph[qr];
+        ul = ml / rl;
+        fl1 = __fma_rn(ml, ul, pressure_fma(E, rl));
       } else {
         rl = sr[ql];
         ml = sm[ql];
-        P = sph[ql];
+        ul = su[ql];
+        fl1 = sf[ql];
       }
       if (sown[qr] >= 0) {
         const Zone& Z = d.zones[sown[qr]];
         rr = Z.eL0;
         mr = Z.eL1;
+        ur = mr / rr;
+        fr1 = __fma_rn(mr, ur, pressure_fma(E, rr));
       } else {
         rr = sr[qr];
         mr = sm[qr];
+        ur = su[qr];
+        fr1 = sf[qr];
       }
-      if (creation && sdet[t + 1] && !sdet[t]) {
-        // App. B: create a cell of the other phase at this face (fluxes of Eq. flux:cavitation /
+      if (CREATION && sdet[t + 1] && !sdet[t]) {
+        // App. B: a cell of the other phase is created at this face (fluxes of Eq. flux:cavitation /
         // flux:nucleation with each boundary's own mass flux)
-        CreateOut C = creation_solve(c_fluid, c_opts, I.tau, P, rl, ml, rr, mr);
-        atomicAdd((unsigned long long*)&I.stats[3], (unsigned long long)C.iters);
-        if (!C.ok) {
+        CreateOut Cr = creation_solve(c_fluid, c_opts, I.tau, P, rl, ml, rr, mr);
+        atomicAdd((unsigned long long*)&I.stats[3], (unsigned long long)Cr.iters);
+        if (!Cr.ok) {
           set_status(I, IMEXDS_ERR_PB_NOCONV);
           F0L[t] = F1L[t] = F0R[t] = F1R[t] = 0.0;
           continue;
         }
-        F0L[t] = -C.z1;
-        F1L[t] = -C.z1 * C.uC + C.pC;
-        F0R[t] = -C.z2;
-        F1R[t] = -C.z2 * C.uC + C.pC;
-        WL[t] = C.w1;
-        WR[t] = C.w2;
+        F0L[t] = -Cr.z1;
+        F1L[t] = -Cr.z1 * Cr.uC + Cr.pC;
+        F0R[t] = -Cr.z2;
+        F1R[t] = -Cr.z2 * Cr.uC + Cr.pC;
+        WL[t] = Cr.w1;
+        WR[t] = Cr.w2;
         if (t < nt) {  // the tile owning the right cell records the event
           int k = atomicAdd(&I.n_ev, 1);
           if (k < EV_CAP) {
-            Event& E = d.ev[tile.x * EV_CAP + k];
-            E.face = f;
-            E.w1 = C.w1;
-            E.w2 = C.w2;
-            E.rhoC = C.rhoC;
-            E.mC = C.rhoC * C.uC;
-            E.phC = 1 - P;
-            E.hl = h + (C.w1 - 0.0) * dt;
-            E.hr = h + (0.0 - C.w2) * dt;
+            Event& Ev = d.ev[tile.x * EV_CAP + k];
+            Ev.face = f;
+            Ev.w1 = Cr.w1;
+            Ev.w2 = Cr.w2;
+            Ev.rhoC = Cr.rhoC;
+            Ev.mC = Cr.rhoC * Cr.uC;
+            Ev.phC = 1 - P;
+            Ev.hl = h + (Cr.w1 - 0.0) * dt;
+            Ev.hr = h + (0.0 - Cr.w2) * dt;
           } else {
             set_status(I, IMEXDS_ERR_CAPACITY);
           }
         }
         continue;
       }
-      hll(c_fluid.ph[P], rl, ml, rr, mr, a0, a1);
+      hll_pre(E.a, rl, ml, ul, fl1, rr, mr, ur, fr1, a0, a1);
     }
     F0L[t] = F0R[t] = a0;
     F1L[t] = F1R[t] = a1;
@@ -434,12 +453,18 @@ __global__ void __launch_bounds__(TILE) k_sweep(Dev d) {
   __syncthreads();
   double smax = 0.0;
   for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-    int q = t + 2;
+    const int q = t + 2;
     if (sown[q] != -1) continue;
-    int j = j0 + t;
-    double hnp1 = h + (WL[t + 1] - WR[t]) * dt;
-    double r1 = (h * sr[q] - dt * (F0L[t + 1] - F0R[t])) / hnp1;
-    double m1 = (h * sm[q] - dt * (F1L[t + 1] - F1R[t])) / hnp1;
+    const int j = j0 + t;
+    double r1, m1;
+    if (CREATION && (WL[t + 1] != 0.0 || WR[t] != 0.0)) {
+      double hnp1 = h + (WL[t + 1] - WR[t]) * dt;
+      r1 = (h * sr[q] - dt * (F0L[t + 1] - F0R[t])) / hnp1;
+      m1 = (h * sm[q] - dt * (F1L[t + 1] - F1R[t])) / hnp1;
+    } else {
+      r1 = __fma_rn(-lam, F0L[t + 1] - F0R[t], sr[q]);
+      m1 = __fma_rn(-lam, F1L[t + 1] - F1R[t], sm[q]);
+    }
     nr[j] = r1;
     nm[j] = m1;
     if (!(r1 > 0.0) || !isfinite(r1) || !isfinite(m1)) set_status(I, IMEXDS_ERR_NONPHYSICAL);
@@ -449,9 +474,9 @@ __global__ void __launch_bounds__(TILE) k_sweep(Dev d) {
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = smax;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = fmax(s, red[w]);
-    if (s > 0.0) atomicMax(&I.smax_bits, dbits(s));
+    double sx = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sx = fmax(sx, red[w]);
+    if (sx > 0.0) atomicMax(&I.smax_bits, dbits(sx));
   }
 }
 
@@ -469,8 +494,8 @@ struct BlockCtx {
 
 __device__ inline bool block_fluxes(const BlockCtx& B, int lo, int hi, const double* Wr, const double* Wm,
                                     double FL0, double FL1, double FR0, double FR1, double tau, double dt,
-                                    double* F0, double* F1, double* wc, double* hl, long long& newton,
-                                    long long& solves, bool& nonconv) {
+                                    double* F0, double* F1, double* wc, double* hl, double* gl, double* gr,
+                                    long long& newton, long long& solves, bool& nonconv) {
   F0[lo] = FL0;
   F1[lo] = FL1;
   F0[hi + 1] = FR0;
@@ -479,7 +504,8 @@ __device__ inline bool block_fluxes(const BlockCtx& B, int lo, int hi, const dou
   wc[hi + 1] = 0.0;
   for (int g = lo + 1; g <= hi; ++g) {
     if (B.fpb[g]) {
-      PBOut R = pb_solve(c_fluid, c_opts, tau, B.ph[g - 1], Wr[g - 1], Wm[g - 1], B.ph[g], Wr[g], Wm[g]);
+      PBOut R = pb_solve_warm(c_fluid, c_opts, tau, B.ph[g - 1], Wr[g - 1], Wm[g - 1], B.ph[g], Wr[g], Wm[g], gl[g],
+                              gr[g]);
       newton += R.iters;
       solves++;
       if (!R.ok) {
@@ -490,7 +516,7 @@ __device__ inline bool block_fluxes(const BlockCtx& B, int lo, int hi, const dou
       F1[g] = R.F1;
       wc[g] = R.w;
     } else {
-      hll(c_fluid.ph[B.ph[g]], Wr[g - 1], Wm[g - 1], Wr[g], Wm[g], F0[g], F1[g]);
+      hll_fast(c_fluid.ph[B.ph[g]], Wr[g - 1], Wm[g - 1], Wr[g], Wm[g], F0[g], F1[g]);
       wc[g] = 0.0;
     }
   }
@@ -552,16 +578,16 @@ __global__ void k_dts(Dev d, int n_zone_slots) {
     }
     if (q == 0) {
       if (Z.oA > 0)
-        hll(c_fluid.ph[B.ph[0]], lr[Z.oA - 1], lm[Z.oA - 1], B.r[0], B.m[0], Fx0[q], Fx1[q]);
+        hll_fast(c_fluid.ph[B.ph[0]], lr[Z.oA - 1], lm[Z.oA - 1], B.r[0], B.m[0], Fx0[q], Fx1[q]);
       else
-        phys_flux(c_fluid.ph[B.ph[0]], B.r[0], B.m[0], Fx0[q], Fx1[q]);
+        phys_flux_fast(c_fluid.ph[B.ph[0]], B.r[0], B.m[0], Fx0[q], Fx1[q]);
     } else if (q == nq) {
       if (Z.oB < N)
-        hll(c_fluid.ph[B.ph[nq - 1]], B.r[nq - 1], B.m[nq - 1], lr[Z.oB], lm[Z.oB], Fx0[q], Fx1[q]);
+        hll_fast(c_fluid.ph[B.ph[nq - 1]], B.r[nq - 1], B.m[nq - 1], lr[Z.oB], lm[Z.oB], Fx0[q], Fx1[q]);
       else
-        phys_flux(c_fluid.ph[B.ph[nq - 1]], B.r[nq - 1], B.m[nq - 1], Fx0[q], Fx1[q]);
+        phys_flux_fast(c_fluid.ph[B.ph[nq - 1]], B.r[nq - 1], B.m[nq - 1], Fx0[q], Fx1[q]);
     } else {
-      hll(c_fluid.ph[B.ph[q]], B.r[q - 1], B.m[q - 1], B.r[q], B.m[q], Fx0[q], Fx1[q]);
+      hll_fast(c_fluid.ph[B.ph[q]], B.r[q - 1], B.m[q - 1], B.r[q], B.m[q], Fx0[q], Fx1[q]);
     }
   }
   int inblk[ZB];
@@ -594,9 +620,17 @@ __global__ void k_dts(Dev d, int n_zone_slots) {
       theta[q] = fmin(c_opts.theta_nb, hp / h);
     }
     bool stop = false, nonconv = false;
+    double gl[ZB + 1], gr[ZB + 1];  // Newton starts per face: the zone's last solution, then the previous iterate
+    for (int g = 0; g <= nq; ++g) {
+      int e = g + e0;
+      bool zf = (e >= 1 && e <= Z.nc - 1);
+      gl[g] = zf ? Z.pwl[e] : 0.0;
+      gr[g] = zf ? Z.pwr[e] : 0.0;
+    }
     int l;
     for (l = 0; l < c_opts.l_max && !stop; ++l) {
-      if (!block_fluxes(B, lo, hi, Wr, Wm, FL0, FL1, FR0, FR1, tau, dt, F0, F1, wc, hl, newton, solves, nonconv)) {
+      if (!block_fluxes(B, lo, hi, Wr, Wm, FL0, FL1, FR0, FR1, tau, dt, F0, F1, wc, hl, gl, gr, newton, solves,
+                        nonconv)) {
         set_status(I, nonconv ? IMEXDS_ERR_PB_NOCONV : IMEXDS_ERR_VANISH);
         return;
       }
@@ -626,10 +660,16 @@ __global__ void k_dts(Dev d, int n_zone_slots) {
     if (!stop) maxiter++;
     iters_sum += l;
     iters_max = max(iters_max, (long long)l);
-    if (!block_fluxes(B, lo, hi, Wr, Wm, FL0, FL1, FR0, FR1, tau, dt, F0, F1, wc, hl, newton, solves, nonconv)) {
+    if (!block_fluxes(B, lo, hi, Wr, Wm, FL0, FL1, FR0, FR1, tau, dt, F0, F1, wc, hl, gl, gr, newton, solves,
+                      nonconv)) {
       set_status(I, nonconv ? IMEXDS_ERR_PB_NOCONV : IMEXDS_ERR_VANISH);
       return;
     }
+    for (int g = lo + 1; g <= hi; ++g)
+      if (B.fpb[g]) {
+        Z.pwl[g + e0] = gl[g];
+        Z.pwr[g + e0] = gr[g];
+      }
     for (int q = lo; q <= hi; ++q) {
       out_r[q] = (B.w[q] * B.r[q] - dt * (F0[q + 1] - F0[q])) / hl[q];
       out_m[q] = (B.w[q] * B.m[q] - dt * (F1[q + 1] - F1[q])) / hl[q];
@@ -687,6 +727,8 @@ __device__ inline int zone_insert_cell(Zone& Z, int pos) {
     Z.fpb[k] = Z.fpb[k - 1];
     Z.fj[k] = Z.fj[k - 1];
     Z.fx[k] = Z.fx[k - 1];
+    Z.pwl[k] = Z.pwl[k - 1];
+    Z.pwr[k] = Z.pwr[k - 1];
   }
   Z.nc++;
   return 1;
@@ -780,6 +822,66 @@ __global__ void k_post(Dev d, int n_inst) {
       Z.fpb[Z.nc] = 0;
     }
   }
+  // split a zone at an interior run of at least ZONE_GAP regular lattice cells (returned to the lattice);
+  // the part right of the run becomes a new zone (a pure change of representation)
+  for (int z = 0; z < I.zone_cap; ++z) {
+    Zone& Z = zones[z];
+    if (!Z.alive) continue;
+    int a = -1, b = -1;
+    for (int k = 1; k < Z.nc - 1 && b < 0; ++k) {
+      bool reg = !Z.fpb[k] && !Z.fpb[k + 1] && Z.fj[k + 1] == Z.fj[k] + 1 && Z.w[k] == h;
+      if (reg) {
+        if (a < 0) a = k;
+        if (k + 1 - a >= ZONE_GAP) {
+          int e = k + 1;  // extend to the end of the run
+          while (e < Z.nc - 1 && !Z.fpb[e] && !Z.fpb[e + 1] && Z.fj[e + 1] == Z.fj[e] + 1 && Z.w[e] == h) ++e;
+          b = e;
+        }
+      } else {
+        a = -1;
+      }
+    }
+    if (b < 0) continue;
+    int slot = -1;
+    for (int y = 0; y < I.zone_cap; ++y)
+      if (!zones[y].alive) {
+        slot = y;
+        break;
+      }
+    if (slot < 0) {
+      set_status(I, IMEXDS_ERR_CAPACITY);
+      break;
+    }
+    Zone& Zn = zones[slot];
+    Zn.alive = 1;
+    Zn.inst = ii;
+    Zn.merge_mask = 0;
+    Zn.oA = Zn.oB = 0;
+    Zn.nc = Z.nc - b;
+    for (int i = 0; i < Zn.nc; ++i) {
+      Zn.w[i] = Z.w[b + i];
+      Zn.r[i] = Z.r[b + i];
+      Zn.m[i] = Z.m[b + i];
+      Zn.ph[i] = Z.ph[b + i];
+    }
+    for (int k = 0; k <= Zn.nc; ++k) {
+      Zn.fpb[k] = Z.fpb[b + k];
+      Zn.fj[k] = Z.fj[b + k];
+      Zn.fx[k] = Z.fx[b + k];
+      Zn.pwl[k] = Z.pwl[b + k];
+      Zn.pwr[k] = Z.pwr[b + k];
+    }
+    Zn.A = Z.fj[b];
+    Zn.B = Z.B;
+    for (int k = a; k < b; ++k) {
+      int j = Z.fj[k];
+      nr[j] = Z.r[k];
+      nm[j] = Z.m[k];
+      lph[j] = (unsigned char)Z.ph[k];
+    }
+    Z.nc = a;
+    Z.B = Z.fj[a];
+  }
   double smax = __longlong_as_double((long long)I.smax_bits);
   // creation events -> new zones
   int nev = min(I.n_ev, EV_CAP);
@@ -825,6 +927,7 @@ __global__ void k_post(Dev d, int n_inst) {
     Z.fj[3] = f + 1;
     Z.oA = Z.oB = 0;
     Z.merge_mask = 0;
+    for (int k = 0; k <= ZC; ++k) Z.pwl[k] = Z.pwr[k] = 0.0;
     smax = fmax(smax, fabs(E.mC / E.rhoC) + c_fluid.ph[E.phC].a);
     creations++;
   }
@@ -856,6 +959,7 @@ __global__ void k_post(Dev d, int n_inst) {
         Za.ph[i] = lph[j];
         Za.fpb[i] = 0;
         Za.fj[i] = j;
+        Za.pwl[i] = Za.pwr[i] = 0.0;
         Za.nc++;
       }
       for (int i = 0; i < Zb.nc; ++i) {
@@ -867,6 +971,8 @@ __global__ void k_post(Dev d, int n_inst) {
         Za.fpb[k] = Zb.fpb[i];
         Za.fj[k] = Zb.fj[i];
         Za.fx[k] = Zb.fx[i];
+        Za.pwl[k] = Zb.pwl[i];
+        Za.pwr[k] = Zb.pwr[i];
         Za.nc++;
       }
       Za.fpb[Za.nc] = 0;
@@ -1052,7 +1158,10 @@ void launch_step(imexds_ctx* c, cudaEvent_t* ev = nullptr) {
   if (ev) cudaEventRecord(ev[1], c->stream);
   k_plan<<<zb, zt, 0, c->stream>>>(c->d, c->n_zone_slots);
   if (ev) cudaEventRecord(ev[2], c->stream);
-  k_sweep<<<c->n_tiles, TILE, 0, c->stream>>>(c->d);
+  if (c->opts.creation)
+    k_sweep<true><<<c->n_tiles, TILE, 0, c->stream>>>(c->d);
+  else
+    k_sweep<false><<<c->n_tiles, TILE, 0, c->stream>>>(c->d);
   if (ev) cudaEventRecord(ev[3], c->stream);
   k_dts<<<zb, zt, 0, c->stream>>>(c->d, c->n_zone_slots);
   if (ev) cudaEventRecord(ev[4], c->stream);
@@ -1098,7 +1207,7 @@ imexds_status run_steps(imexds_ctx* c, long long max_steps, bool until_done) {
     c->stream = cs;
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     long long l0 = c->launches;
-    for (int s = 0; s < S; ++s) launch_step(c, c->timing ? &c->tev[6 * s] : nullptr);
+    for (int s = 0; s < S; ++s) launch_step(c);
     k_count_active<<<1, 256, 0, cs>>>(c->d, c->n_inst);
     cudaGraph_t g;
     CK(cudaStreamEndCapture(cs, &g));
@@ -1110,6 +1219,22 @@ imexds_status run_steps(imexds_ctx* c, long long max_steps, bool until_done) {
     c->graph_steps = S;
   }
   long long done = 0;
+  if (c->timing) {
+    // measurement mode: eager launches with an event between the kernels of every step
+    while (done < max_steps) {
+      int n = (int)std::min<long long>(S, max_steps - done);
+      for (int s = 0; s < n; ++s) launch_step(c, &c->tev[6 * s]);
+      k_count_active<<<1, 256, 0, c->stream>>>(c->d, c->n_inst);
+      c->launches += 1;
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(c->h_active, &c->d.ctrl->n_active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      accumulate_times(c, n);
+      done += n;
+      if (until_done && *c->h_active == 0) break;
+    }
+    return IMEXDS_OK;
+  }
   while (done < max_steps) {
     if (!until_done && max_steps - done < S) {
       for (long long s = done; s < max_steps; ++s) launch_step(c);
@@ -1122,11 +1247,10 @@ imexds_status run_steps(imexds_ctx* c, long long max_steps, bool until_done) {
     CK(cudaGraphLaunch(c->graph, c->stream));
     c->launches += 5 * S + 1;
     done += S;
-    if (until_done || c->timing) {
+    if (until_done) {
       CK(cudaMemcpyAsync(c->h_active, &c->d.ctrl->n_active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
       CK(cudaStreamSynchronize(c->stream));
-      if (c->timing) accumulate_times(c, S);
-      if (until_done && *c->h_active == 0) break;
+      if (*c->h_active == 0) break;
     }
   }
   CK(cudaStreamSynchronize(c->stream));

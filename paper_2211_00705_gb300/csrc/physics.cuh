@@ -67,6 +67,42 @@ __device__ inline void hll(const Phase& e, double rl, double ml, double rr, doub
   }
 }
 
+// The same HLL flux arranged for the sweep: the physical fluxes come in precomputed (u = m/rho once per
+// cell) and one reciprocal of S_R - S_L serves both components; every product-sum is an explicit
+// fused multiply-add so that every kernel computing the flux at a face gets the same bits.
+__device__ inline double pressure_fma(const Phase& e, double rho) {
+  return e.kind == 0 ? e.a2 * rho : __fma_rn(e.a2, rho - e.rho0, e.p0);
+}
+__device__ inline void hll_pre(double a, double rl, double ml, double ul, double fl1, double rr, double mr, double ur,
+                               double fr1, double& F0, double& F1) {
+  double umin = ul < ur ? ul : ur;
+  double umax = ul < ur ? ur : ul;
+  double SL = umin - a, SR = umax + a;
+  if (SL >= 0.0) {
+    F0 = ml;
+    F1 = fl1;
+  } else if (SR <= 0.0) {
+    F0 = mr;
+    F1 = fr1;
+  } else {
+    double inv = 1.0 / (SR - SL);
+    double slsr = SL * SR;
+    F0 = __fma_rn(-SL, mr, __fma_rn(slsr, rr - rl, SR * ml)) * inv;
+    F1 = __fma_rn(-SL, fr1, __fma_rn(slsr, mr - ml, SR * fl1)) * inv;
+  }
+}
+__device__ inline void phys_flux_fast(const Phase& e, double r, double m, double& F0, double& F1) {
+  double u = m / r;
+  F0 = m;
+  F1 = __fma_rn(m, u, pressure_fma(e, r));
+}
+__device__ inline void hll_fast(const Phase& e, double rl, double ml, double rr, double mr, double& F0, double& F1) {
+  double ul = ml / rl, ur = mr / rr;
+  double fl1 = __fma_rn(ml, ul, pressure_fma(e, rl));
+  double fr1 = __fma_rn(mr, ur, pressure_fma(e, rr));
+  hll_pre(e.a, rl, ml, ul, fl1, rr, mr, ur, fr1, F0, F1);
+}
+
 // Outer-wave function f_K of App. A for an isothermal linear EOS: shock sqrt((p* - p_K)(v_K - v*)),
 // rarefaction a ln(rho*/rho_K); derivative in dfdp.
 __device__ inline double wave_f(const Phase& e, double pstar, double rhoK, double& dfdp) {
@@ -232,6 +268,163 @@ __device__ inline PBOut pb_solve(const Fluid& F, const Opts& o, double tau, int 
   R.pl = x0;
   R.pr = x1;
   R.ok = 1;
+  return R;
+}
+
+// ---- the same boundary solve arranged for repeated calls: one logarithm per side and evaluation
+// (ln(rho*/rho_K) = ln(rho*/rho_sat) + ln(rho_sat/rho_K) with the last term fixed per solve), reciprocals
+// of the fixed data computed once, and an optional starting point (the previous solution) with the
+// HLLC start of App. A as fallback. Converges to the same root as pb_solve to round-off.
+struct SideData {
+  const Phase* E;
+  double rK, pK, invK, CK, ia2, ia, isat;
+};
+
+__device__ inline SideData side_data(const Phase& e, double rK) {
+  SideData s;
+  s.E = &e;
+  s.rK = rK;
+  s.pK = pressure(e, rK);
+  s.invK = 1.0 / rK;
+  s.isat = 1.0 / e.rho_sat;
+  s.CK = log(e.rho_sat * s.invK);
+  s.ia2 = 1.0 / e.a2;
+  s.ia = 1.0 / e.a;
+  return s;
+}
+
+struct SideEval {
+  double p, v, g, dv, f, df;
+};
+
+__device__ inline bool side_eval(const SideData& s, double p, SideEval& o) {
+  const Phase& e = *s.E;
+  double rs = e.kind == 0 ? p * s.ia2 : e.rho0 + (p - e.p0) * s.ia2;
+  if (!(rs > 0.0) || !isfinite(p)) return false;
+  double v = 1.0 / rs;
+  double Ls = log(rs * s.isat);
+  o.p = p;
+  o.v = v;
+  o.g = e.a2 * Ls;
+  o.dv = -v * v * s.ia2;
+  if (p > s.pK) {
+    double dvk = s.invK - v;
+    double q = (p - s.pK) * dvk;
+    double f = sqrt(q);
+    double dq = dvk + (p - s.pK) * v * v * s.ia2;
+    o.f = f;
+    o.df = (f > 0.0) ? 0.5 * dq / f : v * s.ia;
+  } else {
+    o.f = e.a * (Ls + s.CK);
+    o.df = v * s.ia;
+  }
+  return true;
+}
+
+struct PBFast {
+  double G0, G1, J00, J01, J10, J11, z;
+  SideEval L, R;
+};
+
+__device__ inline bool pbf_eval(const SideData& sl, const SideData& sr, bool left_vap, double tau, double du,
+                                double pl, double pr, PBFast& S) {
+  if (!side_eval(sl, pl, S.L) || !side_eval(sr, pr, S.R)) return false;
+  const SideEval &L = S.L, &R = S.R;
+  double pV = left_vap ? pl : pr;
+  double jp = pr - pl, jv = R.v - L.v, vs = L.v + R.v;
+  double Q = (R.g - L.g) - 0.5 * jp * vs;
+  double dQl = -L.v + 0.5 * vs - 0.5 * jp * L.dv;
+  double dQr = R.v - 0.5 * vs - 0.5 * jp * R.dv;
+  double dzl = tau * ((left_vap ? Q : 0.0) + pV * dQl);
+  double dzr = tau * ((left_vap ? 0.0 : Q) + pV * dQr);
+  double z = tau * pV * Q;
+  S.z = z;
+  S.G0 = jp + z * z * jv;
+  S.G1 = L.f + R.f + z * jv + du;
+  S.J00 = -1.0 + 2.0 * z * dzl * jv - z * z * L.dv;
+  S.J01 = 1.0 + 2.0 * z * dzr * jv + z * z * R.dv;
+  S.J10 = L.df + dzl * jv - z * L.dv;
+  S.J11 = R.df + dzr * jv + z * R.dv;
+  return isfinite(S.G0) && isfinite(S.G1);
+}
+
+// Newton-Armijo from (x0, x1); returns 1 on convergence.
+__device__ inline int pbf_newton(const Fluid& F, const Opts& o, const SideData& sl, const SideData& sr, bool left_vap,
+                                 double tau, double du, double imp, double& x0, double& x1, PBFast& S, int& iters) {
+  if (!pbf_eval(sl, sr, left_vap, tau, du, x0, x1, S)) return 0;
+  double nrm = hypot(S.G0 / imp, S.G1);
+  bool conv = (nrm == 0.0);
+  int it = 0;
+  while (!conv && it < o.newton_itmax) {
+    ++it;
+    double det = S.J00 * S.J11 - S.J01 * S.J10;
+    if (!isfinite(det) || det == 0.0) break;
+    double idet = 1.0 / det;
+    double d0 = -(S.J11 * S.G0 - S.J01 * S.G1) * idet;
+    double d1 = -(-S.J10 * S.G0 + S.J00 * S.G1) * idet;
+    double lam = 1.0;
+    bool acc = false;
+    PBFast T;
+    for (int ls = 0; ls <= 20; ++ls) {
+      if (pbf_eval(sl, sr, left_vap, tau, du, x0 + lam * d0, x1 + lam * d1, T)) {
+        double nt = hypot(T.G0 / imp, T.G1);
+        if (nt <= (1.0 - 1e-4 * lam) * nrm) {
+          acc = true;
+          nrm = nt;
+          break;
+        }
+      }
+      lam *= 0.5;
+    }
+    double s0 = fabs(d0) / fmax(fabs(x0), F.p_sat);
+    double s1 = fabs(d1) / fmax(fabs(x1), F.p_sat);
+    if (!acc) {
+      if (fmax(s0, s1) <= 1e-9) conv = true;
+      break;
+    }
+    x0 += lam * d0;
+    x1 += lam * d1;
+    S = T;
+    if (lam * fmax(s0, s1) <= o.newton_tol || nrm == 0.0) conv = true;
+  }
+  iters += it;
+  return conv ? 1 : 0;
+}
+
+// Boundary solve with an optional start (gl, gr > 0 ... valid pressures); writes the converged star
+// pressures back to gl/gr for the next call.
+__device__ inline PBOut pb_solve_warm(const Fluid& F, const Opts& o, double tau, int phl, double rl, double ml, int phr,
+                                      double rr, double mr, double& gl, double& gr) {
+  PBOut R;
+  R.ok = 0;
+  R.iters = 0;
+  R.F0 = R.F1 = R.w = R.z = R.pl = R.pr = 0.0;
+  double ul = ml / rl, ur = mr / rr;
+  const SideData sl = side_data(F.ph[phl], rl), sr = side_data(F.ph[phr], rr);
+  const bool left_vap = (phl == VAP);
+  const double imp = rl * F.ph[phl].a + rr * F.ph[phr].a, du = ur - ul;
+  PBFast S;
+  double x0 = gl, x1 = gr;
+  int ok = 0;
+  if (gl != 0.0 || gr != 0.0) ok = pbf_newton(F, o, sl, sr, left_vap, tau, du, imp, x0, x1, S, R.iters);
+  if (!ok) {
+    pb_initial_guess(F, phl, rl, ul, phr, rr, ur, x0, x1);
+    ok = pbf_newton(F, o, sl, sr, left_vap, tau, du, imp, x0, x1, S, R.iters);
+  }
+  if (!ok) return R;
+  double ulS = ul - S.L.f, urS = ur + S.R.f;
+  double uV = left_vap ? ulS : urS;
+  double vV = left_vap ? S.L.v : S.R.v;
+  double pV = left_vap ? x0 : x1;
+  R.z = S.z;
+  R.w = uV + R.z * vV;
+  R.F0 = -R.z;
+  R.F1 = -R.z * uV + pV;
+  R.pl = x0;
+  R.pr = x1;
+  R.ok = 1;
+  gl = x0;
+  gr = x1;
   return R;
 }
 
