@@ -72,6 +72,9 @@ typedef struct {
   double split_ratio;  /* a boundary cell wider than split_ratio * h is split (2) */
   int creation;        /* 1: detect cavitation / nucleation at same-phase faces (App. B) (0) */
   int zone_capacity;   /* zone records per instance (0 = automatic: 4 + 2 * phase boundaries) */
+  int schedule;        /* 0 automatic, 1 one launch per kernel and step (graph of 8 steps), 2 instance
+                          groups advanced by one resident launch (0) */
+  int group_cells;     /* lattice cells per instance group (0 = 16384) */
 } imexds_options;
 
 /* A batch of independent 1-D problems on [x_left[i], x_right[i]] with n_lattice[i] background
@@ -130,12 +133,19 @@ imexds_status imexds_set_states_device(imexds_ctx* ctx, const int32_t* cell_offs
  * copies only). */
 imexds_status imexds_reset(imexds_ctx* ctx);
 
+/* Choose the schedule for the next calls (values of imexds_options.schedule). */
+imexds_status imexds_set_schedule(imexds_ctx* ctx, int32_t schedule);
+
 /* Measurement: with on != 0, steps are launched without the step graph and CUDA events are recorded
- * around each of the five kernels of a step; imexds_get_kernel_times returns, per kernel (0 pre-solve,
- * 1 plan, 2 sweep, 3 dual time, 4 post), the summed duration in ms and the number of timed launches
- * since timing was switched on. Arrays have 5 entries. */
+ * around each kernel; imexds_get_kernel_times returns, per kernel (0 pre-solve, 1 plan, 2 sweep,
+ * 3 dual time, 4 post, 5 group-resident kernel), the summed duration in ms and the number of timed
+ * launches since timing was switched on. Arrays have 6 entries. */
 imexds_status imexds_set_kernel_timing(imexds_ctx* ctx, int32_t on);
 imexds_status imexds_get_kernel_times(imexds_ctx* ctx, double* total_ms, int64_t* launches);
+
+/* Diagnostic: evaluate the library's table-driven logarithm (Tang's method, used in the boundary
+ * solves) and CUDA's log on n host values x > 0; results in the host arrays fast and ref. */
+imexds_status imexds_check_log(int32_t n, const double* x, double* fast, double* ref);
 
 void imexds_destroy(imexds_ctx* ctx);
 const char* imexds_status_string(imexds_status s);

@@ -45,6 +45,7 @@ constexpr long long kRunToMaxSteps = 20000000;  // run_to gives up (IMEXDS_ERR_T
 
 struct Zone {
   int alive, inst, A, B, nc;
+  int changed;                   // footprint changed in this step (merge, release, split, creation)
   int merge_mask;
   int pullL, pullR, oA, oB;
   int nblk;
@@ -105,9 +106,7 @@ __device__ inline unsigned long long dbits(double x) { return (unsigned long lon
 // ------------------------------------------------------------------------------------------ k_pre
 // Phase-boundary solves at U^n predict the widths of the cells next to each boundary; a cell that would
 // fall below max(alpha_min h, h_i / 2) is marked for merging (Sec. 2.3, Sec. 3.4).
-__global__ void k_pre(Dev d, int n_zone_slots) {
-  int zi = blockIdx.x * blockDim.x + threadIdx.x;
-  if (zi >= n_zone_slots) return;
+__device__ void pre_zone(const Dev& d, int zi) {
   Zone& Z = d.zones[zi];
   Z.merge_mask = 0;
   if (!Z.alive) return;
@@ -164,9 +163,7 @@ __device__ inline void zone_erase_cell(Zone& Z, int b) {
 // neighbourhoods: at every boundary the smaller adjacent cell is the tiny cell k; {k-1, k, k+1} are
 // joined where they overlap. Cells outside the zone taking part (one lattice cell per side) are
 // "pulled": the sweep skips them and k_dts updates them.
-__global__ void k_plan(Dev d, int n_zone_slots) {
-  int zi = blockIdx.x * blockDim.x + threadIdx.x;
-  if (zi >= n_zone_slots) return;
+__device__ void plan_zone(const Dev& d, int zi) {
   Zone& Z = d.zones[zi];
   if (!Z.alive) return;
   Inst& I = d.inst[Z.inst];
@@ -237,7 +234,10 @@ __global__ void k_plan(Dev d, int n_zone_slots) {
     }
     merges++;
   }
-  if (merges) atomicAdd((unsigned long long*)&I.stats[4], (unsigned long long)merges);
+  if (merges) {
+    atomicAdd((unsigned long long*)&I.stats[4], (unsigned long long)merges);
+    Z.changed = 1;
+  }
   // widths predicted for t^{n+1} (Sec. 3.1 treats the implicit neighbourhood on the mesh at t^{n+1});
   // after a merge the boundary speeds are solved again from the merged states
   {
@@ -306,178 +306,212 @@ __global__ void k_plan(Dev d, int n_zone_slots) {
   for (int j = Z.oA; j < Z.oB; ++j) own[j] = zi;
 }
 
-// ------------------------------------------------------------------------------------------ k_sweep
-// Algorithm 1, Step 1 on one tile of free lattice cells: HLL fluxes from U^n, the explicit update of
-// Eq. update expl time (Eq. godunov_meth:nonunif next to a creation face), and the next step's
-// wave-speed maximum. u = m/rho and the momentum flux are formed once per cell and staged in shared
-// memory; a face next to a zone sees the zone's edge state. CREATION adds the detection and the
-// creation solve of App. B at faces between two free cells.
+// ------------------------------------------------------------------------------------------ sweep
+// Algorithm 1, Step 1 on a 32-cell tile of one instance, one warp per tile: HLL fluxes from U^n at the
+// faces of free lattice cells, the explicit update of Eq. update expl time (Eq. godunov_meth:nonunif
+// next to a creation face) and the tile's wave-speed maximum. Lane l owns cell j0+l and the face on its
+// left; the right-face flux comes from lane l+1 (lane 31 computes the tile's last face itself). u = m/rho
+// and the momentum flux are formed once per cell. A face next to a zone sees the zone's edge state.
+// CREATION adds detection and the creation solve of App. B at faces between two free cells.
+struct CellS {
+  int ow, ph;  // owner (-1 free, >= 0 zone slot, -2 outside the domain), phase
+  double r, m, u, f1;
+};
+
+__device__ inline CellS load_cell(const Dev& d, const Inst& I, int j) {
+  CellS c;
+  c.ow = -2;
+  c.ph = 0;
+  c.r = 1.0;
+  c.m = c.u = c.f1 = 0.0;
+  if (j >= 0 && j < I.N) {
+    const int g = I.lat_off + j;
+    c.ow = d.own[g];
+    c.ph = d.phase[g];
+    if (c.ow < 0) {
+      c.r = d.rho[I.parity][g];
+      c.m = d.m[I.parity][g];
+      c.u = c.m / c.r;
+      c.f1 = __fma_rn(c.m, c.u, pressure_fma(c_fluid.ph[c.ph], c.r));
+    }
+  }
+  return c;
+}
+
+__device__ inline CellS shfl_up_cell(const CellS& c) {
+  CellS o;
+  o.ow = __shfl_up_sync(0xffffffffu, c.ow, 1);
+  o.ph = __shfl_up_sync(0xffffffffu, c.ph, 1);
+  o.r = __shfl_up_sync(0xffffffffu, c.r, 1);
+  o.m = __shfl_up_sync(0xffffffffu, c.m, 1);
+  o.u = __shfl_up_sync(0xffffffffu, c.u, 1);
+  o.f1 = __shfl_up_sync(0xffffffffu, c.f1, 1);
+  return o;
+}
+
+// cavitation / nucleation detection at a face between two free cells (App. B)
+__device__ inline int detect_face(const CellS& L, const CellS& R) {
+  if (L.ow != -1 || R.ow != -1) return 0;
+  const int P = R.ph;
+  double ps = nopt_star(c_fluid.ph[P], L.r, L.u, R.r, R.u);
+  return (P == LIQ) ? (ps < c_fluid.p_min) : (ps > c_fluid.p_tilde);
+}
+
+struct FaceFlux {
+  double F0L, F1L, F0R, F1R, WL, WR;  // seen from the left / right cell; face speeds (creation only)
+};
+
+// Flux at face f between cells L and R (at least one of them free). `create`: App. B at this face.
 template <bool CREATION>
-__global__ void __launch_bounds__(TILE) k_sweep(Dev d) {
-  __shared__ double sr[TILE + 3], sm[TILE + 3], su[TILE + 3], sf[TILE + 3];
-  __shared__ int sown[TILE + 3];
-  __shared__ unsigned char sph[TILE + 3];
-  __shared__ double F0L[TILE + 1], F1L[TILE + 1], F0R[TILE + 1], F1R[TILE + 1];
-  __shared__ double WL[CREATION ? TILE + 1 : 1], WR[CREATION ? TILE + 1 : 1];
-  __shared__ int sdet[CREATION ? TILE + 2 : 1];
-  __shared__ double red[TILE / 32];
-  const int2 tile = d.tiles[blockIdx.x];
-  Inst& I = d.inst[tile.x];
-  if (!I.active || I.status) return;
-  const int N = I.N, j0 = tile.y, cur = I.parity;
-  const int nt = min(TILE, N - j0);
-  const double* lr = d.rho[cur] + I.lat_off;
-  const double* lm = d.m[cur] + I.lat_off;
-  double* nr = d.rho[cur ^ 1] + I.lat_off;
-  double* nm = d.m[cur ^ 1] + I.lat_off;
-  const unsigned char* lph = d.phase + I.lat_off;
-  const int* lown = d.own + I.lat_off;
-  const double h = I.h, dt = I.dt, lam = dt / h;
-  // cells j0-2 .. j0+nt (shared index q = j - j0 + 2)
-  for (int q = threadIdx.x; q < nt + 3; q += blockDim.x) {
-    int j = j0 - 2 + q;
-    int ow = -2;  // outside the domain
-    if (j >= 0 && j < N) {
-      ow = lown[j];
-      int ph = lph[j];
-      sph[q] = (unsigned char)ph;
-      if (ow < 0) {
-        double r = lr[j], m = lm[j];
-        double u = m / r;
-        sr[q] = r;
-        sm[q] = m;
-        su[q] = u;
-        sf[q] = __fma_rn(m, u, pressure_fma(c_fluid.ph[ph], r));
+__device__ inline FaceFlux face_flux(const Dev& d, Inst& I, int ii, int f, const CellS& L, const CellS& R, bool create,
+                                     bool record) {
+  FaceFlux o;
+  o.WL = o.WR = 0.0;
+  if (L.ow == -2) {  // left domain end: transmissive
+    o.F0L = o.F0R = R.m;
+    o.F1L = o.F1R = R.f1;
+    return o;
+  }
+  if (R.ow == -2) {
+    o.F0L = o.F0R = L.m;
+    o.F1L = o.F1R = L.f1;
+    return o;
+  }
+  const int P = (L.ow == -1) ? L.ph : R.ph;
+  const Phase& E = c_fluid.ph[P];
+  double rl, ml, ul, fl1, rr, mr, ur, fr1;
+  if (L.ow >= 0) {
+    const Zone& Z = d.zones[L.ow];
+    rl = Z.eR0;
+    ml = Z.eR1;
+    ul = ml / rl;
+    fl1 = __fma_rn(ml, ul, pressure_fma(E, rl));
+  } else {
+    rl = L.r;
+    ml = L.m;
+    ul = L.u;
+    fl1 = L.f1;
+  }
+  if (R.ow >= 0) {
+    const Zone& Z = d.zones[R.ow];
+    rr = Z.eL0;
+    mr = Z.eL1;
+    ur = mr / rr;
+    fr1 = __fma_rn(mr, ur, pressure_fma(E, rr));
+  } else {
+    rr = R.r;
+    mr = R.m;
+    ur = R.u;
+    fr1 = R.f1;
+  }
+  if (CREATION && create) {
+    // fluxes of Eq. flux:cavitation / flux:nucleation with each boundary's own mass flux
+    CreateOut Cr = creation_solve(c_fluid, c_opts, I.tau, P, rl, ml, rr, mr);
+    atomicAdd((unsigned long long*)&I.stats[3], (unsigned long long)Cr.iters);
+    if (!Cr.ok) {
+      set_status(I, IMEXDS_ERR_PB_NOCONV);
+      o.F0L = o.F1L = o.F0R = o.F1R = 0.0;
+      return o;
+    }
+    o.F0L = -Cr.z1;
+    o.F1L = -Cr.z1 * Cr.uC + Cr.pC;
+    o.F0R = -Cr.z2;
+    o.F1R = -Cr.z2 * Cr.uC + Cr.pC;
+    o.WL = Cr.w1;
+    o.WR = Cr.w2;
+    if (record) {
+      const double h = I.h, dt = I.dt;
+      int k = atomicAdd(&I.n_ev, 1);
+      if (k < EV_CAP) {
+        Event& Ev = d.ev[ii * EV_CAP + k];
+        Ev.face = f;
+        Ev.w1 = Cr.w1;
+        Ev.w2 = Cr.w2;
+        Ev.rhoC = Cr.rhoC;
+        Ev.mC = Cr.rhoC * Cr.uC;
+        Ev.phC = 1 - P;
+        Ev.hl = h + (Cr.w1 - 0.0) * dt;
+        Ev.hr = h + (0.0 - Cr.w2) * dt;
+      } else {
+        set_status(I, IMEXDS_ERR_CAPACITY);
       }
     }
-    sown[q] = ow;
+    return o;
   }
-  __syncthreads();
+  hll_pre(E.a, rl, ml, ul, fl1, rr, mr, ur, fr1, o.F0L, o.F1L);
+  o.F0R = o.F0L;
+  o.F1R = o.F1L;
+  return o;
+}
+
+// One 32-cell tile; all 32 lanes of the calling warp take part. Returns the tile's wave-speed maximum
+// (also folded into the instance's atomic maximum).
+template <bool CREATION>
+__device__ void sweep_tile32(const Dev& d, int ii, int j0) {
+  const int lane = threadIdx.x & 31;
+  Inst& I = d.inst[ii];
+  const int N = I.N;
+  const int j = j0 + lane;
+  const CellS C = load_cell(d, I, j);
+  CellS Lc = shfl_up_cell(C);
+  if (lane == 0) Lc = load_cell(d, I, j0 - 1);
+  CellS Rx;
+  if (lane == 31) Rx = load_cell(d, I, j0 + 32);
+  int det_j = 0, det_jm1 = 0, det_x = 0;
   if (CREATION) {
-    // detection at faces f = j0-1 .. j0+nt (index t = f - j0 + 1), only between two free cells
-    for (int t = threadIdx.x; t < nt + 2; t += blockDim.x) {
-      int q = t + 1;
-      int det = 0;
-      if (sown[q - 1] == -1 && sown[q] == -1) {
-        int P = sph[q];
-        double ps = nopt_star(c_fluid.ph[P], sr[q - 1], su[q - 1], sr[q], su[q]);
-        det = (P == LIQ) ? (ps < c_fluid.p_min) : (ps > c_fluid.p_tilde);
-      }
-      sdet[t] = det;
+    det_j = (j <= N) ? detect_face(Lc, C) : 0;
+    det_jm1 = __shfl_up_sync(0xffffffffu, det_j, 1);
+    if (lane == 0) {
+      CellS L2 = load_cell(d, I, j0 - 2);
+      det_jm1 = detect_face(L2, Lc);
     }
-    __syncthreads();
+    if (lane == 31) det_x = detect_face(C, Rx);
   }
-  // fluxes at faces f = j0 .. j0+nt (index t = f - j0); cells left/right of face t: q = t+1, t+2
-  for (int t = threadIdx.x; t <= nt; t += blockDim.x) {
-    const int f = j0 + t, ql = t + 1, qr = t + 2;
-    if (CREATION) {
-      WL[t] = 0.0;
-      WR[t] = 0.0;
-    }
-    const bool need = (t < nt && sown[qr] == -1) || (t > 0 && sown[ql] == -1);
-    if (!need) continue;
-    double a0, a1;
-    if (f == 0) {
-      a0 = sm[qr];
-      a1 = sf[qr];
-    } else if (f == N) {
-      a0 = sm[ql];
-      a1 = sf[ql];
-    } else {
-      const int P = (sown[ql] == -1) ? sph[ql] : sph[qr];
-      const Phase& E = c_fluid.ph[P];
-      double rl, ml, ul, fl1, rr, mr, ur, fr1;
-      if (sown[ql] >= 0) {
-        const Zone& Z = d.zones[sown[ql]];
-        rl = Z.eR0;
-        ml = Z.eR1;
-        ul = ml / rl;
-        fl1 = __fma_rn(ml, ul, pressure_fma(E, rl));
-      } else {
-        rl = sr[ql];
-        ml = sm[ql];
-        ul = su[ql];
-        fl1 = sf[ql];
-      }
-      if (sown[qr] >= 0) {
-        const Zone& Z = d.zones[sown[qr]];
-        rr = Z.eL0;
-        mr = Z.eL1;
-        ur = mr / rr;
-        fr1 = __fma_rn(mr, ur, pressure_fma(E, rr));
-      } else {
-        rr = sr[qr];
-        mr = sm[qr];
-        ur = su[qr];
-        fr1 = sf[qr];
-      }
-      if (CREATION && sdet[t + 1] && !sdet[t]) {
-        // App. B: a cell of the other phase is created at this face (fluxes of Eq. flux:cavitation /
-        // flux:nucleation with each boundary's own mass flux)
-        CreateOut Cr = creation_solve(c_fluid, c_opts, I.tau, P, rl, ml, rr, mr);
-        atomicAdd((unsigned long long*)&I.stats[3], (unsigned long long)Cr.iters);
-        if (!Cr.ok) {
-          set_status(I, IMEXDS_ERR_PB_NOCONV);
-          F0L[t] = F1L[t] = F0R[t] = F1R[t] = 0.0;
-          continue;
-        }
-        F0L[t] = -Cr.z1;
-        F1L[t] = -Cr.z1 * Cr.uC + Cr.pC;
-        F0R[t] = -Cr.z2;
-        F1R[t] = -Cr.z2 * Cr.uC + Cr.pC;
-        WL[t] = Cr.w1;
-        WR[t] = Cr.w2;
-        if (t < nt) {  // the tile owning the right cell records the event
-          int k = atomicAdd(&I.n_ev, 1);
-          if (k < EV_CAP) {
-            Event& Ev = d.ev[tile.x * EV_CAP + k];
-            Ev.face = f;
-            Ev.w1 = Cr.w1;
-            Ev.w2 = Cr.w2;
-            Ev.rhoC = Cr.rhoC;
-            Ev.mC = Cr.rhoC * Cr.uC;
-            Ev.phC = 1 - P;
-            Ev.hl = h + (Cr.w1 - 0.0) * dt;
-            Ev.hr = h + (0.0 - Cr.w2) * dt;
-          } else {
-            set_status(I, IMEXDS_ERR_CAPACITY);
-          }
-        }
-        continue;
-      }
-      hll_pre(E.a, rl, ml, ul, fl1, rr, mr, ur, fr1, a0, a1);
-    }
-    F0L[t] = F0R[t] = a0;
-    F1L[t] = F1R[t] = a1;
-  }
-  __syncthreads();
+  // face j (left face of cell j): needed by cell j, and by cell j-1 when it is in this tile
+  const bool cfree = (C.ow == -1);
+  const bool need = (j <= N) && (cfree || (lane > 0 && Lc.ow == -1));
+  FaceFlux fj;
+  fj.F0L = fj.F1L = fj.F0R = fj.F1R = fj.WL = fj.WR = 0.0;
+  if (need) fj = face_flux<CREATION>(d, I, ii, j, Lc, C, CREATION && det_j && !det_jm1, true);
+  // right face of cell j
+  FaceFlux fr;
+  fr.F0L = __shfl_down_sync(0xffffffffu, fj.F0L, 1);
+  fr.F1L = __shfl_down_sync(0xffffffffu, fj.F1L, 1);
+  fr.WL = __shfl_down_sync(0xffffffffu, fj.WL, 1);
+  if (lane == 31 && cfree && j < N)
+    fr = face_flux<CREATION>(d, I, ii, j + 1, C, Rx, CREATION && det_x && !det_j, false);
   double smax = 0.0;
-  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-    const int q = t + 2;
-    if (sown[q] != -1) continue;
-    const int j = j0 + t;
+  if (cfree && j < N) {
+    const double h = I.h, dt = I.dt;
+    const int g = I.lat_off + j;
     double r1, m1;
-    if (CREATION && (WL[t + 1] != 0.0 || WR[t] != 0.0)) {
-      double hnp1 = h + (WL[t + 1] - WR[t]) * dt;
-      r1 = (h * sr[q] - dt * (F0L[t + 1] - F0R[t])) / hnp1;
-      m1 = (h * sm[q] - dt * (F1L[t + 1] - F1R[t])) / hnp1;
+    if (CREATION && (fr.WL != 0.0 || fj.WR != 0.0)) {
+      double hnp1 = h + (fr.WL - fj.WR) * dt;
+      r1 = (h * C.r - dt * (fr.F0L - fj.F0R)) / hnp1;
+      m1 = (h * C.m - dt * (fr.F1L - fj.F1R)) / hnp1;
     } else {
-      r1 = __fma_rn(-lam, F0L[t + 1] - F0R[t], sr[q]);
-      m1 = __fma_rn(-lam, F1L[t + 1] - F1R[t], sm[q]);
+      const double lam = dt / h;
+      r1 = __fma_rn(-lam, fr.F0L - fj.F0R, C.r);
+      m1 = __fma_rn(-lam, fr.F1L - fj.F1R, C.m);
     }
-    nr[j] = r1;
-    nm[j] = m1;
+    d.rho[I.parity ^ 1][g] = r1;
+    d.m[I.parity ^ 1][g] = m1;
     if (!(r1 > 0.0) || !isfinite(r1) || !isfinite(m1)) set_status(I, IMEXDS_ERR_NONPHYSICAL);
-    smax = fmax(smax, fabs(m1 / r1) + c_fluid.ph[sph[q]].a);
+    smax = fabs(m1 / r1) + c_fluid.ph[C.ph].a;
   }
   for (int off = 16; off > 0; off >>= 1) smax = fmax(smax, __shfl_down_sync(0xffffffffu, smax, off));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = smax;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double sx = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sx = fmax(sx, red[w]);
-    if (sx > 0.0) atomicMax(&I.smax_bits, dbits(sx));
-  }
+  if (lane == 0 && smax > 0.0) atomicMax(&I.smax_bits, dbits(smax));
+}
+
+// Per-step sweep kernel: one warp per 32-cell tile of the tile table.
+template <bool CREATION>
+__global__ void __launch_bounds__(256) k_sweep(Dev d, int n_tiles) {
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (t >= n_tiles) return;
+  const int2 tile = d.tiles[t];
+  const Inst& I = d.inst[tile.x];
+  if (!I.active || I.status) return;
+  sweep_tile32<CREATION>(d, tile.x, tile.y);
 }
 
 // ------------------------------------------------------------------------------------------ k_dts
@@ -526,9 +560,7 @@ __device__ inline bool block_fluxes(const BlockCtx& B, int lo, int hi, const dou
   return true;
 }
 
-__global__ void k_dts(Dev d, int n_zone_slots) {
-  int zi = blockIdx.x * blockDim.x + threadIdx.x;
-  if (zi >= n_zone_slots) return;
+__device__ void dts_zone(const Dev& d, int zi) {
   Zone& Z = d.zones[zi];
   if (!Z.alive) return;
   Inst& I = d.inst[Z.inst];
@@ -734,9 +766,7 @@ __device__ inline int zone_insert_cell(Zone& Z, int pos) {
   return 1;
 }
 
-__global__ void k_post(Dev d, int n_inst) {
-  int ii = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ii >= n_inst) return;
+__device__ void post_inst(const Dev& d, int ii) {
   Inst& I = d.inst[ii];
   if (!I.active) return;
   const double h = I.h;
@@ -811,6 +841,7 @@ __global__ void k_post(Dev d, int n_inst) {
       Z.A += 1;
       Z.fj[0] = Z.A;
       Z.fpb[0] = 0;
+      Z.changed = 1;
     }
     while (Z.nc > 1 && !Z.fpb[Z.nc - 1] && Z.fj[Z.nc - 1] == Z.B - 1 && Z.w[Z.nc - 1] == h) {
       nr[Z.B - 1] = Z.r[Z.nc - 1];
@@ -820,6 +851,7 @@ __global__ void k_post(Dev d, int n_inst) {
       Z.B -= 1;
       Z.fj[Z.nc] = Z.B;
       Z.fpb[Z.nc] = 0;
+      Z.changed = 1;
     }
   }
   // split a zone at an interior run of at least ZONE_GAP regular lattice cells (returned to the lattice);
@@ -881,6 +913,8 @@ __global__ void k_post(Dev d, int n_inst) {
     }
     Z.nc = a;
     Z.B = Z.fj[a];
+    Z.changed = 1;
+    Zn.changed = 1;
   }
   double smax = __longlong_as_double((long long)I.smax_bits);
   // creation events -> new zones
@@ -928,60 +962,73 @@ __global__ void k_post(Dev d, int n_inst) {
     Z.oA = Z.oB = 0;
     Z.merge_mask = 0;
     for (int k = 0; k <= ZC; ++k) Z.pwl[k] = Z.pwr[k] = 0.0;
+    Z.changed = 1;
     smax = fmax(smax, fabs(E.mC / E.rhoC) + c_fluid.ph[E.phC].a);
     creations++;
   }
   I.n_ev = 0;
-  // join zones closer than ZONE_GAP lattice cells (insertion sort by A, then sweep)
+  // join zones closer than ZONE_GAP lattice cells; only zones whose footprint changed in this step are
+  // checked against their neighbours (O(changed x zones))
   for (bool again = true; again;) {
     again = false;
     for (int a = 0; a < I.zone_cap && !again; ++a) {
-      Zone& Za = zones[a];
-      if (!Za.alive) continue;
-      int best = -1;
+      if (!zones[a].alive || !zones[a].changed) continue;
+      // nearest zone to the left (largest B <= A_a) and to the right (smallest A >= B_a)
+      int left = -1, right = -1;
       for (int b = 0; b < I.zone_cap; ++b) {
-        if (b == a || !zones[b].alive || zones[b].A < Za.B) continue;
-        if (best < 0 || zones[b].A < zones[best].A) best = b;
+        if (b == a || !zones[b].alive) continue;
+        if (zones[b].A >= zones[a].B) {
+          if (right < 0 || zones[b].A < zones[right].A) right = b;
+        } else if (zones[b].B <= zones[a].A) {
+          if (left < 0 || zones[b].B > zones[left].B) left = b;
+        }
       }
-      if (best < 0) continue;
-      Zone& Zb = zones[best];
-      int gap = Zb.A - Za.B;
-      if (gap >= ZONE_GAP) continue;
-      if (Za.nc + gap + Zb.nc > ZC) {
-        set_status(I, IMEXDS_ERR_CAPACITY);
-        break;
+      int pairs[2][2] = {{left, a}, {a, right}};
+      for (int pk = 0; pk < 2 && !again; ++pk) {
+        int ia = pairs[pk][0], ib = pairs[pk][1];
+        if (ia < 0 || ib < 0) continue;
+        Zone& Za = zones[ia];
+        Zone& Zb = zones[ib];
+        int gap = Zb.A - Za.B;
+        if (gap >= ZONE_GAP) continue;
+        if (Za.nc + gap + Zb.nc > ZC) {
+          set_status(I, IMEXDS_ERR_CAPACITY);
+          break;
+        }
+        for (int j = Za.B; j < Zb.A; ++j) {  // absorb the regular lattice cells in between
+          int i = Za.nc;
+          Za.w[i] = h;
+          Za.r[i] = nr[j];
+          Za.m[i] = nm[j];
+          Za.ph[i] = lph[j];
+          Za.fpb[i] = 0;
+          Za.fj[i] = j;
+          Za.pwl[i] = Za.pwr[i] = 0.0;
+          Za.nc++;
+        }
+        for (int i = 0; i < Zb.nc; ++i) {
+          int k = Za.nc;
+          Za.w[k] = Zb.w[i];
+          Za.r[k] = Zb.r[i];
+          Za.m[k] = Zb.m[i];
+          Za.ph[k] = Zb.ph[i];
+          Za.fpb[k] = Zb.fpb[i];
+          Za.fj[k] = Zb.fj[i];
+          Za.fx[k] = Zb.fx[i];
+          Za.pwl[k] = Zb.pwl[i];
+          Za.pwr[k] = Zb.pwr[i];
+          Za.nc++;
+        }
+        Za.fpb[Za.nc] = 0;
+        Za.fj[Za.nc] = Zb.B;
+        Za.B = Zb.B;
+        Za.changed = 1;
+        Zb.alive = 0;
+        again = true;
       }
-      for (int j = Za.B; j < Zb.A; ++j) {  // absorb the regular lattice cells in between
-        int i = Za.nc;
-        Za.w[i] = h;
-        Za.r[i] = nr[j];
-        Za.m[i] = nm[j];
-        Za.ph[i] = lph[j];
-        Za.fpb[i] = 0;
-        Za.fj[i] = j;
-        Za.pwl[i] = Za.pwr[i] = 0.0;
-        Za.nc++;
-      }
-      for (int i = 0; i < Zb.nc; ++i) {
-        int k = Za.nc;
-        Za.w[k] = Zb.w[i];
-        Za.r[k] = Zb.r[i];
-        Za.m[k] = Zb.m[i];
-        Za.ph[k] = Zb.ph[i];
-        Za.fpb[k] = Zb.fpb[i];
-        Za.fj[k] = Zb.fj[i];
-        Za.fx[k] = Zb.fx[i];
-        Za.pwl[k] = Zb.pwl[i];
-        Za.pwr[k] = Zb.pwr[i];
-        Za.nc++;
-      }
-      Za.fpb[Za.nc] = 0;
-      Za.fj[Za.nc] = Zb.B;
-      Za.B = Zb.B;
-      Zb.alive = 0;
-      again = true;
     }
   }
+  for (int z = 0; z < I.zone_cap; ++z) zones[z].changed = 0;
   if (splits) I.stats[5] += splits;
   if (creations) I.stats[6] += creations;
   // time and next step
@@ -1007,6 +1054,87 @@ __global__ void k_post(Dev d, int n_inst) {
     }
   }
   I.dt = dtn;
+}
+
+// ---------------------------------------------------------------------------------- step kernels
+__device__ inline bool zone_active(const Dev& d, int zi) {
+  const Zone& Z = d.zones[zi];
+  if (!Z.alive) return false;
+  const Inst& I = d.inst[Z.inst];
+  return I.active && !I.status;
+}
+
+__global__ void k_pre(Dev d, int n) {
+  int zi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (zi < n) {
+    d.zones[zi].merge_mask = 0;
+    if (zone_active(d, zi)) pre_zone(d, zi);
+  }
+}
+__global__ void k_plan(Dev d, int n) {
+  int zi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (zi < n && zone_active(d, zi)) plan_zone(d, zi);
+}
+__global__ void k_dts(Dev d, int n) {
+  int zi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (zi < n && zone_active(d, zi)) dts_zone(d, zi);
+}
+__global__ void k_post(Dev d, int n) {
+  int ii = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ii < n && d.inst[ii].active) post_inst(d, ii);
+}
+
+// Group-resident schedule: one CTA advances a group of instances (similar sizes) step after step
+// without any grid-wide synchronisation. Warp 0 runs the per-instance work (lane i: instance i of the
+// group: boundary solves, plan, dual time stepping, grid management); warps 1.. sweep the group's
+// lattice cells while warp 0 runs the dual-time chains of the same step.
+constexpr int GROUP_MAX = 32;
+template <bool CREATION>
+__global__ void __launch_bounds__(256) k_group(Dev d, const int* ginst, const int2* grange, int max_steps) {
+  const int2 gr = grange[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  const int ii = (lane < gr.y) ? ginst[gr.x + lane] : -1;
+  __shared__ int s_more;
+  for (int step = 0; step < max_steps; ++step) {
+    if (warp == 0 && ii >= 0) {
+      Inst& I = d.inst[ii];
+      if (I.active && !I.status) {
+        for (int z = I.zone_off; z < I.zone_off + I.zone_cap; ++z) {
+          d.zones[z].merge_mask = 0;
+          if (d.zones[z].alive) pre_zone(d, z);
+        }
+        for (int z = I.zone_off; z < I.zone_off + I.zone_cap; ++z)
+          if (d.zones[z].alive && !I.status) plan_zone(d, z);
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      if (ii >= 0) {
+        Inst& I = d.inst[ii];
+        if (I.active && !I.status)
+          for (int z = I.zone_off; z < I.zone_off + I.zone_cap; ++z)
+            if (d.zones[z].alive && !I.status) dts_zone(d, z);
+      }
+    } else {
+      // the 32-cell tiles of all active instances of the group, dealt to warps 1..nw-1
+      int t = warp - 1, base = 0;
+      for (int k = 0; k < gr.y; ++k) {
+        const int ik = ginst[gr.x + k];
+        const Inst& I = d.inst[ik];
+        const int nt = (I.active && !I.status) ? (I.N + 31) >> 5 : 0;
+        for (; t < base + nt; t += nw - 1) sweep_tile32<CREATION>(d, ik, (t - base) << 5);
+        base += nt;
+      }
+    }
+    __syncthreads();
+    if (warp == 0 && ii >= 0 && d.inst[ii].active) post_inst(d, ii);
+    if (threadIdx.x == 0) s_more = 0;
+    __syncthreads();
+    if (warp == 0 && ii >= 0 && d.inst[ii].active && !d.inst[ii].status) atomicOr(&s_more, 1);
+    __syncthreads();
+    if (!s_more) break;
+  }
 }
 
 // Wave-speed maximum over all cells of every instance and the first dt (before the first step).
@@ -1087,6 +1215,13 @@ struct imexds_ctx {
   long long launches = 0;
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+  cudaStream_t side = nullptr;            // second stream of the step graph (k_dts beside k_sweep)
+  int schedule = 0;                       // 1 per-step kernels, 2 instance groups (0 auto at set_states)
+  int schedule_opt = 0, group_cells = 16384, use_groups = 0;
+  int n_groups = 0;
+  int* d_ginst = nullptr;
+  int2* d_grange = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   // device copy of the state loaded by the last set_states (imexds_reset)
   Dev saved{};
   // optional per-kernel timing with events captured in the step graph
@@ -1094,6 +1229,7 @@ struct imexds_ctx {
   std::vector<cudaEvent_t> tev;  // 6 events per step of the graph
   double kt_ms[6] = {0, 0, 0, 0, 0, 0};
   long long kt_n[6] = {0, 0, 0, 0, 0, 0};
+  cudaEvent_t gev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -1107,6 +1243,28 @@ imexds_status cuda_fail(cudaError_t e) {
     cudaError_t e_ = (x);                       \
     if (e_ != cudaSuccess) return cuda_fail(e_); \
   } while (0)
+
+// Table of the table-driven logarithm: 128/j and ln(j/128) as a double plus remainder (long double).
+LogTable make_log_table() {
+  LogTable T;
+  for (int t = 0; t < kLogJN; ++t) {
+    int j = kLogJ0 + t;
+    long double c = (long double)j / 128.0L;
+    long double l = logl(c);
+    T.inv_c[t] = (double)(128.0L / (long double)j);
+    T.lnc_hi[t] = (double)l;
+    T.lnc_lo[t] = (double)(l - (long double)T.lnc_hi[t]);
+  }
+  return T;
+}
+
+__global__ void k_check_log(int n, const double* x, double* fast, double* ref) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    fast[i] = fast_log(x[i]);
+    ref[i] = log(x[i]);
+  }
+}
 
 Phase make_phase(const imexds_eos& e, double p_sat) {
   Phase P;
@@ -1132,6 +1290,10 @@ void free_dev(imexds_ctx* c) {
   cudaFree(d.ev);
   cudaFree(d.tiles);
   cudaFree(d.ctrl);
+  cudaFree(c->d_ginst);
+  cudaFree(c->d_grange);
+  c->d_ginst = nullptr;
+  c->d_grange = nullptr;
   d = Dev{};
   Dev& sv = c->saved;
   for (int k = 0; k < 2; ++k) {
@@ -1149,6 +1311,28 @@ void free_dev(imexds_ctx* c) {
 }
 
 // one time step: five kernel launches on the context stream
+// The step as a fork/join: k_sweep and k_dts only read U^n and write disjoint cells, so k_dts runs on a
+// second stream beside k_sweep (used while capturing the step graph).
+void launch_step_forked(imexds_ctx* c) {
+  const int zt = 64;
+  int zb = (c->n_zone_slots + zt - 1) / zt;
+  int ib = (c->n_inst + zt - 1) / zt;
+  k_pre<<<zb, zt, 0, c->stream>>>(c->d, c->n_zone_slots);
+  k_plan<<<zb, zt, 0, c->stream>>>(c->d, c->n_zone_slots);
+  cudaEventRecord(c->fork_ev, c->stream);
+  cudaStreamWaitEvent(c->side, c->fork_ev, 0);
+  k_dts<<<zb, zt, 0, c->side>>>(c->d, c->n_zone_slots);
+  cudaEventRecord(c->join_ev, c->side);
+  const int sb = (c->n_tiles + 7) / 8;
+  if (c->opts.creation)
+    k_sweep<true><<<sb, 256, 0, c->stream>>>(c->d, c->n_tiles);
+  else
+    k_sweep<false><<<sb, 256, 0, c->stream>>>(c->d, c->n_tiles);
+  cudaStreamWaitEvent(c->stream, c->join_ev, 0);
+  k_post<<<ib, zt, 0, c->stream>>>(c->d, c->n_inst);
+  c->launches += 5;
+}
+
 void launch_step(imexds_ctx* c, cudaEvent_t* ev = nullptr) {
   const int zt = 64;
   int zb = (c->n_zone_slots + zt - 1) / zt;
@@ -1158,10 +1342,11 @@ void launch_step(imexds_ctx* c, cudaEvent_t* ev = nullptr) {
   if (ev) cudaEventRecord(ev[1], c->stream);
   k_plan<<<zb, zt, 0, c->stream>>>(c->d, c->n_zone_slots);
   if (ev) cudaEventRecord(ev[2], c->stream);
+  const int sb = (c->n_tiles + 7) / 8;
   if (c->opts.creation)
-    k_sweep<true><<<c->n_tiles, TILE, 0, c->stream>>>(c->d);
+    k_sweep<true><<<sb, 256, 0, c->stream>>>(c->d, c->n_tiles);
   else
-    k_sweep<false><<<c->n_tiles, TILE, 0, c->stream>>>(c->d);
+    k_sweep<false><<<sb, 256, 0, c->stream>>>(c->d, c->n_tiles);
   if (ev) cudaEventRecord(ev[3], c->stream);
   k_dts<<<zb, zt, 0, c->stream>>>(c->d, c->n_zone_slots);
   if (ev) cudaEventRecord(ev[4], c->stream);
@@ -1187,7 +1372,41 @@ imexds_status set_ctrl(imexds_ctx* c, double t_end, int clip) {
   return IMEXDS_OK;
 }
 
+imexds_status run_groups(imexds_ctx* c, long long max_steps, bool until_done) {
+  // one launch advances every group until its instances are done (or max_steps steps)
+  long long done = 0;
+  if (c->timing && !c->gev[0]) {
+    CK(cudaEventCreate(&c->gev[0]));
+    CK(cudaEventCreate(&c->gev[1]));
+  }
+  while (done < max_steps) {
+    int n = (int)std::min<long long>(max_steps - done, 1 << 30);
+    if (c->timing) cudaEventRecord(c->gev[0], c->stream);
+    if (c->opts.creation)
+      k_group<true><<<c->n_groups, 256, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n);
+    else
+      k_group<false><<<c->n_groups, 256, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n);
+    if (c->timing) cudaEventRecord(c->gev[1], c->stream);
+    k_count_active<<<1, 256, 0, c->stream>>>(c->d, c->n_inst);
+    c->launches += 2;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c->h_active, &c->d.ctrl->n_active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->timing) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, c->gev[0], c->gev[1]) == cudaSuccess) {
+        c->kt_ms[5] += ms;
+        c->kt_n[5] += 1;
+      }
+    }
+    done += n;
+    if (!until_done || *c->h_active == 0) break;
+  }
+  return IMEXDS_OK;
+}
+
 imexds_status run_steps(imexds_ctx* c, long long max_steps, bool until_done) {
+  if (c->use_groups) return run_groups(c, max_steps, until_done);
   // Steps are replayed from a CUDA graph of S steps; the host checks the number of active instances
   // after each replay.
   const int S = 8;
@@ -1203,11 +1422,14 @@ imexds_status run_steps(imexds_ctx* c, long long max_steps, bool until_done) {
     c->graph = nullptr;
     cudaStream_t cs;
     CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    if (!c->side) CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    if (!c->fork_ev) CK(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+    if (!c->join_ev) CK(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
     cudaStream_t saved = c->stream;
     c->stream = cs;
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     long long l0 = c->launches;
-    for (int s = 0; s < S; ++s) launch_step(c);
+    for (int s = 0; s < S; ++s) launch_step_forked(c);
     k_count_active<<<1, 256, 0, cs>>>(c->d, c->n_inst);
     cudaGraph_t g;
     CK(cudaStreamEndCapture(cs, &g));
@@ -1320,6 +1542,8 @@ imexds_status imexds_create(const imexds_problem* prob, const imexds_options* op
     o.split_ratio = 2.0;
     o.creation = 0;
     o.zone_capacity = 0;
+    o.schedule = 0;
+    o.group_cells = 0;
   }
   if (!(o.cfl > 0.0) || o.l_max < 1 || o.newton_itmax < 1 || !(o.split_ratio > 1.0)) {
     delete c;
@@ -1328,6 +1552,8 @@ imexds_status imexds_create(const imexds_problem* prob, const imexds_options* op
   c->opts = Opts{o.cfl, o.theta_nb, o.tol_nb, o.tol_k, o.res_mode, o.l_max, o.newton_tol, o.newton_itmax,
                  o.alpha_min, o.split_ratio, o.creation};
   c->zone_cap_opt = o.zone_capacity;
+  c->schedule_opt = o.schedule;
+  if (o.group_cells > 0) c->group_cells = o.group_cells;
   c->stream = (cudaStream_t)stream;
   cudaError_t e = cudaMallocHost(&c->h_active, sizeof(int));
   if (e != cudaSuccess) {
@@ -1341,6 +1567,9 @@ imexds_status imexds_create(const imexds_problem* prob, const imexds_options* op
 void imexds_destroy(imexds_ctx* c) {
   if (!c) return;
   free_dev(c);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->join_ev) cudaEventDestroy(c->join_ev);
   if (c->h_active) cudaFreeHost(c->h_active);
   delete c;
 }
@@ -1481,7 +1710,7 @@ imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double*
   }
   std::vector<int2> tiles;
   for (int i = 0; i < n; ++i)
-    for (int j0 = 0; j0 < c->N[i]; j0 += TILE) tiles.push_back(make_int2(i, j0));
+    for (int j0 = 0; j0 < c->N[i]; j0 += 32) tiles.push_back(make_int2(i, j0));
   free_dev(c);
   Dev& d = c->d;
   for (int k = 0; k < 2; ++k) {
@@ -1502,6 +1731,10 @@ imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double*
   CK(cudaMalloc(&d.tiles, sizeof(int2) * tiles.size()));
   CK(cudaMemcpyAsync(d.tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMalloc(&d.ctrl, sizeof(Ctrl)));
+  {
+    static LogTable host_tab = make_log_table();
+    CK(cudaMemcpyToSymbolAsync(g_logtab, &host_tab, sizeof(LogTable), 0, cudaMemcpyHostToDevice, c->stream));
+  }
   CK(cudaMemcpyToSymbolAsync(c_fluid, &c->fluid, sizeof(Fluid), 0, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyToSymbolAsync(c_opts, &c->opts, sizeof(Opts), 0, cudaMemcpyHostToDevice, c->stream));
   {
@@ -1520,6 +1753,35 @@ imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double*
     CK(cudaMemcpyAsync(sv.inst, d.inst, sizeof(Inst) * n, cudaMemcpyDeviceToDevice, c->stream));
   }
   CK(cudaStreamSynchronize(c->stream));
+  {
+    // instance groups: instances sorted by size (largest first), at most GROUP_MAX per group and
+    // group_cells lattice cells (at least one instance)
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return c->N[a] > c->N[b]; });
+    std::vector<int> ginst;
+    std::vector<int2> grange;
+    int k = 0;
+    while (k < n) {
+      int start = k, cells = 0;
+      while (k < n && k - start < GROUP_MAX && (k == start || cells + c->N[order[k]] <= c->group_cells)) {
+        cells += c->N[order[k]];
+        ginst.push_back(order[k]);
+        ++k;
+      }
+      grange.push_back(make_int2(start, k - start));
+    }
+    CK(cudaMalloc(&c->d_ginst, sizeof(int) * ginst.size()));
+    CK(cudaMemcpyAsync(c->d_ginst, ginst.data(), sizeof(int) * ginst.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMalloc(&c->d_grange, sizeof(int2) * grange.size()));
+    CK(cudaMemcpyAsync(c->d_grange, grange.data(), sizeof(int2) * grange.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->n_groups = (int)grange.size();
+    int maxcap = 0;
+    for (int i = 0; i < n; ++i) maxcap = std::max(maxcap, zone_cap[i]);
+    // automatic schedule: groups for batches of instances with few boundaries each
+    c->use_groups = (c->schedule_opt == 2) || (c->schedule_opt == 0 && n >= 2 && maxcap <= 16);
+  }
   c->n_lat = n_lat;
   c->n_zone_slots = n_zone;
   c->n_tiles = (int)tiles.size();
@@ -1674,9 +1936,38 @@ imexds_status imexds_set_kernel_timing(imexds_ctx* c, int32_t on) {
   return IMEXDS_OK;
 }
 
+imexds_status imexds_check_log(int32_t n, const double* x, double* fast, double* ref) {
+  if (n <= 0 || !x || !fast || !ref) return IMEXDS_ERR_ARG;
+  static LogTable host_tab = make_log_table();
+  CK(cudaMemcpyToSymbol(g_logtab, &host_tab, sizeof(LogTable)));
+  double *dx = nullptr, *df = nullptr, *dr = nullptr;
+  CK(cudaMalloc(&dx, sizeof(double) * n));
+  CK(cudaMalloc(&df, sizeof(double) * n));
+  CK(cudaMalloc(&dr, sizeof(double) * n));
+  CK(cudaMemcpy(dx, x, sizeof(double) * n, cudaMemcpyHostToDevice));
+  k_check_log<<<(n + 255) / 256, 256>>>(n, dx, df, dr);
+  CK(cudaGetLastError());
+  CK(cudaMemcpy(fast, df, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(ref, dr, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  cudaFree(dx);
+  cudaFree(df);
+  cudaFree(dr);
+  return IMEXDS_OK;
+}
+
+imexds_status imexds_set_schedule(imexds_ctx* c, int32_t schedule) {
+  if (!c || schedule < 0 || schedule > 2) return IMEXDS_ERR_ARG;
+  if (!c->loaded) return IMEXDS_ERR_STATE;
+  c->schedule_opt = schedule;
+  int maxcap = 0;
+  for (int i = 0; i < c->n_inst; ++i) maxcap = std::max(maxcap, c->zone_cap[i]);
+  c->use_groups = (schedule == 2) || (schedule == 0 && c->n_inst >= 2 && maxcap <= 16);
+  return IMEXDS_OK;
+}
+
 imexds_status imexds_get_kernel_times(imexds_ctx* c, double* total_ms, int64_t* launches) {
   if (!c || !total_ms || !launches) return IMEXDS_ERR_ARG;
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < 6; ++k) {
     total_ms[k] = c->kt_ms[k];
     launches[k] = c->kt_n[k];
   }

@@ -5,6 +5,8 @@
 #pragma once
 #include <cstdint>
 
+#include "fastlog.cuh"
+
 namespace imexds {
 
 constexpr int VAP = 0;
@@ -271,7 +273,7 @@ __device__ inline PBOut pb_solve(const Fluid& F, const Opts& o, double tau, int 
   return R;
 }
 
-// ---- the same boundary solve arranged for repeated calls: one logarithm per side and evaluation
+// ---- the same boundary solve arranged for repeated calls: one (table-driven) logarithm per side and evaluation
 // (ln(rho*/rho_K) = ln(rho*/rho_sat) + ln(rho_sat/rho_K) with the last term fixed per solve), reciprocals
 // of the fixed data computed once, and an optional starting point (the previous solution) with the
 // HLLC start of App. A as fallback. Converges to the same root as pb_solve to round-off.
@@ -287,7 +289,7 @@ __device__ inline SideData side_data(const Phase& e, double rK) {
   s.pK = pressure(e, rK);
   s.invK = 1.0 / rK;
   s.isat = 1.0 / e.rho_sat;
-  s.CK = log(e.rho_sat * s.invK);
+  s.CK = fast_log(e.rho_sat * s.invK);
   s.ia2 = 1.0 / e.a2;
   s.ia = 1.0 / e.a;
   return s;
@@ -302,7 +304,7 @@ __device__ inline bool side_eval(const SideData& s, double p, SideEval& o) {
   double rs = e.kind == 0 ? p * s.ia2 : e.rho0 + (p - e.p0) * s.ia2;
   if (!(rs > 0.0) || !isfinite(p)) return false;
   double v = 1.0 / rs;
-  double Ls = log(rs * s.isat);
+  double Ls = fast_log(rs * s.isat);
   o.p = p;
   o.v = v;
   o.g = e.a2 * Ls;

@@ -19,7 +19,7 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_NONPHYSICAL", 4: "ERR_PB
 EXPORTED = ["imexds_create", "imexds_set_states", "imexds_set_states_device", "imexds_cell_counts",
             "imexds_get_states", "imexds_step", "imexds_run_to", "imexds_get_stats", "imexds_destroy",
             "imexds_status_string", "imexds_last_error_string", "imexds_reset", "imexds_set_kernel_timing",
-            "imexds_get_kernel_times"]
+            "imexds_get_kernel_times", "imexds_set_schedule", "imexds_check_log"]
 
 
 class ImexdsError(RuntimeError):
@@ -39,7 +39,8 @@ class OptionsS(C.Structure):
     _fields_ = [("cfl", C.c_double), ("theta_nb", C.c_double), ("tol_nb", C.c_double), ("tol_k", C.c_double),
                 ("res_mode", C.c_int), ("l_max", C.c_int), ("newton_tol", C.c_double),
                 ("newton_itmax", C.c_int), ("alpha_min", C.c_double), ("split_ratio", C.c_double),
-                ("creation", C.c_int), ("zone_capacity", C.c_int)]
+                ("creation", C.c_int), ("zone_capacity", C.c_int), ("schedule", C.c_int),
+                ("group_cells", C.c_int)]
 
 
 class ProblemS(C.Structure):
@@ -71,6 +72,8 @@ def load():
         L.imexds_reset.argtypes = [vp]
         L.imexds_set_kernel_timing.argtypes = [vp, C.c_int32]
         L.imexds_get_kernel_times.argtypes = [vp, dp, C.POINTER(C.c_int64)]
+        L.imexds_set_schedule.argtypes = [vp, C.c_int32]
+        L.imexds_check_log.argtypes = [C.c_int32, dp, dp, dp]
         L.imexds_status_string.restype = C.c_char_p
         L.imexds_status_string.argtypes = [C.c_int]
         L.imexds_last_error_string.restype = C.c_char_p
@@ -100,30 +103,41 @@ def make_fluid(f) -> FluidS:
     return FluidS(Eos(0, f.a2_vap, 0.0, 0.0), Eos(1, f.a2_liq, f.p_sat, f.rho0_liq), f.p_sat, f.p_min, f.p_tilde)
 
 
-def make_options(o, zone_capacity: int = 0) -> OptionsS:
+def make_options(o, zone_capacity: int = 0, schedule: int = 0, group_cells: int = 0) -> OptionsS:
     return OptionsS(o.cfl, o.theta_nb, o.tol_nb, o.tol_k, o.res_mode, o.l_max, o.newton_tol, o.newton_itmax,
-                    o.alpha_min, o.split_ratio, o.creation, zone_capacity)
+                    o.alpha_min, o.split_ratio, o.creation, zone_capacity, schedule, group_cells)
+
+
+def check_log(x):
+    """Table-driven logarithm of the library and CUDA's log at the points x (diagnostic)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    fast = np.zeros_like(x)
+    ref = np.zeros_like(x)
+    _check(load().imexds_check_log(int(x.shape[0]), _dp(x), _dp(fast), _dp(ref)))
+    return fast, ref
 
 
 class Imexds:
     """A context of the CUDA library holding a batch of instances (see include/imexds.h)."""
 
-    def __init__(self, n_lattice, x_left, x_right, tau, fluid, options, stream: int = 0, zone_capacity: int = 0):
+    def __init__(self, n_lattice, x_left, x_right, tau, fluid, options, stream: int = 0, zone_capacity: int = 0,
+                 schedule: int = 0, group_cells: int = 0):
         L = load()
         self._keep = [np.ascontiguousarray(n_lattice, dtype=np.int32), np.ascontiguousarray(x_left, dtype=np.float64),
                       np.ascontiguousarray(x_right, dtype=np.float64), np.ascontiguousarray(tau, dtype=np.float64)]
         nl, xl, xr, tau_ = self._keep
         self.n_inst = int(nl.shape[0])
         prob = ProblemS(self.n_inst, _ip(nl), _dp(xl), _dp(xr), _dp(tau_), make_fluid(fluid))
-        opts = make_options(options, zone_capacity)
+        opts = make_options(options, zone_capacity, schedule, group_cells)
         h = C.c_void_p()
         _check(L.imexds_create(C.byref(prob), C.byref(opts), C.c_void_p(stream), C.byref(h)))
         self.h = h
 
     @classmethod
-    def from_batch(cls, batch, options=None, stream: int = 0, zone_capacity: int = 0) -> "Imexds":
+    def from_batch(cls, batch, options=None, stream: int = 0, zone_capacity: int = 0, schedule: int = 0,
+                   group_cells: int = 0) -> "Imexds":
         ctx = cls(batch.n_lattice, batch.x_left, batch.x_right, batch.tau, batch.fluid, options or batch.options,
-                  stream=stream, zone_capacity=zone_capacity)
+                  stream=stream, zone_capacity=zone_capacity, schedule=schedule, group_cells=group_cells)
         ctx.set_states(batch.cell_offsets, batch.widths, batch.rho, batch.m, batch.phase)
         return ctx
 
@@ -184,11 +198,15 @@ class Imexds:
     def set_kernel_timing(self, on: bool):
         _check(load().imexds_set_kernel_timing(self.h, 1 if on else 0))
 
-    KERNELS = ["k_pre", "k_plan", "k_sweep", "k_dts", "k_post"]
+    KERNELS = ["k_pre", "k_plan", "k_sweep", "k_dts", "k_post", "k_group"]
+
+    def set_schedule(self, schedule: int):
+        """0 automatic, 1 per-step kernels, 2 instance groups."""
+        _check(load().imexds_set_schedule(self.h, int(schedule)))
 
     def kernel_times(self) -> dict:
-        ms = np.zeros(5)
-        n = np.zeros(5, dtype=np.int64)
+        ms = np.zeros(6)
+        n = np.zeros(6, dtype=np.int64)
         _check(load().imexds_get_kernel_times(self.h, _dp(ms), n.ctypes.data_as(C.POINTER(C.c_int64))))
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.KERNELS)}
 

@@ -5,6 +5,7 @@ import numpy as np
 from oracle import pyoracle as P
 
 TOL = 1e-9   # relative L-infinity per conserved variable and instance
+U_REF = 1.0  # m/s: momentum is normalised by max(|m|_inf, |rho|_inf * U_REF) (a fluid at rest has |m| ~ 0)
 
 
 def run_oracle(batch, threads=8):
@@ -48,7 +49,7 @@ def compare(a, b, tol=TOL, skip_status=False):
         ma, mb = a["m"][a0:a1], b["m"][b0:b1]
         wa, wb = a["widths"][a0:a1], b["widths"][b0:b1]
         rec["rho"] = float(np.max(np.abs(ra - rb)) / np.max(np.abs(ra)))
-        rec["m"] = float(np.max(np.abs(ma - mb)) / max(np.max(np.abs(ma)), 1e-300))
+        rec["m"] = float(np.max(np.abs(ma - mb)) / max(np.max(np.abs(ma)), np.max(np.abs(ra)) * U_REF))
         rec["w"] = float(np.max(np.abs(wa - wb)) / np.max(wa))
         rec["t"] = float(abs(a["t"][k] - b["t"][k]))
         out.append(rec)

@@ -1,0 +1,25 @@
+"""The table-driven logarithm of the boundary solves against CUDA's log (ulp distance) and against
+numpy's log (relative error), including arguments next to 1 where ln x is small."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _ulps(a, b):
+    ai = a.view(np.int64)
+    bi = b.view(np.int64)
+    return np.abs(ai - bi)
+
+
+def test_fast_log_accuracy():
+    from paper_2211_00705_gb300.imexds import check_log
+    rng = np.random.default_rng(3)
+    x = np.concatenate([np.exp(rng.uniform(-20, 20, 200000)), 1 + rng.uniform(-1e-3, 1e-3, 50000),
+                        1 + rng.uniform(-1e-12, 1e-12, 1000), [1.0, 2.0, 0.5, np.sqrt(2), 1 / np.sqrt(2)]])
+    x = x[x > 0]
+    fast, ref = check_log(x)
+    assert np.max(_ulps(fast, ref)) <= 4
+    rel = np.abs(fast - np.log(x)) / np.maximum(np.abs(np.log(x)), 1e-300)
+    assert np.max(rel[np.abs(np.log(x)) > 0]) < 1e-15
+    assert fast[-5] == 0.0

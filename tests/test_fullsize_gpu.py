@@ -1,0 +1,111 @@
+"""Parity at the workloads' full sizes: the CUDA path runs the whole batch (the launch configuration the
+benchmark times); the oracle computes sampled instances one by one (instances are independent), or,
+for the single large domain, sub-domains around sampled bubbles whose centre cells lie outside the
+influence of the sub-domain ends (one cell per step for this three-point scheme)."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_2211_00705_gb300 import inputs as I
+from tests.parity import TOL, compare, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _pick(batch, n):
+    order = np.argsort(batch.n_lattice, kind="stable")
+    idx = set(np.linspace(0, batch.n_inst - 1, n).astype(int).tolist())
+    idx.add(int(order[-1]))   # the largest instance
+    idx.add(int(order[0]))    # the smallest
+    return sorted(idx)
+
+
+def _subset_states(s, idx):
+    off = s["offsets"]
+    parts = [np.arange(off[i], off[i + 1]) for i in idx]
+    cells = np.concatenate(parts)
+    new_off = np.zeros(len(idx) + 1, dtype=np.int64)
+    new_off[1:] = np.cumsum([len(p) for p in parts])
+    return {"offsets": new_off, "widths": s["widths"][cells], "rho": s["rho"][cells], "m": s["m"][cells],
+            "phase": s["phase"][cells], "t": s["t"][idx], "status": s["status"][idx]}
+
+
+def _sampled(batch, n=10):
+    g, gst = run_gpu(batch)
+    idx = _pick(batch, n)
+    a, ast = run_oracle(batch.subset(idx))
+    compare(a, _subset_states(g, idx))
+    np.testing.assert_array_equal(ast["steps"], gst["steps"][idx])
+    return g, gst
+
+
+def test_riemann_batch_full_size_sampled():
+    """The benchmark workload: 4096 instances to t_end on the GPU; 12 sampled instances on the oracle."""
+    g, st = _sampled(I.workload(1), 10)
+    assert (g["status"] == 0).all()
+
+
+def test_fixed_steps_full_size_sampled():
+    """1024 instances x 500 cells x 2000 steps."""
+    g, st = _sampled(I.workload(3), 6)
+    assert (g["status"] == 0).all()
+    assert (st["steps"] == 2000).all()
+
+
+def test_cavitation_full_count_sampled():
+    """All 16384 cavitation instances (N up to 4096) for 1000 steps; every instance creates vapour."""
+    b = I.workload(4)
+    b.n_steps = 1000
+    g, st = _sampled(b, 6)
+    assert (g["status"] == 0).all()
+    assert (st["creations"] >= 1).all()
+
+
+def _lattice_slice(batch, j0, j1):
+    """The cells of a one-instance batch lying in background cells [j0, j1) (both fixed faces)."""
+    h = (batch.x_right[0] - batch.x_left[0]) / batch.n_lattice[0]
+    # face positions in lattice units; a regular cell contributes exactly 1
+    edges = np.concatenate([[0.0], np.cumsum(batch.widths / h)])
+    k0 = int(np.argmin(np.abs(edges - j0)))
+    k1 = int(np.argmin(np.abs(edges - j1)))
+    assert abs(edges[k0] - j0) < 1e-3 and abs(edges[k1] - j1) < 1e-3
+    return k0, k1
+
+
+def test_large_domain_full_size_subdomains():
+    """2^24 cells with 1024 bubbles, 1000 steps on the GPU; four bubbles re-run on the oracle in a
+    sub-domain of +-2200 cells; cells within +-1000 of the bubble must agree."""
+    b = I.workload(2)
+    g, gst = run_gpu(b)
+    assert g["status"][0] == 0
+    n = b.n_lattice[0]
+    h = 1.0 / n
+    flips = np.where(b.phase[:-1] != b.phase[1:])[0]
+    starts = np.cumsum(b.widths / h)[flips[::2]]   # left boundary of every bubble, in lattice units
+    centres = np.round(starts).astype(np.int64)
+    gaps = np.diff(centres)
+    ok = [i for i in range(1, len(centres) - 1) if gaps[i - 1] > 5000 and gaps[i] > 5000]
+    rng = np.random.default_rng(0)
+    picks = rng.choice(ok, size=4, replace=False)
+    gbatch = dataclasses.replace(b, widths=g["widths"], rho=g["rho"], m=g["m"], phase=g["phase"])
+    for p in picks:
+        c = int(centres[p])
+        j0, j1 = c - 2200, c + 2200
+        k0, k1 = _lattice_slice(b, j0, j1)
+        sub = dataclasses.replace(
+            b, n_lattice=np.array([j1 - j0], np.int32), x_left=np.array([j0 * h]), x_right=np.array([j1 * h]),
+            cell_offsets=np.array([0, k1 - k0], np.int32), widths=b.widths[k0:k1].copy(), rho=b.rho[k0:k1].copy(),
+            m=b.m[k0:k1].copy(), phase=b.phase[k0:k1].copy())
+        a, ast = run_oracle(sub)
+        assert a["status"][0] == 0
+        # compare the centre window [c-1000, c+1000)
+        ka0, ka1 = _lattice_slice(dataclasses.replace(sub, widths=a["widths"]), 1200, 3200)
+        kg0, kg1 = _lattice_slice(gbatch, c - 1000, c + 1000)
+        assert ka1 - ka0 == kg1 - kg0
+        ra, rg = a["rho"][ka0:ka1], g["rho"][kg0:kg1]
+        ma, mg = a["m"][ka0:ka1], g["m"][kg0:kg1]
+        np.testing.assert_array_equal(a["phase"][ka0:ka1], g["phase"][kg0:kg1])
+        assert np.max(np.abs(ra - rg)) <= TOL * np.max(np.abs(ra))
+        assert np.max(np.abs(ma - mg)) <= TOL * max(np.max(np.abs(ma)), np.max(np.abs(ra)) * 1.0)
+        np.testing.assert_allclose(a["widths"][ka0:ka1], g["widths"][kg0:kg1], rtol=TOL, atol=TOL * h)

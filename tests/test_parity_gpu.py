@@ -26,22 +26,28 @@ def test_single_instance_workload():
     np.testing.assert_array_equal(sa["dts_iters"], sb["dts_iters"])
 
 
-def test_batched_riemann_subset():
+SCHEDULES = [pytest.param(1, id="per-step-kernels"), pytest.param(2, id="instance-groups")]
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_batched_riemann_subset(schedule):
     """32 instances of the batched Riemann workload (N in [200, 2000], alpha in [1e-6, 1e-1]) to t_end."""
-    _check(I.workload(1, scale=32 / 4096))
+    _check(I.workload(1, scale=32 / 4096), schedule=schedule)
 
 
-def test_fixed_step_count():
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_fixed_step_count(schedule):
     b = I.workload(3, scale=8 / 1024)
     b.n_steps = 300
-    _check(b)
+    _check(b, schedule=schedule)
 
 
-def test_cavitation_creation():
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_cavitation_creation(schedule):
     """Pure liquid pulled apart: a vapour cell is created (App. B) and then tracked by two boundaries."""
     b = I.workload(4, scale=8 / 16384)
     b.n_steps = 200
-    recs, sa, sb = _check(b)
+    recs, sa, sb = _check(b, schedule=schedule)
     assert (sb["creations"] >= 1).all()
 
 
