@@ -39,7 +39,6 @@ constexpr int ZB = ZC + 2;        // block index space: zone cells plus one pull
 constexpr int MAXBLK = ZC;        // max blocks per zone
 constexpr int ZONE_GAP = 4;       // minimum number of lattice cells between two zones
 constexpr int EV_CAP = 4;         // creation events per instance and step
-constexpr int TILE = 256;         // lattice cells per sweep CTA
 constexpr int N_STATS = 9;
 constexpr long long kRunToMaxSteps = 20000000;  // run_to gives up (IMEXDS_ERR_TIMEOUT) after this many steps
 
@@ -1194,6 +1193,10 @@ __global__ void k_count_active(Dev d, int n_inst) {
   if (threadIdx.x == 0) d.ctrl->n_active = cnt;
 }
 
+}  // namespace
+#include "noalloc.cuh"
+namespace {
+
 // ---------------------------------------------------------------------------------------- host side
 std::string g_last_error;
 
@@ -1367,6 +1370,9 @@ void accumulate_times(imexds_ctx* c, int steps) {
 }
 
 imexds_status set_ctrl(imexds_ctx* c, double t_end, int clip) {
+  // the fluid and options live in module constants shared by every context: load this context's
+  CK(cudaMemcpyToSymbolAsync(c_fluid, &c->fluid, sizeof(Fluid), 0, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyToSymbolAsync(c_opts, &c->opts, sizeof(Opts), 0, cudaMemcpyHostToDevice, c->stream));
   Ctrl C{t_end, clip, 0};
   CK(cudaMemcpyAsync(c->d.ctrl, &C, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream));
   return IMEXDS_OK;
@@ -1953,6 +1959,53 @@ imexds_status imexds_check_log(int32_t n, const double* x, double* fast, double*
   cudaFree(df);
   cudaFree(dr);
   return IMEXDS_OK;
+}
+
+imexds_status imexds_step_uniform_noalloc(const imexds_fluid* fluid, double cfl, int32_t n_inst,
+                                          const int32_t* n_lattice, const double* x_left, const double* x_right,
+                                          const double* rho_in, const double* m_in, const uint8_t* phase,
+                                          double* rho_out, double* m_out, double* dt_out, void* stream) {
+  namespace na = imexds_noalloc;
+  if (!fluid || !n_lattice || !x_left || !x_right || !rho_in || !m_in || !phase || !rho_out || !m_out || !dt_out ||
+      !(cfl > 0.0) || n_inst <= 0)
+    return IMEXDS_ERR_ARG;
+  if (n_inst > na::kMaxInst) {
+    g_last_error = "imexds_step_uniform_noalloc: n_inst exceeds the fixed scratch size (16384 instances)";
+    return IMEXDS_ERR_CAPACITY;
+  }
+  long long cells = 0, tiles = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    if (n_lattice[i] < 2 || !(x_right[i] > x_left[i])) return IMEXDS_ERR_ARG;
+    cells += n_lattice[i];
+    tiles += (n_lattice[i] + 31) / 32;
+  }
+  if (cells > 0x7fffffffLL) return IMEXDS_ERR_ARG;
+  // set-up once per device, with that device current: the device address of the scratch array
+  static void* scratch_ptr[64] = {nullptr};
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return IMEXDS_ERR_ARG;
+  if (!scratch_ptr[dev]) CK(cudaGetSymbolAddress(&scratch_ptr[dev], na::g_scratch));
+  na::Scratch* scr = (na::Scratch*)scratch_ptr[dev];
+  cudaStream_t st = (cudaStream_t)stream;
+  Fluid F;
+  F.ph[VAP] = make_phase(fluid->vapour, fluid->p_sat);
+  F.ph[LIQ] = make_phase(fluid->liquid, fluid->p_sat);
+  F.p_sat = fluid->p_sat;
+  F.p_min = fluid->p_min;
+  F.p_tilde = fluid->p_tilde;
+  CK(cudaMemcpyAsync(scr->n_lattice, n_lattice, sizeof(int) * n_inst, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(scr->x_left, x_left, sizeof(double) * n_inst, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(scr->x_right, x_right, sizeof(double) * n_inst, cudaMemcpyHostToDevice, st));
+  na::k_setup<<<1, 32, 0, st>>>(scr, n_inst);
+  na::k_dt<<<n_inst, 256, 0, st>>>(scr, F, cfl, rho_in, m_in, phase, dt_out);
+  na::k_sweep<<<(int)((tiles + 7) / 8), 256, 0, st>>>(scr, F, n_inst, (int)tiles, rho_in, m_in, phase, rho_out,
+                                                      m_out);
+  CK(cudaGetLastError());
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, &scr->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return err ? IMEXDS_ERR_ARG : IMEXDS_OK;
 }
 
 imexds_status imexds_set_schedule(imexds_ctx* c, int32_t schedule) {

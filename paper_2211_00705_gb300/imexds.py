@@ -19,7 +19,7 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_NONPHYSICAL", 4: "ERR_PB
 EXPORTED = ["imexds_create", "imexds_set_states", "imexds_set_states_device", "imexds_cell_counts",
             "imexds_get_states", "imexds_step", "imexds_run_to", "imexds_get_stats", "imexds_destroy",
             "imexds_status_string", "imexds_last_error_string", "imexds_reset", "imexds_set_kernel_timing",
-            "imexds_get_kernel_times", "imexds_set_schedule", "imexds_check_log"]
+            "imexds_get_kernel_times", "imexds_set_schedule", "imexds_check_log", "imexds_step_uniform_noalloc"]
 
 
 class ImexdsError(RuntimeError):
@@ -74,6 +74,8 @@ def load():
         L.imexds_get_kernel_times.argtypes = [vp, dp, C.POINTER(C.c_int64)]
         L.imexds_set_schedule.argtypes = [vp, C.c_int32]
         L.imexds_check_log.argtypes = [C.c_int32, dp, dp, dp]
+        L.imexds_step_uniform_noalloc.argtypes = [C.POINTER(FluidS), C.c_double, C.c_int32, ip, dp, dp, vp, vp, vp,
+                                                  vp, vp, vp, vp]
         L.imexds_status_string.restype = C.c_char_p
         L.imexds_status_string.argtypes = [C.c_int]
         L.imexds_last_error_string.restype = C.c_char_p
@@ -106,6 +108,20 @@ def make_fluid(f) -> FluidS:
 def make_options(o, zone_capacity: int = 0, schedule: int = 0, group_cells: int = 0) -> OptionsS:
     return OptionsS(o.cfl, o.theta_nb, o.tol_nb, o.tol_k, o.res_mode, o.l_max, o.newton_tol, o.newton_itmax,
                     o.alpha_min, o.split_ratio, o.creation, zone_capacity, schedule, group_cells)
+
+
+def step_uniform_noalloc(fluid, cfl, n_lattice, x_left, x_right, rho_in, m_in, phase, rho_out, m_out, dt_out,
+                         stream: int = 0):
+    """One explicit step of single-phase instances without any GPU allocation by the library (see
+    include/imexds.h). rho_in/m_in/phase/rho_out/m_out/dt_out are CUDA tensors (float64, uint8)."""
+    nl = np.ascontiguousarray(n_lattice, dtype=np.int32)
+    xl = np.ascontiguousarray(x_left, dtype=np.float64)
+    xr = np.ascontiguousarray(x_right, dtype=np.float64)
+    fl = make_fluid(fluid)
+    _check(load().imexds_step_uniform_noalloc(
+        C.byref(fl), float(cfl), int(nl.shape[0]), _ip(nl), _dp(xl), _dp(xr), C.c_void_p(rho_in.data_ptr()),
+        C.c_void_p(m_in.data_ptr()), C.c_void_p(phase.data_ptr()), C.c_void_p(rho_out.data_ptr()),
+        C.c_void_p(m_out.data_ptr()), C.c_void_p(dt_out.data_ptr()), C.c_void_p(stream)))
 
 
 def check_log(x):
