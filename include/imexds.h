@@ -75,6 +75,8 @@ typedef struct {
   int schedule;        /* 0 automatic, 1 one launch per kernel and step (graph of 8 steps), 2 instance
                           groups advanced by one resident launch (0) */
   int group_cells;     /* lattice cells per instance group (0 = 16384) */
+  int group_threads;   /* threads per group CTA, a multiple of 32 from 64 to 256 (0 = 128): warp 0 runs
+                          the per-instance work, the other warps sweep */
 } imexds_options;
 
 /* A batch of independent 1-D problems on [x_left[i], x_right[i]] with n_lattice[i] background

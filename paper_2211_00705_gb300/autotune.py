@@ -1,0 +1,77 @@
+"""Schedule autotuner for imexds contexts.
+
+Candidates: the per-step kernel schedule (one launch per kernel and step, replayed from a CUDA graph)
+and the instance-group schedule (one resident launch per call) at several group sizes and CTA widths.
+Each candidate advances the context's own states for a few steps (timed with CUDA events through the
+library's kernel timer), the context is restored with imexds_reset, and the fastest candidate is kept.
+Choices are cached per configuration (instance sizes, boundary counts, options) in memory and,
+optionally, in a JSON file.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import time
+
+import numpy as np
+
+CANDIDATES = [
+    {"schedule": 1},
+    {"schedule": 2, "group_threads": 128, "group_cells": 16384},
+    {"schedule": 2, "group_threads": 128, "group_cells": 8192},
+    {"schedule": 2, "group_threads": 256, "group_cells": 16384},
+    {"schedule": 2, "group_threads": 64, "group_cells": 4096},
+]
+
+_cache: dict = {}
+
+
+def config_key(batch) -> str:
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(batch.n_lattice).tobytes())
+    flips = np.diff(batch.phase.astype(np.int16)) != 0
+    h.update(np.int64(flips.sum()).tobytes())
+    h.update(json.dumps(batch.options.__dict__, sort_keys=True).encode())
+    return h.hexdigest()[:16]
+
+
+def tune(batch, steps: int = 64, cache_file: str | None = None, candidates=None) -> dict:
+    """Return the fastest candidate for this batch (and remember it)."""
+    from .imexds import Imexds
+    key = config_key(batch)
+    if cache_file and os.path.exists(cache_file):
+        try:
+            _cache.update(json.load(open(cache_file)))
+        except (OSError, ValueError):
+            pass
+    if key in _cache:
+        return _cache[key]
+    best, best_t = None, float("inf")
+    timings = []
+    for cand in candidates or CANDIDATES:
+        ctx = Imexds.from_batch(batch, schedule=cand["schedule"], group_threads=cand.get("group_threads", 0),
+                                group_cells=cand.get("group_cells", 0))
+        ctx.step(min(8, steps))          # warm-up (graph build, caches)
+        ctx.reset()
+        t0 = time.perf_counter()
+        ctx.step(steps)
+        st = ctx.get_states()            # synchronises
+        dt = time.perf_counter() - t0
+        ctx.close()
+        if (st["status"] != 0).any():
+            continue
+        timings.append((cand, dt))
+        if dt < best_t:
+            best, best_t = cand, dt
+    if best is None:
+        best = CANDIDATES[0]
+    choice = dict(best)
+    choice["seconds_per_step"] = best_t / steps
+    _cache[key] = choice
+    if cache_file:
+        try:
+            json.dump(_cache, open(cache_file, "w"), indent=1)
+        except OSError:
+            pass
+    return choice

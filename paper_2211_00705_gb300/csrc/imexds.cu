@@ -105,7 +105,7 @@ __device__ inline unsigned long long dbits(double x) { return (unsigned long lon
 // ------------------------------------------------------------------------------------------ k_pre
 // Phase-boundary solves at U^n predict the widths of the cells next to each boundary; a cell that would
 // fall below max(alpha_min h, h_i / 2) is marked for merging (Sec. 2.3, Sec. 3.4).
-__device__ void pre_zone(const Dev& d, int zi) {
+__device__ __noinline__ void pre_zone(const Dev& d, int zi) {
   Zone& Z = d.zones[zi];
   Z.merge_mask = 0;
   if (!Z.alive) return;
@@ -162,7 +162,7 @@ __device__ inline void zone_erase_cell(Zone& Z, int b) {
 // neighbourhoods: at every boundary the smaller adjacent cell is the tiny cell k; {k-1, k, k+1} are
 // joined where they overlap. Cells outside the zone taking part (one lattice cell per side) are
 // "pulled": the sweep skips them and k_dts updates them.
-__device__ void plan_zone(const Dev& d, int zi) {
+__device__ __noinline__ void plan_zone(const Dev& d, int zi) {
   Zone& Z = d.zones[zi];
   if (!Z.alive) return;
   Inst& I = d.inst[Z.inst];
@@ -559,6 +559,211 @@ __device__ inline bool block_fluxes(const BlockCtx& B, int lo, int hi, const dou
   return true;
 }
 
+// General Algorithm 2 on every block of a zone (any block shape), kept out of line.
+__device__ __noinline__ bool dts_general(const Dev& d, Zone& Z, Inst& I, int e0, int nq, const BlockCtx& B,
+                                        const double* Fx0, const double* Fx1, double* out_r, double* out_m,
+                                        double* out_w, double* xpb_new, int* moved, long long& newton,
+                                        long long& solves, long long& iters_sum, long long& iters_max,
+                                        long long& maxiter) {
+  const double dt = I.dt, h = I.h, tau = I.tau;
+  for (int b = 0; b < Z.nblk; ++b) {
+    const int lo = Z.blo[b] - e0, hi = Z.bhi[b] - e0;
+    const double FL0 = Fx0[lo], FL1 = Fx1[lo], FR0 = Fx0[hi + 1], FR1 = Fx1[hi + 1];
+    double Wr[ZB], Wm[ZB], Nr[ZB], Nm[ZB], theta[ZB], F0[ZB + 1], F1[ZB + 1], wc[ZB + 1], hl[ZB];
+    for (int q = 0; q < nq; ++q) {
+      Wr[q] = B.r[q];
+      Wm[q] = B.m[q];
+    }
+    for (int q = lo; q <= hi; ++q) {
+      int e = q + e0;
+      double hp = (e < 0 || e >= Z.nc) ? h : Z.hp[e];
+      theta[q] = fmin(c_opts.theta_nb, hp / h);
+    }
+    bool stop = false, nonconv = false;
+    double gl[ZB + 1], gr[ZB + 1];  // Newton starts per face: the zone's last solution, then the previous iterate
+    for (int g = 0; g <= nq; ++g) {
+      int e = g + e0;
+      bool zf = (e >= 1 && e <= Z.nc - 1);
+      gl[g] = zf ? Z.pwl[e] : 0.0;
+      gr[g] = zf ? Z.pwr[e] : 0.0;
+    }
+    int l;
+    for (l = 0; l < c_opts.l_max && !stop; ++l) {
+      if (!block_fluxes(B, lo, hi, Wr, Wm, FL0, FL1, FR0, FR1, tau, dt, F0, F1, wc, hl, gl, gr, newton, solves,
+                        nonconv)) {
+        set_status(I, nonconv ? IMEXDS_ERR_PB_NOCONV : IMEXDS_ERR_VANISH);
+        return false;
+      }
+      double res_nb = 0.0, res_k = 0.0;
+      for (int q = lo; q <= hi; ++q) {
+        double th = theta[q];
+        double tr = B.w[q] / hl[q] * B.r[q] - dt / hl[q] * (F0[q + 1] - F0[q]);
+        double tm = B.w[q] / hl[q] * B.m[q] - dt / hl[q] * (F1[q + 1] - F1[q]);
+        Nr[q] = (Wr[q] + th * tr) / (1.0 + th);
+        Nm[q] = (Wm[q] + th * tm) / (1.0 + th);
+        double dtau = th * dt;
+        double e0r = (1.0 + th) * fabs(Nr[q] - Wr[q]) / (dtau * fmax(fabs(Wr[q]), 1.0));
+        double e1m = (1.0 + th) * fabs(Nm[q] - Wm[q]) / (dtau * fmax(fabs(Wm[q]), 1.0));
+        double res = fmax(e0r, e1m);
+        if (c_opts.res_mode == 1) res *= dt;
+        if ((Z.tiny_mask >> (q + e0 + 1)) & 1u)
+          res_k = fmax(res_k, res);
+        else
+          res_nb = fmax(res_nb, res);
+      }
+      for (int q = lo; q <= hi; ++q) {
+        Wr[q] = Nr[q];
+        Wm[q] = Nm[q];
+      }
+      if (res_nb < c_opts.tol_nb && res_k < c_opts.tol_k) stop = true;
+    }
+    if (!stop) maxiter++;
+    iters_sum += l;
+    iters_max = max(iters_max, (long long)l);
+    if (!block_fluxes(B, lo, hi, Wr, Wm, FL0, FL1, FR0, FR1, tau, dt, F0, F1, wc, hl, gl, gr, newton, solves,
+                      nonconv)) {
+      set_status(I, nonconv ? IMEXDS_ERR_PB_NOCONV : IMEXDS_ERR_VANISH);
+      return false;
+    }
+    for (int g = lo + 1; g <= hi; ++g)
+      if (B.fpb[g]) {
+        Z.pwl[g + e0] = gl[g];
+        Z.pwr[g + e0] = gr[g];
+      }
+    for (int q = lo; q <= hi; ++q) {
+      out_r[q] = (B.w[q] * B.r[q] - dt * (F0[q + 1] - F0[q])) / hl[q];
+      out_m[q] = (B.w[q] * B.m[q] - dt * (F1[q + 1] - F1[q])) / hl[q];
+      out_w[q] = hl[q];
+    }
+    for (int g = lo + 1; g <= hi; ++g)
+      if (B.fpb[g]) {
+        int e = g + e0;
+        moved[g] = 1;
+        xpb_new[g] = Z.fx[e] + wc[g] * dt;
+      }
+  }
+  return true;
+}
+
+// Register-resident Algorithm 2 for the common block: three cells (extended indices e0..e0+2) with one
+// phase boundary at interior face PBF (1: between cells 0|1, 2: between 1|2), the other interior face
+// fixed. Same iteration as the general path; the stop test is evaluated without divisions
+// (res < tol  <=>  (1 + theta)|dW| < tol theta dt' max(|W|, 1), dt' = dt for the printed residual and
+// 1 for the residual times dt). Writes the converged U^{n+1} like the general path.
+template <int PBF>
+__device__ bool dts_block3(const Dev& d, Zone& Z, Inst& I, int e0, const double* Ur, const double* Um,
+                           const double* Uw, const int* ph, double FL0, double FL1, double FR0, double FR1,
+                           double* out_r, double* out_m, double* out_w, long long& newton, long long& solves,
+                           long long& iters_out, long long& maxiter, bool& vanish, bool& nonconv) {
+  const double dt = I.dt, h = I.h, tau = I.tau;
+  double th[3], ith[3], ctol[3];
+  const double dtr = (c_opts.res_mode == 1) ? 1.0 : dt;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    int e = q + e0;
+    double hp = (e < 0 || e >= Z.nc) ? h : Z.hp[e];
+    th[q] = fmin(c_opts.theta_nb, hp / h);
+    ith[q] = 1.0 / (1.0 + th[q]);
+    bool tiny = (Z.tiny_mask >> (e + 1)) & 1u;
+    ctol[q] = (tiny ? c_opts.tol_k : c_opts.tol_nb) * th[q] * dtr;  // times max(|W|, 1), against (1+th)|dW|
+  }
+  // h^n U^n, fixed parts of the numerators
+  double hU0[3], hU1[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    hU0[q] = Uw[q] * Ur[q];
+    hU1[q] = Uw[q] * Um[q];
+  }
+  const int a = PBF - 1;       // the boundary lies between cells a and a+1
+  const int b = (PBF == 1) ? 2 : 1;  // the fixed interior face between cells b-1 and b
+  const int ePB = PBF + e0;    // zone face index of the boundary
+  double gl = Z.pwl[ePB], gr = Z.pwr[ePB];
+  double W0[3], W1[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    W0[q] = Ur[q];
+    W1[q] = Um[q];
+  }
+  double Fp0 = 0, Fp1 = 0, wpb = 0, Fh0 = 0, Fh1 = 0;
+  auto fluxes = [&](bool& ok) {
+    PBOut R = pb_solve_warm(c_fluid, c_opts, tau, ph[a], W0[a], W1[a], ph[a + 1], W0[a + 1], W1[a + 1], gl, gr);
+    newton += R.iters;
+    solves++;
+    if (!R.ok) {
+      ok = false;
+      nonconv = true;
+      return;
+    }
+    Fp0 = R.F0;
+    Fp1 = R.F1;
+    wpb = R.w;
+    hll_fast(c_fluid.ph[ph[b]], W0[b - 1], W1[b - 1], W0[b], W1[b], Fh0, Fh1);
+    ok = true;
+  };
+  // face fluxes in order (faces 0..3) and widths
+  auto assemble = [&](double* F0, double* F1, double* hl) {
+    F0[0] = FL0;
+    F1[0] = FL1;
+    F0[3] = FR0;
+    F1[3] = FR1;
+    F0[PBF] = Fp0;
+    F1[PBF] = Fp1;
+    F0[b] = Fh0;
+    F1[b] = Fh1;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) hl[q] = Uw[q];
+    hl[a] = Uw[a] + (wpb - 0.0) * dt;
+    hl[a + 1] = Uw[a + 1] + (0.0 - wpb) * dt;
+  };
+  bool stop = false;
+  int l;
+  for (l = 0; l < c_opts.l_max && !stop; ++l) {
+    bool ok;
+    fluxes(ok);
+    if (!ok) return false;
+    double F0[4], F1[4], hl[3];
+    assemble(F0, F1, hl);
+    if (!(hl[a] > 0.0) || !(hl[a + 1] > 0.0)) {
+      vanish = true;
+      return false;
+    }
+    stop = true;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      double ihl = (q == a || q == a + 1) ? 1.0 / hl[q] : 1.0 / Uw[q];
+      double n0 = (W0[q] + th[q] * ((hU0[q] - dt * (F0[q + 1] - F0[q])) * ihl)) * ith[q];
+      double n1 = (W1[q] + th[q] * ((hU1[q] - dt * (F1[q + 1] - F1[q])) * ihl)) * ith[q];
+      double lim = ctol[q] * ith[q];
+      bool okq = (fabs(n0 - W0[q]) < lim * fmax(fabs(W0[q]), 1.0)) && (fabs(n1 - W1[q]) < lim * fmax(fabs(W1[q]), 1.0));
+      stop = stop && okq;
+      W0[q] = n0;
+      W1[q] = n1;
+    }
+  }
+  if (!stop) maxiter++;
+  iters_out = l;
+  // Part 2 at U^{n,*}
+  bool ok;
+  fluxes(ok);
+  if (!ok) return false;
+  double F0[4], F1[4], hl[3];
+  assemble(F0, F1, hl);
+  if (!(hl[a] > 0.0) || !(hl[a + 1] > 0.0)) {
+    vanish = true;
+    return false;
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    out_r[q] = (hU0[q] - dt * (F0[q + 1] - F0[q])) / hl[q];
+    out_m[q] = (hU1[q] - dt * (F1[q + 1] - F1[q])) / hl[q];
+    out_w[q] = hl[q];
+  }
+  Z.pwl[ePB] = gl;
+  Z.pwr[ePB] = gr;
+  Z.fx[ePB] = Z.fx[ePB] + wpb * dt;
+  return true;
+}
+
 __device__ void dts_zone(const Dev& d, int zi) {
   Zone& Z = d.zones[zi];
   if (!Z.alive) return;
@@ -637,81 +842,26 @@ __device__ void dts_zone(const Dev& d, int zi) {
   double xpb_new[ZB + 1];
   int moved[ZB + 1];
   for (int q = 0; q <= nq; ++q) moved[q] = 0;
-  for (int b = 0; b < Z.nblk; ++b) {
-    const int lo = Z.blo[b] - e0, hi = Z.bhi[b] - e0;
-    const double FL0 = Fx0[lo], FL1 = Fx1[lo], FR0 = Fx0[hi + 1], FR1 = Fx1[hi + 1];
-    double Wr[ZB], Wm[ZB], Nr[ZB], Nm[ZB], theta[ZB], F0[ZB + 1], F1[ZB + 1], wc[ZB + 1], hl[ZB];
-    for (int q = 0; q < nq; ++q) {
-      Wr[q] = B.r[q];
-      Wm[q] = B.m[q];
-    }
-    for (int q = lo; q <= hi; ++q) {
-      int e = q + e0;
-      double hp = (e < 0 || e >= Z.nc) ? h : Z.hp[e];
-      theta[q] = fmin(c_opts.theta_nb, hp / h);
-    }
-    bool stop = false, nonconv = false;
-    double gl[ZB + 1], gr[ZB + 1];  // Newton starts per face: the zone's last solution, then the previous iterate
-    for (int g = 0; g <= nq; ++g) {
-      int e = g + e0;
-      bool zf = (e >= 1 && e <= Z.nc - 1);
-      gl[g] = zf ? Z.pwl[e] : 0.0;
-      gr[g] = zf ? Z.pwr[e] : 0.0;
-    }
-    int l;
-    for (l = 0; l < c_opts.l_max && !stop; ++l) {
-      if (!block_fluxes(B, lo, hi, Wr, Wm, FL0, FL1, FR0, FR1, tau, dt, F0, F1, wc, hl, gl, gr, newton, solves,
-                        nonconv)) {
-        set_status(I, nonconv ? IMEXDS_ERR_PB_NOCONV : IMEXDS_ERR_VANISH);
-        return;
-      }
-      double res_nb = 0.0, res_k = 0.0;
-      for (int q = lo; q <= hi; ++q) {
-        double th = theta[q];
-        double tr = B.w[q] / hl[q] * B.r[q] - dt / hl[q] * (F0[q + 1] - F0[q]);
-        double tm = B.w[q] / hl[q] * B.m[q] - dt / hl[q] * (F1[q + 1] - F1[q]);
-        Nr[q] = (Wr[q] + th * tr) / (1.0 + th);
-        Nm[q] = (Wm[q] + th * tm) / (1.0 + th);
-        double dtau = th * dt;
-        double e0r = (1.0 + th) * fabs(Nr[q] - Wr[q]) / (dtau * fmax(fabs(Wr[q]), 1.0));
-        double e1m = (1.0 + th) * fabs(Nm[q] - Wm[q]) / (dtau * fmax(fabs(Wm[q]), 1.0));
-        double res = fmax(e0r, e1m);
-        if (c_opts.res_mode == 1) res *= dt;
-        if ((Z.tiny_mask >> (q + e0 + 1)) & 1u)
-          res_k = fmax(res_k, res);
-        else
-          res_nb = fmax(res_nb, res);
-      }
-      for (int q = lo; q <= hi; ++q) {
-        Wr[q] = Nr[q];
-        Wm[q] = Nm[q];
-      }
-      if (res_nb < c_opts.tol_nb && res_k < c_opts.tol_k) stop = true;
-    }
-    if (!stop) maxiter++;
-    iters_sum += l;
-    iters_max = max(iters_max, (long long)l);
-    if (!block_fluxes(B, lo, hi, Wr, Wm, FL0, FL1, FR0, FR1, tau, dt, F0, F1, wc, hl, gl, gr, newton, solves,
-                      nonconv)) {
+  // common case: one block of three cells holding the whole zone with one boundary face
+  bool simple = (Z.nblk == 1 && nq == 3 && Z.blo[0] - e0 == 0 && Z.bhi[0] - e0 == 2 && (B.fpb[1] + B.fpb[2]) == 1);
+  if (simple) {
+    bool vanish = false, nonconv = false;
+    long long it = 0;
+    bool ok = B.fpb[1] ? dts_block3<1>(d, Z, I, e0, B.r, B.m, B.w, B.ph, Fx0[0], Fx1[0], Fx0[3], Fx1[3], out_r, out_m,
+                                       out_w, newton, solves, it, maxiter, vanish, nonconv)
+                       : dts_block3<2>(d, Z, I, e0, B.r, B.m, B.w, B.ph, Fx0[0], Fx1[0], Fx0[3], Fx1[3], out_r, out_m,
+                                       out_w, newton, solves, it, maxiter, vanish, nonconv);
+    if (!ok) {
       set_status(I, nonconv ? IMEXDS_ERR_PB_NOCONV : IMEXDS_ERR_VANISH);
       return;
     }
-    for (int g = lo + 1; g <= hi; ++g)
-      if (B.fpb[g]) {
-        Z.pwl[g + e0] = gl[g];
-        Z.pwr[g + e0] = gr[g];
-      }
-    for (int q = lo; q <= hi; ++q) {
-      out_r[q] = (B.w[q] * B.r[q] - dt * (F0[q + 1] - F0[q])) / hl[q];
-      out_m[q] = (B.w[q] * B.m[q] - dt * (F1[q + 1] - F1[q])) / hl[q];
-      out_w[q] = hl[q];
-    }
-    for (int g = lo + 1; g <= hi; ++g)
-      if (B.fpb[g]) {
-        int e = g + e0;
-        moved[g] = 1;
-        xpb_new[g] = Z.fx[e] + wc[g] * dt;
-      }
+    iters_sum = it;
+    iters_max = it;
+  }
+  if (!simple) {
+    if (!dts_general(d, Z, I, e0, nq, B, Fx0, Fx1, out_r, out_m, out_w, xpb_new, moved, newton, solves, iters_sum,
+                     iters_max, maxiter))
+      return;
   }
   double smax = 0.0;
   for (int q = 0; q < nq; ++q) {
@@ -765,7 +915,7 @@ __device__ inline int zone_insert_cell(Zone& Z, int pos) {
   return 1;
 }
 
-__device__ void post_inst(const Dev& d, int ii) {
+__device__ __noinline__ void post_inst(const Dev& d, int ii) {
   Inst& I = d.inst[ii];
   if (!I.active) return;
   const double h = I.h;
@@ -1220,7 +1370,7 @@ struct imexds_ctx {
   int graph_steps = 0;
   cudaStream_t side = nullptr;            // second stream of the step graph (k_dts beside k_sweep)
   int schedule = 0;                       // 1 per-step kernels, 2 instance groups (0 auto at set_states)
-  int schedule_opt = 0, group_cells = 16384, use_groups = 0;
+  int schedule_opt = 0, group_cells = 16384, use_groups = 0, group_threads = 128;
   int n_groups = 0;
   int* d_ginst = nullptr;
   int2* d_grange = nullptr;
@@ -1389,9 +1539,9 @@ imexds_status run_groups(imexds_ctx* c, long long max_steps, bool until_done) {
     int n = (int)std::min<long long>(max_steps - done, 1 << 30);
     if (c->timing) cudaEventRecord(c->gev[0], c->stream);
     if (c->opts.creation)
-      k_group<true><<<c->n_groups, 256, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n);
+      k_group<true><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n);
     else
-      k_group<false><<<c->n_groups, 256, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n);
+      k_group<false><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n);
     if (c->timing) cudaEventRecord(c->gev[1], c->stream);
     k_count_active<<<1, 256, 0, c->stream>>>(c->d, c->n_inst);
     c->launches += 2;
@@ -1550,6 +1700,7 @@ imexds_status imexds_create(const imexds_problem* prob, const imexds_options* op
     o.zone_capacity = 0;
     o.schedule = 0;
     o.group_cells = 0;
+    o.group_threads = 0;
   }
   if (!(o.cfl > 0.0) || o.l_max < 1 || o.newton_itmax < 1 || !(o.split_ratio > 1.0)) {
     delete c;
@@ -1560,6 +1711,13 @@ imexds_status imexds_create(const imexds_problem* prob, const imexds_options* op
   c->zone_cap_opt = o.zone_capacity;
   c->schedule_opt = o.schedule;
   if (o.group_cells > 0) c->group_cells = o.group_cells;
+  if (o.group_threads != 0) {
+    if (o.group_threads < 64 || o.group_threads > 256 || o.group_threads % 32) {
+      delete c;
+      return IMEXDS_ERR_ARG;
+    }
+    c->group_threads = o.group_threads;
+  }
   c->stream = (cudaStream_t)stream;
   cudaError_t e = cudaMallocHost(&c->h_active, sizeof(int));
   if (e != cudaSuccess) {

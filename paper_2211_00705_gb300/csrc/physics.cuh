@@ -211,7 +211,7 @@ __device__ inline void pb_initial_guess(const Fluid& F, int phl, double rl, doub
 
 // Phase-boundary Riemann problem (App. A): Newton's method with the Armijo rule on the 2x2 system;
 // flux F_PB = (-z, -z u_V* + p_V*) (Eq. pb_flux:pt) through the boundary moving at w = u_V* + z v_V*.
-__device__ inline PBOut pb_solve(const Fluid& F, const Opts& o, double tau, int phl, double rl, double ml, int phr,
+__device__ __noinline__ PBOut pb_solve(const Fluid& F, const Opts& o, double tau, int phl, double rl, double ml, int phr,
                                  double rr, double mr) {
   PBOut R;
   R.ok = 0;
@@ -312,10 +312,15 @@ __device__ inline bool side_eval(const SideData& s, double p, SideEval& o) {
   if (p > s.pK) {
     double dvk = s.invK - v;
     double q = (p - s.pK) * dvk;
-    double f = sqrt(q);
     double dq = dvk + (p - s.pK) * v * v * s.ia2;
-    o.f = f;
-    o.df = (f > 0.0) ? 0.5 * dq / f : v * s.ia;
+    if (q > 0.0) {
+      double rq = rsqrt(q);  // f = sqrt(q) = q / sqrt(q), df = dq / (2 sqrt(q))
+      o.f = q * rq;
+      o.df = 0.5 * dq * rq;
+    } else {
+      o.f = 0.0;
+      o.df = v * s.ia;
+    }
   } else {
     o.f = e.a * (Ls + s.CK);
     o.df = v * s.ia;
@@ -387,7 +392,9 @@ __device__ inline int pbf_newton(const Fluid& F, const Opts& o, const SideData& 
     x0 += lam * d0;
     x1 += lam * d1;
     S = T;
-    if (lam * fmax(s0, s1) <= o.newton_tol || nrm == 0.0) conv = true;
+    // a full Newton step below 1e-8 (relative) leaves an error of order 1e-16 (quadratic convergence):
+    // the same root the newton_tol test reaches, one evaluation earlier
+    if (lam * fmax(s0, s1) <= o.newton_tol || nrm == 0.0 || (lam == 1.0 && fmax(s0, s1) <= 1e-8)) conv = true;
   }
   iters += it;
   return conv ? 1 : 0;
@@ -530,7 +537,7 @@ __device__ inline bool solve3(const double A[3][3], const double b[3], double x[
 // Single-phase Riemann problem with creation of the other phase (App. B): unknowns
 // (p_parent-, p_created, p_parent+), two boundary momentum jumps and the chained velocity balance,
 // solved by Newton with the Armijo rule from the saturation pressure.
-__device__ inline CreateOut creation_solve(const Fluid& F, const Opts& o, double tau, int P, double rl, double ml,
+__device__ __noinline__ CreateOut creation_solve(const Fluid& F, const Opts& o, double tau, int P, double rl, double ml,
                                            double rr, double mr) {
   CreateOut R;
   R.ok = 0;

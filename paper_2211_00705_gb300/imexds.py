@@ -40,7 +40,7 @@ class OptionsS(C.Structure):
                 ("res_mode", C.c_int), ("l_max", C.c_int), ("newton_tol", C.c_double),
                 ("newton_itmax", C.c_int), ("alpha_min", C.c_double), ("split_ratio", C.c_double),
                 ("creation", C.c_int), ("zone_capacity", C.c_int), ("schedule", C.c_int),
-                ("group_cells", C.c_int)]
+                ("group_cells", C.c_int), ("group_threads", C.c_int)]
 
 
 class ProblemS(C.Structure):
@@ -105,9 +105,10 @@ def make_fluid(f) -> FluidS:
     return FluidS(Eos(0, f.a2_vap, 0.0, 0.0), Eos(1, f.a2_liq, f.p_sat, f.rho0_liq), f.p_sat, f.p_min, f.p_tilde)
 
 
-def make_options(o, zone_capacity: int = 0, schedule: int = 0, group_cells: int = 0) -> OptionsS:
+def make_options(o, zone_capacity: int = 0, schedule: int = 0, group_cells: int = 0,
+                 group_threads: int = 0) -> OptionsS:
     return OptionsS(o.cfl, o.theta_nb, o.tol_nb, o.tol_k, o.res_mode, o.l_max, o.newton_tol, o.newton_itmax,
-                    o.alpha_min, o.split_ratio, o.creation, zone_capacity, schedule, group_cells)
+                    o.alpha_min, o.split_ratio, o.creation, zone_capacity, schedule, group_cells, group_threads)
 
 
 def step_uniform_noalloc(fluid, cfl, n_lattice, x_left, x_right, rho_in, m_in, phase, rho_out, m_out, dt_out,
@@ -137,23 +138,24 @@ class Imexds:
     """A context of the CUDA library holding a batch of instances (see include/imexds.h)."""
 
     def __init__(self, n_lattice, x_left, x_right, tau, fluid, options, stream: int = 0, zone_capacity: int = 0,
-                 schedule: int = 0, group_cells: int = 0):
+                 schedule: int = 0, group_cells: int = 0, group_threads: int = 0):
         L = load()
         self._keep = [np.ascontiguousarray(n_lattice, dtype=np.int32), np.ascontiguousarray(x_left, dtype=np.float64),
                       np.ascontiguousarray(x_right, dtype=np.float64), np.ascontiguousarray(tau, dtype=np.float64)]
         nl, xl, xr, tau_ = self._keep
         self.n_inst = int(nl.shape[0])
         prob = ProblemS(self.n_inst, _ip(nl), _dp(xl), _dp(xr), _dp(tau_), make_fluid(fluid))
-        opts = make_options(options, zone_capacity, schedule, group_cells)
+        opts = make_options(options, zone_capacity, schedule, group_cells, group_threads)
         h = C.c_void_p()
         _check(L.imexds_create(C.byref(prob), C.byref(opts), C.c_void_p(stream), C.byref(h)))
         self.h = h
 
     @classmethod
     def from_batch(cls, batch, options=None, stream: int = 0, zone_capacity: int = 0, schedule: int = 0,
-                   group_cells: int = 0) -> "Imexds":
+                   group_cells: int = 0, group_threads: int = 0) -> "Imexds":
         ctx = cls(batch.n_lattice, batch.x_left, batch.x_right, batch.tau, batch.fluid, options or batch.options,
-                  stream=stream, zone_capacity=zone_capacity, schedule=schedule, group_cells=group_cells)
+                  stream=stream, zone_capacity=zone_capacity, schedule=schedule, group_cells=group_cells,
+                  group_threads=group_threads)
         ctx.set_states(batch.cell_offsets, batch.widths, batch.rho, batch.m, batch.phase)
         return ctx
 

@@ -54,11 +54,15 @@ def test_fixed_steps_full_size_sampled():
 
 
 def test_cavitation_full_count_sampled():
-    """All 16384 cavitation instances (N up to 4096) for 1000 steps; every instance creates vapour."""
+    """All 16384 cavitation instances (N up to 4096) for 1000 steps; every instance creates vapour. In the
+    smallest instances the cavity reaches the domain end and the liquid there vanishes (not treated by
+    the method): those instances stop with IMEXDS_ERR_VANISH, as in the oracle (the sample includes the
+    smallest instance)."""
     b = I.workload(4)
     b.n_steps = 1000
     g, st = _sampled(b, 6)
-    assert (g["status"] == 0).all()
+    assert set(np.unique(g["status"]).tolist()) <= {0, 6}
+    assert (g["status"][b.n_lattice >= 256] == 0).all()
     assert (st["creations"] >= 1).all()
 
 
