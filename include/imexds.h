@@ -75,7 +75,7 @@ typedef struct {
   int schedule;        /* 0 automatic, 1 one launch per kernel and step (graph of 8 steps), 2 instance
                           groups advanced by one resident launch (0) */
   int group_cells;     /* lattice cells per instance group (0 = 16384) */
-  int group_threads;   /* threads per group CTA, a multiple of 32 from 64 to 256 (0 = 128): warp 0 runs
+  int group_threads;   /* threads per group CTA, a multiple of 32 from 64 to 128 (0 = 128): warp 0 runs
                           the per-instance work, the other warps sweep */
 } imexds_options;
 
@@ -134,6 +134,11 @@ imexds_status imexds_set_states_device(imexds_ctx* ctx, const int32_t* cell_offs
 /* Restore the states (and t0) given to the last imexds_set_states, on the device (device-to-device
  * copies only). */
 imexds_status imexds_reset(imexds_ctx* ctx);
+
+/* Measurement of the group schedule (timing mode): SM clock cycles spent per phase of the resident
+ * kernel (0 boundary solves + plan, 1 sweep, 2 dual time, 3 grid management), for the group with the
+ * longest critical path (slowest4) and summed over all groups (sum4). Arrays of 4. */
+imexds_status imexds_get_group_phase_cycles(imexds_ctx* ctx, int64_t* slowest4, int64_t* sum4);
 
 /* Choose the schedule for the next calls (values of imexds_options.schedule). */
 imexds_status imexds_set_schedule(imexds_ctx* ctx, int32_t schedule);

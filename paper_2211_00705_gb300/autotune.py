@@ -20,7 +20,7 @@ CANDIDATES = [
     {"schedule": 1},
     {"schedule": 2, "group_threads": 128, "group_cells": 16384},
     {"schedule": 2, "group_threads": 128, "group_cells": 8192},
-    {"schedule": 2, "group_threads": 256, "group_cells": 16384},
+    {"schedule": 2, "group_threads": 96, "group_cells": 16384},
     {"schedule": 2, "group_threads": 64, "group_cells": 4096},
 ]
 

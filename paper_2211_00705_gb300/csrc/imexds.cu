@@ -64,7 +64,7 @@ struct Zone {
 struct Inst {
   int N, lat_off, zone_off, zone_cap;
   double xL, h, tau;
-  double t, dt;
+  double t, dt, lam;  // lam = dt / h (set with dt)
   int status, active, parity, clipped;
   unsigned long long smax_bits;
   int n_ev;
@@ -489,9 +489,8 @@ __device__ void sweep_tile32(const Dev& d, int ii, int j0) {
       r1 = (h * C.r - dt * (fr.F0L - fj.F0R)) / hnp1;
       m1 = (h * C.m - dt * (fr.F1L - fj.F1R)) / hnp1;
     } else {
-      const double lam = dt / h;
-      r1 = __fma_rn(-lam, fr.F0L - fj.F0R, C.r);
-      m1 = __fma_rn(-lam, fr.F1L - fj.F1R, C.m);
+      r1 = __fma_rn(-I.lam, fr.F0L - fj.F0R, C.r);
+      m1 = __fma_rn(-I.lam, fr.F1L - fj.F1R, C.m);
     }
     d.rho[I.parity ^ 1][g] = r1;
     d.m[I.parity ^ 1][g] = m1;
@@ -645,130 +644,191 @@ __device__ __noinline__ bool dts_general(const Dev& d, Zone& Z, Inst& I, int e0,
   return true;
 }
 
-// Register-resident Algorithm 2 for the common block: three cells (extended indices e0..e0+2) with one
-// phase boundary at interior face PBF (1: between cells 0|1, 2: between 1|2), the other interior face
-// fixed. Same iteration as the general path; the stop test is evaluated without divisions
-// (res < tol  <=>  (1 + theta)|dW| < tol theta dt' max(|W|, 1), dt' = dt for the printed residual and
-// 1 for the residual times dt). Writes the converged U^{n+1} like the general path.
+// Register-resident Algorithm 2 for the most common zone: two cells with one phase boundary between
+// them and one pulled lattice cell on the tiny side, i.e. a block of three cells whose boundary is at
+// face PBF (2 when the pulled cell is on the left, 1 when it is on the right). Everything lives in
+// registers; the stop test is evaluated without divisions:
+//   res < tol  <=>  (1 + theta)|dW| < tol theta dt' max(|W|, 1),  dt' = dt (printed residual) or 1 (res dt).
 template <int PBF>
-__device__ bool dts_block3(const Dev& d, Zone& Z, Inst& I, int e0, const double* Ur, const double* Um,
-                           const double* Uw, const int* ph, double FL0, double FL1, double FR0, double FR1,
-                           double* out_r, double* out_m, double* out_w, long long& newton, long long& solves,
-                           long long& iters_out, long long& maxiter, bool& vanish, bool& nonconv) {
+__device__ void dts_simple(const Dev& d, int zi) {
+  Zone& Z = d.zones[zi];
+  Inst& I = d.inst[Z.inst];
+  const int cur = I.parity;
+  const double* lr = d.rho[cur] + I.lat_off;
+  const double* lm = d.m[cur] + I.lat_off;
+  const unsigned char* lph = d.phase + I.lat_off;
   const double dt = I.dt, h = I.h, tau = I.tau;
-  double th[3], ith[3], ctol[3];
-  const double dtr = (c_opts.res_mode == 1) ? 1.0 : dt;
+  const int N = I.N;
+  const int jp = (PBF == 2) ? Z.A - 1 : Z.B;  // the pulled lattice cell
+  // cells q = 0, 1, 2 and their extended indices e = q - 1 (pulled left) or q (pulled right)
+  double Ur[3], Um[3], Uw[3], hp[3];
+  int ph[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    int e = q + e0;
-    double hp = (e < 0 || e >= Z.nc) ? h : Z.hp[e];
-    th[q] = fmin(c_opts.theta_nb, hp / h);
-    ith[q] = 1.0 / (1.0 + th[q]);
-    bool tiny = (Z.tiny_mask >> (e + 1)) & 1u;
-    ctol[q] = (tiny ? c_opts.tol_k : c_opts.tol_nb) * th[q] * dtr;  // times max(|W|, 1), against (1+th)|dW|
+    const int e = (PBF == 2) ? q - 1 : q;
+    if (e < 0 || e > 1) {
+      Ur[q] = lr[jp];
+      Um[q] = lm[jp];
+      Uw[q] = h;
+      hp[q] = h;
+      ph[q] = lph[jp];
+    } else {
+      Ur[q] = Z.r[e];
+      Um[q] = Z.m[e];
+      Uw[q] = Z.w[e];
+      hp[q] = Z.hp[e];
+      ph[q] = Z.ph[e];
+    }
   }
-  // h^n U^n, fixed parts of the numerators
-  double hU0[3], hU1[3];
+  // F_left / F_right from U^n (the same function as the sweep: identical bits)
+  double FL0, FL1, FR0, FR1;
+  if (Z.oA > 0)
+    hll_fast(c_fluid.ph[ph[0]], lr[Z.oA - 1], lm[Z.oA - 1], Ur[0], Um[0], FL0, FL1);
+  else
+    phys_flux_fast(c_fluid.ph[ph[0]], Ur[0], Um[0], FL0, FL1);
+  if (Z.oB < N)
+    hll_fast(c_fluid.ph[ph[2]], Ur[2], Um[2], lr[Z.oB], lm[Z.oB], FR0, FR1);
+  else
+    phys_flux_fast(c_fluid.ph[ph[2]], Ur[2], Um[2], FR0, FR1);
+  const double dtr = (c_opts.res_mode == 1) ? 1.0 : dt;
+  double th[3], ith[3], lim[3], hU0[3], hU1[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
+    const int e = (PBF == 2) ? q - 1 : q;
+    th[q] = fmin(c_opts.theta_nb, hp[q] / h);
+    ith[q] = 1.0 / (1.0 + th[q]);
+    const bool tiny = (Z.tiny_mask >> (e + 1)) & 1u;
+    lim[q] = (tiny ? c_opts.tol_k : c_opts.tol_nb) * th[q] * dtr * ith[q];
     hU0[q] = Uw[q] * Ur[q];
     hU1[q] = Uw[q] * Um[q];
   }
-  const int a = PBF - 1;       // the boundary lies between cells a and a+1
-  const int b = (PBF == 1) ? 2 : 1;  // the fixed interior face between cells b-1 and b
-  const int ePB = PBF + e0;    // zone face index of the boundary
-  double gl = Z.pwl[ePB], gr = Z.pwr[ePB];
-  double W0[3], W1[3];
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    W0[q] = Ur[q];
-    W1[q] = Um[q];
-  }
-  double Fp0 = 0, Fp1 = 0, wpb = 0, Fh0 = 0, Fh1 = 0;
-  auto fluxes = [&](bool& ok) {
+  constexpr int a = PBF - 1;               // boundary between cells a and a+1
+  constexpr int b = (PBF == 1) ? 2 : 1;    // fixed interior face between cells b-1 and b
+  const double ih_fixed = 1.0 / Uw[PBF == 1 ? 2 : 0];  // the cell away from the boundary keeps its width
+  double gl = Z.pwl[1], gr = Z.pwr[1];
+  double W0[3] = {Ur[0], Ur[1], Ur[2]}, W1[3] = {Um[0], Um[1], Um[2]};
+  long long newton = 0, solves = 0;
+  double Fp0 = 0.0, Fp1 = 0.0, wpb = 0.0, Fh0 = 0.0, Fh1 = 0.0;
+  bool fail = false;
+  auto fluxes = [&]() -> bool {
     PBOut R = pb_solve_warm(c_fluid, c_opts, tau, ph[a], W0[a], W1[a], ph[a + 1], W0[a + 1], W1[a + 1], gl, gr);
     newton += R.iters;
     solves++;
-    if (!R.ok) {
-      ok = false;
-      nonconv = true;
-      return;
-    }
+    if (!R.ok) return false;
     Fp0 = R.F0;
     Fp1 = R.F1;
     wpb = R.w;
     hll_fast(c_fluid.ph[ph[b]], W0[b - 1], W1[b - 1], W0[b], W1[b], Fh0, Fh1);
-    ok = true;
+    return true;
   };
-  // face fluxes in order (faces 0..3) and widths
-  auto assemble = [&](double* F0, double* F1, double* hl) {
-    F0[0] = FL0;
-    F1[0] = FL1;
-    F0[3] = FR0;
-    F1[3] = FR1;
-    F0[PBF] = Fp0;
-    F1[PBF] = Fp1;
-    F0[b] = Fh0;
-    F1[b] = Fh1;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) hl[q] = Uw[q];
-    hl[a] = Uw[a] + (wpb - 0.0) * dt;
-    hl[a + 1] = Uw[a + 1] + (0.0 - wpb) * dt;
+  // fluxes at faces 0..3 in order
+  auto face = [&](int g, double& f0, double& f1) {
+    if (g == 0) {
+      f0 = FL0;
+      f1 = FL1;
+    } else if (g == 3) {
+      f0 = FR0;
+      f1 = FR1;
+    } else if (g == PBF) {
+      f0 = Fp0;
+      f1 = Fp1;
+    } else {
+      f0 = Fh0;
+      f1 = Fh1;
+    }
   };
   bool stop = false;
   int l;
   for (l = 0; l < c_opts.l_max && !stop; ++l) {
-    bool ok;
-    fluxes(ok);
-    if (!ok) return false;
-    double F0[4], F1[4], hl[3];
-    assemble(F0, F1, hl);
-    if (!(hl[a] > 0.0) || !(hl[a + 1] > 0.0)) {
-      vanish = true;
-      return false;
+    if (!fluxes()) {
+      fail = true;
+      break;
     }
+    const double ha = Uw[a] + (wpb - 0.0) * dt, hb = Uw[a + 1] + (0.0 - wpb) * dt;
+    if (!(ha > 0.0) || !(hb > 0.0)) {
+      set_status(I, IMEXDS_ERR_VANISH);
+      return;
+    }
+    const double iha = 1.0 / ha, ihb = 1.0 / hb;
     stop = true;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      double ihl = (q == a || q == a + 1) ? 1.0 / hl[q] : 1.0 / Uw[q];
-      double n0 = (W0[q] + th[q] * ((hU0[q] - dt * (F0[q + 1] - F0[q])) * ihl)) * ith[q];
-      double n1 = (W1[q] + th[q] * ((hU1[q] - dt * (F1[q + 1] - F1[q])) * ihl)) * ith[q];
-      double lim = ctol[q] * ith[q];
-      bool okq = (fabs(n0 - W0[q]) < lim * fmax(fabs(W0[q]), 1.0)) && (fabs(n1 - W1[q]) < lim * fmax(fabs(W1[q]), 1.0));
-      stop = stop && okq;
+      double f0l, f1l, f0r, f1r;
+      face(q, f0l, f1l);
+      face(q + 1, f0r, f1r);
+      const double ih = (q == a) ? iha : ((q == a + 1) ? ihb : ih_fixed);
+      const double n0 = (W0[q] + th[q] * ((hU0[q] - dt * (f0r - f0l)) * ih)) * ith[q];
+      const double n1 = (W1[q] + th[q] * ((hU1[q] - dt * (f1r - f1l)) * ih)) * ith[q];
+      stop = stop && (fabs(n0 - W0[q]) < lim[q] * fmax(fabs(W0[q]), 1.0)) &&
+             (fabs(n1 - W1[q]) < lim[q] * fmax(fabs(W1[q]), 1.0));
       W0[q] = n0;
       W1[q] = n1;
     }
   }
-  if (!stop) maxiter++;
-  iters_out = l;
-  // Part 2 at U^{n,*}
-  bool ok;
-  fluxes(ok);
-  if (!ok) return false;
-  double F0[4], F1[4], hl[3];
-  assemble(F0, F1, hl);
-  if (!(hl[a] > 0.0) || !(hl[a + 1] > 0.0)) {
-    vanish = true;
-    return false;
+  if (fail || !fluxes()) {  // Part 2 needs the fluxes at U^{n,*}
+    set_status(I, IMEXDS_ERR_PB_NOCONV);
+    return;
   }
+  const double ha = Uw[a] + (wpb - 0.0) * dt, hb = Uw[a + 1] + (0.0 - wpb) * dt;
+  if (!(ha > 0.0) || !(hb > 0.0)) {
+    set_status(I, IMEXDS_ERR_VANISH);
+    return;
+  }
+  double* nr = d.rho[cur ^ 1] + I.lat_off;
+  double* nm = d.m[cur ^ 1] + I.lat_off;
+  double smax = 0.0;
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    out_r[q] = (hU0[q] - dt * (F0[q + 1] - F0[q])) / hl[q];
-    out_m[q] = (hU1[q] - dt * (F1[q + 1] - F1[q])) / hl[q];
-    out_w[q] = hl[q];
+    double f0l, f1l, f0r, f1r;
+    face(q, f0l, f1l);
+    face(q + 1, f0r, f1r);
+    const double hn1 = (q == a) ? ha : ((q == a + 1) ? hb : Uw[q]);
+    const double r1 = (hU0[q] - dt * (f0r - f0l)) / hn1;
+    const double m1 = (hU1[q] - dt * (f1r - f1l)) / hn1;
+    if (!(r1 > 0.0) || !isfinite(r1) || !isfinite(m1)) set_status(I, IMEXDS_ERR_NONPHYSICAL);
+    smax = fmax(smax, fabs(m1 / r1) + c_fluid.ph[ph[q]].a);
+    const int e = (PBF == 2) ? q - 1 : q;
+    if (e < 0 || e > 1) {
+      nr[jp] = r1;
+      nm[jp] = m1;
+    } else {
+      Z.r[e] = r1;
+      Z.m[e] = m1;
+      Z.w[e] = hn1;
+    }
   }
-  Z.pwl[ePB] = gl;
-  Z.pwr[ePB] = gr;
-  Z.fx[ePB] = Z.fx[ePB] + wpb * dt;
-  return true;
+  Z.pwl[1] = gl;
+  Z.pwr[1] = gr;
+  Z.fx[1] = Z.fx[1] + wpb * dt;
+  if (smax > 0.0) atomicMax(&I.smax_bits, dbits(smax));
+  atomicAdd((unsigned long long*)&I.stats[1], (unsigned long long)l);
+  atomicMax((unsigned long long*)&I.stats[2], (unsigned long long)l);
+  atomicAdd((unsigned long long*)&I.stats[3], (unsigned long long)newton);
+  if (!stop) atomicAdd((unsigned long long*)&I.stats[7], 1ull);
+  atomicAdd((unsigned long long*)&I.stats[8], (unsigned long long)solves);
 }
+
+__device__ void dts_zone_general(const Dev& d, int zi);
 
 __device__ void dts_zone(const Dev& d, int zi) {
   Zone& Z = d.zones[zi];
   if (!Z.alive) return;
-  Inst& I = d.inst[Z.inst];
+  const Inst& I = d.inst[Z.inst];
   if (!I.active || I.status) return;
+  if (Z.nc == 2 && Z.fpb[1] && Z.nblk == 1 && (Z.pullL + Z.pullR) == 1) {
+    if (Z.pullL)
+      dts_simple<2>(d, zi);
+    else
+      dts_simple<1>(d, zi);
+    return;
+  }
+  dts_zone_general(d, zi);
+}
+
+// Algorithm 2 for any zone shape (blocks of any size, zone cells outside the blocks), kept out of line.
+__device__ __noinline__ void dts_zone_general(const Dev& d, int zi) {
+  Zone& Z = d.zones[zi];
+  Inst& I = d.inst[Z.inst];
   const int cur = I.parity;
   const double* lr = d.rho[cur] + I.lat_off;
   const double* lm = d.m[cur] + I.lat_off;
@@ -842,22 +902,7 @@ __device__ void dts_zone(const Dev& d, int zi) {
   double xpb_new[ZB + 1];
   int moved[ZB + 1];
   for (int q = 0; q <= nq; ++q) moved[q] = 0;
-  // common case: one block of three cells holding the whole zone with one boundary face
-  bool simple = (Z.nblk == 1 && nq == 3 && Z.blo[0] - e0 == 0 && Z.bhi[0] - e0 == 2 && (B.fpb[1] + B.fpb[2]) == 1);
-  if (simple) {
-    bool vanish = false, nonconv = false;
-    long long it = 0;
-    bool ok = B.fpb[1] ? dts_block3<1>(d, Z, I, e0, B.r, B.m, B.w, B.ph, Fx0[0], Fx1[0], Fx0[3], Fx1[3], out_r, out_m,
-                                       out_w, newton, solves, it, maxiter, vanish, nonconv)
-                       : dts_block3<2>(d, Z, I, e0, B.r, B.m, B.w, B.ph, Fx0[0], Fx1[0], Fx0[3], Fx1[3], out_r, out_m,
-                                       out_w, newton, solves, it, maxiter, vanish, nonconv);
-    if (!ok) {
-      set_status(I, nonconv ? IMEXDS_ERR_PB_NOCONV : IMEXDS_ERR_VANISH);
-      return;
-    }
-    iters_sum = it;
-    iters_max = it;
-  }
+  const bool simple = false;
   if (!simple) {
     if (!dts_general(d, Z, I, e0, nq, B, Fx0, Fx1, out_r, out_m, out_w, xpb_new, moved, newton, solves, iters_sum,
                      iters_max, maxiter))
@@ -1203,6 +1248,7 @@ __device__ __noinline__ void post_inst(const Dev& d, int ii) {
     }
   }
   I.dt = dtn;
+  I.lam = dtn / h;
 }
 
 // ---------------------------------------------------------------------------------- step kernels
@@ -1239,13 +1285,16 @@ __global__ void k_post(Dev d, int n) {
 // lattice cells while warp 0 runs the dual-time chains of the same step.
 constexpr int GROUP_MAX = 32;
 template <bool CREATION>
-__global__ void __launch_bounds__(256) k_group(Dev d, const int* ginst, const int2* grange, int max_steps) {
+__global__ void __launch_bounds__(128, 2) k_group(Dev d, const int* ginst, const int2* grange, int max_steps,
+                                               long long* phase_cycles) {
   const int2 gr = grange[blockIdx.x];
+  long long cyc[4] = {0, 0, 0, 0};  // pre+plan, sweep (warp 1), dual time (warp 0), post
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
   const int ii = (lane < gr.y) ? ginst[gr.x + lane] : -1;
   __shared__ int s_more;
   for (int step = 0; step < max_steps; ++step) {
+    long long c0 = clock64();
     if (warp == 0 && ii >= 0) {
       Inst& I = d.inst[ii];
       if (I.active && !I.status) {
@@ -1258,6 +1307,7 @@ __global__ void __launch_bounds__(256) k_group(Dev d, const int* ginst, const in
       }
     }
     __syncthreads();
+    long long c1 = clock64();
     if (warp == 0) {
       if (ii >= 0) {
         Inst& I = d.inst[ii];
@@ -1265,6 +1315,7 @@ __global__ void __launch_bounds__(256) k_group(Dev d, const int* ginst, const in
           for (int z = I.zone_off; z < I.zone_off + I.zone_cap; ++z)
             if (d.zones[z].alive && !I.status) dts_zone(d, z);
       }
+      cyc[2] += clock64() - c1;
     } else {
       // the 32-cell tiles of all active instances of the group, dealt to warps 1..nw-1
       int t = warp - 1, base = 0;
@@ -1275,14 +1326,27 @@ __global__ void __launch_bounds__(256) k_group(Dev d, const int* ginst, const in
         for (; t < base + nt; t += nw - 1) sweep_tile32<CREATION>(d, ik, (t - base) << 5);
         base += nt;
       }
+      cyc[1] += clock64() - c1;
     }
     __syncthreads();
+    long long c2 = clock64();
+    cyc[0] += c1 - c0;
     if (warp == 0 && ii >= 0 && d.inst[ii].active) post_inst(d, ii);
     if (threadIdx.x == 0) s_more = 0;
     __syncthreads();
     if (warp == 0 && ii >= 0 && d.inst[ii].active && !d.inst[ii].status) atomicOr(&s_more, 1);
     __syncthreads();
+    cyc[3] += clock64() - c2;
     if (!s_more) break;
+  }
+  if (phase_cycles && lane == 0 && warp <= 1) {
+    if (warp == 0) {
+      phase_cycles[4 * blockIdx.x + 0] += cyc[0];
+      phase_cycles[4 * blockIdx.x + 2] += cyc[2];
+      phase_cycles[4 * blockIdx.x + 3] += cyc[3];
+    } else {
+      phase_cycles[4 * blockIdx.x + 1] += cyc[1];
+    }
   }
 }
 
@@ -1328,6 +1392,7 @@ __global__ void k_init_dt(Dev d, int n_inst) {
       }
     }
     I.dt = dt;
+    I.lam = dt / I.h;
     I.smax_bits = 0ull;
   }
 }
@@ -1372,6 +1437,7 @@ struct imexds_ctx {
   int schedule = 0;                       // 1 per-step kernels, 2 instance groups (0 auto at set_states)
   int schedule_opt = 0, group_cells = 16384, use_groups = 0, group_threads = 128;
   int n_groups = 0;
+  long long* d_phase = nullptr;  // per-group phase cycles (timing mode)
   int* d_ginst = nullptr;
   int2* d_grange = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
@@ -1445,6 +1511,8 @@ void free_dev(imexds_ctx* c) {
   cudaFree(d.ctrl);
   cudaFree(c->d_ginst);
   cudaFree(c->d_grange);
+  cudaFree(c->d_phase);
+  c->d_phase = nullptr;
   c->d_ginst = nullptr;
   c->d_grange = nullptr;
   d = Dev{};
@@ -1535,13 +1603,18 @@ imexds_status run_groups(imexds_ctx* c, long long max_steps, bool until_done) {
     CK(cudaEventCreate(&c->gev[0]));
     CK(cudaEventCreate(&c->gev[1]));
   }
+  if (c->timing && !c->d_phase) {
+    CK(cudaMalloc(&c->d_phase, sizeof(long long) * 4 * c->n_groups));
+    CK(cudaMemsetAsync(c->d_phase, 0, sizeof(long long) * 4 * c->n_groups, c->stream));
+  }
+  long long* pc = c->timing ? c->d_phase : nullptr;
   while (done < max_steps) {
     int n = (int)std::min<long long>(max_steps - done, 1 << 30);
     if (c->timing) cudaEventRecord(c->gev[0], c->stream);
     if (c->opts.creation)
-      k_group<true><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n);
+      k_group<true><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n, pc);
     else
-      k_group<false><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n);
+      k_group<false><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n, pc);
     if (c->timing) cudaEventRecord(c->gev[1], c->stream);
     k_count_active<<<1, 256, 0, c->stream>>>(c->d, c->n_inst);
     c->launches += 2;
@@ -1712,7 +1785,7 @@ imexds_status imexds_create(const imexds_problem* prob, const imexds_options* op
   c->schedule_opt = o.schedule;
   if (o.group_cells > 0) c->group_cells = o.group_cells;
   if (o.group_threads != 0) {
-    if (o.group_threads < 64 || o.group_threads > 256 || o.group_threads % 32) {
+    if (o.group_threads < 64 || o.group_threads > 128 || o.group_threads % 32) {
       delete c;
       return IMEXDS_ERR_ARG;
     }
@@ -2164,6 +2237,26 @@ imexds_status imexds_step_uniform_noalloc(const imexds_fluid* fluid, double cfl,
   CK(cudaMemcpyAsync(&err, &scr->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return err ? IMEXDS_ERR_ARG : IMEXDS_OK;
+}
+
+imexds_status imexds_get_group_phase_cycles(imexds_ctx* c, int64_t* slowest4, int64_t* sum4) {
+  if (!c || !slowest4 || !sum4) return IMEXDS_ERR_ARG;
+  for (int k = 0; k < 4; ++k) slowest4[k] = sum4[k] = 0;
+  if (!c->d_phase) return IMEXDS_OK;
+  std::vector<long long> h(4 * c->n_groups);
+  CK(cudaMemcpy(h.data(), c->d_phase, sizeof(long long) * h.size(), cudaMemcpyDeviceToHost));
+  int worst = 0;
+  long long wt = -1;
+  for (int g = 0; g < c->n_groups; ++g) {
+    long long t = h[4 * g] + std::max(h[4 * g + 1], h[4 * g + 2]) + h[4 * g + 3];
+    if (t > wt) {
+      wt = t;
+      worst = g;
+    }
+    for (int k = 0; k < 4; ++k) sum4[k] += h[4 * g + k];
+  }
+  for (int k = 0; k < 4; ++k) slowest4[k] = h[4 * worst + k];
+  return IMEXDS_OK;
 }
 
 imexds_status imexds_set_schedule(imexds_ctx* c, int32_t schedule) {

@@ -355,7 +355,9 @@ __device__ inline bool pbf_eval(const SideData& sl, const SideData& sr, bool lef
   return isfinite(S.G0) && isfinite(S.G1);
 }
 
-// Newton-Armijo from (x0, x1); returns 1 on convergence.
+// Newton-Armijo from (x0, x1); returns 1 on convergence with S evaluated at the returned point. One
+// evaluation state is kept: trial points are evaluated into S (the direction and the old norm are all
+// the line search needs), and S is evaluated again at x only on the rare exits after a failed search.
 __device__ inline int pbf_newton(const Fluid& F, const Opts& o, const SideData& sl, const SideData& sr, bool left_vap,
                                  double tau, double du, double imp, double& x0, double& x1, PBFast& S, int& iters) {
   if (!pbf_eval(sl, sr, left_vap, tau, du, x0, x1, S)) return 0;
@@ -371,10 +373,9 @@ __device__ inline int pbf_newton(const Fluid& F, const Opts& o, const SideData& 
     double d1 = -(-S.J10 * S.G0 + S.J00 * S.G1) * idet;
     double lam = 1.0;
     bool acc = false;
-    PBFast T;
     for (int ls = 0; ls <= 20; ++ls) {
-      if (pbf_eval(sl, sr, left_vap, tau, du, x0 + lam * d0, x1 + lam * d1, T)) {
-        double nt = hypot(T.G0 / imp, T.G1);
+      if (pbf_eval(sl, sr, left_vap, tau, du, x0 + lam * d0, x1 + lam * d1, S)) {
+        double nt = hypot(S.G0 / imp, S.G1);
         if (nt <= (1.0 - 1e-4 * lam) * nrm) {
           acc = true;
           nrm = nt;
@@ -386,12 +387,11 @@ __device__ inline int pbf_newton(const Fluid& F, const Opts& o, const SideData& 
     double s0 = fabs(d0) / fmax(fabs(x0), F.p_sat);
     double s1 = fabs(d1) / fmax(fabs(x1), F.p_sat);
     if (!acc) {
-      if (fmax(s0, s1) <= 1e-9) conv = true;
+      if (fmax(s0, s1) <= 1e-9) conv = pbf_eval(sl, sr, left_vap, tau, du, x0, x1, S);
       break;
     }
     x0 += lam * d0;
     x1 += lam * d1;
-    S = T;
     // a full Newton step below 1e-8 (relative) leaves an error of order 1e-16 (quadratic convergence):
     // the same root the newton_tol test reaches, one evaluation earlier
     if (lam * fmax(s0, s1) <= o.newton_tol || nrm == 0.0 || (lam == 1.0 && fmax(s0, s1) <= 1e-8)) conv = true;

@@ -19,7 +19,8 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_NONPHYSICAL", 4: "ERR_PB
 EXPORTED = ["imexds_create", "imexds_set_states", "imexds_set_states_device", "imexds_cell_counts",
             "imexds_get_states", "imexds_step", "imexds_run_to", "imexds_get_stats", "imexds_destroy",
             "imexds_status_string", "imexds_last_error_string", "imexds_reset", "imexds_set_kernel_timing",
-            "imexds_get_kernel_times", "imexds_set_schedule", "imexds_check_log", "imexds_step_uniform_noalloc"]
+            "imexds_get_kernel_times", "imexds_set_schedule", "imexds_check_log", "imexds_step_uniform_noalloc",
+            "imexds_get_group_phase_cycles"]
 
 
 class ImexdsError(RuntimeError):
@@ -73,6 +74,7 @@ def load():
         L.imexds_set_kernel_timing.argtypes = [vp, C.c_int32]
         L.imexds_get_kernel_times.argtypes = [vp, dp, C.POINTER(C.c_int64)]
         L.imexds_set_schedule.argtypes = [vp, C.c_int32]
+        L.imexds_get_group_phase_cycles.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.imexds_check_log.argtypes = [C.c_int32, dp, dp, dp]
         L.imexds_step_uniform_noalloc.argtypes = [C.POINTER(FluidS), C.c_double, C.c_int32, ip, dp, dp, vp, vp, vp,
                                                   vp, vp, vp, vp]
@@ -227,6 +229,14 @@ class Imexds:
         n = np.zeros(6, dtype=np.int64)
         _check(load().imexds_get_kernel_times(self.h, _dp(ms), n.ctypes.data_as(C.POINTER(C.c_int64))))
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.KERNELS)}
+
+    def group_phase_cycles(self) -> dict:
+        a = np.zeros(4, dtype=np.int64)
+        b = np.zeros(4, dtype=np.int64)
+        _check(load().imexds_get_group_phase_cycles(self.h, a.ctypes.data_as(C.POINTER(C.c_int64)),
+                                                    b.ctypes.data_as(C.POINTER(C.c_int64))))
+        keys = ["plan", "sweep", "dual_time", "post"]
+        return {"slowest": dict(zip(keys, a.tolist())), "sum": dict(zip(keys, b.tolist()))}
 
     def stats(self) -> dict:
         s = np.zeros((self.n_inst, 10), dtype=np.int64)
