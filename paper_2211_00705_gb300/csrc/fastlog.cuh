@@ -12,6 +12,7 @@ namespace imexds {
 constexpr int kLogJ0 = 90;    // first table index (90/128 < sqrt(1/2))
 constexpr int kLogJN = 93;    // entries for j = 90 .. 182
 struct LogTable {
+  double c[kLogJN];           // j / 128 (exact)
   double inv_c[kLogJN];       // 128 / j rounded
   double lnc_hi[kLogJN];      // ln(j/128) rounded to double ...
   double lnc_lo[kLogJN];      // ... and the remainder
@@ -25,17 +26,19 @@ __device__ __forceinline__ double fast_log(double x) {
   int e = (hi >> 20) & 0x7ff;
   if (e == 0 || e == 0x7ff || hi < 0) return log(x);  // zero, subnormal, inf, nan, negative
   int k = e - 1023;
-  int mhi = (hi & 0x000fffff) | 0x3ff00000;          // m in [1, 2)
-  if (mhi >= 0x3ff6a09e) {                           // m >= sqrt(2) (to 20 bits): use m/2, k+1
+  int frac = hi & 0x000fffff;                        // top 20 bits of the fraction f of m = 1 + f
+  int mhi = frac | 0x3ff00000;                       // m in [1, 2)
+  int j;
+  if (frac >= 0x6a09e) {                             // m >= sqrt(2) (to 20 bits): use m/2, k + 1
     mhi -= 0x00100000;
     k += 1;
+    j = 64 + ((frac + (1 << 13)) >> 14);             // round(64 (1 + f)), integer arithmetic only
+  } else {
+    j = 128 + ((frac + (1 << 12)) >> 13);            // round(128 (1 + f))
   }
   double m = __hiloint2double(mhi, lo);
-  // nearest grid point c = j/128 (j from the leading mantissa bits of m; m in [0.707, 1.415))
-  int j = __double2int_rn(m * 128.0);
-  double c = (double)j * 0.0078125;
   int t = j - kLogJ0;
-  double r = (m - c) * __ldg(&g_logtab.inv_c[t]);
+  double r = (m - __ldg(&g_logtab.c[t])) * __ldg(&g_logtab.inv_c[t]);
   // ln(1 + r) = r - r^2/2 + r^3/3 - ... - r^8/8 by Estrin's scheme
   double r2 = r * r;
   double r4 = r2 * r2;
@@ -47,7 +50,7 @@ __device__ __forceinline__ double fast_log(double x) {
   const double LN2_HI = 6.93147180369123816490e-01;  // ln 2 with the low 21 bits zero (k LN2_HI is exact)
   const double LN2_LO = 1.90821492927058770002e-10;  // ln 2 - LN2_HI
   double kd = (double)k;
-  double s_hi = __fma_rn(kd, LN2_HI, __ldg(&g_logtab.lnc_hi[t]));  // exact: both terms are short
+  double s_hi = __fma_rn(kd, LN2_HI, __ldg(&g_logtab.lnc_hi[t]));
   double s_lo = __fma_rn(kd, LN2_LO, __ldg(&g_logtab.lnc_lo[t]));
   return s_hi + (s_lo + p);
 }

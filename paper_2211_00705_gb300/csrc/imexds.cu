@@ -711,6 +711,8 @@ __device__ void dts_simple(const Dev& d, int zi) {
   double Fp0 = 0.0, Fp1 = 0.0, wpb = 0.0, Fh0 = 0.0, Fh1 = 0.0;
   bool fail = false;
   auto fluxes = [&]() -> bool {
+    // the fixed face first: its divisions overlap the boundary solve that follows
+    hll_fast(c_fluid.ph[ph[b]], W0[b - 1], W1[b - 1], W0[b], W1[b], Fh0, Fh1);
     PBOut R = pb_solve_warm(c_fluid, c_opts, tau, ph[a], W0[a], W1[a], ph[a + 1], W0[a + 1], W1[a + 1], gl, gr);
     newton += R.iters;
     solves++;
@@ -718,7 +720,6 @@ __device__ void dts_simple(const Dev& d, int zi) {
     Fp0 = R.F0;
     Fp1 = R.F1;
     wpb = R.w;
-    hll_fast(c_fluid.ph[ph[b]], W0[b - 1], W1[b - 1], W0[b], W1[b], Fh0, Fh1);
     return true;
   };
   // fluxes at faces 0..3 in order
@@ -1470,6 +1471,7 @@ LogTable make_log_table() {
     int j = kLogJ0 + t;
     long double c = (long double)j / 128.0L;
     long double l = logl(c);
+    T.c[t] = (double)j / 128.0;
     T.inv_c[t] = (double)(128.0L / (long double)j);
     T.lnc_hi[t] = (double)l;
     T.lnc_lo[t] = (double)(l - (long double)T.lnc_hi[t]);
@@ -1493,6 +1495,9 @@ Phase make_phase(const imexds_eos& e, double p_sat) {
   P.p0 = e.p0;
   P.rho0 = e.rho0;
   P.rho_sat = (e.kind == 0) ? p_sat / e.a2 : e.rho0 + (p_sat - e.p0) / e.a2;
+  P.ia2 = 1.0 / e.a2;
+  P.ia = 1.0 / P.a;
+  P.ln_rho_sat = std::log(P.rho_sat);
   return P;
 }
 

@@ -17,6 +17,7 @@ struct Phase {
   double a2, a;   // squared sound speed, sound speed
   double p0, rho0;
   double rho_sat; // density at the saturation pressure (zero of g)
+  double ia2, ia, ln_rho_sat;  // 1/a2, 1/a, ln(rho_sat) (set on the host)
 };
 
 struct Fluid {
@@ -289,9 +290,9 @@ __device__ inline SideData side_data(const Phase& e, double rK) {
   s.pK = pressure(e, rK);
   s.invK = 1.0 / rK;
   s.isat = 1.0 / e.rho_sat;
-  s.CK = fast_log(e.rho_sat * s.invK);
-  s.ia2 = 1.0 / e.a2;
-  s.ia = 1.0 / e.a;
+  s.CK = e.ln_rho_sat - fast_log(rK);  // ln(rho_sat / rho_K), independent of 1/rho_K
+  s.ia2 = e.ia2;
+  s.ia = e.ia;
   return s;
 }
 
@@ -299,33 +300,27 @@ struct SideEval {
   double p, v, g, dv, f, df;
 };
 
+// Branch-free: both wave branches are formed and one is selected, so the two sides of a boundary can be
+// interleaved by the instruction scheduler.
 __device__ inline bool side_eval(const SideData& s, double p, SideEval& o) {
   const Phase& e = *s.E;
-  double rs = e.kind == 0 ? p * s.ia2 : e.rho0 + (p - e.p0) * s.ia2;
-  if (!(rs > 0.0) || !isfinite(p)) return false;
+  double rs = e.kind == 0 ? p * s.ia2 : __fma_rn(p - e.p0, s.ia2, e.rho0);
   double v = 1.0 / rs;
   double Ls = fast_log(rs * s.isat);
   o.p = p;
   o.v = v;
   o.g = e.a2 * Ls;
   o.dv = -v * v * s.ia2;
-  if (p > s.pK) {
-    double dvk = s.invK - v;
-    double q = (p - s.pK) * dvk;
-    double dq = dvk + (p - s.pK) * v * v * s.ia2;
-    if (q > 0.0) {
-      double rq = rsqrt(q);  // f = sqrt(q) = q / sqrt(q), df = dq / (2 sqrt(q))
-      o.f = q * rq;
-      o.df = 0.5 * dq * rq;
-    } else {
-      o.f = 0.0;
-      o.df = v * s.ia;
-    }
-  } else {
-    o.f = e.a * (Ls + s.CK);
-    o.df = v * s.ia;
-  }
-  return true;
+  // shock (p > p_K): f = sqrt(q), q = (p - p_K)(v_K - v); rarefaction: f = a ln(rho*/rho_K)
+  double dvk = s.invK - v;
+  double dp = p - s.pK;
+  double q = dp * dvk;
+  double dq = __fma_rn(dp * v * v, s.ia2, dvk);
+  double rq = rsqrt(fmax(q, 1e-300));
+  bool shock = (dp > 0.0) && (q > 0.0);
+  o.f = shock ? q * rq : e.a * (Ls + s.CK);
+  o.df = shock ? 0.5 * dq * rq : v * s.ia;
+  return (rs > 0.0) && isfinite(p);
 }
 
 struct PBFast {
@@ -361,8 +356,11 @@ __device__ inline bool pbf_eval(const SideData& sl, const SideData& sr, bool lef
 __device__ inline int pbf_newton(const Fluid& F, const Opts& o, const SideData& sl, const SideData& sr, bool left_vap,
                                  double tau, double du, double imp, double& x0, double& x1, PBFast& S, int& iters) {
   if (!pbf_eval(sl, sr, left_vap, tau, du, x0, x1, S)) return 0;
-  double nrm = hypot(S.G0 / imp, S.G1);
-  bool conv = (nrm == 0.0);
+  const double iimp = 1.0 / imp;
+  // the Armijo test on squared norms: |G_t|^2 <= (1 - 1e-4 lam)^2 |G|^2
+  double g0 = S.G0 * iimp;
+  double nrm2 = __fma_rn(g0, g0, S.G1 * S.G1);
+  bool conv = (nrm2 == 0.0);
   int it = 0;
   while (!conv && it < o.newton_itmax) {
     ++it;
@@ -375,10 +373,12 @@ __device__ inline int pbf_newton(const Fluid& F, const Opts& o, const SideData& 
     bool acc = false;
     for (int ls = 0; ls <= 20; ++ls) {
       if (pbf_eval(sl, sr, left_vap, tau, du, x0 + lam * d0, x1 + lam * d1, S)) {
-        double nt = hypot(S.G0 / imp, S.G1);
-        if (nt <= (1.0 - 1e-4 * lam) * nrm) {
+        double t0 = S.G0 * iimp;
+        double nt2 = __fma_rn(t0, t0, S.G1 * S.G1);
+        double f = 1.0 - 1e-4 * lam;
+        if (nt2 <= f * f * nrm2) {
           acc = true;
-          nrm = nt;
+          nrm2 = nt2;
           break;
         }
       }
@@ -394,7 +394,7 @@ __device__ inline int pbf_newton(const Fluid& F, const Opts& o, const SideData& 
     x1 += lam * d1;
     // a full Newton step below 1e-8 (relative) leaves an error of order 1e-16 (quadratic convergence):
     // the same root the newton_tol test reaches, one evaluation earlier
-    if (lam * fmax(s0, s1) <= o.newton_tol || nrm == 0.0 || (lam == 1.0 && fmax(s0, s1) <= 1e-8)) conv = true;
+    if (lam * fmax(s0, s1) <= o.newton_tol || nrm2 == 0.0 || (lam == 1.0 && fmax(s0, s1) <= 1e-8)) conv = true;
   }
   iters += it;
   return conv ? 1 : 0;
