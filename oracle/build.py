@@ -9,8 +9,8 @@ LIB = os.path.join(HERE, "liboracle.so")
 
 def build(force: bool = False) -> str:
     src = os.path.join(HERE, "oracle.cpp")
-    hdr = os.path.join(HERE, "oracle.h")
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(src), os.path.getmtime(hdr)):
+    deps = [src] + [os.path.join(HERE, h) for h in ("oracle.h", "dual.h")]
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in deps):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",

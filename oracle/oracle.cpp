@@ -12,6 +12,8 @@
 // notes of the repository.
 #include "oracle.h"
 
+#include "dual.h"
+
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -57,20 +59,64 @@ Fluid make_fluid(const orc_fluid* f) {
   return F;
 }
 
+// Every function below is a template on the scalar type T: T = double is the oracle itself; T = a
+// forward-mode dual number (dual.h) gives the derivative of the same computation (the oracle's
+// tangent-linear mode). Branches, maxima and stop tests act on values only.
+using orcdual::tmax;
+using orcdual::tmin;
+using orcdual::val;
+template <class T>
+T tsqrt(const T& x) {
+  using orcdual::sqrt;
+  using std::sqrt;
+  return sqrt(x);
+}
+template <class T>
+T tlog(const T& x) {
+  using orcdual::log;
+  using std::log;
+  return log(x);
+}
+template <class T>
+T texp(const T& x) {
+  using orcdual::exp;
+  using std::exp;
+  return exp(x);
+}
+template <class T>
+T tfabs(const T& x) {
+  using orcdual::fabs;
+  using std::fabs;
+  return fabs(x);
+}
+
 // Vapour: ideal gas p = (kT0/m) rho (Eq. eos:isoT_idgas). Liquid: linear Tait p = p0 + K0(rho/rho0 - 1)
 // (Eq. eos:isoT_lintait; Reading: the printed "- p0" inside the bracket is read as "- 1", a2 = K0/rho0).
-double pressure(const Phase& e, double rho) { return e.kind == 0 ? e.a2 * rho : e.p0 + e.a2 * (rho - e.rho0); }
-double density(const Phase& e, double p) { return e.kind == 0 ? p / e.a2 : e.rho0 + (p - e.p0) / e.a2; }
+template <class T>
+T pressure(const Phase& e, const T& rho) {
+  return e.kind == 0 ? T(e.a2 * rho) : T(e.p0 + e.a2 * (rho - e.rho0));
+}
+template <class T>
+T density(const Phase& e, const T& p) {
+  return e.kind == 0 ? T(p / e.a2) : T(e.rho0 + (p - e.p0) / e.a2);
+}
 // Admissible pressure range of a phase: the density it maps to must be positive.
-bool valid_pressure(const Phase& e, double p) { return std::isfinite(p) && density(e, p) > 0.0; }
+template <class T>
+bool valid_pressure(const Phase& e, const T& p) {
+  return std::isfinite(val(p)) && val(density(e, p)) > 0.0;
+}
 // Gibbs energy g = f + p/rho with dg = v dp at fixed T (Sec. 2.1). For both EOS, dp = a2 drho, so
 // g = a2 ln(rho/rho_sat). Reading: both phases share the zero at the saturation pressure, where
 // the Maxwell construction makes the Gibbs energies equal.
-double gibbs(const Phase& e, double rho) { return e.a2 * std::log(rho / e.rho_sat); }
+template <class T>
+T gibbs(const Phase& e, const T& rho) {
+  return e.a2 * tlog(T(rho / e.rho_sat));
+}
 
 // Physical flux F(U) = (rho u, rho u^2 + p) of the isothermal Euler system (Eq. eeq:isoT both).
-void phys_flux(const Phase& e, double r, double m, double F[2]) {
-  double u = m / r;
+template <class T>
+void phys_flux(const Phase& e, const T& r, const T& m, T F[2]) {
+  T u = m / r;
   F[0] = m;
   F[1] = m * u + pressure(e, r);
 }
@@ -78,21 +124,22 @@ void phys_flux(const Phase& e, double r, double m, double F[2]) {
 // HLL approximate Riemann solver (Toro) at a face between two cells of the same phase, used at all
 // regular faces (Sec. 4). Reading: Davis wave-speed estimates S_L = min(u_l - a, u_r - a),
 // S_R = max(u_l + a, u_r + a).
-void hll(const Phase& e, double rl, double ml, double rr, double mr, double F[2]) {
-  double ul = ml / rl, ur = mr / rr;
-  double Fl[2], Fr[2];
+template <class T>
+void hll(const Phase& e, const T& rl, const T& ml, const T& rr, const T& mr, T F[2]) {
+  T ul = ml / rl, ur = mr / rr;
+  T Fl[2], Fr[2];
   phys_flux(e, rl, ml, Fl);
   phys_flux(e, rr, mr, Fr);
-  double SL = std::min(ul - e.a, ur - e.a);
-  double SR = std::max(ul + e.a, ur + e.a);
-  if (SL >= 0.0) {
+  T SL = tmin(T(ul - e.a), T(ur - e.a));
+  T SR = tmax(T(ul + e.a), T(ur + e.a));
+  if (val(SL) >= 0.0) {
     F[0] = Fl[0];
     F[1] = Fl[1];
-  } else if (SR <= 0.0) {
+  } else if (val(SR) <= 0.0) {
     F[0] = Fr[0];
     F[1] = Fr[1];
   } else {
-    double Ul[2] = {rl, ml}, Ur[2] = {rr, mr};
+    T Ul[2] = {rl, ml}, Ur[2] = {rr, mr};
     for (int c = 0; c < 2; ++c) F[c] = (SR * Fl[c] - SL * Fr[c] + SL * SR * (Ur[c] - Ul[c])) / (SR - SL);
   }
 }
@@ -100,29 +147,32 @@ void hll(const Phase& e, double rl, double ml, double rr, double mr, double F[2]
 // Wave function of a classical outer wave (App. A): f_K(p*) = sqrt(-[[p]][[v]]) for a shock
 // (p* > p_K), and the integral of v/a from p_K to p* for a rarefaction. For an isothermal linear EOS
 // (dp = a2 drho) that integral is a ln(rho*/rho_K). df/dp* is returned in *dfdp.
-double wave_f(const Phase& e, double pstar, double rhoK, double* dfdp) {
-  double pK = pressure(e, rhoK);
-  double rs = density(e, pstar);
-  double vs = 1.0 / rs;
-  if (pstar > pK) {
-    double dv = 1.0 / rhoK - vs;  // v_K - v* >= 0
-    double q = (pstar - pK) * dv;
-    double f = std::sqrt(q);
-    double dq = dv + (pstar - pK) * vs * vs / e.a2;  // d/dp* of (p* - p_K)(v_K - v*)
-    *dfdp = (f > 0.0) ? 0.5 * dq / f : vs / e.a;
+template <class T>
+T wave_f(const Phase& e, const T& pstar, const T& rhoK, T* dfdp) {
+  T pK = pressure(e, rhoK);
+  T rs = density(e, pstar);
+  T vs = 1.0 / rs;
+  if (val(pstar) > val(pK)) {
+    T dv = 1.0 / rhoK - vs;  // v_K - v* >= 0
+    T q = (pstar - pK) * dv;
+    T f = tsqrt(q);
+    T dq = dv + (pstar - pK) * vs * vs / e.a2;  // d/dp* of (p* - p_K)(v_K - v*)
+    *dfdp = (val(f) > 0.0) ? T(0.5 * dq / f) : T(vs / e.a);
     return f;
   }
   *dfdp = vs / e.a;
-  return e.a * std::log(rs / rhoK);
+  return e.a * tlog(T(rs / rhoK));
 }
 
 // One side of a phase boundary: star pressure, phase, density, volume, Gibbs energy and dv/dp.
+template <class T>
 struct Side {
-  double p, rho, v, g, dv;
+  T p, rho, v, g, dv;
 };
 
-Side side_at(const Phase& e, double p) {
-  Side s;
+template <class T>
+Side<T> side_at(const Phase& e, const T& p) {
+  Side<T> s;
   s.p = p;
   s.rho = density(e, p);
   s.v = 1.0 / s.rho;
@@ -135,40 +185,43 @@ Side side_at(const Phase& e, double p) {
 // side L and right star side R. Reading: e_kin = (u - w)^2 / 2 is taken relative to the moving
 // boundary, so [[e_kin]] = z^2 [[v^2]] / 2, and z^2 = -[[p]]/[[v]] (Eq. isoT:pb_mom_balance) turns it
 // into [[e_kin]] = -[[p]] (v_L + v_R) / 2. dz/dp of both sides in *dzl, *dzr.
-double kinetic_z(double tau, bool left_is_vapour, const Side& L, const Side& R, double* dzl, double* dzr) {
-  double pV = left_is_vapour ? L.p : R.p;
-  double jp = R.p - L.p;
-  double Q = (R.g - L.g) - 0.5 * jp * (L.v + R.v);
+template <class T>
+T kinetic_z(const T& tau, bool left_is_vapour, const Side<T>& L, const Side<T>& R, T* dzl, T* dzr) {
+  T pV = left_is_vapour ? L.p : R.p;
+  T jp = R.p - L.p;
+  T Q = (R.g - L.g) - 0.5 * jp * (L.v + R.v);
   // dQ/dp_L = -v_L + (v_L+v_R)/2 - jp dv_L/2 ; dQ/dp_R = v_R - (v_L+v_R)/2 - jp dv_R/2 (dg/dp = v)
-  double dQl = -L.v + 0.5 * (L.v + R.v) - 0.5 * jp * L.dv;
-  double dQr = R.v - 0.5 * (L.v + R.v) - 0.5 * jp * R.dv;
-  *dzl = tau * ((left_is_vapour ? Q : 0.0) + pV * dQl);
-  *dzr = tau * ((left_is_vapour ? 0.0 : Q) + pV * dQr);
+  T dQl = -L.v + 0.5 * (L.v + R.v) - 0.5 * jp * L.dv;
+  T dQr = R.v - 0.5 * (L.v + R.v) - 0.5 * jp * R.dv;
+  *dzl = tau * ((left_is_vapour ? Q : T(0.0)) + pV * dQl);
+  *dzr = tau * ((left_is_vapour ? T(0.0) : Q) + pV * dQr);
   return tau * pV * Q;
 }
 
 // The 2x2 system G(p_l*, p_r*) of Eq. 2p_RP:ex_sys, oriented left/right:
 //   G1 = [[p]] + z^2 [[v]],  G2 = f_l + f_r + z [[v]] + (u_r - u_l)
 // and its Jacobian (Eq. jacobian:ex_sys).
+template <class T>
 struct PBSys {
-  double G[2], J[2][2], z;
-  Side L, R;
-  double fl, fr;
+  T G[2], J[2][2], z;
+  Side<T> L, R;
+  T fl, fr;
 };
 
-bool pb_eval(const Fluid& F, double tau, int phl, double rl, double ul, int phr, double rr, double ur,
-             double pls, double prs, PBSys* S) {
+template <class T>
+bool pb_eval(const Fluid& F, const T& tau, int phl, const T& rl, const T& ul, int phr, const T& rr, const T& ur,
+             const T& pls, const T& prs, PBSys<T>* S) {
   const Phase& El = F.ph[phl];
   const Phase& Er = F.ph[phr];
   if (!valid_pressure(El, pls) || !valid_pressure(Er, prs)) return false;
   S->L = side_at(El, pls);
   S->R = side_at(Er, prs);
-  double dzl, dzr;
-  double z = kinetic_z(tau, phl == VAP, S->L, S->R, &dzl, &dzr);
-  double dfl, dfr;
+  T dzl, dzr;
+  T z = kinetic_z(tau, phl == VAP, S->L, S->R, &dzl, &dzr);
+  T dfl, dfr;
   S->fl = wave_f(El, pls, rl, &dfl);
   S->fr = wave_f(Er, prs, rr, &dfr);
-  double jp = prs - pls, jv = S->R.v - S->L.v;
+  T jp = prs - pls, jv = S->R.v - S->L.v;
   S->z = z;
   S->G[0] = jp + z * z * jv;
   S->G[1] = S->fl + S->fr + z * jv + (ur - ul);
@@ -177,11 +230,12 @@ bool pb_eval(const Fluid& F, double tau, int phl, double rl, double ul, int phr,
   S->J[0][1] = 1.0 + 2.0 * z * dzr * jv + z * z * S->R.dv;
   S->J[1][0] = dfl + dzl * jv - z * S->L.dv;
   S->J[1][1] = dfr + dzr * jv + z * S->R.dv;
-  return std::isfinite(S->G[0]) && std::isfinite(S->G[1]);
+  return std::isfinite(val(S->G[0])) && std::isfinite(val(S->G[1]));
 }
 
+template <class T>
 struct PBResult {
-  double pl, pr, rl, rr, ul, ur, z, w, F[2];
+  T pl, pr, rl, rr, ul, ur, z, w, F[2];
   int iters;
   int ok;
 };
@@ -189,7 +243,8 @@ struct PBResult {
 // Initial guess (App. A, Eq. HLLC:2p_nopt): HLLC wave-speed estimates give the boundary speed w and
 // the liquid star density; the liquid EOS gives a star pressure used for both unknowns.
 // Reading: if that pressure is not positive, the vapour side starts at max(p_vapour, 1e-3 p_sat) and
-// the liquid side at its own pressure.
+// the liquid side at its own pressure. (Computed on values: the converged Newton solution does not
+// depend on where it started.)
 void pb_initial_guess(const Fluid& F, int phl, double rl, double ul, int phr, double rr, double ur,
                       double* pl0, double* pr0) {
   const Phase& El = F.ph[phl];
@@ -219,32 +274,34 @@ void pb_initial_guess(const Fluid& F, int phl, double rl, double ul, int phr, do
 // ||G(x + lam d)|| <= (1 - 1e-4 lam) ||G(x)||. Reading: the merit norm is the Euclidean norm of
 // (G1 / (rho_l a_l + rho_r a_r), G2), both in m/s; at most 20 halvings; convergence when the
 // accepted step is below newton_tol relative to max(|p|, p_sat).
-PBResult pb_solve(const Fluid& F, const orc_opts& o, double tau, int phl, double rl, double ml, int phr,
-                  double rr, double mr) {
-  PBResult R;
+template <class T>
+PBResult<T> pb_solve(const Fluid& F, const orc_opts& o, const T& tau, int phl, const T& rl, const T& ml, int phr,
+                     const T& rr, const T& mr) {
+  PBResult<T> R;
   R.ok = 0;
   R.iters = 0;
-  double ul = ml / rl, ur = mr / rr;
-  double imp = rl * F.ph[phl].a + rr * F.ph[phr].a;
-  double x[2];
-  pb_initial_guess(F, phl, rl, ul, phr, rr, ur, &x[0], &x[1]);
-  PBSys S;
+  T ul = ml / rl, ur = mr / rr;
+  double imp = val(rl) * F.ph[phl].a + val(rr) * F.ph[phr].a;
+  double x0, x1;
+  pb_initial_guess(F, phl, val(rl), val(ul), phr, val(rr), val(ur), &x0, &x1);
+  T x[2] = {x0, x1};
+  PBSys<T> S;
   if (!pb_eval(F, tau, phl, rl, ul, phr, rr, ur, x[0], x[1], &S)) return R;
-  double nrm = std::hypot(S.G[0] / imp, S.G[1]);
+  double nrm = std::hypot(val(S.G[0]) / imp, val(S.G[1]));
   bool conv = (nrm == 0.0);
   int it = 0;
   while (!conv && it < o.newton_itmax) {
     ++it;
-    double det = S.J[0][0] * S.J[1][1] - S.J[0][1] * S.J[1][0];
-    if (!(std::isfinite(det)) || det == 0.0) break;
-    double d0 = -(S.J[1][1] * S.G[0] - S.J[0][1] * S.G[1]) / det;
-    double d1 = -(-S.J[1][0] * S.G[0] + S.J[0][0] * S.G[1]) / det;
+    T det = S.J[0][0] * S.J[1][1] - S.J[0][1] * S.J[1][0];
+    if (!(std::isfinite(val(det))) || val(det) == 0.0) break;
+    T d0 = -(S.J[1][1] * S.G[0] - S.J[0][1] * S.G[1]) / det;
+    T d1 = -(-S.J[1][0] * S.G[0] + S.J[0][0] * S.G[1]) / det;
     double lam = 1.0;
     bool acc = false;
-    PBSys T;
+    PBSys<T> Tr;
     for (int ls = 0; ls <= 20; ++ls) {
-      if (pb_eval(F, tau, phl, rl, ul, phr, rr, ur, x[0] + lam * d0, x[1] + lam * d1, &T)) {
-        double nt = std::hypot(T.G[0] / imp, T.G[1]);
+      if (pb_eval(F, tau, phl, rl, ul, phr, rr, ur, T(x[0] + lam * d0), T(x[1] + lam * d1), &Tr)) {
+        double nt = std::hypot(val(Tr.G[0]) / imp, val(Tr.G[1]));
         if (nt <= (1.0 - 1e-4 * lam) * nrm) {
           acc = true;
           nrm = nt;
@@ -253,16 +310,16 @@ PBResult pb_solve(const Fluid& F, const orc_opts& o, double tau, int phl, double
       }
       lam *= 0.5;
     }
-    double s0 = std::fabs(d0) / std::max(std::fabs(x[0]), F.p_sat);
-    double s1 = std::fabs(d1) / std::max(std::fabs(x[1]), F.p_sat);
+    double s0 = std::fabs(val(d0)) / std::max(std::fabs(val(x[0])), F.p_sat);
+    double s1 = std::fabs(val(d1)) / std::max(std::fabs(val(x[1])), F.p_sat);
     if (!acc) {
       // No decrease possible: accept only if the full Newton step is already at round-off level.
       if (std::max(s0, s1) <= 1e-9) conv = true;
       break;
     }
-    x[0] += lam * d0;
-    x[1] += lam * d1;
-    S = T;
+    x[0] = x[0] + lam * d0;
+    x[1] = x[1] + lam * d1;
+    S = Tr;
     if (lam * std::max(s0, s1) <= o.newton_tol || nrm == 0.0) conv = true;
   }
   R.iters = it;
@@ -277,9 +334,9 @@ PBResult pb_solve(const Fluid& F, const orc_opts& o, double tau, int phl, double
   R.ul = ul - S.fl;
   R.ur = ur + S.fr;
   R.z = S.z;
-  double uV = (phl == VAP) ? R.ul : R.ur;
-  double vV = (phl == VAP) ? S.L.v : S.R.v;
-  double pV = (phl == VAP) ? R.pl : R.pr;
+  T uV = (phl == VAP) ? R.ul : R.ur;
+  T vV = (phl == VAP) ? S.L.v : S.R.v;
+  T pV = (phl == VAP) ? R.pl : R.pr;
   R.w = uV + R.z * vV;
   R.F[0] = -R.z;
   R.F[1] = -R.z * uV + pV;
@@ -291,7 +348,7 @@ PBResult pb_solve(const Fluid& F, const orc_opts& o, double tau, int phl, double
 // phi(p) = f(p; W_l) + f(p; W_r) + (u_r - u_l). Two rarefactions give the closed form
 // rho* = sqrt(rho_l rho_r) exp((u_l - u_r) / (2a)), exact when p* <= min(p_l, p_r). Otherwise the
 // root lies in [min(p_l, p_r), p_TR] (a shock curve lies above the rarefaction curve) and is found by
-// bisection to round-off.
+// bisection to round-off. (Used for the creation decision only: values.)
 double nopt_star(const Phase& e, double rl, double ul, double rr, double ur) {
   double pl = pressure(e, rl), pr = pressure(e, rr);
   double pm = std::min(pl, pr);
@@ -316,20 +373,23 @@ double nopt_star(const Phase& e, double rl, double ul, double rr, double ur) {
 // two boundaries each satisfy the momentum jump [[p]] + z^2 [[v]] = 0 with their own z from the
 // kinetic relation, and the velocity chains through both boundaries:
 //   f_P(p_P-; W_l) + f_P(p_P+; W_r) + z1 [[v]]_1 + z2 [[v]]_2 + (u_r - u_l) = 0.
+template <class T>
 struct CreateResult {
-  double pPl, pC, pPr, rhoC, uC, z1, z2, w1, w2, uPl, uPr;
+  T pPl, pC, pPr, rhoC, uC, z1, z2, w1, w2, uPl, uPr;
   int iters;
   int ok;
 };
 
+template <class T>
 struct CrSys {
-  double E[3], J[3][3];
-  Side Pl, C, Pr;
-  double z1, z2, fl, fr;
+  T E[3], J[3][3];
+  Side<T> Pl, C, Pr;
+  T z1, z2, fl, fr;
 };
 
-bool cr_eval(const Fluid& F, double tau, int P, double rl, double ul, double rr, double ur, const double x[3],
-             CrSys* S) {
+template <class T>
+bool cr_eval(const Fluid& F, const T& tau, int P, const T& rl, const T& ul, const T& rr, const T& ur, const T x[3],
+             CrSys<T>* S) {
   int Cph = 1 - P;
   const Phase& EP = F.ph[P];
   const Phase& EC = F.ph[Cph];
@@ -337,15 +397,15 @@ bool cr_eval(const Fluid& F, double tau, int P, double rl, double ul, double rr,
   S->Pl = side_at(EP, x[0]);
   S->C = side_at(EC, x[1]);
   S->Pr = side_at(EP, x[2]);
-  double dz1a, dz1b, dz2a, dz2b;
+  T dz1a, dz1b, dz2a, dz2b;
   // left boundary: parent (left) | created (right); right boundary: created (left) | parent (right)
   S->z1 = kinetic_z(tau, P == VAP, S->Pl, S->C, &dz1a, &dz1b);
   S->z2 = kinetic_z(tau, Cph == VAP, S->C, S->Pr, &dz2a, &dz2b);
-  double dfl, dfr;
+  T dfl, dfr;
   S->fl = wave_f(EP, x[0], rl, &dfl);
   S->fr = wave_f(EP, x[2], rr, &dfr);
-  double jv1 = S->C.v - S->Pl.v, jv2 = S->Pr.v - S->C.v;
-  double z1 = S->z1, z2 = S->z2;
+  T jv1 = S->C.v - S->Pl.v, jv2 = S->Pr.v - S->C.v;
+  T z1 = S->z1, z2 = S->z2;
   S->E[0] = (x[1] - x[0]) + z1 * z1 * jv1;
   S->E[1] = (x[2] - x[1]) + z2 * z2 * jv2;
   S->E[2] = S->fl + S->fr + z1 * jv1 + z2 * jv2 + (ur - ul);
@@ -359,12 +419,13 @@ bool cr_eval(const Fluid& F, double tau, int P, double rl, double ul, double rr,
   S->J[2][0] = dfl + dz1a * jv1 - z1 * S->Pl.dv;
   S->J[2][1] = dz1b * jv1 + z1 * S->C.dv + dz2a * jv2 - z2 * S->C.dv;
   S->J[2][2] = dfr + dz2b * jv2 + z2 * S->Pr.dv;
-  return std::isfinite(S->E[0]) && std::isfinite(S->E[1]) && std::isfinite(S->E[2]);
+  return std::isfinite(val(S->E[0])) && std::isfinite(val(S->E[1])) && std::isfinite(val(S->E[2]));
 }
 
 // Solve a 3x3 linear system by Gaussian elimination with partial pivoting.
-bool solve3(double A[3][3], double b[3], double x[3]) {
-  double M[3][4];
+template <class T>
+bool solve3(T A[3][3], T b[3], T x[3]) {
+  T M[3][4];
   for (int i = 0; i < 3; ++i) {
     for (int j = 0; j < 3; ++j) M[i][j] = A[i][j];
     M[i][3] = b[i];
@@ -372,18 +433,18 @@ bool solve3(double A[3][3], double b[3], double x[3]) {
   for (int c = 0; c < 3; ++c) {
     int p = c;
     for (int r = c + 1; r < 3; ++r)
-      if (std::fabs(M[r][c]) > std::fabs(M[p][c])) p = r;
-    if (M[p][c] == 0.0 || !std::isfinite(M[p][c])) return false;
+      if (std::fabs(val(M[r][c])) > std::fabs(val(M[p][c]))) p = r;
+    if (val(M[p][c]) == 0.0 || !std::isfinite(val(M[p][c]))) return false;
     if (p != c)
       for (int j = 0; j < 4; ++j) std::swap(M[p][j], M[c][j]);
     for (int r = c + 1; r < 3; ++r) {
-      double f = M[r][c] / M[c][c];
-      for (int j = c; j < 4; ++j) M[r][j] -= f * M[c][j];
+      T f = M[r][c] / M[c][c];
+      for (int j = c; j < 4; ++j) M[r][j] = M[r][j] - f * M[c][j];
     }
   }
   for (int i = 2; i >= 0; --i) {
-    double s = M[i][3];
-    for (int j = i + 1; j < 3; ++j) s -= M[i][j] * x[j];
+    T s = M[i][3];
+    for (int j = i + 1; j < 3; ++j) s = s - M[i][j] * x[j];
     x[i] = s / M[i][i];
   }
   return true;
@@ -392,33 +453,35 @@ bool solve3(double A[3][3], double b[3], double x[3]) {
 // Newton-Armijo for the creation system, as for the two-phase boundary. Reading: all three
 // pressures start at the saturation pressure; the merit norm scales the two momentum jumps by the
 // parent impedance rho a.
-CreateResult creation_solve(const Fluid& F, const orc_opts& o, double tau, int P, double rl, double ml, double rr,
-                            double mr) {
-  CreateResult R;
+template <class T>
+CreateResult<T> creation_solve(const Fluid& F, const orc_opts& o, const T& tau, int P, const T& rl, const T& ml,
+                               const T& rr, const T& mr) {
+  CreateResult<T> R;
   R.ok = 0;
   R.iters = 0;
-  double ul = ml / rl, ur = mr / rr;
-  double imp = (rl + rr) * F.ph[P].a;
-  double x[3] = {F.p_sat, F.p_sat, F.p_sat};
-  CrSys S;
+  T ul = ml / rl, ur = mr / rr;
+  double imp = (val(rl) + val(rr)) * F.ph[P].a;
+  T x[3] = {F.p_sat, F.p_sat, F.p_sat};
+  CrSys<T> S;
   if (!cr_eval(F, tau, P, rl, ul, rr, ur, x, &S)) return R;
-  auto norm = [&](const CrSys& s) {
-    return std::sqrt((s.E[0] / imp) * (s.E[0] / imp) + (s.E[1] / imp) * (s.E[1] / imp) + s.E[2] * s.E[2]);
+  auto norm = [&](const CrSys<T>& s) {
+    double e0 = val(s.E[0]), e1 = val(s.E[1]), e2 = val(s.E[2]);
+    return std::sqrt((e0 / imp) * (e0 / imp) + (e1 / imp) * (e1 / imp) + e2 * e2);
   };
   double nrm = norm(S);
   bool conv = (nrm == 0.0);
   int it = 0;
   while (!conv && it < o.newton_itmax) {
     ++it;
-    double b[3] = {-S.E[0], -S.E[1], -S.E[2]}, d[3];
+    T b[3] = {-S.E[0], -S.E[1], -S.E[2]}, d[3];
     if (!solve3(S.J, b, d)) break;
     double lam = 1.0;
     bool acc = false;
-    CrSys T;
+    CrSys<T> Tr;
     for (int ls = 0; ls <= 20; ++ls) {
-      double xt[3] = {x[0] + lam * d[0], x[1] + lam * d[1], x[2] + lam * d[2]};
-      if (cr_eval(F, tau, P, rl, ul, rr, ur, xt, &T)) {
-        double nt = norm(T);
+      T xt[3] = {x[0] + lam * d[0], x[1] + lam * d[1], x[2] + lam * d[2]};
+      if (cr_eval(F, tau, P, rl, ul, rr, ur, xt, &Tr)) {
+        double nt = norm(Tr);
         if (nt <= (1.0 - 1e-4 * lam) * nrm) {
           acc = true;
           nrm = nt;
@@ -428,13 +491,13 @@ CreateResult creation_solve(const Fluid& F, const orc_opts& o, double tau, int P
       lam *= 0.5;
     }
     double s = 0.0;
-    for (int i = 0; i < 3; ++i) s = std::max(s, std::fabs(d[i]) / std::max(std::fabs(x[i]), F.p_sat));
+    for (int i = 0; i < 3; ++i) s = std::max(s, std::fabs(val(d[i])) / std::max(std::fabs(val(x[i])), F.p_sat));
     if (!acc) {
       if (s <= 1e-9) conv = true;
       break;
     }
-    for (int i = 0; i < 3; ++i) x[i] += lam * d[i];
-    S = T;
+    for (int i = 0; i < 3; ++i) x[i] = x[i] + lam * d[i];
+    S = Tr;
     if (lam * s <= o.newton_tol || nrm == 0.0) conv = true;
   }
   R.iters = it;
@@ -450,53 +513,55 @@ CreateResult creation_solve(const Fluid& F, const orc_opts& o, double tau, int P
   R.uC = R.uPl - S.z1 * (S.C.v - S.Pl.v);  // velocity jump across the left boundary: [[u]] = -z [[v]]
   R.w1 = R.uC + S.z1 * S.C.v;              // z = -rho (u - w) on the created side
   R.w2 = R.uC + S.z2 * S.C.v;
-  R.ok = (R.w2 > R.w1) ? 1 : 0;
+  R.ok = (val(R.w2) > val(R.w1)) ? 1 : 0;
   return R;
 }
 
 // ---------------------------------------------------------------- moving grid (Sec. 2.3, Sec. 3.4)
 
+template <class T>
 struct Face {
   int pb;     // 1: phase boundary (moves with w); 0: fixed face on the background lattice
   long j;     // lattice index of a fixed face (position x_left + j h)
-  double x;   // position of a phase boundary
+  T x;        // position of a phase boundary
 };
 
+template <class T>
 struct Inst {
   long N = 0;
-  double xL = 0, xR = 0, h = 0, tau = 0;
-  std::vector<Face> f;                  // M + 1 faces
-  std::vector<double> w, r, m;          // M cells: width, rho, rho u
+  double xL = 0, xR = 0, h = 0;
+  T tau = 0.0;
+  std::vector<Face<T>> f;               // M + 1 faces
+  std::vector<T> w, r, m;               // M cells: width, rho, rho u
   std::vector<int> ph;                  // M cells: phase label
-  double t = 0;
+  T t = 0.0;
   int status = 0;
   long long steps = 0, dts_iters = 0, dts_max = 0, newton = 0, merges = 0, splits = 0, creations = 0,
             maxiter = 0, pb_solves = 0;
   double last_implicit_res = 0;
   int M() const { return (int)r.size(); }
-  double face_x(int i) const { return f[i].pb ? f[i].x : xL + (double)f[i].j * h; }
+  T face_x(int i) const { return f[i].pb ? f[i].x : T(xL + (double)f[i].j * h); }
 };
 
-struct Ctx {
-  Fluid F;
-  orc_opts o;
-  std::vector<Inst> inst;
-};
+struct Ctx;
 
 double sound(const Fluid& F, int ph) { return F.ph[ph].a; }
 
-bool finite_state(const Inst& I) {
+template <class T>
+bool finite_state(const Inst<T>& I) {
   for (int i = 0; i < I.M(); ++i)
-    if (!(I.r[i] > 0.0) || !std::isfinite(I.r[i]) || !std::isfinite(I.m[i]) || !(I.w[i] > 0.0)) return false;
+    if (!(val(I.r[i]) > 0.0) || !std::isfinite(val(I.r[i])) || !std::isfinite(val(I.m[i])) || !(val(I.w[i]) > 0.0))
+      return false;
   return true;
 }
 
 // Merge cell i with its neighbour nb (same phase, shared fixed face): conservative average.
-void merge_cells(Inst& I, int i, int nb) {
+template <class T>
+void merge_cells(Inst<T>& I, int i, int nb) {
   int a = std::min(i, nb), b = std::max(i, nb);
-  double wm = I.w[a] + I.w[b];
-  double rm = (I.w[a] * I.r[a] + I.w[b] * I.r[b]) / wm;
-  double mm = (I.w[a] * I.m[a] + I.w[b] * I.m[b]) / wm;
+  T wm = I.w[a] + I.w[b];
+  T rm = (I.w[a] * I.r[a] + I.w[b] * I.r[b]) / wm;
+  T mm = (I.w[a] * I.m[a] + I.w[b] * I.m[b]) / wm;
   I.w[a] = wm;
   I.r[a] = rm;
   I.m[a] = mm;
@@ -509,8 +574,10 @@ void merge_cells(Inst& I, int i, int nb) {
 }
 
 // Solve the phase-boundary problem at face g between cells g-1 and g of the given states.
-PBResult solve_face(Ctx& C, Inst& I, int phl, double rl, double ml, int phr, double rr, double mr) {
-  PBResult R = pb_solve(C.F, C.o, I.tau, phl, rl, ml, phr, rr, mr);
+template <class T>
+PBResult<T> solve_face(const Fluid& F, const orc_opts& o, Inst<T>& I, int phl, const T& rl, const T& ml, int phr,
+                       const T& rr, const T& mr) {
+  PBResult<T> R = pb_solve(F, o, I.tau, phl, rl, ml, phr, rr, mr);
   I.pb_solves++;
   I.newton += R.iters;
   return R;
@@ -518,16 +585,17 @@ PBResult solve_face(Ctx& C, Inst& I, int phl, double rl, double ml, int phr, dou
 
 // Flux of the dual-time loop / Part 2 at an interior face g of a block, given the block states
 // W (indexed by cell). Returns the face speed (0 for a fixed face).
-bool block_face_flux(Ctx& C, Inst& I, int g, const std::vector<double>& Wr, const std::vector<double>& Wm,
-                     double F[2], double* wface) {
+template <class T>
+bool block_face_flux(const Fluid& Fl, const orc_opts& o, Inst<T>& I, int g, const std::vector<T>& Wr,
+                     const std::vector<T>& Wm, T F[2], T* wface) {
   if (I.f[g].pb) {
-    PBResult R = solve_face(C, I, I.ph[g - 1], Wr[g - 1], Wm[g - 1], I.ph[g], Wr[g], Wm[g]);
+    PBResult<T> R = solve_face(Fl, o, I, I.ph[g - 1], Wr[g - 1], Wm[g - 1], I.ph[g], Wr[g], Wm[g]);
     if (!R.ok) return false;
     F[0] = R.F[0];
     F[1] = R.F[1];
     *wface = R.w;
   } else {
-    hll(C.F.ph[I.ph[g]], Wr[g - 1], Wm[g - 1], Wr[g], Wm[g], F);
+    hll(Fl.ph[I.ph[g]], Wr[g - 1], Wm[g - 1], Wr[g], Wm[g], F);
     *wface = 0.0;
   }
   return true;
@@ -536,30 +604,29 @@ bool block_face_flux(Ctx& C, Inst& I, int g, const std::vector<double>& Wr, cons
 // One time step of Algorithm 1 with the dual-time stepping of Algorithm 2 on every block,
 // including the moving-grid width updates (Eq. godunov_meth:nonunif) and grid management.
 // t_end > 0 clips the step to land on t_end.
-void step_instance(Ctx& C, Inst& I, double t_end) {
+template <class T>
+void step_instance(const Fluid& F, const orc_opts& o, Inst<T>& I, double t_end) {
   if (I.status != ORC_OK) return;
-  const Fluid& F = C.F;
-  const orc_opts& o = C.o;
   // (1) time step from the CFL condition, Eq. cfl_cond:unif, with the regular width h.
   //     Reading: S_max is taken over all cells, the width is always the background h.
-  double S = 0.0;
-  for (int i = 0; i < I.M(); ++i) S = std::max(S, std::fabs(I.m[i] / I.r[i]) + sound(F, I.ph[i]));
-  double dt = o.cfl * I.h / S;
+  T S = 0.0;
+  for (int i = 0; i < I.M(); ++i) S = tmax(S, T(tfabs(T(I.m[i] / I.r[i])) + sound(F, I.ph[i])));
+  T dt = o.cfl * I.h / S;
   bool clipped = false;
-  if (t_end > 0.0 && t_end - I.t <= dt) {
+  if (t_end > 0.0 && val(t_end - I.t) <= val(dt)) {
     dt = t_end - I.t;
     clipped = true;
   }
   // (2) Grid management before the step (Sec. 2.3, Sec. 3.4): phase-boundary speeds at U^n predict
   //     the widths; a cell next to a phase boundary that would fall below max(alpha_min h, h_i/2)
   //     is merged with its neighbour across its fixed face (possible only within one phase).
-  std::vector<double> hpred;  // predicted widths at t^{n+1} after the merges (Sec. 3.1: the model mesh is the mesh at t^{n+1})
+  std::vector<T> hpred;  // predicted widths at t^{n+1} after the merges (Sec. 3.1: the model mesh is the mesh at t^{n+1})
   {
     int M = I.M();
-    std::vector<double> wf(M + 1, 0.0);
+    std::vector<T> wf(M + 1, T(0.0));
     for (int g = 1; g < M; ++g) {
       if (!I.f[g].pb) continue;
-      PBResult R = solve_face(C, I, I.ph[g - 1], I.r[g - 1], I.m[g - 1], I.ph[g], I.r[g], I.m[g]);
+      PBResult<T> R = solve_face(F, o, I, I.ph[g - 1], I.r[g - 1], I.m[g - 1], I.ph[g], I.r[g], I.m[g]);
       if (!R.ok) {
         I.status = ORC_ERR_PB_NOCONV;
         return;
@@ -569,8 +636,8 @@ void step_instance(Ctx& C, Inst& I, double t_end) {
     std::vector<int> mark(M, 0);
     for (int i = 0; i < M; ++i) {
       if (!(I.f[i].pb || I.f[i + 1].pb)) continue;
-      double hp = I.w[i] + (wf[i + 1] - wf[i]) * dt;
-      if (hp < std::max(o.alpha_min * I.h, 0.5 * I.w[i])) mark[i] = 1;
+      T hp = I.w[i] + (wf[i + 1] - wf[i]) * dt;
+      if (val(hp) < std::max(o.alpha_min * I.h, 0.5 * val(I.w[i]))) mark[i] = 1;
     }
     for (int i = 0; i < I.M(); ++i) {
       if (!mark[i]) continue;
@@ -595,10 +662,10 @@ void step_instance(Ctx& C, Inst& I, double t_end) {
   {
     // predicted widths on the merged grid: boundary speeds from U^n of the (possibly merged) cells
     hpred.assign(I.w.begin(), I.w.end());
-    std::vector<double> wf(M + 1, 0.0);
+    std::vector<T> wf(M + 1, T(0.0));
     for (int g = 1; g < M; ++g) {
       if (!I.f[g].pb) continue;
-      PBResult R = solve_face(C, I, I.ph[g - 1], I.r[g - 1], I.m[g - 1], I.ph[g], I.r[g], I.m[g]);
+      PBResult<T> R = solve_face(F, o, I, I.ph[g - 1], I.r[g - 1], I.m[g - 1], I.ph[g], I.r[g], I.m[g]);
       if (!R.ok) {
         I.status = ORC_ERR_PB_NOCONV;
         return;
@@ -613,7 +680,7 @@ void step_instance(Ctx& C, Inst& I, double t_end) {
   std::vector<std::pair<int, int>> blocks;
   for (int g = 1; g < M; ++g) {
     if (!I.f[g].pb) continue;
-    int k = (I.w[g - 1] < I.w[g]) ? g - 1 : g;
+    int k = (val(I.w[g - 1]) < val(I.w[g])) ? g - 1 : g;
     tiny[k] = 1;
     int lo = std::max(k - 1, 0), hi = std::min(k + 1, M - 1);
     if (!blocks.empty() && lo <= blocks.back().second)
@@ -625,18 +692,19 @@ void step_instance(Ctx& C, Inst& I, double t_end) {
     for (int i = blocks[b].first; i <= blocks[b].second; ++i) blk[i] = (int)b;
   // (4) Phase creation (App. B) at same-phase faces between two explicit cells.
   std::vector<int> create(M + 1, 0);
-  std::vector<CreateResult> cres(M + 1);
+  std::vector<CreateResult<T>> cres(M + 1);
   if (o.creation) {
     std::vector<int> det(M + 1, 0);
     for (int g = 1; g < M; ++g) {
       if (I.f[g].pb || blk[g - 1] >= 0 || blk[g] >= 0) continue;
       int P = I.ph[g];
-      double ps = nopt_star(F.ph[P], I.r[g - 1], I.m[g - 1] / I.r[g - 1], I.r[g], I.m[g] / I.r[g]);
+      double ps = nopt_star(F.ph[P], val(I.r[g - 1]), val(I.m[g - 1] / I.r[g - 1]), val(I.r[g]),
+                            val(I.m[g] / I.r[g]));
       det[g] = (P == LIQ) ? (ps < F.p_min) : (ps > F.p_tilde);
     }
     for (int g = 1; g < M; ++g) {
       if (!det[g] || det[g - 1]) continue;
-      CreateResult R = creation_solve(F, o, I.tau, I.ph[g], I.r[g - 1], I.m[g - 1], I.r[g], I.m[g]);
+      CreateResult<T> R = creation_solve(F, o, I.tau, I.ph[g], I.r[g - 1], I.m[g - 1], I.r[g], I.m[g]);
       I.newton += R.iters;
       if (!R.ok) {
         I.status = ORC_ERR_PB_NOCONV;
@@ -649,10 +717,10 @@ void step_instance(Ctx& C, Inst& I, double t_end) {
   // (5) Algorithm 1, Step 1: fluxes from U^n at every face that is not inside a block, and the
   //     explicit update of every cell outside the blocks. Fl[g]/Fr[g] are the fluxes seen by the cell
   //     left/right of face g (they differ only at a creation face, Eq. flux:cavitation/nucleation).
-  std::vector<double> Fl0(M + 1, 0.0), Fl1(M + 1, 0.0), Fr0(M + 1, 0.0), Fr1(M + 1, 0.0);
-  std::vector<double> wl(M + 1, 0.0), wr(M + 1, 0.0);  // speed of face g seen from left/right cell
+  std::vector<T> Fl0(M + 1, T(0.0)), Fl1(M + 1, T(0.0)), Fr0(M + 1, T(0.0)), Fr1(M + 1, T(0.0));
+  std::vector<T> wl(M + 1, T(0.0)), wr(M + 1, T(0.0));  // speed of face g seen from left/right cell
   for (int g = 0; g <= M; ++g) {
-    double Fx[2];
+    T Fx[2];
     if (g == 0) {
       phys_flux(F.ph[I.ph[0]], I.r[0], I.m[0], Fx);  // transmissive boundary (Reading: ghost = cell)
     } else if (g == M) {
@@ -660,7 +728,7 @@ void step_instance(Ctx& C, Inst& I, double t_end) {
     } else if (blk[g - 1] >= 0 && blk[g - 1] == blk[g]) {
       continue;  // interior face of a block: computed in Algorithm 2
     } else if (create[g]) {
-      const CreateResult& R = cres[g];
+      const CreateResult<T>& R = cres[g];
       // Eq. flux:cavitation / flux:nucleation with each boundary's own mass flux
       Fl0[g] = -R.z1;
       Fl1[g] = -R.z1 * R.uC + R.pC;
@@ -675,31 +743,31 @@ void step_instance(Ctx& C, Inst& I, double t_end) {
     Fl0[g] = Fr0[g] = Fx[0];
     Fl1[g] = Fr1[g] = Fx[1];
   }
-  std::vector<double> rn = I.r, mn = I.m, wn = I.w;  // U^n and h^n
+  std::vector<T> rn = I.r, mn = I.m, wn = I.w;  // U^n and h^n
   for (int i = 0; i < M; ++i) {
     if (blk[i] >= 0) continue;
-    double hnp1 = wn[i] + (wl[i + 1] - wr[i]) * dt;
+    T hnp1 = wn[i] + (wl[i + 1] - wr[i]) * dt;
     I.r[i] = (wn[i] * rn[i] - dt * (Fl0[i + 1] - Fr0[i])) / hnp1;
     I.m[i] = (wn[i] * mn[i] - dt * (Fl1[i + 1] - Fr1[i])) / hnp1;
     I.w[i] = hnp1;
   }
   // (6) Algorithm 1, Step 2 = Algorithm 2 on each block, with the local pseudo time steps of
   //     Eq. dual time tau diff and the width iterates of Sec. 3.4.
-  std::vector<double> xpb_new(M + 1, 0.0);
+  std::vector<T> xpb_new(M + 1, T(0.0));
   std::vector<int> pb_moved(M + 1, 0);
   double worst_defect = 0.0;
   for (size_t b = 0; b < blocks.size(); ++b) {
     int lo = blocks[b].first, hi = blocks[b].second;
-    double FL[2] = {Fr0[lo], Fr1[lo]};        // F_left  = flux at face lo from U^n
-    double FR[2] = {Fl0[hi + 1], Fl1[hi + 1]}; // F_right = flux at face hi+1 from U^n
-    std::vector<double> Wr = rn, Wm = mn;      // dual-time iterate, indexed like the cells
-    std::vector<double> theta(M, 0.0);
+    T FL[2] = {Fr0[lo], Fr1[lo]};        // F_left  = flux at face lo from U^n
+    T FR[2] = {Fl0[hi + 1], Fl1[hi + 1]}; // F_right = flux at face hi+1 from U^n
+    std::vector<T> Wr = rn, Wm = mn;      // dual-time iterate, indexed like the cells
+    std::vector<T> theta(M, T(0.0));
     // Delta tau_i = theta_i dt with theta_i <= h_i/h for stability (Sec. 3.3). Reading: the widths are
     // those of the mesh at t^{n+1} (Sec. 3.1 treats the model mesh as the mesh at t^{n+1}), predicted
     // with the boundary speeds at U^n.
-    for (int i = lo; i <= hi; ++i) theta[i] = std::min(o.theta_nb, hpred[i] / I.h);
-    std::vector<double> Fc0(M + 1), Fc1(M + 1), wc(M + 1, 0.0), hl(M);
-    auto fluxes = [&](const std::vector<double>& Ar, const std::vector<double>& Am) -> bool {
+    for (int i = lo; i <= hi; ++i) theta[i] = tmin(T(o.theta_nb), T(hpred[i] / I.h));
+    std::vector<T> Fc0(M + 1), Fc1(M + 1), wc(M + 1, T(0.0)), hl(M);
+    auto fluxes = [&](const std::vector<T>& Ar, const std::vector<T>& Am) -> bool {
       Fc0[lo] = FL[0];
       Fc1[lo] = FL[1];
       Fc0[hi + 1] = FR[0];
@@ -707,15 +775,15 @@ void step_instance(Ctx& C, Inst& I, double t_end) {
       wc[lo] = 0.0;
       wc[hi + 1] = 0.0;
       for (int g = lo + 1; g <= hi; ++g) {
-        double Fx[2], wx;
-        if (!block_face_flux(C, I, g, Ar, Am, Fx, &wx)) return false;
+        T Fx[2], wx;
+        if (!block_face_flux(F, o, I, g, Ar, Am, Fx, &wx)) return false;
         Fc0[g] = Fx[0];
         Fc1[g] = Fx[1];
         wc[g] = wx;
       }
       for (int i = lo; i <= hi; ++i) hl[i] = wn[i] + (wc[i + 1] - wc[i]) * dt;
       for (int i = lo; i <= hi; ++i)
-        if (!(hl[i] > 0.0)) return false;
+        if (!(val(hl[i]) > 0.0)) return false;
       return true;
     };
     int l = 0;
@@ -727,19 +795,20 @@ void step_instance(Ctx& C, Inst& I, double t_end) {
         return;
       }
       double res_nb = 0.0, res_k = 0.0;
-      std::vector<double> Nr = Wr, Nm = Wm;
+      std::vector<T> Nr = Wr, Nm = Wm;
       for (int i = lo; i <= hi; ++i) {
-        double th = theta[i];
-        double tr = wn[i] / hl[i] * rn[i] - dt / hl[i] * (Fc0[i + 1] - Fc0[i]);
-        double tm = wn[i] / hl[i] * mn[i] - dt / hl[i] * (Fc1[i + 1] - Fc1[i]);
+        T th = theta[i];
+        T tr = wn[i] / hl[i] * rn[i] - dt / hl[i] * (Fc0[i + 1] - Fc0[i]);
+        T tm = wn[i] / hl[i] * mn[i] - dt / hl[i] * (Fc1[i + 1] - Fc1[i]);
         Nr[i] = (Wr[i] + th * tr) / (1.0 + th);
         Nm[i] = (Wm[i] + th * tm) / (1.0 + th);
         // residual of Sec. 4: ||(1 + dtau/dt)(W^{l+1} - W^l) / (dtau max(|W^l|, 1))||_inf
-        double dtau = th * dt;
-        double e0 = (1.0 + th) * std::fabs(Nr[i] - Wr[i]) / (dtau * std::max(std::fabs(Wr[i]), 1.0));
-        double e1 = (1.0 + th) * std::fabs(Nm[i] - Wm[i]) / (dtau * std::max(std::fabs(Wm[i]), 1.0));
+        double thv = val(th), dtv = val(dt);
+        double dtau = thv * dtv;
+        double e0 = (1.0 + thv) * std::fabs(val(Nr[i]) - val(Wr[i])) / (dtau * std::max(std::fabs(val(Wr[i])), 1.0));
+        double e1 = (1.0 + thv) * std::fabs(val(Nm[i]) - val(Wm[i])) / (dtau * std::max(std::fabs(val(Wm[i])), 1.0));
         double res = std::max(e0, e1);
-        if (o.res_mode == 1) res *= dt;
+        if (o.res_mode == 1) res *= dtv;
         if (tiny[i])
           res_k = std::max(res_k, res);
         else
@@ -760,10 +829,10 @@ void step_instance(Ctx& C, Inst& I, double t_end) {
     }
     for (int i = lo; i <= hi; ++i) {
       // fixed-point defect of the implicit system at U^{n,*} (diagnostic)
-      double gr = (wn[i] * rn[i] - dt * (Fc0[i + 1] - Fc0[i])) / hl[i];
-      double gm = (wn[i] * mn[i] - dt * (Fc1[i + 1] - Fc1[i])) / hl[i];
-      worst_defect = std::max(worst_defect, std::fabs(gr - Wr[i]) / std::max(std::fabs(Wr[i]), 1.0));
-      worst_defect = std::max(worst_defect, std::fabs(gm - Wm[i]) / std::max(std::fabs(Wm[i]), 1.0));
+      T gr = (wn[i] * rn[i] - dt * (Fc0[i + 1] - Fc0[i])) / hl[i];
+      T gm = (wn[i] * mn[i] - dt * (Fc1[i + 1] - Fc1[i])) / hl[i];
+      worst_defect = std::max(worst_defect, std::fabs(val(gr) - val(Wr[i])) / std::max(std::fabs(val(Wr[i])), 1.0));
+      worst_defect = std::max(worst_defect, std::fabs(val(gm) - val(Wm[i])) / std::max(std::fabs(val(Wm[i])), 1.0));
       I.r[i] = gr;
       I.m[i] = gm;
       I.w[i] = hl[i];
@@ -780,9 +849,9 @@ void step_instance(Ctx& C, Inst& I, double t_end) {
   // (7) Insert created cells (App. B): width (w_right - w_left) dt between the two new boundaries.
   for (int g = M - 1; g >= 1; --g) {
     if (!create[g]) continue;
-    const CreateResult& R = cres[g];
-    double xg = I.face_x(g);
-    Face f1{1, 0, xg + R.w1 * dt}, f2{1, 0, xg + R.w2 * dt};
+    const CreateResult<T>& R = cres[g];
+    T xg = I.face_x(g);
+    Face<T> f1{1, 0, xg + R.w1 * dt}, f2{1, 0, xg + R.w2 * dt};
     I.f[g] = f1;
     I.f.insert(I.f.begin() + g + 1, f2);
     I.w.insert(I.w.begin() + g, (R.w2 - R.w1) * dt);
@@ -797,8 +866,8 @@ void step_instance(Ctx& C, Inst& I, double t_end) {
   //     boundaries is cut at the lattice face nearest its midpoint. Both parts keep the state.
   for (int i = 0; i < I.M(); ++i) {
     bool lpb = I.f[i].pb, rpb = I.f[i + 1].pb;
-    if (!(lpb || rpb) || !(I.w[i] > o.split_ratio * I.h)) continue;
-    double w1, w2;
+    if (!(lpb || rpb) || !(val(I.w[i]) > o.split_ratio * I.h)) continue;
+    T w1, w2;
     long jc;
     if (!lpb) {
       jc = I.f[i].j + 1;
@@ -809,13 +878,13 @@ void step_instance(Ctx& C, Inst& I, double t_end) {
       w2 = I.h;
       w1 = I.w[i] - I.h;
     } else {
-      double xm = 0.5 * (I.f[i].x + I.f[i + 1].x);
+      double xm = 0.5 * (val(I.f[i].x) + val(I.f[i + 1].x));
       jc = std::lround((xm - I.xL) / I.h);
       w1 = (I.xL + (double)jc * I.h) - I.f[i].x;
       w2 = I.w[i] - w1;
-      if (!(w1 > 0.0) || !(w2 > 0.0)) continue;
+      if (!(val(w1) > 0.0) || !(val(w2) > 0.0)) continue;
     }
-    Face fc{0, jc, 0.0};
+    Face<T> fc{0, jc, T(0.0)};
     I.f.insert(I.f.begin() + i + 1, fc);
     I.w[i] = w1;
     I.w.insert(I.w.begin() + i + 1, w2);
@@ -825,7 +894,7 @@ void step_instance(Ctx& C, Inst& I, double t_end) {
     I.splits++;
     ++i;  // the new cell is not examined again in this step
   }
-  I.t = clipped ? t_end : I.t + dt;
+  I.t = clipped ? T(t_end) : T(I.t + dt);
   I.steps++;
   if (!finite_state(I)) I.status = ORC_ERR_NONPHYSICAL;
 }
@@ -833,9 +902,8 @@ void step_instance(Ctx& C, Inst& I, double t_end) {
 // Fully explicit moving-grid scheme used as a brute-force reference: every cell, including the
 // phase-boundary cells, is updated by Eq. godunov_meth:nonunif with fluxes from U^n, and the time
 // step obeys the CFL condition of the smallest cell.
-void explicit_step(Ctx& C, Inst& I, double t_end) {
+void explicit_step(const Fluid& F, const orc_opts& o, Inst<double>& I, double t_end) {
   if (I.status != ORC_OK) return;
-  const Fluid& F = C.F;
   int M = I.M();
   double S = 0.0, hmin = I.h;
   for (int i = 0; i < M; ++i) {
@@ -843,11 +911,11 @@ void explicit_step(Ctx& C, Inst& I, double t_end) {
     hmin = std::min(hmin, I.w[i]);
   }
   // A cell shrinking towards zero would drive this step to zero: stop the instance instead.
-  if (hmin < C.o.alpha_min * I.h) {
+  if (hmin < o.alpha_min * I.h) {
     I.status = ORC_ERR_VANISH;
     return;
   }
-  double dt = C.o.cfl * hmin / S;
+  double dt = o.cfl * hmin / S;
   bool clipped = false;
   if (t_end - I.t <= dt) {
     dt = t_end - I.t;
@@ -861,7 +929,7 @@ void explicit_step(Ctx& C, Inst& I, double t_end) {
     else if (g == M)
       phys_flux(F.ph[I.ph[M - 1]], I.r[M - 1], I.m[M - 1], Fx);
     else if (I.f[g].pb) {
-      PBResult R = solve_face(C, I, I.ph[g - 1], I.r[g - 1], I.m[g - 1], I.ph[g], I.r[g], I.m[g]);
+      PBResult<double> R = solve_face(F, o, I, I.ph[g - 1], I.r[g - 1], I.m[g - 1], I.ph[g], I.r[g], I.m[g]);
       if (!R.ok) {
         I.status = ORC_ERR_PB_NOCONV;
         return;
@@ -890,6 +958,16 @@ void explicit_step(Ctx& C, Inst& I, double t_end) {
   I.steps++;
   if (!finite_state(I)) I.status = ORC_ERR_NONPHYSICAL;
 }
+
+struct Ctx {
+  Fluid F;
+  orc_opts o;
+  std::vector<Inst<double>> inst;
+  // tangent-linear results of the last orc_tangent call: per instance, per direction, the final
+  // (width, rho, m) derivatives of every cell
+  std::vector<std::vector<double>> tan_w, tan_r, tan_m;
+  int tan_dirs = 0;
+};
 
 template <class Fn>
 void parallel_for(int n, int n_threads, Fn fn) {
@@ -939,7 +1017,7 @@ void orc_hll(const orc_fluid* fl, int ph, double rl, double ml, double rr, doubl
 void orc_pb_system(const orc_fluid* fl, double tau, int phl, double rl, double ul, int phr, double rr, double ur,
                    double pls, double prs, double out[7]) {
   Fluid Fd = make_fluid(fl);
-  PBSys S;
+  PBSys<double> S;
   bool ok = pb_eval(Fd, tau, phl, rl, ul, phr, rr, ur, pls, prs, &S);
   if (!ok) {
     for (int i = 0; i < 7; ++i) out[i] = NAN;
@@ -957,7 +1035,7 @@ void orc_pb_system(const orc_fluid* fl, double tau, int phl, double rl, double u
 int orc_pb_solve(const orc_fluid* fl, const orc_opts* o, double tau, int phl, double rl, double ul, int phr,
                  double rr, double ur, double out[11]) {
   Fluid Fd = make_fluid(fl);
-  PBResult R = pb_solve(Fd, *o, tau, phl, rl, rl * ul, phr, rr, rr * ur);
+  PBResult<double> R = pb_solve(Fd, *o, tau, phl, rl, rl * ul, phr, rr, rr * ur);
   out[10] = R.iters;
   if (!R.ok) return ORC_ERR_PB_NOCONV;
   double v[10] = {R.pl, R.pr, R.rl, R.rr, R.ul, R.ur, R.z, R.w, R.F[0], R.F[1]};
@@ -973,7 +1051,7 @@ double orc_nopt_star(const orc_fluid* fl, int ph, double rl, double ul, double r
 int orc_creation_solve(const orc_fluid* fl, const orc_opts* o, double tau, int ph, double rl, double ul, double rr,
                        double ur, double out[12]) {
   Fluid Fd = make_fluid(fl);
-  CreateResult R = creation_solve(Fd, *o, tau, ph, rl, rl * ul, rr, rr * ur);
+  CreateResult<double> R = creation_solve(Fd, *o, tau, ph, rl, rl * ul, rr, rr * ur);
   out[11] = R.iters;
   if (!R.ok) return ORC_ERR_PB_NOCONV;
   double v[11] = {R.pPl, R.pC, R.pPr, R.rhoC, R.uC, R.z1, R.z2, R.w1, R.w2, R.uPl, R.uPr};
@@ -984,7 +1062,7 @@ int orc_creation_solve(const orc_fluid* fl, const orc_opts* o, double tau, int p
 int orc_exact_sample(const orc_fluid* fl, const orc_opts* o, double tau, int phl, double rl, double ul, int phr,
                      double rr, double ur, int n, const double* xi, double* rho, double* u, int* ph) {
   Fluid Fd = make_fluid(fl);
-  PBResult R = pb_solve(Fd, *o, tau, phl, rl, rl * ul, phr, rr, rr * ur);
+  PBResult<double> R = pb_solve(Fd, *o, tau, phl, rl, rl * ul, phr, rr, rr * ur);
   if (!R.ok) return ORC_ERR_PB_NOCONV;
   const Phase& El = Fd.ph[phl];
   const Phase& Er = Fd.ph[phr];
@@ -1057,7 +1135,7 @@ void* orc_create(int n_inst, const int* n_lattice, const double* x_left, const d
     orc_default_opts(&C->o);
   C->inst.resize(n_inst);
   for (int i = 0; i < n_inst; ++i) {
-    Inst& I = C->inst[i];
+    Inst<double>& I = C->inst[i];
     I.N = n_lattice[i];
     I.xL = x_left[i];
     I.xR = x_right[i];
@@ -1074,10 +1152,10 @@ int orc_set_states(void* H, const int* off, const double* widths, const double* 
   Ctx* C = (Ctx*)H;
   int rc = ORC_OK;
   for (size_t k = 0; k < C->inst.size(); ++k) {
-    Inst& I = C->inst[k];
+    Inst<double>& I = C->inst[k];
     int a = off[k], b = off[k + 1];
     int M = b - a;
-    I.f.assign(M + 1, Face{0, 0, 0.0});
+    I.f.assign(M + 1, Face<double>{0, 0, 0.0});
     I.w.assign(widths + a, widths + b);
     I.r.assign(rho + a, rho + b);
     I.m.assign(m + a, m + b);
@@ -1090,11 +1168,11 @@ int orc_set_states(void* H, const int* off, const double* widths, const double* 
     // a face between cells of one phase must land on a lattice face (to 1e-9 h).
     long jfix = 0;
     double part = 0.0;
-    I.f[0] = Face{0, 0, 0.0};
+    I.f[0] = Face<double>{0, 0, 0.0};
     for (int i = 0; i < M; ++i) {
       part += I.w[i];
       if (i + 1 < M && I.ph[i + 1] != I.ph[i]) {
-        I.f[i + 1] = Face{1, 0, I.xL + (double)jfix * I.h + part};
+        I.f[i + 1] = Face<double>{1, 0, I.xL + (double)jfix * I.h + part};
       } else {
         double units = part / I.h;
         long j = jfix + std::lround(units);
@@ -1102,7 +1180,7 @@ int orc_set_states(void* H, const int* off, const double* widths, const double* 
           I.status = ORC_ERR_ARG;
           rc = ORC_ERR_ARG;
         }
-        I.f[i + 1] = Face{0, j, 0.0};
+        I.f[i + 1] = Face<double>{0, j, 0.0};
         jfix = j;
         part = 0.0;
       }
@@ -1129,7 +1207,7 @@ int orc_get_states(void* H, int* off, double* widths, double* rho, double* m, un
   Ctx* C = (Ctx*)H;
   int o = 0;
   for (size_t k = 0; k < C->inst.size(); ++k) {
-    const Inst& I = C->inst[k];
+    const Inst<double>& I = C->inst[k];
     off[k] = o;
     for (int i = 0; i < I.M(); ++i, ++o) {
       widths[o] = I.w[i];
@@ -1148,7 +1226,7 @@ int orc_get_pbs(void* H, int* off, double* x) {
   Ctx* C = (Ctx*)H;
   int o = 0;
   for (size_t k = 0; k < C->inst.size(); ++k) {
-    const Inst& I = C->inst[k];
+    const Inst<double>& I = C->inst[k];
     off[k] = o;
     for (int g = 1; g < I.M(); ++g)
       if (I.f[g].pb) x[o++] = I.f[g].x;
@@ -1160,7 +1238,7 @@ int orc_get_pbs(void* H, int* off, double* x) {
 int orc_get_stats(void* H, long long* s) {
   Ctx* C = (Ctx*)H;
   for (size_t k = 0; k < C->inst.size(); ++k) {
-    const Inst& I = C->inst[k];
+    const Inst<double>& I = C->inst[k];
     long long v[10] = {I.steps, I.dts_iters, I.dts_max, I.newton, I.merges, I.splits, I.creations, I.maxiter,
                        I.pb_solves, 0};
     for (int j = 0; j < 10; ++j) s[10 * k + j] = v[j];
@@ -1171,8 +1249,8 @@ int orc_get_stats(void* H, long long* s) {
 int orc_run_to(void* H, double t_end, int n_threads) {
   Ctx* C = (Ctx*)H;
   parallel_for((int)C->inst.size(), n_threads, [&](int k) {
-    Inst& I = C->inst[k];
-    while (I.status == ORC_OK && I.t < t_end) step_instance(*C, I, t_end);
+    Inst<double>& I = C->inst[k];
+    while (I.status == ORC_OK && I.t < t_end) step_instance(C->F, C->o, I, t_end);
   });
   return ORC_OK;
 }
@@ -1180,8 +1258,8 @@ int orc_run_to(void* H, double t_end, int n_threads) {
 int orc_step(void* H, int n_steps, int n_threads) {
   Ctx* C = (Ctx*)H;
   parallel_for((int)C->inst.size(), n_threads, [&](int k) {
-    Inst& I = C->inst[k];
-    for (int s = 0; s < n_steps && I.status == ORC_OK; ++s) step_instance(*C, I, -1.0);
+    Inst<double>& I = C->inst[k];
+    for (int s = 0; s < n_steps && I.status == ORC_OK; ++s) step_instance(C->F, C->o, I, -1.0);
   });
   return ORC_OK;
 }
@@ -1189,12 +1267,136 @@ int orc_step(void* H, int n_steps, int n_threads) {
 int orc_explicit_run_to(void* H, double t_end, int n_threads) {
   Ctx* C = (Ctx*)H;
   parallel_for((int)C->inst.size(), n_threads, [&](int k) {
-    Inst& I = C->inst[k];
-    while (I.status == ORC_OK && I.t < t_end) explicit_step(*C, I, t_end);
+    Inst<double>& I = C->inst[k];
+    while (I.status == ORC_OK && I.t < t_end) explicit_step(C->F, C->o, I, t_end);
   });
   return ORC_OK;
 }
 
 double orc_last_implicit_residual(void* H, int inst) { return ((Ctx*)H)->inst[inst].last_implicit_res; }
+
+// Tangent-linear mode: every instance is re-run from its current states with K-direction dual
+// numbers; the value parts reproduce the plain run bit for bit, the derivative parts are the
+// directional derivatives of the computed final states (decisions frozen).
+typedef orcdual::Dual<8> D8;
+
+int orc_tangent(void* H, int n_dir, const double* seed_w, const double* seed_rho, const double* seed_m,
+                const double* seed_tau, int n_prog, const int* prog_kind, const double* prog_arg, int n_threads) {
+  Ctx* C = (Ctx*)H;
+  const int n = (int)C->inst.size();
+  if (n_dir < 1 || n_prog < 0) return ORC_ERR_ARG;
+  std::vector<long> off(n + 1, 0);
+  for (int k = 0; k < n; ++k) off[k + 1] = off[k] + C->inst[k].M();
+  const long tot = off[n];
+  std::vector<Inst<double>> start = C->inst;
+  std::vector<Inst<double>> final_state(n);
+  C->tan_w.assign(n, {});
+  C->tan_r.assign(n, {});
+  C->tan_m.assign(n, {});
+  C->tan_dirs = n_dir;
+  for (int d0 = 0; d0 < n_dir; d0 += 8) {
+    parallel_for(n, n_threads, [&](int k) {
+      const Inst<double>& S = start[k];
+      Inst<D8> I;
+      I.N = S.N;
+      I.xL = S.xL;
+      I.xR = S.xR;
+      I.h = S.h;
+      I.tau = S.tau;
+      I.t = S.t;
+      I.status = S.status;
+      I.ph = S.ph;
+      const int M = S.M();
+      I.w.resize(M);
+      I.r.resize(M);
+      I.m.resize(M);
+      I.f.resize(M + 1);
+      for (int i = 0; i < M; ++i) {
+        I.w[i] = S.w[i];
+        I.r[i] = S.r[i];
+        I.m[i] = S.m[i];
+      }
+      for (int i = 0; i <= M; ++i) I.f[i] = Face<D8>{S.f[i].pb, S.f[i].j, D8(S.f[i].x)};
+      for (int q = 0; q < 8 && d0 + q < n_dir; ++q) {
+        const long base = (long)(d0 + q) * tot + off[k];
+        if (seed_tau) I.tau.d[q] = seed_tau[(long)(d0 + q) * n + k];
+        // a phase boundary sits at the last fixed face plus the widths since it: its position moves
+        // with the seeded widths
+        double part = 0.0;
+        for (int i = 0; i < M; ++i) {
+          if (seed_w) I.w[i].d[q] = seed_w[base + i];
+          if (seed_rho) I.r[i].d[q] = seed_rho[base + i];
+          if (seed_m) I.m[i].d[q] = seed_m[base + i];
+          part += seed_w ? seed_w[base + i] : 0.0;
+          if (I.f[i + 1].pb)
+            I.f[i + 1].x.d[q] = part;
+          else
+            part = 0.0;
+        }
+      }
+      for (int p = 0; p < n_prog; ++p) {
+        if (prog_kind[p] == 0) {
+          for (long s = 0; s < (long)prog_arg[p] && I.status == ORC_OK; ++s) step_instance(C->F, C->o, I, -1.0);
+        } else {
+          while (I.status == ORC_OK && val(I.t) < prog_arg[p]) step_instance(C->F, C->o, I, prog_arg[p]);
+        }
+      }
+      const int Mf = I.M();
+      if (d0 == 0) {
+        C->tan_w[k].assign((size_t)n_dir * Mf, 0.0);
+        C->tan_r[k].assign((size_t)n_dir * Mf, 0.0);
+        C->tan_m[k].assign((size_t)n_dir * Mf, 0.0);
+        Inst<double>& O = final_state[k];
+        O = S;
+        O.w.resize(Mf);
+        O.r.resize(Mf);
+        O.m.resize(Mf);
+        O.f.resize(Mf + 1);
+        for (int i = 0; i < Mf; ++i) {
+          O.w[i] = I.w[i].v;
+          O.r[i] = I.r[i].v;
+          O.m[i] = I.m[i].v;
+        }
+        for (int i = 0; i <= Mf; ++i) O.f[i] = Face<double>{I.f[i].pb, I.f[i].j, I.f[i].x.v};
+        O.ph = I.ph;
+        O.t = I.t.v;
+        O.status = I.status;
+        O.steps = S.steps + I.steps;
+        O.dts_iters = S.dts_iters + I.dts_iters;
+        O.dts_max = std::max(S.dts_max, I.dts_max);
+        O.newton = S.newton + I.newton;
+        O.merges = S.merges + I.merges;
+        O.splits = S.splits + I.splits;
+        O.creations = S.creations + I.creations;
+        O.maxiter = S.maxiter + I.maxiter;
+        O.pb_solves = S.pb_solves + I.pb_solves;
+        O.last_implicit_res = I.last_implicit_res;
+      }
+      for (int q = 0; q < 8 && d0 + q < n_dir; ++q)
+        for (int i = 0; i < Mf; ++i) {
+          C->tan_w[k][(size_t)(d0 + q) * Mf + i] = I.w[i].d[q];
+          C->tan_r[k][(size_t)(d0 + q) * Mf + i] = I.r[i].d[q];
+          C->tan_m[k][(size_t)(d0 + q) * Mf + i] = I.m[i].d[q];
+        }
+    });
+  }
+  C->inst = final_state;
+  return ORC_OK;
+}
+
+int orc_get_tangent(void* H, int dir, double* d_w, double* d_rho, double* d_m) {
+  Ctx* C = (Ctx*)H;
+  if (dir < 0 || dir >= C->tan_dirs) return ORC_ERR_ARG;
+  long o = 0;
+  for (size_t k = 0; k < C->inst.size(); ++k) {
+    const long Mf = C->inst[k].M();
+    for (long i = 0; i < Mf; ++i, ++o) {
+      d_w[o] = C->tan_w[k][(size_t)dir * Mf + i];
+      d_rho[o] = C->tan_r[k][(size_t)dir * Mf + i];
+      d_m[o] = C->tan_m[k][(size_t)dir * Mf + i];
+    }
+  }
+  return ORC_OK;
+}
 
 }  // extern "C"

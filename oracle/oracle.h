@@ -95,6 +95,20 @@ int orc_explicit_run_to(void* H, double t_end, int n_threads);
  * recorded when the dual-time loop ends (diagnostic for tests). */
 double orc_last_implicit_residual(void* H, int inst);
 
+/* ---- tangent-linear (forward-mode) derivative: the oracle's own derivative of the scheme ----
+ * Re-runs every instance from its current states through the same code with dual numbers (value +
+ * 8 directional derivatives per pass, more directions in further passes) and keeps the derivatives
+ * of the final cell states. Branch decisions (CFL argmax, merges, blocks, splits, stop tests) are
+ * frozen; iterations (Newton, dual time) are differentiated as computed. Seeds are laid out
+ * [n_dir][total cells] for widths, rho and m and [n_dir][n_inst] for tau; any may be NULL (zero).
+ * Seeding the widths of the two cells next to a phase boundary with +d and -d moves the boundary by
+ * d. The program is a list of calls: kind 0 = step(arg) steps, kind 1 = run_to(arg). Afterwards
+ * the instances hold the final states (as if the program had run). */
+int orc_tangent(void* H, int n_dir, const double* seed_w, const double* seed_rho, const double* seed_m,
+                const double* seed_tau, int n_prog, const int* prog_kind, const double* prog_arg, int n_threads);
+/* Direction dir of the last orc_tangent: final-state derivatives, in orc_get_states order. */
+int orc_get_tangent(void* H, int dir, double* d_w, double* d_rho, double* d_m);
+
 #ifdef __cplusplus
 }
 #endif

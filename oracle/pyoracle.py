@@ -58,6 +58,9 @@ def lib():
         L.orc_nopt_star.argtypes = [C.POINTER(OFluid), C.c_int, C.c_double, C.c_double, C.c_double, C.c_double]
         L.orc_creation_solve.argtypes = [C.POINTER(OFluid), C.POINTER(OOpts), C.c_double, C.c_int, C.c_double,
                                          C.c_double, C.c_double, C.c_double, dp]
+        if hasattr(L, "orc_tangent"):
+            L.orc_tangent.argtypes = [C.c_void_p, C.c_int, dp, dp, dp, dp, C.c_int, ip, dp, C.c_int]
+            L.orc_get_tangent.argtypes = [C.c_void_p, C.c_int, dp, dp, dp]
         L.orc_exact_sample.argtypes = [C.POINTER(OFluid), C.POINTER(OOpts), C.c_double, C.c_int, C.c_double,
                                        C.c_double, C.c_int, C.c_double, C.c_double, C.c_int, dp, dp, dp, ip]
         _lib = L
@@ -196,6 +199,30 @@ class Oracle:
         lib().orc_get_stats(self.h, s.ctypes.data_as(C.POINTER(C.c_longlong)))
         keys = ["steps", "dts_iters", "dts_max", "newton", "merges", "splits", "creations", "maxiter", "pb_solves"]
         return {k: s[:, i].copy() for i, k in enumerate(keys)}
+
+    def tangent(self, program, seed_w=None, seed_rho=None, seed_m=None, seed_tau=None, threads=1):
+        """Forward-mode derivative of the program [("step", n) | ("run_to", t_end), ...] from the current
+        states. Seeds: arrays [n_dir, total cells] (widths, rho, m) and [n_dir, n_inst] (tau), any None.
+        Returns the final states and a dict of derivative arrays [n_dir, final cells]."""
+        seeds = [s for s in (seed_w, seed_rho, seed_m, seed_tau) if s is not None]
+        n_dir = seeds[0].shape[0]
+        conv = [None if s is None else np.ascontiguousarray(s, dtype=np.float64) for s in
+                (seed_w, seed_rho, seed_m, seed_tau)]
+        ptr = [C.cast(None, C.POINTER(C.c_double)) if s is None else _dp(s) for s in conv]
+        kinds = np.array([0 if k == "step" else 1 for k, _ in program], dtype=np.int32)
+        args = np.array([float(a) for _, a in program], dtype=np.float64)
+        rc = lib().orc_tangent(self.h, n_dir, ptr[0], ptr[1], ptr[2], ptr[3], len(program), _ip(kinds), _dp(args),
+                               threads)
+        if rc != 0:
+            raise RuntimeError(f"oracle tangent: status {rc}")
+        st = self.states()
+        tot = st["offsets"][-1]
+        d = {"widths": np.zeros((n_dir, tot)), "rho": np.zeros((n_dir, tot)), "m": np.zeros((n_dir, tot))}
+        for q in range(n_dir):
+            dw, dr, dm = np.zeros(tot), np.zeros(tot), np.zeros(tot)
+            lib().orc_get_tangent(self.h, q, _dp(dw), _dp(dr), _dp(dm))
+            d["widths"][q], d["rho"][q], d["m"][q] = dw, dr, dm
+        return st, d
 
     def implicit_defect(self, i=0):
         return lib().orc_last_implicit_residual(self.h, i)

@@ -1,0 +1,83 @@
+"""Pins of the oracle's tangent-linear mode (its forward-mode derivative by dual numbers), the reference
+for the CUDA adjoint: the value part reproduces the plain oracle bit for bit, and the derivative parts
+match central finite differences of the plain oracle (a computation that shares no derivative code),
+direction by direction, on the jittered adjoint workload at small size."""
+import dataclasses
+
+import numpy as np
+
+from oracle import pyoracle as P
+from paper_2211_00705_gb300 import inputs as I
+
+
+def _run(b, steps):
+    o = P.Oracle(b)
+    o.step(steps)
+    return o.states()
+
+
+def _dirs(b):
+    rng = np.random.default_rng(3)
+    M = int(b.cell_offsets[-1])
+    z = np.zeros(M)
+    out = [dict(tau=b.tau.copy(), rho=z, m=z, widths=z)]
+    for c in rng.choice(M, 2, replace=False):
+        e = np.zeros(M)
+        e[c] = b.rho[c]
+        out.append(dict(tau=np.zeros(b.n_inst), rho=e, m=z, widths=z))
+    for c in rng.choice(M, 2, replace=False):
+        e = np.zeros(M)
+        e[c] = max(abs(b.m[c]), b.rho[c])
+        out.append(dict(tau=np.zeros(b.n_inst), rho=z, m=e, widths=z))
+    dw = np.zeros(M)
+    f = int(np.where(b.phase[:-1] != b.phase[1:])[0][0])
+    dw[f], dw[f + 1] = 0.1 * b.widths[f + 1], -0.1 * b.widths[f + 1]   # the boundary moves right
+    out.append(dict(tau=np.zeros(b.n_inst), rho=z, m=z, widths=dw))
+    return out
+
+
+def test_tangent_values_are_the_plain_oracle():
+    b = I.adjoint_batch(n_inst=2, n_lattice=60, n_steps=40)
+    plain = _run(b, 40)
+    st, _ = P.Oracle(b).tangent([("step", 40)], seed_rho=np.ones((1, int(b.cell_offsets[-1]))))
+    for k in ("offsets", "widths", "rho", "m", "phase", "t", "status"):
+        np.testing.assert_array_equal(plain[k], st[k])
+
+
+def test_tangent_matches_central_differences():
+    """Final-state derivatives in the directions tau, rho and m of single cells, and the boundary
+    position, against central differences (relative step 1e-6 for states, 1e-4 for tau and the
+    boundary, whose effect on the states is ~1e-7 relative and needs the larger step to rise above
+    round-off)."""
+    b = I.adjoint_batch(n_inst=1, n_lattice=60, n_steps=40)
+    dirs = _dirs(b)
+    st, d = P.Oracle(b).tangent([("step", 40)], seed_w=np.stack([x["widths"] for x in dirs]),
+                               seed_rho=np.stack([x["rho"] for x in dirs]), seed_m=np.stack([x["m"] for x in dirs]),
+                               seed_tau=np.stack([x["tau"] for x in dirs]))
+    for q, dd in enumerate(dirs):
+        eps = 1e-4 if (dd["tau"].any() or dd["widths"].any()) else 1e-6
+        sp = _run(dataclasses.replace(b, tau=b.tau + eps * dd["tau"], rho=b.rho + eps * dd["rho"],
+                                      m=b.m + eps * dd["m"], widths=b.widths + eps * dd["widths"]), 40)
+        sm = _run(dataclasses.replace(b, tau=b.tau - eps * dd["tau"], rho=b.rho - eps * dd["rho"],
+                                      m=b.m - eps * dd["m"], widths=b.widths - eps * dd["widths"]), 40)
+        assert len(sp["rho"]) == len(st["rho"]) == len(sm["rho"])
+        for key in ("rho", "m"):
+            fd = (sp[key] - sm[key]) / (2 * eps)
+            tg = d[key][q]
+            err = np.max(np.abs(fd - tg)) / np.max(np.abs(tg))
+            assert err <= 2e-5, (q, key, err)
+
+
+def test_tangent_of_a_uniform_state_is_exact():
+    """Closed form: a uniform liquid state is left unchanged by a step (every face flux is the same
+    physical flux), and so is a uniform shift of its momentum (every face flux shifts by the same amount,
+    HLL being consistent): d rho_T / d m0 = 0 and d m_T / d m0 = 1 in every cell, whatever dt is."""
+    N = 40
+    fl = I.workload_fluid()
+    b = I.Batch(n_lattice=np.array([N], np.int32), x_left=np.zeros(1), x_right=np.ones(1),
+                tau=np.array([1e-7]), cell_offsets=np.array([0, N], np.int32), widths=np.full(N, 1.0 / N),
+                rho=np.full(N, 1000.0), m=np.full(N, 5000.0), phase=np.ones(N, np.uint8), fluid=fl,
+                options=I.Options(), t_end=0.0, n_steps=3, name="uniform liquid")
+    st, d = P.Oracle(b).tangent([("step", 3)], seed_m=np.ones((1, N)))
+    np.testing.assert_allclose(d["rho"][0], 0.0, atol=1e-12)
+    np.testing.assert_allclose(d["m"][0], 1.0, atol=1e-12)
