@@ -179,6 +179,38 @@ imexds_status imexds_step_uniform_noalloc(const imexds_fluid* fluid, double cfl,
  * solves) and CUDA's log on n host values x > 0; results in the host arrays fast and ref. */
 imexds_status imexds_check_log(int32_t n, const double* x, double* fast, double* ref);
 
+/* ---- discrete adjoint ----
+ * Gradient of a loss J of the final cell states of the last forward run (the imexds_step / imexds_run_to
+ * calls since the last imexds_set_states or imexds_reset) with respect to the initial cell states, the
+ * initial widths (which place the phase boundaries) and the kinetic coefficient tau of each instance.
+ * The paper has no adjoint; this differentiates its discrete scheme (Algorithm 1 / Algorithm 2 with the
+ * App. A boundary solver) along the replayed trajectory, with every decision frozen (CFL argmax cell,
+ * merges, implicit blocks, splits): the explicit sweep by its transposed HLL Jacobians, each block's
+ * converged dual-time system by one transposed solve (implicit function theorem, not by unrolling the
+ * pseudo-iterations), the boundary flux by the implicit function theorem on the 2x2 system of
+ * Eq. 2p_RP:ex_sys, forward states checkpointed every k steps and recomputed per segment.
+ * Phase creation (App. B) is not differentiated (an instance that creates a phase reports
+ * IMEXDS_ERR_STATE). The gradient is that of the converged implicit system: use tight dual-time
+ * tolerances when it is compared with finite differences of the forward run.
+ *
+ * Inputs (host arrays in imexds_get_states order, sized from imexds_cell_counts): dJ_drho_T, dJ_dm_T
+ * and dJ_dw_T (may be NULL: J independent of the widths). Outputs (host arrays in imexds_set_states
+ * order): dJ_drho0, dJ_dm0, dJ_dw0 (may be NULL; zero for cells with two fixed faces, whose width is
+ * the lattice's; for a cell next to a boundary it moves that boundary with the width), dJ_dtau
+ * (n_inst), inst_status (n_inst, may be NULL): IMEXDS_OK, or why the instance has no gradient (its
+ * entries are NaN). The replay uses the context's options; device memory for the checkpoints and the
+ * tape of one segment is allocated on the first call and kept (about (38 n_ck + 26 k) bytes per cell
+ * slot). */
+imexds_status imexds_adjoint(imexds_ctx* ctx, const double* dJ_dw_T, const double* dJ_drho_T,
+                             const double* dJ_dm_T, double* dJ_dw0, double* dJ_drho0, double* dJ_dm0,
+                             double* dJ_dtau, int32_t* inst_status);
+/* Checkpoint interval k of the adjoint (default 64). */
+imexds_status imexds_set_adjoint_checkpoint(imexds_ctx* ctx, int32_t every);
+/* The last imexds_adjoint: device time of its kernel (ms), the largest relative deviation of its
+ * replayed final states from the forward run's (rho and m relative to max|rho|, widths relative to h),
+ * and the cell-steps it replayed (initial cells x steps, per instance, summed). Any may be NULL. */
+imexds_status imexds_adjoint_info(imexds_ctx* ctx, double* kernel_ms, double* replay_err, int64_t* cell_steps);
+
 void imexds_destroy(imexds_ctx* ctx);
 const char* imexds_status_string(imexds_status s);
 /* Text of the last CUDA error seen by any context of this process (thread-unsafe, static storage). */

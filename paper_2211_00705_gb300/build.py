@@ -8,7 +8,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libimexds.so")
 SOURCES = [os.path.join(HERE, "csrc", "imexds.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", "physics.cuh"), os.path.join(ROOT, "include", "imexds.h")]
+DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in sorted(os.listdir(os.path.join(HERE, "csrc")))
+        if f.endswith(".cuh")] + [os.path.join(ROOT, "include", "imexds.h")]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-fmad=false", "-Xcompiler", "-fPIC", "-shared", "-Xptxas", "-v"]

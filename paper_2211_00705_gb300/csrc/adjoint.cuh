@@ -1,0 +1,1167 @@
+// Discrete adjoint of the explicit-implicit splitting scheme (arXiv 2211.00705): gradients of a loss of
+// the final cell states with respect to the initial states, the initial boundary positions (through the
+// widths) and the kinetic coefficient tau of every instance.
+//
+// Design (one CTA per instance, all instances in one launch):
+//   * Replay: the step of Algorithm 1 / Algorithm 2 runs again on a plain cell list of the instance
+//     (the paper's moving grid: one entry per cell, faces with their kind), from the initial states of
+//     the last forward call, with the same device physics as the forward kernels. Every k steps the
+//     whole list is written to a checkpoint.
+//   * Reverse: for the checkpoint segments from last to first, the segment is recomputed from its
+//     checkpoint while each step's pre-step list and its decisions (dt, the CFL argmax cell, merges,
+//     blocks, the last dual-time iterate of each block, the converged boundary pressures, splits) are
+//     taped; then the steps are reversed one by one:
+//       splits^T -> boundary positions^T -> per block: the converged implicit system differentiated by
+//       the implicit function theorem (one transposed solve of (I - dg/dW)^T mu = lambda_W, not an
+//       unrolled dual-time loop) -> explicit sweep^T (HLL Jacobians at U^n) -> merges^T -> dt^T through
+//       the argmax cell (or t^T for a step clipped to an end time).
+//   * Face Jacobians come from forward-mode dual numbers (adjoint_local.cuh); the boundary flux is
+//     differentiated at the converged star pressures by the implicit function theorem.
+// Decisions (merges, blocks, splits, the argmax cell, dual-time stop) are frozen: the gradient is that
+// of the discrete map along the replayed trajectory. Phase creation (App. B) is not differentiated: a
+// replay that creates a phase stops the instance with IMEXDS_ERR_STATE.
+#pragma once
+#include "adjoint_local.cuh"
+
+namespace imexds {
+namespace adj {
+
+constexpr int ATHREADS = 128;
+constexpr int AMAXPB = 16;   // phase boundaries per instance
+constexpr int AMAXBLK = 8;   // blocks per step
+constexpr int AMAXB = 8;     // cells per block
+constexpr int AMAXBC = 32;   // block cells per step, all blocks
+constexpr int AMAXEV = 8;    // merges and splits per step
+constexpr int ACAP_PAD = 64; // cells a list may grow by (splits) beyond its initial count
+
+struct StepRec {
+  double dt;
+  int clipped, kmax, n_merge, n_blk, n_split, n_pbf;
+  int mg_a[AMAXEV], mg_b[AMAXEV];
+  double mg_v[AMAXEV][6];  // w_a, r_a, m_a, w_b, r_b, m_b before the merge
+  int blo[AMAXBLK], bhi[AMAXBLK];
+  double Wr[AMAXBC], Wm[AMAXBC];  // last dual-time iterate of each block cell, block after block
+  double ppl[AMAXPB], ppr[AMAXPB];  // converged star pressures at that iterate, interior boundary faces in order
+  int sp_i[AMAXEV], sp_case[AMAXEV];
+};
+
+struct AInst {
+  long long off;  // first slot of this instance in every per-cell / per-face array (stride cap + 1)
+  long long done; // steps done inside the current program call
+  int M, cap, status, pc;
+  int nsteps, M_seed, pad0, pad1;
+  double h, xL, tau, t;
+  double lam_t, lam_tau;
+};
+
+struct ACk {
+  long long done;
+  int M, status, pc, pad;
+  double t;
+};
+
+struct ADev {
+  AInst* I;
+  int n_inst, k, n_ck, n_prog;
+  long long stride;
+  const int* pk;     // program: 0 = step(arg), 1 = run_to(arg)
+  const double* pa;
+  // working cell list and faces
+  double *w, *r, *m, *fx;
+  unsigned char *ph, *fpb;
+  int* fj;
+  // face scratch
+  double *F0, *F1, *LF0, *LF1, *CL0, *CL1, *CR0, *CR1;
+  // post-merge list (reverse)
+  double *pw, *pr, *pm;
+  unsigned char *pph, *pfpb;
+  // adjoints (current) and accumulators
+  double *lw, *lr, *lm, *lx, *nw, *nr, *nm, *nx;
+  // checkpoints
+  double *ck_w, *ck_r, *ck_m, *ck_fx;
+  unsigned char *ck_ph, *ck_fpb;
+  int* ck_fj;
+  ACk* ck_h;
+  // final replay states
+  double *fin_w, *fin_r, *fin_m;
+  unsigned char* fin_ph;
+  int* fin_M;
+  // tape
+  double *tp_w, *tp_r, *tp_m;
+  unsigned char *tp_ph, *tp_fpb;
+  int* tp_M;
+  StepRec* rec;
+};
+
+__device__ inline void afail(AInst& I, int code) {
+  if (I.status == 0) I.status = code;
+}
+
+// ------------------------------------------------------------------------------ list helpers
+// copy n cells (and n + 1 faces when faces) between two lists of the same layout, whole CTA
+__device__ inline void cta_copy_d(double* dst, const double* src, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+__device__ inline void cta_copy_b(unsigned char* dst, const unsigned char* src, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+__device__ inline void cta_copy_i(int* dst, const int* src, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+__device__ inline void cta_zero(double* dst, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = 0.0;
+}
+
+// one thread: erase cell b (and face b) of a list
+__device__ void list_erase(double* w, double* r, double* m, unsigned char* ph, unsigned char* fpb, int* fj,
+                           double* fx, int M, int b) {
+  for (int i = b; i + 1 < M; ++i) {
+    w[i] = w[i + 1];
+    r[i] = r[i + 1];
+    m[i] = m[i + 1];
+    ph[i] = ph[i + 1];
+  }
+  for (int g = b; g < M; ++g) {
+    fpb[g] = fpb[g + 1];
+    if (fj) fj[g] = fj[g + 1];
+    if (fx) fx[g] = fx[g + 1];
+  }
+}
+// one thread: open a slot at cell p (cells p.. and faces p.. move one up)
+__device__ void list_open(double* w, double* r, double* m, unsigned char* ph, unsigned char* fpb, int* fj,
+                          double* fx, int M, int p) {
+  for (int i = M - 1; i >= p; --i) {
+    w[i + 1] = w[i];
+    r[i + 1] = r[i];
+    m[i + 1] = m[i];
+    ph[i + 1] = ph[i];
+  }
+  for (int g = M; g >= p; --g) {
+    fpb[g + 1] = fpb[g];
+    if (fj) fj[g + 1] = fj[g];
+    if (fx) fx[g + 1] = fx[g];
+  }
+}
+// adjoint lists: erase / open cell b of (lw, lr, lm) and face b of lx
+__device__ void lam_erase(double* lw, double* lr, double* lm, double* lx, int M, int b) {
+  for (int i = b; i + 1 < M; ++i) {
+    lw[i] = lw[i + 1];
+    lr[i] = lr[i + 1];
+    lm[i] = lm[i + 1];
+  }
+  for (int g = b; g < M; ++g) lx[g] = lx[g + 1];
+}
+__device__ void lam_open(double* lw, double* lr, double* lm, double* lx, int M, int p) {
+  for (int i = M - 1; i >= p; --i) {
+    lw[i + 1] = lw[i];
+    lr[i + 1] = lr[i];
+    lm[i + 1] = lm[i];
+  }
+  for (int g = M; g >= p; --g) lx[g + 1] = lx[g];
+}
+
+struct SharedStep {
+  double dt, lam, red_v[ATHREADS / 32], lam_dt;
+  int red_i[ATHREADS / 32];
+  int M, kmax, clipped, done, bad;
+  int n_pb, pb[AMAXPB];
+  int n_blk, blo[AMAXBLK], bhi[AMAXBLK];
+  double t_end;
+};
+
+__device__ inline bool in_block(const SharedStep& S, int i) {
+  for (int b = 0; b < S.n_blk; ++b)
+    if (i >= S.blo[b] && i <= S.bhi[b]) return true;
+  return false;
+}
+__device__ inline bool face_in_block(const SharedStep& S, int g) {
+  for (int b = 0; b < S.n_blk; ++b)
+    if (g > S.blo[b] && g <= S.bhi[b]) return true;
+  return false;
+}
+
+// CTA max of s (first index among equal maxima); result in S.red_v[0] / S.red_i[0]
+__device__ void cta_argmax(SharedStep& S, double v, int idx) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    double v2 = __shfl_down_sync(0xffffffffu, v, o);
+    int i2 = __shfl_down_sync(0xffffffffu, idx, o);
+    if (v2 > v || (v2 == v && i2 < idx)) {
+      v = v2;
+      idx = i2;
+    }
+  }
+  if (lane == 0) {
+    S.red_v[wid] = v;
+    S.red_i[wid] = idx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
+      if (S.red_v[q] > S.red_v[0] || (S.red_v[q] == S.red_v[0] && S.red_i[q] < S.red_i[0])) {
+        S.red_v[0] = S.red_v[q];
+        S.red_i[0] = S.red_i[q];
+      }
+  }
+  __syncthreads();
+}
+__device__ double cta_sum(SharedStep& S, double v) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) S.red_v[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += S.red_v[q];
+  return s;  // valid in thread 0
+}
+
+// collect the phase-boundary faces of a list (ascending) into S.pb; false if there are too many
+__device__ bool collect_pbs(SharedStep& S, const unsigned char* fpb, int M) {
+  if (threadIdx.x == 0) S.n_pb = 0;
+  __syncthreads();
+  for (int g = 1 + threadIdx.x; g < M; g += blockDim.x)
+    if (fpb[g]) {
+      int q = atomicAdd(&S.n_pb, 1);
+      if (q < AMAXPB) S.pb[q] = g;
+    }
+  __syncthreads();
+  bool ok = S.n_pb <= AMAXPB;
+  __syncthreads();
+  if (threadIdx.x == 0 && ok) {
+    for (int a = 1; a < S.n_pb; ++a) {  // insertion sort of a handful of faces
+      int v = S.pb[a], b = a - 1;
+      while (b >= 0 && S.pb[b] > v) {
+        S.pb[b + 1] = S.pb[b];
+        --b;
+      }
+      S.pb[b + 1] = v;
+    }
+  }
+  __syncthreads();
+  return ok;
+}
+
+// ------------------------------------------------------------------------------ forward step
+// Program position: advance past finished calls; returns false when the instance has no step left.
+__device__ bool prog_next(const ADev& A, AInst& I, double& t_end) {
+  while (I.pc < A.n_prog) {
+    if (A.pk[I.pc] == 0) {
+      if (I.done < (long long)A.pa[I.pc]) break;
+    } else {
+      if (I.t < A.pa[I.pc]) break;
+    }
+    I.pc++;
+    I.done = 0;
+  }
+  if (I.pc >= A.n_prog || I.status) return false;
+  t_end = (A.pk[I.pc] == 1) ? A.pa[I.pc] : -1.0;
+  return true;
+}
+
+// Algorithm 2 on one block of the list (thread 0). U^n of the block cells is still in the list (the
+// sweep does not touch them); FL/FR are the explicit fluxes at faces lo and hi+1. Writes the last
+// iterate and converged boundary pressures to the step record (when rec != nullptr) and the Part 2
+// result to out_*.
+__device__ bool dts_block(const ADev& A, AInst& I, const SharedStep& S, int lo, int hi, const double* hp,
+                          const int* tiny, double FL0, double FL1, double FR0, double FR1, StepRec* rec,
+                          int& rec_cell, int& rec_pbf, double* out_r, double* out_m, double* out_w, double* wcf) {
+  const long long o = I.off;
+  const double dt = S.dt, h = I.h, tau = I.tau;
+  const int nb = hi - lo + 1;
+  double Ur[AMAXB], Um[AMAXB], Uw[AMAXB], Wr[AMAXB], Wm[AMAXB], th[AMAXB];
+  double F0[AMAXB + 1], F1[AMAXB + 1], wc[AMAXB + 1], hl[AMAXB], gl[AMAXB + 1], gr[AMAXB + 1];
+  int ph[AMAXB], fp[AMAXB + 1];
+  for (int q = 0; q < nb; ++q) {
+    Ur[q] = Wr[q] = A.r[o + lo + q];
+    Um[q] = Wm[q] = A.m[o + lo + q];
+    Uw[q] = A.w[o + lo + q];
+    ph[q] = A.ph[o + lo + q];
+    th[q] = fmin(c_opts.theta_nb, hp[q] / h);
+  }
+  for (int q = 0; q <= nb; ++q) {
+    fp[q] = (q > 0 && q < nb) ? A.fpb[o + lo + q] : 0;
+    gl[q] = gr[q] = 0.0;
+  }
+  auto fluxes = [&]() -> int {  // 0 ok, 1 boundary solve failed, 2 non-positive width
+    F0[0] = FL0;
+    F1[0] = FL1;
+    F0[nb] = FR0;
+    F1[nb] = FR1;
+    wc[0] = wc[nb] = 0.0;
+    for (int q = 1; q < nb; ++q) {
+      if (fp[q]) {
+        PBOut R = pb_solve_warm(c_fluid, c_opts, tau, ph[q - 1], Wr[q - 1], Wm[q - 1], ph[q], Wr[q], Wm[q], gl[q],
+                                gr[q]);
+        if (!R.ok) return 1;
+        F0[q] = R.F0;
+        F1[q] = R.F1;
+        wc[q] = R.w;
+      } else {
+        hll_fast(c_fluid.ph[ph[q]], Wr[q - 1], Wm[q - 1], Wr[q], Wm[q], F0[q], F1[q]);
+        wc[q] = 0.0;
+      }
+    }
+    for (int q = 0; q < nb; ++q) hl[q] = Uw[q] + (wc[q + 1] - wc[q]) * dt;
+    for (int q = 0; q < nb; ++q)
+      if (!(hl[q] > 0.0)) return 2;
+    return 0;
+  };
+  bool stop = false;
+  for (int l = 0; l < c_opts.l_max && !stop; ++l) {
+    int e = fluxes();
+    if (e) {
+      afail(I, e == 1 ? IMEXDS_ERR_PB_NOCONV : IMEXDS_ERR_VANISH);
+      return false;
+    }
+    double res_nb = 0.0, res_k = 0.0;
+    double Nr[AMAXB], Nm[AMAXB];
+    for (int q = 0; q < nb; ++q) {
+      double t = th[q];
+      double tr = Uw[q] / hl[q] * Ur[q] - dt / hl[q] * (F0[q + 1] - F0[q]);
+      double tm = Uw[q] / hl[q] * Um[q] - dt / hl[q] * (F1[q + 1] - F1[q]);
+      Nr[q] = (Wr[q] + t * tr) / (1.0 + t);
+      Nm[q] = (Wm[q] + t * tm) / (1.0 + t);
+      double dtau = t * dt;
+      double e0 = (1.0 + t) * fabs(Nr[q] - Wr[q]) / (dtau * fmax(fabs(Wr[q]), 1.0));
+      double e1 = (1.0 + t) * fabs(Nm[q] - Wm[q]) / (dtau * fmax(fabs(Wm[q]), 1.0));
+      double res = fmax(e0, e1);
+      if (c_opts.res_mode == 1) res *= dt;
+      if (tiny[q])
+        res_k = fmax(res_k, res);
+      else
+        res_nb = fmax(res_nb, res);
+    }
+    for (int q = 0; q < nb; ++q) {
+      Wr[q] = Nr[q];
+      Wm[q] = Nm[q];
+    }
+    if (res_nb < c_opts.tol_nb && res_k < c_opts.tol_k) stop = true;
+  }
+  int e = fluxes();  // Part 2 at the last iterate
+  if (e) {
+    afail(I, e == 1 ? IMEXDS_ERR_PB_NOCONV : IMEXDS_ERR_VANISH);
+    return false;
+  }
+  for (int q = 0; q < nb; ++q) {
+    out_r[q] = (Uw[q] * Ur[q] - dt * (F0[q + 1] - F0[q])) / hl[q];
+    out_m[q] = (Uw[q] * Um[q] - dt * (F1[q + 1] - F1[q])) / hl[q];
+    out_w[q] = hl[q];
+  }
+  for (int q = 0; q <= nb; ++q) wcf[q] = wc[q];
+  if (rec) {
+    if (rec_cell + nb > AMAXBC) {
+      afail(I, IMEXDS_ERR_CAPACITY);
+      return false;
+    }
+    for (int q = 0; q < nb; ++q) {
+      rec->Wr[rec_cell + q] = Wr[q];
+      rec->Wm[rec_cell + q] = Wm[q];
+    }
+    rec_cell += nb;
+    for (int q = 1; q < nb; ++q)
+      if (fp[q]) {
+        if (rec_pbf >= AMAXPB) {
+          afail(I, IMEXDS_ERR_CAPACITY);
+          return false;
+        }
+        rec->ppl[rec_pbf] = gl[q];
+        rec->ppr[rec_pbf] = gr[q];
+        rec_pbf++;
+      }
+  }
+  return true;
+}
+
+// One time step of the replay (whole CTA). Tapes the pre-step list into tape slot `slot` and the
+// decisions into *rec when rec != nullptr.
+__device__ void fwd_step(const ADev& A, AInst& I, SharedStep& S, double t_end, StepRec* rec, int slot) {
+  const long long o = I.off;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    S.M = I.M;
+    S.bad = 0;
+  }
+  __syncthreads();
+  int M = S.M;
+  if (rec) {
+    const long long to = (long long)slot * A.stride + o;
+    cta_copy_d(A.tp_w + to, A.w + o, M);
+    cta_copy_d(A.tp_r + to, A.r + o, M);
+    cta_copy_d(A.tp_m + to, A.m + o, M);
+    cta_copy_b(A.tp_ph + to, A.ph + o, M);
+    cta_copy_b(A.tp_fpb + to, A.fpb + o, M + 1);
+    if (tid == 0) A.tp_M[(long long)slot * A.n_inst + (int)(&I - A.I)] = M;
+  }
+  // (1) CFL time step (Eq. cfl_cond:unif) over all cells, with the argmax cell
+  {
+    double v = -1.0;
+    int idx = 0x7fffffff;
+    for (int i = tid; i < M; i += blockDim.x) {
+      double s = fabs(A.m[o + i] / A.r[o + i]) + c_fluid.ph[A.ph[o + i]].a;
+      if (s > v) {
+        v = s;
+        idx = i;
+      }
+    }
+    cta_argmax(S, v, idx);
+    if (tid == 0) {
+      double dt = c_opts.cfl * I.h / S.red_v[0];
+      int clipped = 0;
+      if (t_end > 0.0 && t_end - I.t <= dt) {
+        dt = t_end - I.t;
+        clipped = 1;
+      }
+      S.dt = dt;
+      S.lam = dt / I.h;
+      S.kmax = S.red_i[0];
+      S.clipped = clipped;
+      if (rec) {
+        rec->dt = dt;
+        rec->clipped = clipped;
+        rec->kmax = S.red_i[0];
+        rec->n_merge = rec->n_blk = rec->n_split = rec->n_pbf = 0;
+      }
+    }
+  }
+  if (!collect_pbs(S, A.fpb + o, M)) {
+    if (tid == 0) afail(I, IMEXDS_ERR_CAPACITY);
+    __syncthreads();
+    return;
+  }
+  // (2) grid management: boundary solves at U^n, marks, merges (thread 0; the list is short-edited)
+  __shared__ double s_hp[AMAXBC];
+  __shared__ int s_tiny[AMAXBC];
+  if (tid == 0) {
+    const double dt = S.dt;
+    double wf[AMAXPB];
+    int nmk = 0, mk[2 * AMAXPB];
+    bool ok = true;
+    for (int q = 0; q < S.n_pb && ok; ++q) {
+      int g = S.pb[q];
+      double gl = 0.0, gr = 0.0;
+      PBOut R = pb_solve_warm(c_fluid, c_opts, I.tau, A.ph[o + g - 1], A.r[o + g - 1], A.m[o + g - 1], A.ph[o + g],
+                              A.r[o + g], A.m[o + g], gl, gr);
+      if (!R.ok) {
+        afail(I, IMEXDS_ERR_PB_NOCONV);
+        ok = false;
+      }
+      wf[q] = R.w;
+    }
+    // candidate cells: both neighbours of every boundary, ascending, without repeats
+    for (int q = 0; q < S.n_pb && ok; ++q)
+      for (int s = 0; s < 2; ++s) {
+        int i = S.pb[q] - 1 + s;
+        if (nmk > 0 && mk[nmk - 1] >= i) continue;
+        int ql = -1, qr = -1;  // boundary indices on the left / right face of i
+        for (int p = 0; p < S.n_pb; ++p) {
+          if (S.pb[p] == i) ql = p;
+          if (S.pb[p] == i + 1) qr = p;
+        }
+        double wl = ql >= 0 ? wf[ql] : 0.0, wr = qr >= 0 ? wf[qr] : 0.0;
+        double hp = A.w[o + i] + (wr - wl) * dt;
+        if (hp < fmax(c_opts.alpha_min * I.h, 0.5 * A.w[o + i])) mk[nmk++] = i;
+      }
+    // merges in ascending order with the index shifts of earlier merges
+    int nmerge = 0, shift = 0;
+    bool any = false;
+    for (int q = 0; q < nmk && ok; ++q) {
+      if (mk[q] < 0) continue;  // consumed by the merge before it
+      int i = mk[q] - shift;
+      int Mi = S.M;
+      bool left_fixed = (i > 0) && !A.fpb[o + i];
+      bool right_fixed = (i + 1 < Mi) && !A.fpb[o + i + 1];
+      int a, b;
+      if (left_fixed) {
+        a = i - 1;
+        b = i;
+      } else if (right_fixed) {
+        a = i;
+        b = i + 1;
+        // the right neighbour is consumed: a later mark on it is dropped
+        if (q + 1 < nmk && mk[q + 1] - shift == i + 1) mk[q + 1] = -1000000;
+      } else {
+        afail(I, IMEXDS_ERR_VANISH);
+        ok = false;
+        break;
+      }
+      if (nmerge >= AMAXEV) {
+        afail(I, IMEXDS_ERR_CAPACITY);
+        ok = false;
+        break;
+      }
+      double wa = A.w[o + a], ra = A.r[o + a], ma = A.m[o + a];
+      double wb = A.w[o + b], rb = A.r[o + b], mb = A.m[o + b];
+      double wm = wa + wb;
+      A.r[o + a] = (wa * ra + wb * rb) / wm;
+      A.m[o + a] = (wa * ma + wb * mb) / wm;
+      A.w[o + a] = wm;
+      list_erase(A.w + o, A.r + o, A.m + o, A.ph + o, A.fpb + o, A.fj + o, A.fx + o, Mi, b);
+      S.M = Mi - 1;
+      if (rec) {
+        rec->mg_a[nmerge] = a;
+        rec->mg_b[nmerge] = b;
+        double* v = rec->mg_v[nmerge];
+        v[0] = wa, v[1] = ra, v[2] = ma, v[3] = wb, v[4] = rb, v[5] = mb;
+      }
+      nmerge++;
+      shift++;
+      any = true;
+      for (int p = 0; p < S.n_pb; ++p)
+        if (S.pb[p] > b) S.pb[p]--;
+    }
+    if (rec) rec->n_merge = nmerge;
+    // predicted widths on the merged grid (boundary speeds at U^n of the merged cells)
+    if (ok && any)
+      for (int q = 0; q < S.n_pb && ok; ++q) {
+        int g = S.pb[q];
+        double gl = 0.0, gr = 0.0;
+        PBOut R = pb_solve_warm(c_fluid, c_opts, I.tau, A.ph[o + g - 1], A.r[o + g - 1], A.m[o + g - 1],
+                                A.ph[o + g], A.r[o + g], A.m[o + g], gl, gr);
+        if (!R.ok) {
+          afail(I, IMEXDS_ERR_PB_NOCONV);
+          ok = false;
+        }
+        wf[q] = R.w;
+      }
+    // (3) blocks {k-1, k, k+1} around the tiny cell of every boundary, joined where they overlap
+    int nbk = 0;
+    const int Mm = S.M;
+    for (int q = 0; q < S.n_pb && ok; ++q) {
+      int g = S.pb[q];
+      int k = (A.w[o + g - 1] < A.w[o + g]) ? g - 1 : g;
+      int lo = max(k - 1, 0), hi = min(k + 1, Mm - 1);
+      if (nbk > 0 && lo <= S.bhi[nbk - 1]) {
+        S.bhi[nbk - 1] = max(S.bhi[nbk - 1], hi);
+      } else {
+        if (nbk >= AMAXBLK) {
+          afail(I, IMEXDS_ERR_CAPACITY);
+          ok = false;
+          break;
+        }
+        S.blo[nbk] = lo;
+        S.bhi[nbk] = hi;
+        nbk++;
+      }
+    }
+    S.n_blk = ok ? nbk : 0;
+    // per block cell: predicted width and tiny flag (block cells numbered block after block)
+    int c = 0;
+    for (int b = 0; b < S.n_blk && ok; ++b) {
+      if (S.bhi[b] - S.blo[b] + 1 > AMAXB || c + S.bhi[b] - S.blo[b] + 1 > AMAXBC) {
+        afail(I, IMEXDS_ERR_CAPACITY);
+        ok = false;
+        break;
+      }
+      for (int i = S.blo[b]; i <= S.bhi[b]; ++i, ++c) {
+        double wl = 0.0, wr = 0.0;
+        int tiny = 0;
+        for (int q = 0; q < S.n_pb; ++q) {
+          int g = S.pb[q];
+          if (g == i) wl = wf[q];
+          if (g == i + 1) wr = wf[q];
+          int k = (A.w[o + g - 1] < A.w[o + g]) ? g - 1 : g;
+          if (k == i) tiny = 1;
+        }
+        s_hp[c] = A.w[o + i] + (wr - wl) * S.dt;
+        s_tiny[c] = tiny;
+      }
+    }
+    if (rec && ok) {
+      rec->n_blk = S.n_blk;
+      for (int b = 0; b < S.n_blk; ++b) {
+        rec->blo[b] = S.blo[b];
+        rec->bhi[b] = S.bhi[b];
+      }
+    }
+    if (!ok) S.bad = 1;
+  }
+  __syncthreads();
+  if (S.bad) return;
+  M = S.M;
+  // (4) phase creation is not part of the differentiated scheme
+  // (5) explicit fluxes from U^n at every face outside the blocks, then the explicit update
+  for (int g = tid; g <= M; g += blockDim.x) {
+    if (face_in_block(S, g)) continue;
+    double f0, f1;
+    if (g == 0)
+      phys_flux_fast(c_fluid.ph[A.ph[o]], A.r[o], A.m[o], f0, f1);
+    else if (g == M)
+      phys_flux_fast(c_fluid.ph[A.ph[o + M - 1]], A.r[o + M - 1], A.m[o + M - 1], f0, f1);
+    else
+      hll_fast(c_fluid.ph[A.ph[o + g]], A.r[o + g - 1], A.m[o + g - 1], A.r[o + g], A.m[o + g], f0, f1);
+    A.F0[o + g] = f0;
+    A.F1[o + g] = f1;
+  }
+  __syncthreads();
+  for (int i = tid; i < M; i += blockDim.x) {
+    if (in_block(S, i)) continue;
+    const double wi = A.w[o + i];
+    if (wi == I.h) {
+      A.r[o + i] = __fma_rn(-S.lam, A.F0[o + i + 1] - A.F0[o + i], A.r[o + i]);
+      A.m[o + i] = __fma_rn(-S.lam, A.F1[o + i + 1] - A.F1[o + i], A.m[o + i]);
+    } else {
+      A.r[o + i] = (wi * A.r[o + i] - S.dt * (A.F0[o + i + 1] - A.F0[o + i])) / wi;
+      A.m[o + i] = (wi * A.m[o + i] - S.dt * (A.F1[o + i + 1] - A.F1[o + i])) / wi;
+    }
+  }
+  __syncthreads();
+  // (6) Algorithm 2 on every block, Part 2, boundary positions; (8) splits
+  if (tid == 0) {
+    bool ok = true;
+    int rc = 0, rp = 0, c = 0;
+    for (int b = 0; b < S.n_blk && ok; ++b) {
+      const int lo = S.blo[b], hi = S.bhi[b], nb = hi - lo + 1;
+      double orr[AMAXB], om[AMAXB], ow[AMAXB], wc[AMAXB + 1];
+      ok = dts_block(A, I, S, lo, hi, s_hp + c, s_tiny + c, A.F0[o + lo], A.F1[o + lo], A.F0[o + hi + 1],
+                     A.F1[o + hi + 1], rec, rc, rp, orr, om, ow, wc);
+      c += nb;
+      if (!ok) break;
+      for (int q = 0; q < nb; ++q) {
+        A.r[o + lo + q] = orr[q];
+        A.m[o + lo + q] = om[q];
+        A.w[o + lo + q] = ow[q];
+      }
+      for (int q = 1; q < nb; ++q)
+        if (A.fpb[o + lo + q]) A.fx[o + lo + q] += wc[q] * S.dt;
+    }
+    if (rec) rec->n_pbf = rp;
+    // splits of boundary cells wider than split_ratio h (Sec. 3.4), keeping fixed faces on the lattice
+    int nsp = 0;
+    if (ok) {
+      int Mi = S.M;
+      int last = -1;
+      for (int q = 0; q < S.n_pb && ok; ++q)
+        for (int s = 0; s < 2; ++s) {
+          int i = S.pb[q] - 1 + s + nsp;  // boundary faces shift by the cells inserted so far
+          if (i <= last) continue;
+          last = i;
+          bool lpb = A.fpb[o + i], rpb = A.fpb[o + i + 1];
+          if (!(lpb || rpb) || !(A.w[o + i] > c_opts.split_ratio * I.h)) continue;
+          double w1, w2;
+          int jc, cs;
+          if (!lpb) {
+            jc = A.fj[o + i] + 1;
+            w1 = I.h;
+            w2 = A.w[o + i] - I.h;
+            cs = 1;
+          } else if (!rpb) {
+            jc = A.fj[o + i + 1] - 1;
+            w2 = I.h;
+            w1 = A.w[o + i] - I.h;
+            cs = 2;
+          } else {
+            double xm = 0.5 * (A.fx[o + i] + A.fx[o + i + 1]);
+            jc = (int)llround((xm - I.xL) / I.h);
+            w1 = (I.xL + (double)jc * I.h) - A.fx[o + i];
+            w2 = A.w[o + i] - w1;
+            cs = 3;
+            if (!(w1 > 0.0) || !(w2 > 0.0)) continue;
+          }
+          if (Mi + 1 > I.cap || nsp >= AMAXEV) {
+            afail(I, IMEXDS_ERR_CAPACITY);
+            ok = false;
+            break;
+          }
+          list_open(A.w + o, A.r + o, A.m + o, A.ph + o, A.fpb + o, A.fj + o, A.fx + o, Mi, i + 1);
+          Mi++;
+          A.fpb[o + i + 1] = 0;
+          A.fj[o + i + 1] = jc;
+          A.fx[o + i + 1] = 0.0;
+          A.w[o + i] = w1;
+          A.w[o + i + 1] = w2;
+          if (rec) {
+            rec->sp_i[nsp] = i;
+            rec->sp_case[nsp] = cs;
+          }
+          nsp++;
+          last = i + 1;  // the new cell is not examined in this step
+        }
+      S.M = Mi;
+    }
+    if (rec) rec->n_split = nsp;
+    if (!ok) S.bad = 1;
+    I.M = S.M;
+    I.t = S.clipped ? t_end : I.t + S.dt;
+    I.done++;
+  }
+  __syncthreads();
+  M = S.M;
+  int badc = 0;
+  for (int i = tid; i < M; i += blockDim.x) {
+    double ri = A.r[o + i], mi = A.m[o + i], wi = A.w[o + i];
+    if (!(ri > 0.0) || !isfinite(ri) || !isfinite(mi) || !(wi > 0.0)) badc = 1;
+  }
+  badc = __syncthreads_or(badc);
+  if (tid == 0 && badc) afail(I, IMEXDS_ERR_NONPHYSICAL);
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------------------ reverse step
+// Transposed solve (I - Aw)^T mu = b for a block of nb cells (2 nb unknowns), partial pivoting.
+__device__ bool solve_T(int n, double (*Aw)[2 * AMAXB], const double* b, double* mu) {
+  double Mx[2 * AMAXB][2 * AMAXB + 1];
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) Mx[i][j] = (i == j ? 1.0 : 0.0) - Aw[j][i];
+    Mx[i][n] = b[i];
+  }
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(Mx[r][c]) > fabs(Mx[p][c])) p = r;
+    if (!(Mx[p][c] != 0.0) || !isfinite(Mx[p][c])) return false;
+    if (p != c)
+      for (int j = 0; j <= n; ++j) {
+        double t = Mx[p][j];
+        Mx[p][j] = Mx[c][j];
+        Mx[c][j] = t;
+      }
+    for (int r = c + 1; r < n; ++r) {
+      double f = Mx[r][c] / Mx[c][c];
+      if (f != 0.0)
+        for (int j = c; j <= n; ++j) Mx[r][j] -= f * Mx[c][j];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = Mx[i][n];
+    for (int j = i + 1; j < n; ++j) s -= Mx[i][j] * mu[j];
+    mu[i] = s / Mx[i][i];
+  }
+  return true;
+}
+
+// Adjoint of one block (thread 0): reads lambda of the outputs (lw, lr, lm, lx in post-merge numbering),
+// writes the accumulators of the block cells' U^n and widths, the face adjoints of F_left/F_right and
+// the boundary faces' positions, and returns the dt and tau contributions.
+__device__ __noinline__ bool block_adjoint(const ADev& A, AInst& I, const StepRec& R, int lo, int hi, int cell0,
+                                           int& pbf, double dt, double& lam_dt, double& lam_tau) {
+  const long long o = I.off;
+  const int nb = hi - lo + 1, n = 2 * nb;
+  double Ur[AMAXB], Um[AMAXB], Uw[AMAXB], Wr[AMAXB], Wm[AMAXB], hl[AMAXB], gv[AMAXB][2];
+  double Fv[AMAXB + 1][2], wcv[AMAXB + 1];
+  double DF[AMAXB + 1][3][5];  // per interior face: d(F0, F1, w)/d(W_l r, W_l m, W_r r, W_r m, tau)
+  int ph[AMAXB];
+  for (int q = 0; q < nb; ++q) {
+    Ur[q] = A.pr[o + lo + q];
+    Um[q] = A.pm[o + lo + q];
+    Uw[q] = A.pw[o + lo + q];
+    ph[q] = A.pph[o + lo + q];
+    Wr[q] = R.Wr[cell0 + q];
+    Wm[q] = R.Wm[cell0 + q];
+  }
+  Fv[0][0] = A.F0[o + lo];
+  Fv[0][1] = A.F1[o + lo];
+  Fv[nb][0] = A.F0[o + hi + 1];
+  Fv[nb][1] = A.F1[o + hi + 1];
+  wcv[0] = wcv[nb] = 0.0;
+  for (int q = 1; q < nb; ++q) {
+    Dual<5> rl = dvar<5>(Wr[q - 1], 0), ml = dvar<5>(Wm[q - 1], 1), rr = dvar<5>(Wr[q], 2), mr = dvar<5>(Wm[q], 3);
+    Dual<5> ta = dvar<5>(I.tau, 4);
+    Dual<5> f0, f1, wq;
+    if (A.pfpb[o + lo + q]) {
+      if (!pb_face_d<5>(c_fluid, ph[q - 1], ph[q], rl, ml, rr, mr, ta, R.ppl[pbf], R.ppr[pbf], f0, f1, wq))
+        return false;
+      pbf++;
+    } else {
+      hll_d<5>(c_fluid.ph[ph[q]], rl, ml, rr, mr, f0, f1);
+      wq = dconst<5>(0.0);
+    }
+    Fv[q][0] = f0.v;
+    Fv[q][1] = f1.v;
+    wcv[q] = wq.v;
+    for (int k = 0; k < 5; ++k) {
+      DF[q][0][k] = f0.d[k];
+      DF[q][1][k] = f1.d[k];
+      DF[q][2][k] = wq.d[k];
+    }
+  }
+  for (int q = 0; q < nb; ++q) {
+    hl[q] = Uw[q] + (wcv[q + 1] - wcv[q]) * dt;
+    gv[q][0] = (Uw[q] * Ur[q] - dt * (Fv[q + 1][0] - Fv[q][0])) / hl[q];
+    gv[q][1] = (Uw[q] * Um[q] - dt * (Fv[q + 1][1] - Fv[q][1])) / hl[q];
+  }
+  // lambda of the outputs
+  double lwq[AMAXB], lu[AMAXB][2], lxf[AMAXB + 1], lwc_out[AMAXB + 1];
+  for (int q = 0; q < nb; ++q) {
+    lwq[q] = A.lw[o + lo + q];
+    lu[q][0] = A.lr[o + lo + q];
+    lu[q][1] = A.lm[o + lo + q];
+  }
+  for (int q = 0; q <= nb; ++q) {
+    lxf[q] = (q > 0 && q < nb && A.pfpb[o + lo + q]) ? A.lx[o + lo + q] : 0.0;
+    lwc_out[q] = (q > 0 && q < nb) ? dt * (lwq[q - 1] - lwq[q] + lxf[q]) : 0.0;
+  }
+  // Aw = dg/dW and b = lambda_W
+  double Aw[2 * AMAXB][2 * AMAXB], b[2 * AMAXB], mu[2 * AMAXB];
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) Aw[i][j] = 0.0;
+    b[i] = lu[i >> 1][i & 1];
+  }
+  for (int q = 1; q < nb; ++q) {
+    const int il = q - 1, ir = q;
+    const double cl = dt / hl[il], cr = dt / hl[ir];
+    for (int c = 0; c < 2; ++c)
+      for (int k = 0; k < 4; ++k) {
+        const int col = 2 * (il + (k >> 1)) + (k & 1);  // k 0,1 -> W_il; 2,3 -> W_ir
+        Aw[2 * il + c][col] += -cl * DF[q][c][k] - gv[il][c] * cl * DF[q][2][k];
+        Aw[2 * ir + c][col] += cr * DF[q][c][k] + gv[ir][c] * cr * DF[q][2][k];
+      }
+    for (int k = 0; k < 4; ++k) b[2 * (il + (k >> 1)) + (k & 1)] += lwc_out[q] * DF[q][2][k];
+  }
+  if (!solve_T(n, Aw, b, mu)) return false;
+  // parameter adjoints
+  for (int q = 0; q < nb; ++q) {
+    const double s = Uw[q] / hl[q];
+    A.nr[o + lo + q] += s * mu[2 * q];
+    A.nm[o + lo + q] += s * mu[2 * q + 1];
+    A.nw[o + lo + q] += lwq[q] + (mu[2 * q] * (Ur[q] - gv[q][0]) + mu[2 * q + 1] * (Um[q] - gv[q][1])) / hl[q];
+    const double dwc = wcv[q + 1] - wcv[q];
+    lam_dt += (mu[2 * q] * (-(Fv[q + 1][0] - Fv[q][0]) - gv[q][0] * dwc) +
+               mu[2 * q + 1] * (-(Fv[q + 1][1] - Fv[q][1]) - gv[q][1] * dwc)) /
+                  hl[q] +
+              lwq[q] * dwc;
+  }
+  A.LF0[o + lo] += dt / hl[0] * mu[0];
+  A.LF1[o + lo] += dt / hl[0] * mu[1];
+  A.LF0[o + hi + 1] += -dt / hl[nb - 1] * mu[2 * nb - 2];
+  A.LF1[o + hi + 1] += -dt / hl[nb - 1] * mu[2 * nb - 1];
+  for (int q = 1; q < nb; ++q) {
+    const int il = q - 1, ir = q;
+    const double cl = dt / hl[il], cr = dt / hl[ir];
+    double lf0 = -cl * mu[2 * il] + cr * mu[2 * ir];
+    double lf1 = -cl * mu[2 * il + 1] + cr * mu[2 * ir + 1];
+    double lwc = -cl * (mu[2 * il] * gv[il][0] + mu[2 * il + 1] * gv[il][1]) +
+                 cr * (mu[2 * ir] * gv[ir][0] + mu[2 * ir + 1] * gv[ir][1]) + lwc_out[q];
+    lam_tau += lf0 * DF[q][0][4] + lf1 * DF[q][1][4] + lwc * DF[q][2][4];
+    if (A.pfpb[o + lo + q]) {
+      lam_dt += lxf[q] * wcv[q];
+      A.nx[o + lo + q] += lxf[q];
+    }
+  }
+  return true;
+}
+
+__device__ void rev_step(const ADev& A, AInst& I, SharedStep& S, int slot, const StepRec& R) {
+  const long long o = I.off;
+  const int tid = threadIdx.x;
+  const long long to = (long long)slot * A.stride + o;
+  const int Mn = A.tp_M[(long long)slot * A.n_inst + (int)(&I - A.I)];
+  const double dt = R.dt;
+  // (a) splits^T on the adjoint list
+  if (tid == 0) {
+    int Mc = I.M;
+    for (int q = R.n_split - 1; q >= 0; --q) {
+      const int i = R.sp_i[q];
+      A.lr[o + i] += A.lr[o + i + 1];
+      A.lm[o + i] += A.lm[o + i + 1];
+      if (R.sp_case[q] == 1) {
+        A.lw[o + i] = A.lw[o + i + 1];
+      } else if (R.sp_case[q] == 3) {
+        A.lx[o + i] += -A.lw[o + i] + A.lw[o + i + 1];
+        A.lw[o + i] = A.lw[o + i + 1];
+      }
+      lam_erase(A.lw + o, A.lr + o, A.lm + o, A.lx + o, Mc, i + 1);
+      Mc--;
+    }
+    S.M = Mc;  // post-merge count
+    S.n_blk = R.n_blk;
+    for (int b = 0; b < R.n_blk; ++b) {
+      S.blo[b] = R.blo[b];
+      S.bhi[b] = R.bhi[b];
+    }
+    S.bad = 0;
+  }
+  __syncthreads();
+  // (b) the post-merge list: the taped pre-step list with the recorded merges applied
+  cta_copy_d(A.pw + o, A.tp_w + to, Mn);
+  cta_copy_d(A.pr + o, A.tp_r + to, Mn);
+  cta_copy_d(A.pm + o, A.tp_m + to, Mn);
+  cta_copy_b(A.pph + o, A.tp_ph + to, Mn);
+  cta_copy_b(A.pfpb + o, A.tp_fpb + to, Mn + 1);
+  __syncthreads();
+  if (tid == 0) {
+    int Mc = Mn;
+    for (int q = 0; q < R.n_merge; ++q) {
+      const int a = R.mg_a[q], b = R.mg_b[q];
+      const double* v = R.mg_v[q];
+      double wm = v[0] + v[3];
+      A.pr[o + a] = (v[0] * v[1] + v[3] * v[4]) / wm;
+      A.pm[o + a] = (v[0] * v[2] + v[3] * v[5]) / wm;
+      A.pw[o + a] = wm;
+      list_erase(A.pw + o, A.pr + o, A.pm + o, A.pph + o, A.pfpb + o, nullptr, nullptr, Mc, b);
+      Mc--;
+    }
+    if (Mc != S.M) S.bad = 1;
+  }
+  __syncthreads();
+  if (S.bad) {
+    if (tid == 0) afail(I, IMEXDS_ERR_STATE);
+    __syncthreads();
+    return;
+  }
+  const int M = S.M;
+  // (c) zero the accumulators; explicit fluxes at U^n (post-merge)
+  cta_zero(A.nw + o, M);
+  cta_zero(A.nr + o, M);
+  cta_zero(A.nm + o, M);
+  cta_zero(A.nx + o, M + 1);
+  cta_zero(A.LF0 + o, M + 1);
+  cta_zero(A.LF1 + o, M + 1);
+  for (int g = tid; g <= M; g += blockDim.x) {
+    if (face_in_block(S, g)) continue;
+    double f0, f1;
+    if (g == 0)
+      phys_flux_fast(c_fluid.ph[A.pph[o]], A.pr[o], A.pm[o], f0, f1);
+    else if (g == M)
+      phys_flux_fast(c_fluid.ph[A.pph[o + M - 1]], A.pr[o + M - 1], A.pm[o + M - 1], f0, f1);
+    else
+      hll_fast(c_fluid.ph[A.pph[o + g]], A.pr[o + g - 1], A.pm[o + g - 1], A.pr[o + g], A.pm[o + g], f0, f1);
+    A.F0[o + g] = f0;
+    A.F1[o + g] = f1;
+  }
+  __syncthreads();
+  // (d) blocks (thread 0)
+  double lam_dt = 0.0;
+  if (tid == 0) {
+    int cell0 = 0, pbf = 0;
+    double ltau = 0.0;
+    for (int b = 0; b < S.n_blk; ++b) {
+      if (!block_adjoint(A, I, R, S.blo[b], S.bhi[b], cell0, pbf, dt, lam_dt, ltau)) {
+        S.bad = 1;
+        break;
+      }
+      cell0 += S.bhi[b] - S.blo[b] + 1;
+    }
+    I.lam_tau += ltau;
+  }
+  __syncthreads();
+  if (S.bad) {
+    if (tid == 0) afail(I, IMEXDS_ERR_STATE);
+    __syncthreads();
+    return;
+  }
+  // (e) explicit sweep^T: face adjoints from the explicit cells, then the face Jacobians at U^n
+  for (int g = tid; g <= M; g += blockDim.x) {
+    if (face_in_block(S, g)) continue;
+    double l0 = A.LF0[o + g], l1 = A.LF1[o + g];
+    if (g > 0 && !in_block(S, g - 1)) {
+      const double c = dt / A.pw[o + g - 1];
+      l0 -= c * A.lr[o + g - 1];
+      l1 -= c * A.lm[o + g - 1];
+    }
+    if (g < M && !in_block(S, g)) {
+      const double c = dt / A.pw[o + g];
+      l0 += c * A.lr[o + g];
+      l1 += c * A.lm[o + g];
+    }
+    double cl0 = 0.0, cl1 = 0.0, cr0 = 0.0, cr1 = 0.0;
+    if (g == 0 || g == M) {
+      const int i = (g == 0) ? 0 : M - 1;
+      Dual<2> rr = dvar<2>(A.pr[o + i], 0), mm = dvar<2>(A.pm[o + i], 1), f0, f1;
+      phys_flux_d<2>(c_fluid.ph[A.pph[o + i]], rr, mm, f0, f1);
+      const double a0 = l0 * f0.d[0] + l1 * f1.d[0], a1 = l0 * f0.d[1] + l1 * f1.d[1];
+      if (g == 0) {
+        cr0 = a0;
+        cr1 = a1;
+      } else {
+        cl0 = a0;
+        cl1 = a1;
+      }
+    } else {
+      Dual<4> rl = dvar<4>(A.pr[o + g - 1], 0), ml = dvar<4>(A.pm[o + g - 1], 1);
+      Dual<4> rr = dvar<4>(A.pr[o + g], 2), mr = dvar<4>(A.pm[o + g], 3), f0, f1;
+      hll_d<4>(c_fluid.ph[A.pph[o + g]], rl, ml, rr, mr, f0, f1);
+      cl0 = l0 * f0.d[0] + l1 * f1.d[0];
+      cl1 = l0 * f0.d[1] + l1 * f1.d[1];
+      cr0 = l0 * f0.d[2] + l1 * f1.d[2];
+      cr1 = l0 * f0.d[3] + l1 * f1.d[3];
+    }
+    A.CL0[o + g] = cl0;
+    A.CL1[o + g] = cl1;
+    A.CR0[o + g] = cr0;
+    A.CR1[o + g] = cr1;
+  }
+  double ldt_part = 0.0;
+  for (int i = tid; i < M; i += blockDim.x) {
+    if (in_block(S, i)) continue;
+    const double wi = A.pw[o + i], lr = A.lr[o + i], lm = A.lm[o + i];
+    const double dF = (A.F0[o + i + 1] - A.F0[o + i]) * lr + (A.F1[o + i + 1] - A.F1[o + i]) * lm;
+    A.nr[o + i] += lr;
+    A.nm[o + i] += lm;
+    A.nw[o + i] += A.lw[o + i] + dt * dF / (wi * wi);
+    ldt_part -= dF / wi;
+  }
+  __syncthreads();
+  // (f) gather the face contributions into the cells (faces inside a block contribute nothing here)
+  for (int i = tid; i < M; i += blockDim.x) {
+    double a0 = 0.0, a1 = 0.0;
+    if (!face_in_block(S, i)) {
+      a0 += A.CR0[o + i];
+      a1 += A.CR1[o + i];
+    }
+    if (!face_in_block(S, i + 1)) {
+      a0 += A.CL0[o + i + 1];
+      a1 += A.CL1[o + i + 1];
+    }
+    A.nr[o + i] += a0;
+    A.nm[o + i] += a1;
+  }
+  double tot = cta_sum(S, ldt_part);
+  __syncthreads();
+  // (g) merges^T and (h) dt^T (thread 0)
+  if (tid == 0) {
+    lam_dt += tot;
+    int Mc = M;
+    for (int q = R.n_merge - 1; q >= 0; --q) {
+      const int a = R.mg_a[q], b = R.mg_b[q];
+      const double* v = R.mg_v[q];
+      const double wm = v[0] + v[3];
+      const double rm = (v[0] * v[1] + v[3] * v[4]) / wm, mm = (v[0] * v[2] + v[3] * v[5]) / wm;
+      const double Lw = A.nw[o + a], Lr = A.nr[o + a], Lm = A.nm[o + a];
+      lam_open(A.nw + o, A.nr + o, A.nm + o, A.nx + o, Mc, b);
+      Mc++;
+      A.nx[o + b] = 0.0;
+      A.nr[o + a] = Lr * v[0] / wm;
+      A.nm[o + a] = Lm * v[0] / wm;
+      A.nw[o + a] = Lw + (Lr * (v[1] - rm) + Lm * (v[2] - mm)) / wm;
+      A.nr[o + b] = Lr * v[3] / wm;
+      A.nm[o + b] = Lm * v[3] / wm;
+      A.nw[o + b] = Lw + (Lr * (v[4] - rm) + Lm * (v[5] - mm)) / wm;
+    }
+    if (R.clipped) {
+      I.lam_t = -lam_dt;
+    } else {
+      lam_dt += I.lam_t;
+      const int k = R.kmax;
+      const double rk = A.tp_r[to + k], mk = A.tp_m[to + k];
+      const double S_ = fabs(mk / rk) + c_fluid.ph[A.tp_ph[to + k]].a;
+      const double lS = -lam_dt * dt / S_;
+      const double sg = (mk > 0.0) ? 1.0 : ((mk < 0.0) ? -1.0 : 0.0);
+      A.nm[o + k] += lS * sg / rk;
+      A.nr[o + k] += -lS * sg * mk / (rk * rk);
+    }
+    I.M = Mc;
+    if (Mc != Mn) afail(I, IMEXDS_ERR_STATE);
+  }
+  __syncthreads();
+  // lambda^n <- accumulators
+  cta_copy_d(A.lw + o, A.nw + o, Mn);
+  cta_copy_d(A.lr + o, A.nr + o, Mn);
+  cta_copy_d(A.lm + o, A.nm + o, Mn);
+  cta_copy_d(A.lx + o, A.nx + o, Mn + 1);
+  __syncthreads();
+}
+
+__device__ void save_list(const ADev& A, AInst& I, long long dst_off, double* w, double* r, double* m,
+                          unsigned char* ph, unsigned char* fpb, int* fj, double* fx) {
+  const long long o = I.off;
+  cta_copy_d(w + dst_off, A.w + o, I.M);
+  cta_copy_d(r + dst_off, A.r + o, I.M);
+  cta_copy_d(m + dst_off, A.m + o, I.M);
+  cta_copy_b(ph + dst_off, A.ph + o, I.M);
+  if (fpb) cta_copy_b(fpb + dst_off, A.fpb + o, I.M + 1);
+  if (fj) cta_copy_i(fj + dst_off, A.fj + o, I.M + 1);
+  if (fx) cta_copy_d(fx + dst_off, A.fx + o, I.M + 1);
+}
+__device__ void load_list(const ADev& A, AInst& I, long long src_off, int M) {
+  const long long o = I.off;
+  cta_copy_d(A.w + o, A.ck_w + src_off, M);
+  cta_copy_d(A.r + o, A.ck_r + src_off, M);
+  cta_copy_d(A.m + o, A.ck_m + src_off, M);
+  cta_copy_b(A.ph + o, A.ck_ph + src_off, M);
+  cta_copy_b(A.fpb + o, A.ck_fpb + src_off, M + 1);
+  cta_copy_i(A.fj + o, A.ck_fj + src_off, M + 1);
+  cta_copy_d(A.fx + o, A.ck_fx + src_off, M + 1);
+}
+
+// The whole adjoint of one instance: replay with checkpoints, then the segments in reverse.
+__global__ void __launch_bounds__(ATHREADS) k_adjoint(ADev A) {
+  const int ii = blockIdx.x;
+  if (ii >= A.n_inst) return;
+  AInst& I = A.I[ii];
+  __shared__ SharedStep S;
+  __shared__ int s_go;
+  __shared__ double s_tend;
+  // phase A: replay from the initial states, a checkpoint every k steps
+  int n = 0;
+  for (;;) {
+    if (n % A.k == 0) {
+      const int c = n / A.k;
+      if (c >= A.n_ck) {
+        if (threadIdx.x == 0) afail(I, IMEXDS_ERR_CAPACITY);
+        __syncthreads();
+        break;
+      }
+      save_list(A, I, (long long)c * A.stride + I.off, A.ck_w, A.ck_r, A.ck_m, A.ck_ph, A.ck_fpb, A.ck_fj, A.ck_fx);
+      if (threadIdx.x == 0) {
+        ACk& h = A.ck_h[(long long)c * A.n_inst + ii];
+        h.done = I.done;
+        h.M = I.M;
+        h.status = I.status;
+        h.pc = I.pc;
+        h.t = I.t;
+      }
+    }
+    if (threadIdx.x == 0) {
+      double te = -1.0;
+      s_go = prog_next(A, I, te) ? 1 : 0;
+      s_tend = te;
+    }
+    __syncthreads();
+    if (!s_go) break;
+    fwd_step(A, I, S, s_tend, nullptr, 0);
+    ++n;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) I.nsteps = n;
+  save_list(A, I, I.off, A.fin_w, A.fin_r, A.fin_m, A.fin_ph, nullptr, nullptr, nullptr);
+  if (threadIdx.x == 0) A.fin_M[ii] = I.M;
+  __syncthreads();
+  if (I.status) return;
+  if (I.M != I.M_seed) {
+    if (threadIdx.x == 0) afail(I, IMEXDS_ERR_STATE);
+    return;
+  }
+  // phase B: segments from last to first
+  const int n_seg = (n + A.k - 1) / A.k;
+  for (int sg = n_seg - 1; sg >= 0; --sg) {
+    const int first = sg * A.k, last = min(n, first + A.k) - 1;
+    const ACk& h = A.ck_h[(long long)sg * A.n_inst + ii];
+    const int Mlam = I.M;  // the adjoint list length (cells of the state after step last)
+    __syncthreads();
+    load_list(A, I, (long long)sg * A.stride + I.off, h.M);
+    if (threadIdx.x == 0) {
+      I.M = h.M;
+      I.t = h.t;
+      I.pc = h.pc;
+      I.done = h.done;
+    }
+    __syncthreads();
+    for (int s = first; s <= last; ++s) {
+      if (threadIdx.x == 0) {
+        double te = -1.0;
+        s_go = prog_next(A, I, te) ? 1 : 0;
+        s_tend = te;
+      }
+      __syncthreads();
+      if (!s_go) {
+        if (threadIdx.x == 0) afail(I, IMEXDS_ERR_STATE);
+        __syncthreads();
+        return;
+      }
+      fwd_step(A, I, S, s_tend, A.rec + (long long)(s - first) * A.n_inst + ii, s - first);
+      if (I.status) return;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) I.M = Mlam;
+    __syncthreads();
+    for (int s = last; s >= first; --s) {
+      rev_step(A, I, S, s - first, A.rec[(long long)(s - first) * A.n_inst + ii]);
+      if (I.status) return;
+    }
+  }
+}
+
+}  // namespace adj
+}  // namespace imexds

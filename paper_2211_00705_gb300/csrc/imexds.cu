@@ -1411,6 +1411,7 @@ __global__ void k_count_active(Dev d, int n_inst) {
 
 }  // namespace
 #include "noalloc.cuh"
+#include "adjoint.cuh"
 namespace {
 
 // ---------------------------------------------------------------------------------------- host side
@@ -1450,6 +1451,19 @@ struct imexds_ctx {
   double kt_ms[6] = {0, 0, 0, 0, 0, 0};
   long long kt_n[6] = {0, 0, 0, 0, 0, 0};
   cudaEvent_t gev[2] = {nullptr, nullptr};
+  // the initial cell lists of the last imexds_set_states and the calls made since (the adjoint replays them)
+  std::vector<int> u0_off;
+  std::vector<double> u0_w, u0_r, u0_m;
+  std::vector<uint8_t> u0_ph;
+  double u0_t = 0.0;
+  std::vector<int> prog_k;
+  std::vector<double> prog_a;
+  // adjoint buffers (kept between calls, grown on demand)
+  int adj_k = 64;
+  size_t adj_bytes = 0;
+  void* adj_mem = nullptr;
+  double adj_ms = 0.0, adj_replay_err = 0.0;
+  long long adj_cell_steps = 0;
 };
 
 namespace {
@@ -1813,6 +1827,7 @@ void imexds_destroy(imexds_ctx* c) {
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   if (c->join_ev) cudaEventDestroy(c->join_ev);
   if (c->h_active) cudaFreeHost(c->h_active);
+  if (c->adj_mem) cudaFree(c->adj_mem);
   delete c;
 }
 
@@ -2031,6 +2046,15 @@ imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double*
   c->zone_off = zone_off;
   c->zone_cap = zone_cap;
   c->loaded = true;
+  const int ncell = off[n];
+  c->u0_off.assign(off, off + n + 1);
+  c->u0_w.assign(widths, widths + ncell);
+  c->u0_r.assign(rho, rho + ncell);
+  c->u0_m.assign(m, m + ncell);
+  c->u0_ph.assign(phase, phase + ncell);
+  c->u0_t = t0;
+  c->prog_k.clear();
+  c->prog_a.clear();
   return IMEXDS_OK;
 }
 
@@ -2057,7 +2081,12 @@ imexds_status imexds_step(imexds_ctx* c, int32_t n_steps) {
   int gb = c->n_inst;
   k_init_dt<<<gb, 256, 0, c->stream>>>(c->d, c->n_inst);
   c->launches += 1;
-  return run_steps(c, n_steps, false);
+  imexds_status st = run_steps(c, n_steps, false);
+  if (st == IMEXDS_OK && n_steps > 0) {
+    c->prog_k.push_back(0);
+    c->prog_a.push_back((double)n_steps);
+  }
+  return st;
 }
 
 imexds_status imexds_run_to(imexds_ctx* c, double t_end) {
@@ -2070,6 +2099,10 @@ imexds_status imexds_run_to(imexds_ctx* c, double t_end) {
   c->launches += 1;
   imexds_status st = run_steps(c, kRunToMaxSteps, true);
   if (st == IMEXDS_OK && *c->h_active != 0) return IMEXDS_ERR_TIMEOUT;
+  if (st == IMEXDS_OK) {
+    c->prog_k.push_back(1);
+    c->prog_a.push_back(t_end);
+  }
   return st;
 }
 
@@ -2161,6 +2194,8 @@ imexds_status imexds_reset(imexds_ctx* c) {
   CK(cudaMemcpyAsync(d.zones, sv.zones, sizeof(Zone) * c->n_zone_slots, cudaMemcpyDeviceToDevice, c->stream));
   CK(cudaMemcpyAsync(d.inst, sv.inst, sizeof(Inst) * c->n_inst, cudaMemcpyDeviceToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  c->prog_k.clear();
+  c->prog_a.clear();
   return IMEXDS_OK;
 }
 
@@ -2293,6 +2328,254 @@ imexds_status imexds_get_stats(imexds_ctx* c, int64_t* stats) {
     for (int k = 0; k < N_STATS; ++k) stats[10 * i + k] = hi[i].stats[k];
     stats[10 * i + 9] = c->launches;
   }
+  return IMEXDS_OK;
+}
+
+imexds_status imexds_set_adjoint_checkpoint(imexds_ctx* c, int32_t every) {
+  if (!c || every < 1) return IMEXDS_ERR_ARG;
+  c->adj_k = every;
+  return IMEXDS_OK;
+}
+
+imexds_status imexds_adjoint(imexds_ctx* c, const double* dJ_dw_T, const double* dJ_drho_T, const double* dJ_dm_T,
+                             double* dJ_dw0, double* dJ_drho0, double* dJ_dm0, double* dJ_dtau,
+                             int32_t* inst_status) {
+  using namespace imexds::adj;
+  if (!c || !dJ_drho_T || !dJ_dm_T || !dJ_drho0 || !dJ_dm0 || !dJ_dtau) return IMEXDS_ERR_ARG;
+  if (!c->loaded || c->u0_off.empty()) return IMEXDS_ERR_STATE;
+  const int n = c->n_inst;
+  // the last forward: final cell counts and steps per instance
+  std::vector<int32_t> MT(n);
+  imexds_status st = imexds_cell_counts(c, MT.data());
+  if (st) return st;
+  std::vector<int64_t> stats((size_t)n * 10);
+  st = imexds_get_stats(c, stats.data());
+  if (st) return st;
+  long long max_steps = 0;
+  for (int i = 0; i < n; ++i) max_steps = std::max<long long>(max_steps, stats[10 * i]);
+  const int k = c->adj_k;
+  const int n_ck = (int)(max_steps / k) + 1;
+  // layout: instance i owns slots [off_i, off_i + cap_i + 1) of every per-cell / per-face array
+  std::vector<long long> offs(n);
+  std::vector<int> caps(n);
+  long long stride = 0;
+  for (int i = 0; i < n; ++i) {
+    const int M0 = c->u0_off[i + 1] - c->u0_off[i];
+    caps[i] = std::max(M0, (int)MT[i]) + ACAP_PAD;
+    offs[i] = stride;
+    stride += caps[i] + 1;
+  }
+  const int n_prog = (int)c->prog_k.size();
+  // one device allocation carved into the arrays
+  const size_t nd_cell = 26, nb_cell = 5, ni_cell = 1;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  size_t bytes = 0;
+  bytes += al(sizeof(AInst) * n) + al(sizeof(int) * (n_prog + 1)) + al(sizeof(double) * (n_prog + 1));
+  bytes += nd_cell * al(sizeof(double) * stride) + nb_cell * al(stride) + ni_cell * al(sizeof(int) * stride);
+  bytes += 4 * al(sizeof(double) * stride * n_ck) + 2 * al(stride * n_ck) + al(sizeof(int) * stride * n_ck);
+  bytes += al(sizeof(ACk) * (size_t)n * n_ck) + al(sizeof(int) * n);
+  bytes += 3 * al(sizeof(double) * stride * k) + 2 * al(stride * k) + al(sizeof(int) * (size_t)n * k);
+  bytes += al(sizeof(StepRec) * (size_t)n * k);
+  if (bytes > c->adj_bytes) {
+    if (c->adj_mem) cudaFree(c->adj_mem);
+    c->adj_mem = nullptr;
+    c->adj_bytes = 0;
+    CK(cudaMalloc(&c->adj_mem, bytes));
+    c->adj_bytes = bytes;
+  }
+  char* p = (char*)c->adj_mem;
+  auto take = [&](size_t b) {
+    char* q = p;
+    p += al(b);
+    return (void*)q;
+  };
+  ADev A{};
+  A.n_inst = n;
+  A.k = k;
+  A.n_ck = n_ck;
+  A.n_prog = n_prog;
+  A.stride = stride;
+  A.I = (AInst*)take(sizeof(AInst) * n);
+  int* d_pk = (int*)take(sizeof(int) * (n_prog + 1));
+  double* d_pa = (double*)take(sizeof(double) * (n_prog + 1));
+  A.pk = d_pk;
+  A.pa = d_pa;
+  double** dcell[26] = {&A.w,  &A.r,  &A.m,  &A.fx, &A.F0, &A.F1, &A.LF0, &A.LF1, &A.CL0,
+                        &A.CL1, &A.CR0, &A.CR1, &A.pw, &A.pr, &A.pm, &A.lw,  &A.lr,  &A.lm,
+                        &A.lx, &A.nw, &A.nr, &A.nm, &A.nx, &A.fin_w, &A.fin_r, &A.fin_m};
+  for (auto q : dcell) *q = (double*)take(sizeof(double) * stride);
+  unsigned char** bcell[5] = {&A.ph, &A.fpb, &A.pph, &A.pfpb, &A.fin_ph};
+  for (auto q : bcell) *q = (unsigned char*)take(stride);
+  A.fj = (int*)take(sizeof(int) * stride);
+  A.ck_w = (double*)take(sizeof(double) * stride * n_ck);
+  A.ck_r = (double*)take(sizeof(double) * stride * n_ck);
+  A.ck_m = (double*)take(sizeof(double) * stride * n_ck);
+  A.ck_fx = (double*)take(sizeof(double) * stride * n_ck);
+  A.ck_ph = (unsigned char*)take(stride * n_ck);
+  A.ck_fpb = (unsigned char*)take(stride * n_ck);
+  A.ck_fj = (int*)take(sizeof(int) * stride * n_ck);
+  A.ck_h = (ACk*)take(sizeof(ACk) * (size_t)n * n_ck);
+  A.fin_M = (int*)take(sizeof(int) * n);
+  A.tp_w = (double*)take(sizeof(double) * stride * k);
+  A.tp_r = (double*)take(sizeof(double) * stride * k);
+  A.tp_m = (double*)take(sizeof(double) * stride * k);
+  A.tp_ph = (unsigned char*)take(stride * k);
+  A.tp_fpb = (unsigned char*)take(stride * k);
+  A.tp_M = (int*)take(sizeof(int) * (size_t)n * k);
+  A.rec = (StepRec*)take(sizeof(StepRec) * (size_t)n * k);
+  // initial lists (faces as in imexds_set_states: positions accumulate from the last fixed face) and seeds
+  std::vector<double> hw(stride, 0.0), hr(stride, 0.0), hm(stride, 0.0), hfx(stride, 0.0);
+  std::vector<unsigned char> hph(stride, 0), hfpb(stride, 0);
+  std::vector<int> hfj(stride, 0);
+  std::vector<double> lw(stride, 0.0), lr(stride, 0.0), lm(stride, 0.0);
+  std::vector<AInst> hI(n);
+  int oT = 0;
+  for (int i = 0; i < n; ++i) {
+    const int a = c->u0_off[i], M0 = c->u0_off[i + 1] - a;
+    const long long o = offs[i];
+    const double h = (c->xR[i] - c->xL[i]) / c->N[i];
+    long jfix = 0;
+    double part = 0.0;
+    hfpb[o] = 0;
+    hfj[o] = 0;
+    for (int q = 0; q < M0; ++q) {
+      hw[o + q] = c->u0_w[a + q];
+      hr[o + q] = c->u0_r[a + q];
+      hm[o + q] = c->u0_m[a + q];
+      hph[o + q] = c->u0_ph[a + q];
+      part += c->u0_w[a + q];
+      if (q + 1 < M0 && c->u0_ph[a + q + 1] != c->u0_ph[a + q]) {
+        hfpb[o + q + 1] = 1;
+        hfx[o + q + 1] = c->xL[i] + (double)jfix * h + part;
+      } else {
+        long j = jfix + std::lround(part / h);
+        hfj[o + q + 1] = (int)j;
+        jfix = j;
+        part = 0.0;
+      }
+    }
+    for (int q = 0; q < M0; ++q)  // a cell with two fixed faces is a whole number of lattice cells
+      if (!hfpb[o + q] && !hfpb[o + q + 1]) hw[o + q] = (double)(hfj[o + q + 1] - hfj[o + q]) * h;
+    for (int q = 0; q < MT[i]; ++q, ++oT) {
+      lw[o + q] = dJ_dw_T ? dJ_dw_T[oT] : 0.0;
+      lr[o + q] = dJ_drho_T[oT];
+      lm[o + q] = dJ_dm_T[oT];
+    }
+    AInst& I = hI[i];
+    I = AInst{};
+    I.off = o;
+    I.cap = caps[i];
+    I.M = M0;
+    I.M_seed = MT[i];
+    I.h = h;
+    I.xL = c->xL[i];
+    I.tau = c->tau[i];
+    I.t = c->u0_t;
+  }
+  cudaStream_t sm = c->stream;
+  st = set_ctrl(c, 0.0, 0);
+  if (st) return st;
+  CK(cudaMemcpyAsync(A.I, hI.data(), sizeof(AInst) * n, cudaMemcpyHostToDevice, sm));
+  if (n_prog) {
+    CK(cudaMemcpyAsync(d_pk, c->prog_k.data(), sizeof(int) * n_prog, cudaMemcpyHostToDevice, sm));
+    CK(cudaMemcpyAsync(d_pa, c->prog_a.data(), sizeof(double) * n_prog, cudaMemcpyHostToDevice, sm));
+  }
+  CK(cudaMemcpyAsync(A.w, hw.data(), sizeof(double) * stride, cudaMemcpyHostToDevice, sm));
+  CK(cudaMemcpyAsync(A.r, hr.data(), sizeof(double) * stride, cudaMemcpyHostToDevice, sm));
+  CK(cudaMemcpyAsync(A.m, hm.data(), sizeof(double) * stride, cudaMemcpyHostToDevice, sm));
+  CK(cudaMemcpyAsync(A.fx, hfx.data(), sizeof(double) * stride, cudaMemcpyHostToDevice, sm));
+  CK(cudaMemcpyAsync(A.ph, hph.data(), stride, cudaMemcpyHostToDevice, sm));
+  CK(cudaMemcpyAsync(A.fpb, hfpb.data(), stride, cudaMemcpyHostToDevice, sm));
+  CK(cudaMemcpyAsync(A.fj, hfj.data(), sizeof(int) * stride, cudaMemcpyHostToDevice, sm));
+  CK(cudaMemcpyAsync(A.lw, lw.data(), sizeof(double) * stride, cudaMemcpyHostToDevice, sm));
+  CK(cudaMemcpyAsync(A.lr, lr.data(), sizeof(double) * stride, cudaMemcpyHostToDevice, sm));
+  CK(cudaMemcpyAsync(A.lm, lm.data(), sizeof(double) * stride, cudaMemcpyHostToDevice, sm));
+  CK(cudaMemsetAsync(A.lx, 0, sizeof(double) * stride, sm));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, sm));
+  k_adjoint<<<n, ATHREADS, 0, sm>>>(A);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(e1, sm));
+  // results
+  CK(cudaMemcpyAsync(hI.data(), A.I, sizeof(AInst) * n, cudaMemcpyDeviceToHost, sm));
+  CK(cudaMemcpyAsync(lw.data(), A.lw, sizeof(double) * stride, cudaMemcpyDeviceToHost, sm));
+  CK(cudaMemcpyAsync(lr.data(), A.lr, sizeof(double) * stride, cudaMemcpyDeviceToHost, sm));
+  CK(cudaMemcpyAsync(lm.data(), A.lm, sizeof(double) * stride, cudaMemcpyDeviceToHost, sm));
+  std::vector<double> lx(stride);
+  CK(cudaMemcpyAsync(lx.data(), A.lx, sizeof(double) * stride, cudaMemcpyDeviceToHost, sm));
+  std::vector<double> fw(stride), fr(stride), fm(stride);
+  std::vector<int> fM(n);
+  CK(cudaMemcpyAsync(fw.data(), A.fin_w, sizeof(double) * stride, cudaMemcpyDeviceToHost, sm));
+  CK(cudaMemcpyAsync(fr.data(), A.fin_r, sizeof(double) * stride, cudaMemcpyDeviceToHost, sm));
+  CK(cudaMemcpyAsync(fm.data(), A.fin_m, sizeof(double) * stride, cudaMemcpyDeviceToHost, sm));
+  CK(cudaMemcpyAsync(fM.data(), A.fin_M, sizeof(int) * n, cudaMemcpyDeviceToHost, sm));
+  CK(cudaStreamSynchronize(sm));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->adj_ms = ms;
+  // the replay must reproduce the last forward: same steps, same cells, states to round-off
+  std::vector<int32_t> toff(n + 1);
+  std::vector<double> gw(oT), gr(oT), gm(oT), gt(n);
+  std::vector<uint8_t> gph(oT);
+  std::vector<int32_t> gst(n);
+  st = imexds_get_states(c, toff.data(), gw.data(), gr.data(), gm.data(), gph.data(), gt.data(), gst.data());
+  if (st) return st;
+  double err = 0.0;
+  long long cell_steps = 0;
+  for (int i = 0; i < n; ++i) {
+    AInst& I = hI[i];
+    if (I.status == 0 && (I.nsteps != stats[10 * i] || fM[i] != MT[i])) I.status = IMEXDS_ERR_STATE;
+    if (I.status) continue;
+    double rmax = 0.0, dr = 0.0, dm = 0.0, dw = 0.0;
+    for (int q = 0; q < MT[i]; ++q) rmax = std::max(rmax, std::fabs(gr[toff[i] + q]));
+    for (int q = 0; q < MT[i]; ++q) {
+      const long long o = offs[i] + q;
+      dr = std::max(dr, std::fabs(fr[o] - gr[toff[i] + q]));
+      dm = std::max(dm, std::fabs(fm[o] - gm[toff[i] + q]));
+      dw = std::max(dw, std::fabs(fw[o] - gw[toff[i] + q]) / ((c->xR[i] - c->xL[i]) / c->N[i]));
+    }
+    err = std::max(err, std::max(dr / rmax, std::max(dm / rmax, dw)));
+    cell_steps += (long long)I.nsteps * (c->u0_off[i + 1] - c->u0_off[i]);
+  }
+  c->adj_replay_err = err;
+  c->adj_cell_steps = cell_steps;
+  // gradients with respect to the initial lists; a boundary position is the last fixed face plus the
+  // widths after it, so its adjoint adds to the widths of those cells; lattice cells have fixed widths
+  const double nan = std::nan("");
+  for (int i = 0; i < n; ++i) {
+    const AInst& I = hI[i];
+    const int a = c->u0_off[i], M0 = c->u0_off[i + 1] - a;
+    const long long o = offs[i];
+    if (inst_status) inst_status[i] = I.status;
+    dJ_dtau[i] = I.status ? nan : I.lam_tau;
+    double acc = 0.0;  // adjoint of the boundary positions to the right of the current cell, within its segment
+    std::vector<double> wtot(M0, 0.0);
+    for (int q = M0 - 1; q >= 0; --q) {
+      if (!hfpb[o + q + 1]) acc = 0.0;
+      if (hfpb[o + q + 1]) acc += lx[o + q + 1];
+      wtot[q] = lw[o + q] + acc;
+    }
+    for (int q = 0; q < M0; ++q) {
+      dJ_drho0[a + q] = I.status ? nan : lr[o + q];
+      dJ_dm0[a + q] = I.status ? nan : lm[o + q];
+      if (dJ_dw0) {
+        const bool lattice = !hfpb[o + q] && !hfpb[o + q + 1];
+        dJ_dw0[a + q] = I.status ? nan : (lattice ? 0.0 : wtot[q]);
+      }
+    }
+  }
+  return IMEXDS_OK;
+}
+
+imexds_status imexds_adjoint_info(imexds_ctx* c, double* kernel_ms, double* replay_err, int64_t* cell_steps) {
+  if (!c) return IMEXDS_ERR_ARG;
+  if (kernel_ms) *kernel_ms = c->adj_ms;
+  if (replay_err) *replay_err = c->adj_replay_err;
+  if (cell_steps) *cell_steps = c->adj_cell_steps;
   return IMEXDS_OK;
 }
 

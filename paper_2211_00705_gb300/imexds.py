@@ -20,7 +20,8 @@ EXPORTED = ["imexds_create", "imexds_set_states", "imexds_set_states_device", "i
             "imexds_get_states", "imexds_step", "imexds_run_to", "imexds_get_stats", "imexds_destroy",
             "imexds_status_string", "imexds_last_error_string", "imexds_reset", "imexds_set_kernel_timing",
             "imexds_get_kernel_times", "imexds_set_schedule", "imexds_check_log", "imexds_step_uniform_noalloc",
-            "imexds_get_group_phase_cycles"]
+            "imexds_get_group_phase_cycles", "imexds_adjoint", "imexds_set_adjoint_checkpoint",
+            "imexds_adjoint_info"]
 
 
 class ImexdsError(RuntimeError):
@@ -78,6 +79,9 @@ def load():
         L.imexds_check_log.argtypes = [C.c_int32, dp, dp, dp]
         L.imexds_step_uniform_noalloc.argtypes = [C.POINTER(FluidS), C.c_double, C.c_int32, ip, dp, dp, vp, vp, vp,
                                                   vp, vp, vp, vp]
+        L.imexds_adjoint.argtypes = [vp, dp, dp, dp, dp, dp, dp, dp, ip]
+        L.imexds_set_adjoint_checkpoint.argtypes = [vp, C.c_int32]
+        L.imexds_adjoint_info.argtypes = [vp, dp, dp, C.POINTER(C.c_int64)]
         L.imexds_status_string.restype = C.c_char_p
         L.imexds_status_string.argtypes = [C.c_int]
         L.imexds_last_error_string.restype = C.c_char_p
@@ -180,6 +184,7 @@ class Imexds:
         ph = np.ascontiguousarray(phase, dtype=np.uint8)
         _check(load().imexds_set_states(self.h, _ip(off), _dp(w), _dp(r), _dp(mm),
                                         ph.ctypes.data_as(C.POINTER(C.c_uint8)), t0))
+        self._n0 = int(off[-1])
 
     def set_states_device(self, offsets, widths_d, rho_d, m_d, phase_d, t0: float = 0.0):
         """Device-pointer variant: widths_d/rho_d/m_d (float64) and phase_d (uint8) are CUDA tensors."""
@@ -187,6 +192,7 @@ class Imexds:
         _check(load().imexds_set_states_device(self.h, _ip(off), C.c_void_p(widths_d.data_ptr()),
                                                C.c_void_p(rho_d.data_ptr()), C.c_void_p(m_d.data_ptr()),
                                                C.c_void_p(phase_d.data_ptr()), t0))
+        self._n0 = int(off[-1])
 
     def step(self, n_steps: int):
         _check(load().imexds_step(self.h, int(n_steps)))
@@ -237,6 +243,32 @@ class Imexds:
                                                     b.ctypes.data_as(C.POINTER(C.c_int64))))
         keys = ["plan", "sweep", "dual_time", "post"]
         return {"slowest": dict(zip(keys, a.tolist())), "sum": dict(zip(keys, b.tolist()))}
+
+    def set_adjoint_checkpoint(self, every: int):
+        _check(load().imexds_set_adjoint_checkpoint(self.h, int(every)))
+
+    def adjoint(self, dJ_drho_T, dJ_dm_T, dJ_dw_T=None) -> dict:
+        """Gradient of a loss of the final states of the last forward run (see include/imexds.h).
+        Inputs follow get_states' cell order; outputs the initial states' order (set_states)."""
+        n0 = self._n_initial_cells()
+        r = np.ascontiguousarray(dJ_drho_T, dtype=np.float64)
+        m = np.ascontiguousarray(dJ_dm_T, dtype=np.float64)
+        w = None if dJ_dw_T is None else np.ascontiguousarray(dJ_dw_T, dtype=np.float64)
+        g = {"rho": np.zeros(n0), "m": np.zeros(n0), "widths": np.zeros(n0), "tau": np.zeros(self.n_inst),
+             "status": np.zeros(self.n_inst, dtype=np.int32)}
+        null = C.cast(None, C.POINTER(C.c_double))
+        _check(load().imexds_adjoint(self.h, null if w is None else _dp(w), _dp(r), _dp(m), _dp(g["widths"]),
+                                     _dp(g["rho"]), _dp(g["m"]), _dp(g["tau"]), _ip(g["status"])))
+        return g
+
+    def adjoint_info(self) -> dict:
+        ms, err = np.zeros(1), np.zeros(1)
+        cs = np.zeros(1, dtype=np.int64)
+        _check(load().imexds_adjoint_info(self.h, _dp(ms), _dp(err), cs.ctypes.data_as(C.POINTER(C.c_int64))))
+        return {"kernel_ms": float(ms[0]), "replay_err": float(err[0]), "cell_steps": int(cs[0])}
+
+    def _n_initial_cells(self) -> int:
+        return int(self._n0)
 
     def stats(self) -> dict:
         s = np.zeros((self.n_inst, 10), dtype=np.int64)

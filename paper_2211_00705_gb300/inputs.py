@@ -225,6 +225,48 @@ def riemann_batch(workload_id: int, n_inst: int, n_range=(100, 100), alpha_range
     return _assemble(cells, N, tau, fluid, options, t_end=t_end, n_steps=n_steps, name=name)
 
 
+def jitter_states(batch: Batch, workload_id: int, eps: float = 1e-3) -> Batch:
+    """Per-cell jitter of the states: rho (1 + eps U[-1,1]), m + eps rho U[-1,1] (1 m/s). The discrete
+    scheme is not differentiable where the CFL maximum is attained by several cells at once (piecewise
+    constant data); the jitter makes it unique, so gradient checks compare derivatives, not one-sided
+    slopes. Streams: one splitmix64 lane per cell, seeded from (1000 + workload_id, cell index)."""
+    n = int(batch.cell_offsets[-1])
+    rng = SplitMix64(instance_seeds(1000 + workload_id, n))
+    a, b = rng.uniform(), rng.uniform()
+    return dataclasses.replace(batch, rho=batch.rho * (1.0 + eps * (2.0 * a - 1.0)),
+                               m=batch.m + eps * batch.rho * (2.0 * b - 1.0))
+
+
+def adjoint_batch(n_inst: int = 1024, n_lattice: int = 500, n_steps: int = 2000, tol_scale: float = 1e-4,
+                  jitter: float = 1e-3, workload_id: int = 3) -> Batch:
+    """The adjoint workload: Riemann instances as in workload 3 (N cells, alpha = 1e-3, tau = 1e-3 tau_paper,
+    states as workload 0) with jittered states and dual-time tolerances tightened by tol_scale, so that
+    the forward run is the converged implicit scheme that the adjoint differentiates."""
+    b = riemann_batch(workload_id, n_inst, n_range=(n_lattice, n_lattice), alpha_range=(1e-3, 1e-3),
+                      coef_range=(1e-3, 1e-3),
+                      options=scaled_options(tol_nb=3e-9 * tol_scale, tol_k=3e-7 * tol_scale), t_end=0.0,
+                      n_steps=n_steps, name=f"{n_inst} Riemann instances, N={n_lattice}, {n_steps} steps, adjoint")
+    return jitter_states(b, workload_id, jitter) if jitter > 0 else b
+
+
+def sample_density(batch_or_states, offsets, n_lattice, x_left, x_right):
+    """rho at the background cell centres x_j of every instance (piecewise-constant sampling of the cell
+    list) and, per sample, the index of the cell that holds it. Returns (rho_samples, cell_index) with
+    one entry per background cell, instances concatenated."""
+    w, r = batch_or_states["widths"], batch_or_states["rho"]
+    out_r, out_i = [], []
+    for i in range(len(n_lattice)):
+        a, b = int(offsets[i]), int(offsets[i + 1])
+        N = int(n_lattice[i])
+        h = (x_right[i] - x_left[i]) / N
+        xc = x_left[i] + (np.arange(N) + 0.5) * h
+        edges = x_left[i] + np.concatenate([[0.0], np.cumsum(w[a:b])])
+        k = np.clip(np.searchsorted(edges, xc, side="right") - 1, 0, b - a - 1)
+        out_r.append(r[a + k])
+        out_i.append(a + k)
+    return np.concatenate(out_r), np.concatenate(out_i)
+
+
 def workload(wid: int, scale: float = 1.0) -> Batch:
     """The five synthetic workloads. scale < 1 shrinks instance counts (not sizes) for tests."""
     if wid == 0:

@@ -1,0 +1,153 @@
+"""The discrete adjoint (imexds_adjoint) against the oracle's own derivative (forward mode through the
+oracle, an independent computation) and against central finite differences of the CUDA forward run, on
+the adjoint workload (Riemann instances, jittered states, tight dual-time tolerances) scaled down."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import pyoracle as P
+from paper_2211_00705_gb300 import inputs as I
+from tests.adjoint_util import directions, grad_dot, misfit, target_samples
+
+pytestmark = pytest.mark.gpu
+
+TOL_TANGENT = 1e-7   # adjoint vs oracle tangent (both exact derivatives; differ by convergence level)
+TOL_FD = 1e-5        # adjoint vs central differences, step 1e-6 relative (the spec bar)
+
+
+def _forward(batch, program, k=16, **kw):
+    from paper_2211_00705_gb300.imexds import Imexds
+    ctx = Imexds.from_batch(batch, **kw)
+    ctx.set_adjoint_checkpoint(k)
+    for kind, arg in program:
+        ctx.step(arg) if kind == "step" else ctx.run_to(arg)
+    return ctx
+
+
+def _target(batch, program):
+    tb = dataclasses.replace(batch, tau=batch.tau * 1.1)
+    ctx = _forward(tb, program)
+    s = ctx.get_states()
+    ctx.close()
+    return target_samples(s, tb)
+
+
+def _grad(batch, program, k=16, **kw):
+    tgt = _target(batch, program)
+    ctx = _forward(batch, program, k, **kw)
+    s = ctx.get_states()
+    assert (s["status"] == 0).all()
+    J, gr = misfit(s, tgt, batch)
+    g = ctx.adjoint(gr, np.zeros_like(gr))
+    info = ctx.adjoint_info()
+    stats = ctx.stats()
+    ctx.close()
+    return tgt, s, J, g, info, stats
+
+
+def _oracle_dirs(batch, program, tgt, dirs):
+    o = P.Oracle(batch)
+    st, d = o.tangent(program, seed_w=np.stack([x["widths"] for x in dirs]),
+                      seed_rho=np.stack([x["rho"] for x in dirs]), seed_m=np.stack([x["m"] for x in dirs]),
+                      seed_tau=np.stack([x["tau"] for x in dirs]), threads=8)
+    J, gr = misfit(st, tgt, batch)
+    off = st["offsets"]
+    out = []
+    for q in range(len(dirs)):
+        v = np.zeros(batch.n_inst)
+        for i in range(batch.n_inst):
+            s = slice(off[i], off[i + 1])
+            v[i] = float(np.dot(gr[s], d["rho"][q][s]))
+        out.append(v)
+    return out
+
+
+def _rel(a, b, scale):
+    return np.abs(a - b) / np.maximum(scale, 1e-300)
+
+
+@pytest.mark.parametrize("program", [[("step", 150)], [("step", 60), ("step", 90)]])
+def test_adjoint_matches_oracle_tangent(program):
+    """Every directional derivative (tau, random rho and m fields, the boundary position) of every
+    instance agrees with the oracle's forward-mode derivative of the same run."""
+    b = I.adjoint_batch(n_inst=6, n_lattice=120, n_steps=150)
+    tgt, s, J, g, info, stats = _grad(b, program)
+    assert (g["status"] == 0).all(), g["status"]
+    assert info["replay_err"] <= 1e-9, info
+    assert stats["merges"].sum() + stats["splits"].sum() > 0  # grid management is differentiated too
+    dirs = directions(b)
+    ref = _oracle_dirs(b, program, tgt, dirs)
+    for q, d in enumerate(dirs):
+        got = grad_dot(b, g, d)
+        scale = np.max(np.abs(ref[q]))
+        err = _rel(got, ref[q], scale)
+        print(q, np.max(err), scale)
+        assert np.max(err) <= TOL_TANGENT, (q, got, ref[q])
+
+
+def test_adjoint_matches_central_differences():
+    """dJ/dtau and dJ/d(rho, m) at sampled cells against central differences of the CUDA forward run
+    (relative step 1e-6), for every instance."""
+    program = [("step", 150)]
+    b = I.adjoint_batch(n_inst=4, n_lattice=120, n_steps=150)
+    tgt, s, J, g, info, stats = _grad(b, program)
+    rng = np.random.default_rng(11)
+    cases = [("tau", i, None) for i in range(b.n_inst)]
+    for i in range(b.n_inst):
+        a0, a1 = b.cell_offsets[i], b.cell_offsets[i + 1]
+        for c in rng.choice(np.arange(a0, a1), 3, replace=False):
+            cases += [("rho", i, int(c)), ("m", i, int(c))]
+    from paper_2211_00705_gb300.imexds import Imexds
+    worst = 0.0
+    for kind, i, c in cases:
+        vals = []
+        for sgn in (+1, -1):
+            bb = dataclasses.replace(b, tau=b.tau.copy(), rho=b.rho.copy(), m=b.m.copy())
+            if kind == "tau":
+                eps = 1e-6 * b.tau[i]
+                bb.tau[i] += sgn * eps
+            elif kind == "rho":
+                eps = 1e-6 * b.rho[c]
+                bb.rho[c] += sgn * eps
+            else:
+                eps = 1e-6 * max(abs(b.m[c]), b.rho[c])
+                bb.m[c] += sgn * eps
+            ctx = Imexds.from_batch(bb)
+            ctx.step(150)
+            ss = ctx.get_states()
+            ctx.close()
+            Jp, _ = misfit(ss, tgt, bb)
+            vals.append(Jp[i])
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        ad = g["tau"][i] if kind == "tau" else g[kind][c]
+        err = abs(fd - ad) / max(abs(ad), abs(fd), 1e-300)
+        print(kind, i, c, ad, fd, err)
+        worst = max(worst, err)
+    assert worst <= TOL_FD
+
+
+def test_adjoint_segments_do_not_change_the_gradient():
+    """Checkpoint intervals 7 and 1000 (one segment) give the same gradient bit for bit."""
+    program = [("step", 90)]
+    b = I.adjoint_batch(n_inst=3, n_lattice=100, n_steps=90)
+    _, _, _, g1, _, _ = _grad(b, program, k=7)
+    _, _, _, g2, _, _ = _grad(b, program, k=1000)
+    for key in ("rho", "m", "widths", "tau"):
+        np.testing.assert_array_equal(g1[key], g2[key])
+
+
+def test_adjoint_run_to_clipped_last_step():
+    """run_to: the last step of each instance is shortened to land on t_end, so t^n enters that step's dt;
+    the adjoint carries it back (checked against the oracle tangent)."""
+    b = I.adjoint_batch(n_inst=4, n_lattice=100, n_steps=0)
+    b = dataclasses.replace(b, t_end=3.3e-5)
+    program = [("run_to", 3.3e-5)]
+    tgt, s, J, g, info, stats = _grad(b, program)
+    assert (g["status"] == 0).all()
+    dirs = directions(b, n_rand=2)
+    ref = _oracle_dirs(b, program, tgt, dirs)
+    for q, d in enumerate(dirs):
+        got = grad_dot(b, g, d)
+        err = _rel(got, ref[q], np.max(np.abs(ref[q])))
+        assert np.max(err) <= TOL_TANGENT, (q, got, ref[q])
