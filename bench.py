@@ -32,6 +32,9 @@ UNIT = "cell-steps/s"
 # algorithmic FP64 operations of one explicit cell-step (HLL face + cell update, counted in the design doc)
 SWEEP_FLOP_PER_CELL = 33
 FP64_PEAK_TFLOPS = 1.25   # GB300 dense FP64 (nominal; no FP64 figure in MEASURED_PEAKS.json)
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_sweep launch on this workload (ncu capture of the
+# per-step schedule, launches 301-302: 91.7 + 38.8 MB); valid while k_sweep is unchanged
+SWEEP_TRAFFIC_BYTES = 130.6e6
 
 
 def dist_env():
@@ -296,7 +299,9 @@ def main():
     per_launch_s = kt_steps["k_sweep"][0] / 1e3 / n_sw
     achieved = flops / per_launch_s / 1e12 if per_launch_s > 0 else None
     roof = {"bound": "alu", "kernel": "k_sweep", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": None,
+            "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+            "traffic": SWEEP_TRAFFIC_BYTES if args.scale == 1.0 else None,
+            "algorithmic_bytes": 32.0 * sweep_cells / n_sw,
             "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table; no FP64 entry in MEASURED_PEAKS.json)",
             "timed_schedule_kernel": dominant,
             "per_step_schedule_share": {k: round(v[0] / tot, 4) if tot else None for k, v in kt_steps.items()},

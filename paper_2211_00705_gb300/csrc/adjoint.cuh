@@ -671,6 +671,9 @@ __device__ void fwd_step(const ADev& A, AInst& I, SharedStep& S, double t_end, S
           A.fx[o + i + 1] = 0.0;
           A.w[o + i] = w1;
           A.w[o + i + 1] = w2;
+          A.r[o + i + 1] = A.r[o + i];  // both parts keep the state of the split cell
+          A.m[o + i + 1] = A.m[o + i];
+          A.ph[o + i + 1] = A.ph[o + i];
           if (rec) {
             rec->sp_i[nsp] = i;
             rec->sp_case[nsp] = cs;
