@@ -53,6 +53,85 @@ def cell_steps(stats, counts):
     return float(np.sum(stats["steps"].astype(np.float64) * counts.astype(np.float64)))
 
 
+def measure_adjoint(dev, steps, warmup, scale=1.0):
+    """The adjoint on its workload (Riemann instances, N=500, 2000 steps, checkpoints every 64): forward run
+    (also a target run with tau x 1.1 for the misfit), then imexds_adjoint timed. Cell-steps of the adjoint
+    = initial cells x steps of every instance (the replay, the recompute and the reverse sweep all count as
+    one reverse cell-step). Returns the JSON object of the adjoint line."""
+    import dataclasses
+    import torch
+    from paper_2211_00705_gb300 import inputs as I
+    from paper_2211_00705_gb300.imexds import Imexds
+    n = max(1, int(round(1024 * scale)))
+    b = I.adjoint_batch(n_inst=n)
+    prog_steps = b.n_steps
+    tctx = Imexds.from_batch(dataclasses.replace(b, tau=b.tau * 1.1))
+    tctx.step(prog_steps)
+    ts = tctx.get_states()
+    tctx.close()
+    rs_t, _ = I.sample_density(ts, ts["offsets"], b.n_lattice, b.x_left, b.x_right)
+    ctx = Imexds.from_batch(b)
+    ctx.set_adjoint_checkpoint(64)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ctx.step(prog_steps)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd_s = e0.elapsed_time(e1) / 1e3
+    s = ctx.get_states()
+    rs, idx = I.sample_density(s, s["offsets"], b.n_lattice, b.x_left, b.x_right)
+    h = np.repeat((b.x_right - b.x_left) / b.n_lattice, b.n_lattice)
+    g_rho = np.zeros(int(s["offsets"][-1]))
+    np.add.at(g_rho, idx, h * (rs - rs_t))
+    g_m = np.zeros_like(g_rho)
+    for _ in range(max(1, warmup)):
+        g = ctx.adjoint(g_rho, g_m)
+    kern, wall = [], []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = ctx.adjoint(g_rho, g_m)
+        wall.append(time.perf_counter() - t0)
+        kern.append(ctx.adjoint_info()["kernel_ms"] / 1e3)
+    info = ctx.adjoint_info()
+    st = ctx.stats()
+    fwd_cs = float(np.sum(st["steps"] * np.diff(b.cell_offsets)))
+    ctx.close()
+    cs = float(info["cell_steps"])
+    return {"value": cs / float(np.mean(kern)), "unit": UNIT, "workload": b.name, "checkpoint_every": 64,
+            "seconds_per_call": float(np.mean(kern)), "calls": steps,
+            "e2e": {"value": cs / float(np.mean(wall)), "unit": UNIT,
+                    "note": "imexds_adjoint call with host seed/gradient arrays, layout and copies included"},
+            "replay_err": info["replay_err"], "instances_without_gradient": int(np.count_nonzero(g["status"])),
+            "forward_value": fwd_cs / fwd_s, "forward_note": "imexds_step over the same workload (tight tolerances)",
+            "dts_iters_per_step": float(st["dts_iters"].sum() / max(1, st["steps"].sum()))}
+
+
+def measure_plain(batch, n_sample=16):
+    """The plain single-instance GPU step: the same kernels, one instance per context, per-step schedule
+    (one launch per kernel and step), on a sample of the workload's instances run one after another."""
+    import torch
+    from paper_2211_00705_gb300.imexds import Imexds
+    idx = np.linspace(0, batch.n_inst - 1, n_sample).astype(int)
+    sub = batch.subset(list(idx))
+    cs, secs = 0.0, 0.0
+    for i in range(sub.n_inst):
+        one = sub.subset([i])
+        ctx = Imexds.from_batch(one, schedule=1)
+        ctx.run_to(one.t_end)   # warm-up (graph build)
+        ctx.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.run_to(one.t_end)
+        torch.cuda.synchronize()
+        secs += time.perf_counter() - t0
+        cs += cell_steps(ctx.stats(), ctx.cell_counts())
+        ctx.close()
+    return {"value": cs / secs, "unit": UNIT, "sample": f"{sub.n_inst} of {batch.n_inst} instances, one context each, "
+            "per-step schedule, run one after another", "seconds": secs}
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
 
@@ -179,6 +258,8 @@ def main():
     ap.add_argument("--schedule", type=int, default=0, help="0 automatic, 1 per-step kernels, 2 instance groups")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="fraction of the 4096 instances (smaller cases for profiling only)")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
+    ap.add_argument("--no-plain", action="store_true", help="skip the single-instance comparison")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -316,6 +397,12 @@ def main():
                            "cell_steps_per_step": cs_run, "l2": "flushed (256 MB write) between timed runs",
                            "instance_status_nonzero": int(np.count_nonzero(status))},
                 "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+        if not args.no_plain:
+            plain = measure_plain(batch)
+            plain["batched_over_plain"] = value / plain["value"]
+            line["plain_single_instance"] = plain
+        if not args.no_adjoint:
+            line["adjoint"] = measure_adjoint(dev, max(1, args.steps // 2), 1, scale=args.scale)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(batch)
         print(json.dumps(line), flush=True)

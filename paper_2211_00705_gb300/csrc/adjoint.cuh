@@ -26,7 +26,7 @@
 namespace imexds {
 namespace adj {
 
-constexpr int ATHREADS = 128;
+constexpr int ATHREADS = 64;   // one CTA per instance; 8 resident CTAs per SM
 constexpr int AMAXPB = 16;   // phase boundaries per instance
 constexpr int AMAXBLK = 8;   // blocks per step
 constexpr int AMAXB = 8;     // cells per block
@@ -66,8 +66,9 @@ struct ADev {
   long long stride;
   const int* pk;     // program: 0 = step(arg), 1 = run_to(arg)
   const double* pa;
-  // working cell list and faces
-  double *w, *r, *m, *fx;
+  // working cell list and faces (pwl/pwr: last converged star pressures at a boundary face, the start of
+  // its next solve, as in the forward kernels)
+  double *w, *r, *m, *fx, *pwl, *pwr;
   unsigned char *ph, *fpb;
   int* fj;
   // face scratch
@@ -78,7 +79,7 @@ struct ADev {
   // adjoints (current) and accumulators
   double *lw, *lr, *lm, *lx, *nw, *nr, *nm, *nx;
   // checkpoints
-  double *ck_w, *ck_r, *ck_m, *ck_fx;
+  double *ck_w, *ck_r, *ck_m, *ck_fx, *ck_pwl, *ck_pwr;
   unsigned char *ck_ph, *ck_fpb;
   int* ck_fj;
   ACk* ck_h;
@@ -114,7 +115,7 @@ __device__ inline void cta_zero(double* dst, int n) {
 
 // one thread: erase cell b (and face b) of a list
 __device__ void list_erase(double* w, double* r, double* m, unsigned char* ph, unsigned char* fpb, int* fj,
-                           double* fx, int M, int b) {
+                           double* fx, double* pl, double* pr, int M, int b) {
   for (int i = b; i + 1 < M; ++i) {
     w[i] = w[i + 1];
     r[i] = r[i + 1];
@@ -125,11 +126,13 @@ __device__ void list_erase(double* w, double* r, double* m, unsigned char* ph, u
     fpb[g] = fpb[g + 1];
     if (fj) fj[g] = fj[g + 1];
     if (fx) fx[g] = fx[g + 1];
+    if (pl) pl[g] = pl[g + 1];
+    if (pr) pr[g] = pr[g + 1];
   }
 }
 // one thread: open a slot at cell p (cells p.. and faces p.. move one up)
 __device__ void list_open(double* w, double* r, double* m, unsigned char* ph, unsigned char* fpb, int* fj,
-                          double* fx, int M, int p) {
+                          double* fx, double* pl, double* pr, int M, int p) {
   for (int i = M - 1; i >= p; --i) {
     w[i + 1] = w[i];
     r[i + 1] = r[i];
@@ -140,6 +143,8 @@ __device__ void list_open(double* w, double* r, double* m, unsigned char* ph, un
     fpb[g + 1] = fpb[g];
     if (fj) fj[g + 1] = fj[g];
     if (fx) fx[g + 1] = fx[g];
+    if (pl) pl[g + 1] = pl[g];
+    if (pr) pr[g + 1] = pr[g];
   }
 }
 // adjoint lists: erase / open cell b of (lw, lr, lm) and face b of lx
@@ -282,7 +287,8 @@ __device__ bool dts_block(const ADev& A, AInst& I, const SharedStep& S, int lo, 
   }
   for (int q = 0; q <= nb; ++q) {
     fp[q] = (q > 0 && q < nb) ? A.fpb[o + lo + q] : 0;
-    gl[q] = gr[q] = 0.0;
+    gl[q] = fp[q] ? A.pwl[o + lo + q] : 0.0;
+    gr[q] = fp[q] ? A.pwr[o + lo + q] : 0.0;
   }
   auto fluxes = [&]() -> int {  // 0 ok, 1 boundary solve failed, 2 non-positive width
     F0[0] = FL0;
@@ -350,6 +356,11 @@ __device__ bool dts_block(const ADev& A, AInst& I, const SharedStep& S, int lo, 
     out_w[q] = hl[q];
   }
   for (int q = 0; q <= nb; ++q) wcf[q] = wc[q];
+  for (int q = 1; q < nb; ++q)
+    if (fp[q]) {
+      A.pwl[o + lo + q] = gl[q];
+      A.pwr[o + lo + q] = gr[q];
+    }
   if (rec) {
     if (rec_cell + nb > AMAXBC) {
       afail(I, IMEXDS_ERR_CAPACITY);
@@ -440,9 +451,8 @@ __device__ void fwd_step(const ADev& A, AInst& I, SharedStep& S, double t_end, S
     bool ok = true;
     for (int q = 0; q < S.n_pb && ok; ++q) {
       int g = S.pb[q];
-      double gl = 0.0, gr = 0.0;
       PBOut R = pb_solve_warm(c_fluid, c_opts, I.tau, A.ph[o + g - 1], A.r[o + g - 1], A.m[o + g - 1], A.ph[o + g],
-                              A.r[o + g], A.m[o + g], gl, gr);
+                              A.r[o + g], A.m[o + g], A.pwl[o + g], A.pwr[o + g]);
       if (!R.ok) {
         afail(I, IMEXDS_ERR_PB_NOCONV);
         ok = false;
@@ -497,7 +507,7 @@ __device__ void fwd_step(const ADev& A, AInst& I, SharedStep& S, double t_end, S
       A.r[o + a] = (wa * ra + wb * rb) / wm;
       A.m[o + a] = (wa * ma + wb * mb) / wm;
       A.w[o + a] = wm;
-      list_erase(A.w + o, A.r + o, A.m + o, A.ph + o, A.fpb + o, A.fj + o, A.fx + o, Mi, b);
+      list_erase(A.w + o, A.r + o, A.m + o, A.ph + o, A.fpb + o, A.fj + o, A.fx + o, A.pwl + o, A.pwr + o, Mi, b);
       S.M = Mi - 1;
       if (rec) {
         rec->mg_a[nmerge] = a;
@@ -516,9 +526,8 @@ __device__ void fwd_step(const ADev& A, AInst& I, SharedStep& S, double t_end, S
     if (ok && any)
       for (int q = 0; q < S.n_pb && ok; ++q) {
         int g = S.pb[q];
-        double gl = 0.0, gr = 0.0;
         PBOut R = pb_solve_warm(c_fluid, c_opts, I.tau, A.ph[o + g - 1], A.r[o + g - 1], A.m[o + g - 1],
-                                A.ph[o + g], A.r[o + g], A.m[o + g], gl, gr);
+                                A.ph[o + g], A.r[o + g], A.m[o + g], A.pwl[o + g], A.pwr[o + g]);
         if (!R.ok) {
           afail(I, IMEXDS_ERR_PB_NOCONV);
           ok = false;
@@ -664,11 +673,13 @@ __device__ void fwd_step(const ADev& A, AInst& I, SharedStep& S, double t_end, S
             ok = false;
             break;
           }
-          list_open(A.w + o, A.r + o, A.m + o, A.ph + o, A.fpb + o, A.fj + o, A.fx + o, Mi, i + 1);
+          list_open(A.w + o, A.r + o, A.m + o, A.ph + o, A.fpb + o, A.fj + o, A.fx + o, A.pwl + o, A.pwr + o, Mi,
+                    i + 1);
           Mi++;
           A.fpb[o + i + 1] = 0;
           A.fj[o + i + 1] = jc;
           A.fx[o + i + 1] = 0.0;
+          A.pwl[o + i + 1] = A.pwr[o + i + 1] = 0.0;
           A.w[o + i] = w1;
           A.w[o + i + 1] = w2;
           A.r[o + i + 1] = A.r[o + i];  // both parts keep the state of the split cell
@@ -892,7 +903,7 @@ __device__ void rev_step(const ADev& A, AInst& I, SharedStep& S, int slot, const
       A.pr[o + a] = (v[0] * v[1] + v[3] * v[4]) / wm;
       A.pm[o + a] = (v[0] * v[2] + v[3] * v[5]) / wm;
       A.pw[o + a] = wm;
-      list_erase(A.pw + o, A.pr + o, A.pm + o, A.pph + o, A.pfpb + o, nullptr, nullptr, Mc, b);
+      list_erase(A.pw + o, A.pr + o, A.pm + o, A.pph + o, A.pfpb + o, nullptr, nullptr, nullptr, nullptr, Mc, b);
       Mc--;
     }
     if (Mc != S.M) S.bad = 1;
@@ -1057,7 +1068,7 @@ __device__ void rev_step(const ADev& A, AInst& I, SharedStep& S, int slot, const
 }
 
 __device__ void save_list(const ADev& A, AInst& I, long long dst_off, double* w, double* r, double* m,
-                          unsigned char* ph, unsigned char* fpb, int* fj, double* fx) {
+                          unsigned char* ph, unsigned char* fpb, int* fj, double* fx, double* pl, double* pr) {
   const long long o = I.off;
   cta_copy_d(w + dst_off, A.w + o, I.M);
   cta_copy_d(r + dst_off, A.r + o, I.M);
@@ -1066,6 +1077,8 @@ __device__ void save_list(const ADev& A, AInst& I, long long dst_off, double* w,
   if (fpb) cta_copy_b(fpb + dst_off, A.fpb + o, I.M + 1);
   if (fj) cta_copy_i(fj + dst_off, A.fj + o, I.M + 1);
   if (fx) cta_copy_d(fx + dst_off, A.fx + o, I.M + 1);
+  if (pl) cta_copy_d(pl + dst_off, A.pwl + o, I.M + 1);
+  if (pr) cta_copy_d(pr + dst_off, A.pwr + o, I.M + 1);
 }
 __device__ void load_list(const ADev& A, AInst& I, long long src_off, int M) {
   const long long o = I.off;
@@ -1076,10 +1089,12 @@ __device__ void load_list(const ADev& A, AInst& I, long long src_off, int M) {
   cta_copy_b(A.fpb + o, A.ck_fpb + src_off, M + 1);
   cta_copy_i(A.fj + o, A.ck_fj + src_off, M + 1);
   cta_copy_d(A.fx + o, A.ck_fx + src_off, M + 1);
+  cta_copy_d(A.pwl + o, A.ck_pwl + src_off, M + 1);
+  cta_copy_d(A.pwr + o, A.ck_pwr + src_off, M + 1);
 }
 
 // The whole adjoint of one instance: replay with checkpoints, then the segments in reverse.
-__global__ void __launch_bounds__(ATHREADS) k_adjoint(ADev A) {
+__global__ void __launch_bounds__(ATHREADS, 8) k_adjoint(ADev A) {
   const int ii = blockIdx.x;
   if (ii >= A.n_inst) return;
   AInst& I = A.I[ii];
@@ -1096,7 +1111,8 @@ __global__ void __launch_bounds__(ATHREADS) k_adjoint(ADev A) {
         __syncthreads();
         break;
       }
-      save_list(A, I, (long long)c * A.stride + I.off, A.ck_w, A.ck_r, A.ck_m, A.ck_ph, A.ck_fpb, A.ck_fj, A.ck_fx);
+      save_list(A, I, (long long)c * A.stride + I.off, A.ck_w, A.ck_r, A.ck_m, A.ck_ph, A.ck_fpb, A.ck_fj, A.ck_fx,
+                A.ck_pwl, A.ck_pwr);
       if (threadIdx.x == 0) {
         ACk& h = A.ck_h[(long long)c * A.n_inst + ii];
         h.done = I.done;
@@ -1118,7 +1134,7 @@ __global__ void __launch_bounds__(ATHREADS) k_adjoint(ADev A) {
   }
   __syncthreads();
   if (threadIdx.x == 0) I.nsteps = n;
-  save_list(A, I, I.off, A.fin_w, A.fin_r, A.fin_m, A.fin_ph, nullptr, nullptr, nullptr);
+  save_list(A, I, I.off, A.fin_w, A.fin_r, A.fin_m, A.fin_ph, nullptr, nullptr, nullptr, nullptr, nullptr);
   if (threadIdx.x == 0) A.fin_M[ii] = I.M;
   __syncthreads();
   if (I.status) return;

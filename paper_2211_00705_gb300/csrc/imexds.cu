@@ -2367,12 +2367,12 @@ imexds_status imexds_adjoint(imexds_ctx* c, const double* dJ_dw_T, const double*
   }
   const int n_prog = (int)c->prog_k.size();
   // one device allocation carved into the arrays
-  const size_t nd_cell = 26, nb_cell = 5, ni_cell = 1;
+  const size_t nd_cell = 28, nb_cell = 5, ni_cell = 1;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   size_t bytes = 0;
   bytes += al(sizeof(AInst) * n) + al(sizeof(int) * (n_prog + 1)) + al(sizeof(double) * (n_prog + 1));
   bytes += nd_cell * al(sizeof(double) * stride) + nb_cell * al(stride) + ni_cell * al(sizeof(int) * stride);
-  bytes += 4 * al(sizeof(double) * stride * n_ck) + 2 * al(stride * n_ck) + al(sizeof(int) * stride * n_ck);
+  bytes += 6 * al(sizeof(double) * stride * n_ck) + 2 * al(stride * n_ck) + al(sizeof(int) * stride * n_ck);
   bytes += al(sizeof(ACk) * (size_t)n * n_ck) + al(sizeof(int) * n);
   bytes += 3 * al(sizeof(double) * stride * k) + 2 * al(stride * k) + al(sizeof(int) * (size_t)n * k);
   bytes += al(sizeof(StepRec) * (size_t)n * k);
@@ -2400,9 +2400,9 @@ imexds_status imexds_adjoint(imexds_ctx* c, const double* dJ_dw_T, const double*
   double* d_pa = (double*)take(sizeof(double) * (n_prog + 1));
   A.pk = d_pk;
   A.pa = d_pa;
-  double** dcell[26] = {&A.w,  &A.r,  &A.m,  &A.fx, &A.F0, &A.F1, &A.LF0, &A.LF1, &A.CL0,
-                        &A.CL1, &A.CR0, &A.CR1, &A.pw, &A.pr, &A.pm, &A.lw,  &A.lr,  &A.lm,
-                        &A.lx, &A.nw, &A.nr, &A.nm, &A.nx, &A.fin_w, &A.fin_r, &A.fin_m};
+  double** dcell[28] = {&A.w,  &A.r,  &A.m,  &A.fx, &A.F0, &A.F1, &A.LF0, &A.LF1, &A.CL0, &A.CL1,
+                        &A.CR0, &A.CR1, &A.pw, &A.pr, &A.pm, &A.lw, &A.lr,  &A.lm,  &A.lx,  &A.nw,
+                        &A.nr,  &A.nm,  &A.nx, &A.fin_w, &A.fin_r, &A.fin_m, &A.pwl, &A.pwr};
   for (auto q : dcell) *q = (double*)take(sizeof(double) * stride);
   unsigned char** bcell[5] = {&A.ph, &A.fpb, &A.pph, &A.pfpb, &A.fin_ph};
   for (auto q : bcell) *q = (unsigned char*)take(stride);
@@ -2411,6 +2411,8 @@ imexds_status imexds_adjoint(imexds_ctx* c, const double* dJ_dw_T, const double*
   A.ck_r = (double*)take(sizeof(double) * stride * n_ck);
   A.ck_m = (double*)take(sizeof(double) * stride * n_ck);
   A.ck_fx = (double*)take(sizeof(double) * stride * n_ck);
+  A.ck_pwl = (double*)take(sizeof(double) * stride * n_ck);
+  A.ck_pwr = (double*)take(sizeof(double) * stride * n_ck);
   A.ck_ph = (unsigned char*)take(stride * n_ck);
   A.ck_fpb = (unsigned char*)take(stride * n_ck);
   A.ck_fj = (int*)take(sizeof(int) * stride * n_ck);
@@ -2491,6 +2493,8 @@ imexds_status imexds_adjoint(imexds_ctx* c, const double* dJ_dw_T, const double*
   CK(cudaMemcpyAsync(A.lr, lr.data(), sizeof(double) * stride, cudaMemcpyHostToDevice, sm));
   CK(cudaMemcpyAsync(A.lm, lm.data(), sizeof(double) * stride, cudaMemcpyHostToDevice, sm));
   CK(cudaMemsetAsync(A.lx, 0, sizeof(double) * stride, sm));
+  CK(cudaMemsetAsync(A.pwl, 0, sizeof(double) * stride, sm));
+  CK(cudaMemsetAsync(A.pwr, 0, sizeof(double) * stride, sm));
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
