@@ -94,9 +94,10 @@ def test_adjoint_matches_central_differences():
     """dJ/dtau and dJ/d(rho, m) at sampled cells against central differences of the CUDA forward run, for
     every instance. Steps: 1e-6 relative for the cell states; 1e-4 relative for tau, whose effect on the
     states is ~1e-7 relative, so that a 1e-6 step sits on the solver's noise floor (FD error ~ 1/step,
-    measured 3e-5..9e-5 at 1e-6). The error of a cell derivative is taken relative to
-    max(|dJ/dtheta|, 1e-2 max over the instance's cells of the same kind): a cell far from every wave has a
-    derivative ~1e-4 of the largest, below FD resolution."""
+    measured 3e-5..9e-5 at 1e-6). Cells are drawn among those whose derivative is within a factor 10 of
+    the instance's largest of the same kind: a derivative ~1e-2 of the largest moved by 2.7e-5 (relative)
+    between two builds whose results agree to 1e-12, i.e. a 1e-6 step does not resolve it (the oracle
+    tangent comparison covers every cell through random directions)."""
     program = [("step", 150)]
     b = I.adjoint_batch(n_inst=4, n_lattice=120, n_steps=150)
     tgt, s, J, g, info, stats = _grad(b, program)
@@ -104,8 +105,12 @@ def test_adjoint_matches_central_differences():
     cases = [("tau", i, None) for i in range(b.n_inst)]
     for i in range(b.n_inst):
         a0, a1 = b.cell_offsets[i], b.cell_offsets[i + 1]
-        for c in rng.choice(np.arange(a0, a1), 3, replace=False):
-            cases += [("rho", i, int(c)), ("m", i, int(c))]
+        for kind in ("rho", "m"):
+            gk = np.abs(g[kind][a0:a1])
+            # cells whose derivative a 1e-6 step resolves: within a factor 10 of the instance's largest
+            cand = a0 + np.nonzero(gk >= 0.1 * gk.max())[0]
+            for c in rng.choice(cand, min(3, len(cand)), replace=False):
+                cases.append((kind, i, int(c)))
     from paper_2211_00705_gb300.imexds import Imexds
     from paper_2211_00705_gb300.inputs import sample_density
     h = np.repeat((b.x_right - b.x_left) / b.n_lattice, b.n_lattice)
@@ -134,13 +139,8 @@ def test_adjoint_matches_central_differences():
         sel = inst == i
         dp, sm_ = vals[0][sel] - vals[1][sel], vals[0][sel] + vals[1][sel] - 2.0 * tgt[sel]
         fd = float(np.sum(0.5 * h[sel] * dp * sm_)) / (2 * eps)
-        if kind == "tau":
-            ad, scale = g["tau"][i], abs(g["tau"][i])
-        else:
-            ad = g[kind][c]
-            sl = slice(b.cell_offsets[i], b.cell_offsets[i + 1])
-            scale = max(abs(ad), 1e-2 * np.max(np.abs(g[kind][sl])))
-        err = abs(fd - ad) / scale
+        ad = g["tau"][i] if kind == "tau" else g[kind][c]
+        err = abs(fd - ad) / abs(ad)
         print(kind, i, c, ad, fd, err)
         worst = max(worst, err)
     assert worst <= TOL_FD
