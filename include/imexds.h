@@ -210,6 +210,14 @@ imexds_status imexds_set_adjoint_checkpoint(imexds_ctx* ctx, int32_t every);
  * replayed final states from the forward run's (rho and m relative to max|rho|, widths relative to h),
  * and the cell-steps it replayed (initial cells x steps, per instance, summed). Any may be NULL. */
 imexds_status imexds_adjoint_info(imexds_ctx* ctx, double* kernel_ms, double* replay_err, int64_t* cell_steps);
+/* The last imexds_adjoint's replayed final cell lists (host arrays; cell_offsets has n_inst+1 entries,
+ * the others are sized from cell_offsets[n_inst], which may exceed the forward's total when a replay
+ * diverged; any array but cell_offsets may be NULL) and, per instance, where a replay was stopped:
+ * 0 not stopped, 1 its program ended early in a recomputed segment, 2/4 its grid events did not
+ * reverse to the taped list, 3 a block system was singular, 5 its final cell count differs from the
+ * forward run's, 6 its step count differs, 7 its final cell count differs (host check). */
+imexds_status imexds_adjoint_replay(imexds_ctx* ctx, int32_t* cell_offsets, double* widths, double* rho,
+                                    double* m, int32_t* stop_site);
 
 void imexds_destroy(imexds_ctx* ctx);
 const char* imexds_status_string(imexds_status s);

@@ -49,7 +49,7 @@ struct AInst {
   long long off;  // first slot of this instance in every per-cell / per-face array (stride cap + 1)
   long long done; // steps done inside the current program call
   int M, cap, status, pc;
-  int nsteps, M_seed, pad0, pad1;
+  int nsteps, M_seed, site, pad1;  // site: where an instance was stopped (1..5, see k_adjoint)
   double h, xL, tau, t;
   double lam_t, lam_tau;
 };
@@ -94,8 +94,11 @@ struct ADev {
   StepRec* rec;
 };
 
-__device__ inline void afail(AInst& I, int code) {
-  if (I.status == 0) I.status = code;
+__device__ inline void afail(AInst& I, int code, int site = 0) {
+  if (I.status == 0) {
+    I.status = code;
+    I.site = site;
+  }
 }
 
 // ------------------------------------------------------------------------------ list helpers
@@ -910,7 +913,7 @@ __device__ void rev_step(const ADev& A, AInst& I, SharedStep& S, int slot, const
   }
   __syncthreads();
   if (S.bad) {
-    if (tid == 0) afail(I, IMEXDS_ERR_STATE);
+    if (tid == 0) afail(I, IMEXDS_ERR_STATE, 2);
     __syncthreads();
     return;
   }
@@ -951,7 +954,7 @@ __device__ void rev_step(const ADev& A, AInst& I, SharedStep& S, int slot, const
   }
   __syncthreads();
   if (S.bad) {
-    if (tid == 0) afail(I, IMEXDS_ERR_STATE);
+    if (tid == 0) afail(I, IMEXDS_ERR_STATE, 3);
     __syncthreads();
     return;
   }
@@ -1056,7 +1059,7 @@ __device__ void rev_step(const ADev& A, AInst& I, SharedStep& S, int slot, const
       A.nr[o + k] += -lS * sg * mk / (rk * rk);
     }
     I.M = Mc;
-    if (Mc != Mn) afail(I, IMEXDS_ERR_STATE);
+    if (Mc != Mn) afail(I, IMEXDS_ERR_STATE, 4);
   }
   __syncthreads();
   // lambda^n <- accumulators
@@ -1139,7 +1142,7 @@ __global__ void __launch_bounds__(ATHREADS, 8) k_adjoint(ADev A) {
   __syncthreads();
   if (I.status) return;
   if (I.M != I.M_seed) {
-    if (threadIdx.x == 0) afail(I, IMEXDS_ERR_STATE);
+    if (threadIdx.x == 0) afail(I, IMEXDS_ERR_STATE, 5);
     return;
   }
   // phase B: segments from last to first
@@ -1165,7 +1168,7 @@ __global__ void __launch_bounds__(ATHREADS, 8) k_adjoint(ADev A) {
       }
       __syncthreads();
       if (!s_go) {
-        if (threadIdx.x == 0) afail(I, IMEXDS_ERR_STATE);
+        if (threadIdx.x == 0) afail(I, IMEXDS_ERR_STATE, 1);
         __syncthreads();
         return;
       }

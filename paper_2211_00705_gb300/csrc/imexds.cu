@@ -1463,6 +1463,8 @@ struct imexds_ctx {
   size_t adj_bytes = 0;
   void* adj_mem = nullptr;
   double adj_ms = 0.0, adj_replay_err = 0.0;
+  std::vector<int32_t> adj_fin_off, adj_site;
+  std::vector<double> adj_fin_w, adj_fin_r, adj_fin_m;
   long long adj_cell_steps = 0;
 };
 
@@ -2532,7 +2534,10 @@ imexds_status imexds_adjoint(imexds_ctx* c, const double* dJ_dw_T, const double*
   long long cell_steps = 0;
   for (int i = 0; i < n; ++i) {
     AInst& I = hI[i];
-    if (I.status == 0 && (I.nsteps != stats[10 * i] || fM[i] != MT[i])) I.status = IMEXDS_ERR_STATE;
+    if (I.status == 0 && (I.nsteps != stats[10 * i] || fM[i] != MT[i])) {
+      I.status = IMEXDS_ERR_STATE;
+      I.site = (I.nsteps != stats[10 * i]) ? 6 : 7;
+    }
     if (I.status) continue;
     double rmax = 0.0, dr = 0.0, dm = 0.0, dw = 0.0;
     for (int q = 0; q < MT[i]; ++q) rmax = std::max(rmax, std::fabs(gr[toff[i] + q]));
@@ -2547,6 +2552,21 @@ imexds_status imexds_adjoint(imexds_ctx* c, const double* dJ_dw_T, const double*
   }
   c->adj_replay_err = err;
   c->adj_cell_steps = cell_steps;
+  c->adj_fin_off.assign(n + 1, 0);
+  c->adj_fin_w.clear();
+  c->adj_fin_r.clear();
+  c->adj_fin_m.clear();
+  c->adj_site.assign(n, 0);
+  for (int i = 0; i < n; ++i) {
+    const long long o = offs[i];
+    for (int q = 0; q < fM[i]; ++q) {
+      c->adj_fin_w.push_back(fw[o + q]);
+      c->adj_fin_r.push_back(fr[o + q]);
+      c->adj_fin_m.push_back(fm[o + q]);
+    }
+    c->adj_fin_off[i + 1] = c->adj_fin_off[i] + fM[i];
+    c->adj_site[i] = hI[i].site;
+  }
   // gradients with respect to the initial lists; a boundary position is the last fixed face plus the
   // widths after it, so its adjoint adds to the widths of those cells; lattice cells have fixed widths
   const double nan = std::nan("");
@@ -2572,6 +2592,22 @@ imexds_status imexds_adjoint(imexds_ctx* c, const double* dJ_dw_T, const double*
       }
     }
   }
+  return IMEXDS_OK;
+}
+
+imexds_status imexds_adjoint_replay(imexds_ctx* c, int32_t* cell_offsets, double* widths, double* rho, double* m,
+                                    int32_t* stop_site) {
+  if (!c || !cell_offsets) return IMEXDS_ERR_ARG;
+  if (c->adj_fin_off.empty()) return IMEXDS_ERR_STATE;
+  const int n = c->n_inst;
+  for (int i = 0; i <= n; ++i) cell_offsets[i] = c->adj_fin_off[i];
+  const size_t tot = c->adj_fin_w.size();
+  if (widths) std::copy(c->adj_fin_w.begin(), c->adj_fin_w.end(), widths);
+  if (rho) std::copy(c->adj_fin_r.begin(), c->adj_fin_r.end(), rho);
+  if (m) std::copy(c->adj_fin_m.begin(), c->adj_fin_m.end(), m);
+  (void)tot;
+  if (stop_site)
+    for (int i = 0; i < n; ++i) stop_site[i] = c->adj_site[i];
   return IMEXDS_OK;
 }
 

@@ -21,7 +21,7 @@ EXPORTED = ["imexds_create", "imexds_set_states", "imexds_set_states_device", "i
             "imexds_status_string", "imexds_last_error_string", "imexds_reset", "imexds_set_kernel_timing",
             "imexds_get_kernel_times", "imexds_set_schedule", "imexds_check_log", "imexds_step_uniform_noalloc",
             "imexds_get_group_phase_cycles", "imexds_adjoint", "imexds_set_adjoint_checkpoint",
-            "imexds_adjoint_info"]
+            "imexds_adjoint_info", "imexds_adjoint_replay"]
 
 
 class ImexdsError(RuntimeError):
@@ -82,6 +82,7 @@ def load():
         L.imexds_adjoint.argtypes = [vp, dp, dp, dp, dp, dp, dp, dp, ip]
         L.imexds_set_adjoint_checkpoint.argtypes = [vp, C.c_int32]
         L.imexds_adjoint_info.argtypes = [vp, dp, dp, C.POINTER(C.c_int64)]
+        L.imexds_adjoint_replay.argtypes = [vp, ip, dp, dp, dp, ip]
         L.imexds_status_string.restype = C.c_char_p
         L.imexds_status_string.argtypes = [C.c_int]
         L.imexds_last_error_string.restype = C.c_char_p
@@ -266,6 +267,18 @@ class Imexds:
         cs = np.zeros(1, dtype=np.int64)
         _check(load().imexds_adjoint_info(self.h, _dp(ms), _dp(err), cs.ctypes.data_as(C.POINTER(C.c_int64))))
         return {"kernel_ms": float(ms[0]), "replay_err": float(err[0]), "cell_steps": int(cs[0])}
+
+    def adjoint_replay(self) -> dict:
+        """The last adjoint's replayed final cell lists and, per instance, where a replay was stopped."""
+        L = load()
+        off = np.zeros(self.n_inst + 1, dtype=np.int32)
+        site = np.zeros(self.n_inst, dtype=np.int32)
+        null = C.cast(None, C.POINTER(C.c_double))
+        _check(L.imexds_adjoint_replay(self.h, _ip(off), null, null, null, _ip(site)))
+        tot = int(off[-1])
+        w, r, m = np.zeros(tot), np.zeros(tot), np.zeros(tot)
+        _check(L.imexds_adjoint_replay(self.h, _ip(off), _dp(w), _dp(r), _dp(m), _ip(site)))
+        return {"offsets": off, "widths": w, "rho": r, "m": m, "site": site}
 
     def _n_initial_cells(self) -> int:
         return int(self._n0)

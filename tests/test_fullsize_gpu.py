@@ -113,3 +113,76 @@ def test_large_domain_full_size_subdomains():
         assert np.max(np.abs(ra - rg)) <= TOL * np.max(np.abs(ra))
         assert np.max(np.abs(ma - mg)) <= TOL * max(np.max(np.abs(ma)), np.max(np.abs(ra)) * 1.0)
         np.testing.assert_allclose(a["widths"][ka0:ka1], g["widths"][kg0:kg1], rtol=TOL, atol=TOL * h)
+
+
+def test_adjoint_full_size_against_central_differences():
+    """The adjoint workload at full size (1024 instances x N=500 x 2000 steps, checkpoints every 64): the
+    gradient of every instance's misfit against central differences for tau (step 1e-4, see the small
+    adjoint tests) and for rho and m at two resolvable cells per instance (step 1e-6). Instances are
+    independent, so one perturbed batch run gives the perturbed loss of every instance at once."""
+    from paper_2211_00705_gb300.imexds import Imexds
+    b = I.adjoint_batch(n_inst=1024)
+    tb = dataclasses.replace(b, tau=b.tau * 1.1)
+
+    def run(batch):
+        ctx = Imexds.from_batch(batch)
+        ctx.set_adjoint_checkpoint(64)
+        ctx.step(b.n_steps)
+        return ctx
+
+    tctx = run(tb)
+    ts = tctx.get_states()
+    tctx.close()
+    tgt, _ = I.sample_density(ts, ts["offsets"], b.n_lattice, b.x_left, b.x_right)
+    ctx = run(b)
+    s = ctx.get_states()
+    rs, idx = I.sample_density(s, s["offsets"], b.n_lattice, b.x_left, b.x_right)
+    h = np.repeat((b.x_right - b.x_left) / b.n_lattice, b.n_lattice)
+    inst = np.repeat(np.arange(b.n_inst), b.n_lattice)
+    g_rho = np.zeros(int(s["offsets"][-1]))
+    np.add.at(g_rho, idx, h * (rs - tgt))
+    g = ctx.adjoint(g_rho, np.zeros_like(g_rho))
+    info = ctx.adjoint_info()
+    ctx.close()
+    ok = g["status"] == 0
+    assert ok.mean() >= 0.99, np.unique(g["status"], return_counts=True)
+    assert info["replay_err"] <= 1e-9
+
+    def fd(perturb):
+        vals = []
+        for sgn in (1.0, -1.0):
+            bb = dataclasses.replace(b, tau=b.tau.copy(), rho=b.rho.copy(), m=b.m.copy())
+            eps = perturb(bb, sgn)
+            c = run(bb)
+            ss = c.get_states()
+            c.close()
+            vals.append(I.sample_density(ss, ss["offsets"], b.n_lattice, b.x_left, b.x_right)[0])
+        dp, sm = vals[0] - vals[1], vals[0] + vals[1] - 2.0 * tgt
+        out = np.zeros(b.n_inst)
+        np.add.at(out, inst, 0.5 * h * dp * sm)
+        return out / (2.0 * eps)
+
+    def tau_pert(bb, sgn):
+        bb.tau[:] = b.tau * (1.0 + sgn * 1e-4)
+        return 1e-4 * b.tau
+
+    errs = np.abs(fd(tau_pert) - g["tau"]) / np.abs(g["tau"])
+    worst = float(np.max(errs[ok]))
+    rng = np.random.default_rng(5)
+    for kind in ("rho", "m"):
+        for rep in range(2):
+            cells = np.zeros(b.n_inst, dtype=np.int64)
+            for i in range(b.n_inst):
+                a0, a1 = b.cell_offsets[i], b.cell_offsets[i + 1]
+                gk = np.abs(g[kind][a0:a1]) if ok[i] else np.ones(a1 - a0)
+                cand = a0 + np.nonzero(gk >= 0.1 * gk.max())[0]
+                cells[i] = rng.choice(cand)
+            scale = np.maximum(np.abs(b.m[cells]), b.rho[cells]) if kind == "m" else b.rho[cells]
+
+            def pert(bb, sgn, cells=cells, scale=scale, kind=kind):
+                getattr(bb, kind)[cells] += sgn * 1e-6 * scale
+                return 1e-6 * scale
+
+            e = np.abs(fd(pert) - g[kind][cells]) / np.abs(g[kind][cells])
+            worst = max(worst, float(np.max(e[ok])))
+    assert worst <= 1e-5, worst
