@@ -179,18 +179,21 @@ __device__ __forceinline__ SideD<K> side_d(const Phase& e, const Dual<K>& p) {
   s.dv = -(s.v * s.v) / e.a2;
   return s;
 }
-// Outer-wave function f_K(p*) (shock / rarefaction branch on values) and df/dp*.
+// Outer-wave function f_K(p*) (shock / rarefaction branch on values) and df/dp*. Shock branch: for both
+// linear EOS p* - p_K = a^2 (rho* - rho_K), so (p* - p_K)(v_K - v*) = (p* - p_K)^2 / (a^2 rho_K rho*) and
+// f = (p* - p_K) / (a sqrt(rho_K rho*)): the same function without the product of two vanishing factors
+// under a square root, whose derivative turns into 0/0 where p* -> p_K (cells next to a boundary sit in
+// the star region once the outer waves have left).
 template <int K>
 __device__ Dual<K> wave_f_d(const Phase& e, const Dual<K>& ps, const Dual<K>& rK, Dual<K>& dfdp) {
   Dual<K> pK = pressure_d(e, rK);
   Dual<K> rs = density_d(e, ps);
   Dual<K> vs = 1.0 / rs;
   if (ps.v > pK.v) {
-    Dual<K> dv = 1.0 / rK - vs;
-    Dual<K> q = (ps - pK) * dv;
-    Dual<K> f = dsqrt(q);
-    Dual<K> dq = dv + (ps - pK) * vs * vs / e.a2;
-    dfdp = (f.v > 0.0) ? 0.5 * dq / f : vs / e.a;
+    Dual<K> den = e.a * dsqrt(rK * rs);
+    Dual<K> dp = ps - pK;
+    Dual<K> f = dp / den;
+    dfdp = (1.0 - dp * vs / (2.0 * e.a2)) / den;
     return f;
   }
   dfdp = vs / e.a;
