@@ -376,9 +376,8 @@ __device__ inline int pbf_newton(const Fluid& F, const Opts& o, const SideData& 
       // convergence), the point the newton_tol test reaches: take it without the line-search evaluation
       // and carry the recovery quantities (f, v, z) to it to first order (their second-order terms are
       // O(1e-16) relative as well).
-      double s0 = fabs(d0) / fmax(fabs(x0), F.p_sat);
-      double s1 = fabs(d1) / fmax(fabs(x1), F.p_sat);
-      if (fmax(s0, s1) <= 1e-8) {
+      // (tested without dividing: |d| <= 1e-8 max(|x|, p_sat) for both unknowns)
+      if (fabs(d0) <= 1e-8 * fmax(fabs(x0), F.p_sat) && fabs(d1) <= 1e-8 * fmax(fabs(x1), F.p_sat)) {
         S.L.f = __fma_rn(S.L.df, d0, S.L.f);
         S.R.f = __fma_rn(S.R.df, d1, S.R.f);
         S.L.v = __fma_rn(S.L.dv, d0, S.L.v);

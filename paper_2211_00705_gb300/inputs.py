@@ -313,6 +313,32 @@ def cavitation_batch(workload_id: int, n_inst: int, n_range=(64, 4096), v_range=
                      name=name)
 
 
+def nucleation_batch(workload_id: int, n_inst: int, n_range=(64, 1024), v_range=(14.0, 16.0), n_steps: int = 500,
+                     p_vap: float = 70000.0, name: str = "") -> Batch:
+    """Pure vapour at pressure p_vap (below p_sat, as in the paper's nucleation test, Sec. 4.3) with
+    u = +V left of face floor(N/2) and -V right of it (compression), V uniform in v_range: the same-phase
+    star pressure at the centre exceeds the maximum vapour pressure and a liquid cell nucleates there
+    (App. B, the mirror of workload 4). With the workload fluid (a_V = 415 m/s, p_tilde = 72.3 kPa) the
+    threshold lies near V = 13.5 m/s; V in [14, 16] nucleates exactly one droplet that persists (faster
+    collisions supersaturate the post-shock vapour and nucleate several droplets, whose vapour gaps then
+    vanish, a case the method does not treat)."""
+    fluid = workload_fluid(rho0_liq=1000.0)
+    rng = SplitMix64(instance_seeds(workload_id, n_inst))
+    uN, uV = rng.uniform(), rng.uniform()
+    N = np.minimum(n_range[0] + np.floor(uN * (n_range[1] - n_range[0] + 1)).astype(np.int64), n_range[1])
+    V = v_range[0] + uV * (v_range[1] - v_range[0])
+    rho_v = p_vap / fluid.a2_vap
+    cells = []
+    for i in range(n_inst):
+        n = int(N[i])
+        h = 1.0 / n
+        u = np.where(np.arange(n) < n // 2, V[i], -V[i])
+        rho = np.full(n, rho_v)
+        cells.append((np.full(n, h), rho, rho * u, np.zeros(n, dtype=np.uint8)))
+    return _assemble(cells, N, np.full(n_inst, tau_paper()), fluid, scaled_options(creation=1), n_steps=n_steps,
+                     name=name or f"{n_inst} nucleation instances, N in {list(n_range)}, {n_steps} steps")
+
+
 def bubbles_domain(workload_id: int, n_cells: int = 1 << 24, n_bubbles: int = 1024, width_range=(2, 20),
                    alpha_range=(1e-6, 1e-1), n_steps: int = 1000, gap: int = 4, name: str = "") -> Batch:
     """One liquid domain on [0, 1] (rho = rho0 = 1000, u = 0) with vapour bubbles (workload 2). A bubble of

@@ -202,3 +202,27 @@ def test_dts_iterations_grow_mildly_with_smaller_alpha():
         counts.append(st["dts_iters"][0] / st["steps"][0])
     assert counts[-1] < 1e3
     assert counts[-1] < 100 * counts[0]
+
+
+def test_nucleation_creates_one_persistent_droplet_and_conserves_mass():
+    """Compressed vapour (App. B, nucleation): one liquid cell appears at the collision face, persists, and
+    total mass changes only by the end-face fluxes."""
+    import numpy as np
+    from oracle import pyoracle as P
+    from paper_2211_00705_gb300 import inputs as I
+    b = I.nucleation_batch(5, 4, n_range=(64, 128), n_steps=100)
+    o = P.Oracle(b)
+    o.step(100, 4)
+    s, st = o.states(), o.stats()
+    assert (s["status"] == 0).all() and (st["creations"] == 1).all()
+    for i in range(b.n_inst):
+        a0, a1 = s["offsets"][i], s["offsets"][i + 1]
+        liquid = np.nonzero(s["phase"][a0:a1] == 1)[0]
+        assert len(liquid) == 1 and s["rho"][a0 + liquid[0]] > 900.0
+        # the outer waves have not reached the ends (100 steps at CFL 0.5 travel < N/2 cells), so the
+        # end fluxes are those of the initial states: mass in = rho u at both ends, times t
+        m0 = np.sum(b.widths[b.cell_offsets[i]:b.cell_offsets[i + 1]] * b.rho[b.cell_offsets[i]:b.cell_offsets[i + 1]])
+        m1 = np.sum(s["widths"][a0:a1] * s["rho"][a0:a1])
+        r_end, m_end = b.rho[b.cell_offsets[i]], b.m[b.cell_offsets[i]]   # u = +V left: mass enters; right: u = -V
+        inflow = 2.0 * abs(m_end) * s["t"][i]
+        assert abs(m1 - (m0 + inflow)) <= 1e-10 * m0   # measured 4e-12 (round-off of 100 steps)

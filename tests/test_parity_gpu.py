@@ -51,6 +51,14 @@ def test_cavitation_creation(schedule):
     assert (sb["creations"] >= 1).all()
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_nucleation_creation(schedule):
+    """Pure vapour compressed: a liquid cell nucleates (App. B, the mirror of cavitation) and is tracked."""
+    b = I.nucleation_batch(5, 8, n_steps=200)
+    recs, sa, sb = _check(b, schedule=schedule)
+    assert (sb["creations"] >= 1).all()
+
+
 def test_bubbles_small_domain():
     """Many boundaries in one domain (the large-domain layout at 4096 cells with 64 bubbles)."""
     b = I.bubbles_domain(2, n_cells=4096, n_bubbles=64, n_steps=60)
