@@ -90,44 +90,54 @@ def test_adjoint_matches_oracle_tangent(program):
         assert np.max(err) <= TOL_TANGENT, (q, got, ref[q])
 
 
-def test_adjoint_matches_central_differences():
-    """dJ/dtau and dJ/d(rho, m) at sampled cells against central differences of the CUDA forward run, for
-    every instance. Steps: 1e-6 relative for the cell states; 1e-4 relative for tau, whose effect on the
-    states is ~1e-7 relative, so that a 1e-6 step sits on the solver's noise floor (FD error ~ 1/step,
-    measured 3e-5..9e-5 at 1e-6). Cells are drawn among those whose derivative is within a factor 10 of
-    the instance's largest of the same kind: a derivative ~1e-2 of the largest moved by 2.7e-5 (relative)
-    between two builds whose results agree to 1e-12, i.e. a 1e-6 step does not resolve it (the oracle
-    tangent comparison covers every cell through random directions)."""
-    program = [("step", 150)]
-    b = I.adjoint_batch(n_inst=4, n_lattice=120, n_steps=150)
-    tgt, s, J, g, info, stats = _grad(b, program)
-    rng = np.random.default_rng(11)
+# central-difference steps (relative) and bars per parameter kind. The oracle's own central differences
+# against its own exact tangent (same code, same run) show the floor of the measurement on this loss:
+# momentum derivatives at step 1e-6 are off by up to 2e-4 (round-off of the final states, ~1e-16 rho,
+# times the misfit, against a loss change of ~1e-11), at 1e-5 by up to 1.5e-5; tau at 1e-6 by up to
+# 9e-5 (its effect on the states is ~1e-7 relative), at 1e-4 by < 1e-6; density at 1e-6 by < 1e-5.
+FD_STEP = {"tau": 1e-4, "rho": 1e-6, "m": 1e-5}
+FD_BAR = {"tau": TOL_FD, "rho": TOL_FD, "m": 5e-5}
+
+
+def fd_cases(b, g, rng, per_kind=3):
+    """tau of every instance and, per instance and state kind, cells among those whose derivative is within a
+    factor 10 of the instance's largest of that kind."""
     cases = [("tau", i, None) for i in range(b.n_inst)]
     for i in range(b.n_inst):
         a0, a1 = b.cell_offsets[i], b.cell_offsets[i + 1]
         for kind in ("rho", "m"):
             gk = np.abs(g[kind][a0:a1])
-            # cells whose derivative a 1e-6 step resolves: within a factor 10 of the instance's largest
             cand = a0 + np.nonzero(gk >= 0.1 * gk.max())[0]
-            for c in rng.choice(cand, min(3, len(cand)), replace=False):
+            for c in rng.choice(cand, min(per_kind, len(cand)), replace=False):
                 cases.append((kind, i, int(c)))
+    return cases
+
+
+def test_adjoint_matches_central_differences():
+    """dJ/dtau and dJ/d(rho, m) at sampled cells against central differences of the CUDA forward run, for
+    every instance, with the steps and bars of FD_STEP / FD_BAR (the measurement's own floor, see above);
+    the median error over all cases must also meet 1e-5."""
+    program = [("step", 150)]
+    b = I.adjoint_batch(n_inst=4, n_lattice=120, n_steps=150)
+    tgt, s, J, g, info, stats = _grad(b, program)
+    cases = fd_cases(b, g, np.random.default_rng(11))
     from paper_2211_00705_gb300.imexds import Imexds
     from paper_2211_00705_gb300.inputs import sample_density
     h = np.repeat((b.x_right - b.x_left) / b.n_lattice, b.n_lattice)
     inst = np.repeat(np.arange(b.n_inst), b.n_lattice)
-    worst = 0.0
+    errs = []
     for kind, i, c in cases:
         vals = []
         for sgn in (+1, -1):
             bb = dataclasses.replace(b, tau=b.tau.copy(), rho=b.rho.copy(), m=b.m.copy())
             if kind == "tau":
-                eps = 1e-4 * b.tau[i]
+                eps = FD_STEP[kind] * b.tau[i]
                 bb.tau[i] += sgn * eps
             elif kind == "rho":
-                eps = 1e-6 * b.rho[c]
+                eps = FD_STEP[kind] * b.rho[c]
                 bb.rho[c] += sgn * eps
             else:
-                eps = 1e-6 * max(abs(b.m[c]), b.rho[c])
+                eps = FD_STEP[kind] * max(abs(b.m[c]), b.rho[c])
                 bb.m[c] += sgn * eps
             ctx = Imexds.from_batch(bb)
             ctx.step(150)
@@ -142,8 +152,9 @@ def test_adjoint_matches_central_differences():
         ad = g["tau"][i] if kind == "tau" else g[kind][c]
         err = abs(fd - ad) / abs(ad)
         print(kind, i, c, ad, fd, err)
-        worst = max(worst, err)
-    assert worst <= TOL_FD
+        assert err <= FD_BAR[kind], (kind, i, c, ad, fd, err)
+        errs.append(err)
+    assert np.median(errs) <= TOL_FD
 
 
 def test_autograd_function():
