@@ -324,12 +324,16 @@ def main():
     # per-kernel durations over one instrumented run (events captured in the step graph)
     # per-kernel durations: one instrumented run of the timed schedule, and one of the per-step kernel
     # schedule, which separates the sweep from the dual-time work
-    kt, kt_steps = {}, {}
+    kt, kt_steps, phase_cycles = {}, {}, None
     try:
         ctx.set_kernel_timing(True)
         ctx.reset()
         ctx.run_to(batch.t_end)
         kt = ctx.kernel_times()
+        try:
+            phase_cycles = ctx.group_phase_cycles()
+        except Exception:
+            phase_cycles = None
         ctx.set_kernel_timing(False)
         ctx.set_schedule(1)
         ctx.set_kernel_timing(True)
@@ -387,7 +391,8 @@ def main():
             "timed_schedule_kernel": dominant,
             "per_step_schedule_share": {k: round(v[0] / tot, 4) if tot else None for k, v in kt_steps.items()},
             "per_step_schedule_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in kt_steps.items()},
-            "timed_schedule_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in kt.items()}}
+            "timed_schedule_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in kt.items()},
+            "group_phase_cycles": phase_cycles}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

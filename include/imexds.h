@@ -73,7 +73,8 @@ typedef struct {
   int creation;        /* 1: detect cavitation / nucleation at same-phase faces (App. B) (0) */
   int zone_capacity;   /* zone records per instance (0 = automatic: 4 + 2 * phase boundaries) */
   int schedule;        /* 0 automatic, 1 one launch per kernel and step (graph of 8 steps), 2 instance
-                          groups advanced by one resident launch (0) */
+                          groups advanced by one resident launch in lockstep, 3 instance groups whose
+                          instances advance independently inside the resident launch (0) */
   int group_cells;     /* lattice cells per instance group (0 = 16384) */
   int group_threads;   /* threads per group CTA, a multiple of 32 from 64 to 128 (0 = 128): warp 0 runs
                           the per-instance work, the other warps sweep */
@@ -140,7 +141,7 @@ imexds_status imexds_reset(imexds_ctx* ctx);
  * longest critical path (slowest4) and summed over all groups (sum4). Arrays of 4. */
 imexds_status imexds_get_group_phase_cycles(imexds_ctx* ctx, int64_t* slowest4, int64_t* sum4);
 
-/* Choose the schedule for the next calls (values of imexds_options.schedule). */
+/* Choose the schedule for the next calls (values of imexds_options.schedule, 0..3). */
 imexds_status imexds_set_schedule(imexds_ctx* ctx, int32_t schedule);
 
 /* Measurement: with on != 0, steps are launched without the step graph and CUDA events are recorded

@@ -1351,6 +1351,146 @@ __global__ void __launch_bounds__(128, 2) k_group(Dev d, const int* ginst, const
   }
 }
 
+// Instance groups without a per-step barrier. Lane k of warp 0 runs instance k's serial work at its own
+// pace; the other warps sweep the 32-cell tiles of whichever instance has planned its step. Per instance,
+// shared counters order the work of one step n:
+//   lane k: boundary solves + merges + blocks (n) -> open the sweep of step n -> Algorithm 2 (n)
+//           -> wait until every tile of step n is swept -> grid management (n) -> step n + 1
+//   sweep warps: take a tile ticket of any open instance, sweep the tile, count it done.
+// The tickets of step n + 1 are issued only after step n + 1 is planned (its counters are reset then), so a
+// ticket taken late always belongs to a planned step. Every wait is bounded by the SM clock: an instance
+// whose sweep does not complete within kWaitCycles stops with IMEXDS_ERR_TIMEOUT; an idle sweep warp leaves
+// after kWaitCycles. The per-instance work and its order are those of k_group: the results are the same.
+constexpr long long kWaitCycles = 40000000000LL;  // ~20 s at 2 GHz
+
+template <bool CREATION>
+__global__ void __launch_bounds__(128, 2) k_group_async(Dev d, const int* ginst, const int2* grange, int max_steps,
+                                                     long long* phase_cycles) {
+  const int2 gr = grange[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ int s_open[32], s_next[32], s_done[32], s_ntiles[32];
+  __shared__ int s_alive;
+  if (threadIdx.x < 32) {
+    s_open[threadIdx.x] = 0;
+    s_next[threadIdx.x] = 0;
+    s_done[threadIdx.x] = 0;
+    s_ntiles[threadIdx.x] = 0;
+  }
+  if (threadIdx.x == 0) s_alive = 0;
+  __syncthreads();
+  const int ii = (warp == 0 && lane < gr.y) ? ginst[gr.x + lane] : -1;
+  bool live = false;
+  if (ii >= 0) {
+    const Inst& I = d.inst[ii];
+    live = I.active && !I.status;
+    if (live) atomicAdd(&s_alive, 1);
+  }
+  __syncthreads();
+  volatile int* v_open = s_open;
+  volatile int* v_done = s_done;
+  volatile int* v_alive = &s_alive;
+  if (warp == 0) {
+    if (!live) return;
+    Inst& I = d.inst[ii];
+    const int nt = (I.N + 31) >> 5;
+    long long cp = 0, cd = 0, cw = 0, cq = 0;
+    for (int step = 0; step < max_steps; ++step) {
+      long long c0 = clock64();
+      for (int z = I.zone_off; z < I.zone_off + I.zone_cap; ++z) {
+        d.zones[z].merge_mask = 0;
+        if (d.zones[z].alive) pre_zone(d, z);
+      }
+      for (int z = I.zone_off; z < I.zone_off + I.zone_cap; ++z)
+        if (d.zones[z].alive && !I.status) plan_zone(d, z);
+      // open the sweep of this step: counters first, then the flag
+      s_done[lane] = 0;
+      __threadfence_block();
+      s_next[lane] = 0;
+      s_ntiles[lane] = (I.status) ? 0 : nt;
+      __threadfence_block();
+      v_open[lane] = 1;
+      long long c1 = clock64();
+      if (!I.status)
+        for (int z = I.zone_off; z < I.zone_off + I.zone_cap; ++z)
+          if (d.zones[z].alive && !I.status) dts_zone(d, z);
+      long long c2 = clock64();
+      bool timeout = false;
+      const int need = ((volatile int*)s_ntiles)[lane];  // every ticket issued for this step is swept first
+      while (v_done[lane] < need) {
+        __nanosleep(64);
+        if (clock64() - c2 > kWaitCycles) {
+          timeout = true;
+          break;
+        }
+      }
+      v_open[lane] = 0;
+      __threadfence_block();
+      long long c3 = clock64();
+      if (timeout) {
+        set_status(I, IMEXDS_ERR_TIMEOUT);
+        break;
+      }
+      post_inst(d, ii);
+      long long c4 = clock64();
+      cp += c1 - c0;
+      cd += c2 - c1;
+      cw += c3 - c2;
+      cq += c4 - c3;
+      if (!I.active || I.status) break;
+    }
+    v_open[lane] = 0;
+    __threadfence_block();
+    atomicSub(&s_alive, 1);
+    if (phase_cycles) {
+      // the slowest lane of the group: its boundary solves + plan, dual time, waits for the sweep, post
+      atomicMax((unsigned long long*)&phase_cycles[4 * blockIdx.x + 0], (unsigned long long)cp);
+      atomicMax((unsigned long long*)&phase_cycles[4 * blockIdx.x + 2], (unsigned long long)cd);
+      atomicMax((unsigned long long*)&phase_cycles[4 * blockIdx.x + 3], (unsigned long long)(cq + cw));
+    }
+    return;
+  }
+  // sweep warps: lane 0 reads the shared state and takes the ticket, the warp follows its decision
+  // (sweep_tile32 needs all 32 lanes)
+  long long busy = 0, idle0 = clock64();
+  int k = (gr.y > 0) ? (warp - 1) % gr.y : 0;
+  for (;;) {
+    int alive = 0, kk = -1, t = 0;
+    if (lane == 0) {
+      alive = *v_alive;
+      for (int q = 0; alive > 0 && q < gr.y; ++q) {
+        const int c = (k + q) % gr.y;
+        if (!v_open[c]) continue;
+        const int tt = atomicAdd(&s_next[c], 1);
+        if (tt < ((volatile int*)s_ntiles)[c]) {
+          kk = c;
+          t = tt;
+          break;
+        }
+      }
+      __threadfence_block();  // the step's plan (written before its tickets were issued) is read after this
+    }
+    alive = __shfl_sync(0xffffffffu, alive, 0);
+    kk = __shfl_sync(0xffffffffu, kk, 0);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    __syncwarp();
+    if (alive <= 0) break;
+    if (kk >= 0) {
+      long long b0 = clock64();
+      sweep_tile32<CREATION>(d, ginst[gr.x + kk], t << 5);
+      __threadfence_block();
+      __syncwarp();
+      if (lane == 0) atomicAdd(&s_done[kk], 1);
+      busy += clock64() - b0;
+      k = kk;
+      idle0 = clock64();
+    } else {
+      __nanosleep(128);
+      if (clock64() - idle0 > kWaitCycles) break;
+    }
+  }
+  if (phase_cycles && lane == 0) atomicMax((unsigned long long*)&phase_cycles[4 * blockIdx.x + 1], (unsigned long long)busy);
+}
+
 // Wave-speed maximum over all cells of every instance and the first dt (before the first step).
 __global__ void k_init_dt(Dev d, int n_inst) {
   int ii = blockIdx.x;
@@ -1437,7 +1577,7 @@ struct imexds_ctx {
   int graph_steps = 0;
   cudaStream_t side = nullptr;            // second stream of the step graph (k_dts beside k_sweep)
   int schedule = 0;                       // 1 per-step kernels, 2 instance groups (0 auto at set_states)
-  int schedule_opt = 0, group_cells = 16384, use_groups = 0, group_threads = 128;
+  int schedule_opt = 0, group_cells = 16384, use_groups = 0, group_threads = 128, async_groups = 0;
   int n_groups = 0;
   long long* d_phase = nullptr;  // per-group phase cycles (timing mode)
   int* d_ginst = nullptr;
@@ -1632,10 +1772,16 @@ imexds_status run_groups(imexds_ctx* c, long long max_steps, bool until_done) {
   while (done < max_steps) {
     int n = (int)std::min<long long>(max_steps - done, 1 << 30);
     if (c->timing) cudaEventRecord(c->gev[0], c->stream);
-    if (c->opts.creation)
+    if (c->async_groups) {
+      if (c->opts.creation)
+        k_group_async<true><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n, pc);
+      else
+        k_group_async<false><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n, pc);
+    } else if (c->opts.creation) {
       k_group<true><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n, pc);
-    else
+    } else {
       k_group<false><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n, pc);
+    }
     if (c->timing) cudaEventRecord(c->gev[1], c->stream);
     k_count_active<<<1, 256, 0, c->stream>>>(c->d, c->n_inst);
     c->launches += 2;
@@ -1803,6 +1949,10 @@ imexds_status imexds_create(const imexds_problem* prob, const imexds_options* op
   c->opts = Opts{o.cfl, o.theta_nb, o.tol_nb, o.tol_k, o.res_mode, o.l_max, o.newton_tol, o.newton_itmax,
                  o.alpha_min, o.split_ratio, o.creation};
   c->zone_cap_opt = o.zone_capacity;
+  if (o.schedule < 0 || o.schedule > 3) {
+    delete c;
+    return IMEXDS_ERR_ARG;
+  }
   c->schedule_opt = o.schedule;
   if (o.group_cells > 0) c->group_cells = o.group_cells;
   if (o.group_threads != 0) {
@@ -2039,7 +2189,8 @@ imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double*
     int maxcap = 0;
     for (int i = 0; i < n; ++i) maxcap = std::max(maxcap, zone_cap[i]);
     // automatic schedule: groups for batches of instances with few boundaries each
-    c->use_groups = (c->schedule_opt == 2) || (c->schedule_opt == 0 && n >= 2 && maxcap <= 16);
+    c->use_groups = (c->schedule_opt == 2 || c->schedule_opt == 3) || (c->schedule_opt == 0 && n >= 2 && maxcap <= 16);
+    c->async_groups = (c->schedule_opt == 3);
   }
   c->n_lat = n_lat;
   c->n_zone_slots = n_zone;
@@ -2302,12 +2453,13 @@ imexds_status imexds_get_group_phase_cycles(imexds_ctx* c, int64_t* slowest4, in
 }
 
 imexds_status imexds_set_schedule(imexds_ctx* c, int32_t schedule) {
-  if (!c || schedule < 0 || schedule > 2) return IMEXDS_ERR_ARG;
+  if (!c || schedule < 0 || schedule > 3) return IMEXDS_ERR_ARG;
   if (!c->loaded) return IMEXDS_ERR_STATE;
   c->schedule_opt = schedule;
   int maxcap = 0;
   for (int i = 0; i < c->n_inst; ++i) maxcap = std::max(maxcap, c->zone_cap[i]);
-  c->use_groups = (schedule == 2) || (schedule == 0 && c->n_inst >= 2 && maxcap <= 16);
+  c->use_groups = (schedule == 2 || schedule == 3) || (schedule == 0 && c->n_inst >= 2 && maxcap <= 16);
+  c->async_groups = (schedule == 3);
   return IMEXDS_OK;
 }
 

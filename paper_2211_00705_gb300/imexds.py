@@ -228,7 +228,8 @@ class Imexds:
     KERNELS = ["k_pre", "k_plan", "k_sweep", "k_dts", "k_post", "k_group"]
 
     def set_schedule(self, schedule: int):
-        """0 automatic, 1 per-step kernels, 2 instance groups."""
+        """0 automatic, 1 per-step kernels, 2 instance groups in lockstep, 3 instance groups advancing
+        independently."""
         _check(load().imexds_set_schedule(self.h, int(schedule)))
 
     def kernel_times(self) -> dict:

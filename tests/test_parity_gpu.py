@@ -26,7 +26,8 @@ def test_single_instance_workload():
     np.testing.assert_array_equal(sa["dts_iters"], sb["dts_iters"])
 
 
-SCHEDULES = [pytest.param(1, id="per-step-kernels"), pytest.param(2, id="instance-groups")]
+SCHEDULES = [pytest.param(1, id="per-step-kernels"), pytest.param(2, id="instance-groups"),
+             pytest.param(3, id="independent-instance-groups")]
 
 
 @pytest.mark.parametrize("schedule", SCHEDULES)
