@@ -108,6 +108,39 @@ def measure_adjoint(dev, steps, warmup, scale=1.0):
             "dts_iters_per_step": float(st["dts_iters"].sum() / max(1, st["steps"].sum()))}
 
 
+def measure_large_domain_sweep(n_steps=100):
+    """The explicit sweep on the large single domain (2^24 cells, 1024 vapour bubbles, 2048 boundaries): the
+    per-step schedule with CUDA events around every kernel; the sweep's algorithmic traffic is 32 B per
+    lattice cell (rho, m read and written; phase and owner bytes not counted) against the measured HBM copy
+    bandwidth. State arrays: 2 x 268 MB, far above L2, so every launch streams from HBM."""
+    from paper_2211_00705_gb300 import inputs as I
+    from paper_2211_00705_gb300.imexds import Imexds
+    b = I.workload(2)
+    ctx = Imexds.from_batch(b, schedule=1)
+    ctx.step(8)                                  # warm-up: graph build, first steps
+    ctx.set_kernel_timing(True)
+    ctx.step(n_steps)
+    kt = ctx.kernel_times()
+    ctx.set_kernel_timing(False)
+    st = ctx.get_states()
+    ctx.close()
+    ms, n = kt["k_sweep"]
+    per = ms / 1e3 / max(n, 1)
+    cells = int(b.n_lattice[0])
+    gbs = 32.0 * cells / per / 1e9
+    peak = None
+    try:
+        peak = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, ValueError, KeyError):
+        peak = None
+    tot = sum(v[0] for v in kt.values())
+    return {"workload": b.name, "steps_timed": n_steps, "k_sweep_ms_per_launch": per * 1e3,
+            "algorithmic_bytes_per_launch": 32.0 * cells, "achieved_gbs": gbs, "peak_gbs": peak,
+            "frac": (gbs / peak) if peak else None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+            "cell_steps_per_s_sweep": cells / per, "status": int(st["status"][0]),
+            "per_step_share": {k: round(v[0] / tot, 4) if tot else None for k, v in kt.items()}}
+
+
 def measure_plain(batch, n_sample=16):
     """The plain single-instance GPU step: the same kernels, one instance per context, per-step schedule
     (one launch per kernel and step), on a sample of the workload's instances run one after another."""
@@ -260,6 +293,7 @@ def main():
                     help="fraction of the 4096 instances (smaller cases for profiling only)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--no-plain", action="store_true", help="skip the single-instance comparison")
+    ap.add_argument("--no-hbm", action="store_true", help="skip the large-domain sweep (HBM) measurement")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -408,6 +442,8 @@ def main():
             line["plain_single_instance"] = plain
         if not args.no_adjoint:
             line["adjoint"] = measure_adjoint(dev, max(1, args.steps // 2), 1, scale=args.scale)
+        if not args.no_hbm:
+            line["large_domain_sweep"] = measure_large_domain_sweep()
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(batch)
         print(json.dumps(line), flush=True)

@@ -18,8 +18,6 @@ import numpy as np
 
 CANDIDATES = [
     {"schedule": 1},
-    {"schedule": 3, "group_threads": 128, "group_cells": 16384},
-    {"schedule": 3, "group_threads": 128, "group_cells": 8192},
     {"schedule": 2, "group_threads": 128, "group_cells": 16384},
     {"schedule": 2, "group_threads": 128, "group_cells": 8192},
     {"schedule": 2, "group_threads": 96, "group_cells": 16384},

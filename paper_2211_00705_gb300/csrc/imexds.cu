@@ -86,6 +86,7 @@ struct Ctrl {
 struct Dev {
   double* rho[2];
   double* m[2];
+  double* u[2];  // u = m / rho of every lattice cell, written by whoever writes the cell (saves a division)
   unsigned char* phase;
   int* own;
   Zone* zones;
@@ -330,7 +331,7 @@ __device__ inline CellS load_cell(const Dev& d, const Inst& I, int j) {
     if (c.ow < 0) {
       c.r = d.rho[I.parity][g];
       c.m = d.m[I.parity][g];
-      c.u = c.m / c.r;
+      c.u = d.u[I.parity][g];
       c.f1 = __fma_rn(c.m, c.u, pressure_fma(c_fluid.ph[c.ph], c.r));
     }
   }
@@ -492,10 +493,12 @@ __device__ void sweep_tile32(const Dev& d, int ii, int j0) {
       r1 = __fma_rn(-I.lam, fr.F0L - fj.F0R, C.r);
       m1 = __fma_rn(-I.lam, fr.F1L - fj.F1R, C.m);
     }
+    const double u1 = m1 / r1;
     d.rho[I.parity ^ 1][g] = r1;
     d.m[I.parity ^ 1][g] = m1;
+    d.u[I.parity ^ 1][g] = u1;
     if (!(r1 > 0.0) || !isfinite(r1) || !isfinite(m1)) set_status(I, IMEXDS_ERR_NONPHYSICAL);
-    smax = fabs(m1 / r1) + c_fluid.ph[C.ph].a;
+    smax = fabs(u1) + c_fluid.ph[C.ph].a;
   }
   for (int off = 16; off > 0; off >>= 1) smax = fmax(smax, __shfl_down_sync(0xffffffffu, smax, off));
   if (lane == 0 && smax > 0.0) atomicMax(&I.smax_bits, dbits(smax));
@@ -777,6 +780,7 @@ __device__ void dts_simple(const Dev& d, int zi) {
   }
   double* nr = d.rho[cur ^ 1] + I.lat_off;
   double* nm = d.m[cur ^ 1] + I.lat_off;
+  double* nu = d.u[cur ^ 1] + I.lat_off;
   double smax = 0.0;
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
@@ -787,11 +791,13 @@ __device__ void dts_simple(const Dev& d, int zi) {
     const double r1 = (hU0[q] - dt * (f0r - f0l)) / hn1;
     const double m1 = (hU1[q] - dt * (f1r - f1l)) / hn1;
     if (!(r1 > 0.0) || !isfinite(r1) || !isfinite(m1)) set_status(I, IMEXDS_ERR_NONPHYSICAL);
-    smax = fmax(smax, fabs(m1 / r1) + c_fluid.ph[ph[q]].a);
+    const double u1 = m1 / r1;
+    smax = fmax(smax, fabs(u1) + c_fluid.ph[ph[q]].a);
     const int e = (PBF == 2) ? q - 1 : q;
     if (e < 0 || e > 1) {
       nr[jp] = r1;
       nm[jp] = m1;
+      nu[jp] = u1;
     } else {
       Z.r[e] = r1;
       Z.m[e] = m1;
@@ -910,17 +916,21 @@ __device__ __noinline__ void dts_zone_general(const Dev& d, int zi) {
       return;
   }
   double smax = 0.0;
+  double* nu = d.u[cur ^ 1] + I.lat_off;
   for (int q = 0; q < nq; ++q) {
     int e = q + e0;
     double r1 = out_r[q], m1 = out_m[q];
     if (!(r1 > 0.0) || !isfinite(r1) || !isfinite(m1) || !(out_w[q] > 0.0)) set_status(I, IMEXDS_ERR_NONPHYSICAL);
-    smax = fmax(smax, fabs(m1 / r1) + c_fluid.ph[B.ph[q]].a);
+    const double u1 = m1 / r1;
+    smax = fmax(smax, fabs(u1) + c_fluid.ph[B.ph[q]].a);
     if (e < 0) {
       nr[Z.A - 1] = r1;
       nm[Z.A - 1] = m1;
+      nu[Z.A - 1] = u1;
     } else if (e >= Z.nc) {
       nr[Z.B] = r1;
       nm[Z.B] = m1;
+      nu[Z.B] = u1;
     } else {
       Z.r[e] = r1;
       Z.m[e] = m1;
@@ -969,6 +979,7 @@ __device__ __noinline__ void post_inst(const Dev& d, int ii) {
   const int nxt = I.parity ^ 1;
   double* nr = d.rho[nxt] + I.lat_off;
   double* nm = d.m[nxt] + I.lat_off;
+  double* nu = d.u[nxt] + I.lat_off;
   unsigned char* lph = d.phase + I.lat_off;
   Zone* zones = d.zones + I.zone_off;
   for (int z = 0; z < I.zone_cap; ++z) {
@@ -1031,6 +1042,7 @@ __device__ __noinline__ void post_inst(const Dev& d, int ii) {
     while (Z.nc > 1 && !Z.fpb[1] && Z.fj[1] == Z.A + 1 && Z.w[0] == h) {
       nr[Z.A] = Z.r[0];
       nm[Z.A] = Z.m[0];
+      nu[Z.A] = Z.m[0] / Z.r[0];
       lph[Z.A] = (unsigned char)Z.ph[0];
       zone_erase_cell(Z, 0);
       Z.A += 1;
@@ -1041,6 +1053,7 @@ __device__ __noinline__ void post_inst(const Dev& d, int ii) {
     while (Z.nc > 1 && !Z.fpb[Z.nc - 1] && Z.fj[Z.nc - 1] == Z.B - 1 && Z.w[Z.nc - 1] == h) {
       nr[Z.B - 1] = Z.r[Z.nc - 1];
       nm[Z.B - 1] = Z.m[Z.nc - 1];
+      nu[Z.B - 1] = Z.m[Z.nc - 1] / Z.r[Z.nc - 1];
       lph[Z.B - 1] = (unsigned char)Z.ph[Z.nc - 1];
       Z.nc--;
       Z.B -= 1;
@@ -1104,6 +1117,7 @@ __device__ __noinline__ void post_inst(const Dev& d, int ii) {
       int j = Z.fj[k];
       nr[j] = Z.r[k];
       nm[j] = Z.m[k];
+      nu[j] = Z.m[k] / Z.r[k];
       lph[j] = (unsigned char)Z.ph[k];
     }
     Z.nc = a;
@@ -1662,6 +1676,7 @@ void free_dev(imexds_ctx* c) {
   for (int k = 0; k < 2; ++k) {
     cudaFree(d.rho[k]);
     cudaFree(d.m[k]);
+    cudaFree(d.u[k]);
   }
   cudaFree(d.phase);
   cudaFree(d.own);
@@ -1681,6 +1696,7 @@ void free_dev(imexds_ctx* c) {
   for (int k = 0; k < 2; ++k) {
     cudaFree(sv.rho[k]);
     cudaFree(sv.m[k]);
+    cudaFree(sv.u[k]);
   }
   cudaFree(sv.phase);
   cudaFree(sv.zones);
@@ -2120,13 +2136,17 @@ imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double*
   std::vector<int2> tiles;
   for (int i = 0; i < n; ++i)
     for (int j0 = 0; j0 < c->N[i]; j0 += 32) tiles.push_back(make_int2(i, j0));
+  std::vector<double> hu(n_lat);
+  for (int g = 0; g < n_lat; ++g) hu[g] = hm[g] / hr[g];  // IEEE division: the bits the kernels produce
   free_dev(c);
   Dev& d = c->d;
   for (int k = 0; k < 2; ++k) {
     CK(cudaMalloc(&d.rho[k], sizeof(double) * n_lat));
     CK(cudaMalloc(&d.m[k], sizeof(double) * n_lat));
+    CK(cudaMalloc(&d.u[k], sizeof(double) * n_lat));
     CK(cudaMemcpyAsync(d.rho[k], hr.data(), sizeof(double) * n_lat, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(d.m[k], hm.data(), sizeof(double) * n_lat, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(d.u[k], hu.data(), sizeof(double) * n_lat, cudaMemcpyHostToDevice, c->stream));
   }
   CK(cudaMalloc(&d.phase, n_lat));
   CK(cudaMemcpyAsync(d.phase, hph.data(), n_lat, cudaMemcpyHostToDevice, c->stream));
@@ -2151,8 +2171,10 @@ imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double*
     for (int k = 0; k < 2; ++k) {
       CK(cudaMalloc(&sv.rho[k], sizeof(double) * n_lat));
       CK(cudaMalloc(&sv.m[k], sizeof(double) * n_lat));
+      CK(cudaMalloc(&sv.u[k], sizeof(double) * n_lat));
       CK(cudaMemcpyAsync(sv.rho[k], d.rho[k], sizeof(double) * n_lat, cudaMemcpyDeviceToDevice, c->stream));
       CK(cudaMemcpyAsync(sv.m[k], d.m[k], sizeof(double) * n_lat, cudaMemcpyDeviceToDevice, c->stream));
+      CK(cudaMemcpyAsync(sv.u[k], d.u[k], sizeof(double) * n_lat, cudaMemcpyDeviceToDevice, c->stream));
     }
     CK(cudaMalloc(&sv.phase, n_lat));
     CK(cudaMemcpyAsync(sv.phase, d.phase, n_lat, cudaMemcpyDeviceToDevice, c->stream));
@@ -2341,6 +2363,7 @@ imexds_status imexds_reset(imexds_ctx* c) {
   for (int k = 0; k < 2; ++k) {
     CK(cudaMemcpyAsync(d.rho[k], sv.rho[k], sizeof(double) * c->n_lat, cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaMemcpyAsync(d.m[k], sv.m[k], sizeof(double) * c->n_lat, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(d.u[k], sv.u[k], sizeof(double) * c->n_lat, cudaMemcpyDeviceToDevice, c->stream));
   }
   CK(cudaMemcpyAsync(d.phase, sv.phase, c->n_lat, cudaMemcpyDeviceToDevice, c->stream));
   CK(cudaMemsetAsync(d.own, 0xff, sizeof(int) * c->n_lat, c->stream));
