@@ -18,8 +18,9 @@
 //   * Face Jacobians come from forward-mode dual numbers (adjoint_local.cuh); the boundary flux is
 //     differentiated at the converged star pressures by the implicit function theorem.
 // Decisions (merges, blocks, splits, the argmax cell, dual-time stop) are frozen: the gradient is that
-// of the discrete map along the replayed trajectory. Phase creation (App. B) is not differentiated: a
-// replay that creates a phase stops the instance with IMEXDS_ERR_STATE.
+// of the discrete map along the replayed trajectory. Phase creation (App. B) is differentiated too: the
+// created cell's insertion, the per-side fluxes and moving faces at the creation face, and the creation
+// system itself by the implicit function theorem.
 #pragma once
 #include "adjoint_local.cuh"
 
@@ -32,7 +33,8 @@ constexpr int AMAXBLK = 8;   // blocks per step
 constexpr int AMAXB = 8;     // cells per block
 constexpr int AMAXBC = 32;   // block cells per step, all blocks
 constexpr int AMAXEV = 8;    // merges and splits per step
-constexpr int ACAP_PAD = 64; // cells a list may grow by (splits) beyond its initial count
+constexpr int ACAP_PAD = 64; // cells a list may grow by (splits, created cells) beyond its initial count
+constexpr int AMAXCR = 4;    // phase creations per step
 
 struct StepRec {
   double dt;
@@ -43,6 +45,9 @@ struct StepRec {
   double Wr[AMAXBC], Wm[AMAXBC];  // last dual-time iterate of each block cell, block after block
   double ppl[AMAXPB], ppr[AMAXPB];  // converged star pressures at that iterate, interior boundary faces in order
   int sp_i[AMAXEV], sp_case[AMAXEV];
+  int n_cr, cr_g[AMAXCR], cr_P[AMAXCR];  // creation faces (post-merge numbering) and parent phases
+  double cr_x[AMAXCR][3];                // converged (p_P-, p_C, p_P+)
+  double cr_o[AMAXCR][7];                // z1, z2, u_C, p_C, rho_C, w1, w2
 };
 
 struct AInst {
@@ -69,7 +74,7 @@ struct ADev {
   // working cell list and faces (pwl/pwr: last converged star pressures at a boundary face, the start of
   // its next solve, as in the forward kernels)
   double *w, *r, *m, *fx, *pwl, *pwr;
-  unsigned char *ph, *fpb;
+  unsigned char *ph, *fpb, *cdet;  // cdet: creation detected at a face (App. B)
   int* fj;
   // face scratch
   double *F0, *F1, *LF0, *LF1, *CL0, *CL1, *CR0, *CR1;
@@ -174,8 +179,50 @@ struct SharedStep {
   int M, kmax, clipped, done, bad;
   int n_pb, pb[AMAXPB];
   int n_blk, blo[AMAXBLK], bhi[AMAXBLK];
+  int n_cr, cr_g[AMAXCR], cr_P[AMAXCR];
+  double cr_o[AMAXCR][7];
   double t_end;
 };
+
+// creation event at face g of this step, or -1
+__device__ inline int cr_at(const SharedStep& S, int g) {
+  for (int k = 0; k < S.n_cr; ++k)
+    if (S.cr_g[k] == g) return k;
+  return -1;
+}
+
+// The explicit update of cell i (Eq. godunov_meth:nonunif): the fluxes it sees at its right and left faces
+// and its new width. At a creation face the cell on each side sees that side's flux (mass flux z1 on the
+// left, z2 on the right) and the face moves with w1 / w2; elsewhere F0/F1 hold the face flux.
+struct CellUpd {
+  double fr0, fr1, fl0, fl1, wl, wr, h1;
+};
+__device__ inline CellUpd cell_upd(const double* F0, const double* F1, const SharedStep& S, int i, double w,
+                                   double dt) {
+  CellUpd c;
+  c.fr0 = F0[i + 1];
+  c.fr1 = F1[i + 1];
+  c.fl0 = F0[i];
+  c.fl1 = F1[i];
+  c.wl = c.wr = 0.0;
+  if (S.n_cr) {
+    const int kr = cr_at(S, i + 1), kl = cr_at(S, i);
+    if (kr >= 0) {
+      const double* e = S.cr_o[kr];
+      c.fr0 = -e[0];
+      c.fr1 = -e[0] * e[2] + e[3];
+      c.wl = e[5];
+    }
+    if (kl >= 0) {
+      const double* e = S.cr_o[kl];
+      c.fl0 = -e[1];
+      c.fl1 = -e[1] * e[2] + e[3];
+      c.wr = e[6];
+    }
+  }
+  c.h1 = w + (c.wl - c.wr) * dt;
+  return c;
+}
 
 __device__ inline bool in_block(const SharedStep& S, int i) {
   for (int b = 0; b < S.n_blk; ++b)
@@ -592,10 +639,72 @@ __device__ void fwd_step(const ADev& A, AInst& I, SharedStep& S, double t_end, S
   __syncthreads();
   if (S.bad) return;
   M = S.M;
-  // (4) phase creation is not part of the differentiated scheme
+  // (4) phase creation (App. B) at same-phase faces between two explicit cells: detection by the
+  //     no-transition star pressure, a face whose left neighbour face is also detected is not used
+  if (tid == 0) S.n_cr = 0;
+  __syncthreads();
+  if (c_opts.creation) {
+    for (int g = tid; g <= M; g += blockDim.x) {
+      unsigned char det = 0;
+      if (g >= 1 && g < M && !A.fpb[o + g] && !in_block(S, g - 1) && !in_block(S, g)) {
+        const int P = A.ph[o + g];
+        const double ps = nopt_star(c_fluid.ph[P], A.r[o + g - 1], A.m[o + g - 1] / A.r[o + g - 1], A.r[o + g],
+                                    A.m[o + g] / A.r[o + g]);
+        det = (P == LIQ) ? (ps < c_fluid.p_min) : (ps > c_fluid.p_tilde);
+      }
+      A.cdet[o + g] = det;
+    }
+    __syncthreads();
+    for (int g = 1 + tid; g < M; g += blockDim.x)
+      if (A.cdet[o + g] && !A.cdet[o + g - 1]) {
+        const int q = atomicAdd(&S.n_cr, 1);
+        if (q < AMAXCR) S.cr_g[q] = g;
+      }
+    __syncthreads();
+    if (tid == 0) {
+      if (S.n_cr > AMAXCR) {
+        afail(I, IMEXDS_ERR_CAPACITY);
+        S.bad = 1;
+        S.n_cr = 0;
+      }
+      for (int a = 1; a < S.n_cr; ++a) {
+        int v = S.cr_g[a], b = a - 1;
+        while (b >= 0 && S.cr_g[b] > v) {
+          S.cr_g[b + 1] = S.cr_g[b];
+          --b;
+        }
+        S.cr_g[b + 1] = v;
+      }
+      for (int k = 0; k < S.n_cr && !S.bad; ++k) {
+        const int g = S.cr_g[k];
+        const int P = A.ph[o + g];
+        CreateOut R = creation_solve(c_fluid, c_opts, I.tau, P, A.r[o + g - 1], A.m[o + g - 1], A.r[o + g], A.m[o + g]);
+        if (!R.ok) {
+          afail(I, IMEXDS_ERR_PB_NOCONV);
+          S.bad = 1;
+          break;
+        }
+        S.cr_P[k] = P;
+        const double out[7] = {R.z1, R.z2, R.uC, R.pC, R.rhoC, R.w1, R.w2};
+        for (int q = 0; q < 7; ++q) S.cr_o[k][q] = out[q];
+        if (rec) {
+          rec->cr_g[k] = g;
+          rec->cr_P[k] = P;
+          rec->cr_x[k][0] = R.pPl;
+          rec->cr_x[k][1] = R.pC;
+          rec->cr_x[k][2] = R.pPr;
+          for (int q = 0; q < 7; ++q) rec->cr_o[k][q] = out[q];
+        }
+      }
+    }
+    __syncthreads();
+    if (S.bad) return;
+  }
+  if (rec && tid == 0) rec->n_cr = S.n_cr;
   // (5) explicit fluxes from U^n at every face outside the blocks, then the explicit update
   for (int g = tid; g <= M; g += blockDim.x) {
     if (face_in_block(S, g)) continue;
+    if (S.n_cr && cr_at(S, g) >= 0) continue;  // creation faces: the per-side fluxes of the event
     double f0, f1;
     if (g == 0)
       phys_flux_fast(c_fluid.ph[A.ph[o]], A.r[o], A.m[o], f0, f1);
@@ -610,7 +719,12 @@ __device__ void fwd_step(const ADev& A, AInst& I, SharedStep& S, double t_end, S
   for (int i = tid; i < M; i += blockDim.x) {
     if (in_block(S, i)) continue;
     const double wi = A.w[o + i];
-    if (wi == I.h) {
+    if (S.n_cr && (cr_at(S, i) >= 0 || cr_at(S, i + 1) >= 0)) {
+      const CellUpd c = cell_upd(A.F0 + o, A.F1 + o, S, i, wi, S.dt);
+      A.r[o + i] = (wi * A.r[o + i] - S.dt * (c.fr0 - c.fl0)) / c.h1;
+      A.m[o + i] = (wi * A.m[o + i] - S.dt * (c.fr1 - c.fl1)) / c.h1;
+      A.w[o + i] = c.h1;
+    } else if (wi == I.h) {
       A.r[o + i] = __fma_rn(-S.lam, A.F0[o + i + 1] - A.F0[o + i], A.r[o + i]);
       A.m[o + i] = __fma_rn(-S.lam, A.F1[o + i + 1] - A.F1[o + i], A.m[o + i]);
     } else {
@@ -639,6 +753,48 @@ __device__ void fwd_step(const ADev& A, AInst& I, SharedStep& S, double t_end, S
         if (A.fpb[o + lo + q]) A.fx[o + lo + q] += wc[q] * S.dt;
     }
     if (rec) rec->n_pbf = rp;
+    // (7) created cells (App. B), highest face first: width (w2 - w1) dt between two new boundaries at
+    //     x_g + w1 dt and x_g + w2 dt, state (rho_C, rho_C u_C), the other phase
+    for (int k = S.n_cr - 1; k >= 0 && ok; --k) {
+      const int g = S.cr_g[k];
+      const double* e = S.cr_o[k];
+      const int Mi = S.M;
+      if (Mi + 1 > I.cap || S.n_pb + 2 > AMAXPB) {
+        afail(I, IMEXDS_ERR_CAPACITY);
+        ok = false;
+        break;
+      }
+      const double xg = I.xL + (double)A.fj[o + g] * I.h;
+      list_open(A.w + o, A.r + o, A.m + o, A.ph + o, A.fpb + o, A.fj + o, A.fx + o, A.pwl + o, A.pwr + o, Mi, g);
+      S.M = Mi + 1;
+      A.w[o + g] = (e[6] - e[5]) * S.dt;
+      A.r[o + g] = e[4];
+      A.m[o + g] = e[4] * e[2];
+      A.ph[o + g] = (unsigned char)(1 - S.cr_P[k]);
+      A.fpb[o + g] = 1;
+      A.fx[o + g] = xg + e[5] * S.dt;
+      A.fpb[o + g + 1] = 1;
+      A.fx[o + g + 1] = xg + e[6] * S.dt;
+      A.pwl[o + g] = A.pwr[o + g] = A.pwl[o + g + 1] = A.pwr[o + g + 1] = 0.0;
+      // boundary list: faces at or after g move one up; the two new boundaries join it (kept sorted)
+      int np = 0, tmp[AMAXPB];
+      bool put = false;
+      for (int p = 0; p < S.n_pb; ++p) {
+        int f = S.pb[p] >= g ? S.pb[p] + 1 : S.pb[p];
+        if (!put && f > g) {
+          tmp[np++] = g;
+          tmp[np++] = g + 1;
+          put = true;
+        }
+        tmp[np++] = f;
+      }
+      if (!put) {
+        tmp[np++] = g;
+        tmp[np++] = g + 1;
+      }
+      for (int p = 0; p < np; ++p) S.pb[p] = tmp[p];
+      S.n_pb = np;
+    }
     // splits of boundary cells wider than split_ratio h (Sec. 3.4), keeping fixed faces on the lattice
     int nsp = 0;
     if (ok) {
@@ -865,7 +1021,9 @@ __device__ void rev_step(const ADev& A, AInst& I, SharedStep& S, int slot, const
   const long long to = (long long)slot * A.stride + o;
   const int Mn = A.tp_M[(long long)slot * A.n_inst + (int)(&I - A.I)];
   const double dt = R.dt;
-  // (a) splits^T on the adjoint list
+  double lam_dt = 0.0;        // thread 0 accumulates d(dt) contributions here
+  double lcr[AMAXCR][7];      // thread 0: adjoints of the creation outputs z1, z2, u_C, p_C, rho_C, w1, w2
+  // (a) splits^T on the adjoint list, then the created cells leave it (insertion^T)
   if (tid == 0) {
     int Mc = I.M;
     for (int q = R.n_split - 1; q >= 0; --q) {
@@ -880,6 +1038,31 @@ __device__ void rev_step(const ADev& A, AInst& I, SharedStep& S, int slot, const
       }
       lam_erase(A.lw + o, A.lr + o, A.lm + o, A.lx + o, Mc, i + 1);
       Mc--;
+    }
+    S.n_cr = R.n_cr;
+    for (int k = 0; k < R.n_cr; ++k) {
+      S.cr_g[k] = R.cr_g[k];
+      S.cr_P[k] = R.cr_P[k];
+      for (int q = 0; q < 7; ++q) {
+        S.cr_o[k][q] = R.cr_o[k][q];
+        lcr[k][q] = 0.0;
+      }
+    }
+    // the created cell of event k sits at g_k + k (each earlier event shifted it by one): highest first.
+    // w_C = (w2 - w1) dt, rho_C, m_C = rho_C u_C, boundaries at x_g + w1 dt and x_g + w2 dt
+    for (int k = R.n_cr - 1; k >= 0; --k) {
+      const int p = R.cr_g[k] + k;
+      const double* e = R.cr_o[k];
+      const double lwC = A.lw[o + p], lrC = A.lr[o + p], lmC = A.lm[o + p];
+      const double lxl = A.lx[o + p], lxr = A.lx[o + p + 1];
+      lcr[k][5] += (-lwC + lxl) * dt;
+      lcr[k][6] += (lwC + lxr) * dt;
+      lcr[k][4] += lrC + lmC * e[2];
+      lcr[k][2] += lmC * e[4];
+      lam_dt += lwC * (e[6] - e[5]) + lxl * e[5] + lxr * e[6];
+      lam_erase(A.lw + o, A.lr + o, A.lm + o, A.lx + o, Mc, p);
+      Mc--;
+      A.lx[o + p] = 0.0;  // the fixed face the boundaries were created at
     }
     S.M = Mc;  // post-merge count
     S.n_blk = R.n_blk;
@@ -927,6 +1110,7 @@ __device__ void rev_step(const ADev& A, AInst& I, SharedStep& S, int slot, const
   cta_zero(A.LF1 + o, M + 1);
   for (int g = tid; g <= M; g += blockDim.x) {
     if (face_in_block(S, g)) continue;
+    if (S.n_cr && cr_at(S, g) >= 0) continue;
     double f0, f1;
     if (g == 0)
       phys_flux_fast(c_fluid.ph[A.pph[o]], A.pr[o], A.pm[o], f0, f1);
@@ -939,7 +1123,6 @@ __device__ void rev_step(const ADev& A, AInst& I, SharedStep& S, int slot, const
   }
   __syncthreads();
   // (d) blocks (thread 0)
-  double lam_dt = 0.0;
   if (tid == 0) {
     int cell0 = 0, pbf = 0;
     double ltau = 0.0;
@@ -961,14 +1144,18 @@ __device__ void rev_step(const ADev& A, AInst& I, SharedStep& S, int slot, const
   // (e) explicit sweep^T: face adjoints from the explicit cells, then the face Jacobians at U^n
   for (int g = tid; g <= M; g += blockDim.x) {
     if (face_in_block(S, g)) continue;
+    if (S.n_cr && cr_at(S, g) >= 0) {  // a creation face: its adjoint goes to the event (thread 0, below)
+      A.CL0[o + g] = A.CL1[o + g] = A.CR0[o + g] = A.CR1[o + g] = 0.0;
+      continue;
+    }
     double l0 = A.LF0[o + g], l1 = A.LF1[o + g];
     if (g > 0 && !in_block(S, g - 1)) {
-      const double c = dt / A.pw[o + g - 1];
+      const double c = dt / cell_upd(A.F0 + o, A.F1 + o, S, g - 1, A.pw[o + g - 1], dt).h1;
       l0 -= c * A.lr[o + g - 1];
       l1 -= c * A.lm[o + g - 1];
     }
     if (g < M && !in_block(S, g)) {
-      const double c = dt / A.pw[o + g];
+      const double c = dt / cell_upd(A.F0 + o, A.F1 + o, S, g, A.pw[o + g], dt).h1;
       l0 += c * A.lr[o + g];
       l1 += c * A.lm[o + g];
     }
@@ -1003,11 +1190,22 @@ __device__ void rev_step(const ADev& A, AInst& I, SharedStep& S, int slot, const
   for (int i = tid; i < M; i += blockDim.x) {
     if (in_block(S, i)) continue;
     const double wi = A.pw[o + i], lr = A.lr[o + i], lm = A.lm[o + i];
-    const double dF = (A.F0[o + i + 1] - A.F0[o + i]) * lr + (A.F1[o + i + 1] - A.F1[o + i]) * lm;
-    A.nr[o + i] += lr;
-    A.nm[o + i] += lm;
-    A.nw[o + i] += A.lw[o + i] + dt * dF / (wi * wi);
-    ldt_part -= dF / wi;
+    const CellUpd c = cell_upd(A.F0 + o, A.F1 + o, S, i, wi, dt);
+    const double dF = (c.fr0 - c.fl0) * lr + (c.fr1 - c.fl1) * lm;
+    if (c.wl == 0.0 && c.wr == 0.0) {
+      A.nr[o + i] += lr;
+      A.nm[o + i] += lm;
+      A.nw[o + i] += A.lw[o + i] + dt * dF / (wi * wi);
+      ldt_part -= dF / wi;
+    } else {  // next to a creation face: the width moves with w1 / w2
+      const double r1 = (wi * A.pr[o + i] - dt * (c.fr0 - c.fl0)) / c.h1;
+      const double m1 = (wi * A.pm[o + i] - dt * (c.fr1 - c.fl1)) / c.h1;
+      const double sc = wi / c.h1, dw = c.wl - c.wr;
+      A.nr[o + i] += lr * sc;
+      A.nm[o + i] += lm * sc;
+      A.nw[o + i] += A.lw[o + i] + (lr * (A.pr[o + i] - r1) + lm * (A.pm[o + i] - m1)) / c.h1;
+      ldt_part += (-dF - (lr * r1 + lm * m1) * dw) / c.h1 + A.lw[o + i] * dw;
+    }
   }
   __syncthreads();
   // (f) gather the face contributions into the cells (faces inside a block contribute nothing here)
@@ -1026,6 +1224,45 @@ __device__ void rev_step(const ADev& A, AInst& I, SharedStep& S, int slot, const
   }
   double tot = cta_sum(S, ldt_part);
   __syncthreads();
+  // (g') creation faces^T (thread 0): the two cells beside each creation face see its per-side fluxes and
+  //      move its faces; the event's outputs go back to the adjacent states and tau through the implicit
+  //      function theorem on the creation system
+  if (tid == 0) {
+    for (int k = 0; k < S.n_cr; ++k) {
+      const int g = S.cr_g[k];
+      const double* e = S.cr_o[k];
+      double* L = lcr[k];
+      for (int side = 0; side < 2; ++side) {
+        const int i = g - 1 + side;
+        const double wi = A.pw[o + i], lr = A.lr[o + i], lm = A.lm[o + i], lw = A.lw[o + i];
+        const CellUpd c = cell_upd(A.F0 + o, A.F1 + o, S, i, wi, dt);
+        const double r1 = (wi * A.pr[o + i] - dt * (c.fr0 - c.fl0)) / c.h1;
+        const double m1 = (wi * A.pm[o + i] - dt * (c.fr1 - c.fl1)) / c.h1;
+        const double sgn = side ? 1.0 : -1.0;  // the flux enters the right face of cell g-1, the left of cell g
+        const double a0 = sgn * dt / c.h1 * lr, a1 = sgn * dt / c.h1 * lm;
+        const double zs = side ? e[1] : e[0];
+        L[side] += -a0 - a1 * e[2];  // (-z, -z u_C + p_C)
+        L[2] += -a1 * zs;
+        L[3] += a1;
+        L[5 + side] += -sgn * dt * (lw - (lr * r1 + lm * m1) / c.h1);  // h1 = w + (w_l - w_r) dt
+      }
+      Dual<5> rl = dvar<5>(A.pr[o + g - 1], 0), ml = dvar<5>(A.pm[o + g - 1], 1);
+      Dual<5> rr = dvar<5>(A.pr[o + g], 2), mr = dvar<5>(A.pm[o + g], 3), ta = dvar<5>(I.tau, 4);
+      Dual<5> out[7];
+      if (!creation_d<5>(c_fluid, S.cr_P[k], rl, ml, rr, mr, ta, R.cr_x[k], out)) {
+        afail(I, IMEXDS_ERR_STATE, 3);
+        break;
+      }
+      double lt[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int q = 0; q < 7; ++q)
+        for (int kk = 0; kk < 5; ++kk) lt[kk] += L[q] * out[q].d[kk];
+      A.nr[o + g - 1] += lt[0];
+      A.nm[o + g - 1] += lt[1];
+      A.nr[o + g] += lt[2];
+      A.nm[o + g] += lt[3];
+      I.lam_tau += lt[4];
+    }
+  }
   // (g) merges^T and (h) dt^T (thread 0)
   if (tid == 0) {
     lam_dt += tot;

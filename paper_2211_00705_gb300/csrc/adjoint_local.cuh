@@ -265,5 +265,59 @@ __device__ bool pb_face_d(const Fluid& F, int phl, int phr, const Dual<K>& rl, c
   return true;
 }
 
+// Phase creation at a same-phase face (App. B): the outputs (z1, z2, u_C, p_C, rho_C, w1, w2) as functions of
+// the adjacent states and tau, differentiated at the converged pressures x = (p_P-, p_C, p_P+) of the 3x3
+// system E(x; W_l, W_r, tau) = 0: dx = -DE^{-1} (dE/dtheta) dtheta, then the recovery on duals.
+template <int K>
+__device__ bool creation_d(const Fluid& F, int P, const Dual<K>& rl, const Dual<K>& ml, const Dual<K>& rr,
+                           const Dual<K>& mr, const Dual<K>& tau, const double x[3], Dual<K> out[7]) {
+  const int Cph = 1 - P;
+  const Phase& EP = F.ph[P];
+  const Phase& EC = F.ph[Cph];
+  Dual<K> ul = ml / rl, ur = mr / rr;
+  Dual<K> X[3] = {dconst<K>(x[0]), dconst<K>(x[1]), dconst<K>(x[2])};
+  double J[3][3];
+  Dual<K> E[3];
+  for (int pass = 0; pass < 2; ++pass) {
+    SideD<K> Pl = side_d(EP, X[0]), C = side_d(EC, X[1]), Pr = side_d(EP, X[2]);
+    Dual<K> dz1a, dz1b, dz2a, dz2b, dfl, dfr;
+    Dual<K> z1 = kinetic_z_d(tau, P == VAP, Pl, C, dz1a, dz1b);
+    Dual<K> z2 = kinetic_z_d(tau, Cph == VAP, C, Pr, dz2a, dz2b);
+    Dual<K> fl = wave_f_d(EP, X[0], rl, dfl);
+    Dual<K> fr = wave_f_d(EP, X[2], rr, dfr);
+    Dual<K> jv1 = C.v - Pl.v, jv2 = Pr.v - C.v;
+    if (pass == 0) {
+      E[0] = (X[1] - X[0]) + z1 * z1 * jv1;
+      E[1] = (X[2] - X[1]) + z2 * z2 * jv2;
+      E[2] = fl + fr + z1 * jv1 + z2 * jv2 + (ur - ul);
+      J[0][0] = -1.0 + 2.0 * z1.v * dz1a.v * jv1.v - z1.v * z1.v * Pl.dv.v;
+      J[0][1] = 1.0 + 2.0 * z1.v * dz1b.v * jv1.v + z1.v * z1.v * C.dv.v;
+      J[0][2] = 0.0;
+      J[1][0] = 0.0;
+      J[1][1] = -1.0 + 2.0 * z2.v * dz2a.v * jv2.v - z2.v * z2.v * C.dv.v;
+      J[1][2] = 1.0 + 2.0 * z2.v * dz2b.v * jv2.v + z2.v * z2.v * Pr.dv.v;
+      J[2][0] = dfl.v + dz1a.v * jv1.v - z1.v * Pl.dv.v;
+      J[2][1] = dz1b.v * jv1.v + z1.v * C.dv.v + dz2a.v * jv2.v - z2.v * C.dv.v;
+      J[2][2] = dfr.v + dz2b.v * jv2.v + z2.v * Pr.dv.v;
+      for (int k = 0; k < K; ++k) {
+        double b[3] = {-E[0].d[k], -E[1].d[k], -E[2].d[k]}, dx[3];
+        if (!solve3(J, b, dx)) return false;
+        for (int i = 0; i < 3; ++i) X[i].d[k] = dx[i];
+      }
+    } else {
+      Dual<K> uPl = ul - fl;
+      Dual<K> uC = uPl - z1 * (C.v - Pl.v);
+      out[0] = z1;
+      out[1] = z2;
+      out[2] = uC;
+      out[3] = X[1];
+      out[4] = C.rho;
+      out[5] = uC + z1 * C.v;
+      out[6] = uC + z2 * C.v;
+    }
+  }
+  return true;
+}
+
 }  // namespace adj
 }  // namespace imexds

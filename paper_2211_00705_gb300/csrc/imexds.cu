@@ -2544,7 +2544,7 @@ imexds_status imexds_adjoint(imexds_ctx* c, const double* dJ_dw_T, const double*
   }
   const int n_prog = (int)c->prog_k.size();
   // one device allocation carved into the arrays
-  const size_t nd_cell = 28, nb_cell = 5, ni_cell = 1;
+  const size_t nd_cell = 28, nb_cell = 6, ni_cell = 1;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   size_t bytes = 0;
   bytes += al(sizeof(AInst) * n) + al(sizeof(int) * (n_prog + 1)) + al(sizeof(double) * (n_prog + 1));
@@ -2581,7 +2581,7 @@ imexds_status imexds_adjoint(imexds_ctx* c, const double* dJ_dw_T, const double*
                         &A.CR0, &A.CR1, &A.pw, &A.pr, &A.pm, &A.lw, &A.lr,  &A.lm,  &A.lx,  &A.nw,
                         &A.nr,  &A.nm,  &A.nx, &A.fin_w, &A.fin_r, &A.fin_m, &A.pwl, &A.pwr};
   for (auto q : dcell) *q = (double*)take(sizeof(double) * stride);
-  unsigned char** bcell[5] = {&A.ph, &A.fpb, &A.pph, &A.pfpb, &A.fin_ph};
+  unsigned char** bcell[6] = {&A.ph, &A.fpb, &A.pph, &A.pfpb, &A.fin_ph, &A.cdet};
   for (auto q : bcell) *q = (unsigned char*)take(stride);
   A.fj = (int*)take(sizeof(int) * stride);
   A.ck_w = (double*)take(sizeof(double) * stride * n_ck);

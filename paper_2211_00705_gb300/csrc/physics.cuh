@@ -481,6 +481,7 @@ __device__ inline double nopt_star(const Phase& e, double rl, double ul, double 
 
 struct CreateOut {
   double pC, rhoC, uC, z1, z2, w1, w2;
+  double pPl, pPr;  // converged parent-side pressures
   int iters;
   int ok;
 };
@@ -602,6 +603,8 @@ __device__ __noinline__ CreateOut creation_solve(const Fluid& F, const Opts& o, 
   R.iters = it;
   if (!conv) return R;
   R.pC = x[1];
+  R.pPl = x[0];
+  R.pPr = x[2];
   R.rhoC = S.C.rho;
   R.z1 = S.z1;
   R.z2 = S.z2;

@@ -204,3 +204,69 @@ def test_adjoint_run_to_clipped_last_step():
         got = grad_dot(b, g, d)
         err = _rel(got, ref[q], np.max(np.abs(ref[q])))
         assert np.max(err) <= TOL_TANGENT, (q, got, ref[q])
+
+
+def _mean_pressure(st, b):
+    """J_i = sum_c w_c p(rho_c) / sum_c w_c over the final cells of instance i; gradients w.r.t. rho and w."""
+    f = b.fluid
+    off = st["offsets"]
+    J = np.zeros(b.n_inst)
+    gr = np.zeros(int(off[-1]))
+    gw = np.zeros(int(off[-1]))
+    for i in range(b.n_inst):
+        sl = slice(off[i], off[i + 1])
+        ph, r, w = st["phase"][sl], st["rho"][sl], st["widths"][sl]
+        a2 = np.where(ph == 0, f.a2_vap, f.a2_liq)
+        p = np.where(ph == 0, f.a2_vap * r, f.p_sat + f.a2_liq * (r - f.rho0_liq))
+        W = w.sum()
+        J[i] = float((w * p).sum() / W)
+        gr[sl] = w * a2 / W
+        gw[sl] = (p - J[i]) / W
+    return J, gr, gw
+
+
+def test_adjoint_through_phase_creation_dJ_dV():
+    """Cavitation (App. B): liquid pulled apart at +-V creates a vapour cell. dJ/dV of the mean final pressure
+    (V enters the initial momentum, m0 = rho0 (-+V)) from the adjoint against the oracle's tangent in the V
+    direction and against central differences of the CUDA forward run (step 1e-6 relative)."""
+    from paper_2211_00705_gb300.imexds import Imexds
+    b = I.cavitation_batch(4, 4, n_range=(64, 128), n_steps=60)
+    b = dataclasses.replace(b, options=I.scaled_options(creation=1, tol_nb=3e-13, tol_k=3e-11))
+    program = [("step", 60)]
+    ctx = _forward(b, program)
+    s = ctx.get_states()
+    st = ctx.stats()
+    assert (s["status"] == 0).all() and (st["creations"] >= 1).all()
+    J, gr, gw = _mean_pressure(s, b)
+    g = ctx.adjoint(gr, np.zeros_like(gr), gw)
+    info = ctx.adjoint_info()
+    ctx.close()
+    assert (g["status"] == 0).all(), g["status"]
+    assert info["replay_err"] <= 1e-9, info
+    dmdV = np.zeros(int(b.cell_offsets[-1]))
+    V = np.zeros(b.n_inst)
+    for i in range(b.n_inst):
+        sl = slice(b.cell_offsets[i], b.cell_offsets[i + 1])
+        u = b.m[sl] / b.rho[sl]
+        V[i] = abs(u[0])
+        dmdV[sl] = np.sign(u) * b.rho[sl]
+    adj = np.array([np.dot(g["m"][b.cell_offsets[i]:b.cell_offsets[i + 1]],
+                           dmdV[b.cell_offsets[i]:b.cell_offsets[i + 1]]) for i in range(b.n_inst)])
+    o = P.Oracle(b)
+    sto, d = o.tangent(program, seed_m=dmdV[None, :], threads=4)
+    Jo, gro, gwo = _mean_pressure(sto, b)
+    off = sto["offsets"]
+    tang = np.array([np.dot(gro[off[i]:off[i + 1]], d["rho"][0][off[i]:off[i + 1]])
+                     + np.dot(gwo[off[i]:off[i + 1]], d["widths"][0][off[i]:off[i + 1]]) for i in range(b.n_inst)])
+    print("adjoint", adj, "tangent", tang)
+    assert np.max(np.abs(adj - tang) / np.abs(tang)) <= TOL_TANGENT
+    vals = []
+    for sgn in (1.0, -1.0):
+        bb = dataclasses.replace(b, m=b.m + sgn * 1e-6 * np.repeat(V, np.diff(b.cell_offsets)) * dmdV)
+        c = Imexds.from_batch(bb)
+        c.step(60)
+        vals.append(_mean_pressure(c.get_states(), bb)[0])
+        c.close()
+    fd = (vals[0] - vals[1]) / (2e-6 * V)
+    print("fd", fd)
+    assert np.max(np.abs(adj - fd) / np.abs(adj)) <= 1e-5
