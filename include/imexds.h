@@ -76,8 +76,9 @@ typedef struct {
                           groups advanced by one resident launch in lockstep, 3 instance groups whose
                           instances advance independently inside the resident launch (0) */
   int group_cells;     /* lattice cells per instance group (0 = 16384) */
-  int group_threads;   /* threads per group CTA, a multiple of 32 from 64 to 128 (0 = 128): warp 0 runs
-                          the per-instance work, the other warps sweep */
+  int group_threads;   /* threads per group CTA, a multiple of 32 from 64 to 256 (0 = 128): warp 0 runs
+                          the per-instance work, the other warps sweep; above 128 one CTA per SM (the
+                          independent-group schedule 3 takes at most 128) */
 } imexds_options;
 
 /* A batch of independent 1-D problems on [x_left[i], x_right[i]] with n_lattice[i] background

@@ -19,6 +19,9 @@ import numpy as np
 CANDIDATES = [
     {"schedule": 1},
     {"schedule": 2, "group_threads": 128, "group_cells": 16384},
+    {"schedule": 2, "group_threads": 256, "group_cells": 16384},
+    {"schedule": 2, "group_threads": 256, "group_cells": 24576},
+    {"schedule": 2, "group_threads": 192, "group_cells": 16384},
     {"schedule": 2, "group_threads": 128, "group_cells": 8192},
     {"schedule": 2, "group_threads": 96, "group_cells": 16384},
     {"schedule": 2, "group_threads": 64, "group_cells": 4096},

@@ -1299,8 +1299,10 @@ __global__ void k_post(Dev d, int n) {
 // group: boundary solves, plan, dual time stepping, grid management); warps 1.. sweep the group's
 // lattice cells while warp 0 runs the dual-time chains of the same step.
 constexpr int GROUP_MAX = 32;
-template <bool CREATION>
-__global__ void __launch_bounds__(128, 2) k_group(Dev d, const int* ginst, const int2* grange, int max_steps,
+// NT: the CTA width the kernel is compiled for (128: two CTAs per SM, three sweep warps; 256: one CTA per SM,
+// seven sweep warps); launched with at most NT threads.
+template <bool CREATION, int NT>
+__global__ void __launch_bounds__(NT, (NT <= 128 ? 2 : 1)) k_group(Dev d, const int* ginst, const int2* grange, int max_steps,
                                                long long* phase_cycles) {
   const int2 gr = grange[blockIdx.x];
   long long cyc[4] = {0, 0, 0, 0};  // pre+plan, sweep (warp 1), dual time (warp 0), post
@@ -1788,15 +1790,20 @@ imexds_status run_groups(imexds_ctx* c, long long max_steps, bool until_done) {
   while (done < max_steps) {
     int n = (int)std::min<long long>(max_steps - done, 1 << 30);
     if (c->timing) cudaEventRecord(c->gev[0], c->stream);
-    if (c->async_groups) {
+    if (c->async_groups && c->group_threads <= 128) {
       if (c->opts.creation)
         k_group_async<true><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n, pc);
       else
         k_group_async<false><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n, pc);
+    } else if (c->group_threads > 128) {
+      if (c->opts.creation)
+        k_group<true, 256><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n, pc);
+      else
+        k_group<false, 256><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n, pc);
     } else if (c->opts.creation) {
-      k_group<true><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n, pc);
+      k_group<true, 128><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n, pc);
     } else {
-      k_group<false><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n, pc);
+      k_group<false, 128><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n, pc);
     }
     if (c->timing) cudaEventRecord(c->gev[1], c->stream);
     k_count_active<<<1, 256, 0, c->stream>>>(c->d, c->n_inst);
@@ -1972,7 +1979,7 @@ imexds_status imexds_create(const imexds_problem* prob, const imexds_options* op
   c->schedule_opt = o.schedule;
   if (o.group_cells > 0) c->group_cells = o.group_cells;
   if (o.group_threads != 0) {
-    if (o.group_threads < 64 || o.group_threads > 128 || o.group_threads % 32) {
+    if (o.group_threads < 64 || o.group_threads > 256 || o.group_threads % 32) {
       delete c;
       return IMEXDS_ERR_ARG;
     }

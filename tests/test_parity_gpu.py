@@ -36,6 +36,11 @@ def test_batched_riemann_subset(schedule):
     _check(I.workload(1, scale=32 / 4096), schedule=schedule)
 
 
+def test_batched_riemann_subset_wide_groups():
+    """Instance groups of 256 threads (one CTA per SM, seven sweep warps)."""
+    _check(I.workload(1, scale=32 / 4096), schedule=2, group_threads=256)
+
+
 @pytest.mark.parametrize("schedule", SCHEDULES)
 def test_fixed_step_count(schedule):
     b = I.workload(3, scale=8 / 1024)
