@@ -32,9 +32,9 @@ UNIT = "cell-steps/s"
 # algorithmic FP64 operations of one explicit cell-step (HLL face + cell update, counted in the design doc)
 SWEEP_FLOP_PER_CELL = 33
 FP64_PEAK_TFLOPS = 1.25   # GB300 dense FP64 (nominal; no FP64 figure in MEASURED_PEAKS.json)
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_sweep launch on this workload (ncu capture of the
-# per-step schedule, launches 301-302: 91.7 + 38.8 MB); valid while k_sweep is unchanged
-SWEEP_TRAFFIC_BYTES = 130.6e6
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_sweep launch on this workload from an ncu capture of
+# the per-step schedule; None while no capture of the current k_sweep exists
+SWEEP_TRAFFIC_BYTES = None
 
 
 def dist_env():
