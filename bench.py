@@ -53,7 +53,7 @@ def cell_steps(stats, counts):
     return float(np.sum(stats["steps"].astype(np.float64) * counts.astype(np.float64)))
 
 
-def measure_adjoint(dev, steps, warmup, scale=1.0):
+def measure_adjoint(dev, steps, warmup, scale=1.0, n_steps=2000):
     """The adjoint on its workload (Riemann instances, N=500, 2000 steps, checkpoints every 64): forward run
     (also a target run with tau x 1.1 for the misfit), then imexds_adjoint timed. Cell-steps of the adjoint
     = initial cells x steps of every instance (the replay, the recompute and the reverse sweep all count as
@@ -63,7 +63,7 @@ def measure_adjoint(dev, steps, warmup, scale=1.0):
     from paper_2211_00705_gb300 import inputs as I
     from paper_2211_00705_gb300.imexds import Imexds
     n = max(1, int(round(1024 * scale)))
-    b = I.adjoint_batch(n_inst=n)
+    b = I.adjoint_batch(n_inst=n, n_steps=n_steps)
     prog_steps = b.n_steps
     tctx = Imexds.from_batch(dataclasses.replace(b, tau=b.tau * 1.1))
     tctx.step(prog_steps)
@@ -294,6 +294,9 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--no-plain", action="store_true", help="skip the single-instance comparison")
     ap.add_argument("--no-hbm", action="store_true", help="skip the large-domain sweep (HBM) measurement")
+    ap.add_argument("--only", choices=["adjoint", "hbm"], default=None,
+                    help="run one auxiliary measurement alone and print its JSON (profiling)")
+    ap.add_argument("--adjoint-steps", type=int, default=2000, help="steps of the adjoint workload")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -307,6 +310,12 @@ def main():
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
     from paper_2211_00705_gb300.imexds import Imexds
+    if args.only == "adjoint":
+        print(json.dumps(measure_adjoint(dev, args.steps, args.warmup, scale=args.scale, n_steps=args.adjoint_steps)))
+        return 0
+    if args.only == "hbm":
+        print(json.dumps(measure_large_domain_sweep()))
+        return 0
 
     batch = workload(args.scale)
     tuned = None
@@ -450,7 +459,8 @@ def main():
             plain["batched_over_plain"] = value / plain["value"]
             line["plain_single_instance"] = plain
         if not args.no_adjoint:
-            line["adjoint"] = measure_adjoint(dev, max(1, args.steps // 2), 1, scale=args.scale)
+            line["adjoint"] = measure_adjoint(dev, max(1, args.steps // 2), 1, scale=args.scale,
+                                              n_steps=args.adjoint_steps)
         if not args.no_hbm:
             line["large_domain_sweep"] = measure_large_domain_sweep()
         if ws == 1 and not args.no_cpu_baseline:

@@ -40,7 +40,9 @@ def config_key(batch) -> str:
 
 
 def tune(batch, steps: int = 64, cache_file: str | None = None, candidates=None) -> dict:
-    """Return the fastest candidate for this batch (and remember it)."""
+    """Return the fastest candidate for this batch (and remember it). A batch with an end time is timed over
+    a whole run_to (the early steps of a run are not representative of its cost); otherwise over `steps`
+    steps. The returned dict carries every candidate's time under "timings"."""
     from .imexds import Imexds
     key = config_key(batch)
     if cache_file and os.path.exists(cache_file):
@@ -55,22 +57,25 @@ def tune(batch, steps: int = 64, cache_file: str | None = None, candidates=None)
     for cand in candidates or CANDIDATES:
         ctx = Imexds.from_batch(batch, schedule=cand["schedule"], group_threads=cand.get("group_threads", 0),
                                 group_cells=cand.get("group_cells", 0))
-        ctx.step(min(8, steps))          # warm-up (graph build, caches)
+        run = (lambda: ctx.run_to(batch.t_end)) if batch.t_end > 0 else (lambda: ctx.step(steps))
+        run()                            # warm-up (graph build, caches)
         ctx.reset()
+        ctx.get_states()                 # synchronises
         t0 = time.perf_counter()
-        ctx.step(steps)
+        run()
         st = ctx.get_states()            # synchronises
         dt = time.perf_counter() - t0
         ctx.close()
         if (st["status"] != 0).any():
             continue
-        timings.append((cand, dt))
+        timings.append({**cand, "seconds": dt})
         if dt < best_t:
             best, best_t = cand, dt
     if best is None:
         best = CANDIDATES[0]
     choice = dict(best)
-    choice["seconds_per_step"] = best_t / steps
+    choice["seconds"] = best_t
+    choice["timings"] = timings
     _cache[key] = choice
     if cache_file:
         try:
