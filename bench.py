@@ -165,6 +165,80 @@ def measure_plain(batch, n_sample=16):
             "per-step schedule, run one after another", "seconds": secs}
 
 
+def oracle_rate(batch, n_steps=None, max_inst=None, threads=None):
+    """Oracle cell-steps/s on a bounded sample of a batch (all host cores over instances)."""
+    from oracle import pyoracle as P
+    cores = threads or os.cpu_count() or 1
+    b = batch if max_inst is None or batch.n_inst <= max_inst else batch.subset(
+        list(np.linspace(0, batch.n_inst - 1, max_inst).astype(int)))
+    o = P.Oracle(b)
+    t0 = time.perf_counter()
+    if n_steps is None and b.t_end > 0:
+        o.run_to(b.t_end, cores)
+    else:
+        o.step(n_steps or b.n_steps, cores)
+    secs = time.perf_counter() - t0
+    st = o.stats()
+    cs = float(np.sum(st["steps"] * np.diff(b.cell_offsets)))
+    return cs / secs, cores, f"{b.n_inst} of {batch.n_inst} instances, {int(st['steps'].max())} steps, {secs:.1f} s"
+
+
+def gpu_rate(batch, n_steps=None, **kw):
+    """Batched GPU cell-steps/s of one run (after a warm-up run) and the run's statistics."""
+    import torch
+    from paper_2211_00705_gb300.imexds import Imexds
+    ctx = Imexds.from_batch(batch, **kw)
+    run = (lambda: ctx.run_to(batch.t_end)) if (n_steps is None and batch.t_end > 0) else \
+        (lambda: ctx.step(n_steps or batch.n_steps))
+    run()
+    ctx.reset()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    run()
+    e1.record()
+    torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    st = ctx.stats()
+    cs = float(np.sum(st["steps"] * np.diff(batch.cell_offsets)))
+    ctx.close()
+    return cs / secs, st
+
+
+def table(args):
+    """One row per workload: GPU batched, the plain single-instance GPU step, the oracle on the host cores
+    (bounded samples, stated), for the BASELINE table."""
+    from paper_2211_00705_gb300 import inputs as I
+    rows = {}
+    b0 = I.workload(0)
+    g0, _ = gpu_rate(b0)
+    o0 = oracle_rate(b0)
+    rows["0"] = {"workload": b0.name, "gpu_batched": g0, "gpu_plain": g0, "oracle": o0[0], "cores": o0[1],
+                 "oracle_sample": o0[2]}
+    b1 = I.workload(1)
+    g1, _ = gpu_rate(b1)
+    p1 = measure_plain(b1)
+    o1 = oracle_rate(b1, max_inst=512)
+    rows["1"] = {"workload": b1.name, "gpu_batched": g1, "gpu_plain": p1["value"], "oracle": o1[0],
+                 "cores": o1[1], "oracle_sample": o1[2]}
+    b2 = I.workload(2)
+    g2, _ = gpu_rate(b2, n_steps=100, schedule=1)
+    o2 = oracle_rate(b2, n_steps=5)
+    rows["2"] = {"workload": b2.name, "gpu_batched": g2, "gpu_note": "100 steps (per-step schedule)",
+                 "oracle": o2[0], "cores": o2[1], "oracle_sample": o2[2] + " (extrapolated per cell-step)"}
+    b3 = I.adjoint_batch()
+    g3, _ = gpu_rate(b3)
+    o3 = oracle_rate(b3, max_inst=64)
+    rows["3"] = {"workload": b3.name, "gpu_batched": g3, "oracle": o3[0], "cores": o3[1], "oracle_sample": o3[2]}
+    b4 = I.workload(4, scale=1024 / 16384)
+    g4, _ = gpu_rate(b4)
+    o4 = oracle_rate(b4, max_inst=64, n_steps=500)
+    rows["4"] = {"workload": b4.name, "gpu_batched": g4, "gpu_note": "1024 of the 16384 instances, 5000 steps",
+                 "oracle": o4[0], "cores": o4[1], "oracle_sample": o4[2]}
+    print(json.dumps(rows))
+    return 0
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
 
@@ -297,6 +371,7 @@ def main():
     ap.add_argument("--only", choices=["adjoint", "hbm"], default=None,
                     help="run one auxiliary measurement alone and print its JSON (profiling)")
     ap.add_argument("--adjoint-steps", type=int, default=2000, help="steps of the adjoint workload")
+    ap.add_argument("--table", action="store_true", help="per-workload rates (GPU, plain GPU, oracle) as JSON")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -310,6 +385,8 @@ def main():
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
     from paper_2211_00705_gb300.imexds import Imexds
+    if args.table:
+        return table(args)
     if args.only == "adjoint":
         print(json.dumps(measure_adjoint(dev, args.steps, args.warmup, scale=args.scale, n_steps=args.adjoint_steps)))
         return 0
