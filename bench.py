@@ -235,6 +235,8 @@ def table(args):
     o4 = oracle_rate(b4, max_inst=64, n_steps=500)
     rows["4"] = {"workload": b4.name, "gpu_batched": g4, "gpu_note": "1024 of the 16384 instances, 5000 steps",
                  "oracle": o4[0], "cores": o4[1], "oracle_sample": o4[2]}
+    import platform
+    rows["host"] = {"machine": platform.machine(), "cores": os.cpu_count(), "python": platform.python_version()}
     print(json.dumps(rows))
     return 0
 
