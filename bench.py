@@ -45,6 +45,23 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_max(x: float, ws: int, device) -> float:
+    """Maximum of a per-rank value over all ranks (the timed region's slowest rank); x itself for one rank."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(cell_steps_per_rank: float, steps: int, ws: int, t_max: float) -> float:
+    """Whole-job throughput: the cell-steps every rank processed (one replica of the batch per GPU, weak
+    scaling) over the slowest rank's time."""
+    return cell_steps_per_rank * steps * ws / t_max
+
+
 def workload(scale=1.0):
     from paper_2211_00705_gb300 import inputs as I
     return I.workload(1, scale=scale)
@@ -450,14 +467,8 @@ def main():
         launches += int(ctx.stats()["launches"][0])
     clocks = sampler.stop() if sampler else None
     ms = sum(e0.elapsed_time(e1) for e0, e1 in zip(ev0, ev1))
-    t_local = ms / 1e3
-    if ws > 1:
-        t = torch.tensor([t_local], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
-    value = cs_run * args.steps * ws / t_max
+    t_max = reduce_max(ms / 1e3, ws, dev)
+    value = job_value(cs_run, args.steps, ws, t_max)
 
     # per-kernel durations over one instrumented run (events captured in the step graph)
     # per-kernel durations: one instrumented run of the timed schedule, and one of the per-step kernel
@@ -505,12 +516,8 @@ def main():
         barrier()
         d2h = int(out["widths"].nbytes + out["rho"].nbytes + out["m"].nbytes + out["phase"].nbytes
                   + out["offsets"].nbytes + out["t"].nbytes + out["status"].nbytes)
-    e2e_s = sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / 1e3
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": cs_run * args.steps * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+    e2e_s = reduce_max(sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / 1e3, ws, dev)
+    e2e = {"value": job_value(cs_run, args.steps, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
     # roofline of the dominant kernel

@@ -1,0 +1,52 @@
+"""Host logic of the multi-rank benchmark on CPU (gloo, two ranks): the timed region's maximum over ranks
+and the whole-job throughput (one replica of the batch per rank, weak scaling); the reference arm prints
+on rank 0 only."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, ws, port, out):
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=ws)
+    t_local = 1.0 + rank      # rank 1 is the slower one
+    t_max = bench.reduce_max(t_local, ws, torch.device("cpu"))
+    out[rank] = (t_max, bench.job_value(100.0, 3, ws, t_max))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_job_value():
+    ws = 2
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_worker, args=(ws, port, out), nprocs=ws, start_method="spawn", join=True)
+    for r in range(ws):
+        t_max, value = out[r]
+        assert t_max == 2.0
+        assert value == pytest.approx(100.0 * 3 * 2 / 2.0)
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under torchrun, ranks other than 0 exit 0 without work or output."""
+    env = dict(os.environ, WORLD_SIZE="2", RANK="1", LOCAL_RANK="1", MASTER_ADDR="127.0.0.1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2"],
+                       env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""
