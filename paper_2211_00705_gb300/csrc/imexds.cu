@@ -2192,31 +2192,19 @@ imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double*
   }
   CK(cudaStreamSynchronize(c->stream));
   {
-    // instance groups: instances sorted by size (largest first), at most GROUP_MAX per group, group_cells
-    // lattice cells, and a share of the batch's work: an instance's cost is cells x steps, and its step
-    // count grows with N on a domain of fixed length (dt ~ h), so a group holds at most
-    // sum(N^2) / (resident group CTAs) of sum(N_i^2) (at least one instance)
+    // instance groups: instances sorted by size (largest first), at most GROUP_MAX per group and
+    // group_cells lattice cells (at least one instance). (Capping each group's work, sum of N^2, at the
+    // balanced share was measured slower: more groups per SM lengthen every group's dual-time chain.)
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return c->N[a] > c->N[b]; });
-    int dev = 0, n_sm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    const int per_sm = (c->group_threads > 128) ? 1 : 2;
-    double wtot = 0.0;
-    for (int i = 0; i < n; ++i) wtot += (double)c->N[i] * (double)c->N[i];
-    const double wcap = wtot / (double)std::max(1, n_sm * per_sm);
     std::vector<int> ginst;
     std::vector<int2> grange;
     int k = 0;
     while (k < n) {
       int start = k, cells = 0;
-      double work = 0.0;
-      while (k < n && k - start < GROUP_MAX) {
-        const double nk = (double)c->N[order[k]];
-        if (k > start && (cells + c->N[order[k]] > c->group_cells || work + nk * nk > wcap)) break;
+      while (k < n && k - start < GROUP_MAX && (k == start || cells + c->N[order[k]] <= c->group_cells)) {
         cells += c->N[order[k]];
-        work += nk * nk;
         ginst.push_back(order[k]);
         ++k;
       }
