@@ -75,7 +75,8 @@ typedef struct {
   int schedule;        /* 0 automatic, 1 one launch per kernel and step (graph of 8 steps), 2 instance
                           groups advanced by one resident launch in lockstep, 3 instance groups whose
                           instances advance independently inside the resident launch (0) */
-  int group_cells;     /* lattice cells per instance group (0 = 16384) */
+  int group_cells;     /* lattice cells per instance group (0 = 16384, or total cells / SMs when the batch
+                          is too small to fill every SM with 16384-cell groups) */
   int group_threads;   /* threads per group CTA, a multiple of 32 from 64 to 256 (0 = 128): warp 0 runs
                           the per-instance work, the other warps sweep; above 128 one CTA per SM (the
                           independent-group schedule 3 takes at most 128) */

@@ -1594,6 +1594,7 @@ struct imexds_ctx {
   cudaStream_t side = nullptr;            // second stream of the step graph (k_dts beside k_sweep)
   int schedule = 0;                       // 1 per-step kernels, 2 instance groups (0 auto at set_states)
   int schedule_opt = 0, group_cells = 16384, use_groups = 0, group_threads = 128, async_groups = 0;
+  bool group_cells_set = false;  // group_cells given by the caller (otherwise sized to fill the SMs)
   int n_groups = 0;
   long long* d_phase = nullptr;  // per-group phase cycles (timing mode)
   int* d_ginst = nullptr;
@@ -1977,7 +1978,10 @@ imexds_status imexds_create(const imexds_problem* prob, const imexds_options* op
     return IMEXDS_ERR_ARG;
   }
   c->schedule_opt = o.schedule;
-  if (o.group_cells > 0) c->group_cells = o.group_cells;
+  if (o.group_cells > 0) {
+    c->group_cells = o.group_cells;
+    c->group_cells_set = true;
+  }
   if (o.group_threads != 0) {
     if (o.group_threads < 64 || o.group_threads > 256 || o.group_threads % 32) {
       delete c;
@@ -2198,12 +2202,23 @@ imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double*
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return c->N[a] > c->N[b]; });
+    // a batch too small to give every SM a group of group_cells cells gets smaller groups (unless the
+    // caller fixed group_cells): about total cells / SMs each, at least one instance
+    int gcells = c->group_cells;
+    if (!c->group_cells_set) {
+      int dev = 0, n_sm = 1;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+      long long tot = 0;
+      for (int i = 0; i < n; ++i) tot += c->N[i];
+      if (tot < (long long)gcells * n_sm) gcells = (int)std::max<long long>(1, (tot + n_sm - 1) / n_sm);
+    }
     std::vector<int> ginst;
     std::vector<int2> grange;
     int k = 0;
     while (k < n) {
       int start = k, cells = 0;
-      while (k < n && k - start < GROUP_MAX && (k == start || cells + c->N[order[k]] <= c->group_cells)) {
+      while (k < n && k - start < GROUP_MAX && (k == start || cells + c->N[order[k]] <= gcells)) {
         cells += c->N[order[k]];
         ginst.push_back(order[k]);
         ++k;
