@@ -546,6 +546,8 @@ def main():
                 "config": {"workload": batch.name, "instances": batch.n_inst, "cells": int(batch.rho.shape[0]),
                            "schedule": tuned if tuned else {"schedule": args.schedule},
                            "cell_steps_per_step": cs_run, "l2": "flushed (256 MB write) between timed runs",
+                           "dts_iters_per_step": float(st["dts_iters"].sum() / max(1, st["steps"].sum())),
+                           "newton_iters_per_step": float(st["newton"].sum() / max(1, st["steps"].sum())),
                            "instance_status_nonzero": int(np.count_nonzero(status))},
                 "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
         if not args.no_plain:
