@@ -178,6 +178,10 @@ imexds_status imexds_step_uniform_noalloc(const imexds_fluid* fluid, double cfl,
                                           const double* rho_in, const double* m_in, const uint8_t* phase,
                                           double* rho_out, double* m_out, double* dt_out, void* stream);
 
+/* Diagnostic: the library's quotient a / b (a times the Newton-Raphson-refined reciprocal of b, used for
+ * the lattice velocity and the HLL weights) and CUDA's division on n host pairs; results in fast and ref. */
+imexds_status imexds_check_div(int32_t n, const double* a, const double* b, double* fast, double* ref);
+
 /* Diagnostic: evaluate the library's table-driven logarithm (Tang's method, used in the boundary
  * solves) and CUDA's log on n host values x > 0; results in the host arrays fast and ref. */
 imexds_status imexds_check_log(int32_t n, const double* x, double* fast, double* ref);

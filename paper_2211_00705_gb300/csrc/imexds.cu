@@ -384,7 +384,7 @@ __device__ inline FaceFlux face_flux(const Dev& d, Inst& I, int ii, int f, const
     const Zone& Z = d.zones[L.ow];
     rl = Z.eR0;
     ml = Z.eR1;
-    ul = ml / rl;
+    ul = div_nr(ml, rl);
     fl1 = __fma_rn(ml, ul, pressure_fma(E, rl));
   } else {
     rl = L.r;
@@ -396,7 +396,7 @@ __device__ inline FaceFlux face_flux(const Dev& d, Inst& I, int ii, int f, const
     const Zone& Z = d.zones[R.ow];
     rr = Z.eL0;
     mr = Z.eL1;
-    ur = mr / rr;
+    ur = div_nr(mr, rr);
     fr1 = __fma_rn(mr, ur, pressure_fma(E, rr));
   } else {
     rr = R.r;
@@ -493,7 +493,7 @@ __device__ void sweep_tile32(const Dev& d, int ii, int j0) {
       r1 = __fma_rn(-I.lam, fr.F0L - fj.F0R, C.r);
       m1 = __fma_rn(-I.lam, fr.F1L - fj.F1R, C.m);
     }
-    const double u1 = m1 / r1;
+    const double u1 = div_nr(m1, r1);
     d.rho[I.parity ^ 1][g] = r1;
     d.m[I.parity ^ 1][g] = m1;
     d.u[I.parity ^ 1][g] = u1;
@@ -791,7 +791,7 @@ __device__ void dts_simple(const Dev& d, int zi) {
     const double r1 = (hU0[q] - dt * (f0r - f0l)) / hn1;
     const double m1 = (hU1[q] - dt * (f1r - f1l)) / hn1;
     if (!(r1 > 0.0) || !isfinite(r1) || !isfinite(m1)) set_status(I, IMEXDS_ERR_NONPHYSICAL);
-    const double u1 = m1 / r1;
+    const double u1 = div_nr(m1, r1);
     smax = fmax(smax, fabs(u1) + c_fluid.ph[ph[q]].a);
     const int e = (PBF == 2) ? q - 1 : q;
     if (e < 0 || e > 1) {
@@ -921,7 +921,7 @@ __device__ __noinline__ void dts_zone_general(const Dev& d, int zi) {
     int e = q + e0;
     double r1 = out_r[q], m1 = out_m[q];
     if (!(r1 > 0.0) || !isfinite(r1) || !isfinite(m1) || !(out_w[q] > 0.0)) set_status(I, IMEXDS_ERR_NONPHYSICAL);
-    const double u1 = m1 / r1;
+    const double u1 = div_nr(m1, r1);
     smax = fmax(smax, fabs(u1) + c_fluid.ph[B.ph[q]].a);
     if (e < 0) {
       nr[Z.A - 1] = r1;
@@ -1042,7 +1042,7 @@ __device__ __noinline__ void post_inst(const Dev& d, int ii) {
     while (Z.nc > 1 && !Z.fpb[1] && Z.fj[1] == Z.A + 1 && Z.w[0] == h) {
       nr[Z.A] = Z.r[0];
       nm[Z.A] = Z.m[0];
-      nu[Z.A] = Z.m[0] / Z.r[0];
+      nu[Z.A] = div_nr(Z.m[0], Z.r[0]);
       lph[Z.A] = (unsigned char)Z.ph[0];
       zone_erase_cell(Z, 0);
       Z.A += 1;
@@ -1053,7 +1053,7 @@ __device__ __noinline__ void post_inst(const Dev& d, int ii) {
     while (Z.nc > 1 && !Z.fpb[Z.nc - 1] && Z.fj[Z.nc - 1] == Z.B - 1 && Z.w[Z.nc - 1] == h) {
       nr[Z.B - 1] = Z.r[Z.nc - 1];
       nm[Z.B - 1] = Z.m[Z.nc - 1];
-      nu[Z.B - 1] = Z.m[Z.nc - 1] / Z.r[Z.nc - 1];
+      nu[Z.B - 1] = div_nr(Z.m[Z.nc - 1], Z.r[Z.nc - 1]);
       lph[Z.B - 1] = (unsigned char)Z.ph[Z.nc - 1];
       Z.nc--;
       Z.B -= 1;
@@ -1117,7 +1117,7 @@ __device__ __noinline__ void post_inst(const Dev& d, int ii) {
       int j = Z.fj[k];
       nr[j] = Z.r[k];
       nm[j] = Z.m[k];
-      nu[j] = Z.m[k] / Z.r[k];
+      nu[j] = div_nr(Z.m[k], Z.r[k]);
       lph[j] = (unsigned char)Z.ph[k];
     }
     Z.nc = a;
@@ -1505,6 +1505,12 @@ __global__ void __launch_bounds__(128, 2) k_group_async(Dev d, const int* ginst,
     }
   }
   if (phase_cycles && lane == 0) atomicMax((unsigned long long*)&phase_cycles[4 * blockIdx.x + 1], (unsigned long long)busy);
+}
+
+// u = m / rho of every lattice cell, with the quotient the kernels use (set_states)
+__global__ void k_init_u(const double* rho, const double* m, double* u, int n) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) u[g] = div_nr(m[g], rho[g]);
 }
 
 // Wave-speed maximum over all cells of every instance and the first dt (before the first step).
@@ -2147,8 +2153,6 @@ imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double*
   std::vector<int2> tiles;
   for (int i = 0; i < n; ++i)
     for (int j0 = 0; j0 < c->N[i]; j0 += 32) tiles.push_back(make_int2(i, j0));
-  std::vector<double> hu(n_lat);
-  for (int g = 0; g < n_lat; ++g) hu[g] = hm[g] / hr[g];  // IEEE division: the bits the kernels produce
   free_dev(c);
   Dev& d = c->d;
   for (int k = 0; k < 2; ++k) {
@@ -2157,7 +2161,8 @@ imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double*
     CK(cudaMalloc(&d.u[k], sizeof(double) * n_lat));
     CK(cudaMemcpyAsync(d.rho[k], hr.data(), sizeof(double) * n_lat, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(d.m[k], hm.data(), sizeof(double) * n_lat, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(d.u[k], hu.data(), sizeof(double) * n_lat, cudaMemcpyHostToDevice, c->stream));
+    k_init_u<<<(n_lat + 255) / 256, 256, 0, c->stream>>>(d.rho[k], d.m[k], d.u[k], n_lat);
+    CK(cudaGetLastError());
   }
   CK(cudaMalloc(&d.phase, n_lat));
   CK(cudaMemcpyAsync(d.phase, hph.data(), n_lat, cudaMemcpyHostToDevice, c->stream));
@@ -2409,6 +2414,29 @@ imexds_status imexds_set_kernel_timing(imexds_ctx* c, int32_t on) {
     c->kt_ms[k] = 0.0;
     c->kt_n[k] = 0;
   }
+  return IMEXDS_OK;
+}
+
+__global__ void k_check_div(const double* a, const double* b, double* fast, double* ref, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    fast[i] = div_nr(a[i], b[i]);
+    ref[i] = a[i] / b[i];
+  }
+}
+
+imexds_status imexds_check_div(int32_t n, const double* a, const double* b, double* fast, double* ref) {
+  if (n <= 0 || !a || !b || !fast || !ref) return IMEXDS_ERR_ARG;
+  double* d = nullptr;
+  CK(cudaMalloc(&d, sizeof(double) * 4 * (size_t)n));
+  CK(cudaMemcpy(d, a, sizeof(double) * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d + n, b, sizeof(double) * n, cudaMemcpyHostToDevice));
+  k_check_div<<<(n + 255) / 256, 256>>>(d, d + n, d + 2 * (size_t)n, d + 3 * (size_t)n, n);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpy(fast, d + 2 * (size_t)n, sizeof(double) * n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(ref, d + 3 * (size_t)n, sizeof(double) * n, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e);
   return IMEXDS_OK;
 }
 

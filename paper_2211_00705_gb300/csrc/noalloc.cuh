@@ -47,7 +47,7 @@ __global__ void k_dt(Scratch* s, Fluid F, double cfl, const double* rho, const d
   double S = 0.0;
   int mixed = 0;
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    S = fmax(S, fabs(m[o + j] / rho[o + j]) + F.ph[ph[o + j]].a);
+    S = fmax(S, fabs(div_nr(m[o + j], rho[o + j])) + F.ph[ph[o + j]].a);
     mixed |= (ph[o + j] != p0);
   }
   __shared__ double red[32];
@@ -89,7 +89,7 @@ __global__ void k_sweep(const Scratch* s, Fluid F, int n, int n_tiles, const dou
   auto load = [&](int j, double& r, double& mm, double& u, double& f1) {
     r = rho[o + j];
     mm = m[o + j];
-    u = mm / r;
+    u = div_nr(mm, r);
     f1 = __fma_rn(mm, u, pressure_fma(E, r));
   };
   const int j = j0 + lane;

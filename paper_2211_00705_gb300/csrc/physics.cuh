@@ -9,6 +9,22 @@
 
 namespace imexds {
 
+// Reciprocal by Newton-Raphson refinement of the hardware estimate (PTX rcp.approx.ftz.f64, ~23 bits):
+// two steps y <- y + y (1 - b y) reach full double precision (error squared per step); a / b is then a
+// times it, within 2 ulp of the correctly rounded quotient (checked against CUDA's division by
+// imexds_check_div). Used where the same quotient is formed by several kernels (the lattice velocity
+// m / rho, the HLL weight 1 / (S_R - S_L)), so that all of them produce the same bits. Arguments are
+// normal, non-zero doubles (densities, wave-speed spans).
+__device__ __forceinline__ double rcp_nr(double b) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(b));
+  double e = __fma_rn(-b, y, 1.0);
+  y = __fma_rn(y, e, y);
+  e = __fma_rn(-b, y, 1.0);
+  return __fma_rn(y, e, y);
+}
+__device__ __forceinline__ double div_nr(double a, double b) { return a * rcp_nr(b); }
+
 constexpr int VAP = 0;
 constexpr int LIQ = 1;
 
@@ -88,19 +104,19 @@ __device__ inline void hll_pre(double a, double rl, double ml, double ul, double
     F0 = mr;
     F1 = fr1;
   } else {
-    double inv = 1.0 / (SR - SL);
+    double inv = rcp_nr(SR - SL);
     double slsr = SL * SR;
     F0 = __fma_rn(-SL, mr, __fma_rn(slsr, rr - rl, SR * ml)) * inv;
     F1 = __fma_rn(-SL, fr1, __fma_rn(slsr, mr - ml, SR * fl1)) * inv;
   }
 }
 __device__ inline void phys_flux_fast(const Phase& e, double r, double m, double& F0, double& F1) {
-  double u = m / r;
+  double u = div_nr(m, r);
   F0 = m;
   F1 = __fma_rn(m, u, pressure_fma(e, r));
 }
 __device__ inline void hll_fast(const Phase& e, double rl, double ml, double rr, double mr, double& F0, double& F1) {
-  double ul = ml / rl, ur = mr / rr;
+  double ul = div_nr(ml, rl), ur = div_nr(mr, rr);
   double fl1 = __fma_rn(ml, ul, pressure_fma(e, rl));
   double fr1 = __fma_rn(mr, ur, pressure_fma(e, rr));
   hll_pre(e.a, rl, ml, ul, fl1, rr, mr, ur, fr1, F0, F1);

@@ -21,7 +21,7 @@ EXPORTED = ["imexds_create", "imexds_set_states", "imexds_set_states_device", "i
             "imexds_status_string", "imexds_last_error_string", "imexds_reset", "imexds_set_kernel_timing",
             "imexds_get_kernel_times", "imexds_set_schedule", "imexds_check_log", "imexds_step_uniform_noalloc",
             "imexds_get_group_phase_cycles", "imexds_adjoint", "imexds_set_adjoint_checkpoint",
-            "imexds_adjoint_info", "imexds_adjoint_replay"]
+            "imexds_adjoint_info", "imexds_adjoint_replay", "imexds_check_div"]
 
 
 class ImexdsError(RuntimeError):
@@ -77,6 +77,7 @@ def load():
         L.imexds_set_schedule.argtypes = [vp, C.c_int32]
         L.imexds_get_group_phase_cycles.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.imexds_check_log.argtypes = [C.c_int32, dp, dp, dp]
+        L.imexds_check_div.argtypes = [C.c_int32, dp, dp, dp, dp]
         L.imexds_step_uniform_noalloc.argtypes = [C.POINTER(FluidS), C.c_double, C.c_int32, ip, dp, dp, vp, vp, vp,
                                                   vp, vp, vp, vp]
         L.imexds_adjoint.argtypes = [vp, dp, dp, dp, dp, dp, dp, dp, ip]
@@ -130,6 +131,16 @@ def step_uniform_noalloc(fluid, cfl, n_lattice, x_left, x_right, rho_in, m_in, p
         C.byref(fl), float(cfl), int(nl.shape[0]), _ip(nl), _dp(xl), _dp(xr), C.c_void_p(rho_in.data_ptr()),
         C.c_void_p(m_in.data_ptr()), C.c_void_p(phase.data_ptr()), C.c_void_p(rho_out.data_ptr()),
         C.c_void_p(m_out.data_ptr()), C.c_void_p(dt_out.data_ptr()), C.c_void_p(stream)))
+
+
+def check_div(a, b):
+    """The library's quotient (Newton-Raphson-refined reciprocal) and CUDA's division at the pairs (a, b)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    fast = np.zeros_like(a)
+    ref = np.zeros_like(a)
+    _check(load().imexds_check_div(int(a.shape[0]), _dp(a), _dp(b), _dp(fast), _dp(ref)))
+    return fast, ref
 
 
 def check_log(x):

@@ -23,3 +23,17 @@ def test_fast_log_accuracy():
     rel = np.abs(fast - np.log(x)) / np.maximum(np.abs(np.log(x)), 1e-300)
     assert np.max(rel[np.abs(np.log(x)) > 0]) < 1e-15
     assert fast[-5] == 0.0
+
+
+def test_newton_raphson_quotient_against_division():
+    """a * rcp_nr(b) against CUDA's correctly rounded division over the ranges the kernels use (densities
+    1e-3..1e4, momenta and wave-speed spans of either sign): within 2 ulp."""
+    import numpy as np
+    from paper_2211_00705_gb300.imexds import check_div
+    rng = np.random.default_rng(0)
+    n = 1 << 20
+    b = 10.0 ** rng.uniform(-3, 4, n)
+    a = rng.standard_normal(n) * 10.0 ** rng.uniform(-3, 6, n)
+    fast, ref = check_div(a, b)
+    ulp = np.spacing(np.abs(ref))
+    assert np.max(np.abs(fast - ref) / ulp) <= 2.0
