@@ -842,7 +842,7 @@ __device__ __noinline__ void dts_zone_general(const Dev& d, int zi) {
   double* nr = d.rho[cur ^ 1] + I.lat_off;
   double* nm = d.m[cur ^ 1] + I.lat_off;
   const unsigned char* lph = d.phase + I.lat_off;
-  const double dt = I.dt, h = I.h, tau = I.tau;
+  const double dt = I.dt, h = I.h;
   const int N = I.N;
   BlockCtx B;
   const int e0 = -Z.pullL;              // first extended index

@@ -60,35 +60,10 @@ __device__ inline bool valid_pressure(const Phase& e, double p) { return isfinit
 // Gibbs energy with dg = v dp: g = a2 ln(rho / rho_sat), zero at the saturation pressure (Sec. 2.1).
 __device__ inline double gibbs(const Phase& e, double rho) { return e.a2 * log(rho / e.rho_sat); }
 
-// Physical flux (rho u, rho u^2 + p) of the isothermal Euler equations (Eq. eeq:isoT both).
-__device__ inline void phys_flux(const Phase& e, double r, double m, double& F0, double& F1) {
-  double u = m / r;
-  F0 = m;
-  F1 = m * u + pressure(e, r);
-}
-
-// HLL flux at a same-phase face (Toro), Davis wave speeds S_L = min(u_l, u_r) - a, S_R = max + a.
-__device__ inline void hll(const Phase& e, double rl, double ml, double rr, double mr, double& F0, double& F1) {
-  double ul = ml / rl, ur = mr / rr;
-  double Fl0 = ml, Fl1 = ml * ul + pressure(e, rl);
-  double Fr0 = mr, Fr1 = mr * ur + pressure(e, rr);
-  double SL = fmin(ul - e.a, ur - e.a);
-  double SR = fmax(ul + e.a, ur + e.a);
-  if (SL >= 0.0) {
-    F0 = Fl0;
-    F1 = Fl1;
-  } else if (SR <= 0.0) {
-    F0 = Fr0;
-    F1 = Fr1;
-  } else {
-    F0 = (SR * Fl0 - SL * Fr0 + SL * SR * (rr - rl)) / (SR - SL);
-    F1 = (SR * Fl1 - SL * Fr1 + SL * SR * (mr - ml)) / (SR - SL);
-  }
-}
-
-// The same HLL flux arranged for the sweep: the physical fluxes come in precomputed (u = m/rho once per
-// cell) and one reciprocal of S_R - S_L serves both components; every product-sum is an explicit
-// fused multiply-add so that every kernel computing the flux at a face gets the same bits.
+// HLL flux at a same-phase face (Toro), Davis wave speeds S_L = min(u_l, u_r) - a, S_R = max + a, physical
+// flux (rho u, rho u^2 + p) (Eq. eeq:isoT both), arranged for the sweep: the physical fluxes come in
+// precomputed (u = m/rho once per cell) and one reciprocal of S_R - S_L serves both components; every
+// product-sum is an explicit fused multiply-add so that every kernel computing a face flux gets the same bits.
 __device__ inline double pressure_fma(const Phase& e, double rho) {
   return e.kind == 0 ? e.a2 * rho : __fma_rn(e.a2, rho - e.rho0, e.p0);
 }
@@ -168,36 +143,6 @@ __device__ inline double kinetic_z(double tau, bool left_is_vapour, const Side& 
   return tau * pV * Q;
 }
 
-struct PBSys {
-  double G0, G1, J00, J01, J10, J11, z;
-  Side L, R;
-  double fl, fr;
-};
-
-// G(p_l*, p_r*) of Eq. 2p_RP:ex_sys with left/right orientation and its Jacobian (Eq. jacobian:ex_sys).
-__device__ inline bool pb_eval(const Fluid& F, double tau, int phl, double rl, double ul, int phr, double rr,
-                               double ur, double pls, double prs, PBSys& S) {
-  const Phase& El = F.ph[phl];
-  const Phase& Er = F.ph[phr];
-  if (!valid_pressure(El, pls) || !valid_pressure(Er, prs)) return false;
-  S.L = side_at(El, pls);
-  S.R = side_at(Er, prs);
-  double dzl, dzr;
-  double z = kinetic_z(tau, phl == VAP, S.L, S.R, dzl, dzr);
-  double dfl, dfr;
-  S.fl = wave_f(El, pls, rl, dfl);
-  S.fr = wave_f(Er, prs, rr, dfr);
-  double jp = prs - pls, jv = S.R.v - S.L.v;
-  S.z = z;
-  S.G0 = jp + z * z * jv;
-  S.G1 = S.fl + S.fr + z * jv + (ur - ul);
-  S.J00 = -1.0 + 2.0 * z * dzl * jv - z * z * S.L.dv;
-  S.J01 = 1.0 + 2.0 * z * dzr * jv + z * z * S.R.dv;
-  S.J10 = dfl + dzl * jv - z * S.L.dv;
-  S.J11 = dfr + dzr * jv + z * S.R.dv;
-  return isfinite(S.G0) && isfinite(S.G1);
-}
-
 struct PBOut {
   double F0, F1, w, z, pl, pr;
   int iters;
@@ -226,74 +171,12 @@ __device__ inline void pb_initial_guess(const Fluid& F, int phl, double rl, doub
   pr0 = (phr == VAP) ? pvg : pliq;
 }
 
-// Phase-boundary Riemann problem (App. A): Newton's method with the Armijo rule on the 2x2 system;
-// flux F_PB = (-z, -z u_V* + p_V*) (Eq. pb_flux:pt) through the boundary moving at w = u_V* + z v_V*.
-__device__ __noinline__ PBOut pb_solve(const Fluid& F, const Opts& o, double tau, int phl, double rl, double ml, int phr,
-                                 double rr, double mr) {
-  PBOut R;
-  R.ok = 0;
-  R.iters = 0;
-  R.F0 = R.F1 = R.w = R.z = R.pl = R.pr = 0.0;
-  double ul = ml / rl, ur = mr / rr;
-  double imp = rl * F.ph[phl].a + rr * F.ph[phr].a;
-  double x0, x1;
-  pb_initial_guess(F, phl, rl, ul, phr, rr, ur, x0, x1);
-  PBSys S;
-  if (!pb_eval(F, tau, phl, rl, ul, phr, rr, ur, x0, x1, S)) return R;
-  double nrm = hypot(S.G0 / imp, S.G1);
-  bool conv = (nrm == 0.0);
-  int it = 0;
-  while (!conv && it < o.newton_itmax) {
-    ++it;
-    double det = S.J00 * S.J11 - S.J01 * S.J10;
-    if (!isfinite(det) || det == 0.0) break;
-    double d0 = -(S.J11 * S.G0 - S.J01 * S.G1) / det;
-    double d1 = -(-S.J10 * S.G0 + S.J00 * S.G1) / det;
-    double lam = 1.0;
-    bool acc = false;
-    PBSys T;
-    for (int ls = 0; ls <= 20; ++ls) {
-      if (pb_eval(F, tau, phl, rl, ul, phr, rr, ur, x0 + lam * d0, x1 + lam * d1, T)) {
-        double nt = hypot(T.G0 / imp, T.G1);
-        if (nt <= (1.0 - 1e-4 * lam) * nrm) {
-          acc = true;
-          nrm = nt;
-          break;
-        }
-      }
-      lam *= 0.5;
-    }
-    double s0 = fabs(d0) / fmax(fabs(x0), F.p_sat);
-    double s1 = fabs(d1) / fmax(fabs(x1), F.p_sat);
-    if (!acc) {
-      if (fmax(s0, s1) <= 1e-9) conv = true;
-      break;
-    }
-    x0 += lam * d0;
-    x1 += lam * d1;
-    S = T;
-    if (lam * fmax(s0, s1) <= o.newton_tol || nrm == 0.0) conv = true;
-  }
-  R.iters = it;
-  if (!conv) return R;
-  double ulS = ul - S.fl, urS = ur + S.fr;
-  double uV = (phl == VAP) ? ulS : urS;
-  double vV = (phl == VAP) ? S.L.v : S.R.v;
-  double pV = (phl == VAP) ? x0 : x1;
-  R.z = S.z;
-  R.w = uV + R.z * vV;
-  R.F0 = -R.z;
-  R.F1 = -R.z * uV + pV;
-  R.pl = x0;
-  R.pr = x1;
-  R.ok = 1;
-  return R;
-}
-
-// ---- the same boundary solve arranged for repeated calls: one (table-driven) logarithm per side and evaluation
-// (ln(rho*/rho_K) = ln(rho*/rho_sat) + ln(rho_sat/rho_K) with the last term fixed per solve), reciprocals
-// of the fixed data computed once, and an optional starting point (the previous solution) with the
-// HLLC start of App. A as fallback. Converges to the same root as pb_solve to round-off.
+// ---- the phase-boundary Riemann problem of App. A: Newton's method with the Armijo rule on the 2x2 system
+// G(p_l*, p_r*) (Eq. 2p_RP:ex_sys), flux F_PB = (-z, -z u_V* + p_V*) (Eq. pb_flux:pt) through the boundary
+// moving at w = u_V* + z v_V*. Arranged for repeated calls: one (table-driven) logarithm per side and
+// evaluation (ln(rho*/rho_K) = ln(rho*/rho_sat) + ln(rho_sat/rho_K) with the last term fixed per solve),
+// reciprocals of the fixed data computed once, and an optional starting point (the previous solution) with
+// the HLLC start of App. A as fallback.
 struct SideData {
   const Phase* E;
   double rK, pK, invK, CK, ia2, ia, isat;
