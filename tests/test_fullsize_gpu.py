@@ -164,14 +164,22 @@ def test_adjoint_full_size_against_central_differences():
         np.add.at(out, inst, 0.5 * h * dp * sm)
         return out / (2.0 * eps)
 
-    def tau_pert(bb, sgn):
-        bb.tau[:] = b.tau * (1.0 + sgn * FD_STEP["tau"])
-        return FD_STEP["tau"] * b.tau
+    def tau_pert(step):
+        def f(bb, sgn):
+            bb.tau[:] = b.tau * (1.0 + sgn * step)
+            return step * b.tau
+        return f
 
-    errs = np.abs(fd(tau_pert) - g["tau"]) / np.abs(g["tau"])
-    # over 2000 steps with ~40 grid events per instance, a 1e-4 change of tau can move an event by a step in
-    # a few instances (measured: one of 1024 at 2.2e-5, the others ~1e-7): bar 5e-5, median below
-    assert np.max(errs[ok]) <= 5e-5, np.max(errs[ok])
+    # over 2000 steps with ~40 grid events per instance, a change of tau can move an event by a step in a few
+    # instances, where the loss is not differentiable at that scale: such an instance's central differences
+    # at steps 1e-4 and 2e-4 disagree. The bar applies where they agree (a window of fixed topology), and
+    # at least 95 % of the instances must qualify.
+    fd1 = fd(tau_pert(FD_STEP["tau"]))
+    fd2 = fd(tau_pert(2.0 * FD_STEP["tau"]))
+    smooth = ok & (np.abs(fd1 - fd2) <= 1e-5 * np.abs(fd1))
+    assert smooth.mean() >= 0.95, smooth.mean()
+    errs = np.abs(fd1 - g["tau"]) / np.abs(g["tau"])
+    assert np.max(errs[smooth]) <= FD_BAR["tau"], np.max(errs[smooth])
     all_errs = list(errs[ok])
     rng = np.random.default_rng(5)
     for kind in ("rho", "m"):
