@@ -81,3 +81,29 @@ def test_tangent_of_a_uniform_state_is_exact():
     st, d = P.Oracle(b).tangent([("step", 3)], seed_m=np.ones((1, N)))
     np.testing.assert_allclose(d["rho"][0], 0.0, atol=1e-12)
     np.testing.assert_allclose(d["m"][0], 1.0, atol=1e-12)
+
+
+def test_tangent_through_phase_creation():
+    """Cavitation (App. B): the derivative of the final states with respect to V (the initial momentum
+    rho0 (-+V)) through the creation step, the created cell and its two boundaries, against central
+    differences of the plain oracle (relative step 1e-6)."""
+    b = I.cavitation_batch(4, 2, n_range=(64, 96), n_steps=40)
+    b = dataclasses.replace(b, options=I.scaled_options(creation=1, tol_nb=3e-13, tol_k=3e-11))
+    dm = np.zeros(int(b.cell_offsets[-1]))
+    V = np.zeros(b.n_inst)
+    for i in range(b.n_inst):
+        sl = slice(b.cell_offsets[i], b.cell_offsets[i + 1])
+        u = b.m[sl] / b.rho[sl]
+        V[i] = abs(u[0])
+        dm[sl] = np.sign(u) * b.rho[sl] * V[i]          # d m0 for a relative change of V
+    st, d = P.Oracle(b).tangent([("step", 40)], seed_m=dm[None, :])
+    assert (st["status"] == 0).all()
+    eps = 1e-6
+    sp = _run(dataclasses.replace(b, m=b.m + eps * dm), 40)
+    sm = _run(dataclasses.replace(b, m=b.m - eps * dm), 40)
+    assert len(sp["rho"]) == len(st["rho"]) == len(sm["rho"])
+    for key in ("rho", "m", "widths"):
+        fd = (sp[key] - sm[key]) / (2 * eps)
+        tg = d[key][0]
+        err = np.max(np.abs(fd - tg)) / np.max(np.abs(tg))
+        assert err <= 2e-5, (key, err)
