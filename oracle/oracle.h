@@ -5,6 +5,12 @@
  * benchmark compare the CUDA library against. Nothing in the product library links it,
  * includes it or calls it, and it shares no code with the CUDA path.
  *
+ * Pins (tests/test_oracle_pins.py, test_oracle_scheme.py, test_oracle_tangent.py): the boundary solver and
+ * the creation solver against the paper's printed star states, the saturation table, closed forms and
+ * special cases; the scheme against conservation, preserved equilibria, the exact Riemann solution and a
+ * fully explicit run; the tangent mode against central differences. The HLL wave-speed estimate (Davis)
+ * is a reading — the paper names HLL only — pinned by consistency and upwind limits, not by printed values.
+ *
  * Conventions (shared in meaning, not in code, with the product C-ABI):
  *   phase 0 = vapour, phase 1 = liquid.
  *   [[X]] = X_right - X_left at any discontinuity (Sec. 2.1).
