@@ -33,8 +33,9 @@ UNIT = "cell-steps/s"
 SWEEP_FLOP_PER_CELL = 33
 FP64_PEAK_TFLOPS = 1.25   # GB300 dense FP64 (nominal; no FP64 figure in MEASURED_PEAKS.json)
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_sweep launch on this workload from an ncu capture of
-# the per-step schedule; None while no capture of the current k_sweep exists
-SWEEP_TRAFFIC_BYTES = None
+# the per-step schedule (launches 301-302: 125.9 + 78.4 MB; rho, m and the stored velocity u); valid while
+# k_sweep is unchanged
+SWEEP_TRAFFIC_BYTES = 204.3e6
 
 
 def dist_env():
