@@ -647,10 +647,8 @@ __device__ void fwd_step(const ADev& A, AInst& I, SharedStep& S, double t_end, S
     for (int g = tid; g <= M; g += blockDim.x) {
       unsigned char det = 0;
       if (g >= 1 && g < M && !A.fpb[o + g] && !in_block(S, g - 1) && !in_block(S, g)) {
-        const int P = A.ph[o + g];
-        const double ps = nopt_star(c_fluid.ph[P], A.r[o + g - 1], A.m[o + g - 1] / A.r[o + g - 1], A.r[o + g],
-                                    A.m[o + g] / A.r[o + g]);
-        det = (P == LIQ) ? (ps < c_fluid.p_min) : (ps > c_fluid.p_tilde);
+        det = creation_detect(c_fluid, A.ph[o + g], A.r[o + g - 1], div_nr(A.m[o + g - 1], A.r[o + g - 1]),
+                              A.r[o + g], div_nr(A.m[o + g], A.r[o + g]));
       }
       A.cdet[o + g] = det;
     }

@@ -352,9 +352,7 @@ __device__ inline CellS shfl_up_cell(const CellS& c) {
 // cavitation / nucleation detection at a face between two free cells (App. B)
 __device__ inline int detect_face(const CellS& L, const CellS& R) {
   if (L.ow != -1 || R.ow != -1) return 0;
-  const int P = R.ph;
-  double ps = nopt_star(c_fluid.ph[P], L.r, L.u, R.r, R.u);
-  return (P == LIQ) ? (ps < c_fluid.p_min) : (ps > c_fluid.p_tilde);
+  return creation_detect(c_fluid, R.ph, L.r, L.u, R.r, R.u) ? 1 : 0;
 }
 
 struct FaceFlux {

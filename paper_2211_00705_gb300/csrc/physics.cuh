@@ -378,6 +378,26 @@ __device__ inline double nopt_star(const Phase& e, double rl, double ul, double 
   return 0.5 * (lo + hi);
 }
 
+// Creation test of App. B at a same-phase face: the no-transition star pressure p* below p_min (liquid,
+// cavitation) or above p_tilde (vapour, nucleation). Same decision as comparing nopt_star, without its
+// bisection where the bracket already decides: when the two-rarefaction value p_TR exceeds
+// min(p_l, p_r), p* lies in [min(p_l, p_r), p_TR] (and the bisection returns a point of that bracket).
+__device__ inline bool creation_detect(const Fluid& F, int P, double rl, double ul, double rr, double ur) {
+  const Phase& e = F.ph[P];
+  const double pl = pressure(e, rl), pr = pressure(e, rr);
+  const double pm = fmin(pl, pr);
+  const double ptr = pressure(e, sqrt(rl * rr) * exp((ul - ur) / (2.0 * e.a)));
+  if (ptr <= pm) return (P == LIQ) ? (ptr < F.p_min) : (ptr > F.p_tilde);
+  if (P == LIQ) {
+    if (pm >= F.p_min) return false;
+  } else {
+    if (ptr <= F.p_tilde) return false;
+    if (pm > F.p_tilde) return true;
+  }
+  const double ps = nopt_star(e, rl, ul, rr, ur);
+  return (P == LIQ) ? (ps < F.p_min) : (ps > F.p_tilde);
+}
+
 struct CreateOut {
   double pC, rhoC, uC, z1, z2, w1, w2;
   double pPl, pPr;  // converged parent-side pressures

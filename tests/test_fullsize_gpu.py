@@ -172,11 +172,11 @@ def test_adjoint_full_size_against_central_differences():
 
     # over 2000 steps with ~40 grid events per instance, a change of tau can move an event by a step in a few
     # instances, where the loss is not differentiable at that scale: such an instance's central differences
-    # at steps 1e-4 and 2e-4 disagree. The bar applies where they agree to 2e-6 (a window of fixed topology,
+    # at steps 1e-3 and 2e-3 disagree. The bar applies where they agree to 2e-6 (a window of fixed topology,
     # with the differences' own uncertainty well below the bar), and at least 90 % of the instances must
     # qualify.
-    fd1 = fd(tau_pert(FD_STEP["tau"]))
-    fd2 = fd(tau_pert(2.0 * FD_STEP["tau"]))
+    fd1 = fd(tau_pert(1e-3))   # tau moves the states by ~1e-7 relative: steps above the noise floor
+    fd2 = fd(tau_pert(2e-3))
     smooth = ok & (np.abs(fd1 - fd2) <= 2e-6 * np.abs(fd1))
     assert smooth.mean() >= 0.90, smooth.mean()
     errs = np.abs(fd1 - g["tau"]) / np.abs(g["tau"])
