@@ -225,12 +225,17 @@ def _mean_pressure(st, b):
     return J, gr, gw
 
 
-def test_adjoint_through_phase_creation_dJ_dV():
-    """Cavitation (App. B): liquid pulled apart at +-V creates a vapour cell. dJ/dV of the mean final pressure
-    (V enters the initial momentum, m0 = rho0 (-+V)) from the adjoint against the oracle's tangent in the V
-    direction and against central differences of the CUDA forward run (step 1e-6 relative)."""
+@pytest.mark.parametrize("kind", ["cavitation", "nucleation"])
+def test_adjoint_through_phase_creation_dJ_dV(kind):
+    """Phase creation (App. B): liquid pulled apart at +-V creates a vapour cell (cavitation), vapour driven
+    together at +-V nucleates a liquid cell (nucleation). dJ/dV of the mean final pressure (V enters the
+    initial momentum, m0 = rho0 (-+V)) from the adjoint against the oracle's tangent in the V direction and
+    against central differences of the CUDA forward run (step 1e-6 relative)."""
     from paper_2211_00705_gb300.imexds import Imexds
-    b = I.cavitation_batch(4, 4, n_range=(64, 128), n_steps=60)
+    if kind == "cavitation":
+        b = I.cavitation_batch(4, 4, n_range=(64, 128), n_steps=60)
+    else:
+        b = I.nucleation_batch(5, 4, n_range=(64, 128), n_steps=60)
     b = dataclasses.replace(b, options=I.scaled_options(creation=1, tol_nb=3e-13, tol_k=3e-11))
     program = [("step", 60)]
     ctx = _forward(b, program)
