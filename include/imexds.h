@@ -195,10 +195,12 @@ imexds_status imexds_check_log(int32_t n, const double* x, double* fast, double*
  * merges, implicit blocks, splits): the explicit sweep by its transposed HLL Jacobians, each block's
  * converged dual-time system by one transposed solve (implicit function theorem, not by unrolling the
  * pseudo-iterations), the boundary flux by the implicit function theorem on the 2x2 system of
- * Eq. 2p_RP:ex_sys, forward states checkpointed every k steps and recomputed per segment.
- * Phase creation (App. B) is not differentiated (an instance that creates a phase reports
- * IMEXDS_ERR_STATE). The gradient is that of the converged implicit system: use tight dual-time
- * tolerances when it is compared with finite differences of the forward run.
+ * Eq. 2p_RP:ex_sys, phase creation (App. B) through the created cell, the per-side fluxes and moving
+ * faces at the creation face and the implicit function theorem on the 3x3 creation system, forward states
+ * checkpointed every k steps and recomputed per segment. The gradient is that of the converged implicit
+ * system: use tight dual-time tolerances when it is compared with finite differences of the forward run.
+ * An instance whose replay does not reproduce the forward run (steps, cells, or a grid event of its
+ * reverse) reports IMEXDS_ERR_STATE (imexds_adjoint_replay says where).
  *
  * Inputs (host arrays in imexds_get_states order, sized from imexds_cell_counts): dJ_drho_T, dJ_dm_T
  * and dJ_dw_T (may be NULL: J independent of the widths). Outputs (host arrays in imexds_set_states
