@@ -86,6 +86,16 @@ Dual<K> fabs(const Dual<K>& a) {
 }
 
 inline double val(double x) { return x; }
+
+// The value v with the derivatives of `same`, an expression equal to the one that gave v. Used where the
+// defining formula's derivative has a removable 0 * inf (a square root at zero) that an equal form avoids.
+inline double with_value(double v, double /*same*/) { return v; }
+template <int K>
+Dual<K> with_value(double v, const Dual<K>& same) {
+  Dual<K> r = same;
+  r.v = v;
+  return r;
+}
 template <int K>
 double val(const Dual<K>& x) {
   return x.v;

@@ -20,6 +20,7 @@
 #include <cstdint>
 #include <cstring>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 namespace {
@@ -158,6 +159,16 @@ T wave_f(const Phase& e, const T& pstar, const T& rhoK, T* dfdp) {
     T f = tsqrt(q);
     T dq = dv + (pstar - pK) * vs * vs / e.a2;  // d/dp* of (p* - p_K)(v_K - v*)
     *dfdp = (val(f) > 0.0) ? T(0.5 * dq / f) : T(vs / e.a);
+    if constexpr (!std::is_same_v<T, double>) {
+      // Tangent mode only. For the linear isothermal EOS (dp = a2 drho on either branch)
+      // (p* - p_K)(v_K - v*) = (p* - p_K)^2 / (a2 rho_K rho*), so f = (p* - p_K) / (a sqrt(rho_K rho*)) and
+      // df/dp* = (1 - (p* - p_K) v* / (2 a2)) / (a sqrt(rho_K rho*)). The derivative parts come from these
+      // forms: near p* = p_K the product rounds to zero and the square root's derivative is 0 * inf, theirs
+      // stay finite. The values remain those of the definition above.
+      T den = e.a * tsqrt(T(rhoK * rs));
+      f = orcdual::with_value(val(f), T((pstar - pK) / den));
+      *dfdp = orcdual::with_value(val(*dfdp), T((1.0 - (pstar - pK) * vs / (2.0 * e.a2)) / den));
+    }
     return f;
   }
   *dfdp = vs / e.a;
