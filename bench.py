@@ -33,9 +33,8 @@ UNIT = "cell-steps/s"
 SWEEP_FLOP_PER_CELL = 33
 FP64_PEAK_TFLOPS = 1.25   # GB300 dense FP64 (nominal; no FP64 figure in MEASURED_PEAKS.json)
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_sweep launch on this workload from an ncu capture of
-# the per-step schedule (launches 301-302: 125.9 + 78.4 MB; rho, m and the stored velocity u); valid while
-# k_sweep is unchanged
-SWEEP_TRAFFIC_BYTES = 204.3e6
+# the per-step schedule; None until the current k_sweep (31-cell tiles) has been captured
+SWEEP_TRAFFIC_BYTES = None
 
 
 def dist_env():

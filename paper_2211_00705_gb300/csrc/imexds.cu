@@ -307,11 +307,10 @@ __device__ __noinline__ void plan_zone(const Dev& d, int zi) {
 }
 
 // ------------------------------------------------------------------------------------------ sweep
-// Algorithm 1, Step 1 on a 32-cell tile of one instance, one warp per tile: HLL fluxes from U^n at the
-// faces of free lattice cells, the explicit update of Eq. update expl time (Eq. godunov_meth:nonunif
-// next to a creation face) and the tile's wave-speed maximum. Lane l owns cell j0+l and the face on its
-// left; the right-face flux comes from lane l+1 (lane 31 computes the tile's last face itself). u = m/rho
-// and the momentum flux are formed once per cell. A face next to a zone sees the zone's edge state.
+// Algorithm 1, Step 1 on a tile of one instance, one warp per tile: HLL fluxes from U^n at the faces of
+// free lattice cells, the explicit update of Eq. update expl time (Eq. godunov_meth:nonunif next to a
+// creation face) and the tile's wave-speed maximum. Lane l owns cell j0+l and the face on its left; the
+// right-face flux comes from lane l+1. u = m/rho and the momentum flux are formed once per cell. A face next to a zone sees the zone's edge state.
 // CREATION adds detection and the creation solve of App. B at faces between two free cells.
 struct CellS {
   int ow, ph;  // owner (-1 free, >= 0 zone slot, -2 outside the domain), phase
@@ -405,7 +404,7 @@ __device__ inline FaceFlux face_flux(const Dev& d, Inst& I, int ii, int f, const
   if (CREATION && create) {
     // fluxes of Eq. flux:cavitation / flux:nucleation with each boundary's own mass flux
     CreateOut Cr = creation_solve(c_fluid, c_opts, I.tau, P, rl, ml, rr, mr);
-    atomicAdd((unsigned long long*)&I.stats[3], (unsigned long long)Cr.iters);
+    if (record) atomicAdd((unsigned long long*)&I.stats[3], (unsigned long long)Cr.iters);
     if (!Cr.ok) {
       set_status(I, IMEXDS_ERR_PB_NOCONV);
       o.F0L = o.F1L = o.F0R = o.F1R = 0.0;
@@ -442,10 +441,15 @@ __device__ inline FaceFlux face_flux(const Dev& d, Inst& I, int ii, int f, const
   return o;
 }
 
-// One 32-cell tile; all 32 lanes of the calling warp take part. Returns the tile's wave-speed maximum
-// (also folded into the instance's atomic maximum).
+// One tile of TILE = 31 cells; all 32 lanes of the calling warp take part. Lane l holds cell j0+l and
+// computes the face on its left; cells j0..j0+30 are updated, lane 31 only supplies the right face of cell
+// j0+30 (the next tile's lane 0 computes the same face from the same states: identical bits). No lane
+// computes a second face, so the warp's FP64 instructions all run with the tile's lanes active. The
+// tile's wave-speed maximum is folded into the instance's atomic maximum.
+constexpr int TILE = 31;
+
 template <bool CREATION>
-__device__ void sweep_tile32(const Dev& d, int ii, int j0) {
+__device__ void sweep_tile(const Dev& d, int ii, int j0) {
   const int lane = threadIdx.x & 31;
   Inst& I = d.inst[ii];
   const int N = I.N;
@@ -453,9 +457,7 @@ __device__ void sweep_tile32(const Dev& d, int ii, int j0) {
   const CellS C = load_cell(d, I, j);
   CellS Lc = shfl_up_cell(C);
   if (lane == 0) Lc = load_cell(d, I, j0 - 1);
-  CellS Rx;
-  if (lane == 31) Rx = load_cell(d, I, j0 + 32);
-  int det_j = 0, det_jm1 = 0, det_x = 0;
+  int det_j = 0, det_jm1 = 0;
   if (CREATION) {
     det_j = (j <= N) ? detect_face(Lc, C) : 0;
     det_jm1 = __shfl_up_sync(0xffffffffu, det_j, 1);
@@ -463,27 +465,26 @@ __device__ void sweep_tile32(const Dev& d, int ii, int j0) {
       CellS L2 = load_cell(d, I, j0 - 2);
       det_jm1 = detect_face(L2, Lc);
     }
-    if (lane == 31) det_x = detect_face(C, Rx);
   }
-  // face j (left face of cell j): needed by cell j, and by cell j-1 when it is in this tile
-  const bool cfree = (C.ow == -1);
+  // face j (left face of cell j): needed by cell j (updated here for lanes < TILE) and by cell j-1 (lanes > 0)
+  const bool cfree = (lane < TILE) && (C.ow == -1);
   const bool need = (j <= N) && (cfree || (lane > 0 && Lc.ow == -1));
   FaceFlux fj;
   fj.F0L = fj.F1L = fj.F0R = fj.F1R = fj.WL = fj.WR = 0.0;
-  if (need) fj = face_flux<CREATION>(d, I, ii, j, Lc, C, CREATION && det_j && !det_jm1, true);
+  // a creation event is recorded by the lane that updates the cell right of the face (lane 31's face is the
+  // next tile's lane 0 face)
+  if (need) fj = face_flux<CREATION>(d, I, ii, j, Lc, C, CREATION && det_j && !det_jm1, lane < TILE);
   // right face of cell j
   FaceFlux fr;
   fr.F0L = __shfl_down_sync(0xffffffffu, fj.F0L, 1);
   fr.F1L = __shfl_down_sync(0xffffffffu, fj.F1L, 1);
   fr.WL = __shfl_down_sync(0xffffffffu, fj.WL, 1);
-  if (lane == 31 && cfree && j < N)
-    fr = face_flux<CREATION>(d, I, ii, j + 1, C, Rx, CREATION && det_x && !det_j, false);
-  double smax = 0.0;
+  unsigned long long sbits = 0ull;
   if (cfree && j < N) {
     const double h = I.h, dt = I.dt;
     const int g = I.lat_off + j;
     double r1, m1;
-    if (CREATION && (fr.WL != 0.0 || fj.WR != 0.0)) {
+    if (CREATION && (nonzero_bits(fr.WL) || nonzero_bits(fj.WR))) {
       double hnp1 = h + (fr.WL - fj.WR) * dt;
       r1 = (h * C.r - dt * (fr.F0L - fj.F0R)) / hnp1;
       m1 = (h * C.m - dt * (fr.F1L - fj.F1R)) / hnp1;
@@ -495,14 +496,19 @@ __device__ void sweep_tile32(const Dev& d, int ii, int j0) {
     d.rho[I.parity ^ 1][g] = r1;
     d.m[I.parity ^ 1][g] = m1;
     d.u[I.parity ^ 1][g] = u1;
-    if (!(r1 > 0.0) || !isfinite(r1) || !isfinite(m1)) set_status(I, IMEXDS_ERR_NONPHYSICAL);
-    smax = fabs(u1) + c_fluid.ph[C.ph].a;
+    if (!pos_finite_bits(r1) || !finite_bits(m1)) set_status(I, IMEXDS_ERR_NONPHYSICAL);
+    sbits = dbits(fabs(u1) + c_fluid.ph[C.ph].a);
   }
-  for (int off = 16; off > 0; off >>= 1) smax = fmax(smax, __shfl_down_sync(0xffffffffu, smax, off));
-  if (lane == 0 && smax > 0.0) atomicMax(&I.smax_bits, dbits(smax));
+  // the warp maximum of non-negative doubles is the maximum of their bit patterns: high words first, then
+  // the low words of the lanes holding the maximal high word (integer reductions, off the FP64 pipe)
+  const unsigned hi = (unsigned)(sbits >> 32);
+  const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? (unsigned)sbits : 0u);
+  const unsigned long long wmax = ((unsigned long long)mhi << 32) | mlo;
+  if (lane == 0 && wmax != 0ull) atomicMax(&I.smax_bits, wmax);
 }
 
-// Per-step sweep kernel: one warp per 32-cell tile of the tile table.
+// Per-step sweep kernel: one warp per tile of the tile table.
 template <bool CREATION>
 __global__ void __launch_bounds__(256) k_sweep(Dev d, int n_tiles) {
   const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -510,7 +516,7 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, int n_tiles) {
   const int2 tile = d.tiles[t];
   const Inst& I = d.inst[tile.x];
   if (!I.active || I.status) return;
-  sweep_tile32<CREATION>(d, tile.x, tile.y);
+  sweep_tile<CREATION>(d, tile.x, tile.y);
 }
 
 // ------------------------------------------------------------------------------------------ k_dts
@@ -1332,13 +1338,13 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 2 : 1)) k_group(Dev d, const 
       }
       cyc[2] += clock64() - c1;
     } else {
-      // the 32-cell tiles of all active instances of the group, dealt to warps 1..nw-1
+      // the tiles of all active instances of the group, dealt to warps 1..nw-1
       int t = warp - 1, base = 0;
       for (int k = 0; k < gr.y; ++k) {
         const int ik = ginst[gr.x + k];
         const Inst& I = d.inst[ik];
-        const int nt = (I.active && !I.status) ? (I.N + 31) >> 5 : 0;
-        for (; t < base + nt; t += nw - 1) sweep_tile32<CREATION>(d, ik, (t - base) << 5);
+        const int nt = (I.active && !I.status) ? (I.N + TILE - 1) / TILE : 0;
+        for (; t < base + nt; t += nw - 1) sweep_tile<CREATION>(d, ik, (t - base) * TILE);
         base += nt;
       }
       cyc[1] += clock64() - c1;
@@ -1366,7 +1372,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 2 : 1)) k_group(Dev d, const 
 }
 
 // Instance groups without a per-step barrier. Lane k of warp 0 runs instance k's serial work at its own
-// pace; the other warps sweep the 32-cell tiles of whichever instance has planned its step. Per instance,
+// pace; the other warps sweep the tiles of whichever instance has planned its step. Per instance,
 // shared counters order the work of one step n:
 //   lane k: boundary solves + merges + blocks (n) -> open the sweep of step n -> Algorithm 2 (n)
 //           -> wait until every tile of step n is swept -> grid management (n) -> step n + 1
@@ -1406,7 +1412,7 @@ __global__ void __launch_bounds__(128, 2) k_group_async(Dev d, const int* ginst,
   if (warp == 0) {
     if (!live) return;
     Inst& I = d.inst[ii];
-    const int nt = (I.N + 31) >> 5;
+    const int nt = (I.N + TILE - 1) / TILE;
     long long cp = 0, cd = 0, cw = 0, cq = 0;
     for (int step = 0; step < max_steps; ++step) {
       long long c0 = clock64();
@@ -1464,7 +1470,7 @@ __global__ void __launch_bounds__(128, 2) k_group_async(Dev d, const int* ginst,
     return;
   }
   // sweep warps: lane 0 reads the shared state and takes the ticket, the warp follows its decision
-  // (sweep_tile32 needs all 32 lanes)
+  // (sweep_tile needs all 32 lanes)
   long long busy = 0, idle0 = clock64();
   int k = (gr.y > 0) ? (warp - 1) % gr.y : 0;
   for (;;) {
@@ -1490,7 +1496,7 @@ __global__ void __launch_bounds__(128, 2) k_group_async(Dev d, const int* ginst,
     if (alive <= 0) break;
     if (kk >= 0) {
       long long b0 = clock64();
-      sweep_tile32<CREATION>(d, ginst[gr.x + kk], t << 5);
+      sweep_tile<CREATION>(d, ginst[gr.x + kk], t * TILE);
       __threadfence_block();
       __syncwarp();
       if (lane == 0) atomicAdd(&s_done[kk], 1);
@@ -2150,7 +2156,7 @@ imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double*
   }
   std::vector<int2> tiles;
   for (int i = 0; i < n; ++i)
-    for (int j0 = 0; j0 < c->N[i]; j0 += 32) tiles.push_back(make_int2(i, j0));
+    for (int j0 = 0; j0 < c->N[i]; j0 += TILE) tiles.push_back(make_int2(i, j0));
   free_dev(c);
   Dev& d = c->d;
   for (int k = 0; k < 2; ++k) {

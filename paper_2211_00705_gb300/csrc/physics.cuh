@@ -25,6 +25,37 @@ __device__ __forceinline__ double rcp_nr(double b) {
 }
 __device__ __forceinline__ double div_nr(double a, double b) { return a * rcp_nr(b); }
 
+// Comparisons decided on the IEEE-754 bit patterns, in integer instructions. On this GPU an FP64 compare
+// or min/max issues to the narrow FP64 pipe that the sweep's arithmetic already saturates; the integer
+// pipe is ~30x wider. Each helper returns what the FP64 comparison returns for every non-NaN argument.
+// ord_key maps a double to an int64 with the same order (a negative double's magnitude bits inverted);
+// -0 keys below +0, which no caller distinguishes (they only feed sums with a non-zero term).
+__device__ __forceinline__ long long ord_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ __forceinline__ bool lt_bits(double x, double y) { return ord_key(x) < ord_key(y); }
+// x >= 0 (either zero, +inf included; false for NaN)
+__device__ __forceinline__ bool ge0_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return b <= 0x7FF0000000000000ull || b == 0x8000000000000000ull;
+}
+// x <= 0 (either zero, -inf included; false for NaN)
+__device__ __forceinline__ bool le0_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return b == 0ull || (b >= 0x8000000000000000ull && b <= 0xFFF0000000000000ull);
+}
+// 0 < x < inf (false for NaN)
+__device__ __forceinline__ bool pos_finite_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) - 1ull < 0x7FEFFFFFFFFFFFFFull;
+}
+// x finite (false for +-inf and NaN)
+__device__ __forceinline__ bool finite_bits(double x) {
+  return (__double2hiint(x) & 0x7FF00000) != 0x7FF00000;
+}
+// x != 0 (+0 and -0 are zero; true for NaN, as the FP64 comparison)
+__device__ __forceinline__ bool nonzero_bits(double x) { return (__double_as_longlong(x) << 1) != 0; }
+
 constexpr int VAP = 0;
 constexpr int LIQ = 1;
 
@@ -69,13 +100,14 @@ __device__ inline double pressure_fma(const Phase& e, double rho) {
 }
 __device__ inline void hll_pre(double a, double rl, double ml, double ul, double fl1, double rr, double mr, double ur,
                                double fr1, double& F0, double& F1) {
-  double umin = ul < ur ? ul : ur;
-  double umax = ul < ur ? ur : ul;
+  const bool lt = lt_bits(ul, ur);
+  double umin = lt ? ul : ur;
+  double umax = lt ? ur : ul;
   double SL = umin - a, SR = umax + a;
-  if (SL >= 0.0) {
+  if (ge0_bits(SL)) {
     F0 = ml;
     F1 = fl1;
-  } else if (SR <= 0.0) {
+  } else if (le0_bits(SR)) {
     F0 = mr;
     F1 = fr1;
   } else {
