@@ -87,6 +87,11 @@ struct Dev {
   double* rho[2];
   double* m[2];
   double* u[2];  // u = m / rho of every lattice cell, written by whoever writes the cell (saves a division)
+  // The buffers of parity p, selected rather than indexed: a run-time index into the arrays of this
+  // struct (a kernel parameter) makes the compiler copy the whole struct to local memory in every thread.
+  __device__ __forceinline__ double* R(int p) const { return p ? rho[1] : rho[0]; }
+  __device__ __forceinline__ double* M(int p) const { return p ? m[1] : m[0]; }
+  __device__ __forceinline__ double* U(int p) const { return p ? u[1] : u[0]; }
   unsigned char* phase;
   int* own;
   Zone* zones;
@@ -169,8 +174,8 @@ __device__ __noinline__ void plan_zone(const Dev& d, int zi) {
   Inst& I = d.inst[Z.inst];
   if (!I.active || I.status) return;
   const int cur = I.parity;
-  const double* lr = d.rho[cur] + I.lat_off;
-  const double* lm = d.m[cur] + I.lat_off;
+  const double* lr = d.R(cur) + I.lat_off;
+  const double* lm = d.M(cur) + I.lat_off;
   int mark[ZC];
   for (int i = 0; i < Z.nc; ++i) mark[i] = (Z.merge_mask >> i) & 1;
   long long merges = 0;
@@ -318,22 +323,21 @@ struct CellS {
 };
 
 __device__ inline CellS load_cell(const Dev& d, const Inst& I, int j) {
+  // every load is issued unconditionally (index clamped into the instance) and the results are selected,
+  // so that the owner, phase and state loads overlap instead of forming a dependent chain
+  const bool in = (j >= 0) && (j < I.N);
+  const int g = I.lat_off + (in ? j : 0);
+  const int ow = d.own[g];
+  const int ph = d.phase[g];
+  const double r = d.R(I.parity)[g], m = d.M(I.parity)[g], u = d.U(I.parity)[g];
+  const bool fr = in && ow < 0;
   CellS c;
-  c.ow = -2;
-  c.ph = 0;
-  c.r = 1.0;
-  c.m = c.u = c.f1 = 0.0;
-  if (j >= 0 && j < I.N) {
-    const int g = I.lat_off + j;
-    c.ow = d.own[g];
-    c.ph = d.phase[g];
-    if (c.ow < 0) {
-      c.r = d.rho[I.parity][g];
-      c.m = d.m[I.parity][g];
-      c.u = d.u[I.parity][g];
-      c.f1 = __fma_rn(c.m, c.u, pressure_fma(c_fluid.ph[c.ph], c.r));
-    }
-  }
+  c.ow = in ? ow : -2;
+  c.ph = in ? ph : 0;
+  c.r = fr ? r : 1.0;
+  c.m = fr ? m : 0.0;
+  c.u = fr ? u : 0.0;
+  c.f1 = fr ? __fma_rn(m, u, pressure_fma(c_fluid.ph[ph], r)) : 0.0;
   return c;
 }
 
@@ -358,49 +362,44 @@ struct FaceFlux {
   double F0L, F1L, F0R, F1R, WL, WR;  // seen from the left / right cell; face speeds (creation only)
 };
 
-// Flux at face f between cells L and R (at least one of them free). `create`: App. B at this face.
+// Flux at face f between cells L and R (at least one of them free). `create`: App. B at this face. The
+// common case (two free cells of one phase) is straight-line code; zone edges, domain ends and creation
+// adjust inputs or results on their own branches.
 template <bool CREATION>
 __device__ inline FaceFlux face_flux(const Dev& d, Inst& I, int ii, int f, const CellS& L, const CellS& R, bool create,
                                      bool record) {
   FaceFlux o;
   o.WL = o.WR = 0.0;
-  if (L.ow == -2) {  // left domain end: transmissive
-    o.F0L = o.F0R = R.m;
-    o.F1L = o.F1R = R.f1;
-    return o;
-  }
-  if (R.ow == -2) {
-    o.F0L = o.F0R = L.m;
-    o.F1L = o.F1R = L.f1;
-    return o;
-  }
   const int P = (L.ow == -1) ? L.ph : R.ph;
   const Phase& E = c_fluid.ph[P];
-  double rl, ml, ul, fl1, rr, mr, ur, fr1;
-  if (L.ow >= 0) {
+  double rl = L.r, ml = L.m, ul = L.u, fl1 = L.f1;
+  double rr = R.r, mr = R.m, ur = R.u, fr1 = R.f1;
+  // a needed face has a free cell on at least one side: a zone edge faces a free cell
+  if (L.ow >= 0 && R.ow == -1) {  // a zone's last cell: its state at t^n
     const Zone& Z = d.zones[L.ow];
     rl = Z.eR0;
     ml = Z.eR1;
     ul = div_nr(ml, rl);
     fl1 = __fma_rn(ml, ul, pressure_fma(E, rl));
-  } else {
-    rl = L.r;
-    ml = L.m;
-    ul = L.u;
-    fl1 = L.f1;
   }
-  if (R.ow >= 0) {
+  if (R.ow >= 0 && L.ow == -1) {
     const Zone& Z = d.zones[R.ow];
     rr = Z.eL0;
     mr = Z.eL1;
     ur = div_nr(mr, rr);
     fr1 = __fma_rn(mr, ur, pressure_fma(E, rr));
-  } else {
-    rr = R.r;
-    mr = R.m;
-    ur = R.u;
-    fr1 = R.f1;
   }
+  hll_pre(E.a, rl, ml, ul, fl1, rr, mr, ur, fr1, o.F0L, o.F1L);
+  if (R.ow == -2) {  // right domain end: transmissive
+    o.F0L = L.m;
+    o.F1L = L.f1;
+  }
+  if (L.ow == -2) {  // left domain end: transmissive
+    o.F0L = R.m;
+    o.F1L = R.f1;
+  }
+  o.F0R = o.F0L;
+  o.F1R = o.F1L;
   if (CREATION && create) {
     // fluxes of Eq. flux:cavitation / flux:nucleation with each boundary's own mass flux
     CreateOut Cr = creation_solve(c_fluid, c_opts, I.tau, P, rl, ml, rr, mr);
@@ -433,19 +432,16 @@ __device__ inline FaceFlux face_flux(const Dev& d, Inst& I, int ii, int f, const
         set_status(I, IMEXDS_ERR_CAPACITY);
       }
     }
-    return o;
   }
-  hll_pre(E.a, rl, ml, ul, fl1, rr, mr, ur, fr1, o.F0L, o.F1L);
-  o.F0R = o.F0L;
-  o.F1R = o.F1L;
   return o;
 }
 
-// One tile of TILE = 31 cells; all 32 lanes of the calling warp take part. Lane l holds cell j0+l and
-// computes the face on its left; cells j0..j0+30 are updated, lane 31 only supplies the right face of cell
-// j0+30 (the next tile's lane 0 computes the same face from the same states: identical bits). No lane
-// computes a second face, so the warp's FP64 instructions all run with the tile's lanes active. The
-// tile's wave-speed maximum is folded into the instance's atomic maximum.
+// One tile of TILE = 31 cells starting at cell j0; all 32 lanes of the calling warp take part. Lane l holds
+// cell j0 + l and computes the face on its left; cells j0..j0+30 are updated, lane 31 only supplies the
+// right face of cell j0+30 (the next tile's lane 0 computes the same face from the same states: identical
+// bits). No lane computes a second face, so the warp's FP64 instructions all run with the tile's lanes
+// active. The common path is straight-line code. The tile's wave-speed maximum is folded into the
+// instance's atomic maximum.
 constexpr int TILE = 31;
 
 template <bool CREATION>
@@ -455,8 +451,9 @@ __device__ void sweep_tile(const Dev& d, int ii, int j0) {
   const int N = I.N;
   const int j = j0 + lane;
   const CellS C = load_cell(d, I, j);
+  const CellS Lfirst = load_cell(d, I, j0 - 1);  // same address in every lane
   CellS Lc = shfl_up_cell(C);
-  if (lane == 0) Lc = load_cell(d, I, j0 - 1);
+  if (lane == 0) Lc = Lfirst;
   int det_j = 0, det_jm1 = 0;
   if (CREATION) {
     det_j = (j <= N) ? detect_face(Lc, C) : 0;
@@ -466,36 +463,33 @@ __device__ void sweep_tile(const Dev& d, int ii, int j0) {
       det_jm1 = detect_face(L2, Lc);
     }
   }
-  // face j (left face of cell j): needed by cell j (updated here for lanes < TILE) and by cell j-1 (lanes > 0)
-  const bool cfree = (lane < TILE) && (C.ow == -1);
-  const bool need = (j <= N) && (cfree || (lane > 0 && Lc.ow == -1));
-  FaceFlux fj;
-  fj.F0L = fj.F1L = fj.F0R = fj.F1R = fj.WL = fj.WR = 0.0;
-  // a creation event is recorded by the lane that updates the cell right of the face (lane 31's face is the
-  // next tile's lane 0 face)
-  if (need) fj = face_flux<CREATION>(d, I, ii, j, Lc, C, CREATION && det_j && !det_jm1, lane < TILE);
+  // face j (left face of cell j): needed by cell j (updated for lanes < TILE) and by cell j-1 (lanes > 0)
+  const bool upd = (lane < TILE) && (C.ow == -1) && (j < N);
+  const bool need = (j <= N) && (((lane < TILE) && (C.ow == -1)) || (lane > 0 && Lc.ow == -1));
+  // computed in every lane (unneeded lanes hold finite placeholder states); a creation event is recorded by
+  // the lane that updates the cell right of the face (lane 31's face is the next tile's lane 0 face)
+  const FaceFlux fj = face_flux<CREATION>(d, I, ii, j, Lc, C, CREATION && need && det_j && !det_jm1, lane < TILE);
   // right face of cell j
-  FaceFlux fr;
-  fr.F0L = __shfl_down_sync(0xffffffffu, fj.F0L, 1);
-  fr.F1L = __shfl_down_sync(0xffffffffu, fj.F1L, 1);
-  fr.WL = __shfl_down_sync(0xffffffffu, fj.WL, 1);
-  unsigned long long sbits = 0ull;
-  if (cfree && j < N) {
+  const double G0 = __shfl_down_sync(0xffffffffu, fj.F0L, 1);
+  const double G1 = __shfl_down_sync(0xffffffffu, fj.F1L, 1);
+  const double GW = CREATION ? __shfl_down_sync(0xffffffffu, fj.WL, 1) : 0.0;
+  const double lam = I.lam;
+  double r1 = __fma_rn(-lam, G0 - fj.F0R, C.r);
+  double m1 = __fma_rn(-lam, G1 - fj.F1R, C.m);
+  if (CREATION && upd && (nonzero_bits(GW) || nonzero_bits(fj.WR))) {
     const double h = I.h, dt = I.dt;
+    const double hnp1 = h + (GW - fj.WR) * dt;
+    r1 = (h * C.r - dt * (G0 - fj.F0R)) / hnp1;
+    m1 = (h * C.m - dt * (G1 - fj.F1R)) / hnp1;
+  }
+  const double u1 = div_nr(m1, r1);
+  unsigned long long sbits = 0ull;
+  if (upd) {
     const int g = I.lat_off + j;
-    double r1, m1;
-    if (CREATION && (nonzero_bits(fr.WL) || nonzero_bits(fj.WR))) {
-      double hnp1 = h + (fr.WL - fj.WR) * dt;
-      r1 = (h * C.r - dt * (fr.F0L - fj.F0R)) / hnp1;
-      m1 = (h * C.m - dt * (fr.F1L - fj.F1R)) / hnp1;
-    } else {
-      r1 = __fma_rn(-I.lam, fr.F0L - fj.F0R, C.r);
-      m1 = __fma_rn(-I.lam, fr.F1L - fj.F1R, C.m);
-    }
-    const double u1 = div_nr(m1, r1);
-    d.rho[I.parity ^ 1][g] = r1;
-    d.m[I.parity ^ 1][g] = m1;
-    d.u[I.parity ^ 1][g] = u1;
+    const int nxt = I.parity ^ 1;
+    d.R(nxt)[g] = r1;
+    d.M(nxt)[g] = m1;
+    d.U(nxt)[g] = u1;
     if (!pos_finite_bits(r1) || !finite_bits(m1)) set_status(I, IMEXDS_ERR_NONPHYSICAL);
     sbits = dbits(fabs(u1) + c_fluid.ph[C.ph].a);
   }
@@ -661,8 +655,8 @@ __device__ void dts_simple(const Dev& d, int zi) {
   Zone& Z = d.zones[zi];
   Inst& I = d.inst[Z.inst];
   const int cur = I.parity;
-  const double* lr = d.rho[cur] + I.lat_off;
-  const double* lm = d.m[cur] + I.lat_off;
+  const double* lr = d.R(cur) + I.lat_off;
+  const double* lm = d.M(cur) + I.lat_off;
   const unsigned char* lph = d.phase + I.lat_off;
   const double dt = I.dt, h = I.h, tau = I.tau;
   const int N = I.N;
@@ -782,9 +776,9 @@ __device__ void dts_simple(const Dev& d, int zi) {
     set_status(I, IMEXDS_ERR_VANISH);
     return;
   }
-  double* nr = d.rho[cur ^ 1] + I.lat_off;
-  double* nm = d.m[cur ^ 1] + I.lat_off;
-  double* nu = d.u[cur ^ 1] + I.lat_off;
+  double* nr = d.R(cur ^ 1) + I.lat_off;
+  double* nm = d.M(cur ^ 1) + I.lat_off;
+  double* nu = d.U(cur ^ 1) + I.lat_off;
   double smax = 0.0;
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
@@ -841,10 +835,10 @@ __device__ __noinline__ void dts_zone_general(const Dev& d, int zi) {
   Zone& Z = d.zones[zi];
   Inst& I = d.inst[Z.inst];
   const int cur = I.parity;
-  const double* lr = d.rho[cur] + I.lat_off;
-  const double* lm = d.m[cur] + I.lat_off;
-  double* nr = d.rho[cur ^ 1] + I.lat_off;
-  double* nm = d.m[cur ^ 1] + I.lat_off;
+  const double* lr = d.R(cur) + I.lat_off;
+  const double* lm = d.M(cur) + I.lat_off;
+  double* nr = d.R(cur ^ 1) + I.lat_off;
+  double* nm = d.M(cur ^ 1) + I.lat_off;
   const unsigned char* lph = d.phase + I.lat_off;
   const double dt = I.dt, h = I.h;
   const int N = I.N;
@@ -920,7 +914,7 @@ __device__ __noinline__ void dts_zone_general(const Dev& d, int zi) {
       return;
   }
   double smax = 0.0;
-  double* nu = d.u[cur ^ 1] + I.lat_off;
+  double* nu = d.U(cur ^ 1) + I.lat_off;
   for (int q = 0; q < nq; ++q) {
     int e = q + e0;
     double r1 = out_r[q], m1 = out_m[q];
@@ -981,9 +975,9 @@ __device__ __noinline__ void post_inst(const Dev& d, int ii) {
   const double h = I.h;
   int* own = d.own + I.lat_off;
   const int nxt = I.parity ^ 1;
-  double* nr = d.rho[nxt] + I.lat_off;
-  double* nm = d.m[nxt] + I.lat_off;
-  double* nu = d.u[nxt] + I.lat_off;
+  double* nr = d.R(nxt) + I.lat_off;
+  double* nm = d.M(nxt) + I.lat_off;
+  double* nu = d.U(nxt) + I.lat_off;
   unsigned char* lph = d.phase + I.lat_off;
   Zone* zones = d.zones + I.zone_off;
   for (int z = 0; z < I.zone_cap; ++z) {
@@ -1527,8 +1521,8 @@ __global__ void k_init_dt(Dev d, int n_inst) {
     return;
   }
   const int cur = I.parity;
-  const double* lr = d.rho[cur] + I.lat_off;
-  const double* lm = d.m[cur] + I.lat_off;
+  const double* lr = d.R(cur) + I.lat_off;
+  const double* lm = d.M(cur) + I.lat_off;
   const unsigned char* lph = d.phase + I.lat_off;
   const int* own = d.own + I.lat_off;
   double s = 0.0;

@@ -101,21 +101,18 @@ __device__ inline double pressure_fma(const Phase& e, double rho) {
 __device__ inline void hll_pre(double a, double rl, double ml, double ul, double fl1, double rr, double mr, double ur,
                                double fr1, double& F0, double& F1) {
   const bool lt = lt_bits(ul, ur);
-  double umin = lt ? ul : ur;
-  double umax = lt ? ur : ul;
-  double SL = umin - a, SR = umax + a;
-  if (ge0_bits(SL)) {
-    F0 = ml;
-    F1 = fl1;
-  } else if (le0_bits(SR)) {
-    F0 = mr;
-    F1 = fr1;
-  } else {
-    double inv = rcp_nr(SR - SL);
-    double slsr = SL * SR;
-    F0 = __fma_rn(-SL, mr, __fma_rn(slsr, rr - rl, SR * ml)) * inv;
-    F1 = __fma_rn(-SL, fr1, __fma_rn(slsr, mr - ml, SR * fl1)) * inv;
-  }
+  const double umin = lt ? ul : ur;
+  const double umax = lt ? ur : ul;
+  const double SL = umin - a, SR = umax + a;
+  // branch-free: the HLL average is formed for every face (S_R - S_L >= 2a > 0) and the upwind cases
+  // select the one-sided physical flux, the same values the three-way branch gives
+  const double inv = rcp_nr(SR - SL);
+  const double slsr = SL * SR;
+  const double H0 = __fma_rn(-SL, mr, __fma_rn(slsr, rr - rl, SR * ml)) * inv;
+  const double H1 = __fma_rn(-SL, fr1, __fma_rn(slsr, mr - ml, SR * fl1)) * inv;
+  const bool up_l = ge0_bits(SL), up_r = le0_bits(SR);
+  F0 = up_l ? ml : (up_r ? mr : H0);
+  F1 = up_l ? fl1 : (up_r ? fr1 : H1);
 }
 __device__ inline void phys_flux_fast(const Phase& e, double r, double m, double& F0, double& F1) {
   double u = div_nr(m, r);
