@@ -230,7 +230,9 @@ def test_adjoint_through_phase_creation_dJ_dV(kind):
     """Phase creation (App. B): liquid pulled apart at +-V creates a vapour cell (cavitation), vapour driven
     together at +-V nucleates a liquid cell (nucleation). dJ/dV of the mean final pressure (V enters the
     initial momentum, m0 = rho0 (-+V)) from the adjoint against the oracle's tangent in the V direction and
-    against central differences of the CUDA forward run (step 1e-6 relative)."""
+    against central differences of the CUDA forward run. Step 1e-6 relative for cavitation; 1e-4 for
+    nucleation, whose created liquid cell carries its solves' stop-test noise into J amplified by a_L^2
+    (central differences of the oracle's J reach the tangent to 5e-8 at 1e-4 and only to 1e-5 at 1e-6)."""
     from paper_2211_00705_gb300.imexds import Imexds
     if kind == "cavitation":
         b = I.cavitation_batch(4, 4, n_range=(64, 128), n_steps=60)
@@ -265,13 +267,14 @@ def test_adjoint_through_phase_creation_dJ_dV(kind):
                      + np.dot(gwo[off[i]:off[i + 1]], d["widths"][0][off[i]:off[i + 1]]) for i in range(b.n_inst)])
     print("adjoint", adj, "tangent", tang)
     assert np.max(np.abs(adj - tang) / np.abs(tang)) <= TOL_TANGENT
+    eps = 1e-6 if kind == "cavitation" else 1e-4
     vals = []
     for sgn in (1.0, -1.0):
-        bb = dataclasses.replace(b, m=b.m + sgn * 1e-6 * np.repeat(V, np.diff(b.cell_offsets)) * dmdV)
+        bb = dataclasses.replace(b, m=b.m + sgn * eps * np.repeat(V, np.diff(b.cell_offsets)) * dmdV)
         c = Imexds.from_batch(bb)
         c.step(60)
         vals.append(_mean_pressure(c.get_states(), bb)[0])
         c.close()
-    fd = (vals[0] - vals[1]) / (2e-6 * V)
+    fd = (vals[0] - vals[1]) / (2 * eps * V)
     print("fd", fd)
     assert np.max(np.abs(adj - fd) / np.abs(adj)) <= 1e-5
