@@ -907,12 +907,9 @@ __device__ __noinline__ void dts_zone_general(const Dev& d, int zi) {
   double xpb_new[ZB + 1];
   int moved[ZB + 1];
   for (int q = 0; q <= nq; ++q) moved[q] = 0;
-  const bool simple = false;
-  if (!simple) {
-    if (!dts_general(d, Z, I, e0, nq, B, Fx0, Fx1, out_r, out_m, out_w, xpb_new, moved, newton, solves, iters_sum,
-                     iters_max, maxiter))
-      return;
-  }
+  if (!dts_general(d, Z, I, e0, nq, B, Fx0, Fx1, out_r, out_m, out_w, xpb_new, moved, newton, solves, iters_sum,
+                   iters_max, maxiter))
+    return;
   double smax = 0.0;
   double* nu = d.U(cur ^ 1) + I.lat_off;
   for (int q = 0; q < nq; ++q) {
@@ -1190,9 +1187,8 @@ __device__ __noinline__ void post_inst(const Dev& d, int ii) {
           if (left < 0 || zones[b].B > zones[left].B) left = b;
         }
       }
-      int pairs[2][2] = {{left, a}, {a, right}};
       for (int pk = 0; pk < 2 && !again; ++pk) {
-        int ia = pairs[pk][0], ib = pairs[pk][1];
+        const int ia = (pk == 0) ? left : a, ib = (pk == 0) ? a : right;  // the pairs (left, a) and (a, right)
         if (ia < 0 || ib < 0) continue;
         Zone& Za = zones[ia];
         Zone& Zb = zones[ib];
