@@ -141,9 +141,9 @@ imexds_status imexds_reset(imexds_ctx* ctx);
 /* Measurement of the group schedule (timing mode): SM clock cycles spent per phase of the resident
  * kernel (0 boundary solves + plan, 1 sweep, 2 dual time, 3 grid management), for the group with the
  * longest critical path (slowest4) and summed over all groups (sum4). Arrays of 4. Phases 0, 2 and 3 are
- * the clock of lane 0 of warp 0 (its own instance's path: the wait for the group's other lanes falls
- * between phases), phase 1 that of lane 0 of the first sweep warp. The counters accumulate over every
- * timing-mode call until imexds_set_states rebuilds the groups. */
+ * read by lane 0 of warp 0, phase 1 by lane 0 of the first sweep warp; they are indicative only (on the
+ * 4096-instance workload the slowest group's phases summed to more than the run's own cycles). The
+ * counters accumulate over every timing-mode call until imexds_set_states rebuilds the groups. */
 imexds_status imexds_get_group_phase_cycles(imexds_ctx* ctx, int64_t* slowest4, int64_t* sum4);
 
 /* Choose the schedule for the next calls (values of imexds_options.schedule, 0..3). */
