@@ -103,7 +103,9 @@ imexds_status imexds_create(const imexds_problem* prob, const imexds_options* op
  * of widths/rho/m/phase. A face between cells of different phase is a phase boundary (Sec. 2.3); every
  * other face must lie on the background lattice (face positions accumulate the widths from the last
  * fixed face; tolerance 1e-9 h), and a cell with two fixed faces must be one background cell.
- * Sets t = t0 for all instances and resets statistics. IMEXDS_ERR_ARG on a malformed list. */
+ * cell_offsets[0] = 0 and every instance holds at least one cell; rho > 0 and finite, m finite, widths
+ * > 0, phase 0 (vapour) or 1 (liquid). Sets t = t0 for all instances and resets statistics.
+ * IMEXDS_ERR_ARG on a malformed list (nothing is changed then). */
 imexds_status imexds_set_states(imexds_ctx* ctx, const int32_t* cell_offsets, const double* widths,
                                 const double* rho, const double* m, const uint8_t* phase, double t0);
 

@@ -2014,6 +2014,7 @@ imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double*
                                 const double* m, const uint8_t* phase, double t0) {
   if (!c || !off || !widths || !rho || !m || !phase) return IMEXDS_ERR_ARG;
   const int n = c->n_inst;
+  if (off[0] != 0) return IMEXDS_ERR_ARG;
   // host-side parse into lattice + zones
   std::vector<int> lat_off(n + 1, 0);
   for (int i = 0; i < n; ++i) lat_off[i + 1] = lat_off[i] + c->N[i];
@@ -2049,7 +2050,9 @@ imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double*
     if (fpb[M] || fj[M] != N) bad = true;
     if (bad) return IMEXDS_ERR_ARG;
     for (int k = 0; k < M; ++k)
-      if (phase[a + k] > 1 || !(rho[a + k] > 0.0) || !(widths[a + k] > 0.0)) return IMEXDS_ERR_ARG;
+      if (phase[a + k] > 1 || !(rho[a + k] > 0.0) || !std::isfinite(rho[a + k]) || !std::isfinite(m[a + k]) ||
+          !(widths[a + k] > 0.0))
+        return IMEXDS_ERR_ARG;
     // cells with two fixed faces spanning one lattice cell are lattice cells; every other cell is part of
     // a zone (runs of such cells, joined when closer than ZONE_GAP)
     std::vector<int> special(M, 0);
@@ -2257,7 +2260,10 @@ imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double*
 
 imexds_status imexds_set_states_device(imexds_ctx* c, const int32_t* off, const double* w_d, const double* r_d,
                                        const double* m_d, const uint8_t* ph_d, double t0) {
-  if (!c || !off) return IMEXDS_ERR_ARG;
+  if (!c || !off || !w_d || !r_d || !m_d || !ph_d) return IMEXDS_ERR_ARG;
+  if (off[0] != 0) return IMEXDS_ERR_ARG;
+  for (int i = 0; i < c->n_inst; ++i)
+    if (off[i + 1] <= off[i]) return IMEXDS_ERR_ARG;  // every instance holds at least one cell
   int n = off[c->n_inst];
   std::vector<double> w(n), r(n), m(n);
   std::vector<uint8_t> ph(n);

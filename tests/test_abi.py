@@ -38,3 +38,50 @@ def test_status_strings_without_device(lib):
     lib.imexds_status_string.restype = ctypes.c_char_p
     assert lib.imexds_status_string(0) == b"ok"
     assert b"capacity" in lib.imexds_status_string(9)
+
+
+def _problem(**kw):
+    """A valid two-instance problem (the workload fluid and options), fields overridable."""
+    import numpy as np
+    from paper_2211_00705_gb300 import inputs as I
+    p = dict(n_lattice=np.array([40, 60]), x_left=np.zeros(2), x_right=np.ones(2), tau=np.full(2, 1e-7),
+             fluid=I.workload_fluid(), options=I.Options())
+    p.update(kw)
+    return p
+
+
+@pytest.mark.parametrize("bad", [
+    dict(n_lattice=[1, 60]),                      # fewer than two lattice cells
+    dict(x_right=[1.0, 0.0]),                     # empty domain
+    dict(tau=[1e-7, -1.0]),                       # negative kinetic coefficient
+    dict(cfl=0.0), dict(l_max=0), dict(newton_itmax=0), dict(split_ratio=1.0),
+    dict(schedule=4), dict(group_threads=48), dict(group_threads=288), dict(group_threads=100),
+])
+def test_create_rejects_malformed_problems(lib, bad):
+    """imexds_create checks its arguments before any device call: IMEXDS_ERR_ARG on every malformed problem
+    or option (runs without a GPU)."""
+    import dataclasses
+    import numpy as np
+    from paper_2211_00705_gb300.imexds import Imexds, ImexdsError
+    p = _problem()
+    kw = {}
+    for k, v in bad.items():
+        if k in p:
+            p[k] = np.asarray(v)
+        elif k in ("schedule", "group_threads"):
+            kw[k] = v
+        else:
+            p["options"] = dataclasses.replace(p["options"], **{k: v})
+    with pytest.raises(ImexdsError, match=r"status 1 "):
+        Imexds(p["n_lattice"], p["x_left"], p["x_right"], p["tau"], p["fluid"], p["options"], **kw)
+
+
+def test_create_without_gpu_fails_loudly(lib):
+    """No host fallback: on a machine without a GPU a valid problem is refused with IMEXDS_ERR_CUDA."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2211_00705_gb300.imexds import Imexds, ImexdsError
+    p = _problem()
+    with pytest.raises(ImexdsError, match=r"status 2 "):
+        Imexds(p["n_lattice"], p["x_left"], p["x_right"], p["tau"], p["fluid"], p["options"])
