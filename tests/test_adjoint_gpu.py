@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 # tangent itself moves by up to 1.3e-7 (relative) when the dual-time tolerances go from 1e-4 to 1e-6
 # times the scaled ones (measured on this batch), so the bar is 1e-6
 TOL_TANGENT = 1e-6
-TOL_FD = 1e-5        # adjoint vs central differences (the spec bar)
+TOL_FD = 1e-5        # adjoint vs central differences (the target relative error)
 
 
 def _forward(batch, program, k=16, **kw):
