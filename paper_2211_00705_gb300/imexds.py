@@ -264,9 +264,13 @@ class Imexds:
         """Gradient of a loss of the final states of the last forward run (see include/imexds.h).
         Inputs follow get_states' cell order; outputs the initial states' order (set_states)."""
         n0 = self._n_initial_cells()
-        r = np.ascontiguousarray(dJ_drho_T, dtype=np.float64)
-        m = np.ascontiguousarray(dJ_dm_T, dtype=np.float64)
-        w = None if dJ_dw_T is None else np.ascontiguousarray(dJ_dw_T, dtype=np.float64)
+        r = np.ascontiguousarray(dJ_drho_T, dtype=np.float64).ravel()
+        m = np.ascontiguousarray(dJ_dm_T, dtype=np.float64).ravel()
+        w = None if dJ_dw_T is None else np.ascontiguousarray(dJ_dw_T, dtype=np.float64).ravel()
+        nT = int(self.cell_counts().sum())   # the library reads one entry per final cell
+        for name, a in (("dJ_drho_T", r), ("dJ_dm_T", m), ("dJ_dw_T", w)):
+            if a is not None and a.shape[0] != nT:
+                raise ValueError(f"{name} has {a.shape[0]} entries, the final cell lists {nT}")
         g = {"rho": np.zeros(n0), "m": np.zeros(n0), "widths": np.zeros(n0), "tau": np.zeros(self.n_inst),
              "status": np.zeros(self.n_inst, dtype=np.int32)}
         null = C.cast(None, C.POINTER(C.c_double))

@@ -51,3 +51,21 @@ def test_set_states_rejects_malformed_lists_and_keeps_the_loaded_states():
     ref.close()
     for k in ("offsets", "widths", "rho", "m", "phase", "t", "status"):
         np.testing.assert_array_equal(s[k], r[k], err_msg=k)
+
+
+def test_adjoint_checks_the_seed_lengths():
+    """The binding refuses seeds whose length differs from the final cell lists (the library would read
+    one entry per final cell)."""
+    from paper_2211_00705_gb300.imexds import Imexds
+    b = I.adjoint_batch(n_inst=2, n_lattice=60, n_steps=10)
+    ctx = Imexds.from_batch(b)
+    ctx.set_adjoint_checkpoint(4)
+    ctx.step(10)
+    n = int(ctx.cell_counts().sum())
+    with pytest.raises(ValueError, match="dJ_drho_T"):
+        ctx.adjoint(np.zeros(n - 1), np.zeros(n))
+    with pytest.raises(ValueError, match="dJ_dw_T"):
+        ctx.adjoint(np.zeros(n), np.zeros(n), np.zeros(n + 1))
+    g = ctx.adjoint(np.ones(n), np.zeros(n))
+    ctx.close()
+    assert (g["status"] == 0).all()
