@@ -194,6 +194,7 @@ class Imexds:
         r = np.ascontiguousarray(rho, dtype=np.float64)
         mm = np.ascontiguousarray(m, dtype=np.float64)
         ph = np.ascontiguousarray(phase, dtype=np.uint8)
+        self._check_lists(off, [("widths", w), ("rho", r), ("m", mm), ("phase", ph)])
         _check(load().imexds_set_states(self.h, _ip(off), _dp(w), _dp(r), _dp(mm),
                                         ph.ctypes.data_as(C.POINTER(C.c_uint8)), t0))
         self._n0 = int(off[-1])
@@ -201,10 +202,20 @@ class Imexds:
     def set_states_device(self, offsets, widths_d, rho_d, m_d, phase_d, t0: float = 0.0):
         """Device-pointer variant: widths_d/rho_d/m_d (float64) and phase_d (uint8) are CUDA tensors."""
         off = np.ascontiguousarray(offsets, dtype=np.int32)
+        self._check_lists(off, [("widths_d", widths_d), ("rho_d", rho_d), ("m_d", m_d), ("phase_d", phase_d)])
         _check(load().imexds_set_states_device(self.h, _ip(off), C.c_void_p(widths_d.data_ptr()),
                                                C.c_void_p(rho_d.data_ptr()), C.c_void_p(m_d.data_ptr()),
                                                C.c_void_p(phase_d.data_ptr()), t0))
         self._n0 = int(off[-1])
+
+    def _check_lists(self, off, arrays):
+        """The library reads offsets[n_inst] entries of every cell array: refuse shorter (or longer) ones."""
+        if off.ndim != 1 or off.shape[0] != self.n_inst + 1:
+            raise ValueError(f"offsets has {off.shape[0]} entries, expected n_inst + 1 = {self.n_inst + 1}")
+        n = int(off[-1])
+        for name, a in arrays:
+            if a.shape[0] != n:
+                raise ValueError(f"{name} has {a.shape[0]} entries, offsets[-1] is {n}")
 
     def step(self, n_steps: int):
         _check(load().imexds_step(self.h, int(n_steps)))

@@ -85,3 +85,19 @@ def test_create_without_gpu_fails_loudly(lib):
     p = _problem()
     with pytest.raises(ImexdsError, match=r"status 2 "):
         Imexds(p["n_lattice"], p["x_left"], p["x_right"], p["tau"], p["fluid"], p["options"])
+
+
+def test_binding_refuses_cell_lists_shorter_than_the_offsets():
+    """The library reads offsets[n_inst] entries of every cell array: the binding checks the lengths first
+    (host-side logic, no context needed)."""
+    import numpy as np
+    from paper_2211_00705_gb300.imexds import Imexds
+    ctx = object.__new__(Imexds)
+    ctx.n_inst = 2
+    off = np.array([0, 3, 7], dtype=np.int32)
+    ok = np.zeros(7)
+    ctx._check_lists(off, [("widths", ok), ("rho", ok)])
+    with pytest.raises(ValueError, match="rho has 6 entries"):
+        ctx._check_lists(off, [("widths", ok), ("rho", ok[:6])])
+    with pytest.raises(ValueError, match="offsets has 2 entries"):
+        ctx._check_lists(off[:2], [("widths", ok[:3])])

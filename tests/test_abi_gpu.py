@@ -10,7 +10,9 @@ pytestmark = pytest.mark.gpu
 
 def _malformed(b):
     """(name, overrides of the valid cell lists of batch b) for each kind of malformed list."""
-    cases = [("first offset not 0", dict(offsets=b.cell_offsets + 1))]
+    pad = lambda x: np.concatenate([x[:1], x])   # one leading cell that the shifted offsets skip
+    cases = [("first offset not 0", dict(offsets=b.cell_offsets + 1, widths=pad(b.widths), rho=pad(b.rho),
+                                         m=pad(b.m), phase=pad(b.phase)))]
     m = b.m.copy()
     m[3] = np.nan
     cases.append(("NaN momentum", dict(m=m)))
@@ -41,6 +43,9 @@ def test_set_states_rejects_malformed_lists_and_keeps_the_loaded_states():
         a.update(over)
         with pytest.raises(ImexdsError, match=r"status 1 "):
             ctx.set_states(a["offsets"], a["widths"], a["rho"], a["m"], a["phase"])
+    # lists whose lengths disagree with the offsets are refused by the binding before the library reads them
+    with pytest.raises(ValueError, match="rho"):
+        ctx.set_states(b.cell_offsets, b.widths, b.rho[:-1], b.m, b.phase)
     # the context still holds the valid lists loaded first: 5 steps equal those of a fresh context
     ctx.step(5)
     s = ctx.get_states()
