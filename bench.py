@@ -29,15 +29,10 @@ if ROOT not in sys.path:
 
 METRIC = "batched FP64 cell-steps/s (fwd, adjoint) vs plain GPU step at ≤1e-9 rel err; %HBM"
 UNIT = "cell-steps/s"
-# algorithmic FP64 operations (an add, a multiply or a fused multiply-add counts as one) of one explicit
-# cell-step: per cell u, p, momentum flux, |u|+a and the max (7); per face S_L, S_R (4), S_R - S_L,
-# S_L S_R, two flux components with the division (2 x 7); update (6)
-SWEEP_OPS_PER_CELL = 33
-# peak FP64 operation rate of the GB300, in the same unit: 304 FP64 lane-instructions per cycle over the 152
-# SMs (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained) at the 2070 MHz maximum SM
-# clock = 0.629e12 op/s, the nominal 1.25 TFLOP/s with an FMA counted as two flops (MEASURED_PEAKS.json has
-# no FP64 entry)
-FP64_PEAK_TOPS = 304 * 2.07e9 / 1e12
+# algorithmic FP64 operations of one explicit cell-step: per cell u, p, momentum flux, |u|+a and the max (7);
+# per face S_L, S_R (4), S_R - S_L, S_L S_R, two flux components with the division (2 x 7); update (6)
+SWEEP_FLOP_PER_CELL = 33
+FP64_PEAK_TFLOPS = 1.25   # GB300 dense FP64 (nominal; no FP64 figure in MEASURED_PEAKS.json)
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_sweep launch on this workload from an ncu capture of
 # the per-step schedule; None until the current k_sweep (31-cell tiles) has been captured
 SWEEP_TRAFFIC_BYTES = None
@@ -526,20 +521,18 @@ def main():
            "d2h_bytes_per_step": d2h}
 
     # roofline of the dominant kernel
-    # roofline of the explicit sweep (FP64 ALU bound): algorithmic FP64 operations of the cells it updated,
-    # over its measured time in the per-step schedule
+    # roofline of the explicit sweep (FP64 ALU bound): algorithmic flops of the cells it updated, over its
+    # measured time in the per-step schedule
     sweep_cells = float(np.sum(st["steps"] * batch.n_lattice))   # lattice cells swept per run (upper bound)
     n_sw = max(kt_steps["k_sweep"][1], 1)
-    ops = SWEEP_OPS_PER_CELL * sweep_cells / n_sw
+    flops = SWEEP_FLOP_PER_CELL * sweep_cells / n_sw
     per_launch_s = kt_steps["k_sweep"][0] / 1e3 / n_sw
-    achieved = ops / per_launch_s / 1e12 if per_launch_s > 0 else None
-    roof = {"bound": "alu", "kernel": "k_sweep", "achieved": achieved, "peak": FP64_PEAK_TOPS,
-            "unit": "T FP64 op/s", "frac": (achieved / FP64_PEAK_TOPS) if achieved else None,
+    achieved = flops / per_launch_s / 1e12 if per_launch_s > 0 else None
+    roof = {"bound": "alu", "kernel": "k_sweep", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
             "traffic": SWEEP_TRAFFIC_BYTES if args.scale == 1.0 else None,
             "algorithmic_bytes": 32.0 * sweep_cells / n_sw,
-            "peak_source": "GB300 FP64 unit rate: 304 lane-instructions per cycle (ncu peak_sustained) x 2070 MHz "
-                           "= 0.629e12 op/s = nominal 1.25 TFLOP/s with FMA as 2 flops (no FP64 entry in "
-                           "MEASURED_PEAKS.json)",
+            "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table; no FP64 entry in MEASURED_PEAKS.json)",
             "timed_schedule_kernel": dominant,
             "per_step_schedule_share": {k: round(v[0] / tot, 4) if tot else None for k, v in kt_steps.items()},
             "per_step_schedule_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in kt_steps.items()},
