@@ -29,8 +29,9 @@ if ROOT not in sys.path:
 
 METRIC = "batched FP64 cell-steps/s (fwd, adjoint) vs plain GPU step at ≤1e-9 rel err; %HBM"
 UNIT = "cell-steps/s"
-# algorithmic FP64 operations of one explicit cell-step: per cell u, p, momentum flux, |u|+a and the max (7);
-# per face S_L, S_R (4), S_R - S_L, S_L S_R, two flux components with the division (2 x 7); update (6)
+# algorithmic FP64 flops of one explicit cell-step (a multiply and an add count separately, a division as
+# one): per cell u, p, momentum flux, |u|+a and the max (7); per face S_L, S_R (4), S_R - S_L, S_L S_R, two
+# flux components with the division (2 x 7); update (6)
 SWEEP_FLOP_PER_CELL = 33
 FP64_PEAK_TFLOPS = 1.25   # GB300 dense FP64 (nominal; no FP64 figure in MEASURED_PEAKS.json)
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_sweep launch on this workload from an ncu capture of
