@@ -9,7 +9,9 @@
  * the creation solver against the paper's printed star states, the saturation table, closed forms and
  * special cases; the scheme against conservation, preserved equilibria, the exact Riemann solution and a
  * fully explicit run; the tangent mode against central differences. The HLL wave-speed estimate (Davis)
- * is a reading — the paper names HLL only — pinned by consistency and upwind limits, not by printed values.
+ * is a reading — the paper names HLL only — pinned by consistency, upwind limits and Toro's integral
+ * consistency (the HLL state equals the average of the exact two-rarefaction solution over the fan),
+ * not by printed values.
  *
  * Conventions (shared in meaning, not in code, with the product C-ABI):
  *   phase 0 = vapour, phase 1 = liquid.

@@ -14,7 +14,8 @@ import pytest
 from oracle import pyoracle as P
 from paper_2211_00705_gb300 import inputs as I
 
-GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+with open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")) as _f:
+    GOLD = json.load(_f)
 
 
 def _liquid_rho(fl, p):
@@ -227,6 +228,57 @@ def test_hll_consistency_and_upwind_limits():
     np.testing.assert_allclose(F, [r1 * u1, r1 * u1 * u1 + fl.a2_vap * r1], rtol=1e-15)
     F = P.hll(fl, 0, r1, -r1 * u1, r2, -r2 * u2)
     np.testing.assert_allclose(F, [-r2 * u2, r2 * u2 * u2 + fl.a2_vap * r2], rtol=1e-15)
+
+
+def test_hll_state_is_the_fan_average_of_the_exact_two_rarefaction_solution():
+    """Integral consistency of HLL (Toro): when S_L, S_R bound every wave, the HLL intermediate state
+    U* = U_L + (F_HLL - F_L)/S_L is the exact average of the Riemann solution over [S_L t, S_R t]. For two
+    rarefactions in one phase (dp/drho = a^2 constant in both EOS of Sec. 2) the fan heads move at exactly
+    u_l - a and u_r + a, the Davis estimates of reading R6. The exact solution (Riemann invariants
+    u +- a ln rho; star state rho* = sqrt(rho_l rho_r) exp((u_l - u_r)/2a)) is integrated piecewise by
+    quadrature and compared with U* from the oracle's flux, from both sides."""
+    from scipy.integrate import quad
+    fl = I.workload_fluid()
+    rng = np.random.default_rng(5)
+    for ph, a2 in ((0, fl.a2_vap), (1, fl.a2_liq)):
+        a = math.sqrt(a2)
+        p = (lambda r: a2 * r) if ph == 0 else (lambda r: fl.p_sat + a2 * (r - fl.rho0_liq))
+        for _ in range(6):
+            rl = rng.uniform(0.5, 1.0) if ph == 0 else rng.uniform(950, 1000)
+            rr = rl * math.exp(rng.uniform(-0.01, 0.01))
+            ul = rng.uniform(-40, 40)
+            ur = ul + a * (abs(math.log(rl / rr)) + rng.uniform(0.01, 0.05))   # both waves rarefactions
+            rs = math.sqrt(rl * rr) * math.exp((ul - ur) / (2 * a))
+            us = ul + a * math.log(rl / rs)
+            assert rs < min(rl, rr)
+
+            def U(xi):
+                if xi < ul - a:
+                    return rl, rl * ul
+                if xi < us - a:
+                    u = xi + a
+                    r = rl * math.exp((ul - u) / a)
+                    return r, r * u
+                if xi < us + a:
+                    return rs, rs * us
+                if xi < ur + a:
+                    u = xi - a
+                    r = rr * math.exp((u - ur) / a)
+                    return r, r * u
+                return rr, rr * ur
+
+            SL, SR = ul - a, ur + a
+            pts = [SL, us - a, us + a, SR]
+            avg = [sum(quad(lambda x, k=k: U(x)[k], pts[i], pts[i + 1], epsabs=0, epsrel=2e-14, limit=200)[0]
+                       for i in range(3)) / (SR - SL) for k in (0, 1)]
+            F = np.array(P.hll(fl, ph, rl, rl * ul, rr, rr * ur))
+            FL = np.array([rl * ul, rl * ul * ul + p(rl)])
+            FR = np.array([rr * ur, rr * ur * ur + p(rr)])
+            from_left = np.array([rl, rl * ul]) + (F - FL) / SL
+            from_right = np.array([rr, rr * ur]) + (F - FR) / SR
+            scale = np.array([rl, rl * a])
+            np.testing.assert_allclose(from_left / scale, np.array(avg) / scale, rtol=0, atol=1e-11)
+            np.testing.assert_allclose(from_right / scale, np.array(avg) / scale, rtol=0, atol=1e-11)
 
 
 def test_nopt_star_pressure_by_brute_force():
