@@ -269,7 +269,7 @@ def test_hll_state_is_the_fan_average_of_the_exact_two_rarefaction_solution():
 
             SL, SR = ul - a, ur + a
             pts = [SL, us - a, us + a, SR]
-            avg = [sum(quad(lambda x, k=k: U(x)[k], pts[i], pts[i + 1], epsabs=0, epsrel=2e-14, limit=200)[0]
+            avg = [sum(quad(lambda x, k=k: U(x)[k], pts[i], pts[i + 1], epsabs=0, epsrel=1e-12, limit=200)[0]
                        for i in range(3)) / (SR - SL) for k in (0, 1)]
             F = np.array(P.hll(fl, ph, rl, rl * ul, rr, rr * ur))
             FL = np.array([rl * ul, rl * ul * ul + p(rl)])
