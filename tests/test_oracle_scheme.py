@@ -226,3 +226,30 @@ def test_nucleation_creates_one_persistent_droplet_and_conserves_mass():
         r_end, m_end = b.rho[b.cell_offsets[i]], b.m[b.cell_offsets[i]]   # u = +V left: mass enters; right: u = -V
         inflow = 2.0 * abs(m_end) * s["t"][i]
         assert abs(m1 - (m0 + inflow)) <= 1e-10 * m0   # measured 4e-12 (round-off of 100 steps)
+
+
+def test_split_of_a_cell_between_two_boundaries_cuts_at_the_nearest_lattice_face():
+    """Reading of the split rule (Sec. 3.4, "in two parts"; reading R15): a cell between two phase
+    boundaries wider than split_ratio * h is cut at the lattice face nearest its midpoint, so every fixed
+    face stays on the background lattice. A saturation equilibrium at rest keeps both boundaries in place
+    (z = 0, w = 0): the vapour cell on [7.1h, 9.5h] (2.4h, midpoint 8.3h) must become [7.1h, 8h] and
+    [8h, 9.5h] after one step, with every state unchanged."""
+    N = 20
+    h = 1.0 / N
+    fl = I.workload_fluid()
+    rv = fl.p_sat / fl.a2_vap
+    widths = np.array([h] * 7 + [0.1 * h, 2.4 * h, 0.5 * h] + [h] * 10)
+    phase = np.array([1] * 8 + [0] + [1] * 11, dtype=np.uint8)
+    rho = np.where(phase == 1, fl.rho0_liq, rv)
+    b = I.Batch(n_lattice=np.array([N], np.int32), x_left=np.zeros(1), x_right=np.ones(1),
+                tau=np.array([I.tau_paper()]), cell_offsets=np.array([0, len(widths)], np.int32), widths=widths,
+                rho=rho, m=np.zeros_like(rho), phase=phase, fluid=fl, options=I.Options(), t_end=0.0,
+                n_steps=1, name="vapour cell between two boundaries")
+    o, s = run(b)
+    assert s["status"][0] == 0 and o.stats()["splits"][0] == 1
+    vap = np.nonzero(s["phase"] == 0)[0]
+    assert len(vap) == 2
+    x = np.concatenate([[0.0], np.cumsum(s["widths"])])
+    np.testing.assert_allclose(x[vap[0]:vap[1] + 2] / h, [7.1, 8.0, 9.5], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(s["rho"][vap], rv, rtol=1e-12)
+    np.testing.assert_allclose(s["rho"][s["phase"] == 1], fl.rho0_liq, rtol=1e-12)
