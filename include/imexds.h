@@ -109,19 +109,29 @@ imexds_status imexds_create(const imexds_problem* prob, const imexds_options* op
 imexds_status imexds_set_states(imexds_ctx* ctx, const int32_t* cell_offsets, const double* widths,
                                 const double* rho, const double* m, const uint8_t* phase, double t0);
 
-/* Number of cells of every instance now (host array of n_inst entries). */
+/* Number of cells of every instance now (host array of n_inst entries). IMEXDS_ERR_STATE before
+ * imexds_set_states. */
 imexds_status imexds_cell_counts(imexds_ctx* ctx, int32_t* counts);
 
 /* Copy the cell lists back (host arrays sized from imexds_cell_counts; cell_offsets has n_inst+1
- * entries). t and inst_status have n_inst entries; inst_status holds an imexds_status per instance. */
+ * entries). t and inst_status have n_inst entries; inst_status holds an imexds_status per instance: an
+ * instance that met an error (IMEXDS_ERR_NONPHYSICAL, _PB_NOCONV, _VANISH, _CAPACITY) stopped in the
+ * step where it occurred; its states are then not meaningful. IMEXDS_ERR_STATE before
+ * imexds_set_states. */
 imexds_status imexds_get_states(imexds_ctx* ctx, int32_t* cell_offsets, double* widths, double* rho,
                                 double* m, uint8_t* phase, double* t, int32_t* inst_status);
 
-/* Advance every instance by n_steps time steps (no clipping to an end time). */
+/* Advance every instance by n_steps time steps of Algorithm 1 (each with the CFL time step of
+ * Eq. cfl_cond:unif over the instance's cells, Algorithm 2 on every implicit neighbourhood, grid
+ * management and, with options.creation, phase creation of App. B), without clipping to an end time.
+ * Instances that met an error stop and report it through imexds_get_states; the call itself returns
+ * IMEXDS_OK unless an argument, the call order (IMEXDS_ERR_STATE before imexds_set_states) or CUDA
+ * failed. */
 imexds_status imexds_step(imexds_ctx* ctx, int32_t n_steps);
 
-/* Advance every instance until t = t_end (the last step of each instance is shortened to land on
- * t_end). Finished instances idle. */
+/* Advance every instance until t = t_end: the steps of imexds_step, the last step of each instance
+ * shortened to land on t_end (its time step is min(C h / S_max, t_end - t)). Finished instances idle.
+ * IMEXDS_ERR_TIMEOUT if some instance has not arrived after 2e7 steps; errors otherwise as imexds_step. */
 imexds_status imexds_run_to(imexds_ctx* ctx, double t_end);
 
 /* Per-instance counters (n_inst x 10, int64, row-major): steps, dual-time iterations, max dual-time
@@ -129,9 +139,10 @@ imexds_status imexds_run_to(imexds_ctx* ctx, double t_end);
  * solves, kernel launches of the last call (same value in every row). */
 imexds_status imexds_get_stats(imexds_ctx* ctx, int64_t* stats);
 
-/* Device-resident variant of imexds_set_states / imexds_get_states for callers that keep the cell
- * lists in GPU memory: the same arguments as device pointers (cell_offsets stays a host array). The
- * copies run on the context's stream. */
+/* Device-resident variant of imexds_set_states for callers that keep the cell lists in GPU memory: the
+ * same arguments as device pointers (cell_offsets stays a host array, checked before any copy:
+ * cell_offsets[0] = 0 and at least one cell per instance, else IMEXDS_ERR_ARG). The copies run on the
+ * context's stream; the lists are then checked as by imexds_set_states. */
 imexds_status imexds_set_states_device(imexds_ctx* ctx, const int32_t* cell_offsets_host,
                                        const double* widths_d, const double* rho_d, const double* m_d,
                                        const uint8_t* phase_d, double t0);
@@ -233,6 +244,7 @@ imexds_status imexds_adjoint_info(imexds_ctx* ctx, double* kernel_ms, double* re
 imexds_status imexds_adjoint_replay(imexds_ctx* ctx, int32_t* cell_offsets, double* widths, double* rho,
                                     double* m, int32_t* stop_site);
 
+/* Free the context and its device memory (NULL is ignored). */
 void imexds_destroy(imexds_ctx* ctx);
 const char* imexds_status_string(imexds_status s);
 /* Text of the last CUDA error seen by any context of this process (thread-unsafe, static storage). */
