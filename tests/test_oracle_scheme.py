@@ -253,3 +253,34 @@ def test_split_of_a_cell_between_two_boundaries_cuts_at_the_nearest_lattice_face
     np.testing.assert_allclose(x[vap[0]:vap[1] + 2] / h, [7.1, 8.0, 9.5], rtol=0, atol=1e-9)
     np.testing.assert_allclose(s["rho"][vap], rv, rtol=1e-12)
     np.testing.assert_allclose(s["rho"][s["phase"] == 1], fl.rho0_liq, rtol=1e-12)
+
+
+def test_theta_study_isothermal_analogue():
+    """Isothermal analogue of the paper's study of the pseudo-time step (Sec. 4.1, Table of dual-time
+    iterations for theta_{k+-1} in {0.9, 0.1, alpha}, theta_k = alpha): liquid | vapour Riemann data run to
+    t_end = 2e-4 s at N = 100, 200, 400 and alpha = 1e-2, 1e-4, 1e-6 (default l_max = 1e4). The paper's
+    findings hold: theta_{k+-1} = 0.9 needs the fewest iterations per step, and fewer as N grows; 0.1 needs
+    several times more; theta_{k+-1} = alpha needs orders of magnitude more, beyond l_max for alpha <= 1e-4
+    (the paper's run at alpha = 1e-6 did not finish)."""
+    import dataclasses as dc
+    Ns, alphas = (100, 200, 400), (1e-2, 1e-4, 1e-6)
+    per = {}
+    for th in ("0.9", "0.1", "alpha"):
+        for alpha in alphas:
+            for N in Ns:
+                opts = dc.replace(I.scaled_options(), theta_nb=alpha if th == "alpha" else float(th))
+                b = riemann(N, alpha, 972.0, -6.0, 0.40, 4.0, 1e-2 * I.tau_paper(), opts=opts, t_end=2e-4)
+                o, s = run(b)
+                assert s["status"][0] == 0
+                st = o.stats()
+                per[th, alpha, N] = (st["dts_iters"][0] / st["steps"][0], st["maxiter"][0], st["steps"][0])
+    for alpha in alphas:
+        c = [per["0.9", alpha, N][0] for N in Ns]
+        assert c[0] > c[1] > c[2] and c[0] < 30
+        for N in Ns:
+            assert per["0.1", alpha, N][0] > 3 * per["0.9", alpha, N][0]
+    for N in Ns:
+        assert per["alpha", 1e-2, N][0] > 5 * per["0.1", 1e-2, N][0]
+        for alpha in (1e-4, 1e-6):
+            it, maxiter, steps = per["alpha", alpha, N]
+            assert maxiter == steps and it == 10000      # every step stopped by l_max
