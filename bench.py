@@ -390,7 +390,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--schedule", type=int, default=0, help="0 automatic, 1 per-step kernels, 2 instance groups")
+    ap.add_argument("--schedule", type=int, default=0, help="0 autotuned, 1 per-step kernels, 2 instance groups in lockstep, "
+                                                            "3 instance groups advancing independently")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="fraction of the 4096 instances (smaller cases for profiling only)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
