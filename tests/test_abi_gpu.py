@@ -74,3 +74,58 @@ def test_adjoint_checks_the_seed_lengths():
     g = ctx.adjoint(np.ones(n), np.zeros(n))
     ctx.close()
     assert (g["status"] == 0).all()
+
+
+def _collapsing_bubble(fl, N=40, V=100.0):
+    """Liquid converging at +-V onto a vapour cell of half a lattice cell between two boundaries: the cell
+    between the two boundaries would vanish (IMEXDS_ERR_VANISH in the oracle, at step 6)."""
+    h = 1.0 / N
+    widths = np.array([h] * 19 + [0.5 * h, 0.5 * h, h] + [h] * (N - 21))
+    phase = np.array([1] * 20 + [0] + [1] * (N - 20), np.uint8)
+    rho = np.where(phase == 1, 1000.0, fl.p_sat / fl.a2_vap)
+    x = np.cumsum(widths) - widths / 2
+    m = rho * np.where(x < 0.5, V, -V)
+    return I.Batch(n_lattice=np.array([N], np.int32), x_left=np.zeros(1), x_right=np.ones(1),
+                   tau=np.array([I.tau_paper()]), cell_offsets=np.array([0, len(widths)], np.int32), widths=widths,
+                   rho=rho, m=m, phase=phase, fluid=fl, options=I.scaled_options(), t_end=0.0, n_steps=40,
+                   name="collapsing bubble")
+
+
+def _concat(parts):
+    """One batch holding the instances of single-instance batches (same fluid and options)."""
+    off = np.zeros(len(parts) + 1, np.int32)
+    off[1:] = np.cumsum([p.cell_offsets[-1] for p in parts])
+    cat = lambda f: np.concatenate([getattr(p, f) for p in parts])
+    return I.Batch(n_lattice=cat("n_lattice"), x_left=cat("x_left"), x_right=cat("x_right"), tau=cat("tau"),
+                   cell_offsets=off, widths=cat("widths"), rho=cat("rho"), m=cat("m"), phase=cat("phase"),
+                   fluid=parts[0].fluid, options=parts[0].options, t_end=0.0, n_steps=parts[0].n_steps)
+
+
+def _with_a_failing_instance():
+    fl = I.workload_fluid(rho0_liq=1000.0)
+    r = I.riemann_batch(7, 2, n_range=(60, 90), alpha_range=(1e-3, 1e-2), fluid=fl, options=I.scaled_options(),
+                        t_end=0.0, n_steps=40)
+    return _concat([r.subset([0]), _collapsing_bubble(fl), r.subset([1])]), _concat([r.subset([0]), r.subset([1])])
+
+
+def test_an_instance_that_fails_stops_alone():
+    """Fault isolation on data: an instance driven into an error (a vanishing cell between two boundaries)
+    stops with its status, the call returns IMEXDS_OK, and the other instances of the batch end exactly as
+    in a batch without it."""
+    from paper_2211_00705_gb300.imexds import Imexds
+    b3, b2 = _with_a_failing_instance()
+    c3 = Imexds.from_batch(b3)
+    c3.step(40)
+    s3 = c3.get_states()
+    c3.close()
+    c2 = Imexds.from_batch(b2)
+    c2.step(40)
+    s2 = c2.get_states()
+    c2.close()
+    assert s3["status"][1] != 0 and s3["status"][0] == 0 and s3["status"][2] == 0
+    for k, j in ((0, 0), (2, 1)):
+        a = slice(s3["offsets"][k], s3["offsets"][k + 1])
+        b = slice(s2["offsets"][j], s2["offsets"][j + 1])
+        for f in ("widths", "rho", "m", "phase"):
+            np.testing.assert_array_equal(s3[f][a], s2[f][b], err_msg=f"instance {k}: {f}")
+        assert s3["t"][k] == s2["t"][j]
