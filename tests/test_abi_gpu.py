@@ -129,3 +129,24 @@ def test_an_instance_that_fails_stops_alone():
         for f in ("widths", "rho", "m", "phase"):
             np.testing.assert_array_equal(s3[f][a], s2[f][b], err_msg=f"instance {k}: {f}")
         assert s3["t"][k] == s2["t"][j]
+
+
+def test_forced_caps_report_through_status_and_counters():
+    """Caps forced by the options (no GPU fault): one Newton iteration cannot converge a boundary solve from
+    its cold start, so every instance stops with IMEXDS_ERR_PB_NOCONV while the call returns IMEXDS_OK; one
+    dual-time iteration per step ends every step on the cap, which is counted (maxiter) and is not an
+    error (reading R18). The oracle gives the same statuses and counters."""
+    import dataclasses
+    from paper_2211_00705_gb300.imexds import Imexds
+    b = I.riemann_batch(8, 3, n_range=(60, 90), alpha_range=(1e-3, 1e-2), options=I.scaled_options(), t_end=0.0,
+                        n_steps=10)
+    c = Imexds.from_batch(dataclasses.replace(b, options=dataclasses.replace(b.options, newton_itmax=1)))
+    c.step(10)
+    assert (c.get_states()["status"] == 4).all()
+    c.close()
+    c = Imexds.from_batch(dataclasses.replace(b, options=dataclasses.replace(b.options, l_max=1)))
+    c.step(10)
+    s, st = c.get_states(), c.stats()
+    c.close()
+    assert (s["status"] == 0).all() and (st["steps"] == 10).all()
+    assert (st["maxiter"] >= st["steps"]).all() and (st["dts_iters"] == st["steps"]).all()
