@@ -126,3 +126,41 @@ def test_tangent_through_phase_creation(kind):
         tg = d["rho"][0] * st["widths"] + st["rho"] * d["widths"][0]
         err = np.max(np.abs(fd - tg)[stiff] / np.abs(tg[stiff]))
         assert err <= 2e-5, ("created liquid mass", err)
+
+
+def test_tangent_through_the_split_of_a_cell_between_two_boundaries():
+    """Split of a cell between two phase boundaries (Sec. 3.4, cut at the lattice face nearest its midpoint):
+    a vapour cell of 2.4h between boundaries at 7.1h and 9.5h, perturbed states, split in the first step.
+    Derivatives of the final states after 3 steps in the directions rho of the vapour cell and m of a liquid
+    cell against central differences of the plain oracle (relative step 1e-4)."""
+    N = 20
+    h = 1.0 / N
+    fl = I.workload_fluid()
+    rv = fl.p_sat / fl.a2_vap
+    widths = np.array([h] * 7 + [0.1 * h, 2.4 * h, 0.5 * h] + [h] * 10)
+    phase = np.array([1] * 8 + [0] + [1] * 11, np.uint8)
+    rng = np.random.default_rng(4)
+    M = len(widths)
+    rho = np.where(phase == 1, fl.rho0_liq * (1 + 1e-4 * rng.uniform(-1, 1, M)), rv * (1 + 1e-2 * rng.uniform(-1, 1, M)))
+    m = rho * rng.uniform(-2, 2, M)
+    b = I.Batch(n_lattice=np.array([N], np.int32), x_left=np.zeros(1), x_right=np.ones(1),
+                tau=np.array([I.tau_paper()]), cell_offsets=np.array([0, M], np.int32), widths=widths, rho=rho, m=m,
+                phase=phase, fluid=fl, options=I.scaled_options(tol_nb=3e-13, tol_k=3e-11), t_end=0.0, n_steps=3,
+                name="vapour cell between two boundaries")
+    o = P.Oracle(b)
+    o.step(3)
+    assert o.states()["status"][0] == 0 and o.stats()["splits"][0] == 1
+    dr, dm = np.zeros(M), np.zeros(M)
+    dr[8] = rho[8]
+    dm[12] = rho[12]
+    st, d = P.Oracle(b).tangent([("step", 3)], seed_rho=np.stack([dr, np.zeros(M)]), seed_m=np.stack([np.zeros(M), dm]))
+    eps = 1e-4
+    for q, (er, em) in enumerate(((dr, 0 * dm), (0 * dr, dm))):
+        sp = _run(dataclasses.replace(b, rho=b.rho + eps * er, m=b.m + eps * em), 3)
+        sm = _run(dataclasses.replace(b, rho=b.rho - eps * er, m=b.m - eps * em), 3)
+        assert len(sp["rho"]) == len(st["rho"]) == len(sm["rho"])
+        for key in ("rho", "m", "widths"):
+            fd = (sp[key] - sm[key]) / (2 * eps)
+            tg = d[key][q]
+            err = np.max(np.abs(fd - tg)) / np.max(np.abs(tg))
+            assert err <= 2e-5, (q, key, err)
