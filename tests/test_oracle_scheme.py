@@ -284,3 +284,31 @@ def test_theta_study_isothermal_analogue():
         for alpha in (1e-4, 1e-6):
             it, maxiter, steps = per["alpha", alpha, N]
             assert maxiter == steps and it == 10000      # every step stopped by l_max
+
+
+def test_conservation_through_an_asymmetric_creation():
+    """Mass and momentum through phase creation (App. B) with asymmetric data (u = -12 m/s left, +30 m/s
+    right), where the created cell moves (u_C != 0): the mass fluxes of the two new boundaries differ by
+    rho_C (w_2 - w_1), which is exactly what the created cell holds, so sum h_i U_i changes only by the
+    end fluxes. The symmetric creation tests have u_C = 0 and do not see the created cell's momentum."""
+    N = 128
+    fl = I.workload_fluid(rho0_liq=1000.0)
+    h = 1.0 / N
+    rho = np.full(N, 1000.0)
+    m = rho * np.where(np.arange(N) < N // 2, -12.0, 30.0)
+    b = I.Batch(n_lattice=np.array([N], np.int32), x_left=np.zeros(1), x_right=np.ones(1),
+                tau=np.array([I.tau_paper()]), cell_offsets=np.array([0, N], np.int32), widths=np.full(N, h),
+                rho=rho, m=m, phase=np.ones(N, np.uint8), fluid=fl, options=I.scaled_options(creation=1),
+                t_end=0.0, n_steps=30, name="asymmetric cavitation")
+    o, s = run(b)
+    assert s["status"][0] == 0 and o.stats()["creations"][0] == 1
+    vap = s["phase"] == 0
+    assert vap.sum() == 1 and abs(s["m"][vap][0] / s["rho"][vap][0]) > 1.0     # the created cell moves
+    T = s["t"][0]
+    pl = pr = fl.p_sat                                       # rho = rho0: saturation pressure at both ends
+    dM = -T * (m[-1] - m[0])
+    dP = -T * ((m[-1] ** 2 / rho[-1] + pr) - (m[0] ** 2 / rho[0] + pl))
+    M0, P0 = totals(b.widths, b.rho, b.m)
+    M1, P1 = totals(s["widths"], s["rho"], s["m"])
+    assert abs(M1 - M0 - dM) <= 1e-13 * (abs(M0) + abs(dM))
+    assert abs(P1 - P0 - dP) <= 1e-13 * (abs(P0) + abs(T * pl))
