@@ -557,7 +557,8 @@ def main():
             plain["batched_over_plain"] = value / plain["value"]
             line["plain_single_instance"] = plain
         if not args.no_adjoint:
-            line["adjoint"] = measure_adjoint(dev, max(1, args.steps // 2), 1, scale=args.scale,
+            # at most two timed calls (~13 s each at full size): the adjoint is reported beside the headline
+            line["adjoint"] = measure_adjoint(dev, max(1, min(2, args.steps // 2)), 1, scale=args.scale,
                                               n_steps=args.adjoint_steps)
         if not args.no_hbm:
             line["large_domain_sweep"] = measure_large_domain_sweep()
