@@ -9,7 +9,7 @@ LIB = os.path.join(HERE, "liboracle.so")
 
 def build(force: bool = False) -> str:
     src = os.path.join(HERE, "oracle.cpp")
-    deps = [src] + [os.path.join(HERE, h) for h in ("oracle.h", "dual.h")]
+    deps = [src] + [os.path.join(HERE, h) for h in ("oracle.h", "dual.h", "counted.h")]
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in deps):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"

@@ -85,6 +85,16 @@ Dual<K> fabs(const Dual<K>& a) {
   return (a.v < 0.0) ? -a : a;
 }
 
+// true for the dual-number types (derivative-carrying), false for double and the counting type
+template <class T>
+struct is_dual {
+  static constexpr bool value = false;
+};
+template <int K>
+struct is_dual<Dual<K>> {
+  static constexpr bool value = true;
+};
+
 inline double val(double x) { return x; }
 
 // The value v with the derivatives of `same`, an expression equal to the one that gave v. Used where the

@@ -12,6 +12,7 @@
 // notes of the repository.
 #include "oracle.h"
 
+#include "counted.h"
 #include "dual.h"
 
 #include <algorithm>
@@ -159,7 +160,7 @@ T wave_f(const Phase& e, const T& pstar, const T& rhoK, T* dfdp) {
     T f = tsqrt(q);
     T dq = dv + (pstar - pK) * vs * vs / e.a2;  // d/dp* of (p* - p_K)(v_K - v*)
     *dfdp = (val(f) > 0.0) ? T(0.5 * dq / f) : T(vs / e.a);
-    if constexpr (!std::is_same_v<T, double>) {
+    if constexpr (orcdual::is_dual<T>::value) {
       // Tangent mode only. For the linear isothermal EOS (dp = a2 drho on either branch)
       // (p* - p_K)(v_K - v*) = (p* - p_K)^2 / (a2 rho_K rho*), so f = (p* - p_K) / (a sqrt(rho_K rho*)) and
       // df/dp* = (1 - (p* - p_K) v* / (2 a2)) / (a sqrt(rho_K rho*)). The derivative parts come from these
@@ -1392,6 +1393,63 @@ int orc_tangent(void* H, int n_dir, const double* seed_w, const double* seed_rho
     });
   }
   C->inst = final_state;
+  return ORC_OK;
+}
+
+// Operation count: every instance is re-run from its current states with the counting scalar (values
+// bit-identical to the plain run; the oracle's own states are left as they are). counts[0..6]: adds and
+// subtracts, multiplies, divides, square roots, logarithms, exponentials, cell-steps (cells at the start
+// of each step, summed).
+typedef orcdual::Counted CT;
+
+int orc_count_ops(void* H, int n_prog, const int* prog_kind, const double* prog_arg, long long* counts) {
+  Ctx* C = (Ctx*)H;
+  if (n_prog < 0 || !counts) return ORC_ERR_ARG;
+  orcdual::op_count = orcdual::OpCount();
+  long long cell_steps = 0;
+  for (const Inst<double>& S : C->inst) {
+    Inst<CT> I;
+    I.N = S.N;
+    I.xL = S.xL;
+    I.xR = S.xR;
+    I.h = S.h;
+    I.tau = S.tau;
+    I.t = S.t;
+    I.status = S.status;
+    I.ph = S.ph;
+    const int M = S.M();
+    I.w.resize(M);
+    I.r.resize(M);
+    I.m.resize(M);
+    I.f.resize(M + 1);
+    for (int i = 0; i < M; ++i) {
+      I.w[i] = S.w[i];
+      I.r[i] = S.r[i];
+      I.m[i] = S.m[i];
+    }
+    for (int i = 0; i <= M; ++i) I.f[i] = Face<CT>{S.f[i].pb, S.f[i].j, CT(S.f[i].x)};
+    for (int p = 0; p < n_prog; ++p) {
+      if (prog_kind[p] == 0) {
+        for (long s = 0; s < (long)prog_arg[p] && I.status == ORC_OK; ++s) {
+          cell_steps += I.M();
+          step_instance(C->F, C->o, I, -1.0);
+        }
+      } else {
+        while (I.status == ORC_OK && val(I.t) < prog_arg[p]) {
+          cell_steps += I.M();
+          step_instance(C->F, C->o, I, prog_arg[p]);
+        }
+      }
+    }
+  }
+  const orcdual::OpCount& q = orcdual::op_count;
+  counts[0] = q.add;
+  counts[1] = q.mul;
+  counts[2] = q.div;
+  counts[3] = q.sqrt;
+  counts[4] = q.log;
+  counts[5] = q.exp;
+  counts[6] = cell_steps;
   return ORC_OK;
 }
 

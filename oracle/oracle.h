@@ -13,6 +13,9 @@
  * consistency (the HLL state equals the average of the exact two-rarefaction solution over the fan),
  * not by printed values.
  *
+ * Modes: plain (double), tangent (forward-mode dual numbers, oracle/dual.h) and operation counting
+ * (oracle/counted.h); the scheme is one template on the scalar type, so all three run the same code.
+ *
  * Conventions (shared in meaning, not in code, with the product C-ABI):
  *   phase 0 = vapour, phase 1 = liquid.
  *   [[X]] = X_right - X_left at any discontinuity (Sec. 2.1).
@@ -116,6 +119,12 @@ int orc_tangent(void* H, int n_dir, const double* seed_w, const double* seed_rho
                 const double* seed_tau, int n_prog, const int* prog_kind, const double* prog_arg, int n_threads);
 /* Direction dir of the last orc_tangent: final-state derivatives, in orc_get_states order. */
 int orc_get_tangent(void* H, int dir, double* d_w, double* d_rho, double* d_m);
+
+/* Operation count of a program (kinds as in orc_tangent), run on copies of the instances with a
+ * counting scalar (oracle/counted.h): the instances keep their states. counts[7]: adds and subtracts,
+ * multiplies, divides, square roots, logarithms, exponentials, and cell-steps (cells at the start of
+ * every step, summed over steps and instances). */
+int orc_count_ops(void* H, int n_prog, const int* prog_kind, const double* prog_arg, long long* counts);
 
 #ifdef __cplusplus
 }

@@ -61,6 +61,8 @@ def lib():
         if hasattr(L, "orc_tangent"):
             L.orc_tangent.argtypes = [C.c_void_p, C.c_int, dp, dp, dp, dp, C.c_int, ip, dp, C.c_int]
             L.orc_get_tangent.argtypes = [C.c_void_p, C.c_int, dp, dp, dp]
+        if hasattr(L, "orc_count_ops"):
+            L.orc_count_ops.argtypes = [C.c_void_p, C.c_int, ip, dp, C.POINTER(C.c_longlong)]
         L.orc_exact_sample.argtypes = [C.POINTER(OFluid), C.POINTER(OOpts), C.c_double, C.c_int, C.c_double,
                                        C.c_double, C.c_int, C.c_double, C.c_double, C.c_int, dp, dp, dp, ip]
         _lib = L
@@ -199,6 +201,18 @@ class Oracle:
         lib().orc_get_stats(self.h, s.ctypes.data_as(C.POINTER(C.c_longlong)))
         keys = ["steps", "dts_iters", "dts_max", "newton", "merges", "splits", "creations", "maxiter", "pb_solves"]
         return {k: s[:, i].copy() for i, k in enumerate(keys)}
+
+    def count_ops(self, program) -> dict:
+        """Floating-point operations of the program [("step", n) | ("run_to", t_end), ...] run from the
+        current states (which are kept): adds, multiplies, divides, square roots, logarithms, exponentials,
+        and the cell-steps they served."""
+        kinds = np.array([0 if k == "step" else 1 for k, _ in program], dtype=np.int32)
+        args = np.array([float(a) for _, a in program], dtype=np.float64)
+        c = np.zeros(7, dtype=np.int64)
+        rc = lib().orc_count_ops(self.h, len(program), _ip(kinds), _dp(args), c.ctypes.data_as(C.POINTER(C.c_longlong)))
+        if rc != 0:
+            raise RuntimeError(f"oracle count_ops: status {rc}")
+        return dict(zip(["add", "mul", "div", "sqrt", "log", "exp", "cell_steps"], (int(x) for x in c)))
 
     def tangent(self, program, seed_w=None, seed_rho=None, seed_m=None, seed_tau=None, threads=1):
         """Forward-mode derivative of the program [("step", n) | ("run_to", t_end), ...] from the current

@@ -312,3 +312,31 @@ def test_conservation_through_an_asymmetric_creation():
     M1, P1 = totals(s["widths"], s["rho"], s["m"])
     assert abs(M1 - M0 - dM) <= 1e-13 * (abs(M0) + abs(dM))
     assert abs(P1 - P0 - dP) <= 1e-13 * (abs(P0) + abs(T * pl))
+
+
+def test_operation_count_of_the_explicit_step():
+    """The counting scalar (oracle/counted.h) runs the oracle's own templated scheme: its run is bit-identical
+    to the plain one and leaves the oracle's states as they were. On single-phase data (every cell explicit)
+    it gives the oracle's operation mix per explicit cell-step (about 54 flops in the liquid, 50 in the
+    vapour, with u formed at both faces of a cell and one division per flux component), above the 33 flops
+    per cell-step the roofline counts for the minimal arrangement (u once per cell, one reciprocal per face)."""
+    fl = I.workload_fluid()
+    N = 64
+    rng = np.random.default_rng(1)
+    for ph in (1, 0):
+        rho = (fl.rho0_liq if ph == 1 else 0.8) * (1 + 1e-3 * rng.uniform(-1, 1, N))
+        m = rho * rng.uniform(-20, 20, N)
+        b = I.Batch(n_lattice=np.array([N], np.int32), x_left=np.zeros(1), x_right=np.ones(1),
+                    tau=np.array([1e-7]), cell_offsets=np.array([0, N], np.int32), widths=np.full(N, 1.0 / N),
+                    rho=rho, m=m, phase=np.full(N, ph, np.uint8), fluid=fl, options=I.Options(), t_end=0.0,
+                    n_steps=10, name="single phase")
+        o = P.Oracle(b)
+        c = o.count_ops([("step", 10)])
+        assert c["cell_steps"] == 10 * N
+        np.testing.assert_array_equal(o.states()["rho"], b.rho)          # states kept
+        o.step(10)
+        plain = P.Oracle(b)
+        plain.step(10)
+        np.testing.assert_array_equal(o.states()["rho"], plain.states()["rho"])
+        flops = (c["add"] + c["mul"] + c["div"]) / c["cell_steps"]
+        assert 33 <= flops <= 60 and c["sqrt"] == c["log"] == c["exp"] == 0
