@@ -2,10 +2,12 @@
 
 Candidates: the per-step kernel schedule (one launch per kernel and step, replayed from a CUDA graph)
 and the instance-group schedule (one resident launch per call) at several group sizes and CTA widths.
-Each candidate advances the context's own states for a few steps (timed with CUDA events through the
-library's kernel timer), the context is restored with imexds_reset, and the fastest candidate is kept.
-Choices are cached per configuration (instance sizes, boundary counts, options) in memory and,
-optionally, in a JSON file.
+Each candidate gets a context of its own loaded with the batch; one untimed run (graph build, caches) is
+followed by imexds_reset and a timed run, host clock around the call, which returns when the device is
+done: the whole run_to for a batch with an end time (the early steps of a run are not representative of
+its cost), else `steps` steps. A candidate whose run leaves an instance with an error status is skipped.
+The fastest is kept. Choices are cached per configuration (instance sizes, boundary counts, options) in
+memory and, optionally, in a JSON file.
 """
 from __future__ import annotations
 
@@ -47,7 +49,8 @@ def tune(batch, steps: int = 64, cache_file: str | None = None, candidates=None)
     key = config_key(batch)
     if cache_file and os.path.exists(cache_file):
         try:
-            _cache.update(json.load(open(cache_file)))
+            with open(cache_file) as f:
+                _cache.update(json.load(f))
         except (OSError, ValueError):
             pass
     if key in _cache:
@@ -79,7 +82,8 @@ def tune(batch, steps: int = 64, cache_file: str | None = None, candidates=None)
     _cache[key] = choice
     if cache_file:
         try:
-            json.dump(_cache, open(cache_file, "w"), indent=1)
+            with open(cache_file, "w") as f:
+                json.dump(_cache, f, indent=1)
         except OSError:
             pass
     return choice
