@@ -2,22 +2,26 @@
 // two-phase flow with phase transition (May & Thein, arXiv 2211.00705), FP64, sm_103a.
 //
 // Device layout (per instance, batched):
-//   * background lattice: rho[], m[] (double buffered, parity per instance), phase[] (uint8),
-//     own[] (int32: zone slot that currently owns the lattice cell, -1 if it is an explicit cell);
+//   * background lattice: rho[], m[] and the velocity u[] = m/rho (double buffered, parity per
+//     instance), phase[] (uint8), own[] (int32: zone slot that currently owns the lattice cell, -1 if
+//     it is an explicit cell);
 //   * zones: fixed-capacity records holding the irregular cells next to phase boundaries (a maximal
 //     run of cells whose faces are not all on the lattice) with their widths, phases, face kinds and
 //     boundary positions. Zones are kept at least ZONE_GAP lattice cells apart (closer zones are
 //     joined), so every step's work on a zone touches no other zone.
 //
-// One time step = five kernels (captured in a CUDA graph by the host loop):
+// One time step, per-step schedule = five kernels (replayed from a CUDA graph by the host loop):
 //   k_pre    (thread per zone)  phase-boundary solves at U^n -> predicted widths -> merge marks (Sec. 3.4)
 //   k_plan   (thread per zone)  merges, tiny cells, implicit blocks {k-1,k,k+1} (Sec. 3.2), owned range
-//   k_sweep  (tile per CTA)     Algorithm 1 Step 1: HLL fluxes and explicit update of every free lattice
-//                               cell; phase-creation detection at free same-phase faces (App. B)
+//   k_sweep  (31-cell tile per warp) Algorithm 1 Step 1: HLL fluxes and explicit update of every free
+//                               lattice cell; phase-creation detection at free same-phase faces (App. B)
 //   k_dts    (thread per zone)  Algorithm 2 (dual time stepping + Part 2) on the zone's blocks with the
 //                               App. A boundary solver at the implicit faces and the moving widths
 //   k_post   (thread per instance) splits, release of regular cells, creation, t += dt, next dt
-// k_sweep and k_dts read U^n only and write disjoint cells of U^{n+1}.
+// k_sweep and k_dts read U^n only and write disjoint cells of U^{n+1}. Group schedule: k_group, one
+// resident CTA per group of instances for the whole call, runs the same device functions (warp 0 one
+// instance per lane: solves, plan, dual time, grid management; the other warps the sweep tiles).
+// Adjoint: k_adjoint (adjoint.cuh), one CTA per instance.
 #include <cuda_runtime.h>
 
 #include <algorithm>
