@@ -616,6 +616,29 @@ bool block_face_flux(const Fluid& Fl, const orc_opts& o, Inst<T>& I, int g, cons
 // One time step of Algorithm 1 with the dual-time stepping of Algorithm 2 on every block,
 // including the moving-grid width updates (Eq. godunov_meth:nonunif) and grid management.
 // t_end > 0 clips the step to land on t_end.
+// Solve A x = b for the augmented n x (n+1) matrix [A | b] in place by Gaussian elimination with partial
+// pivoting (pivots chosen on values); the solution replaces column n. False if a pivot is zero.
+template <class T>
+bool gauss_solve(std::vector<std::vector<T>>& A, int n) {
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(val(A[r][c])) > std::fabs(val(A[p][c]))) p = r;
+    if (!(std::fabs(val(A[p][c])) > 0.0)) return false;
+    std::swap(A[c], A[p]);
+    for (int r = c + 1; r < n; ++r) {
+      T f = A[r][c] / A[c][c];
+      for (int k = c; k <= n; ++k) A[r][k] = A[r][k] - f * A[c][k];
+    }
+  }
+  for (int c = n - 1; c >= 0; --c) {
+    T sum = A[c][n];
+    for (int k = c + 1; k < n; ++k) sum = sum - A[c][k] * A[k][n];
+    A[c][n] = sum / A[c][c];
+  }
+  return true;
+}
+
 template <class T>
 void step_instance(const Fluid& F, const orc_opts& o, Inst<T>& I, double t_end) {
   if (I.status != ORC_OK) return;
@@ -800,35 +823,103 @@ void step_instance(const Fluid& F, const orc_opts& o, Inst<T>& I, double t_end) 
     };
     int l = 0;
     bool stop = false;
-    for (l = 0; l < o.l_max && !stop; ++l) {
-      // Part 1 (a): fluxes at the current iterate, (b) pseudo-time update.
-      if (!fluxes(Wr, Wm)) {
-        I.status = ORC_ERR_VANISH;
-        return;
+    if (o.block_solver == 1) {
+      // Newton on the block's implicit system R(W) = W - T(W), T the update of Part 1 with fluxes and widths
+      // at W, whose fixed point is the dual-time limit. The Sec. 4 residual of an iterate W is
+      // |R(W)| / (dt max(|W|, 1)) component by component (the pseudo step moves W by theta R / (1 + theta)),
+      // so the same test stops Newton. Jacobian by central differences of T (step 1e-7 max(|W_j|, 1)),
+      // linear solve with partial pivoting.
+      const int n2 = 2 * (hi - lo + 1);
+      std::vector<T> Tv(n2), Tp(n2), Tq(n2);
+      auto target = [&](const std::vector<T>& Ar, const std::vector<T>& Am, std::vector<T>& out) -> bool {
+        if (!fluxes(Ar, Am)) return false;
+        for (int i = lo; i <= hi; ++i) {
+          out[2 * (i - lo)] = wn[i] / hl[i] * rn[i] - dt / hl[i] * (Fc0[i + 1] - Fc0[i]);
+          out[2 * (i - lo) + 1] = wn[i] / hl[i] * mn[i] - dt / hl[i] * (Fc1[i + 1] - Fc1[i]);
+        }
+        return true;
+      };
+      for (l = 0; l < o.l_max; ++l) {
+        if (!target(Wr, Wm, Tv)) {
+          I.status = ORC_ERR_VANISH;
+          return;
+        }
+        double res_nb = 0.0, res_k = 0.0;
+        const double dtv = val(dt);
+        for (int i = lo; i <= hi; ++i) {
+          double e0 = std::fabs(val(Wr[i]) - val(Tv[2 * (i - lo)])) / (dtv * std::max(std::fabs(val(Wr[i])), 1.0));
+          double e1 = std::fabs(val(Wm[i]) - val(Tv[2 * (i - lo) + 1])) / (dtv * std::max(std::fabs(val(Wm[i])), 1.0));
+          double res = std::max(e0, e1);
+          if (o.res_mode == 1) res *= dtv;
+          if (tiny[i])
+            res_k = std::max(res_k, res);
+          else
+            res_nb = std::max(res_nb, res);
+        }
+        if (res_nb < o.tol_nb && res_k < o.tol_k) {
+          stop = true;
+          break;
+        }
+        std::vector<std::vector<T>> A(n2, std::vector<T>(n2 + 1));  // [dR/dW | -R]
+        for (int j = 0; j < n2; ++j) {
+          std::vector<T>& X = (j % 2 == 0) ? Wr : Wm;
+          const int i = lo + j / 2;
+          const T keep = X[i];
+          const double e = 1e-7 * std::max(std::fabs(val(keep)), 1.0);
+          X[i] = keep + e;
+          bool ok = target(Wr, Wm, Tp);
+          X[i] = keep - e;
+          ok = ok && target(Wr, Wm, Tq);
+          X[i] = keep;
+          if (!ok) {
+            I.status = ORC_ERR_VANISH;
+            return;
+          }
+          for (int r = 0; r < n2; ++r) A[r][j] = T(r == j ? 1.0 : 0.0) - (Tp[r] - Tq[r]) / (2.0 * e);
+        }
+        for (int r = 0; r < n2; ++r) A[r][n2] = Tv[r] - ((r % 2 == 0) ? Wr[lo + r / 2] : Wm[lo + r / 2]);
+        if (!gauss_solve(A, n2)) {
+          I.status = ORC_ERR_PB_NOCONV;
+          return;
+        }
+        for (int r = 0; r < n2; ++r) {
+          if (r % 2 == 0)
+            Wr[lo + r / 2] = Wr[lo + r / 2] + A[r][n2];
+          else
+            Wm[lo + r / 2] = Wm[lo + r / 2] + A[r][n2];
+        }
       }
-      double res_nb = 0.0, res_k = 0.0;
-      std::vector<T> Nr = Wr, Nm = Wm;
-      for (int i = lo; i <= hi; ++i) {
-        T th = theta[i];
-        T tr = wn[i] / hl[i] * rn[i] - dt / hl[i] * (Fc0[i + 1] - Fc0[i]);
-        T tm = wn[i] / hl[i] * mn[i] - dt / hl[i] * (Fc1[i + 1] - Fc1[i]);
-        Nr[i] = (Wr[i] + th * tr) / (1.0 + th);
-        Nm[i] = (Wm[i] + th * tm) / (1.0 + th);
-        // residual of Sec. 4: ||(1 + dtau/dt)(W^{l+1} - W^l) / (dtau max(|W^l|, 1))||_inf
-        double thv = val(th), dtv = val(dt);
-        double dtau = thv * dtv;
-        double e0 = (1.0 + thv) * std::fabs(val(Nr[i]) - val(Wr[i])) / (dtau * std::max(std::fabs(val(Wr[i])), 1.0));
-        double e1 = (1.0 + thv) * std::fabs(val(Nm[i]) - val(Wm[i])) / (dtau * std::max(std::fabs(val(Wm[i])), 1.0));
-        double res = std::max(e0, e1);
-        if (o.res_mode == 1) res *= dtv;
-        if (tiny[i])
-          res_k = std::max(res_k, res);
-        else
-          res_nb = std::max(res_nb, res);
+    } else {
+      for (l = 0; l < o.l_max && !stop; ++l) {
+        // Part 1 (a): fluxes at the current iterate, (b) pseudo-time update.
+        if (!fluxes(Wr, Wm)) {
+          I.status = ORC_ERR_VANISH;
+          return;
+        }
+        double res_nb = 0.0, res_k = 0.0;
+        std::vector<T> Nr = Wr, Nm = Wm;
+        for (int i = lo; i <= hi; ++i) {
+          T th = theta[i];
+          T tr = wn[i] / hl[i] * rn[i] - dt / hl[i] * (Fc0[i + 1] - Fc0[i]);
+          T tm = wn[i] / hl[i] * mn[i] - dt / hl[i] * (Fc1[i + 1] - Fc1[i]);
+          Nr[i] = (Wr[i] + th * tr) / (1.0 + th);
+          Nm[i] = (Wm[i] + th * tm) / (1.0 + th);
+          // residual of Sec. 4: ||(1 + dtau/dt)(W^{l+1} - W^l) / (dtau max(|W^l|, 1))||_inf
+          double thv = val(th), dtv = val(dt);
+          double dtau = thv * dtv;
+          double e0 = (1.0 + thv) * std::fabs(val(Nr[i]) - val(Wr[i])) / (dtau * std::max(std::fabs(val(Wr[i])), 1.0));
+          double e1 = (1.0 + thv) * std::fabs(val(Nm[i]) - val(Wm[i])) / (dtau * std::max(std::fabs(val(Wm[i])), 1.0));
+          double res = std::max(e0, e1);
+          if (o.res_mode == 1) res *= dtv;
+          if (tiny[i])
+            res_k = std::max(res_k, res);
+          else
+            res_nb = std::max(res_nb, res);
+        }
+        Wr = Nr;
+        Wm = Nm;
+        if (res_nb < o.tol_nb && res_k < o.tol_k) stop = true;
       }
-      Wr = Nr;
-      Wm = Nm;
-      if (res_nb < o.tol_nb && res_k < o.tol_k) stop = true;
     }
     int iters = l;
     if (!stop) I.maxiter++;
@@ -1019,6 +1110,7 @@ void orc_default_opts(orc_opts* o) {
   o->alpha_min = 1e-8;
   o->split_ratio = 2.0;
   o->creation = 0;
+  o->block_solver = 0;
 }
 
 void orc_hll(const orc_fluid* fl, int ph, double rl, double ml, double rr, double mr, double F[2]) {

@@ -52,6 +52,10 @@ typedef struct {
   double alpha_min;    /* merge floor: a cell predicted below alpha_min*h is merged */
   double split_ratio;  /* a phase-boundary cell wider than split_ratio*h is split (2 in Sec. 3.4) */
   int creation;        /* 1: detect cavitation/nucleation at same-phase faces (App. B) */
+  int block_solver;    /* solver of each block's implicit system: 0 = dual time stepping (Alg. 2, the
+                          paper's); 1 = Newton with a central-difference Jacobian (the paper's outlook):
+                          same system, same stop test (the Sec. 4 residual of the iterate), l_max caps
+                          its iterations; dts_iters then counts Newton iterations */
 } orc_opts;
 
 /* statuses (same numbering as the product library) */

@@ -26,7 +26,7 @@ class OOpts(C.Structure):
     _fields_ = [("cfl", C.c_double), ("theta_nb", C.c_double), ("tol_nb", C.c_double), ("tol_k", C.c_double),
                 ("res_mode", C.c_int), ("l_max", C.c_int), ("newton_tol", C.c_double),
                 ("newton_itmax", C.c_int), ("alpha_min", C.c_double), ("split_ratio", C.c_double),
-                ("creation", C.c_int)]
+                ("creation", C.c_int), ("block_solver", C.c_int)]
 
 
 def lib():
@@ -86,9 +86,10 @@ def make_fluid(f) -> OFluid:
     return of
 
 
-def make_opts(o) -> OOpts:
+def make_opts(o, block_solver: int = 0) -> OOpts:
+    """block_solver: 0 dual time stepping (Alg. 2), 1 Newton on each block's implicit system (oracle only)."""
     return OOpts(o.cfl, o.theta_nb, o.tol_nb, o.tol_k, o.res_mode, o.l_max, o.newton_tol, o.newton_itmax,
-                 o.alpha_min, o.split_ratio, o.creation)
+                 o.alpha_min, o.split_ratio, o.creation, block_solver)
 
 
 def pb_solve(fluid, opts, tau, phl, rl, ul, phr, rr, ur):
@@ -144,12 +145,12 @@ def exact_sample(fluid, opts, tau, phl, rl, ul, phr, rr, ur, xi):
 class Oracle:
     """A batch of instances advanced by the oracle."""
 
-    def __init__(self, batch, options=None):
+    def __init__(self, batch, options=None, block_solver: int = 0):
         L = lib()
         self.batch = batch
         self.n = batch.n_inst
         self._fl = make_fluid(batch.fluid)
-        self._op = make_opts(options or batch.options)
+        self._op = make_opts(options or batch.options, block_solver)
         nl = np.ascontiguousarray(batch.n_lattice, dtype=np.int32)
         self.h = L.orc_create(self.n, _ip(nl), _dp(np.ascontiguousarray(batch.x_left)),
                               _dp(np.ascontiguousarray(batch.x_right)), _dp(np.ascontiguousarray(batch.tau)),

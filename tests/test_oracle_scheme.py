@@ -340,3 +340,26 @@ def test_operation_count_of_the_explicit_step():
         np.testing.assert_array_equal(o.states()["rho"], plain.states()["rho"])
         flops = (c["add"] + c["mul"] + c["div"]) / c["cell_steps"]
         assert 33 <= flops <= 60 and c["sqrt"] == c["log"] == c["exp"] == 0
+
+
+def test_block_newton_option_agrees_with_dual_time():
+    """The oracle's Newton option for each block's implicit system (block_solver = 1: same system, same stop
+    test as Algorithm 2's dual time stepping) reaches the dual-time solution: identical grids, states within
+    1e-10 on the single-instance workload and 1e-7 after whole runs of 16 benchmark instances, with about one
+    Newton iteration per step where dual time takes 16 to 31."""
+    for b, bar, newton_max in ((I.workload(0), 1e-10, 2.0), (I.workload(1, scale=16 / 4096), 1e-7, 2.0)):
+        o0, s0 = run(b)
+        o1, s1 = run(b, block_solver=1)
+        assert (s0["status"] == 0).all() and (s1["status"] == 0).all()
+        np.testing.assert_array_equal(s0["offsets"], s1["offsets"])
+        np.testing.assert_array_equal(s0["phase"], s1["phase"])
+        for k in range(b.n_inst):
+            a = slice(s0["offsets"][k], s0["offsets"][k + 1])
+            scale_r = np.max(np.abs(s0["rho"][a]))
+            scale_m = max(np.max(np.abs(s0["m"][a])), scale_r)
+            assert np.max(np.abs(s0["rho"][a] - s1["rho"][a])) <= bar * scale_r
+            assert np.max(np.abs(s0["m"][a] - s1["m"][a])) <= bar * scale_m
+        st0, st1 = o0.stats(), o1.stats()
+        dts = st0["dts_iters"].sum() / st0["steps"].sum()
+        newton = st1["dts_iters"].sum() / st1["steps"].sum()
+        assert newton <= newton_max and dts >= 8 * newton, (dts, newton)
