@@ -1,0 +1,112 @@
+"""Plant plausible mistakes in the oracle, one at a time, and report which CPU test catches each (a check of
+the oracle's pins; TEST INFRASTRUCTURE ONLY, nothing imports this module).
+
+Each entry names a mistake and replaces one exact string of oracle/oracle.cpp (or oracle/dual.h) that occurs
+once. For each: the file is edited, the oracle rebuilt, the oracle tests run (stopping at the first
+failure), and the original text put back; the original is restored and the oracle rebuilt once more at the
+end, whatever happens. Run from anywhere:
+
+    python oracle/plant_mistakes.py            # every batch (a few minutes)
+    python oracle/plant_mistakes.py dual        # one batch: scheme, batch2, batch3, batch4, dual
+"""
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+TESTS = ["tests/test_oracle_pins.py", "tests/test_oracle_scheme.py", "tests/test_oracle_tangent.py"]
+
+SCHEME = [
+ ("kinetic relation: sign of the kinetic-energy jump", "T Q = (R.g - L.g) - 0.5 * jp * (L.v + R.v);", "T Q = (R.g - L.g) + 0.5 * jp * (L.v + R.v);"),
+ ("kinetic relation: liquid pressure instead of vapour", "T pV = left_is_vapour ? L.p : R.p;", "T pV = left_is_vapour ? R.p : L.p;"),
+ ("Gibbs energy: factor a^2 dropped", "return e.a2 * tlog(T(rho / e.rho_sat));", "return tlog(T(rho / e.rho_sat));"),
+ ("rarefaction wave: density ratio inverted", "return e.a * tlog(T(rs / rhoK));", "return e.a * tlog(T(rhoK / rs));"),
+ ("shock wave: factor 2 in the jump product", "T q = (pstar - pK) * dv;", "T q = 2.0 * (pstar - pK) * dv;"),
+ ("shock wave derivative: sign of the second term", "T dq = dv + (pstar - pK) * vs * vs / e.a2;", "T dq = dv - (pstar - pK) * vs * vs / e.a2;"),
+ ("boundary system G1: sign of z^2 [[v]]", "S->G[0] = jp + z * z * jv;", "S->G[0] = jp - z * z * jv;"),
+ ("boundary system G2: sign of z [[v]]", "S->G[1] = S->fl + S->fr + z * jv + (ur - ul);", "S->G[1] = S->fl + S->fr - z * jv + (ur - ul);"),
+ ("boundary system G2: velocity jump transposed", "S->G[1] = S->fl + S->fr + z * jv + (ur - ul);", "S->G[1] = S->fl + S->fr + z * jv + (ul - ur);"),
+ ("HLL: sign of the dissipation term", "SL * Fr[c] + SL * SR * (Ur[c] - Ul[c])", "SL * Fr[c] - SL * SR * (Ur[c] - Ul[c])"),
+ ("HLL: left and right physical fluxes transposed", "(SR * Fl[c] - SL * Fr[c] +", "(SR * Fr[c] - SL * Fl[c] +"),
+ ("merge: wrong width weighting", "T rm = (I.w[a] * I.r[a] + I.w[b] * I.r[b]) / wm;", "T rm = (I.w[a] * I.r[a] + I.w[a] * I.r[b]) / wm;"),
+ ("dual time: wrong pseudo-time denominator", "Nr[i] = (Wr[i] + th * tr) / (1.0 + th);", "Nr[i] = (Wr[i] + th * tr) / (1.0 + 2.0 * th);"),
+ ("dual time: theta from the current width (convergence only)", "theta[i] = tmin(T(o.theta_nb), T(hpred[i] / I.h));", "theta[i] = tmin(T(o.theta_nb), T(val(I.w[i]) / I.h));"),
+ ("CFL: half the time step", "T dt = o.cfl * I.h / S;", "T dt = 0.5 * o.cfl * I.h / S;"),
+ ("creation: sign of the second boundary's z [[v]] in the velocity balance", "S->E[2] = S->fl + S->fr + z1 * jv1 + z2 * jv2 + (ur - ul);", "S->E[2] = S->fl + S->fr + z1 * jv1 - z2 * jv2 + (ur - ul);"),
+ ("creation: sign of z2^2 [[v]]", "S->E[1] = (x[2] - x[1]) + z2 * z2 * jv2;", "S->E[1] = (x[2] - x[1]) - z2 * z2 * jv2;"),
+ ("split: cut at the quarter point", "double xm = 0.5 * (val(I.f[i].x) + val(I.f[i + 1].x));", "double xm = 0.25 * (val(I.f[i].x) + 3.0 * val(I.f[i + 1].x));"),
+]
+BATCH2 = [
+ ("boundary flux: sign of p* in the momentum flux", "R.F[1] = -R.z * uV + pV;", "R.F[1] = -R.z * uV - pV;"),
+ ("boundary flux: sign of the mass flux", "R.F[0] = -R.z;", "R.F[0] = R.z;"),
+ ("boundary speed: w from the liquid side volume", "T vV = (phl == VAP) ? S.L.v : S.R.v;", "T vV = (phl == VAP) ? S.R.v : S.L.v;"),
+ ("no-transition star: exponent sign", "double rs = std::sqrt(rl * rr) * std::exp((ul - ur) / (2.0 * e.a));", "double rs = std::sqrt(rl * rr) * std::exp((ur - ul) / (2.0 * e.a));"),
+ ("creation detection: thresholds swapped", "det[g] = (P == LIQ) ? (ps < F.p_min) : (ps > F.p_tilde);", "det[g] = (P == LIQ) ? (ps > F.p_tilde) : (ps < F.p_min);"),
+ ("regular update: flux difference transposed", "I.r[i] = (hn * I.r[i] - dt * (F0[i + 1] - F0[i])) / hnp1;", "I.r[i] = (hn * I.r[i] - dt * (F0[i] - F0[i + 1])) / hnp1;"),
+ ("physical flux: pressure dropped", "F[1] = m * u + pressure(e, r);", "F[1] = m * u;"),
+]
+BATCH3 = [
+ ("explicit ALE update: face speeds transposed", "T hnp1 = wn[i] + (wl[i + 1] - wr[i]) * dt;", "T hnp1 = wn[i] + (wr[i] - wl[i + 1]) * dt;"),
+ ("created cell: width from one boundary speed", "I.w.insert(I.w.begin() + g, (R.w2 - R.w1) * dt);", "I.w.insert(I.w.begin() + g, R.w2 * dt);"),
+ ("created cell: momentum with the parent velocity sign", "I.m.insert(I.m.begin() + g, R.rhoC * R.uC);", "I.m.insert(I.m.begin() + g, -R.rhoC * R.uC);"),
+ ("transmissive left end: flux of the second cell", "phys_flux(F.ph[I.ph[0]], I.r[0], I.m[0], Fx);  // transmissive boundary", "phys_flux(F.ph[I.ph[1]], I.r[1], I.m[1], Fx);  // transmissive boundary"),
+ ("boundary position: moved against its speed", "xpb_new[g] = I.f[g].x + wc[g] * dt;", "xpb_new[g] = I.f[g].x - wc[g] * dt;"),
+ ("Part 2: block widths not updated", "      I.w[i] = hl[i];\n    }\n    for (int g = lo + 1; g <= hi; ++g)", "    }\n    for (int g = lo + 1; g <= hi; ++g)"),
+ ("creation flux: created-state pressure dropped", "Fl1[g] = -R.z1 * R.uC + R.pC;", "Fl1[g] = -R.z1 * R.uC;"),
+ ("predicted widths: boundary speeds transposed", "for (int i = 0; i < M; ++i) hpred[i] = I.w[i] + (wf[i + 1] - wf[i]) * dt;", "for (int i = 0; i < M; ++i) hpred[i] = I.w[i] + (wf[i] - wf[i + 1]) * dt;"),
+]
+BATCH4 = [
+ ("tangent shock form: factor 2 dropped in df/dp", "T((1.0 - (pstar - pK) * vs / (2.0 * e.a2)) / den)", "T((1.0 - (pstar - pK) * vs / e.a2) / den)"),
+ ("tangent shock form: sound speed dropped from the denominator", "T den = e.a * tsqrt(T(rhoK * rs));", "T den = tsqrt(T(rhoK * rs));"),
+]
+DUAL = [
+ ("dual numbers: quotient rule sign", "r.d[k] = (a.d[k] - r.v * b.d[k]) / b.v;", "r.d[k] = (a.d[k] + r.v * b.d[k]) / b.v;"),
+ ("dual numbers: logarithm derivative", "r.d[k] = a.d[k] / a.v;", "r.d[k] = a.d[k] * a.v;"),
+ ("dual numbers: product rule term dropped", "r.d[k] = a.d[k] * b.v + a.v * b.d[k];", "r.d[k] = a.d[k] * b.v;"),
+ ("dual numbers: square-root derivative factor", "r.d[k] = 0.5 * a.d[k] / r.v;", "r.d[k] = a.d[k] / r.v;"),
+]
+
+BATCHES = {"scheme": ("oracle.cpp", SCHEME), "batch2": ("oracle.cpp", BATCH2), "batch3": ("oracle.cpp", BATCH3),
+           "batch4": ("oracle.cpp", BATCH4), "dual": ("dual.h", DUAL)}
+
+
+def rebuild():
+    return subprocess.run([sys.executable, "-c", "from oracle import build as b; b.build(force=True)"], cwd=ROOT,
+                          capture_output=True, text=True)
+
+
+def run_batch(fname, mutations):
+    path = os.path.join(HERE, fname)
+    with open(path) as f:
+        orig = f.read()
+    try:
+        for name, old, new in mutations:
+            n = orig.count(old)
+            if n != 1:
+                print(f"{name}: text found {n} times, skipped", flush=True)
+                continue
+            with open(path, "w") as f:
+                f.write(orig.replace(old, new))
+            r = rebuild()
+            if r.returncode:
+                print(f"{name}: build failed", flush=True)
+                continue
+            r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] + TESTS,
+                               cwd=ROOT, capture_output=True, text=True)
+            first = [l for l in r.stdout.splitlines() if l.startswith(("FAILED", "ERROR"))]
+            if r.returncode:
+                print(f"{name}: CAUGHT ({first[0].split()[1] if first else 'pytest exit %d' % r.returncode})",
+                      flush=True)
+            else:
+                print(f"{name}: not caught", flush=True)
+    finally:
+        with open(path, "w") as f:
+            f.write(orig)
+        rebuild()
+
+
+if __name__ == "__main__":
+    names = sys.argv[1:] or list(BATCHES)
+    for nm in names:
+        run_batch(*BATCHES[nm])
