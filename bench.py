@@ -472,8 +472,7 @@ def main():
     t_max = reduce_max(ms / 1e3, ws, dev)
     value = job_value(cs_run, args.steps, ws, t_max)
 
-    # per-kernel durations over one instrumented run (events captured in the step graph)
-    # per-kernel durations: one instrumented run of the timed schedule, and one of the per-step kernel
+    # per-kernel durations (events captured in the step graph): one instrumented run of the timed schedule, and one of the per-step kernel
     # schedule, which separates the sweep from the dual-time work
     kt, kt_steps, phase_cycles = {}, {}, None
     try:
@@ -522,8 +521,8 @@ def main():
     e2e = {"value": job_value(cs_run, args.steps, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
-    # roofline of the dominant kernel
-    # roofline of the explicit sweep (FP64 ALU bound): algorithmic flops of the cells it updated, over its
+    # roofline of the explicit sweep (FP64 ALU bound; the timed schedule's resident group kernel mixes the
+    # sweep with the latency-bound dual-time chains and has no single roofline): algorithmic flops of the cells it updated, over its
     # measured time in the per-step schedule
     sweep_cells = float(np.sum(st["steps"] * batch.n_lattice))   # lattice cells swept per run (upper bound)
     n_sw = max(kt_steps["k_sweep"][1], 1)
