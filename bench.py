@@ -521,9 +521,9 @@ def main():
     e2e = {"value": job_value(cs_run, args.steps, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
-    # roofline of the explicit sweep (FP64 ALU bound; the timed schedule's resident group kernel mixes the
-    # sweep with the latency-bound dual-time chains and has no single roofline): algorithmic flops of the cells it updated, over its
-    # measured time in the per-step schedule
+    # roofline of the explicit sweep (FP64 ALU bound): algorithmic flops of the cells it updated, over its
+    # measured time in the per-step schedule. The timed schedule's resident group kernel mixes the sweep
+    # with the latency-bound dual-time chains and has no single roofline.
     sweep_cells = float(np.sum(st["steps"] * batch.n_lattice))   # lattice cells swept per run (upper bound)
     n_sw = max(kt_steps["k_sweep"][1], 1)
     flops = SWEEP_FLOP_PER_CELL * sweep_cells / n_sw
