@@ -171,24 +171,32 @@ imexds_status imexds_get_kernel_times(imexds_ctx* ctx, double* total_ms, int64_t
 
 /* One explicit time step that allocates no GPU memory, for callers that cannot call cudaMalloc: code
  * running inside a memory-pool-restricted or pre-reserved environment, or a host program that must not
- * grow its GPU footprint after start-up. The paper has no counterpart: this is a variant of the
- * library's explicit sweep (Algorithm 1, Step 1, with dt from the CFL condition) for instances that
- * contain no phase boundary (one phase in every cell), with the same arithmetic as imexds_step.
+ * grow its GPU footprint after start-up. The paper has no counterpart: this is the library's explicit
+ * HLL sweep and CFL time step, restricted to instances that contain no phase boundary (one phase in
+ * every cell), with the same arithmetic as imexds_step.
  *
  * Arguments: fluid and cfl as in imexds_create; n_lattice, x_left, x_right: HOST arrays of n_inst
  * entries (instance i has n_lattice[i] >= 2 cells of width (x_right - x_left)/n_lattice); rho_in, m_in,
  * phase: DEVICE arrays of the concatenated cells (instance after instance); rho_out, m_out: DEVICE
  * arrays of the same size receiving the states after one step (they must not overlap the inputs);
  * dt_out: DEVICE array of n_inst receiving each instance's time step; stream: a cudaStream_t (NULL =
- * default stream). The call returns after the step has completed on the stream.
+ * default stream).
+ *
+ * The call is synchronous: it copies the host arrays with cudaMemcpyAsync, launches its kernels, reads an
+ * error flag back and waits for the stream before it returns. None of these is allowed while a stream is
+ * being captured, so never make this call during a stream capture.
+ *
+ * Errors: IMEXDS_ERR_ARG (imexds_last_error_string says which) for a NULL pointer, cfl <= 0, n_inst <= 0,
+ * an instance with fewer than 2 cells or x_right <= x_left, and, found on the device, a phase byte above 1,
+ * a density that is not positive and finite, a non-finite momentum, or an instance holding cells of both
+ * phases. When the device check fails, rho_out and m_out are not written (dt_out is, but is meaningless).
  *
  * Scratch: a fixed device array of about 0.7 MB inside the library, which every GPU that loads the
  * library holds until the process exits; it limits n_inst to 16384 (larger batches are rejected with
  * IMEXDS_ERR_CAPACITY before any work, see imexds_last_error_string). The first call on a device looks
- * up that array's address (cudaGetSymbolAddress) with the device current; make that first call before
- * any stream capture. Every call reuses the same array and leaves its contents behind, so calls that
- * may overlap on the GPU (other streams, other host threads) race: serialise them. An instance holding
- * cells of both phases gives IMEXDS_ERR_ARG. */
+ * up that array's address (cudaGetSymbolAddress) with the device current. Every call reuses the same
+ * array and leaves its contents behind, so calls that may overlap on the GPU (other streams, other host
+ * threads) race: serialise them. */
 imexds_status imexds_step_uniform_noalloc(const imexds_fluid* fluid, double cfl, int32_t n_inst,
                                           const int32_t* n_lattice, const double* x_left, const double* x_right,
                                           const double* rho_in, const double* m_in, const uint8_t* phase,

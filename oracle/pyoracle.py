@@ -32,7 +32,9 @@ class OOpts(C.Structure):
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
+        # ORACLE_LIB: a library built from a modified copy of the oracle's source (the planted-mistake check of
+        # tests/plant_mistakes.py); otherwise the oracle built from this directory
+        path = os.environ.get("ORACLE_LIB") or _build.build()
         L = C.CDLL(path)
         dp = C.POINTER(C.c_double)
         ip = C.POINTER(C.c_int)

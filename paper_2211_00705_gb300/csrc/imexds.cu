@@ -2468,25 +2468,31 @@ imexds_status imexds_step_uniform_noalloc(const imexds_fluid* fluid, double cfl,
                                           const double* rho_in, const double* m_in, const uint8_t* phase,
                                           double* rho_out, double* m_out, double* dt_out, void* stream) {
   namespace na = imexds_noalloc;
-  if (!fluid || !n_lattice || !x_left || !x_right || !rho_in || !m_in || !phase || !rho_out || !m_out || !dt_out ||
-      !(cfl > 0.0) || n_inst <= 0)
+  auto arg_error = [](const char* why) {
+    g_last_error = std::string("imexds_step_uniform_noalloc: ") + why;
     return IMEXDS_ERR_ARG;
+  };
+  if (!fluid || !n_lattice || !x_left || !x_right || !rho_in || !m_in || !phase || !rho_out || !m_out || !dt_out)
+    return arg_error("a pointer argument is NULL");
+  if (!(cfl > 0.0)) return arg_error("cfl must be positive");
+  if (n_inst <= 0) return arg_error("n_inst must be positive");
   if (n_inst > na::kMaxInst) {
     g_last_error = "imexds_step_uniform_noalloc: n_inst exceeds the fixed scratch size (16384 instances)";
     return IMEXDS_ERR_CAPACITY;
   }
   long long cells = 0, tiles = 0;
   for (int i = 0; i < n_inst; ++i) {
-    if (n_lattice[i] < 2 || !(x_right[i] > x_left[i])) return IMEXDS_ERR_ARG;
+    if (n_lattice[i] < 2) return arg_error("an instance has fewer than 2 cells");
+    if (!(x_right[i] > x_left[i])) return arg_error("an instance has x_right <= x_left");
     cells += n_lattice[i];
     tiles += (n_lattice[i] + 31) / 32;
   }
-  if (cells > 0x7fffffffLL) return IMEXDS_ERR_ARG;
+  if (cells > 0x7fffffffLL) return arg_error("more than 2^31 - 1 cells in total");
   // set-up once per device, with that device current: the device address of the scratch array
   static void* scratch_ptr[64] = {nullptr};
   int dev = 0;
   CK(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return IMEXDS_ERR_ARG;
+  if (dev < 0 || dev >= 64) return arg_error("device ordinal above 63");
   if (!scratch_ptr[dev]) CK(cudaGetSymbolAddress(&scratch_ptr[dev], na::g_scratch));
   na::Scratch* scr = (na::Scratch*)scratch_ptr[dev];
   cudaStream_t st = (cudaStream_t)stream;
@@ -2507,7 +2513,12 @@ imexds_status imexds_step_uniform_noalloc(const imexds_fluid* fluid, double cfl,
   int err = 0;
   CK(cudaMemcpyAsync(&err, &scr->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  return err ? IMEXDS_ERR_ARG : IMEXDS_OK;
+  if (err & na::kErrState)
+    return arg_error("a cell has a phase byte above 1, a density that is not positive and finite, or a non-finite "
+                     "momentum (rho_out and m_out were not written)");
+  if (err & na::kErrMixed)
+    return arg_error("an instance holds cells of both phases (rho_out and m_out were not written)");
+  return IMEXDS_OK;
 }
 
 imexds_status imexds_get_group_phase_cycles(imexds_ctx* c, int64_t* slowest4, int64_t* sum4) {

@@ -15,8 +15,11 @@ struct Scratch {
   double x_right[kMaxInst];
   double h[kMaxInst];
   double dt[kMaxInst];
-  int err;  // set by the kernels: 1 = an instance holds more than one phase
+  int err;  // set by k_dt: kErrMixed, kErrState (bits)
 };
+
+constexpr int kErrMixed = 1;  // an instance holds cells of both phases
+constexpr int kErrState = 2;  // a phase byte above 1, a density that is not positive and finite, or a non-finite m
 
 // The scratch array (about 0.7 MB); every GPU that loads the library holds it until the process exits.
 static __device__ __align__(256) Scratch g_scratch;
@@ -38,25 +41,36 @@ __global__ void k_setup(Scratch* s, int n) {
   }
 }
 
-// Time step of each instance from the CFL condition (Eq. cfl_cond:unif): dt = C h / max_i(|u_i| + a).
+// Time step of each instance from the CFL condition (Eq. cfl_cond:unif): dt = C h / max_i(|u_i| + a). The
+// inputs are device arrays that no host code has seen, so this kernel also checks them: a phase byte above 1,
+// a density that is not positive and finite or a non-finite momentum sets kErrState, and an instance with
+// cells of both phases sets kErrMixed. A phase is only used as an index after masking it to 0 or 1.
 __global__ void k_dt(Scratch* s, Fluid F, double cfl, const double* rho, const double* m, const uint8_t* ph,
                      double* dt_out) {
   const int i = blockIdx.x;
   const int o = s->lat_off[i], N = s->n_lattice[i];
   const int p0 = ph[o];
   double S = 0.0;
-  int mixed = 0;
+  int mixed = 0, bad = 0;
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    S = fmax(S, fabs(div_nr(m[o + j], rho[o + j])) + F.ph[ph[o + j]].a);
-    mixed |= (ph[o + j] != p0);
+    const int pj = ph[o + j];
+    const double r = rho[o + j], mm = m[o + j];
+    const bool ok = pj <= 1 && r > 0.0 && isfinite(r) && isfinite(mm);
+    bad |= ok ? 0 : 1;
+    mixed |= (pj != p0);
+    if (ok) S = fmax(S, fabs(div_nr(mm, r)) + F.ph[pj & 1].a);
   }
   __shared__ double red[32];
-  __shared__ int any_mixed;
-  if (threadIdx.x == 0) any_mixed = 0;
+  __shared__ int any_mixed, any_bad;
+  if (threadIdx.x == 0) {
+    any_mixed = 0;
+    any_bad = 0;
+  }
   for (int off = 16; off > 0; off >>= 1) S = fmax(S, __shfl_down_sync(0xffffffffu, S, off));
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = S;
   if (mixed) atomicOr(&any_mixed, 1);
+  if (bad) atomicOr(&any_bad, 1);
   __syncthreads();
   if (threadIdx.x == 0) {
     double Sx = 0.0;
@@ -64,16 +78,18 @@ __global__ void k_dt(Scratch* s, Fluid F, double cfl, const double* rho, const d
     double dt = cfl * s->h[i] / Sx;
     s->dt[i] = dt;
     dt_out[i] = dt;
-    if (any_mixed) atomicOr(&s->err, 1);
+    if (any_mixed) atomicOr(&s->err, kErrMixed);
+    if (any_bad) atomicOr(&s->err, kErrState);
   }
 }
 
-// Algorithm 1 Step 1 for cells away from any phase boundary: HLL fluxes and the explicit update, one
-// warp per 32-cell tile (the same arithmetic as the library's sweep).
+// The explicit HLL sweep of the library for cells away from any phase boundary: HLL fluxes and the
+// explicit update, one warp per 32-cell tile (the same arithmetic as the library's sweep). Launched after
+// k_dt on the same stream; it writes nothing when k_dt found bad input.
 __global__ void k_sweep(const Scratch* s, Fluid F, int n, int n_tiles, const double* rho, const double* m,
                         const uint8_t* ph, double* rho_out, double* m_out) {
   const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (t >= n_tiles) return;
+  if (t >= n_tiles || s->err) return;
   const int lane = threadIdx.x & 31;
   int lo = 0, hi = n - 1;  // instance holding tile t
   while (lo < hi) {
@@ -85,7 +101,7 @@ __global__ void k_sweep(const Scratch* s, Fluid F, int n, int n_tiles, const dou
   }
   const int i = lo, o = s->lat_off[i], N = s->n_lattice[i];
   const int j0 = (t - s->tile_off[i]) << 5;
-  const Phase& E = F.ph[ph[o]];
+  const Phase& E = F.ph[ph[o] & 1];
   auto load = [&](int j, double& r, double& mm, double& u, double& f1) {
     r = rho[o + j];
     mm = m[o + j];

@@ -100,6 +100,11 @@ def _check(rc):
         raise ImexdsError(f"imexds status {rc} ({msg})")
 
 
+def last_error() -> str:
+    """Text of the library's last recorded error (imexds_last_error_string)."""
+    return load().imexds_last_error_string().decode()
+
+
 def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 

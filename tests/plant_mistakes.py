@@ -1,20 +1,26 @@
-"""Plant plausible mistakes in the oracle, one at a time, and report which CPU test catches each (a check of
-the oracle's pins; TEST INFRASTRUCTURE ONLY, nothing imports this module).
+"""Plant plausible mistakes in a copy of the oracle, one at a time, and report which CPU test catches each
+(a check of the oracle's pins; a tool run by hand, not a test: pytest does not collect this file).
 
-Each entry names a mistake and replaces one exact string of oracle/oracle.cpp (or oracle/dual.h) that occurs
-once. For each: the file is edited, the oracle rebuilt, the oracle tests run (stopping at the first
-failure), and the original text put back; the original is restored and the oracle rebuilt once more at the
-end, whatever happens. Run from anywhere:
+Each entry names a mistake and replaces one exact string of oracle.cpp (or dual.h) that occurs once. For each
+entry the oracle's sources are copied to a temporary directory, the copy is edited and compiled, and the
+oracle tests run against that library (ORACLE_LIB, stopping at the first failure). The tracked sources are
+never written. Run from anywhere:
 
-    python oracle/plant_mistakes.py            # every batch (a few minutes)
-    python oracle/plant_mistakes.py dual        # one batch: scheme, batch2, batch3, batch4, dual
+    python tests/plant_mistakes.py            # every batch (a few minutes)
+    python tests/plant_mistakes.py dual        # one batch: scheme, batch2, batch3, batch4, dual, residual
 """
 import os
 import subprocess
 import sys
 
+import shutil
+import tempfile
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
+ORACLE = os.path.join(ROOT, "oracle")
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
 TESTS = ["tests/test_oracle_pins.py", "tests/test_oracle_scheme.py", "tests/test_oracle_tangent.py"]
 
 SCHEME = [
@@ -71,39 +77,35 @@ BATCHES = {"scheme": ("oracle.cpp", SCHEME), "batch2": ("oracle.cpp", BATCH2), "
            "batch4": ("oracle.cpp", BATCH4), "dual": ("dual.h", DUAL)}
 
 
-def rebuild():
-    return subprocess.run([sys.executable, "-c", "from oracle import build as b; b.build(force=True)"], cwd=ROOT,
-                          capture_output=True, text=True)
-
-
 def run_batch(fname, mutations):
-    path = os.path.join(HERE, fname)
-    with open(path) as f:
+    from oracle import build as ob
+    with open(os.path.join(ORACLE, fname)) as f:
         orig = f.read()
-    try:
-        for name, old, new in mutations:
-            n = orig.count(old)
-            if n != 1:
-                print(f"{name}: text found {n} times, skipped", flush=True)
-                continue
-            with open(path, "w") as f:
+    for name, old, new in mutations:
+        n = orig.count(old)
+        if n != 1:
+            print(f"{name}: text found {n} times, skipped", flush=True)
+            continue
+        with tempfile.TemporaryDirectory() as tmp:
+            for f in os.listdir(ORACLE):
+                if f.endswith((".cpp", ".h")):
+                    shutil.copy(os.path.join(ORACLE, f), tmp)
+            with open(os.path.join(tmp, fname), "w") as f:
                 f.write(orig.replace(old, new))
-            r = rebuild()
-            if r.returncode:
+            lib = os.path.join(tmp, "liboracle_planted.so")
+            try:
+                ob.compile_to(tmp, lib)
+            except subprocess.CalledProcessError:
                 print(f"{name}: build failed", flush=True)
                 continue
+            env = dict(os.environ, ORACLE_LIB=lib)
             r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] + TESTS,
-                               cwd=ROOT, capture_output=True, text=True)
-            first = [l for l in r.stdout.splitlines() if l.startswith(("FAILED", "ERROR"))]
-            if r.returncode:
-                print(f"{name}: CAUGHT ({first[0].split()[1] if first else 'pytest exit %d' % r.returncode})",
-                      flush=True)
-            else:
-                print(f"{name}: not caught", flush=True)
-    finally:
-        with open(path, "w") as f:
-            f.write(orig)
-        rebuild()
+                               cwd=ROOT, capture_output=True, text=True, env=env)
+        first = [l for l in r.stdout.splitlines() if l.startswith(("FAILED", "ERROR"))]
+        if r.returncode:
+            print(f"{name}: CAUGHT ({first[0].split()[1] if first else 'pytest exit %d' % r.returncode})", flush=True)
+        else:
+            print(f"{name}: not caught", flush=True)
 
 
 if __name__ == "__main__":

@@ -101,3 +101,31 @@ def test_binding_refuses_cell_lists_shorter_than_the_offsets():
         ctx._check_lists(off, [("widths", ok), ("rho", ok[:6])])
     with pytest.raises(ValueError, match="offsets has 2 entries"):
         ctx._check_lists(off[:2], [("widths", ok[:3])])
+
+
+class _FakeDevicePtr:
+    """Stands in for a device tensor in calls that are rejected before any pointer is used."""
+
+    def data_ptr(self):
+        return 16
+
+
+def test_noalloc_rejects_oversized_and_malformed_batches_before_any_device_call(lib):
+    """The allocation-free step checks its host arguments first: more instances than its fixed scratch holds
+    gives IMEXDS_ERR_CAPACITY, a malformed instance IMEXDS_ERR_ARG, each with its reason in
+    imexds_last_error_string, and neither touches the (here fake) device pointers or needs a GPU."""
+    import numpy as np
+    from paper_2211_00705_gb300 import inputs as I
+    from paper_2211_00705_gb300.imexds import ImexdsError, last_error, step_uniform_noalloc
+    f = _FakeDevicePtr()
+    n = 16385
+    with pytest.raises(ImexdsError, match=r"status 9 "):
+        step_uniform_noalloc(I.workload_fluid(), 0.5, np.full(n, 64), np.zeros(n), np.ones(n), f, f, f, f, f, f)
+    assert "16384" in last_error()
+    with pytest.raises(ImexdsError, match=r"status 1 "):
+        step_uniform_noalloc(I.workload_fluid(), 0.5, np.array([64, 1]), np.zeros(2), np.ones(2), f, f, f, f, f, f)
+    assert "fewer than 2 cells" in last_error()
+    with pytest.raises(ImexdsError, match=r"status 1 "):
+        step_uniform_noalloc(I.workload_fluid(), 0.5, np.array([64, 64]), np.zeros(2), np.array([1.0, 0.0]),
+                             f, f, f, f, f, f)
+    assert "x_right <= x_left" in last_error()
