@@ -21,7 +21,8 @@ ROOT = os.path.dirname(HERE)
 ORACLE = os.path.join(ROOT, "oracle")
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
-TESTS = ["tests/test_oracle_pins.py", "tests/test_oracle_scheme.py", "tests/test_oracle_tangent.py"]
+TESTS = ["tests/test_oracle_pins.py", "tests/test_oracle_residual.py", "tests/test_oracle_scheme.py",
+         "tests/test_oracle_tangent.py"]
 
 SCHEME = [
  ("kinetic relation: sign of the kinetic-energy jump", "T Q = (R.g - L.g) - 0.5 * jp * (L.v + R.v);", "T Q = (R.g - L.g) + 0.5 * jp * (L.v + R.v);"),
@@ -73,8 +74,18 @@ DUAL = [
  ("dual numbers: square-root derivative factor", "r.d[k] = 0.5 * a.d[k] / r.v;", "r.d[k] = a.d[k] / r.v;"),
 ]
 
+RESIDUAL = [
+ ("dual-time residual: (1 + theta) dropped from the density term", "double e0 = (1.0 + thv) * std::fabs(val(Nr[i]) - val(Wr[i]))", "double e0 = std::fabs(val(Nr[i]) - val(Wr[i]))"),
+ ("dual-time residual: (1 + theta) dropped from the momentum term", "double e1 = (1.0 + thv) * std::fabs(val(Nm[i]) - val(Wm[i]))", "double e1 = std::fabs(val(Nm[i]) - val(Wm[i]))"),
+ ("dual-time residual: |W| instead of max(|W|, 1) (density)", "(dtau * std::max(std::fabs(val(Wr[i])), 1.0));", "(dtau * std::fabs(val(Wr[i])));"),
+ ("dual-time residual: |W| instead of max(|W|, 1) (momentum)", "(dtau * std::max(std::fabs(val(Wm[i])), 1.0));", "(dtau * std::fabs(val(Wm[i])));"),
+ ("dual-time residual: times dt in the printed mode", "          double res = std::max(e0, e1);\n          if (o.res_mode == 1) res *= dtv;\n          if (tiny[i])\n            res_k = std::max(res_k, res);\n          else\n            res_nb = std::max(res_nb, res);\n        }\n        Wr = Nr;", "          double res = std::max(e0, e1);\n          if (o.res_mode == 0) res *= dtv;\n          if (tiny[i])\n            res_k = std::max(res_k, res);\n          else\n            res_nb = std::max(res_nb, res);\n        }\n        Wr = Nr;"),
+ ("dual-time stop: either tolerance met instead of both", "        Wm = Nm;\n        if (res_nb < o.tol_nb && res_k < o.tol_k) stop = true;", "        Wm = Nm;\n        if (res_nb < o.tol_nb || res_k < o.tol_k) stop = true;"),
+ ("dual-time stop: tiny and other cells' residuals exchanged", "          if (tiny[i])\n            res_k = std::max(res_k, res);\n          else\n            res_nb = std::max(res_nb, res);\n        }\n        Wr = Nr;", "          if (!tiny[i])\n            res_k = std::max(res_k, res);\n          else\n            res_nb = std::max(res_nb, res);\n        }\n        Wr = Nr;"),
+]
+
 BATCHES = {"scheme": ("oracle.cpp", SCHEME), "batch2": ("oracle.cpp", BATCH2), "batch3": ("oracle.cpp", BATCH3),
-           "batch4": ("oracle.cpp", BATCH4), "dual": ("dual.h", DUAL)}
+           "batch4": ("oracle.cpp", BATCH4), "dual": ("dual.h", DUAL), "residual": ("oracle.cpp", RESIDUAL)}
 
 
 def run_batch(fname, mutations):
