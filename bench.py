@@ -35,8 +35,11 @@ UNIT = "cell-steps/s"
 SWEEP_FLOP_PER_CELL = 33
 FP64_PEAK_TFLOPS = 1.25   # GB300 dense FP64 (nominal; no FP64 figure in MEASURED_PEAKS.json)
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_sweep launch on this workload from an ncu capture of
-# the per-step schedule; None until the current k_sweep (31-cell tiles) has been captured
+# the per-step schedule; None until the current k_sweep has been captured
 SWEEP_TRAFFIC_BYTES = None
+# DRAM bytes per explicit cell-step of the resident group kernel (ncu capture of a scaled-down run of this
+# workload, scaled to a full launch by its cell-steps); None until the current k_group has been captured
+GROUP_TRAFFIC_BYTES_PER_CELL_STEP = None
 
 
 def dist_env():
@@ -383,6 +386,107 @@ def run_reference(args, ws, rank):
     return 0
 
 
+def with_block_solver(batch, block_solver):
+    import dataclasses
+    return dataclasses.replace(batch, options=dataclasses.replace(batch.options, block_solver=block_solver))
+
+
+def load_peak(key):
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))[key]
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def measure_run(batch, steps, warmup, schedule, flush, barrier, sampler=None, ws=1, dev=None):
+    """The headline measurement of one batch: the autotuned schedule (schedule 0) or the given one, warm-up runs,
+    then `steps` whole runs to t_end timed with CUDA events (L2 flushed between them, outside the events), max
+    over ranks. With a group schedule the library's own events around the resident kernel (on its stream) run
+    inside the same timed region and give that kernel's duration and its per-phase SM cycles; otherwise one
+    extra instrumented run gives the per-kernel durations. Returns the context (still open) and the figures."""
+    import torch
+    from paper_2211_00705_gb300.imexds import Imexds
+    tuned = None
+    if schedule == 0:
+        from paper_2211_00705_gb300 import autotune
+        tuned = autotune.tune(batch, steps=64)
+        ctx = Imexds.from_batch(batch, schedule=tuned["schedule"], group_threads=tuned.get("group_threads", 0),
+                                group_cells=tuned.get("group_cells", 0))
+        schedule_used = tuned["schedule"]
+    else:
+        ctx = Imexds.from_batch(batch, schedule=schedule)
+        schedule_used = schedule
+    group = schedule_used in (2, 3)
+    if group:
+        ctx.set_kernel_timing(True)   # events around the resident kernel; the launch itself is unchanged
+    for _ in range(max(warmup, 3)):
+        ctx.reset()
+        ctx.run_to(batch.t_end)
+    torch.cuda.synchronize()
+    counts = ctx.cell_counts()
+    st = ctx.stats()
+    cs_run = cell_steps(st, counts)
+    status = ctx.get_states()["status"]
+    if group:
+        ctx.set_kernel_timing(True)   # zero the durations and phase counters of the warm-up runs
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    launches = 0
+    barrier()
+    if sampler:
+        sampler.start()
+    for k in range(steps):
+        flush.fill_(float(k))
+        ctx.reset()
+        barrier()
+        ev0[k].record()
+        ctx.run_to(batch.t_end)
+        ev1[k].record()
+        barrier()
+        launches += int(ctx.stats()["launches"][0])
+    clocks = sampler.stop() if sampler else None
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in zip(ev0, ev1))
+    t_max = reduce_max(ms / 1e3, ws, dev)
+    if group:
+        kt = ctx.kernel_times()
+        phase = ctx.group_phase_cycles()
+        ctx.set_kernel_timing(False)
+    else:
+        phase = None
+        ctx.set_kernel_timing(True)
+        ctx.reset()
+        ctx.run_to(batch.t_end)
+        kt = ctx.kernel_times()
+        ctx.set_kernel_timing(False)
+    dominant = max(kt, key=lambda k: kt[k][0])
+    kms, kn = kt[dominant]
+    per_launch_s = kms / 1e3 / max(kn, 1)
+    launches_per_run = kn / (steps if group else 1)
+    # algorithmic work per launch of the dominant kernel: 33 FP64 flops and 32 bytes per explicit cell-step
+    cs_launch = cs_run / max(launches_per_run, 1)
+    ach = SWEEP_FLOP_PER_CELL * cs_launch / per_launch_s / 1e12 if per_launch_s > 0 else None
+    hbm_peak = load_peak("hbm_gbs")
+    gbs = 32.0 * cs_launch / per_launch_s / 1e9 if per_launch_s > 0 else None
+    roof = {"bound": "alu", "kernel": dominant, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": (ach / FP64_PEAK_TFLOPS) if ach else None,
+            "traffic": (GROUP_TRAFFIC_BYTES_PER_CELL_STEP * cs_launch
+                        if dominant == "k_group" and GROUP_TRAFFIC_BYTES_PER_CELL_STEP else None),
+            "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table; no FP64 entry in MEASURED_PEAKS.json)",
+            "ms_per_launch": per_launch_s * 1e3, "launches_per_run": launches_per_run,
+            "algorithmic_flops_per_launch": SWEEP_FLOP_PER_CELL * cs_launch,
+            "algorithmic_bytes_per_launch": 32.0 * cs_launch,
+            "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": (gbs / hbm_peak) if (gbs and hbm_peak) else None,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+            "timed_in": "the timed region (library events around the resident kernel)" if group else
+                        "one instrumented run after the timed region",
+            "phase_cycles": phase}
+    return {"ctx": ctx, "tuned": tuned, "stats": st, "value": job_value(cs_run, steps, ws, t_max),
+            "ms_per_step": 1e3 * t_max / steps, "cell_steps_run": cs_run, "launches": launches, "clocks": clocks,
+            "block_iters_per_step": float(st["dts_iters"].sum() / max(1, st["steps"].sum())),
+            "pb_newton_per_step": float(st["newton"].sum() / max(1, st["steps"].sum())),
+            "status_nonzero": int(np.count_nonzero(status)), "roofline": roof}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -397,10 +501,13 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--no-plain", action="store_true", help="skip the single-instance comparison")
     ap.add_argument("--no-hbm", action="store_true", help="skip the large-domain sweep (HBM) measurement")
+    ap.add_argument("--no-newton", action="store_true", help="skip the Newton block-solver leg")
     ap.add_argument("--only", choices=["adjoint", "hbm"], default=None,
                     help="run one auxiliary measurement alone and print its JSON (profiling)")
     ap.add_argument("--adjoint-steps", type=int, default=2000, help="steps of the adjoint workload")
     ap.add_argument("--table", action="store_true", help="per-workload rates (GPU, plain GPU, oracle) as JSON")
+    ap.add_argument("--block-solver", type=int, default=0, choices=[0, 1],
+                    help="solver of the implicit blocks for the headline run: 0 dual time stepping (Alg. 2), 1 Newton")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -424,15 +531,8 @@ def main():
         return 0
 
     batch = workload(args.scale)
-    tuned = None
-    if args.schedule == 0:
-        # the autotuner's choice for this batch (a few steps per candidate, untimed)
-        from paper_2211_00705_gb300 import autotune
-        tuned = autotune.tune(batch, steps=64)
-        ctx = Imexds.from_batch(batch, schedule=tuned["schedule"], group_threads=tuned.get("group_threads", 0),
-                                group_cells=tuned.get("group_cells", 0))
-    else:
-        ctx = Imexds.from_batch(batch, schedule=args.schedule)
+    if args.block_solver:
+        batch = with_block_solver(batch, args.block_solver)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -440,51 +540,15 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # warm-up (also builds the step graph)
-    for _ in range(max(args.warmup, 3)):
-        ctx.reset()
-        ctx.run_to(batch.t_end)
-    torch.cuda.synchronize()
-    counts = ctx.cell_counts()
-    st = ctx.stats()
-    cs_run = cell_steps(st, counts)
-    status = ctx.get_states()["status"]
-
-    # timed region: K whole runs with inputs resident in HBM; L2 flushed between runs (outside the events)
     sampler = ClockSampler(dev.index) if rank == 0 else None
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    launches = 0
-    barrier()
-    if sampler:
-        sampler.start()
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        ctx.reset()
-        barrier()
-        ev0[k].record()
-        ctx.run_to(batch.t_end)
-        ev1[k].record()
-        barrier()
-        launches += int(ctx.stats()["launches"][0])
-    clocks = sampler.stop() if sampler else None
-    ms = sum(e0.elapsed_time(e1) for e0, e1 in zip(ev0, ev1))
-    t_max = reduce_max(ms / 1e3, ws, dev)
-    value = job_value(cs_run, args.steps, ws, t_max)
+    head = measure_run(batch, args.steps, args.warmup, args.schedule, flush, barrier, sampler=sampler, ws=ws, dev=dev)
+    ctx, tuned, st = head["ctx"], head["tuned"], head["stats"]
+    value = head["value"]
 
-    # per-kernel durations (events captured in the step graph): one instrumented run of the timed schedule, and one of the per-step kernel
-    # schedule, which separates the sweep from the dual-time work
-    kt, kt_steps, phase_cycles = {}, {}, None
+    # per-kernel durations of the per-step kernel schedule (one instrumented run), which separates the sweep
+    # from the block solves
+    kt_steps = {}
     try:
-        ctx.set_kernel_timing(True)
-        ctx.reset()
-        ctx.run_to(batch.t_end)
-        kt = ctx.kernel_times()
-        try:
-            phase_cycles = ctx.group_phase_cycles()
-        except Exception:
-            phase_cycles = None
-        ctx.set_kernel_timing(False)
         ctx.set_schedule(1)
         ctx.set_kernel_timing(True)
         ctx.reset()
@@ -494,10 +558,8 @@ def main():
         ctx.set_schedule(tuned["schedule"] if tuned else args.schedule)
     except Exception as e:  # keep the measured line even if the instrumented pass fails
         print(f"kernel timing failed: {e}", file=sys.stderr)
-        kt = kt or {k: (0.0, 0) for k in Imexds.KERNELS}
-        kt_steps = kt_steps or {k: (0.0, 0) for k in Imexds.KERNELS}
+        kt_steps = {k: (0.0, 0) for k in Imexds.KERNELS}
     tot = sum(v[0] for v in kt_steps.values())
-    dominant = max(kt, key=lambda k: kt[k][0])
 
     # end to end through the public API with host buffers: upload, run, download every step
     h2d = int(batch.widths.nbytes + batch.rho.nbytes + batch.m.nbytes + batch.phase.nbytes
@@ -518,39 +580,51 @@ def main():
         d2h = int(out["widths"].nbytes + out["rho"].nbytes + out["m"].nbytes + out["phase"].nbytes
                   + out["offsets"].nbytes + out["t"].nbytes + out["status"].nbytes)
     e2e_s = reduce_max(sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / 1e3, ws, dev)
-    e2e = {"value": job_value(cs_run, args.steps, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h}
+    e2e = {"value": job_value(head["cell_steps_run"], args.steps, ws, e2e_s), "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    # roofline of the explicit sweep (FP64 ALU bound): algorithmic flops of the cells it updated, over its
-    # measured time in the per-step schedule. The timed schedule's resident group kernel mixes the sweep
-    # with the latency-bound dual-time chains and has no single roofline.
+    # roofline of the timed kernel (the resident group kernel, or the sweep of the per-step schedule)
+    roof = head["roofline"]
+    # the explicit sweep alone (FP64 ALU bound), in the per-step schedule: algorithmic flops of the cells it
+    # updated over its measured time
     sweep_cells = float(np.sum(st["steps"] * batch.n_lattice))   # lattice cells swept per run (upper bound)
     n_sw = max(kt_steps["k_sweep"][1], 1)
-    flops = SWEEP_FLOP_PER_CELL * sweep_cells / n_sw
     per_launch_s = kt_steps["k_sweep"][0] / 1e3 / n_sw
-    achieved = flops / per_launch_s / 1e12 if per_launch_s > 0 else None
-    roof = {"bound": "alu", "kernel": "k_sweep", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-            "traffic": SWEEP_TRAFFIC_BYTES if args.scale == 1.0 else None,
-            "algorithmic_bytes": 32.0 * sweep_cells / n_sw,
-            "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table; no FP64 entry in MEASURED_PEAKS.json)",
-            "timed_schedule_kernel": dominant,
-            "per_step_schedule_share": {k: round(v[0] / tot, 4) if tot else None for k, v in kt_steps.items()},
-            "per_step_schedule_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in kt_steps.items()},
-            "timed_schedule_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in kt.items()},
-            "group_phase_cycles": phase_cycles}
+    sw_ach = SWEEP_FLOP_PER_CELL * sweep_cells / n_sw / per_launch_s / 1e12 if per_launch_s > 0 else None
+    roof["sweep_per_step_schedule"] = {
+        "kernel": "k_sweep", "bound": "alu", "achieved": sw_ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": (sw_ach / FP64_PEAK_TFLOPS) if sw_ach else None,
+        "traffic": SWEEP_TRAFFIC_BYTES if args.scale == 1.0 else None,
+        "algorithmic_bytes": 32.0 * sweep_cells / n_sw, "ms_per_launch": per_launch_s * 1e3,
+        "share": {k: round(v[0] / tot, 4) if tot else None for k, v in kt_steps.items()},
+        "ms_per_launch_by_kernel": {k: (v[0] / v[1] if v[1] else None) for k, v in kt_steps.items()}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+                "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
                 "config": {"workload": batch.name, "instances": batch.n_inst, "cells": int(batch.rho.shape[0]),
+                           "block_solver": "newton" if args.block_solver else "dual time stepping (Alg. 2)",
                            "schedule": tuned if tuned else {"schedule": args.schedule},
-                           "cell_steps_per_step": cs_run, "l2": "flushed (256 MB write) between timed runs",
-                           "dts_iters_per_step": float(st["dts_iters"].sum() / max(1, st["steps"].sum())),
-                           "newton_iters_per_step": float(st["newton"].sum() / max(1, st["steps"].sum())),
-                           "instance_status_nonzero": int(np.count_nonzero(status))},
-                "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+                           "cell_steps_per_step": head["cell_steps_run"],
+                           "l2": "flushed (256 MB write) between timed runs",
+                           "dts_iters_per_step": head["block_iters_per_step"],
+                           "newton_iters_per_step": head["pb_newton_per_step"],
+                           "instance_status_nonzero": head["status_nonzero"]},
+                "roofline": roof, "e2e": e2e, "gpu_launches": head["launches"], "clocks": head["clocks"]}
+        if not args.block_solver and not args.no_newton:
+            # the same workload with Newton's method on every implicit block (the paper's outlook, Sec. 5)
+            nb = with_block_solver(batch, 1)
+            nw = measure_run(nb, args.steps, args.warmup, args.schedule, flush, barrier, sampler=None, ws=ws, dev=dev)
+            nw["ctx"].close()
+            line["newton"] = {"value": nw["value"], "unit": UNIT, "ms_per_step": nw["ms_per_step"],
+                              "over_dual_time": nw["value"] / value,
+                              "schedule": nw["tuned"] if nw["tuned"] else {"schedule": args.schedule},
+                              "newton_steps_per_step": nw["block_iters_per_step"],
+                              "pb_newton_iters_per_step": nw["pb_newton_per_step"],
+                              "instance_status_nonzero": nw["status_nonzero"], "roofline": nw["roofline"],
+                              "note": "options.block_solver = 1: Newton on each implicit block's system with the "
+                                      "Sec. 4 stop test; parity against the oracle's Newton option"}
         if not args.no_plain:
             plain = measure_plain(batch)
             plain["batched_over_plain"] = value / plain["value"]

@@ -80,6 +80,10 @@ typedef struct {
   int group_threads;   /* threads per group CTA, a multiple of 32 from 64 to 256 (0 = 128): warp 0 runs
                           the per-instance work, the other warps sweep; above 128 one CTA per SM (the
                           independent-group schedule 3 takes at most 128) */
+  int block_solver;    /* solver of each implicit block's system of Algorithm 2 Part 1: 0 dual time stepping
+                          (Alg. 2, Eq. dual time tau diff); 1 Newton's method on the same system with the same
+                          stop test of Sec. 4 (the outlook of Sec. 5), the iteration counters then counting
+                          Newton steps (0) */
 } imexds_options;
 
 /* A batch of independent 1-D problems on [x_left[i], x_right[i]] with n_lattice[i] background
@@ -151,13 +155,14 @@ imexds_status imexds_set_states_device(imexds_ctx* ctx, const int32_t* cell_offs
  * copies only). */
 imexds_status imexds_reset(imexds_ctx* ctx);
 
-/* Measurement of the group schedule (timing mode): SM clock cycles spent per phase of the resident
- * kernel (0 boundary solves + plan, 1 sweep, 2 dual time, 3 grid management), for the group with the
- * longest critical path (slowest4) and summed over all groups (sum4). Arrays of 4. Phases 0, 2 and 3 are
- * read by lane 0 of warp 0, phase 1 by lane 0 of the first sweep warp; they are indicative only (on the
- * 4096-instance workload the slowest group's phases summed to more than the run's own cycles). The
- * counters accumulate over every timing-mode call until imexds_set_states rebuilds the groups. */
-imexds_status imexds_get_group_phase_cycles(imexds_ctx* ctx, int64_t* slowest4, int64_t* sum4);
+/* Measurement of the group schedule (timing mode): SM clock cycles per phase of the resident kernel, for
+ * the group whose launch took the most cycles (slowest6) and summed over all groups (sum6). Arrays of 6:
+ * 0 boundary solves + plan, 1 sweep (first sweep warp), 2 dual time or Newton (warp 0), 3 grid management,
+ * 4 the concurrent phase of 1 and 2 (barrier to barrier), 5 the whole launch. With the lockstep groups,
+ * 0 + 4 + 3 equals 5 up to the loop's own instructions and 1, 2 <= 4; with the independent groups (schedule
+ * 3) each entry is the maximum over the group's instances, 4 being dual time plus the wait for the sweep.
+ * The counters accumulate over the timing-mode calls since the last imexds_set_kernel_timing. */
+imexds_status imexds_get_group_phase_cycles(imexds_ctx* ctx, int64_t* slowest6, int64_t* sum6);
 
 /* Choose the schedule for the next calls (values of imexds_options.schedule, 0..3). */
 imexds_status imexds_set_schedule(imexds_ctx* ctx, int32_t schedule);
@@ -165,7 +170,10 @@ imexds_status imexds_set_schedule(imexds_ctx* ctx, int32_t schedule);
 /* Measurement: with on != 0, steps are launched without the step graph and CUDA events are recorded
  * around each kernel; imexds_get_kernel_times returns, per kernel (0 pre-solve, 1 plan, 2 sweep,
  * 3 dual time, 4 post, 5 group-resident kernel), the summed duration in ms and the number of timed
- * launches since timing was switched on. Arrays have 6 entries. */
+ * launches since timing was switched on. Arrays have 6 entries. Every call of imexds_set_kernel_timing zeroes
+ * those durations and counts and the group phase cycles. With a group schedule (2, 3) timing changes no launch
+ * (events around the resident kernel; its phase counters are written at its end); the first timed call of a
+ * context allocates the counters. */
 imexds_status imexds_set_kernel_timing(imexds_ctx* ctx, int32_t on);
 imexds_status imexds_get_kernel_times(imexds_ctx* ctx, double* total_ms, int64_t* launches);
 

@@ -613,6 +613,77 @@ bool block_face_flux(const Fluid& Fl, const orc_opts& o, Inst<T>& I, int g, cons
   return true;
 }
 
+// The update T of Algorithm 2 Part 1 for the cells lo..hi of a block (Eq. godunov_meth:nonunif with fluxes
+// and widths at the iterate W): T_i = (h^n_i U^n_i - dt (F_{i+1/2}(W) - F_{i-1/2}(W))) / h_i(W),
+// h_i(W) = h^n_i + (w_{i+1/2}(W) - w_{i-1/2}(W)) dt, the outer fluxes FL, FR fixed at U^n. Written for any
+// scalar type S of the iterate (everything else as plain values), so that dual numbers give dT/dW.
+template <class S>
+bool block_update(const Fluid& Fl, const orc_opts& o, double tau, const std::vector<int>& ph,
+                  const std::vector<Face<double>>& f, int lo, int hi, const std::vector<double>& wn,
+                  const std::vector<double>& rn, const std::vector<double>& mn, const double FL[2],
+                  const double FR[2], double dt, const std::vector<S>& Wr, const std::vector<S>& Wm,
+                  std::vector<S>& out) {
+  const int n = hi - lo + 1;
+  std::vector<S> F0(n + 1), F1(n + 1), wc(n + 1, S(0.0));
+  F0[0] = FL[0];
+  F1[0] = FL[1];
+  F0[n] = FR[0];
+  F1[n] = FR[1];
+  for (int g = lo + 1; g <= hi; ++g) {
+    const int q = g - lo;
+    S Fx[2];
+    if (f[g].pb) {
+      PBResult<S> R = pb_solve(Fl, o, S(tau), ph[g - 1], Wr[g - 1], Wm[g - 1], ph[g], Wr[g], Wm[g]);
+      if (!R.ok) return false;
+      Fx[0] = R.F[0];
+      Fx[1] = R.F[1];
+      wc[q] = R.w;
+    } else {
+      hll(Fl.ph[ph[g]], Wr[g - 1], Wm[g - 1], Wr[g], Wm[g], Fx);
+    }
+    F0[q] = Fx[0];
+    F1[q] = Fx[1];
+  }
+  for (int i = lo; i <= hi; ++i) {
+    const int q = i - lo;
+    S hl = wn[i] + (wc[q + 1] - wc[q]) * dt;
+    if (!(val(hl) > 0.0)) return false;
+    out[2 * q] = wn[i] / hl * rn[i] - dt / hl * (F0[q + 1] - F0[q]);
+    out[2 * q + 1] = wn[i] / hl * mn[i] - dt / hl * (F1[q + 1] - F1[q]);
+  }
+  return true;
+}
+
+// dT/dW of block_update at the values Wr, Wm of the iterate (row 2q + c: component c of cell lo + q; column
+// likewise), by forward-mode dual numbers, eight unknowns at a time: exact up to rounding (the boundary solve's
+// Newton iteration, carried on dual numbers, gives its converged root's derivative).
+bool block_jacobian(const Fluid& Fl, const orc_opts& o, double tau, const std::vector<int>& ph,
+                    const std::vector<Face<double>>& f, int lo, int hi, const std::vector<double>& wn,
+                    const std::vector<double>& rn, const std::vector<double>& mn, const double FL[2],
+                    const double FR[2], double dt, const std::vector<double>& Wr, const std::vector<double>& Wm,
+                    std::vector<std::vector<double>>& dT) {
+  typedef orcdual::Dual<8> DJ;
+  const int n2 = 2 * (hi - lo + 1);
+  std::vector<DJ> Dr(Wr.size()), Dm(Wm.size()), out(n2);
+  for (int c0 = 0; c0 < n2; c0 += 8) {
+    for (size_t i = 0; i < Wr.size(); ++i) {
+      Dr[i] = DJ(Wr[i]);
+      Dm[i] = DJ(Wm[i]);
+    }
+    for (int j = c0; j < std::min(n2, c0 + 8); ++j) {
+      const int i = lo + j / 2;
+      if (j % 2 == 0)
+        Dr[i].d[j - c0] = 1.0;
+      else
+        Dm[i].d[j - c0] = 1.0;
+    }
+    if (!block_update(Fl, o, tau, ph, f, lo, hi, wn, rn, mn, FL, FR, dt, Dr, Dm, out)) return false;
+    for (int r = 0; r < n2; ++r)
+      for (int j = c0; j < std::min(n2, c0 + 8); ++j) dT[r][j] = out[r].d[j - c0];
+  }
+  return true;
+}
+
 // One time step of Algorithm 1 with the dual-time stepping of Algorithm 2 on every block,
 // including the moving-grid width updates (Eq. godunov_meth:nonunif) and grid management.
 // t_end > 0 clips the step to land on t_end.
@@ -827,10 +898,10 @@ void step_instance(const Fluid& F, const orc_opts& o, Inst<T>& I, double t_end) 
       // Newton on the block's implicit system R(W) = W - T(W), T the update of Part 1 with fluxes and widths
       // at W, whose fixed point is the dual-time limit. The Sec. 4 residual of an iterate W is
       // |R(W)| / (dt max(|W|, 1)) component by component (the pseudo step moves W by theta R / (1 + theta)),
-      // so the same test stops Newton. Jacobian by central differences of T (step 1e-7 max(|W_j|, 1)),
-      // linear solve with partial pivoting.
+      // so the same test stops Newton. Jacobian dR/dW = I - dT/dW by forward-mode dual numbers at the values
+      // of the iterate (block_jacobian), linear solve with partial pivoting.
       const int n2 = 2 * (hi - lo + 1);
-      std::vector<T> Tv(n2), Tp(n2), Tq(n2);
+      std::vector<T> Tv(n2);
       auto target = [&](const std::vector<T>& Ar, const std::vector<T>& Am, std::vector<T>& out) -> bool {
         if (!fluxes(Ar, Am)) return false;
         for (int i = lo; i <= hi; ++i) {
@@ -839,6 +910,17 @@ void step_instance(const Fluid& F, const orc_opts& o, Inst<T>& I, double t_end) 
         }
         return true;
       };
+      // plain values of everything the Jacobian depends on besides the iterate
+      std::vector<Face<double>> fv(I.f.size());
+      for (size_t g = 0; g < I.f.size(); ++g) fv[g] = Face<double>{I.f[g].pb, I.f[g].j, val(I.f[g].x)};
+      std::vector<double> wnv(M), rnv(M), mnv(M), Wrv(M), Wmv(M);
+      for (int i = 0; i < M; ++i) {
+        wnv[i] = val(wn[i]);
+        rnv[i] = val(rn[i]);
+        mnv[i] = val(mn[i]);
+      }
+      const double FLv[2] = {val(FL[0]), val(FL[1])}, FRv[2] = {val(FR[0]), val(FR[1])};
+      std::vector<std::vector<double>> dT(n2, std::vector<double>(n2, 0.0));
       for (l = 0; l < o.l_max; ++l) {
         if (!target(Wr, Wm, Tv)) {
           I.status = ORC_ERR_VANISH;
@@ -860,24 +942,19 @@ void step_instance(const Fluid& F, const orc_opts& o, Inst<T>& I, double t_end) 
           stop = true;
           break;
         }
-        std::vector<std::vector<T>> A(n2, std::vector<T>(n2 + 1));  // [dR/dW | -R]
-        for (int j = 0; j < n2; ++j) {
-          std::vector<T>& X = (j % 2 == 0) ? Wr : Wm;
-          const int i = lo + j / 2;
-          const T keep = X[i];
-          const double e = 1e-7 * std::max(std::fabs(val(keep)), 1.0);
-          X[i] = keep + e;
-          bool ok = target(Wr, Wm, Tp);
-          X[i] = keep - e;
-          ok = ok && target(Wr, Wm, Tq);
-          X[i] = keep;
-          if (!ok) {
-            I.status = ORC_ERR_VANISH;
-            return;
-          }
-          for (int r = 0; r < n2; ++r) A[r][j] = T(r == j ? 1.0 : 0.0) - (Tp[r] - Tq[r]) / (2.0 * e);
+        for (int i = 0; i < M; ++i) {
+          Wrv[i] = val(Wr[i]);
+          Wmv[i] = val(Wm[i]);
         }
-        for (int r = 0; r < n2; ++r) A[r][n2] = Tv[r] - ((r % 2 == 0) ? Wr[lo + r / 2] : Wm[lo + r / 2]);
+        if (!block_jacobian(F, o, val(I.tau), I.ph, fv, lo, hi, wnv, rnv, mnv, FLv, FRv, dtv, Wrv, Wmv, dT)) {
+          I.status = ORC_ERR_VANISH;
+          return;
+        }
+        std::vector<std::vector<T>> A(n2, std::vector<T>(n2 + 1));  // [dR/dW | -R]
+        for (int r = 0; r < n2; ++r) {
+          for (int j = 0; j < n2; ++j) A[r][j] = T((r == j ? 1.0 : 0.0) - dT[r][j]);
+          A[r][n2] = Tv[r] - ((r % 2 == 0) ? Wr[lo + r / 2] : Wm[lo + r / 2]);
+        }
         if (!gauss_solve(A, n2)) {
           I.status = ORC_ERR_PB_NOCONV;
           return;

@@ -88,10 +88,12 @@ def make_fluid(f) -> OFluid:
     return of
 
 
-def make_opts(o, block_solver: int = 0) -> OOpts:
-    """block_solver: 0 dual time stepping (Alg. 2), 1 Newton on each block's implicit system (oracle only)."""
+def make_opts(o, block_solver=None) -> OOpts:
+    """block_solver: 0 dual time stepping (Alg. 2), 1 Newton on each block's implicit system; None takes the
+    options' own block_solver (0 when they have none)."""
+    bs = getattr(o, "block_solver", 0) if block_solver is None else block_solver
     return OOpts(o.cfl, o.theta_nb, o.tol_nb, o.tol_k, o.res_mode, o.l_max, o.newton_tol, o.newton_itmax,
-                 o.alpha_min, o.split_ratio, o.creation, block_solver)
+                 o.alpha_min, o.split_ratio, o.creation, bs)
 
 
 def pb_solve(fluid, opts, tau, phl, rl, ul, phr, rr, ur):
@@ -147,7 +149,7 @@ def exact_sample(fluid, opts, tau, phl, rl, ul, phr, rr, ur, xi):
 class Oracle:
     """A batch of instances advanced by the oracle."""
 
-    def __init__(self, batch, options=None, block_solver: int = 0):
+    def __init__(self, batch, options=None, block_solver=None):
         L = lib()
         self.batch = batch
         self.n = batch.n_inst

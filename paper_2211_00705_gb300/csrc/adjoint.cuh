@@ -340,6 +340,8 @@ __device__ bool dts_block(const ADev& A, AInst& I, const SharedStep& S, int lo, 
     gl[q] = fp[q] ? A.pwl[o + lo + q] : 0.0;
     gr[q] = fp[q] ? A.pwr[o + lo + q] : 0.0;
   }
+  FaceJac fj[AMAXB + 1];  // boundary faces' Jacobians (Newton block solver)
+  const bool newton_solver = (c_opts.block_solver == 1);
   auto fluxes = [&]() -> int {  // 0 ok, 1 boundary solve failed, 2 non-positive width
     F0[0] = FL0;
     F1[0] = FL1;
@@ -348,8 +350,10 @@ __device__ bool dts_block(const ADev& A, AInst& I, const SharedStep& S, int lo, 
     wc[0] = wc[nb] = 0.0;
     for (int q = 1; q < nb; ++q) {
       if (fp[q]) {
-        PBOut R = pb_solve_warm(c_fluid, c_opts, tau, ph[q - 1], Wr[q - 1], Wm[q - 1], ph[q], Wr[q], Wm[q], gl[q],
-                                gr[q]);
+        PBOut R = newton_solver ? pb_solve_core<true>(c_fluid, c_opts, tau, ph[q - 1], Wr[q - 1], Wm[q - 1], ph[q],
+                                                      Wr[q], Wm[q], gl[q], gr[q], &fj[q])
+                                : pb_solve_warm(c_fluid, c_opts, tau, ph[q - 1], Wr[q - 1], Wm[q - 1], ph[q], Wr[q],
+                                                Wm[q], gl[q], gr[q]);
         if (!R.ok) return 1;
         F0[q] = R.F0;
         F1[q] = R.F1;
@@ -365,7 +369,64 @@ __device__ bool dts_block(const ADev& A, AInst& I, const SharedStep& S, int lo, 
     return 0;
   };
   bool stop = false;
-  for (int l = 0; l < c_opts.l_max && !stop; ++l) {
+  if (newton_solver) {
+    // Newton on the block's system R(W) = W - T(W) with the stop test of Sec. 4 (the forward kernels'
+    // newton_simple / newton_general): fluxes at W, T(W), the test, then (I - dT/dW) dW = T(W) - W
+    const double dtr = (c_opts.res_mode == 1) ? 1.0 : dt;
+    const int n2 = 2 * nb;
+    for (int l = 0; l < c_opts.l_max; ++l) {
+      int e = fluxes();
+      if (e) {
+        afail(I, e == 1 ? IMEXDS_ERR_PB_NOCONV : IMEXDS_ERR_VANISH);
+        return false;
+      }
+      double Tr[AMAXB], Tm[AMAXB];
+      stop = true;
+      for (int q = 0; q < nb; ++q) {
+        Tr[q] = (Uw[q] * Ur[q] - dt * (F0[q + 1] - F0[q])) / hl[q];
+        Tm[q] = (Uw[q] * Um[q] - dt * (F1[q + 1] - F1[q])) / hl[q];
+        const double lim = (tiny[q] ? c_opts.tol_k : c_opts.tol_nb) * dtr;
+        stop = stop && (fabs(Tr[q] - Wr[q]) < lim * fmax(fabs(Wr[q]), 1.0)) &&
+               (fabs(Tm[q] - Wm[q]) < lim * fmax(fabs(Wm[q]), 1.0));
+      }
+      if (stop) break;
+      for (int q = 1; q < nb; ++q)
+        if (!fp[q]) hll_jac(c_fluid.ph[ph[q]], Wr[q - 1], Wm[q - 1], Wr[q], Wm[q], fj[q]);
+      double Ab[2 * AMAXB][BAND_W], rhs[2 * AMAXB];
+      for (int r = 0; r < n2; ++r) {
+        for (int k = 0; k < BAND_W; ++k) Ab[r][k] = 0.0;
+        Ab[r][3] = 1.0;
+      }
+      for (int q = 0; q < nb; ++q) {
+        const double coef = dt / hl[q];
+        rhs[2 * q] = Tr[q] - Wr[q];
+        rhs[2 * q + 1] = Tm[q] - Wm[q];
+        for (int c = 0; c < 2; ++c) {
+          const int row = 2 * q + c;
+          const double Tq = c ? Tm[q] : Tr[q];
+          if (q + 1 < nb) {
+            const FaceJac& J = fj[q + 1];
+            for (int k = 0; k < 4; ++k)
+              Ab[row][2 * q + k - row + 3] += coef * ((c ? J.dF1[k] : J.dF0[k]) + Tq * J.dw[k]);
+          }
+          if (q >= 1) {
+            const FaceJac& J = fj[q];
+            for (int k = 0; k < 4; ++k)
+              Ab[row][2 * (q - 1) + k - row + 3] -= coef * ((c ? J.dF1[k] : J.dF0[k]) + Tq * J.dw[k]);
+          }
+        }
+      }
+      if (!solve_band(Ab, rhs, n2)) {
+        afail(I, IMEXDS_ERR_PB_NOCONV);
+        return false;
+      }
+      for (int q = 0; q < nb; ++q) {
+        Wr[q] += rhs[2 * q];
+        Wm[q] += rhs[2 * q + 1];
+      }
+    }
+  }
+  for (int l = 0; !newton_solver && l < c_opts.l_max && !stop; ++l) {
     int e = fluxes();
     if (e) {
       afail(I, e == 1 ? IMEXDS_ERR_PB_NOCONV : IMEXDS_ERR_VANISH);

@@ -167,6 +167,27 @@ __device__ inline void zone_erase_cell(Zone& Z, int b) {
   Z.nc--;
 }
 
+// insert an empty cell at index pos of a zone (cells pos.. and faces pos+1.. move up; face pos+1 is a copy of
+// face pos); 0 when the zone is full
+__device__ inline int zone_insert_cell(Zone& Z, int pos) {
+  if (Z.nc >= ZC) return 0;
+  for (int i = Z.nc; i > pos; --i) {
+    Z.w[i] = Z.w[i - 1];
+    Z.r[i] = Z.r[i - 1];
+    Z.m[i] = Z.m[i - 1];
+    Z.ph[i] = Z.ph[i - 1];
+  }
+  for (int k = Z.nc + 1; k > pos; --k) {
+    Z.fpb[k] = Z.fpb[k - 1];
+    Z.fj[k] = Z.fj[k - 1];
+    Z.fx[k] = Z.fx[k - 1];
+    Z.pwl[k] = Z.pwl[k - 1];
+    Z.pwr[k] = Z.pwr[k - 1];
+  }
+  Z.nc++;
+  return 1;
+}
+
 // ------------------------------------------------------------------------------------------ k_plan
 // Merges (left to right, a marked cell joins its neighbour across its fixed face), then the implicit
 // neighbourhoods: at every boundary the smaller adjacent cell is the tiny cell k; {k-1, k, k+1} are
@@ -487,7 +508,7 @@ __device__ void sweep_tile(const Dev& d, int ii, int j0) {
     m1 = (h * C.m - dt * (G1 - fj.F1R)) / hnp1;
   }
   const double u1 = div_nr(m1, r1);
-  unsigned long long sbits = 0ull;
+  unsigned long long ubits = 0ull;
   if (upd) {
     const int g = I.lat_off + j;
     const int nxt = I.parity ^ 1;
@@ -495,15 +516,27 @@ __device__ void sweep_tile(const Dev& d, int ii, int j0) {
     d.M(nxt)[g] = m1;
     d.U(nxt)[g] = u1;
     if (!pos_finite_bits(r1) || !finite_bits(m1)) set_status(I, IMEXDS_ERR_NONPHYSICAL);
-    sbits = dbits(fabs(u1) + c_fluid.ph[C.ph].a);
+    ubits = dbits(fabs(u1));
   }
-  // the warp maximum of non-negative doubles is the maximum of their bit patterns: high words first, then
-  // the low words of the lanes holding the maximal high word (integer reductions, off the FP64 pipe)
-  const unsigned hi = (unsigned)(sbits >> 32);
-  const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
-  const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? (unsigned)sbits : 0u);
-  const unsigned long long wmax = ((unsigned long long)mhi << 32) | mlo;
-  if (lane == 0 && wmax != 0ull) atomicMax(&I.smax_bits, wmax);
+  // wave-speed maximum max_i(|u_i| + a_i): per phase the maximum of |u| plus that phase's sound speed, which is
+  // the same number (rounded addition is monotone) with one addition per phase and tile instead of one per cell.
+  // The warp maximum of non-negative doubles is the maximum of their bit patterns: high words first, then the
+  // low words of the lanes holding the maximal high word (integer reductions, off the FP64 pipe).
+  unsigned long long wmax[2];
+#pragma unroll
+  for (int P = 0; P < 2; ++P) {
+    const unsigned long long b = (C.ph == P) ? ubits : 0ull;
+    const unsigned hi = (unsigned)(b >> 32);
+    const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? (unsigned)b : 0u);
+    wmax[P] = ((unsigned long long)mhi << 32) | mlo;
+  }
+  const bool any0 = __any_sync(0xffffffffu, upd && C.ph == 0), any1 = __any_sync(0xffffffffu, upd && C.ph == 1);
+  if (lane == 0 && (any0 || any1)) {
+    const double s0 = any0 ? __longlong_as_double((long long)wmax[0]) + c_fluid.ph[0].a : 0.0;
+    const double s1 = any1 ? __longlong_as_double((long long)wmax[1]) + c_fluid.ph[1].a : 0.0;
+    atomicMax(&I.smax_bits, dbits(fmax(s0, s1)));
+  }
 }
 
 // Per-step sweep kernel: one warp per tile of the tile table.
@@ -629,6 +662,139 @@ __device__ __noinline__ bool dts_general(const Dev& d, Zone& Z, Inst& I, int e0,
       set_status(I, nonconv ? IMEXDS_ERR_PB_NOCONV : IMEXDS_ERR_VANISH);
       return false;
     }
+    for (int g = lo + 1; g <= hi; ++g)
+      if (B.fpb[g]) {
+        Z.pwl[g + e0] = gl[g];
+        Z.pwr[g + e0] = gr[g];
+      }
+    for (int q = lo; q <= hi; ++q) {
+      out_r[q] = (B.w[q] * B.r[q] - dt * (F0[q + 1] - F0[q])) / hl[q];
+      out_m[q] = (B.w[q] * B.m[q] - dt * (F1[q + 1] - F1[q])) / hl[q];
+      out_w[q] = hl[q];
+    }
+    for (int g = lo + 1; g <= hi; ++g)
+      if (B.fpb[g]) {
+        int e = g + e0;
+        moved[g] = 1;
+        xpb_new[g] = Z.fx[e] + wc[g] * dt;
+      }
+  }
+  return true;
+}
+
+// Newton on every block of a zone of any shape (the system of newton_simple, any block size): fluxes at the
+// iterate with the boundary faces' Jacobians (kept per face), the stop test, then the block-tridiagonal
+// Jacobian assembled into band storage (HLL faces' Jacobians evaluated here) and solve_band. Kept out of line.
+__device__ __noinline__ bool newton_general(const Dev& d, Zone& Z, Inst& I, int e0, int nq, const BlockCtx& B,
+                                           const double* Fx0, const double* Fx1, double* out_r, double* out_m,
+                                           double* out_w, double* xpb_new, int* moved, long long& newton,
+                                           long long& solves, long long& iters_sum, long long& iters_max,
+                                           long long& maxiter) {
+  const double dt = I.dt, tau = I.tau;
+  const double dtr = (c_opts.res_mode == 1) ? 1.0 : dt;
+  for (int b = 0; b < Z.nblk; ++b) {
+    const int lo = Z.blo[b] - e0, hi = Z.bhi[b] - e0;
+    const int n2 = 2 * (hi - lo + 1);
+    double Wr[ZB], Wm[ZB], F0[ZB + 1], F1[ZB + 1], wc[ZB + 1], hl[ZB], Tr[ZB], Tm[ZB];
+    FaceJac fj[ZB + 1];
+    double A[2 * ZB][BAND_W], rhs[2 * ZB];
+    for (int q = 0; q < nq; ++q) {
+      Wr[q] = B.r[q];
+      Wm[q] = B.m[q];
+    }
+    double gl[ZB + 1], gr[ZB + 1];
+    for (int g = 0; g <= nq; ++g) {
+      int e = g + e0;
+      bool zf = (e >= 1 && e <= Z.nc - 1);
+      gl[g] = zf ? Z.pwl[e] : 0.0;
+      gr[g] = zf ? Z.pwr[e] : 0.0;
+    }
+    // fluxes, face speeds and widths at (Wr, Wm); boundary faces' Jacobians into fj. 0 ok, 1 a boundary
+    // solve failed, 2 a width would vanish
+    auto fluxes = [&]() -> int {
+      F0[lo] = Fx0[lo];
+      F1[lo] = Fx1[lo];
+      F0[hi + 1] = Fx0[hi + 1];
+      F1[hi + 1] = Fx1[hi + 1];
+      wc[lo] = 0.0;
+      wc[hi + 1] = 0.0;
+      for (int g = lo + 1; g <= hi; ++g) {
+        if (B.fpb[g]) {
+          PBOut R = pb_solve_core<true>(c_fluid, c_opts, tau, B.ph[g - 1], Wr[g - 1], Wm[g - 1], B.ph[g], Wr[g],
+                                        Wm[g], gl[g], gr[g], &fj[g]);
+          newton += R.iters;
+          solves++;
+          if (!R.ok) return 1;
+          F0[g] = R.F0;
+          F1[g] = R.F1;
+          wc[g] = R.w;
+        } else {
+          hll_fast(c_fluid.ph[B.ph[g]], Wr[g - 1], Wm[g - 1], Wr[g], Wm[g], F0[g], F1[g]);
+          wc[g] = 0.0;
+        }
+      }
+      for (int q = lo; q <= hi; ++q) hl[q] = B.w[q] + (wc[q + 1] - wc[q]) * dt;
+      for (int q = lo; q <= hi; ++q)
+        if (!(hl[q] > 0.0)) return 2;
+      return 0;
+    };
+    bool stop = false;
+    int l, fail = 0;
+    for (l = 0; l < c_opts.l_max; ++l) {
+      fail = fluxes();
+      if (fail) break;
+      stop = true;
+      for (int q = lo; q <= hi; ++q) {
+        Tr[q] = (B.w[q] * B.r[q] - dt * (F0[q + 1] - F0[q])) / hl[q];
+        Tm[q] = (B.w[q] * B.m[q] - dt * (F1[q + 1] - F1[q])) / hl[q];
+        const double lim = (((Z.tiny_mask >> (q + e0 + 1)) & 1u) ? c_opts.tol_k : c_opts.tol_nb) * dtr;
+        stop = stop && (fabs(Tr[q] - Wr[q]) < lim * fmax(fabs(Wr[q]), 1.0)) &&
+               (fabs(Tm[q] - Wm[q]) < lim * fmax(fabs(Wm[q]), 1.0));
+      }
+      if (stop) break;
+      for (int g = lo + 1; g <= hi; ++g)
+        if (!B.fpb[g]) hll_jac(c_fluid.ph[B.ph[g]], Wr[g - 1], Wm[g - 1], Wr[g], Wm[g], fj[g]);
+      for (int r = 0; r < n2; ++r) {
+        for (int k = 0; k < BAND_W; ++k) A[r][k] = 0.0;
+        A[r][3] = 1.0;  // the identity (column r)
+      }
+      for (int q = lo; q <= hi; ++q) {
+        const int i = q - lo;
+        const double coef = dt / hl[q];
+        rhs[2 * i] = Tr[q] - Wr[q];
+        rhs[2 * i + 1] = Tm[q] - Wm[q];
+        for (int c = 0; c < 2; ++c) {
+          const int row = 2 * i + c;
+          const double Tq = c ? Tm[q] : Tr[q];
+          if (q + 1 <= hi) {  // right face: + coef (dF + T dw) on the columns of cells q, q+1
+            const FaceJac& J = fj[q + 1];
+            for (int k = 0; k < 4; ++k)
+              A[row][2 * i + k - row + 3] += coef * ((c ? J.dF1[k] : J.dF0[k]) + Tq * J.dw[k]);
+          }
+          if (q - 1 >= lo) {  // left face: - coef (dF + T dw) on the columns of cells q-1, q
+            const FaceJac& J = fj[q];
+            for (int k = 0; k < 4; ++k)
+              A[row][2 * (i - 1) + k - row + 3] -= coef * ((c ? J.dF1[k] : J.dF0[k]) + Tq * J.dw[k]);
+          }
+        }
+      }
+      if (!solve_band(A, rhs, n2)) {
+        fail = 3;
+        break;
+      }
+      for (int q = lo; q <= hi; ++q) {
+        Wr[q] += rhs[2 * (q - lo)];
+        Wm[q] += rhs[2 * (q - lo) + 1];
+      }
+    }
+    if (!fail && !stop) fail = fluxes();
+    if (fail) {
+      set_status(I, fail == 2 ? IMEXDS_ERR_VANISH : IMEXDS_ERR_PB_NOCONV);
+      return false;
+    }
+    if (!stop) maxiter++;
+    iters_sum += l;
+    iters_max = max(iters_max, (long long)l);
     for (int g = lo + 1; g <= hi; ++g)
       if (B.fpb[g]) {
         Z.pwl[g + e0] = gl[g];
@@ -817,24 +983,240 @@ __device__ void dts_simple(const Dev& d, int zi) {
   atomicAdd((unsigned long long*)&I.stats[8], (unsigned long long)solves);
 }
 
-__device__ void dts_zone_general(const Dev& d, int zi);
+// Newton's method on the implicit system of a block instead of dual time stepping (the paper's outlook, Sec. 5;
+// Sec. 3.3 notes that dual time is one way to solve that system). The system is R(W) = W - T(W) = 0, T the
+// update of Algorithm 2 Part 1 (Eq. godunov_meth:nonunif) with fluxes and widths at W; its root is the
+// dual-time limit. The Sec. 4 residual of an iterate W is |W - T(W)| / (dt max(|W|, 1)) component by
+// component (a pseudo step moves W by theta (T(W) - W) / (1 + theta)), so the same test stops Newton:
+//   stop  <=>  |T(W) - W| < tol dt' max(|W|, 1)  for every block cell (tol_k for tiny cells, tol_nb else),
+// dt' = dt (printed residual) or 1 (res dt). Each iteration: fluxes at W (the boundary solve also gives the
+// face Jacobian by the implicit function theorem, HLL faces theirs in closed form), T(W), the stop test, then
+// dR/dW = I - dT/dW assembled from the face Jacobians,
+//   dT_i/dW = -(dt / h_i) [(dF_{i+1/2} - dF_{i-1/2}) + T_i (dw_{i+1/2} - dw_{i-1/2})],
+// and one linear solve with partial pivoting. The iteration count reported is the number of Newton steps.
 
+// The common zone of dts_simple (three cells, the boundary at face PBF): a 6 x 6 system in registers.
+template <int PBF>
+__device__ __noinline__ void newton_simple(const Dev& d, int zi) {
+  Zone& Z = d.zones[zi];
+  Inst& I = d.inst[Z.inst];
+  const int cur = I.parity;
+  const double* lr = d.R(cur) + I.lat_off;
+  const double* lm = d.M(cur) + I.lat_off;
+  const unsigned char* lph = d.phase + I.lat_off;
+  const double dt = I.dt, h = I.h, tau = I.tau;
+  const int N = I.N;
+  const int jp = (PBF == 2) ? Z.A - 1 : Z.B;  // the pulled lattice cell
+  double Ur[3], Um[3], Uw[3];
+  int ph[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int e = (PBF == 2) ? q - 1 : q;
+    if (e < 0 || e > 1) {
+      Ur[q] = lr[jp];
+      Um[q] = lm[jp];
+      Uw[q] = h;
+      ph[q] = lph[jp];
+    } else {
+      Ur[q] = Z.r[e];
+      Um[q] = Z.m[e];
+      Uw[q] = Z.w[e];
+      ph[q] = Z.ph[e];
+    }
+  }
+  double FL0, FL1, FR0, FR1;
+  if (Z.oA > 0)
+    hll_fast(c_fluid.ph[ph[0]], lr[Z.oA - 1], lm[Z.oA - 1], Ur[0], Um[0], FL0, FL1);
+  else
+    phys_flux_fast(c_fluid.ph[ph[0]], Ur[0], Um[0], FL0, FL1);
+  if (Z.oB < N)
+    hll_fast(c_fluid.ph[ph[2]], Ur[2], Um[2], lr[Z.oB], lm[Z.oB], FR0, FR1);
+  else
+    phys_flux_fast(c_fluid.ph[ph[2]], Ur[2], Um[2], FR0, FR1);
+  const double dtr = (c_opts.res_mode == 1) ? 1.0 : dt;
+  double lim[3], hU0[3], hU1[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int e = (PBF == 2) ? q - 1 : q;
+    const bool tiny = (Z.tiny_mask >> (e + 1)) & 1u;
+    lim[q] = (tiny ? c_opts.tol_k : c_opts.tol_nb) * dtr;
+    hU0[q] = Uw[q] * Ur[q];
+    hU1[q] = Uw[q] * Um[q];
+  }
+  constexpr int a = PBF - 1;             // boundary between cells a and a+1
+  constexpr int b = (PBF == 1) ? 2 : 1;  // fixed interior face between cells b-1 and b
+  double gl = Z.pwl[1], gr = Z.pwr[1];
+  double W0[3] = {Ur[0], Ur[1], Ur[2]}, W1[3] = {Um[0], Um[1], Um[2]};
+  long long newton = 0, solves = 0;
+  double Fp0 = 0.0, Fp1 = 0.0, wpb = 0.0, Fh0 = 0.0, Fh1 = 0.0;
+  FaceJac Jp;
+  auto face = [&](int g, double& f0, double& f1) {
+    if (g == 0) {
+      f0 = FL0;
+      f1 = FL1;
+    } else if (g == 3) {
+      f0 = FR0;
+      f1 = FR1;
+    } else if (g == PBF) {
+      f0 = Fp0;
+      f1 = Fp1;
+    } else {
+      f0 = Fh0;
+      f1 = Fh1;
+    }
+  };
+  // fluxes at W and the boundary's face Jacobian; widths of the two boundary cells
+  double ha = 0.0, hb = 0.0;
+  auto fluxes = [&]() -> int {  // 0 ok, 1 boundary solve failed, 2 a width would vanish
+    hll_fast(c_fluid.ph[ph[b]], W0[b - 1], W1[b - 1], W0[b], W1[b], Fh0, Fh1);
+    PBOut R = pb_solve_core<true>(c_fluid, c_opts, tau, ph[a], W0[a], W1[a], ph[a + 1], W0[a + 1], W1[a + 1], gl,
+                                  gr, &Jp);
+    newton += R.iters;
+    solves++;
+    if (!R.ok) return 1;
+    Fp0 = R.F0;
+    Fp1 = R.F1;
+    wpb = R.w;
+    ha = Uw[a] + (wpb - 0.0) * dt;
+    hb = Uw[a + 1] + (0.0 - wpb) * dt;
+    if (!(ha > 0.0) || !(hb > 0.0)) return 2;
+    return 0;
+  };
+  bool stop = false;
+  int l, fail = 0;
+  double T0[3], T1[3], ih[3];
+  for (l = 0; l < c_opts.l_max; ++l) {
+    fail = fluxes();
+    if (fail) break;
+    ih[a] = 1.0 / ha;
+    ih[a + 1] = 1.0 / hb;
+    ih[(PBF == 1) ? 2 : 0] = 1.0 / Uw[(PBF == 1) ? 2 : 0];
+    stop = true;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      double f0l, f1l, f0r, f1r;
+      face(q, f0l, f1l);
+      face(q + 1, f0r, f1r);
+      T0[q] = (hU0[q] - dt * (f0r - f0l)) * ih[q];
+      T1[q] = (hU1[q] - dt * (f1r - f1l)) * ih[q];
+      stop = stop && (fabs(T0[q] - W0[q]) < lim[q] * fmax(fabs(W0[q]), 1.0)) &&
+             (fabs(T1[q] - W1[q]) < lim[q] * fmax(fabs(W1[q]), 1.0));
+    }
+    if (stop) break;
+    // dR/dW = I - dT/dW (rows and columns (q, component)), right-hand side T - W
+    FaceJac Jh;
+    hll_jac(c_fluid.ph[ph[b]], W0[b - 1], W1[b - 1], W0[b], W1[b], Jh);
+    double A[6][7];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) A[r][c] = (r == c) ? 1.0 : 0.0;
+      A[r][6] = (r & 1) ? T1[r >> 1] - W1[r >> 1] : T0[r >> 1] - W0[r >> 1];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const double coef = dt * ih[q];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const double Tq = c ? T1[q] : T0[q];
+        if (q + 1 <= 2) {  // right face q+1: + coef (dF + T dw), columns of cells q, q+1
+          const FaceJac& J = (q + 1 == PBF) ? Jp : Jh;
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            A[2 * q + c][2 * q + k] += coef * ((c ? J.dF1[k] : J.dF0[k]) + Tq * J.dw[k]);
+        }
+        if (q >= 1) {  // left face q: - coef (dF + T dw), columns of cells q-1, q
+          const FaceJac& J = (q == PBF) ? Jp : Jh;
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            A[2 * q + c][2 * (q - 1) + k] -= coef * ((c ? J.dF1[k] : J.dF0[k]) + Tq * J.dw[k]);
+        }
+      }
+    }
+    if (!solve_dense<6>(A)) {
+      fail = 3;
+      break;
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      W0[q] += A[2 * q][6];
+      W1[q] += A[2 * q + 1][6];
+    }
+  }
+  // Part 2 needs the fluxes at U^{n,*}: those of the last evaluation when the test stopped the iteration,
+  // else evaluated at the last iterate
+  if (!fail && !stop) fail = fluxes();
+  if (fail) {
+    set_status(I, fail == 2 ? IMEXDS_ERR_VANISH : IMEXDS_ERR_PB_NOCONV);
+    return;
+  }
+  double* nr = d.R(cur ^ 1) + I.lat_off;
+  double* nm = d.M(cur ^ 1) + I.lat_off;
+  double* nu = d.U(cur ^ 1) + I.lat_off;
+  double smax = 0.0;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    double f0l, f1l, f0r, f1r;
+    face(q, f0l, f1l);
+    face(q + 1, f0r, f1r);
+    const double hn1 = (q == a) ? ha : ((q == a + 1) ? hb : Uw[q]);
+    const double r1 = (hU0[q] - dt * (f0r - f0l)) / hn1;
+    const double m1 = (hU1[q] - dt * (f1r - f1l)) / hn1;
+    if (!(r1 > 0.0) || !isfinite(r1) || !isfinite(m1)) set_status(I, IMEXDS_ERR_NONPHYSICAL);
+    const double u1 = div_nr(m1, r1);
+    smax = fmax(smax, fabs(u1) + c_fluid.ph[ph[q]].a);
+    const int e = (PBF == 2) ? q - 1 : q;
+    if (e < 0 || e > 1) {
+      nr[jp] = r1;
+      nm[jp] = m1;
+      nu[jp] = u1;
+    } else {
+      Z.r[e] = r1;
+      Z.m[e] = m1;
+      Z.w[e] = hn1;
+    }
+  }
+  Z.pwl[1] = gl;
+  Z.pwr[1] = gr;
+  Z.fx[1] = Z.fx[1] + wpb * dt;
+  if (smax > 0.0) atomicMax(&I.smax_bits, dbits(smax));
+  atomicAdd((unsigned long long*)&I.stats[1], (unsigned long long)l);
+  atomicMax((unsigned long long*)&I.stats[2], (unsigned long long)l);
+  atomicAdd((unsigned long long*)&I.stats[3], (unsigned long long)newton);
+  if (!stop) atomicAdd((unsigned long long*)&I.stats[7], 1ull);
+  atomicAdd((unsigned long long*)&I.stats[8], (unsigned long long)solves);
+}
+
+template <bool NEWTON>
+__device__ __noinline__ void dts_zone_general(const Dev& d, int zi);
+
+// NEWTON: the kernel was launched for options.block_solver = 1 (Newton on each block); a template parameter so
+// that the dual-time kernels carry none of the Newton code.
+template <bool NEWTON>
 __device__ void dts_zone(const Dev& d, int zi) {
   Zone& Z = d.zones[zi];
   if (!Z.alive) return;
   const Inst& I = d.inst[Z.inst];
   if (!I.active || I.status) return;
   if (Z.nc == 2 && Z.fpb[1] && Z.nblk == 1 && (Z.pullL + Z.pullR) == 1) {
-    if (Z.pullL)
-      dts_simple<2>(d, zi);
-    else
-      dts_simple<1>(d, zi);
+    if (NEWTON) {
+      if (Z.pullL)
+        newton_simple<2>(d, zi);
+      else
+        newton_simple<1>(d, zi);
+    } else {
+      if (Z.pullL)
+        dts_simple<2>(d, zi);
+      else
+        dts_simple<1>(d, zi);
+    }
     return;
   }
-  dts_zone_general(d, zi);
+  dts_zone_general<NEWTON>(d, zi);
 }
 
 // Algorithm 2 for any zone shape (blocks of any size, zone cells outside the blocks), kept out of line.
+template <bool NEWTON>
 __device__ __noinline__ void dts_zone_general(const Dev& d, int zi) {
   Zone& Z = d.zones[zi];
   Inst& I = d.inst[Z.inst];
@@ -899,21 +1281,68 @@ __device__ __noinline__ void dts_zone_general(const Dev& d, int zi) {
   for (int q = 0; q < nq; ++q) inblk[q] = 0;
   for (int b = 0; b < Z.nblk; ++b)
     for (int q = Z.blo[b] - e0; q <= Z.bhi[b] - e0; ++q) inblk[q] = 1;
+  long long newton = 0, solves = 0, iters_sum = 0, iters_max = 0, maxiter = 0;
+  // Phase creation (App. B) at the zone's own faces between two explicit cells of one phase: the interior
+  // faces of a zone joined from two boundary neighbourhoods (the lattice sweep examines the faces between
+  // free lattice cells; a zone's first and last cells are boundary cells and lie in blocks). Detection by the
+  // no-transition star pressure at U^n; a face whose left neighbour face is also detected is not used. The
+  // cell left of a creation face sees the flux with the left boundary's mass flux and a face moving with w1,
+  // the cell right of it the right boundary's and w2 (Eq. flux:cavitation / flux:nucleation); the created
+  // cell is inserted into the zone after the step's update.
+  bool cre[ZB + 1];
+  double cF0L[ZB + 1], cF1L[ZB + 1], cF0R[ZB + 1], cF1R[ZB + 1], cW1[ZB + 1], cW2[ZB + 1], cRho[ZB + 1], cM[ZB + 1];
+  int n_cre = 0;
+  for (int q = 0; q <= nq; ++q) cre[q] = false;
+  if (c_opts.creation) {
+    bool det_prev = false;
+    for (int q = 1; q < nq; ++q) {
+      bool det = false;
+      if (!B.fpb[q] && !inblk[q - 1] && !inblk[q])
+        det = creation_detect(c_fluid, B.ph[q], B.r[q - 1], div_nr(B.m[q - 1], B.r[q - 1]), B.r[q],
+                              div_nr(B.m[q], B.r[q]));
+      if (det && !det_prev) {
+        CreateOut Cr = creation_solve(c_fluid, c_opts, I.tau, B.ph[q], B.r[q - 1], B.m[q - 1], B.r[q], B.m[q]);
+        newton += Cr.iters;
+        if (!Cr.ok) {
+          set_status(I, IMEXDS_ERR_PB_NOCONV);
+          return;
+        }
+        cre[q] = true;
+        cF0L[q] = -Cr.z1;
+        cF1L[q] = -Cr.z1 * Cr.uC + Cr.pC;
+        cF0R[q] = -Cr.z2;
+        cF1R[q] = -Cr.z2 * Cr.uC + Cr.pC;
+        cW1[q] = Cr.w1;
+        cW2[q] = Cr.w2;
+        cRho[q] = Cr.rhoC;
+        cM[q] = Cr.rhoC * Cr.uC;
+        n_cre++;
+      }
+      det_prev = det;
+    }
+  }
   double out_r[ZB], out_m[ZB], out_w[ZB];
   for (int q = 0; q < nq; ++q) {
     out_w[q] = B.w[q];
     if (inblk[q]) continue;
-    double hnp1 = B.w[q] + (0.0 - 0.0) * dt;
-    out_r[q] = (B.w[q] * B.r[q] - dt * (Fx0[q + 1] - Fx0[q])) / hnp1;
-    out_m[q] = (B.w[q] * B.m[q] - dt * (Fx1[q + 1] - Fx1[q])) / hnp1;
+    // fluxes seen at the left / right face and the face speeds (non-zero at a creation face only)
+    const double fl0 = cre[q] ? cF0R[q] : Fx0[q], fl1 = cre[q] ? cF1R[q] : Fx1[q];
+    const double fr0 = cre[q + 1] ? cF0L[q + 1] : Fx0[q + 1], fr1 = cre[q + 1] ? cF1L[q + 1] : Fx1[q + 1];
+    const double wl = cre[q] ? cW2[q] : 0.0, wr = cre[q + 1] ? cW1[q + 1] : 0.0;
+    double hnp1 = B.w[q] + (wr - wl) * dt;
+    out_r[q] = (B.w[q] * B.r[q] - dt * (fr0 - fl0)) / hnp1;
+    out_m[q] = (B.w[q] * B.m[q] - dt * (fr1 - fl1)) / hnp1;
+    out_w[q] = hnp1;
   }
-  long long newton = 0, solves = 0, iters_sum = 0, iters_max = 0, maxiter = 0;
   double xpb_new[ZB + 1];
   int moved[ZB + 1];
   for (int q = 0; q <= nq; ++q) moved[q] = 0;
-  if (!dts_general(d, Z, I, e0, nq, B, Fx0, Fx1, out_r, out_m, out_w, xpb_new, moved, newton, solves, iters_sum,
-                   iters_max, maxiter))
-    return;
+  const bool ok = NEWTON
+                      ? newton_general(d, Z, I, e0, nq, B, Fx0, Fx1, out_r, out_m, out_w, xpb_new, moved, newton,
+                                       solves, iters_sum, iters_max, maxiter)
+                      : dts_general(d, Z, I, e0, nq, B, Fx0, Fx1, out_r, out_m, out_w, xpb_new, moved, newton, solves,
+                                    iters_sum, iters_max, maxiter);
+  if (!ok) return;
   double smax = 0.0;
   double* nu = d.U(cur ^ 1) + I.lat_off;
   for (int q = 0; q < nq; ++q) {
@@ -938,6 +1367,30 @@ __device__ __noinline__ void dts_zone_general(const Dev& d, int zi) {
   }
   for (int q = 1; q < nq; ++q)
     if (moved[q]) Z.fx[q + e0] = xpb_new[q];
+  if (n_cre) {
+    // insert the created cells, right to left so that the indices of the faces still to visit hold
+    for (int q = nq - 1; q >= 1; --q) {
+      if (!cre[q]) continue;
+      const int e = q + e0;  // zone face between zone cells e-1 and e (both explicit, hence zone cells)
+      const double xf = I.xL + (double)Z.fj[e] * h;
+      if (!zone_insert_cell(Z, e)) {
+        set_status(I, IMEXDS_ERR_CAPACITY);
+        return;
+      }
+      Z.w[e] = (cW2[q] - cW1[q]) * dt;
+      Z.r[e] = cRho[q];
+      Z.m[e] = cM[q];
+      Z.ph[e] = 1 - B.ph[q];
+      Z.fpb[e] = 1;
+      Z.fx[e] = xf + cW1[q] * dt;
+      Z.fpb[e + 1] = 1;
+      Z.fx[e + 1] = xf + cW2[q] * dt;
+      Z.pwl[e] = Z.pwr[e] = Z.pwl[e + 1] = Z.pwr[e + 1] = 0.0;
+      smax = fmax(smax, fabs(cM[q] / cRho[q]) + c_fluid.ph[1 - B.ph[q]].a);
+    }
+    Z.changed = 1;
+    atomicAdd((unsigned long long*)&I.stats[6], (unsigned long long)n_cre);
+  }
   if (smax > 0.0) atomicMax(&I.smax_bits, dbits(smax));
   atomicAdd((unsigned long long*)&I.stats[1], (unsigned long long)iters_sum);
   atomicMax((unsigned long long*)&I.stats[2], (unsigned long long)iters_max);
@@ -951,24 +1404,6 @@ __device__ __noinline__ void dts_zone_general(const Dev& d, int zi) {
 // split boundary cells wider than split_ratio*h (keeping fixed faces on the lattice), return regular
 // cells at the zone ends to the lattice, turn creation events into zones, join zones closer than
 // ZONE_GAP, then advance t and set the next dt from the wave-speed maximum.
-__device__ inline int zone_insert_cell(Zone& Z, int pos) {
-  if (Z.nc >= ZC) return 0;
-  for (int i = Z.nc; i > pos; --i) {
-    Z.w[i] = Z.w[i - 1];
-    Z.r[i] = Z.r[i - 1];
-    Z.m[i] = Z.m[i - 1];
-    Z.ph[i] = Z.ph[i - 1];
-  }
-  for (int k = Z.nc + 1; k > pos; --k) {
-    Z.fpb[k] = Z.fpb[k - 1];
-    Z.fj[k] = Z.fj[k - 1];
-    Z.fx[k] = Z.fx[k - 1];
-    Z.pwl[k] = Z.pwl[k - 1];
-    Z.pwr[k] = Z.pwr[k - 1];
-  }
-  Z.nc++;
-  return 1;
-}
 
 __device__ __noinline__ void post_inst(const Dev& d, int ii) {
   Inst& I = d.inst[ii];
@@ -1283,9 +1718,10 @@ __global__ void k_plan(Dev d, int n) {
   int zi = blockIdx.x * blockDim.x + threadIdx.x;
   if (zi < n && zone_active(d, zi)) plan_zone(d, zi);
 }
+template <bool NEWTON>
 __global__ void k_dts(Dev d, int n) {
   int zi = blockIdx.x * blockDim.x + threadIdx.x;
-  if (zi < n && zone_active(d, zi)) dts_zone(d, zi);
+  if (zi < n && zone_active(d, zi)) dts_zone<NEWTON>(d, zi);
 }
 __global__ void k_post(Dev d, int n) {
   int ii = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1299,11 +1735,17 @@ __global__ void k_post(Dev d, int n) {
 constexpr int GROUP_MAX = 32;
 // NT: the CTA width the kernel is compiled for (128: two CTAs per SM, three sweep warps; 256: one CTA per SM,
 // seven sweep warps); launched with at most NT threads.
-template <bool CREATION, int NT>
+template <bool CREATION, int NT, bool NEWTON>
 __global__ void __launch_bounds__(NT, (NT <= 128 ? 2 : 1)) k_group(Dev d, const int* ginst, const int2* grange, int max_steps,
                                                long long* phase_cycles) {
   const int2 gr = grange[blockIdx.x];
-  long long cyc[4] = {0, 0, 0, 0};  // pre+plan, sweep (warp 1), dual time (warp 0), post
+  // SM clock cycles per phase (timing mode; the layout of imexds_get_group_phase_cycles): 0 boundary solves +
+  // plan, 1 sweep (first sweep warp), 2 dual time (warp 0), 3 grid management, 4 the concurrent phase
+  // (barrier to barrier: the longer of 1 and 2), 5 the whole launch. Phases 0, 3 and 4 are intervals between
+  // the block's barriers read by thread 0, so 0 + 4 + 3 = 5 up to the loop's own instructions; 1 and 2 are
+  // read after __syncwarp (every lane of the warp done) and lie within 4.
+  long long cyc[6] = {0, 0, 0, 0, 0, 0};
+  const long long c_start = clock64();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
   const int ii = (lane < gr.y) ? ginst[gr.x + lane] : -1;
@@ -1328,8 +1770,9 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 2 : 1)) k_group(Dev d, const 
         Inst& I = d.inst[ii];
         if (I.active && !I.status)
           for (int z = I.zone_off; z < I.zone_off + I.zone_cap; ++z)
-            if (d.zones[z].alive && !I.status) dts_zone(d, z);
+            if (d.zones[z].alive && !I.status) dts_zone<NEWTON>(d, z);
       }
+      __syncwarp();
       cyc[2] += clock64() - c1;
     } else {
       // the tiles of all active instances of the group, dealt to warps 1..nw-1
@@ -1341,11 +1784,13 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 2 : 1)) k_group(Dev d, const 
         for (; t < base + nt; t += nw - 1) sweep_tile<CREATION>(d, ik, (t - base) * TILE);
         base += nt;
       }
+      __syncwarp();
       cyc[1] += clock64() - c1;
     }
     __syncthreads();
     long long c2 = clock64();
     cyc[0] += c1 - c0;
+    cyc[4] += c2 - c1;
     if (warp == 0 && ii >= 0 && d.inst[ii].active) post_inst(d, ii);
     if (threadIdx.x == 0) s_more = 0;
     __syncthreads();
@@ -1354,13 +1799,17 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 2 : 1)) k_group(Dev d, const 
     cyc[3] += clock64() - c2;
     if (!s_more) break;
   }
+  cyc[5] = clock64() - c_start;
   if (phase_cycles && lane == 0 && warp <= 1) {
+    long long* pc = phase_cycles + 6 * blockIdx.x;
     if (warp == 0) {
-      phase_cycles[4 * blockIdx.x + 0] += cyc[0];
-      phase_cycles[4 * blockIdx.x + 2] += cyc[2];
-      phase_cycles[4 * blockIdx.x + 3] += cyc[3];
+      pc[0] += cyc[0];
+      pc[2] += cyc[2];
+      pc[3] += cyc[3];
+      pc[4] += cyc[4];
+      pc[5] += cyc[5];
     } else {
-      phase_cycles[4 * blockIdx.x + 1] += cyc[1];
+      pc[1] += cyc[1];
     }
   }
 }
@@ -1377,7 +1826,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 2 : 1)) k_group(Dev d, const 
 // after kWaitCycles. The per-instance work and its order are those of k_group: the results are the same.
 constexpr long long kWaitCycles = 40000000000LL;  // ~20 s at 2 GHz
 
-template <bool CREATION>
+template <bool CREATION, bool NEWTON>
 __global__ void __launch_bounds__(128, 2) k_group_async(Dev d, const int* ginst, const int2* grange, int max_steps,
                                                      long long* phase_cycles) {
   const int2 gr = grange[blockIdx.x];
@@ -1426,7 +1875,7 @@ __global__ void __launch_bounds__(128, 2) k_group_async(Dev d, const int* ginst,
       long long c1 = clock64();
       if (!I.status)
         for (int z = I.zone_off; z < I.zone_off + I.zone_cap; ++z)
-          if (d.zones[z].alive && !I.status) dts_zone(d, z);
+          if (d.zones[z].alive && !I.status) dts_zone<NEWTON>(d, z);
       long long c2 = clock64();
       bool timeout = false;
       const int need = ((volatile int*)s_ntiles)[lane];  // every ticket issued for this step is swept first
@@ -1456,10 +1905,14 @@ __global__ void __launch_bounds__(128, 2) k_group_async(Dev d, const int* ginst,
     __threadfence_block();
     atomicSub(&s_alive, 1);
     if (phase_cycles) {
-      // the slowest lane of the group: its boundary solves + plan, dual time, waits for the sweep, post
-      atomicMax((unsigned long long*)&phase_cycles[4 * blockIdx.x + 0], (unsigned long long)cp);
-      atomicMax((unsigned long long*)&phase_cycles[4 * blockIdx.x + 2], (unsigned long long)cd);
-      atomicMax((unsigned long long*)&phase_cycles[4 * blockIdx.x + 3], (unsigned long long)(cq + cw));
+      // the slowest lane of the group: its boundary solves + plan, dual time, dual time plus the wait for the
+      // sweep, grid management, and its whole run
+      unsigned long long* pc = (unsigned long long*)(phase_cycles + 6 * blockIdx.x);
+      atomicMax(&pc[0], (unsigned long long)cp);
+      atomicMax(&pc[2], (unsigned long long)cd);
+      atomicMax(&pc[3], (unsigned long long)cq);
+      atomicMax(&pc[4], (unsigned long long)(cd + cw));
+      atomicMax(&pc[5], (unsigned long long)(cp + cd + cw + cq));
     }
     return;
   }
@@ -1502,7 +1955,7 @@ __global__ void __launch_bounds__(128, 2) k_group_async(Dev d, const int* ginst,
       if (clock64() - idle0 > kWaitCycles) break;
     }
   }
-  if (phase_cycles && lane == 0) atomicMax((unsigned long long*)&phase_cycles[4 * blockIdx.x + 1], (unsigned long long)busy);
+  if (phase_cycles && lane == 0) atomicMax((unsigned long long*)&phase_cycles[6 * blockIdx.x + 1], (unsigned long long)busy);
 }
 
 // u = m / rho of every lattice cell, with the quotient the kernels use (set_states)
@@ -1726,7 +2179,10 @@ void launch_step_forked(imexds_ctx* c) {
   k_plan<<<zb, zt, 0, c->stream>>>(c->d, c->n_zone_slots);
   cudaEventRecord(c->fork_ev, c->stream);
   cudaStreamWaitEvent(c->side, c->fork_ev, 0);
-  k_dts<<<zb, zt, 0, c->side>>>(c->d, c->n_zone_slots);
+  if (c->opts.block_solver == 1)
+    k_dts<true><<<zb, zt, 0, c->side>>>(c->d, c->n_zone_slots);
+  else
+    k_dts<false><<<zb, zt, 0, c->side>>>(c->d, c->n_zone_slots);
   cudaEventRecord(c->join_ev, c->side);
   const int sb = (c->n_tiles + 7) / 8;
   if (c->opts.creation)
@@ -1753,7 +2209,10 @@ void launch_step(imexds_ctx* c, cudaEvent_t* ev = nullptr) {
   else
     k_sweep<false><<<sb, 256, 0, c->stream>>>(c->d, c->n_tiles);
   if (ev) cudaEventRecord(ev[3], c->stream);
-  k_dts<<<zb, zt, 0, c->stream>>>(c->d, c->n_zone_slots);
+  if (c->opts.block_solver == 1)
+    k_dts<true><<<zb, zt, 0, c->stream>>>(c->d, c->n_zone_slots);
+  else
+    k_dts<false><<<zb, zt, 0, c->stream>>>(c->d, c->n_zone_slots);
   if (ev) cudaEventRecord(ev[4], c->stream);
   k_post<<<ib, zt, 0, c->stream>>>(c->d, c->n_inst);
   if (ev) cudaEventRecord(ev[5], c->stream);
@@ -1780,6 +2239,32 @@ imexds_status set_ctrl(imexds_ctx* c, double t_end, int clip) {
   return IMEXDS_OK;
 }
 
+// The group-resident kernel for the context's schedule, creation option and block solver.
+template <bool CREATION, bool NEWTON>
+void launch_group_t(imexds_ctx* c, int n, long long* pc) {
+  if (c->async_groups && c->group_threads <= 128)
+    k_group_async<CREATION, NEWTON><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n,
+                                                                                      pc);
+  else if (c->group_threads > 128)
+    k_group<CREATION, 256, NEWTON><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n,
+                                                                                     pc);
+  else
+    k_group<CREATION, 128, NEWTON><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n,
+                                                                                     pc);
+}
+
+void launch_group(imexds_ctx* c, int n, long long* pc) {
+  const bool cr = c->opts.creation != 0, nw = c->opts.block_solver == 1;
+  if (cr && nw)
+    launch_group_t<true, true>(c, n, pc);
+  else if (cr)
+    launch_group_t<true, false>(c, n, pc);
+  else if (nw)
+    launch_group_t<false, true>(c, n, pc);
+  else
+    launch_group_t<false, false>(c, n, pc);
+}
+
 imexds_status run_groups(imexds_ctx* c, long long max_steps, bool until_done) {
   // one launch advances every group until its instances are done (or max_steps steps)
   long long done = 0;
@@ -1788,28 +2273,14 @@ imexds_status run_groups(imexds_ctx* c, long long max_steps, bool until_done) {
     CK(cudaEventCreate(&c->gev[1]));
   }
   if (c->timing && !c->d_phase) {
-    CK(cudaMalloc(&c->d_phase, sizeof(long long) * 4 * c->n_groups));
-    CK(cudaMemsetAsync(c->d_phase, 0, sizeof(long long) * 4 * c->n_groups, c->stream));
+    CK(cudaMalloc(&c->d_phase, sizeof(long long) * 6 * c->n_groups));
+    CK(cudaMemsetAsync(c->d_phase, 0, sizeof(long long) * 6 * c->n_groups, c->stream));
   }
   long long* pc = c->timing ? c->d_phase : nullptr;
   while (done < max_steps) {
     int n = (int)std::min<long long>(max_steps - done, 1 << 30);
     if (c->timing) cudaEventRecord(c->gev[0], c->stream);
-    if (c->async_groups && c->group_threads <= 128) {
-      if (c->opts.creation)
-        k_group_async<true><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n, pc);
-      else
-        k_group_async<false><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n, pc);
-    } else if (c->group_threads > 128) {
-      if (c->opts.creation)
-        k_group<true, 256><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n, pc);
-      else
-        k_group<false, 256><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n, pc);
-    } else if (c->opts.creation) {
-      k_group<true, 128><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n, pc);
-    } else {
-      k_group<false, 128><<<c->n_groups, c->group_threads, 0, c->stream>>>(c->d, c->d_ginst, c->d_grange, n, pc);
-    }
+    launch_group(c, n, pc);
     if (c->timing) cudaEventRecord(c->gev[1], c->stream);
     k_count_active<<<1, 256, 0, c->stream>>>(c->d, c->n_inst);
     c->launches += 2;
@@ -1969,13 +2440,15 @@ imexds_status imexds_create(const imexds_problem* prob, const imexds_options* op
     o.schedule = 0;
     o.group_cells = 0;
     o.group_threads = 0;
+    o.block_solver = 0;
   }
-  if (!(o.cfl > 0.0) || o.l_max < 1 || o.newton_itmax < 1 || !(o.split_ratio > 1.0)) {
+  if (!(o.cfl > 0.0) || o.l_max < 1 || o.newton_itmax < 1 || !(o.split_ratio > 1.0) || o.block_solver < 0 ||
+      o.block_solver > 1) {
     delete c;
     return IMEXDS_ERR_ARG;
   }
   c->opts = Opts{o.cfl, o.theta_nb, o.tol_nb, o.tol_k, o.res_mode, o.l_max, o.newton_tol, o.newton_itmax,
-                 o.alpha_min, o.split_ratio, o.creation};
+                 o.alpha_min, o.split_ratio, o.creation, o.block_solver};
   c->zone_cap_opt = o.zone_capacity;
   if (o.schedule < 0 || o.schedule > 3) {
     delete c;
@@ -2418,6 +2891,7 @@ imexds_status imexds_set_kernel_timing(imexds_ctx* c, int32_t on) {
     c->kt_ms[k] = 0.0;
     c->kt_n[k] = 0;
   }
+  if (c->d_phase) CK(cudaMemsetAsync(c->d_phase, 0, sizeof(long long) * 6 * c->n_groups, c->stream));
   return IMEXDS_OK;
 }
 
@@ -2521,23 +2995,18 @@ imexds_status imexds_step_uniform_noalloc(const imexds_fluid* fluid, double cfl,
   return IMEXDS_OK;
 }
 
-imexds_status imexds_get_group_phase_cycles(imexds_ctx* c, int64_t* slowest4, int64_t* sum4) {
-  if (!c || !slowest4 || !sum4) return IMEXDS_ERR_ARG;
-  for (int k = 0; k < 4; ++k) slowest4[k] = sum4[k] = 0;
+imexds_status imexds_get_group_phase_cycles(imexds_ctx* c, int64_t* slowest6, int64_t* sum6) {
+  if (!c || !slowest6 || !sum6) return IMEXDS_ERR_ARG;
+  for (int k = 0; k < 6; ++k) slowest6[k] = sum6[k] = 0;
   if (!c->d_phase) return IMEXDS_OK;
-  std::vector<long long> h(4 * c->n_groups);
+  std::vector<long long> h(6 * c->n_groups);
   CK(cudaMemcpy(h.data(), c->d_phase, sizeof(long long) * h.size(), cudaMemcpyDeviceToHost));
   int worst = 0;
-  long long wt = -1;
   for (int g = 0; g < c->n_groups; ++g) {
-    long long t = h[4 * g] + std::max(h[4 * g + 1], h[4 * g + 2]) + h[4 * g + 3];
-    if (t > wt) {
-      wt = t;
-      worst = g;
-    }
-    for (int k = 0; k < 4; ++k) sum4[k] += h[4 * g + k];
+    if (h[6 * g + 5] > h[6 * worst + 5]) worst = g;
+    for (int k = 0; k < 6; ++k) sum6[k] += h[6 * g + k];
   }
-  for (int k = 0; k < 4; ++k) slowest4[k] = h[4 * worst + k];
+  for (int k = 0; k < 6; ++k) slowest6[k] = h[6 * worst + k];
   return IMEXDS_OK;
 }
 

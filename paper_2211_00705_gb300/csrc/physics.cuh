@@ -9,19 +9,18 @@
 
 namespace imexds {
 
-// Reciprocal by Newton-Raphson refinement of the hardware estimate (PTX rcp.approx.ftz.f64, ~23 bits):
-// two steps y <- y + y (1 - b y) reach full double precision (error squared per step); a / b is then a
-// times it, within 2 ulp of the correctly rounded quotient (checked against CUDA's division by
-// imexds_check_div). Used where the same quotient is formed by several kernels (the lattice velocity
-// m / rho, the HLL weight 1 / (S_R - S_L)), so that all of them produce the same bits. Arguments are
-// normal, non-zero doubles (densities, wave-speed spans).
+// Reciprocal refined from the hardware estimate (PTX rcp.approx.ftz.f64, ~23 correct bits) by one third-order
+// step of the series 1/b = y / (b y) = y / (1 - e) = y (1 + e + e^2 + ...), e = 1 - b y: y' = y + y (e + e^2),
+// three fused multiply-adds whose truncation error e^3 (~2^-66) lies far below double precision (two Newton-
+// Raphson steps reach the same accuracy with four). a / b is then a times it, within 2 ulp of the correctly
+// rounded quotient (checked against CUDA's division by imexds_check_div). Used where the same quotient is formed
+// by several kernels (the lattice velocity m / rho, the HLL weight 1 / (S_R - S_L)), so that all of them produce
+// the same bits. Arguments are normal, non-zero doubles (densities, wave-speed spans).
 __device__ __forceinline__ double rcp_nr(double b) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(b));
-  double e = __fma_rn(-b, y, 1.0);
-  y = __fma_rn(y, e, y);
-  e = __fma_rn(-b, y, 1.0);
-  return __fma_rn(y, e, y);
+  const double e = __fma_rn(-b, y, 1.0);
+  return __fma_rn(y, __fma_rn(e, e, e), y);
 }
 __device__ __forceinline__ double div_nr(double a, double b) { return a * rcp_nr(b); }
 
@@ -79,6 +78,7 @@ struct Opts {
   int newton_itmax;
   double alpha_min, split_ratio;
   int creation;
+  int block_solver;  // 0: dual time stepping on each implicit block (Alg. 2); 1: Newton on the block's system
 };
 
 __host__ __device__ inline double pressure(const Phase& e, double rho) {
@@ -348,10 +348,29 @@ __device__ inline int pbf_newton(const Fluid& F, const Opts& o, const SideData& 
   return conv ? 1 : 0;
 }
 
+// Derivatives of one face's flux (F0, F1) and speed w with respect to the states next to it,
+// d/d(rho_l, m_l, rho_r, m_r); the Jacobian rows of Newton's method on an implicit block.
+struct FaceJac {
+  double dF0[4], dF1[4], dw[4];
+};
+
+// d f_K / d rho_K at a fixed star pressure for the outer wave of App. A (isothermal linear EOS): rarefaction
+// f = a ln(rho*/rho_K) gives -a / rho_K; shock f = (p* - p_K) / (a sqrt(rho_K rho*)) (the same function as
+// sqrt((p* - p_K)(v_K - v*)), since p* - p_K = a^2 (rho* - rho_K)) gives -a / sqrt(rho_K rho*) - f / (2 rho_K).
+// Both tend to -a / rho_K as p* -> p_K.
+__device__ inline double dwave_drhoK(const Phase& e, const SideData& s, double p, double v, double f) {
+  if (p > s.pK && f > 0.0) return -e.a * rsqrt(s.rK / v) - 0.5 * f * s.invK;
+  return -e.a * s.invK;
+}
+
 // Boundary solve with an optional start (gl, gr > 0 ... valid pressures); writes the converged star
-// pressures back to gl/gr for the next call.
-__device__ inline PBOut pb_solve_warm(const Fluid& F, const Opts& o, double tau, int phl, double rl, double ml, int phr,
-                                      double rr, double mr, double& gl, double& gr) {
+// pressures back to gl/gr for the next call. JAC: also the face Jacobian J by the implicit function theorem
+// on the converged 2x2 system G(p; W_l, W_r) = 0 (Eq. 2p_RP:ex_sys): only the velocity-balance row G_2
+// depends on the states (through u_l, u_r and the reference densities of the outer waves), so
+// dp = -DG^{-1} (0, dG_2), and the recovery of App. A (z, u_V*, v_V*) is differentiated along.
+template <bool JAC>
+__device__ inline PBOut pb_solve_core(const Fluid& F, const Opts& o, double tau, int phl, double rl, double ml, int phr,
+                                      double rr, double mr, double& gl, double& gr, FaceJac* J) {
   PBOut R;
   R.ok = 0;
   R.iters = 0;
@@ -382,7 +401,179 @@ __device__ inline PBOut pb_solve_warm(const Fluid& F, const Opts& o, double tau,
   R.ok = 1;
   gl = x0;
   gr = x1;
+  if (JAC) {
+    const double irl = 1.0 / rl, irr = 1.0 / rr;
+    const double fKl = dwave_drhoK(F.ph[phl], sl, x0, S.L.v, S.L.f);
+    const double fKr = dwave_drhoK(F.ph[phr], sr, x1, S.R.v, S.R.f);
+    // dG_2 / d(rho_l, m_l, rho_r, m_r): f_l(p_l; rho_l) + f_r(p_r; rho_r) + z [[v]] + u_r - u_l
+    const double g2[4] = {fKl + ul * irl, -irl, fKr - ur * irr, irr};
+    const double det = S.J00 * S.J11 - S.J01 * S.J10;
+    if (!(det != 0.0) || !isfinite(det)) {
+      R.ok = 0;
+      return R;
+    }
+    const double idet = 1.0 / det;
+    const double cl = S.J01 * idet, cr = -S.J00 * idet;  // dp_l = cl g2, dp_r = cr g2
+    const double dul[4] = {-ul * irl, irl, 0.0, 0.0};
+    const double dur[4] = {0.0, 0.0, -ur * irr, irr};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double dpl = cl * g2[k], dpr = cr * g2[k];
+      const double dz = S.dzl * dpl + S.dzr * dpr;
+      double duV, dpV, dvV;
+      if (left_vap) {
+        duV = dul[k] - (S.L.df * dpl + (k == 0 ? fKl : 0.0));
+        dpV = dpl;
+        dvV = S.L.dv * dpl;
+      } else {
+        duV = dur[k] + (S.R.df * dpr + (k == 2 ? fKr : 0.0));
+        dpV = dpr;
+        dvV = S.R.dv * dpr;
+      }
+      J->dF0[k] = -dz;
+      J->dF1[k] = dpV - dz * uV - R.z * duV;
+      J->dw[k] = duV + dz * vV + R.z * dvV;
+    }
+  }
   return R;
+}
+
+__device__ inline PBOut pb_solve_warm(const Fluid& F, const Opts& o, double tau, int phl, double rl, double ml, int phr,
+                                      double rr, double mr, double& gl, double& gr) {
+  return pb_solve_core<false>(F, o, tau, phl, rl, ml, phr, rr, mr, gl, gr, nullptr);
+}
+
+// Jacobian of the HLL flux of hll_pre / hll_fast (Davis speeds, the same branch and the same min/max choice)
+// with respect to (rho_l, m_l, rho_r, m_r); the face does not move (dw = 0).
+__device__ inline void hll_jac(const Phase& e, double rl, double ml, double rr, double mr, FaceJac& J) {
+  const double irl = 1.0 / rl, irr = 1.0 / rr;
+  const double ul = ml * irl, ur = mr * irr;
+  const double a2 = e.a2, a = e.a;
+  const double dul[4] = {-ul * irl, irl, 0.0, 0.0};
+  const double dur[4] = {0.0, 0.0, -ur * irr, irr};
+  // physical fluxes (m, m u + p) and their derivatives: dF1/drho = a^2 - u^2, dF1/dm = 2u
+  const double fl1 = ml * ul + pressure(e, rl), fr1 = mr * ur + pressure(e, rr);
+  const double dFl0[4] = {0.0, 1.0, 0.0, 0.0}, dFr0[4] = {0.0, 0.0, 0.0, 1.0};
+  const double dFl1[4] = {a2 - ul * ul, 2.0 * ul, 0.0, 0.0};
+  const double dFr1[4] = {0.0, 0.0, a2 - ur * ur, 2.0 * ur};
+  const bool lt = lt_bits(ul, ur);
+  const double SL = (lt ? ul : ur) - a, SR = (lt ? ur : ul) + a;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) J.dw[k] = 0.0;
+  if (ge0_bits(SL)) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      J.dF0[k] = dFl0[k];
+      J.dF1[k] = dFl1[k];
+    }
+    return;
+  }
+  if (le0_bits(SR)) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      J.dF0[k] = dFr0[k];
+      J.dF1[k] = dFr1[k];
+    }
+    return;
+  }
+  // H = (S_R F_l - S_L F_r + S_L S_R (U_r - U_l)) / (S_R - S_L): dH = (dN - H (dS_R - dS_L)) / (S_R - S_L)
+  const double iw = 1.0 / (SR - SL);
+  const double H0 = (SR * ml - SL * mr + SL * SR * (rr - rl)) * iw;
+  const double H1 = (SR * fl1 - SL * fr1 + SL * SR * (mr - ml)) * iw;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double dSL = lt ? dul[k] : dur[k];
+    const double dSR = lt ? dur[k] : dul[k];
+    const double dss = dSL * SR + SL * dSR;
+    const double dU0 = (k == 2 ? 1.0 : 0.0) - (k == 0 ? 1.0 : 0.0);
+    const double dU1 = (k == 3 ? 1.0 : 0.0) - (k == 1 ? 1.0 : 0.0);
+    const double dN0 = dSR * ml + SR * dFl0[k] - dSL * mr - SL * dFr0[k] + dss * (rr - rl) + SL * SR * dU0;
+    const double dN1 = dSR * fl1 + SR * dFl1[k] - dSL * fr1 - SL * dFr1[k] + dss * (mr - ml) + SL * SR * dU1;
+    J.dF0[k] = (dN0 - H0 * (dSR - dSL)) * iw;
+    J.dF1[k] = (dN1 - H1 * (dSR - dSL)) * iw;
+  }
+}
+
+// |x| > |y| on the bit patterns (integer pipe), for non-NaN arguments: the pivot choice of the block solves.
+__device__ __forceinline__ bool absgt_bits(double x, double y) {
+  const unsigned long long m = 0x7FFFFFFFFFFFFFFFull;
+  return ((unsigned long long)__double_as_longlong(x) & m) > ((unsigned long long)__double_as_longlong(y) & m);
+}
+
+// Dense N x N solve of A x = b (b in column N) by Gaussian elimination with partial pivoting, fully unrolled
+// so that A stays in registers: each candidate row is compared with the pivot row and the two are swapped by
+// selects when it is larger, which leaves the largest entry in the pivot row. The solution replaces column N.
+template <int N>
+__device__ inline bool solve_dense(double (&A)[N][N + 1]) {
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+#pragma unroll
+    for (int r = c + 1; r < N; ++r) {
+      const bool sw = absgt_bits(A[r][c], A[c][c]);
+#pragma unroll
+      for (int j = c; j <= N; ++j) {
+        const double t = sw ? A[r][j] : A[c][j];
+        A[r][j] = sw ? A[c][j] : A[r][j];
+        A[c][j] = t;
+      }
+    }
+    if (!nonzero_bits(A[c][c]) || !finite_bits(A[c][c])) return false;
+    const double ip = 1.0 / A[c][c];
+#pragma unroll
+    for (int r = c + 1; r < N; ++r) {
+      const double f = A[r][c] * ip;
+#pragma unroll
+      for (int j = c + 1; j <= N; ++j) A[r][j] = __fma_rn(-f, A[c][j], A[r][j]);
+    }
+    A[c][N] *= ip;
+#pragma unroll
+    for (int j = c + 1; j < N; ++j) A[c][j] *= ip;
+  }
+#pragma unroll
+  for (int c = N - 1; c >= 0; --c) {
+#pragma unroll
+    for (int j = c + 1; j < N; ++j) A[c][N] = __fma_rn(-A[c][j], A[j][N], A[c][N]);
+  }
+  return true;
+}
+
+// Banded solve for the implicit systems of general blocks: n unknowns (two per cell), lower and upper
+// bandwidth 3 (a cell couples to its neighbours only), partial pivoting among the 4 rows that reach the
+// pivot column, which widens the upper band to 6. Row r stores columns r-3 .. r+6 in A[r][0..9]
+// (column j at A[r][j - r + 3]); b is the right-hand side and receives the solution.
+constexpr int BAND_W = 10;
+__device__ inline bool solve_band(double (*A)[BAND_W], double* b, int n) {
+  for (int c = 0; c < n; ++c) {
+    const int rmax = min(c + 3, n - 1), jmax = min(c + 6, n - 1);
+    int p = c;
+    for (int r = c + 1; r <= rmax; ++r)
+      if (absgt_bits(A[r][c - r + 3], A[p][c - p + 3])) p = r;
+    const double piv = A[p][c - p + 3];
+    if (!nonzero_bits(piv) || !finite_bits(piv)) return false;
+    if (p != c) {
+      for (int j = c; j <= jmax; ++j) {
+        const double t = A[c][j - c + 3];
+        A[c][j - c + 3] = A[p][j - p + 3];
+        A[p][j - p + 3] = t;
+      }
+      const double t = b[c];
+      b[c] = b[p];
+      b[p] = t;
+    }
+    const double ip = 1.0 / A[c][3];
+    for (int r = c + 1; r <= rmax; ++r) {
+      const double f = A[r][c - r + 3] * ip;
+      for (int j = c + 1; j <= jmax; ++j) A[r][j - r + 3] = __fma_rn(-f, A[c][j - c + 3], A[r][j - r + 3]);
+      b[r] = __fma_rn(-f, b[c], b[r]);
+    }
+  }
+  for (int c = n - 1; c >= 0; --c) {
+    double s = b[c];
+    const int jmax = min(c + 6, n - 1);
+    for (int j = c + 1; j <= jmax; ++j) s = __fma_rn(-A[c][j - c + 3], b[j], s);
+    b[c] = s / A[c][3];
+  }
+  return true;
 }
 
 // Star pressure of the same-phase Riemann problem without transition: closed form for two

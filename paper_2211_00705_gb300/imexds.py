@@ -42,7 +42,7 @@ class OptionsS(C.Structure):
                 ("res_mode", C.c_int), ("l_max", C.c_int), ("newton_tol", C.c_double),
                 ("newton_itmax", C.c_int), ("alpha_min", C.c_double), ("split_ratio", C.c_double),
                 ("creation", C.c_int), ("zone_capacity", C.c_int), ("schedule", C.c_int),
-                ("group_cells", C.c_int), ("group_threads", C.c_int)]
+                ("group_cells", C.c_int), ("group_threads", C.c_int), ("block_solver", C.c_int)]
 
 
 class ProblemS(C.Structure):
@@ -121,7 +121,8 @@ def make_fluid(f) -> FluidS:
 def make_options(o, zone_capacity: int = 0, schedule: int = 0, group_cells: int = 0,
                  group_threads: int = 0) -> OptionsS:
     return OptionsS(o.cfl, o.theta_nb, o.tol_nb, o.tol_k, o.res_mode, o.l_max, o.newton_tol, o.newton_itmax,
-                    o.alpha_min, o.split_ratio, o.creation, zone_capacity, schedule, group_cells, group_threads)
+                    o.alpha_min, o.split_ratio, o.creation, zone_capacity, schedule, group_cells, group_threads,
+                    getattr(o, "block_solver", 0))
 
 
 def step_uniform_noalloc(fluid, cfl, n_lattice, x_left, x_right, rho_in, m_in, phase, rho_out, m_out, dt_out,
@@ -265,12 +266,16 @@ class Imexds:
         _check(load().imexds_get_kernel_times(self.h, _dp(ms), n.ctypes.data_as(C.POINTER(C.c_int64))))
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.KERNELS)}
 
+    PHASES = ["plan", "sweep", "block_solve", "post", "concurrent", "launch"]
+
     def group_phase_cycles(self) -> dict:
-        a = np.zeros(4, dtype=np.int64)
-        b = np.zeros(4, dtype=np.int64)
+        """SM cycles per phase of the group kernel (timing mode), for the slowest group and summed over groups;
+        keys as imexds_get_group_phase_cycles: plan + post + concurrent = launch (lockstep groups)."""
+        a = np.zeros(6, dtype=np.int64)
+        b = np.zeros(6, dtype=np.int64)
         _check(load().imexds_get_group_phase_cycles(self.h, a.ctypes.data_as(C.POINTER(C.c_int64)),
                                                     b.ctypes.data_as(C.POINTER(C.c_int64))))
-        keys = ["plan", "sweep", "dual_time", "post"]
+        keys = self.PHASES
         return {"slowest": dict(zip(keys, a.tolist())), "sum": dict(zip(keys, b.tolist()))}
 
     def set_adjoint_checkpoint(self, every: int):

@@ -91,6 +91,7 @@ class Options:
     alpha_min: float = 1e-8
     split_ratio: float = 2.0
     creation: int = 0
+    block_solver: int = 0      # 0: dual time stepping on each implicit block (Alg. 2); 1: Newton on its system
 
 
 def scaled_options(**kw) -> Options:
@@ -337,6 +338,58 @@ def nucleation_batch(workload_id: int, n_inst: int, n_range=(64, 1024), v_range=
         cells.append((np.full(n, h), rho, rho * u, np.zeros(n, dtype=np.uint8)))
     return _assemble(cells, N, np.full(n_inst, tau_paper()), fluid, scaled_options(creation=1), n_steps=n_steps,
                      name=name or f"{n_inst} nucleation instances, N in {list(n_range)}, {n_steps} steps")
+
+
+def slab_creation_batch(workload_id: int = 6, n_inst: int = 8, n_lattice: int = 64, slab_range=(4, 5),
+                        alpha_cav=(0.08, 0.2), alpha_nuc=(1e-4, 1e-2), v_cav=(20.0, 60.0), v_nuc=(14.0, 16.0),
+                        n_steps: int = 40, name: str = "") -> Batch:
+    """A slab of S lattice cells (S uniform-integer in slab_range) of one phase between two regions of the
+    other, every cell left of the slab's centre face moving at -V and every cell right of it at +V: even
+    instances hold a liquid slab in vapour pulled apart (V in v_cav: cavitation at the centre face), odd
+    instances a vapour slab in liquid compressed (u = +V left, -V right, V in v_nuc: nucleation). Both
+    boundaries sit inside the slab's end lattice cells with the tiny piece (fraction alpha, log-uniform in
+    alpha_cav or alpha_nuc) outside the slab, so the slab's inner cells lie in no implicit neighbourhood and the
+    centre face is a face between two explicit cells; the two boundary neighbourhoods are fewer than four lattice
+    cells apart. A pulled-apart slab's boundaries move outwards into the tiny pieces: alpha_cav and v_cav keep
+    those pieces above half their width in the first step (no merge), so the centre face cavitates in step 1.
+    Both phases at saturation (liquid rho0 = 1000 read as the saturation density)."""
+    fluid = workload_fluid(rho0_liq=1000.0)
+    rng = SplitMix64(instance_seeds(workload_id, n_inst))
+    uS, uV, ua1, ua2 = rng.uniform(), rng.uniform(), rng.uniform(), rng.uniform()
+    rho_v = fluid.p_sat / fluid.a2_vap
+    cells = []
+    for i in range(n_inst):
+        n = n_lattice
+        h = 1.0 / n
+        S = min(slab_range[0] + int(uS[i] * (slab_range[1] - slab_range[0] + 1)), slab_range[1])
+        nuc = (i % 2) == 1
+        lo, hi = (v_nuc if nuc else v_cav)
+        V = lo + uV[i] * (hi - lo)
+        ar = alpha_nuc if nuc else alpha_cav
+        la0, la1 = math.log(ar[0]), math.log(ar[1])
+        a1 = math.exp(la0 + ua1[i] * (la1 - la0))
+        a2 = math.exp(la0 + ua2[i] * (la1 - la0))
+        slab_ph, out_ph = (0, 1) if nuc else (1, 0)
+        rho_of = {0: rho_v, 1: 1000.0}
+        s0 = n // 2 - S // 2
+        c = s0 + S // 2                       # centre face (lattice face index)
+        w, ph, x0 = [], [], []
+        for j in range(s0):
+            w.append(h); ph.append(out_ph); x0.append(j * h)
+        w += [a1 * h, (1.0 - a1) * h]; ph += [out_ph, slab_ph]; x0 += [s0 * h, (s0 + a1) * h]
+        for j in range(s0 + 1, s0 + S - 1):
+            w.append(h); ph.append(slab_ph); x0.append(j * h)
+        j = s0 + S - 1
+        w += [(1.0 - a2) * h, a2 * h]; ph += [slab_ph, out_ph]; x0 += [j * h, (j + 1 - a2) * h]
+        for j in range(s0 + S, n):
+            w.append(h); ph.append(out_ph); x0.append(j * h)
+        w, ph, x0 = np.array(w), np.array(ph, np.uint8), np.array(x0)
+        rho = np.array([rho_of[int(p)] for p in ph])
+        left = x0 < c * h - 0.5 * h * 1e-9
+        u = np.where(left, V if nuc else -V, -V if nuc else V)
+        cells.append((w, rho, rho * u, ph))
+    return _assemble(cells, [n_lattice] * n_inst, np.full(n_inst, tau_paper()), fluid, scaled_options(creation=1),
+                     n_steps=n_steps, name=name or f"{n_inst} slab creation instances, N={n_lattice}, {n_steps} steps")
 
 
 def bubbles_domain(workload_id: int, n_cells: int = 1 << 24, n_bubbles: int = 1024, width_range=(2, 20),

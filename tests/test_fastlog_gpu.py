@@ -37,3 +37,17 @@ def test_newton_raphson_quotient_against_division():
     fast, ref = check_div(a, b)
     ulp = np.spacing(np.abs(ref))
     assert np.max(np.abs(fast - ref) / ulp) <= 2.0
+
+
+def test_refined_reciprocal_against_division():
+    """rcp_nr(b) alone (a = 1) against CUDA's correctly rounded 1 / b, within 1 ulp, over every binade the
+    kernels use and mantissas spread over [1, 2), including the ends of the binade."""
+    import numpy as np
+    from paper_2211_00705_gb300.imexds import check_div
+    rng = np.random.default_rng(5)
+    n = 1 << 20
+    mant = np.concatenate([rng.uniform(1.0, 2.0, n), 1.0 + np.arange(1, 2049) * 2.0 ** -52,
+                           2.0 - np.arange(1, 2049) * 2.0 ** -52])
+    b = np.ldexp(mant, rng.integers(-12, 40, mant.shape[0]))
+    fast, ref = check_div(np.ones_like(b), b)
+    assert np.max(np.abs(fast - ref) / np.spacing(np.abs(ref))) <= 1.0

@@ -105,3 +105,20 @@ def test_bubble_domain_layout():
     assert (b.rho[liq] == 1000.0).all() and (b.m == 0.0).all()
     rho_sat_v = b.fluid.p_sat / b.fluid.a2_vap
     assert np.max(np.abs(b.rho[~liq] / rho_sat_v - 1.0)) <= 0.01 * (1 + 1e-12)
+
+
+def test_slab_creation_layout():
+    """The slab instances: a valid cell list (faces on the lattice except the two boundaries), the slab's
+    inner cells of width h, phases alternating out | slab | out, one velocity jump at the centre face."""
+    b = I.slab_creation_batch(n_inst=6)
+    for i in range(b.n_inst):
+        s = slice(b.cell_offsets[i], b.cell_offsets[i + 1])
+        w, ph, u = b.widths[s], b.phase[s], b.m[s] / b.rho[s]
+        assert abs(w.sum() - 1.0) < 1e-12
+        flips = np.nonzero(np.diff(ph.astype(int)))[0]
+        assert len(flips) == 2
+        slab = ph[flips[0] + 1]
+        assert slab == (0 if i % 2 else 1)
+        inner = w[flips[0] + 2:flips[1]]
+        assert len(inner) >= 2 and np.allclose(inner, 1.0 / b.n_lattice[i])
+        assert np.count_nonzero(np.abs(np.diff(u)) > 1e-9) == 1

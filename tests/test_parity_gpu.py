@@ -80,3 +80,20 @@ def test_single_phase_instance_without_zones():
     b.phase = np.ones(n, dtype=np.uint8)
     b.cell_offsets = np.array([0, n], dtype=np.int32)
     _check(b)
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_creation_at_a_face_inside_a_joined_zone(schedule):
+    """Creation (App. B) at a face between two explicit cells inside one zone: a slab of 4-5 lattice cells
+    between two boundaries whose neighbourhoods are joined into one zone, pulled apart (liquid slab:
+    cavitation) or compressed (vapour slab: nucleation) at its centre face. Every instance creates its cell at
+    that face in the first step; the cavitation instances then run 30 steps (the nucleated droplets, ~1e-7 of
+    a lattice cell, make dual time stepping run into l_max, where the last iterate of 1e4 pseudo steps carries
+    the rounding differences of the two implementations: their 30-step runs are compared with Newton's method
+    in tests/test_newton_gpu.py)."""
+    b = I.slab_creation_batch(n_steps=1)
+    _, sa, sb = _check(b, schedule=schedule)
+    np.testing.assert_array_equal(sb["creations"], 1)
+    b = I.slab_creation_batch(n_steps=30).subset([0, 2, 4, 6])
+    _, sa, sb = _check(b, schedule=schedule)
+    assert (sb["creations"] >= 1).all() and (sa["maxiter"] == 0).all()
