@@ -75,7 +75,7 @@ def cell_steps(stats, counts):
     return float(np.sum(stats["steps"].astype(np.float64) * counts.astype(np.float64)))
 
 
-def measure_adjoint(dev, steps, warmup, scale=1.0, n_steps=2000):
+def measure_adjoint(dev, steps, warmup, scale=1.0, n_steps=2000, block_solver=0):
     """The adjoint on its workload (Riemann instances, N=500, 2000 steps, checkpoints every 64): forward run
     (also a target run with tau x 1.1 for the misfit), then imexds_adjoint timed. Cell-steps of the adjoint
     = initial cells x steps of every instance (the replay, the recompute and the reverse sweep all count as
@@ -86,6 +86,8 @@ def measure_adjoint(dev, steps, warmup, scale=1.0, n_steps=2000):
     from paper_2211_00705_gb300.imexds import Imexds
     n = max(1, int(round(1024 * scale)))
     b = I.adjoint_batch(n_inst=n, n_steps=n_steps)
+    if block_solver:
+        b = with_block_solver(b, block_solver)
     prog_steps = b.n_steps
     tctx = Imexds.from_batch(dataclasses.replace(b, tau=b.tau * 1.1))
     tctx.step(prog_steps)
@@ -127,7 +129,105 @@ def measure_adjoint(dev, steps, warmup, scale=1.0, n_steps=2000):
                     "note": "imexds_adjoint call with host seed/gradient arrays, layout and copies included"},
             "replay_err": info["replay_err"], "instances_without_gradient": int(np.count_nonzero(g["status"])),
             "forward_value": fwd_cs / fwd_s, "forward_note": "imexds_step over the same workload (tight tolerances)",
+            "block_solver": "newton" if block_solver else "dual time stepping (Alg. 2)",
             "dts_iters_per_step": float(st["dts_iters"].sum() / max(1, st["steps"].sum()))}
+
+
+def measure_cavitation(dev, scale=1.0, n_steps=5000, adj_inst=1024, fd_inst=4):
+    """The phase-creation workload (16384 cavitation instances, N in [64, 4096], 5000 steps): the forward run at
+    full size with dual time stepping and with Newton's method on the blocks (autotuned schedule, one timed run
+    each after a 64-step warm-up), then dJ/dV of the mean final pressure (V enters the initial momentum) by the
+    adjoint on the first adj_inst instances (Newton forward run and replay), with central differences of the
+    forward run on fd_inst of them. Returns the JSON object of the cavitation line."""
+    import dataclasses
+    import torch
+    from paper_2211_00705_gb300 import autotune
+    from paper_2211_00705_gb300 import inputs as I
+    from paper_2211_00705_gb300.imexds import Imexds
+    b = I.workload(4, scale=scale)
+    b.n_steps = n_steps
+    out = {"workload": b.name, "instances": b.n_inst, "cells": int(b.rho.shape[0]), "steps": n_steps}
+    for solver in (0, 1):
+        bb = with_block_solver(b, solver)
+        tuned = autotune.tune(bb, steps=64)
+        ctx = Imexds.from_batch(bb, schedule=tuned["schedule"], group_threads=tuned.get("group_threads", 0),
+                                group_cells=tuned.get("group_cells", 0))
+        ctx.step(64)
+        ctx.reset()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.step(n_steps)
+        e1.record()
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+        st = ctx.stats()
+        cs = float(np.sum(st["steps"] * ctx.cell_counts()))
+        status = ctx.get_states()["status"]
+        ctx.close()
+        out["newton" if solver else "dual_time"] = {
+            "value": cs / secs, "unit": UNIT, "seconds": secs, "cell_steps": cs,
+            "schedule": {k: tuned[k] for k in ("schedule", "group_threads", "group_cells") if k in tuned},
+            "block_iters_per_step": float(st["dts_iters"].sum() / max(1, st["steps"].sum())),
+            "creations_per_instance": float(st["creations"].mean()),
+            "instance_status_nonzero": int(np.count_nonzero(status))}
+    # dJ/dV by the adjoint on a sample, Newton forward run
+    sb = with_block_solver(b.subset(list(range(min(adj_inst, b.n_inst)))), 1)
+    sb.n_steps = n_steps
+
+    def mean_pressure(st, bb):
+        f = bb.fluid
+        off = st["offsets"]
+        J = np.zeros(bb.n_inst)
+        gr = np.zeros(int(off[-1]))
+        gw = np.zeros(int(off[-1]))
+        for i in range(bb.n_inst):
+            sl = slice(off[i], off[i + 1])
+            ph, r, w = st["phase"][sl], st["rho"][sl], st["widths"][sl]
+            a2 = np.where(ph == 0, f.a2_vap, f.a2_liq)
+            p = np.where(ph == 0, f.a2_vap * r, f.p_sat + f.a2_liq * (r - f.rho0_liq))
+            W = w.sum()
+            J[i] = float((w * p).sum() / W)
+            gr[sl] = w * a2 / W
+            gw[sl] = (p - J[i]) / W
+        return J, gr, gw
+
+    ctx = Imexds.from_batch(sb)
+    ctx.set_adjoint_checkpoint(64)
+    ctx.step(n_steps)
+    s = ctx.get_states()
+    J, gr, gw = mean_pressure(s, sb)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = ctx.adjoint(gr, np.zeros_like(gr), gw)
+    wall = time.perf_counter() - t0
+    info = ctx.adjoint_info()
+    ctx.close()
+    V = np.array([abs(sb.m[sb.cell_offsets[i]] / sb.rho[sb.cell_offsets[i]]) for i in range(sb.n_inst)])
+    dmdV = np.sign(sb.m / sb.rho) * sb.rho
+    off0 = sb.cell_offsets
+    adj = np.array([np.dot(g["m"][off0[i]:off0[i + 1]], dmdV[off0[i]:off0[i + 1]]) for i in range(sb.n_inst)])
+    fb = sb.subset(list(range(min(fd_inst, sb.n_inst))))
+    fb.n_steps = n_steps
+    eps = 1e-6
+    vals = []
+    Vf = V[:fb.n_inst]
+    for sgn in (1.0, -1.0):
+        bb = dataclasses.replace(fb, m=fb.m + sgn * eps * np.repeat(Vf, np.diff(fb.cell_offsets))
+                                 * (np.sign(fb.m / fb.rho) * fb.rho))
+        c = Imexds.from_batch(bb)
+        c.step(n_steps)
+        vals.append(mean_pressure(c.get_states(), bb)[0])
+        c.close()
+    fd = (vals[0] - vals[1]) / (2 * eps * Vf)
+    out["adjoint"] = {"value": info["cell_steps"] / (info["kernel_ms"] / 1e3), "unit": UNIT,
+                      "instances": sb.n_inst, "seconds": info["kernel_ms"] / 1e3, "wall_seconds": wall,
+                      "replay_err": info["replay_err"], "instances_without_gradient": int(np.count_nonzero(g["status"])),
+                      "dJ_dV_sample": adj[:fb.n_inst].tolist(), "fd_sample": fd.tolist(),
+                      "fd_rel_err_max": float(np.max(np.abs(adj[:fb.n_inst] - fd) / np.abs(adj[:fb.n_inst]))),
+                      "note": "Newton forward run and replay; checkpoints every 64 steps; central differences of "
+                              "the forward run at step 1e-6 V on the first instances"}
+    return out
 
 
 def measure_large_domain_sweep(n_steps=100):
@@ -398,7 +498,8 @@ def load_peak(key):
         return None
 
 
-def measure_run(batch, steps, warmup, schedule, flush, barrier, sampler=None, ws=1, dev=None):
+def measure_run(batch, steps, warmup, schedule, flush, barrier, sampler=None, ws=1, dev=None, group_threads=0,
+                group_cells=0):
     """The headline measurement of one batch: the autotuned schedule (schedule 0) or the given one, warm-up runs,
     then `steps` whole runs to t_end timed with CUDA events (L2 flushed between them, outside the events), max
     over ranks. With a group schedule the library's own events around the resident kernel (on its stream) run
@@ -414,7 +515,7 @@ def measure_run(batch, steps, warmup, schedule, flush, barrier, sampler=None, ws
                                 group_cells=tuned.get("group_cells", 0))
         schedule_used = tuned["schedule"]
     else:
-        ctx = Imexds.from_batch(batch, schedule=schedule)
+        ctx = Imexds.from_batch(batch, schedule=schedule, group_threads=group_threads, group_cells=group_cells)
         schedule_used = schedule
     group = schedule_used in (2, 3)
     if group:
@@ -502,10 +603,14 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the single-instance comparison")
     ap.add_argument("--no-hbm", action="store_true", help="skip the large-domain sweep (HBM) measurement")
     ap.add_argument("--no-newton", action="store_true", help="skip the Newton block-solver leg")
-    ap.add_argument("--only", choices=["adjoint", "hbm"], default=None,
+    ap.add_argument("--only", choices=["adjoint", "hbm", "cavitation"], default=None,
                     help="run one auxiliary measurement alone and print its JSON (profiling)")
     ap.add_argument("--adjoint-steps", type=int, default=2000, help="steps of the adjoint workload")
     ap.add_argument("--table", action="store_true", help="per-workload rates (GPU, plain GPU, oracle) as JSON")
+    ap.add_argument("--group-threads", type=int, default=0,
+                    help="CTA width of the group schedules when --schedule is 2 or 3 (0: the library's default)")
+    ap.add_argument("--group-cells", type=int, default=0,
+                    help="lattice cells per instance group when --schedule is 2 or 3 (0: the library's default)")
     ap.add_argument("--block-solver", type=int, default=0, choices=[0, 1],
                     help="solver of the implicit blocks for the headline run: 0 dual time stepping (Alg. 2), 1 Newton")
     args = ap.parse_args()
@@ -529,6 +634,9 @@ def main():
     if args.only == "hbm":
         print(json.dumps(measure_large_domain_sweep()))
         return 0
+    if args.only == "cavitation":
+        print(json.dumps(measure_cavitation(dev, scale=args.scale)))
+        return 0
 
     batch = workload(args.scale)
     if args.block_solver:
@@ -541,7 +649,8 @@ def main():
         torch.cuda.synchronize()
 
     sampler = ClockSampler(dev.index) if rank == 0 else None
-    head = measure_run(batch, args.steps, args.warmup, args.schedule, flush, barrier, sampler=sampler, ws=ws, dev=dev)
+    head = measure_run(batch, args.steps, args.warmup, args.schedule, flush, barrier, sampler=sampler, ws=ws, dev=dev,
+                       group_threads=args.group_threads, group_cells=args.group_cells)
     ctx, tuned, st = head["ctx"], head["tuned"], head["stats"]
     value = head["value"]
 
@@ -633,6 +742,10 @@ def main():
             # at most two timed calls (~13 s each at full size): the adjoint is reported beside the headline
             line["adjoint"] = measure_adjoint(dev, max(1, min(2, args.steps // 2)), 1, scale=args.scale,
                                               n_steps=args.adjoint_steps)
+            # the same adjoint of a Newton run (forward and replay with Newton on the blocks; the reverse step
+            # differentiates the converged block systems either way)
+            line["adjoint"]["newton"] = measure_adjoint(dev, 1, 1, scale=args.scale, n_steps=args.adjoint_steps,
+                                                        block_solver=1)
         if not args.no_hbm:
             line["large_domain_sweep"] = measure_large_domain_sweep()
         if ws == 1 and not args.no_cpu_baseline:

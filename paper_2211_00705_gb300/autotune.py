@@ -1,7 +1,9 @@
 """Schedule autotuner for imexds contexts.
 
-Candidates: the per-step kernel schedule (one launch per kernel and step, replayed from a CUDA graph)
-and the instance-group schedule (one resident launch per call) at several group sizes and CTA widths.
+Candidates: the per-step kernel schedule (one launch per kernel and step, replayed from a CUDA graph),
+the lockstep instance-group schedule (one resident launch per call) at several group sizes and CTA widths
+(the number of sweep warps beside the warp that solves the blocks), and the independent instance groups
+(each instance of a group at its own pace, tiles dealt to whichever instance is open).
 Each candidate gets a context of its own loaded with the batch; one untimed run (graph build, caches) is
 followed by imexds_reset and a timed run, host clock around the call, which returns when the device is
 done: the whole run_to for a batch with an end time (the early steps of a run are not representative of
@@ -23,10 +25,13 @@ CANDIDATES = [
     {"schedule": 2, "group_threads": 128, "group_cells": 16384},
     {"schedule": 2, "group_threads": 256, "group_cells": 16384},
     {"schedule": 2, "group_threads": 256, "group_cells": 24576},
+    {"schedule": 2, "group_threads": 256, "group_cells": 8192},
     {"schedule": 2, "group_threads": 192, "group_cells": 16384},
     {"schedule": 2, "group_threads": 128, "group_cells": 8192},
     {"schedule": 2, "group_threads": 96, "group_cells": 16384},
     {"schedule": 2, "group_threads": 64, "group_cells": 4096},
+    {"schedule": 3, "group_threads": 128, "group_cells": 16384},
+    {"schedule": 3, "group_threads": 128, "group_cells": 8192},
 ]
 
 _cache: dict = {}
