@@ -151,6 +151,13 @@ imexds_status imexds_set_states_device(imexds_ctx* ctx, const int32_t* cell_offs
                                        const double* widths_d, const double* rho_d, const double* m_d,
                                        const uint8_t* phase_d, double t0);
 
+/* Device-resident variant of imexds_get_states: the cell lists are written into DEVICE arrays widths_d, rho_d,
+ * m_d, phase_d (sized from imexds_cell_counts) by kernels on the context's stream, in the order of
+ * imexds_get_states; cell_offsets (n_inst + 1), t and inst_status (n_inst) are host arrays. No per-cell data
+ * passes through the host. Returns after the copies are complete. */
+imexds_status imexds_get_states_device(imexds_ctx* ctx, int32_t* cell_offsets, double* widths_d, double* rho_d,
+                                       double* m_d, uint8_t* phase_d, double* t, int32_t* inst_status);
+
 /* Restore the states (and t0) given to the last imexds_set_states, on the device (device-to-device
  * copies only). */
 imexds_status imexds_reset(imexds_ctx* ctx);
@@ -245,6 +252,15 @@ imexds_status imexds_check_log(int32_t n, const double* x, double* fast, double*
 imexds_status imexds_adjoint(imexds_ctx* ctx, const double* dJ_dw_T, const double* dJ_drho_T,
                              const double* dJ_dm_T, double* dJ_dw0, double* dJ_drho0, double* dJ_dm0,
                              double* dJ_dtau, int32_t* inst_status);
+/* Device-resident variant of imexds_adjoint: the seeds dJ_dw_T (may be NULL), dJ_drho_T, dJ_dm_T and the outputs
+ * dJ_dw0 (may be NULL), dJ_drho0, dJ_dm0, dJ_dtau are DEVICE arrays in the same orders and sizes; inst_status is
+ * a host array (may be NULL). The seeds are scattered, the replay is checked and the gradients are assembled by
+ * kernels, so no per-cell data passes through the host (the library uploads its own copy of the initial lists
+ * of the last imexds_set_states, as imexds_adjoint does). imexds_adjoint_replay then reports the stop sites
+ * only (its cell lists are empty). Returns after the gradients are complete. */
+imexds_status imexds_adjoint_device(imexds_ctx* ctx, const double* dJ_dw_T, const double* dJ_drho_T,
+                                    const double* dJ_dm_T, double* dJ_dw0, double* dJ_drho0, double* dJ_dm0,
+                                    double* dJ_dtau, int32_t* inst_status);
 /* Checkpoint interval k of the adjoint (default 64). */
 imexds_status imexds_set_adjoint_checkpoint(imexds_ctx* ctx, int32_t every);
 /* The last imexds_adjoint: device time of its kernel (ms), the largest relative deviation of its

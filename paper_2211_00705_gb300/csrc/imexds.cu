@@ -2000,6 +2000,100 @@ __global__ void k_init_dt(Dev d, int n_inst) {
   }
 }
 
+// ---------------------------------------------------------------------- cell lists on the device
+// The current cell lists of every instance in the order of imexds_get_states (lattice cells outside zones
+// and the zones' cells, left to right) written into device arrays, without staging through the host.
+
+// Cells of every instance: its lattice cells plus, per alive zone, the zone's cells minus the lattice cells
+// the zone covers.
+__global__ void k_cell_counts(Dev d, int n_inst, int* counts) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_inst) return;
+  const Inst& I = d.inst[i];
+  int cnt = I.N;
+  for (int z = 0; z < I.zone_cap; ++z) {
+    const Zone& Z = d.zones[I.zone_off + z];
+    if (Z.alive) cnt += Z.nc - (Z.B - Z.A);
+  }
+  counts[i] = cnt;
+}
+
+// One thread per zone slot: at the zone's first lattice cell, the number of cells it adds to the list
+// (delta) and its slot + 1 (zstart); cov marks every lattice cell the zone covers. The three arrays are
+// zero before the call.
+__global__ void k_zone_marks(Dev d, int n_slots, int* delta, int* zstart, unsigned char* cov) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= n_slots) return;
+  const Zone& Z = d.zones[z];
+  if (!Z.alive) return;
+  const int o = d.inst[Z.inst].lat_off;
+  delta[o + Z.A] = Z.nc - (Z.B - Z.A);
+  zstart[o + Z.A] = z + 1;
+  for (int j = Z.A; j < Z.B; ++j) cov[o + j] = 1;
+}
+
+// One CTA (256 threads) per instance, its lattice in chunks of 256 cells: an exclusive block scan of delta
+// gives the cells the zones add before each lattice cell; a cell outside every zone goes to
+// off + j + extra(j), the cells of a zone starting at j to off + j + extra(j) + q.
+__global__ void __launch_bounds__(256) k_gather_states(Dev d, const int* off, double* w, double* r, double* m,
+                                                       unsigned char* ph, const int* delta, const int* zstart,
+                                                       const unsigned char* cov) {
+  const int i = blockIdx.x;
+  const Inst& I = d.inst[i];
+  const int lo = I.lat_off, N = I.N, p = I.parity, o0 = off[i];
+  const double* R = d.R(p);
+  const double* M = d.M(p);
+  __shared__ int wsum[8];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int base = 0; base < N; base += 256) {
+    const int j = base + threadIdx.x;
+    const int v = (j < N) ? delta[lo + j] : 0;
+    int x = v;  // inclusive warp scan
+#pragma unroll
+    for (int k = 1; k < 32; k <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, k);
+      if (lane >= k) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    int before = carry;
+    for (int k = 0; k < wid; ++k) before += wsum[k];
+    const int extra = before + x - v;  // exclusive
+    if (j < N) {
+      const int g = lo + j;
+      const int at = o0 + j + extra;
+      if (!cov[g]) {
+        w[at] = I.h;
+        r[at] = R[g];
+        m[at] = M[g];
+        ph[at] = d.phase[g];
+      } else if (zstart[g]) {
+        const Zone& Z = d.zones[zstart[g] - 1];
+        for (int q = 0; q < Z.nc; ++q) {
+          w[at + q] = Z.w[q];
+          r[at + q] = Z.r[q];
+          m[at + q] = Z.m[q];
+          ph[at + q] = (unsigned char)Z.ph[q];
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 255) carry = before + x;
+    __syncthreads();
+  }
+}
+
+// t and status of every instance, packed for one small copy.
+__global__ void k_inst_ts(Dev d, int n_inst, double* t, int* status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_inst) return;
+  t[i] = d.inst[i].t;
+  status[i] = d.inst[i].status;
+}
+
 __global__ void k_count_active(Dev d, int n_inst) {
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
@@ -2015,6 +2109,85 @@ __global__ void k_count_active(Dev d, int n_inst) {
 #include "noalloc.cuh"
 #include "adjoint.cuh"
 namespace {
+
+// ---- the adjoint's seeds and gradients in device arrays (imexds_adjoint_device)
+// Seeds in imexds_get_states order (offsets toff) into the adjoint's per-instance slots; one CTA per instance.
+__global__ void k_scatter_seeds(const long long* offs, const int* toff, const double* sw, const double* sr,
+                                const double* sm, double* lw, double* lr, double* lm) {
+  const int i = blockIdx.x;
+  const long long o = offs[i];
+  const int a = toff[i], M = toff[i + 1] - a;
+  for (int q = threadIdx.x; q < M; q += blockDim.x) {
+    lw[o + q] = sw ? sw[a + q] : 0.0;
+    lr[o + q] = sr[a + q];
+    lm[o + q] = sm[a + q];
+  }
+}
+
+// Largest deviation of the replayed final states (fin_*) from the forward run's (g*, imexds_get_states order):
+// rho and m relative to max |rho|, widths relative to h; one CTA (128 threads) per instance.
+__global__ void k_replay_err(const imexds::adj::AInst* I, const long long* offs, const int* toff, const double* fw,
+                             const double* fr, const double* fm, const double* gw, const double* gr,
+                             const double* gm, double* err) {
+  const int i = blockIdx.x;
+  const long long o = offs[i];
+  const int a = toff[i], M = toff[i + 1] - a;
+  double rmax = 0.0, dr = 0.0, dm = 0.0, dw = 0.0;
+  for (int q = threadIdx.x; q < M; q += blockDim.x) {
+    rmax = fmax(rmax, fabs(gr[a + q]));
+    dr = fmax(dr, fabs(fr[o + q] - gr[a + q]));
+    dm = fmax(dm, fabs(fm[o + q] - gm[a + q]));
+    dw = fmax(dw, fabs(fw[o + q] - gw[a + q]));
+  }
+  __shared__ double red[4][4];
+  for (int off = 16; off > 0; off >>= 1) {
+    rmax = fmax(rmax, __shfl_down_sync(0xffffffffu, rmax, off));
+    dr = fmax(dr, __shfl_down_sync(0xffffffffu, dr, off));
+    dm = fmax(dm, __shfl_down_sync(0xffffffffu, dm, off));
+    dw = fmax(dw, __shfl_down_sync(0xffffffffu, dw, off));
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[w][0] = rmax;
+    red[w][1] = dr;
+    red[w][2] = dm;
+    red[w][3] = dw;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k)
+      for (int c = 0; c < 4; ++c) red[0][c] = fmax(red[0][c], red[k][c]);
+    const double R = red[0][0];
+    err[i] = fmax(red[0][1] / R, fmax(red[0][2] / R, red[0][3] / I[i].h));
+  }
+}
+
+// Gradients with respect to the initial lists into the caller's device arrays (imexds_set_states order,
+// offsets u0off), one thread per instance: a boundary position is the last fixed face plus the widths after
+// it, so its adjoint adds to the widths of those cells; cells with two fixed faces have the lattice width
+// (gradient 0); an instance without gradient gets NaN.
+__global__ void k_adj_grads(int n, const imexds::adj::AInst* I, const long long* offs, const int* u0off,
+                            const unsigned char* fpb0, const double* lw, const double* lr, const double* lm,
+                            const double* lx, double* gw0, double* gr0, double* gm0, double* gtau) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const imexds::adj::AInst& A = I[i];
+  const int a = u0off[i], M0 = u0off[i + 1] - a;
+  const long long o = offs[i];
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  gtau[i] = A.status ? nan : A.lam_tau;
+  double acc = 0.0;  // adjoint of the boundary positions right of the cell, within its segment
+  for (int q = M0 - 1; q >= 0; --q) {
+    if (!fpb0[o + q + 1]) acc = 0.0;
+    if (fpb0[o + q + 1]) acc += lx[o + q + 1];
+    gr0[a + q] = A.status ? nan : lr[o + q];
+    gm0[a + q] = A.status ? nan : lm[o + q];
+    if (gw0) {
+      const bool lattice = !fpb0[o + q] && !fpb0[o + q + 1];
+      gw0[a + q] = A.status ? nan : (lattice ? 0.0 : lw[o + q] + acc);
+    }
+  }
+}
 
 // ---------------------------------------------------------------------------------------- host side
 std::string g_last_error;
@@ -2069,6 +2242,10 @@ struct imexds_ctx {
   std::vector<int32_t> adj_fin_off, adj_site;
   std::vector<double> adj_fin_w, adj_fin_r, adj_fin_m;
   long long adj_cell_steps = 0;
+  // device scratch of the cell-list gather (imexds_cell_counts, imexds_get_states_device, imexds_adjoint_device)
+  int *g_delta = nullptr, *g_zstart = nullptr, *g_counts = nullptr, *g_off = nullptr, *g_st = nullptr;
+  unsigned char* g_cov = nullptr;
+  double* g_t = nullptr;
 };
 
 namespace {
@@ -2138,6 +2315,16 @@ void free_dev(imexds_ctx* c) {
   cudaFree(c->d_grange);
   cudaFree(c->d_phase);
   c->d_phase = nullptr;
+  cudaFree(c->g_delta);
+  cudaFree(c->g_zstart);
+  cudaFree(c->g_cov);
+  cudaFree(c->g_counts);
+  cudaFree(c->g_off);
+  cudaFree(c->g_t);
+  cudaFree(c->g_st);
+  c->g_delta = c->g_zstart = c->g_counts = c->g_off = c->g_st = nullptr;
+  c->g_cov = nullptr;
+  c->g_t = nullptr;
   c->d_ginst = nullptr;
   c->d_grange = nullptr;
   d = Dev{};
@@ -2775,20 +2962,68 @@ imexds_status imexds_run_to(imexds_ctx* c, double t_end) {
   return st;
 }
 
+// device scratch of the gather, allocated with the context's lattice (freed by free_dev)
+static imexds_status ensure_gather(imexds_ctx* c) {
+  if (c->g_delta) return IMEXDS_OK;
+  CK(cudaMalloc(&c->g_delta, sizeof(int) * std::max(1, c->n_lat)));
+  CK(cudaMalloc(&c->g_zstart, sizeof(int) * std::max(1, c->n_lat)));
+  CK(cudaMalloc(&c->g_cov, std::max(1, c->n_lat)));
+  CK(cudaMalloc(&c->g_counts, sizeof(int) * c->n_inst));
+  CK(cudaMalloc(&c->g_off, sizeof(int) * (c->n_inst + 1)));
+  CK(cudaMalloc(&c->g_t, sizeof(double) * c->n_inst));
+  CK(cudaMalloc(&c->g_st, sizeof(int) * c->n_inst));
+  return IMEXDS_OK;
+}
+
 imexds_status imexds_cell_counts(imexds_ctx* c, int32_t* counts) {
   if (!c || !counts) return IMEXDS_ERR_ARG;
   if (!c->loaded) return IMEXDS_ERR_STATE;
-  std::vector<Zone> hz(c->n_zone_slots);
-  CK(cudaMemcpyAsync(hz.data(), c->d.zones, sizeof(Zone) * hz.size(), cudaMemcpyDeviceToHost, c->stream));
+  imexds_status st = ensure_gather(c);
+  if (st) return st;
+  k_cell_counts<<<(c->n_inst + 127) / 128, 128, 0, c->stream>>>(c->d, c->n_inst, c->g_counts);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(counts, c->g_counts, sizeof(int) * c->n_inst, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  for (int i = 0; i < c->n_inst; ++i) {
-    int cnt = c->N[i];
-    for (int z = 0; z < c->zone_cap[i]; ++z) {
-      const Zone& Z = hz[c->zone_off[i] + z];
-      if (Z.alive) cnt += Z.nc - (Z.B - Z.A);
-    }
-    counts[i] = cnt;
-  }
+  return IMEXDS_OK;
+}
+
+// The cell lists into device arrays (offsets off_host, already computed from the counts, are copied to the
+// device here); no synchronisation.
+static imexds_status gather_states(imexds_ctx* c, const int32_t* off_host, double* w_d, double* r_d, double* m_d,
+                            uint8_t* ph_d) {
+  imexds_status st = ensure_gather(c);
+  if (st) return st;
+  cudaStream_t sm = c->stream;
+  CK(cudaMemcpyAsync(c->g_off, off_host, sizeof(int) * (c->n_inst + 1), cudaMemcpyHostToDevice, sm));
+  CK(cudaMemsetAsync(c->g_delta, 0, sizeof(int) * c->n_lat, sm));
+  CK(cudaMemsetAsync(c->g_zstart, 0, sizeof(int) * c->n_lat, sm));
+  CK(cudaMemsetAsync(c->g_cov, 0, c->n_lat, sm));
+  if (c->n_zone_slots > 0)
+    k_zone_marks<<<(c->n_zone_slots + 127) / 128, 128, 0, sm>>>(c->d, c->n_zone_slots, c->g_delta, c->g_zstart,
+                                                               c->g_cov);
+  k_gather_states<<<c->n_inst, 256, 0, sm>>>(c->d, c->g_off, w_d, r_d, m_d, ph_d, c->g_delta, c->g_zstart,
+                                             c->g_cov);
+  CK(cudaGetLastError());
+  return IMEXDS_OK;
+}
+
+imexds_status imexds_get_states_device(imexds_ctx* c, int32_t* off, double* w_d, double* r_d, double* m_d,
+                                       uint8_t* ph_d, double* t, int32_t* inst_status) {
+  if (!c || !off || !w_d || !r_d || !m_d || !ph_d || !t || !inst_status) return IMEXDS_ERR_ARG;
+  if (!c->loaded) return IMEXDS_ERR_STATE;
+  const int n = c->n_inst;
+  std::vector<int32_t> counts(n);
+  imexds_status st = imexds_cell_counts(c, counts.data());
+  if (st) return st;
+  off[0] = 0;
+  for (int i = 0; i < n; ++i) off[i + 1] = off[i] + counts[i];
+  st = gather_states(c, off, w_d, r_d, m_d, ph_d);
+  if (st) return st;
+  k_inst_ts<<<(n + 127) / 128, 128, 0, c->stream>>>(c->d, n, c->g_t, c->g_st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(t, c->g_t, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(inst_status, c->g_st, sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   return IMEXDS_OK;
 }
 
@@ -3038,34 +3273,58 @@ imexds_status imexds_set_adjoint_checkpoint(imexds_ctx* c, int32_t every) {
   return IMEXDS_OK;
 }
 
-imexds_status imexds_adjoint(imexds_ctx* c, const double* dJ_dw_T, const double* dJ_drho_T, const double* dJ_dm_T,
-                             double* dJ_dw0, double* dJ_drho0, double* dJ_dm0, double* dJ_dtau,
-                             int32_t* inst_status) {
+namespace {
+// One imexds_adjoint / imexds_adjoint_device call: the layout of the per-instance slots and what the host keeps.
+struct AdjRun {
+  int n = 0, oT = 0;
+  long long stride = 0;
+  std::vector<int32_t> MT;   // final cell counts of the forward run
+  std::vector<int64_t> stats;
+  std::vector<long long> offs;
+  std::vector<unsigned char> hfpb;  // initial face kinds, slot layout
+  std::vector<imexds::adj::AInst> hI;
+  imexds::adj::ADev A{};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  // device copies for the device variant
+  long long* d_offs = nullptr;
+  int *d_toff = nullptr, *d_u0off = nullptr;
+  unsigned char *d_fpb0 = nullptr, *chk_ph = nullptr;
+  double *chk_w = nullptr, *chk_r = nullptr, *chk_m = nullptr, *d_err = nullptr;
+};
+}  // namespace
+
+// The steps both adjoint entry points share: the slot layout, one device allocation kept by the context, the
+// initial lists of the last imexds_set_states (the library's own copies), the seeds (host arrays copied in, or
+// device arrays scattered by k_scatter_seeds) and the k_adjoint launch between two events. No synchronisation.
+static imexds_status adjoint_launch(imexds_ctx* c, AdjRun& R, const double* dJ_dw_T, const double* dJ_drho_T,
+                                    const double* dJ_dm_T, bool dev_seeds) {
   using namespace imexds::adj;
-  if (!c || !dJ_drho_T || !dJ_dm_T || !dJ_drho0 || !dJ_dm0 || !dJ_dtau) return IMEXDS_ERR_ARG;
-  if (!c->loaded || c->u0_off.empty()) return IMEXDS_ERR_STATE;
   const int n = c->n_inst;
+  R.n = n;
   // the last forward: final cell counts and steps per instance
-  std::vector<int32_t> MT(n);
-  imexds_status st = imexds_cell_counts(c, MT.data());
+  R.MT.assign(n, 0);
+  imexds_status st = imexds_cell_counts(c, R.MT.data());
   if (st) return st;
-  std::vector<int64_t> stats((size_t)n * 10);
-  st = imexds_get_stats(c, stats.data());
+  R.stats.assign((size_t)n * 10, 0);
+  st = imexds_get_stats(c, R.stats.data());
   if (st) return st;
   long long max_steps = 0;
-  for (int i = 0; i < n; ++i) max_steps = std::max<long long>(max_steps, stats[10 * i]);
+  for (int i = 0; i < n; ++i) max_steps = std::max<long long>(max_steps, R.stats[10 * i]);
   const int k = c->adj_k;
   const int n_ck = (int)(max_steps / k) + 1;
   // layout: instance i owns slots [off_i, off_i + cap_i + 1) of every per-cell / per-face array
-  std::vector<long long> offs(n);
+  R.offs.assign(n, 0);
   std::vector<int> caps(n);
   long long stride = 0;
+  R.oT = 0;
   for (int i = 0; i < n; ++i) {
     const int M0 = c->u0_off[i + 1] - c->u0_off[i];
-    caps[i] = std::max(M0, (int)MT[i]) + ACAP_PAD;
-    offs[i] = stride;
+    caps[i] = std::max(M0, (int)R.MT[i]) + ACAP_PAD;
+    R.offs[i] = stride;
     stride += caps[i] + 1;
+    R.oT += R.MT[i];
   }
+  R.stride = stride;
   const int n_prog = (int)c->prog_k.size();
   // one device allocation carved into the arrays
   const size_t nd_cell = 28, nb_cell = 6, ni_cell = 1;
@@ -3077,6 +3336,10 @@ imexds_status imexds_adjoint(imexds_ctx* c, const double* dJ_dw_T, const double*
   bytes += al(sizeof(ACk) * (size_t)n * n_ck) + al(sizeof(int) * n);
   bytes += 3 * al(sizeof(double) * stride * k) + 2 * al(stride * k) + al(sizeof(int) * (size_t)n * k);
   bytes += al(sizeof(StepRec) * (size_t)n * k);
+  // device variant: slot offsets, final and initial offsets, initial face kinds, the forward run's final
+  // lists for the replay check, per-instance deviations
+  bytes += al(sizeof(long long) * n) + 2 * al(sizeof(int) * (n + 1)) + 2 * al(stride) + 3 * al(sizeof(double) * stride);
+  bytes += al(sizeof(double) * n);
   if (bytes > c->adj_bytes) {
     if (c->adj_mem) cudaFree(c->adj_mem);
     c->adj_mem = nullptr;
@@ -3090,7 +3353,8 @@ imexds_status imexds_adjoint(imexds_ctx* c, const double* dJ_dw_T, const double*
     p += al(b);
     return (void*)q;
   };
-  ADev A{};
+  ADev& A = R.A;
+  A = ADev{};
   A.n_inst = n;
   A.k = k;
   A.n_ck = n_ck;
@@ -3126,16 +3390,25 @@ imexds_status imexds_adjoint(imexds_ctx* c, const double* dJ_dw_T, const double*
   A.tp_fpb = (unsigned char*)take(stride * k);
   A.tp_M = (int*)take(sizeof(int) * (size_t)n * k);
   A.rec = (StepRec*)take(sizeof(StepRec) * (size_t)n * k);
-  // initial lists (faces as in imexds_set_states: positions accumulate from the last fixed face) and seeds
+  R.d_offs = (long long*)take(sizeof(long long) * n);
+  R.d_toff = (int*)take(sizeof(int) * (n + 1));
+  R.d_u0off = (int*)take(sizeof(int) * (n + 1));
+  R.d_fpb0 = (unsigned char*)take(stride);
+  R.chk_ph = (unsigned char*)take(stride);
+  R.chk_w = (double*)take(sizeof(double) * stride);
+  R.chk_r = (double*)take(sizeof(double) * stride);
+  R.chk_m = (double*)take(sizeof(double) * stride);
+  R.d_err = (double*)take(sizeof(double) * n);
+  // initial lists (faces as in imexds_set_states: positions accumulate from the last fixed face)
   std::vector<double> hw(stride, 0.0), hr(stride, 0.0), hm(stride, 0.0), hfx(stride, 0.0);
-  std::vector<unsigned char> hph(stride, 0), hfpb(stride, 0);
+  std::vector<unsigned char> hph(stride, 0);
+  R.hfpb.assign(stride, 0);
+  std::vector<unsigned char>& hfpb = R.hfpb;
   std::vector<int> hfj(stride, 0);
-  std::vector<double> lw(stride, 0.0), lr(stride, 0.0), lm(stride, 0.0);
-  std::vector<AInst> hI(n);
-  int oT = 0;
+  R.hI.assign(n, AInst{});
   for (int i = 0; i < n; ++i) {
     const int a = c->u0_off[i], M0 = c->u0_off[i + 1] - a;
-    const long long o = offs[i];
+    const long long o = R.offs[i];
     const double h = (c->xR[i] - c->xL[i]) / c->N[i];
     long jfix = 0;
     double part = 0.0;
@@ -3159,17 +3432,11 @@ imexds_status imexds_adjoint(imexds_ctx* c, const double* dJ_dw_T, const double*
     }
     for (int q = 0; q < M0; ++q)  // a cell with two fixed faces is a whole number of lattice cells
       if (!hfpb[o + q] && !hfpb[o + q + 1]) hw[o + q] = (double)(hfj[o + q + 1] - hfj[o + q]) * h;
-    for (int q = 0; q < MT[i]; ++q, ++oT) {
-      lw[o + q] = dJ_dw_T ? dJ_dw_T[oT] : 0.0;
-      lr[o + q] = dJ_drho_T[oT];
-      lm[o + q] = dJ_dm_T[oT];
-    }
-    AInst& I = hI[i];
-    I = AInst{};
+    AInst& I = R.hI[i];
     I.off = o;
     I.cap = caps[i];
     I.M = M0;
-    I.M_seed = MT[i];
+    I.M_seed = R.MT[i];
     I.h = h;
     I.xL = c->xL[i];
     I.tau = c->tau[i];
@@ -3178,7 +3445,7 @@ imexds_status imexds_adjoint(imexds_ctx* c, const double* dJ_dw_T, const double*
   cudaStream_t sm = c->stream;
   st = set_ctrl(c, 0.0, 0);
   if (st) return st;
-  CK(cudaMemcpyAsync(A.I, hI.data(), sizeof(AInst) * n, cudaMemcpyHostToDevice, sm));
+  CK(cudaMemcpyAsync(A.I, R.hI.data(), sizeof(AInst) * n, cudaMemcpyHostToDevice, sm));
   if (n_prog) {
     CK(cudaMemcpyAsync(d_pk, c->prog_k.data(), sizeof(int) * n_prog, cudaMemcpyHostToDevice, sm));
     CK(cudaMemcpyAsync(d_pa, c->prog_a.data(), sizeof(double) * n_prog, cudaMemcpyHostToDevice, sm));
@@ -3190,107 +3457,202 @@ imexds_status imexds_adjoint(imexds_ctx* c, const double* dJ_dw_T, const double*
   CK(cudaMemcpyAsync(A.ph, hph.data(), stride, cudaMemcpyHostToDevice, sm));
   CK(cudaMemcpyAsync(A.fpb, hfpb.data(), stride, cudaMemcpyHostToDevice, sm));
   CK(cudaMemcpyAsync(A.fj, hfj.data(), sizeof(int) * stride, cudaMemcpyHostToDevice, sm));
-  CK(cudaMemcpyAsync(A.lw, lw.data(), sizeof(double) * stride, cudaMemcpyHostToDevice, sm));
-  CK(cudaMemcpyAsync(A.lr, lr.data(), sizeof(double) * stride, cudaMemcpyHostToDevice, sm));
-  CK(cudaMemcpyAsync(A.lm, lm.data(), sizeof(double) * stride, cudaMemcpyHostToDevice, sm));
+  // seeds in the slots of the final lists
+  if (dev_seeds) {
+    std::vector<int> toff(n + 1, 0);
+    for (int i = 0; i < n; ++i) toff[i + 1] = toff[i] + R.MT[i];
+    CK(cudaMemcpyAsync(R.d_offs, R.offs.data(), sizeof(long long) * n, cudaMemcpyHostToDevice, sm));
+    CK(cudaMemcpyAsync(R.d_toff, toff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, sm));
+    CK(cudaMemcpyAsync(R.d_u0off, c->u0_off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, sm));
+    CK(cudaMemcpyAsync(R.d_fpb0, hfpb.data(), stride, cudaMemcpyHostToDevice, sm));
+    CK(cudaMemsetAsync(A.lw, 0, sizeof(double) * stride, sm));
+    CK(cudaMemsetAsync(A.lr, 0, sizeof(double) * stride, sm));
+    CK(cudaMemsetAsync(A.lm, 0, sizeof(double) * stride, sm));
+    k_scatter_seeds<<<n, 128, 0, sm>>>(R.d_offs, R.d_toff, dJ_dw_T, dJ_drho_T, dJ_dm_T, A.lw, A.lr, A.lm);
+    CK(cudaGetLastError());
+  } else {
+    std::vector<double> lw(stride, 0.0), lr(stride, 0.0), lm(stride, 0.0);
+    int oT = 0;
+    for (int i = 0; i < n; ++i)
+      for (int q = 0; q < R.MT[i]; ++q, ++oT) {
+        lw[R.offs[i] + q] = dJ_dw_T ? dJ_dw_T[oT] : 0.0;
+        lr[R.offs[i] + q] = dJ_drho_T[oT];
+        lm[R.offs[i] + q] = dJ_dm_T[oT];
+      }
+    CK(cudaMemcpyAsync(A.lw, lw.data(), sizeof(double) * stride, cudaMemcpyHostToDevice, sm));
+    CK(cudaMemcpyAsync(A.lr, lr.data(), sizeof(double) * stride, cudaMemcpyHostToDevice, sm));
+    CK(cudaMemcpyAsync(A.lm, lm.data(), sizeof(double) * stride, cudaMemcpyHostToDevice, sm));
+    CK(cudaStreamSynchronize(sm));  // the staging vectors leave scope
+  }
   CK(cudaMemsetAsync(A.lx, 0, sizeof(double) * stride, sm));
   CK(cudaMemsetAsync(A.pwl, 0, sizeof(double) * stride, sm));
   CK(cudaMemsetAsync(A.pwr, 0, sizeof(double) * stride, sm));
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  CK(cudaEventRecord(e0, sm));
+  CK(cudaEventCreate(&R.e0));
+  CK(cudaEventCreate(&R.e1));
+  CK(cudaEventRecord(R.e0, sm));
   k_adjoint<<<n, ATHREADS, 0, sm>>>(A);
   CK(cudaGetLastError());
-  CK(cudaEventRecord(e1, sm));
+  CK(cudaEventRecord(R.e1, sm));
+  // the host staging of the initial lists must outlive the copies
+  CK(cudaStreamSynchronize(sm));
+  return IMEXDS_OK;
+}
+
+// The kernel time of the last launch and the replay check shared by both entry points: an instance whose
+// replay took another step count or ended with another cell count than the forward run reports
+// IMEXDS_ERR_STATE; err[i] is the instance's largest deviation of its replayed final states.
+static void adjoint_finish(imexds_ctx* c, AdjRun& R, const std::vector<int>& fM, const std::vector<double>& err) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, R.e0, R.e1);
+  cudaEventDestroy(R.e0);
+  cudaEventDestroy(R.e1);
+  c->adj_ms = ms;
+  double worst = 0.0;
+  long long cell_steps = 0;
+  for (int i = 0; i < R.n; ++i) {
+    imexds::adj::AInst& I = R.hI[i];
+    if (I.status == 0 && (I.nsteps != R.stats[10 * i] || fM[i] != R.MT[i])) {
+      I.status = IMEXDS_ERR_STATE;
+      I.site = (I.nsteps != R.stats[10 * i]) ? 6 : 7;
+    }
+    if (I.status) continue;
+    worst = std::max(worst, err[i]);
+    cell_steps += (long long)I.nsteps * (c->u0_off[i + 1] - c->u0_off[i]);
+  }
+  c->adj_replay_err = worst;
+  c->adj_cell_steps = cell_steps;
+}
+
+imexds_status imexds_adjoint(imexds_ctx* c, const double* dJ_dw_T, const double* dJ_drho_T, const double* dJ_dm_T,
+                             double* dJ_dw0, double* dJ_drho0, double* dJ_dm0, double* dJ_dtau,
+                             int32_t* inst_status) {
+  if (!c || !dJ_drho_T || !dJ_dm_T || !dJ_drho0 || !dJ_dm0 || !dJ_dtau) return IMEXDS_ERR_ARG;
+  if (!c->loaded || c->u0_off.empty()) return IMEXDS_ERR_STATE;
+  AdjRun R;
+  imexds_status st = adjoint_launch(c, R, dJ_dw_T, dJ_drho_T, dJ_dm_T, false);
+  if (st) return st;
+  const int n = R.n;
+  const long long stride = R.stride;
+  const imexds::adj::ADev& A = R.A;
+  cudaStream_t sm = c->stream;
   // results
-  CK(cudaMemcpyAsync(hI.data(), A.I, sizeof(AInst) * n, cudaMemcpyDeviceToHost, sm));
+  CK(cudaMemcpyAsync(R.hI.data(), A.I, sizeof(imexds::adj::AInst) * n, cudaMemcpyDeviceToHost, sm));
+  std::vector<double> lw(stride), lr(stride), lm(stride), lx(stride), fw(stride), fr(stride), fm(stride);
+  std::vector<int> fM(n);
   CK(cudaMemcpyAsync(lw.data(), A.lw, sizeof(double) * stride, cudaMemcpyDeviceToHost, sm));
   CK(cudaMemcpyAsync(lr.data(), A.lr, sizeof(double) * stride, cudaMemcpyDeviceToHost, sm));
   CK(cudaMemcpyAsync(lm.data(), A.lm, sizeof(double) * stride, cudaMemcpyDeviceToHost, sm));
-  std::vector<double> lx(stride);
   CK(cudaMemcpyAsync(lx.data(), A.lx, sizeof(double) * stride, cudaMemcpyDeviceToHost, sm));
-  std::vector<double> fw(stride), fr(stride), fm(stride);
-  std::vector<int> fM(n);
   CK(cudaMemcpyAsync(fw.data(), A.fin_w, sizeof(double) * stride, cudaMemcpyDeviceToHost, sm));
   CK(cudaMemcpyAsync(fr.data(), A.fin_r, sizeof(double) * stride, cudaMemcpyDeviceToHost, sm));
   CK(cudaMemcpyAsync(fm.data(), A.fin_m, sizeof(double) * stride, cudaMemcpyDeviceToHost, sm));
   CK(cudaMemcpyAsync(fM.data(), A.fin_M, sizeof(int) * n, cudaMemcpyDeviceToHost, sm));
   CK(cudaStreamSynchronize(sm));
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  c->adj_ms = ms;
   // the replay must reproduce the last forward: same steps, same cells, states to round-off
   std::vector<int32_t> toff(n + 1);
-  std::vector<double> gw(oT), gr(oT), gm(oT), gt(n);
-  std::vector<uint8_t> gph(oT);
+  std::vector<double> gw(R.oT), gr(R.oT), gm(R.oT), gt(n);
+  std::vector<uint8_t> gph(R.oT);
   std::vector<int32_t> gst(n);
   st = imexds_get_states(c, toff.data(), gw.data(), gr.data(), gm.data(), gph.data(), gt.data(), gst.data());
   if (st) return st;
-  double err = 0.0;
-  long long cell_steps = 0;
+  std::vector<double> err(n, 0.0);
   for (int i = 0; i < n; ++i) {
-    AInst& I = hI[i];
-    if (I.status == 0 && (I.nsteps != stats[10 * i] || fM[i] != MT[i])) {
-      I.status = IMEXDS_ERR_STATE;
-      I.site = (I.nsteps != stats[10 * i]) ? 6 : 7;
-    }
-    if (I.status) continue;
+    if (fM[i] != R.MT[i]) continue;
     double rmax = 0.0, dr = 0.0, dm = 0.0, dw = 0.0;
-    for (int q = 0; q < MT[i]; ++q) rmax = std::max(rmax, std::fabs(gr[toff[i] + q]));
-    for (int q = 0; q < MT[i]; ++q) {
-      const long long o = offs[i] + q;
+    for (int q = 0; q < R.MT[i]; ++q) rmax = std::max(rmax, std::fabs(gr[toff[i] + q]));
+    for (int q = 0; q < R.MT[i]; ++q) {
+      const long long o = R.offs[i] + q;
       dr = std::max(dr, std::fabs(fr[o] - gr[toff[i] + q]));
       dm = std::max(dm, std::fabs(fm[o] - gm[toff[i] + q]));
       dw = std::max(dw, std::fabs(fw[o] - gw[toff[i] + q]) / ((c->xR[i] - c->xL[i]) / c->N[i]));
     }
-    err = std::max(err, std::max(dr / rmax, std::max(dm / rmax, dw)));
-    cell_steps += (long long)I.nsteps * (c->u0_off[i + 1] - c->u0_off[i]);
+    err[i] = std::max(dr / rmax, std::max(dm / rmax, dw));
   }
-  c->adj_replay_err = err;
-  c->adj_cell_steps = cell_steps;
+  adjoint_finish(c, R, fM, err);
   c->adj_fin_off.assign(n + 1, 0);
   c->adj_fin_w.clear();
   c->adj_fin_r.clear();
   c->adj_fin_m.clear();
   c->adj_site.assign(n, 0);
   for (int i = 0; i < n; ++i) {
-    const long long o = offs[i];
+    const long long o = R.offs[i];
     for (int q = 0; q < fM[i]; ++q) {
       c->adj_fin_w.push_back(fw[o + q]);
       c->adj_fin_r.push_back(fr[o + q]);
       c->adj_fin_m.push_back(fm[o + q]);
     }
     c->adj_fin_off[i + 1] = c->adj_fin_off[i] + fM[i];
-    c->adj_site[i] = hI[i].site;
+    c->adj_site[i] = R.hI[i].site;
   }
   // gradients with respect to the initial lists; a boundary position is the last fixed face plus the
   // widths after it, so its adjoint adds to the widths of those cells; lattice cells have fixed widths
   const double nan = std::nan("");
   for (int i = 0; i < n; ++i) {
-    const AInst& I = hI[i];
+    const imexds::adj::AInst& I = R.hI[i];
     const int a = c->u0_off[i], M0 = c->u0_off[i + 1] - a;
-    const long long o = offs[i];
+    const long long o = R.offs[i];
     if (inst_status) inst_status[i] = I.status;
     dJ_dtau[i] = I.status ? nan : I.lam_tau;
     double acc = 0.0;  // adjoint of the boundary positions to the right of the current cell, within its segment
     std::vector<double> wtot(M0, 0.0);
     for (int q = M0 - 1; q >= 0; --q) {
-      if (!hfpb[o + q + 1]) acc = 0.0;
-      if (hfpb[o + q + 1]) acc += lx[o + q + 1];
+      if (!R.hfpb[o + q + 1]) acc = 0.0;
+      if (R.hfpb[o + q + 1]) acc += lx[o + q + 1];
       wtot[q] = lw[o + q] + acc;
     }
     for (int q = 0; q < M0; ++q) {
       dJ_drho0[a + q] = I.status ? nan : lr[o + q];
       dJ_dm0[a + q] = I.status ? nan : lm[o + q];
       if (dJ_dw0) {
-        const bool lattice = !hfpb[o + q] && !hfpb[o + q + 1];
+        const bool lattice = !R.hfpb[o + q] && !R.hfpb[o + q + 1];
         dJ_dw0[a + q] = I.status ? nan : (lattice ? 0.0 : wtot[q]);
       }
     }
   }
+  return IMEXDS_OK;
+}
+
+imexds_status imexds_adjoint_device(imexds_ctx* c, const double* dJ_dw_T, const double* dJ_drho_T,
+                                    const double* dJ_dm_T, double* dJ_dw0, double* dJ_drho0, double* dJ_dm0,
+                                    double* dJ_dtau, int32_t* inst_status) {
+  if (!c || !dJ_drho_T || !dJ_dm_T || !dJ_drho0 || !dJ_dm0 || !dJ_dtau) return IMEXDS_ERR_ARG;
+  if (!c->loaded || c->u0_off.empty()) return IMEXDS_ERR_STATE;
+  AdjRun R;
+  imexds_status st = adjoint_launch(c, R, dJ_dw_T, dJ_drho_T, dJ_dm_T, true);
+  if (st) return st;
+  const int n = R.n;
+  const imexds::adj::ADev& A = R.A;
+  cudaStream_t sm = c->stream;
+  // the replay check on the device: the forward run's final lists gathered beside the replayed ones
+  std::vector<int32_t> toff(n + 1, 0);
+  for (int i = 0; i < n; ++i) toff[i + 1] = toff[i] + R.MT[i];
+  st = gather_states(c, toff.data(), R.chk_w, R.chk_r, R.chk_m, R.chk_ph);
+  if (st) return st;
+  k_replay_err<<<n, 128, 0, sm>>>(A.I, R.d_offs, R.d_toff, A.fin_w, A.fin_r, A.fin_m, R.chk_w, R.chk_r, R.chk_m,
+                                  R.d_err);
+  CK(cudaGetLastError());
+  std::vector<int> fM(n);
+  std::vector<double> err(n);
+  CK(cudaMemcpyAsync(R.hI.data(), A.I, sizeof(imexds::adj::AInst) * n, cudaMemcpyDeviceToHost, sm));
+  CK(cudaMemcpyAsync(fM.data(), A.fin_M, sizeof(int) * n, cudaMemcpyDeviceToHost, sm));
+  CK(cudaMemcpyAsync(err.data(), R.d_err, sizeof(double) * n, cudaMemcpyDeviceToHost, sm));
+  CK(cudaStreamSynchronize(sm));
+  adjoint_finish(c, R, fM, err);
+  // the replay's final lists stay on the device: imexds_adjoint_replay reports the sites only
+  c->adj_fin_off.assign(n + 1, 0);
+  c->adj_fin_w.clear();
+  c->adj_fin_r.clear();
+  c->adj_fin_m.clear();
+  c->adj_site.assign(n, 0);
+  for (int i = 0; i < n; ++i) c->adj_site[i] = R.hI[i].site;
+  // gradients into the caller's arrays, with the statuses of the check
+  CK(cudaMemcpyAsync(A.I, R.hI.data(), sizeof(imexds::adj::AInst) * n, cudaMemcpyHostToDevice, sm));
+  k_adj_grads<<<(n + 127) / 128, 128, 0, sm>>>(n, A.I, R.d_offs, R.d_u0off, R.d_fpb0, A.lw, A.lr, A.lm, A.lx,
+                                              dJ_dw0, dJ_drho0, dJ_dm0, dJ_dtau);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(sm));
+  if (inst_status)
+    for (int i = 0; i < n; ++i) inst_status[i] = R.hI[i].status;
   return IMEXDS_OK;
 }
 

@@ -21,7 +21,8 @@ EXPORTED = ["imexds_create", "imexds_set_states", "imexds_set_states_device", "i
             "imexds_status_string", "imexds_last_error_string", "imexds_reset", "imexds_set_kernel_timing",
             "imexds_get_kernel_times", "imexds_set_schedule", "imexds_check_log", "imexds_step_uniform_noalloc",
             "imexds_get_group_phase_cycles", "imexds_adjoint", "imexds_set_adjoint_checkpoint",
-            "imexds_adjoint_info", "imexds_adjoint_replay", "imexds_check_div"]
+            "imexds_adjoint_info", "imexds_adjoint_replay", "imexds_check_div", "imexds_get_states_device",
+            "imexds_adjoint_device"]
 
 
 class ImexdsError(RuntimeError):
@@ -81,6 +82,8 @@ def load():
         L.imexds_step_uniform_noalloc.argtypes = [C.POINTER(FluidS), C.c_double, C.c_int32, ip, dp, dp, vp, vp, vp,
                                                   vp, vp, vp, vp]
         L.imexds_adjoint.argtypes = [vp, dp, dp, dp, dp, dp, dp, dp, ip]
+        L.imexds_adjoint_device.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, ip]
+        L.imexds_get_states_device.argtypes = [vp, ip, vp, vp, vp, vp, dp, ip]
         L.imexds_set_adjoint_checkpoint.argtypes = [vp, C.c_int32]
         L.imexds_adjoint_info.argtypes = [vp, dp, dp, C.POINTER(C.c_int64)]
         L.imexds_adjoint_replay.argtypes = [vp, ip, dp, dp, dp, ip]
@@ -246,6 +249,22 @@ class Imexds:
                                         ph.ctypes.data_as(C.POINTER(C.c_uint8)), _dp(t), _ip(st)))
         return {"offsets": off, "widths": w, "rho": r, "m": m, "phase": ph, "t": t, "status": st}
 
+    def get_states_device(self, widths_d, rho_d, m_d, phase_d) -> dict:
+        """Device-resident get_states: the cell lists are written into the given CUDA tensors (float64 widths,
+        rho, m and uint8 phase, each with cell_counts().sum() entries); offsets, t and status come back as host
+        arrays."""
+        tot = int(self.cell_counts().sum())
+        for name, a in (("widths_d", widths_d), ("rho_d", rho_d), ("m_d", m_d), ("phase_d", phase_d)):
+            if a.shape[0] != tot:
+                raise ValueError(f"{name} has {a.shape[0]} entries, the cell lists {tot}")
+        off = np.zeros(self.n_inst + 1, dtype=np.int32)
+        t = np.zeros(self.n_inst)
+        st = np.zeros(self.n_inst, dtype=np.int32)
+        _check(load().imexds_get_states_device(self.h, _ip(off), C.c_void_p(widths_d.data_ptr()),
+                                               C.c_void_p(rho_d.data_ptr()), C.c_void_p(m_d.data_ptr()),
+                                               C.c_void_p(phase_d.data_ptr()), _dp(t), _ip(st)))
+        return {"offsets": off, "t": t, "status": st}
+
     def reset(self):
         """Restore the states given to the last set_states (device-to-device)."""
         _check(load().imexds_reset(self.h))
@@ -298,6 +317,24 @@ class Imexds:
         _check(load().imexds_adjoint(self.h, null if w is None else _dp(w), _dp(r), _dp(m), _dp(g["widths"]),
                                      _dp(g["rho"]), _dp(g["m"]), _dp(g["tau"]), _ip(g["status"])))
         return g
+
+    def adjoint_device(self, dJ_drho_T, dJ_dm_T, out_rho, out_m, out_tau, dJ_dw_T=None, out_w=None):
+        """Device-resident adjoint: seeds and outputs are CUDA tensors (float64) in the orders of adjoint();
+        dJ_dw_T and out_w may be None. Returns the per-instance statuses (host array)."""
+        nT = int(self.cell_counts().sum())
+        n0 = self._n_initial_cells()
+        for name, a, want in (("dJ_drho_T", dJ_drho_T, nT), ("dJ_dm_T", dJ_dm_T, nT), ("dJ_dw_T", dJ_dw_T, nT),
+                              ("out_rho", out_rho, n0), ("out_m", out_m, n0), ("out_w", out_w, n0),
+                              ("out_tau", out_tau, self.n_inst)):
+            if a is not None and a.shape[0] != want:
+                raise ValueError(f"{name} has {a.shape[0]} entries, expected {want}")
+        st = np.zeros(self.n_inst, dtype=np.int32)
+
+        def ptr(a):
+            return C.c_void_p(None if a is None else a.data_ptr())
+        _check(load().imexds_adjoint_device(self.h, ptr(dJ_dw_T), ptr(dJ_drho_T), ptr(dJ_dm_T), ptr(out_w),
+                                            ptr(out_rho), ptr(out_m), ptr(out_tau), _ip(st)))
+        return st
 
     def adjoint_info(self) -> dict:
         ms, err = np.zeros(1), np.zeros(1)

@@ -159,7 +159,8 @@ def test_adjoint_matches_central_differences():
 
 def test_autograd_function():
     """torch.autograd.Function over the library: the gradient of the misfit through backward() is the
-    adjoint's."""
+    adjoint's. Inputs, outputs and gradients are CUDA tensors passed to the device-resident calls; a second
+    call reuses the RunSpec's context and gives the same gradients."""
     import torch
     from paper_2211_00705_gb300.autograd import ImexdsFunction, RunSpec
     program = [("step", 60)]
@@ -168,16 +169,64 @@ def test_autograd_function():
     spec = RunSpec(b.n_lattice, b.x_left, b.x_right, b.cell_offsets, b.widths, b.phase, b.fluid, b.options,
                    program, checkpoint_every=16)
     dev = torch.device("cuda", 0)
-    rho0 = torch.tensor(b.rho, device=dev, requires_grad=True)
-    m0 = torch.tensor(b.m, device=dev, requires_grad=True)
-    tau = torch.tensor(b.tau, device=dev, requires_grad=True)
-    rT, mT = ImexdsFunction.apply(rho0, m0, tau, spec)
-    st = {"offsets": spec.last_offsets, "widths": spec.last_widths, "rho": rT.detach().cpu().numpy()}
-    _, gr = misfit(st, tgt, b)
-    (rT * torch.tensor(gr, device=dev)).sum().backward()
-    np.testing.assert_allclose(rho0.grad.cpu().numpy(), g["rho"], rtol=0, atol=1e-14 * np.max(np.abs(g["rho"])))
-    np.testing.assert_allclose(m0.grad.cpu().numpy(), g["m"], rtol=0, atol=1e-14 * np.max(np.abs(g["m"])))
-    np.testing.assert_allclose(tau.grad.cpu().numpy(), g["tau"], rtol=1e-14)
+    grads = []
+    for _ in range(2):
+        rho0 = torch.tensor(b.rho, device=dev, requires_grad=True)
+        m0 = torch.tensor(b.m, device=dev, requires_grad=True)
+        tau = torch.tensor(b.tau, device=dev, requires_grad=True)
+        rT, mT = ImexdsFunction.apply(rho0, m0, tau, spec)
+        assert rT.is_cuda and mT.is_cuda
+        st = {"offsets": spec.last_offsets, "widths": spec.last_widths.cpu().numpy(),
+              "rho": rT.detach().cpu().numpy()}
+        _, gr = misfit(st, tgt, b)
+        (rT * torch.tensor(gr, device=dev)).sum().backward()
+        assert rho0.grad.is_cuda
+        np.testing.assert_allclose(rho0.grad.cpu().numpy(), g["rho"], rtol=0, atol=1e-14 * np.max(np.abs(g["rho"])))
+        np.testing.assert_allclose(m0.grad.cpu().numpy(), g["m"], rtol=0, atol=1e-14 * np.max(np.abs(g["m"])))
+        np.testing.assert_allclose(tau.grad.cpu().numpy(), g["tau"], rtol=1e-14)
+        grads.append((rho0.grad.cpu().numpy(), m0.grad.cpu().numpy(), tau.grad.cpu().numpy()))
+    for a, c in zip(grads[0], grads[1]):
+        np.testing.assert_array_equal(a, c)
+
+
+def test_device_resident_calls_match_the_host_ones():
+    """imexds_get_states_device and imexds_adjoint_device against imexds_get_states and imexds_adjoint on a run
+    with splits, merges and created cells (cavitation): the same cell lists and the same gradients, bit for bit
+    (the same kernels; only the staging differs), widths included."""
+    import torch
+    from paper_2211_00705_gb300.imexds import Imexds
+    b = I.cavitation_batch(4, 4, n_range=(64, 128), n_steps=60)
+    b = dataclasses.replace(b, options=I.scaled_options(creation=1, tol_nb=3e-13, tol_k=3e-11))
+    ctx = Imexds.from_batch(b)
+    ctx.set_adjoint_checkpoint(16)
+    ctx.step(60)
+    s = ctx.get_states()
+    assert (ctx.stats()["creations"] >= 1).all()
+    dev = torch.device("cuda", 0)
+    n = int(s["offsets"][-1])
+    wd, rd, md = (torch.empty(n, dtype=torch.float64, device=dev) for _ in range(3))
+    phd = torch.empty(n, dtype=torch.uint8, device=dev)
+    sd = ctx.get_states_device(wd, rd, md, phd)
+    np.testing.assert_array_equal(sd["offsets"], s["offsets"])
+    np.testing.assert_array_equal(sd["t"], s["t"])
+    np.testing.assert_array_equal(wd.cpu().numpy(), s["widths"])
+    np.testing.assert_array_equal(rd.cpu().numpy(), s["rho"])
+    np.testing.assert_array_equal(md.cpu().numpy(), s["m"])
+    np.testing.assert_array_equal(phd.cpu().numpy(), s["phase"])
+    rng = np.random.default_rng(4)
+    sr, sm, sw = rng.standard_normal(n), rng.standard_normal(n), rng.standard_normal(n)
+    g = ctx.adjoint(sr, sm, sw)
+    n0 = int(b.cell_offsets[-1])
+    out = [torch.empty(n0, dtype=torch.float64, device=dev) for _ in range(3)]
+    out_t = torch.empty(b.n_inst, dtype=torch.float64, device=dev)
+    t = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    st = ctx.adjoint_device(t(sr), t(sm), out[0], out[1], out_t, dJ_dw_T=t(sw), out_w=out[2])
+    ctx.close()
+    assert (st == 0).all() and (g["status"] == 0).all()
+    np.testing.assert_array_equal(out[0].cpu().numpy(), g["rho"])
+    np.testing.assert_array_equal(out[1].cpu().numpy(), g["m"])
+    np.testing.assert_array_equal(out[2].cpu().numpy(), g["widths"])
+    np.testing.assert_array_equal(out_t.cpu().numpy(), g["tau"])
 
 
 def test_adjoint_segments_do_not_change_the_gradient():
