@@ -34,12 +34,13 @@ UNIT = "cell-steps/s"
 # flux components with the division (2 x 7); update (6)
 SWEEP_FLOP_PER_CELL = 33
 FP64_PEAK_TFLOPS = 1.25   # GB300 dense FP64 (nominal; no FP64 figure in MEASURED_PEAKS.json)
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_sweep launch on this workload from an ncu capture of
-# the per-step schedule; None until the current k_sweep has been captured
-SWEEP_TRAFFIC_BYTES = None
-# DRAM bytes per explicit cell-step of the resident group kernel (ncu capture of a scaled-down run of this
-# workload, scaled to a full launch by its cell-steps); None until the current k_group has been captured
-GROUP_TRAFFIC_BYTES_PER_CELL_STEP = None
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture each; profiles/) of the kernels as
+# committed, for the traffic entry of the roofline objects: the per-step sweep per lattice cell it updates (a
+# launch with every instance active: 198.4 MB for 4.48 M cells), the resident group kernel per explicit
+# cell-step of a whole run of this workload (dual time, 96 threads: 185.3 GB for 3.69e9; Newton, 256 threads:
+# 177.1 GB). Scaled by the cells or cell-steps of the launch being reported.
+SWEEP_TRAFFIC_BYTES_PER_CELL = 44.31
+GROUP_TRAFFIC_BYTES_PER_CELL_STEP = {0: 50.24, 1: 48.03}
 
 
 def dist_env():
@@ -171,8 +172,12 @@ def measure_cavitation(dev, scale=1.0, n_steps=5000, adj_inst=1024, fd_inst=4):
             "block_iters_per_step": float(st["dts_iters"].sum() / max(1, st["steps"].sum())),
             "creations_per_instance": float(st["creations"].mean()),
             "instance_status_nonzero": int(np.count_nonzero(status))}
-    # dJ/dV by the adjoint on a sample, Newton forward run
+    # dJ/dV by the adjoint on a sample, Newton forward run, block tolerances x 1e-4 (the adjoint differentiates
+    # the converged block systems; near the production tolerance a stop decision taken one iteration apart moves
+    # a state by up to the tolerance, which central differences would see)
     sb = with_block_solver(b.subset(list(range(min(adj_inst, b.n_inst)))), 1)
+    sb = dataclasses.replace(sb, options=dataclasses.replace(sb.options, tol_nb=sb.options.tol_nb * 1e-4,
+                                                             tol_k=sb.options.tol_k * 1e-4))
     sb.n_steps = n_steps
 
     def mean_pressure(st, bb):
@@ -230,11 +235,13 @@ def measure_cavitation(dev, scale=1.0, n_steps=5000, adj_inst=1024, fd_inst=4):
     return out
 
 
-def measure_large_domain_sweep(n_steps=100):
-    """The explicit sweep on the large single domain (2^24 cells, 1024 vapour bubbles, 2048 boundaries): the
-    per-step schedule with CUDA events around every kernel; the sweep's algorithmic traffic is 32 B per
-    lattice cell (rho, m read and written; phase and owner bytes not counted) against the measured HBM copy
-    bandwidth. State arrays: 2 x 268 MB, far above L2, so every launch streams from HBM."""
+def measure_large_domain_sweep(n_steps=100, full_steps=1000):
+    """The large single domain (2^24 cells, 1024 vapour bubbles, 2048 boundaries), per-step schedule. (1) The
+    explicit sweep: n_steps steps with CUDA events around every kernel; its algorithmic traffic is 32 B per
+    lattice cell (rho, m read and written) against the measured HBM copy bandwidth (state arrays 2 x 268 MB,
+    far above L2, so every launch streams from HBM). (2) The workload's configured 1000 steps timed whole, with
+    dual time stepping and with Newton's method on the blocks (cell-steps per second)."""
+    import torch
     from paper_2211_00705_gb300 import inputs as I
     from paper_2211_00705_gb300.imexds import Imexds
     b = I.workload(2)
@@ -250,17 +257,33 @@ def measure_large_domain_sweep(n_steps=100):
     per = ms / 1e3 / max(n, 1)
     cells = int(b.n_lattice[0])
     gbs = 32.0 * cells / per / 1e9
-    peak = None
-    try:
-        peak = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))["hbm_gbs"]
-    except (OSError, ValueError, KeyError):
-        peak = None
+    peak = load_peak("hbm_gbs")
     tot = sum(v[0] for v in kt.values())
-    return {"workload": b.name, "steps_timed": n_steps, "k_sweep_ms_per_launch": per * 1e3,
-            "algorithmic_bytes_per_launch": 32.0 * cells, "achieved_gbs": gbs, "peak_gbs": peak,
-            "frac": (gbs / peak) if peak else None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-            "cell_steps_per_s_sweep": cells / per, "status": int(st["status"][0]),
-            "per_step_share": {k: round(v[0] / tot, 4) if tot else None for k, v in kt.items()}}
+    out = {"workload": b.name, "steps_timed": n_steps, "k_sweep_ms_per_launch": per * 1e3,
+           "algorithmic_bytes_per_launch": 32.0 * cells, "achieved_gbs": gbs, "peak_gbs": peak,
+           "frac": (gbs / peak) if peak else None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+           "cell_steps_per_s_sweep": cells / per, "status": int(st["status"][0]),
+           "per_step_share": {k: round(v[0] / tot, 4) if tot else None for k, v in kt.items()}}
+    for solver in (0, 1):
+        bb = with_block_solver(b, solver)
+        ctx = Imexds.from_batch(bb, schedule=1)
+        ctx.step(8)
+        ctx.reset()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.step(full_steps)
+        e1.record()
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+        stt = ctx.stats()
+        cs = float(np.sum(stt["steps"] * ctx.cell_counts()))
+        out["newton" if solver else "dual_time"] = {
+            "steps": full_steps, "seconds": secs, "ms_per_step": 1e3 * secs / full_steps, "value": cs / secs,
+            "unit": UNIT, "block_iters_per_step_per_block": float(stt["dts_iters"].sum() / max(1, stt["steps"].sum()) / 2048),
+            "status": int(ctx.get_states()["status"][0])}
+        ctx.close()
+    return out
 
 
 def measure_plain(batch, n_sample=16):
@@ -570,8 +593,10 @@ def measure_run(batch, steps, warmup, schedule, flush, barrier, sampler=None, ws
     gbs = 32.0 * cs_launch / per_launch_s / 1e9 if per_launch_s > 0 else None
     roof = {"bound": "alu", "kernel": dominant, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": (ach / FP64_PEAK_TFLOPS) if ach else None,
-            "traffic": (GROUP_TRAFFIC_BYTES_PER_CELL_STEP * cs_launch
-                        if dominant == "k_group" and GROUP_TRAFFIC_BYTES_PER_CELL_STEP else None),
+            "traffic": (GROUP_TRAFFIC_BYTES_PER_CELL_STEP[batch.options.block_solver] * cs_launch
+                        if dominant == "k_group" else None),
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one full launch (profiles/"
+                              "k_group_riemann4096.md), per explicit cell-step, times this launch's cell-steps",
             "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table; no FP64 entry in MEASURED_PEAKS.json)",
             "ms_per_launch": per_launch_s * 1e3, "launches_per_run": launches_per_run,
             "algorithmic_flops_per_launch": SWEEP_FLOP_PER_CELL * cs_launch,
@@ -703,7 +728,9 @@ def main():
     roof["sweep_per_step_schedule"] = {
         "kernel": "k_sweep", "bound": "alu", "achieved": sw_ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
         "frac": (sw_ach / FP64_PEAK_TFLOPS) if sw_ach else None,
-        "traffic": SWEEP_TRAFFIC_BYTES if args.scale == 1.0 else None,
+        "traffic": SWEEP_TRAFFIC_BYTES_PER_CELL * sweep_cells / n_sw,
+        "traffic_source": "ncu DRAM bytes of one launch with every instance active (profiles/k_sweep_riemann4096.md) "
+                          "per lattice cell, times this run's average cells per launch",
         "algorithmic_bytes": 32.0 * sweep_cells / n_sw, "ms_per_launch": per_launch_s * 1e3,
         "share": {k: round(v[0] / tot, 4) if tot else None for k, v in kt_steps.items()},
         "ms_per_launch_by_kernel": {k: (v[0] / v[1] if v[1] else None) for k, v in kt_steps.items()}}

@@ -959,11 +959,22 @@ void step_instance(const Fluid& F, const orc_opts& o, Inst<T>& I, double t_end) 
           I.status = ORC_ERR_PB_NOCONV;
           return;
         }
+        // a correction below 1e-14 max(|W|, 1) in every component cannot move the iterate further than its own
+        // rounding (the residual has reached the floor rounding puts under it): stop as at l_max
+        bool at_floor = true;
+        for (int r = 0; r < n2; ++r) {
+          const double w = std::fabs(val((r % 2 == 0) ? Wr[lo + r / 2] : Wm[lo + r / 2]));
+          at_floor = at_floor && std::fabs(val(A[r][n2])) <= 1e-14 * std::max(w, 1.0);
+        }
         for (int r = 0; r < n2; ++r) {
           if (r % 2 == 0)
             Wr[lo + r / 2] = Wr[lo + r / 2] + A[r][n2];
           else
             Wm[lo + r / 2] = Wm[lo + r / 2] + A[r][n2];
+        }
+        if (at_floor) {
+          ++l;
+          break;
         }
       }
     } else {

@@ -373,18 +373,18 @@ __device__ bool dts_block(const ADev& A, AInst& I, const SharedStep& S, int lo, 
     // Newton on the block's system R(W) = W - T(W) with the stop test of Sec. 4 (the forward kernels'
     // newton_simple / newton_general): fluxes at W, T(W), the test, then (I - dT/dW) dW = T(W) - W
     const double dtr = (c_opts.res_mode == 1) ? 1.0 : dt;
-    const int n2 = 2 * nb;
     for (int l = 0; l < c_opts.l_max; ++l) {
       int e = fluxes();
       if (e) {
         afail(I, e == 1 ? IMEXDS_ERR_PB_NOCONV : IMEXDS_ERR_VANISH);
         return false;
       }
-      double Tr[AMAXB], Tm[AMAXB];
+      double Tr[AMAXB], Tm[AMAXB], ih[AMAXB];
       stop = true;
       for (int q = 0; q < nb; ++q) {
-        Tr[q] = (Uw[q] * Ur[q] - dt * (F0[q + 1] - F0[q])) / hl[q];
-        Tm[q] = (Uw[q] * Um[q] - dt * (F1[q + 1] - F1[q])) / hl[q];
+        ih[q] = 1.0 / hl[q];
+        Tr[q] = (Uw[q] * Ur[q] - dt * (F0[q + 1] - F0[q])) * ih[q];
+        Tm[q] = (Uw[q] * Um[q] - dt * (F1[q + 1] - F1[q])) * ih[q];
         const double lim = (tiny[q] ? c_opts.tol_k : c_opts.tol_nb) * dtr;
         stop = stop && (fabs(Tr[q] - Wr[q]) < lim * fmax(fabs(Wr[q]), 1.0)) &&
                (fabs(Tm[q] - Wm[q]) < lim * fmax(fabs(Wm[q]), 1.0));
@@ -392,38 +392,17 @@ __device__ bool dts_block(const ADev& A, AInst& I, const SharedStep& S, int lo, 
       if (stop) break;
       for (int q = 1; q < nb; ++q)
         if (!fp[q]) hll_jac(c_fluid.ph[ph[q]], Wr[q - 1], Wm[q - 1], Wr[q], Wm[q], fj[q]);
-      double Ab[2 * AMAXB][BAND_W], rhs[2 * AMAXB];
-      for (int r = 0; r < n2; ++r) {
-        for (int k = 0; k < BAND_W; ++k) Ab[r][k] = 0.0;
-        Ab[r][3] = 1.0;
-      }
-      for (int q = 0; q < nb; ++q) {
-        const double coef = dt / hl[q];
-        rhs[2 * q] = Tr[q] - Wr[q];
-        rhs[2 * q + 1] = Tm[q] - Wm[q];
-        for (int c = 0; c < 2; ++c) {
-          const int row = 2 * q + c;
-          const double Tq = c ? Tm[q] : Tr[q];
-          if (q + 1 < nb) {
-            const FaceJac& J = fj[q + 1];
-            for (int k = 0; k < 4; ++k)
-              Ab[row][2 * q + k - row + 3] += coef * ((c ? J.dF1[k] : J.dF0[k]) + Tq * J.dw[k]);
-          }
-          if (q >= 1) {
-            const FaceJac& J = fj[q];
-            for (int k = 0; k < 4; ++k)
-              Ab[row][2 * (q - 1) + k - row + 3] -= coef * ((c ? J.dF1[k] : J.dF0[k]) + Tq * J.dw[k]);
-          }
-        }
-      }
-      if (!solve_band(Ab, rhs, n2)) {
+      double dr[AMAXB], dmv[AMAXB];
+      if (!newton_block_step(nb, dt, ih, Tr, Tm, Wr, Wm, fj, dr, dmv)) {
         afail(I, IMEXDS_ERR_PB_NOCONV);
         return false;
       }
+      const bool at_floor = newton_at_floor(nb, Wr, Wm, dr, dmv);
       for (int q = 0; q < nb; ++q) {
-        Wr[q] += rhs[2 * q];
-        Wm[q] += rhs[2 * q + 1];
+        Wr[q] += dr[q];
+        Wm[q] += dmv[q];
       }
+      if (at_floor) break;
     }
   }
   for (int l = 0; !newton_solver && l < c_opts.l_max && !stop; ++l) {

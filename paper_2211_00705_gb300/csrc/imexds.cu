@@ -72,6 +72,7 @@ struct Inst {
   int status, active, parity, clipped;
   unsigned long long smax_bits;
   int n_ev;
+  int n_work;  // entries of the work list of post_inst
   long long stats[N_STATS];  // steps, dts_iters, dts_max, newton, merges, splits, creations, maxiter, pb_solves
 };
 
@@ -102,6 +103,7 @@ struct Dev {
   Inst* inst;
   Event* ev;
   int2* tiles;  // (instance, first lattice cell)
+  int* work;    // per instance (zone_off ..): zones for post_inst (n_work of them)
   Ctrl* ctrl;
 };
 
@@ -683,10 +685,8 @@ __device__ __noinline__ bool newton_general(const Dev& d, Zone& Z, Inst& I, int 
   const double dtr = (c_opts.res_mode == 1) ? 1.0 : dt;
   for (int b = 0; b < Z.nblk; ++b) {
     const int lo = Z.blo[b] - e0, hi = Z.bhi[b] - e0;
-    const int n2 = 2 * (hi - lo + 1);
-    double Wr[ZB], Wm[ZB], F0[ZB + 1], F1[ZB + 1], wc[ZB + 1], hl[ZB], Tr[ZB], Tm[ZB];
+    double Wr[ZB], Wm[ZB], F0[ZB + 1], F1[ZB + 1], wc[ZB + 1], hl[ZB], Tr[ZB], Tm[ZB], ih[ZB], dr[ZB], dm[ZB];
     FaceJac fj[ZB + 1];
-    double A[2 * ZB][BAND_W], rhs[2 * ZB];
     for (int q = 0; q < nq; ++q) {
       Wr[q] = B.r[q];
       Wm[q] = B.m[q];
@@ -734,8 +734,9 @@ __device__ __noinline__ bool newton_general(const Dev& d, Zone& Z, Inst& I, int 
       if (fail) break;
       stop = true;
       for (int q = lo; q <= hi; ++q) {
-        Tr[q] = (B.w[q] * B.r[q] - dt * (F0[q + 1] - F0[q])) / hl[q];
-        Tm[q] = (B.w[q] * B.m[q] - dt * (F1[q + 1] - F1[q])) / hl[q];
+        ih[q] = 1.0 / hl[q];
+        Tr[q] = (B.w[q] * B.r[q] - dt * (F0[q + 1] - F0[q])) * ih[q];
+        Tm[q] = (B.w[q] * B.m[q] - dt * (F1[q + 1] - F1[q])) * ih[q];
         const double lim = (((Z.tiny_mask >> (q + e0 + 1)) & 1u) ? c_opts.tol_k : c_opts.tol_nb) * dtr;
         stop = stop && (fabs(Tr[q] - Wr[q]) < lim * fmax(fabs(Wr[q]), 1.0)) &&
                (fabs(Tm[q] - Wm[q]) < lim * fmax(fabs(Wm[q]), 1.0));
@@ -743,37 +744,18 @@ __device__ __noinline__ bool newton_general(const Dev& d, Zone& Z, Inst& I, int 
       if (stop) break;
       for (int g = lo + 1; g <= hi; ++g)
         if (!B.fpb[g]) hll_jac(c_fluid.ph[B.ph[g]], Wr[g - 1], Wm[g - 1], Wr[g], Wm[g], fj[g]);
-      for (int r = 0; r < n2; ++r) {
-        for (int k = 0; k < BAND_W; ++k) A[r][k] = 0.0;
-        A[r][3] = 1.0;  // the identity (column r)
-      }
-      for (int q = lo; q <= hi; ++q) {
-        const int i = q - lo;
-        const double coef = dt / hl[q];
-        rhs[2 * i] = Tr[q] - Wr[q];
-        rhs[2 * i + 1] = Tm[q] - Wm[q];
-        for (int c = 0; c < 2; ++c) {
-          const int row = 2 * i + c;
-          const double Tq = c ? Tm[q] : Tr[q];
-          if (q + 1 <= hi) {  // right face: + coef (dF + T dw) on the columns of cells q, q+1
-            const FaceJac& J = fj[q + 1];
-            for (int k = 0; k < 4; ++k)
-              A[row][2 * i + k - row + 3] += coef * ((c ? J.dF1[k] : J.dF0[k]) + Tq * J.dw[k]);
-          }
-          if (q - 1 >= lo) {  // left face: - coef (dF + T dw) on the columns of cells q-1, q
-            const FaceJac& J = fj[q];
-            for (int k = 0; k < 4; ++k)
-              A[row][2 * (i - 1) + k - row + 3] -= coef * ((c ? J.dF1[k] : J.dF0[k]) + Tq * J.dw[k]);
-          }
-        }
-      }
-      if (!solve_band(A, rhs, n2)) {
+      if (!newton_block_step(hi - lo + 1, dt, ih + lo, Tr + lo, Tm + lo, Wr + lo, Wm + lo, fj + lo, dr, dm)) {
         fail = 3;
         break;
       }
+      const bool at_floor = newton_at_floor(hi - lo + 1, Wr + lo, Wm + lo, dr, dm);
       for (int q = lo; q <= hi; ++q) {
-        Wr[q] += rhs[2 * (q - lo)];
-        Wm[q] += rhs[2 * (q - lo) + 1];
+        Wr[q] += dr[q - lo];
+        Wm[q] += dm[q - lo];
+      }
+      if (at_floor) {
+        ++l;
+        break;
       }
     }
     if (!fail && !stop) fail = fluxes();
@@ -1092,44 +1074,24 @@ __device__ __noinline__ void newton_simple(const Dev& d, int zi) {
              (fabs(T1[q] - W1[q]) < lim[q] * fmax(fabs(W1[q]), 1.0));
     }
     if (stop) break;
-    // dR/dW = I - dT/dW (rows and columns (q, component)), right-hand side T - W
-    FaceJac Jh;
-    hll_jac(c_fluid.ph[ph[b]], W0[b - 1], W1[b - 1], W0[b], W1[b], Jh);
-    double A[6][7];
-#pragma unroll
-    for (int r = 0; r < 6; ++r) {
-#pragma unroll
-      for (int c = 0; c < 6; ++c) A[r][c] = (r == c) ? 1.0 : 0.0;
-      A[r][6] = (r & 1) ? T1[r >> 1] - W1[r >> 1] : T0[r >> 1] - W0[r >> 1];
-    }
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const double coef = dt * ih[q];
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const double Tq = c ? T1[q] : T0[q];
-        if (q + 1 <= 2) {  // right face q+1: + coef (dF + T dw), columns of cells q, q+1
-          const FaceJac& J = (q + 1 == PBF) ? Jp : Jh;
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            A[2 * q + c][2 * q + k] += coef * ((c ? J.dF1[k] : J.dF0[k]) + Tq * J.dw[k]);
-        }
-        if (q >= 1) {  // left face q: - coef (dF + T dw), columns of cells q-1, q
-          const FaceJac& J = (q == PBF) ? Jp : Jh;
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            A[2 * q + c][2 * (q - 1) + k] -= coef * ((c ? J.dF1[k] : J.dF0[k]) + Tq * J.dw[k]);
-        }
-      }
-    }
-    if (!solve_dense<6>(A)) {
+    // Newton step: (I - dT/dW) d = T - W
+    FaceJac fjs[3];
+    fjs[PBF] = Jp;
+    hll_jac(c_fluid.ph[ph[b]], W0[b - 1], W1[b - 1], W0[b], W1[b], fjs[b]);
+    double d0[3], d1[3];
+    if (!newton_block_step(3, dt, ih, T0, T1, W0, W1, fjs, d0, d1)) {
       fail = 3;
       break;
     }
+    const bool at_floor = newton_at_floor(3, W0, W1, d0, d1);
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      W0[q] += A[2 * q][6];
-      W1[q] += A[2 * q + 1][6];
+      W0[q] += d0[q];
+      W1[q] += d1[q];
+    }
+    if (at_floor) {
+      ++l;
+      break;
     }
   }
   // Part 2 needs the fluxes at U^{n,*}: those of the last evaluation when the test stopped the iteration,
@@ -1394,33 +1356,52 @@ __device__ __noinline__ void dts_zone_general(const Dev& d, int zi) {
 // cells at the zone ends to the lattice, turn creation events into zones, join zones closer than
 // ZONE_GAP, then advance t and set the next dt from the wave-speed maximum.
 
-__device__ __noinline__ void post_inst(const Dev& d, int ii) {
-  Inst& I = d.inst[ii];
+// Grid management after the step (Sec. 2.3, 3.4), the part of one zone: its owned lattice range is returned,
+// boundary cells wider than split_ratio*h are split (fixed faces stay on the lattice), regular cells at its ends
+// return to the lattice. A zone whose footprint changed in this step or that holds an interior run of ZONE_GAP
+// regular lattice cells goes on its instance's work list for post_inst. Touches only this zone and the lattice
+// cells it owns, so the zones of an instance can run in parallel (k_post_zones).
+__device__ inline bool zone_interior_run(const Zone& Z, double h, int& a_out, int& b_out) {
+  int a = -1, b = -1;
+  for (int k = 1; k < Z.nc - 1 && b < 0; ++k) {
+    bool reg = !Z.fpb[k] && !Z.fpb[k + 1] && Z.fj[k + 1] == Z.fj[k] + 1 && Z.w[k] == h;
+    if (reg) {
+      if (a < 0) a = k;
+      if (k + 1 - a >= ZONE_GAP) {
+        int e = k + 1;  // extend to the end of the run
+        while (e < Z.nc - 1 && !Z.fpb[e] && !Z.fpb[e + 1] && Z.fj[e + 1] == Z.fj[e] + 1 && Z.w[e] == h) ++e;
+        b = e;
+      }
+    } else {
+      a = -1;
+    }
+  }
+  a_out = a;
+  b_out = b;
+  return b >= 0;
+}
+
+__device__ __noinline__ void post_zone(const Dev& d, int zs) {
+  Zone& Z = d.zones[zs];
+  if (!Z.alive) return;
+  Inst& I = d.inst[Z.inst];
   if (!I.active) return;
-  const double h = I.h;
   int* own = d.own + I.lat_off;
+  for (int j = Z.oA; j < Z.oB; ++j) own[j] = -1;
+  Z.oA = Z.oB = 0;
+  if (I.status) {
+    if (Z.changed) d.work[I.zone_off + atomicAdd(&I.n_work, 1)] = zs;
+    return;
+  }
+  const double h = I.h;
   const int nxt = I.parity ^ 1;
   double* nr = d.R(nxt) + I.lat_off;
   double* nm = d.M(nxt) + I.lat_off;
   double* nu = d.U(nxt) + I.lat_off;
   unsigned char* lph = d.phase + I.lat_off;
-  Zone* zones = d.zones + I.zone_off;
-  for (int z = 0; z < I.zone_cap; ++z) {
-    Zone& Z = zones[z];
-    if (!Z.alive) continue;
-    for (int j = Z.oA; j < Z.oB; ++j) own[j] = -1;
-    Z.oA = Z.oB = 0;
-  }
-  if (I.status) {
-    I.active = 0;
-    I.n_ev = 0;
-    return;
-  }
-  long long splits = 0, creations = 0;
+  long long splits = 0;
   // splits
-  for (int z = 0; z < I.zone_cap; ++z) {
-    Zone& Z = zones[z];
-    if (!Z.alive) continue;
+  {
     for (int i = 0; i < Z.nc; ++i) {
       bool lpb = Z.fpb[i], rpb = Z.fpb[i + 1];
       if (!(lpb || rpb) || !(Z.w[i] > c_opts.split_ratio * h)) continue;
@@ -1459,9 +1440,7 @@ __device__ __noinline__ void post_inst(const Dev& d, int ii) {
     }
   }
   // release regular cells at the zone ends back to the lattice (a pure change of representation)
-  for (int z = 0; z < I.zone_cap; ++z) {
-    Zone& Z = zones[z];
-    if (!Z.alive) continue;
+  {
     while (Z.nc > 1 && !Z.fpb[1] && Z.fj[1] == Z.A + 1 && Z.w[0] == h) {
       nr[Z.A] = Z.r[0];
       nm[Z.A] = Z.m[0];
@@ -1485,26 +1464,53 @@ __device__ __noinline__ void post_inst(const Dev& d, int ii) {
       Z.changed = 1;
     }
   }
+  if (splits) atomicAdd((unsigned long long*)&I.stats[5], (unsigned long long)splits);
+  int ra, rb;
+  if (Z.changed || zone_interior_run(Z, h, ra, rb)) d.work[I.zone_off + atomicAdd(&I.n_work, 1)] = zs;
+}
+
+// Grid management after the step, the part of an instance (one thread), after post_zone has run for every
+// zone of the instance: zones split at an interior run of ZONE_GAP regular lattice cells, creation events turned
+// into zones, zones closer than ZONE_GAP lattice cells joined (only zones on the work list changed their
+// footprint, so only they are checked against their neighbours), then t += dt and the next dt from the
+// wave-speed maximum.
+__device__ __noinline__ void post_inst(const Dev& d, int ii) {
+  Inst& I = d.inst[ii];
+  if (!I.active) return;
+  const double h = I.h;
+  const int nxt = I.parity ^ 1;
+  double* nr = d.R(nxt) + I.lat_off;
+  double* nm = d.M(nxt) + I.lat_off;
+  double* nu = d.U(nxt) + I.lat_off;
+  unsigned char* lph = d.phase + I.lat_off;
+  Zone* zones = d.zones + I.zone_off;
+  int* work = d.work + I.zone_off;  // global zone slots
+  int nw = I.n_work;
+  I.n_work = 0;
+  if (I.status) {
+    for (int w = 0; w < nw; ++w) d.zones[work[w]].changed = 0;
+    I.active = 0;
+    I.n_ev = 0;
+    return;
+  }
+  // the work list in slot order (post_zone appends in any order)
+  for (int w = 1; w < nw; ++w) {
+    const int v = work[w];
+    int x = w - 1;
+    while (x >= 0 && work[x] > v) {
+      work[x + 1] = work[x];
+      --x;
+    }
+    work[x + 1] = v;
+  }
+  long long creations = 0;
   // split a zone at an interior run of at least ZONE_GAP regular lattice cells (returned to the lattice);
   // the part right of the run becomes a new zone (a pure change of representation)
-  for (int z = 0; z < I.zone_cap; ++z) {
-    Zone& Z = zones[z];
+  for (int w = 0; w < nw; ++w) {
+    Zone& Z = d.zones[work[w]];
     if (!Z.alive) continue;
-    int a = -1, b = -1;
-    for (int k = 1; k < Z.nc - 1 && b < 0; ++k) {
-      bool reg = !Z.fpb[k] && !Z.fpb[k + 1] && Z.fj[k + 1] == Z.fj[k] + 1 && Z.w[k] == h;
-      if (reg) {
-        if (a < 0) a = k;
-        if (k + 1 - a >= ZONE_GAP) {
-          int e = k + 1;  // extend to the end of the run
-          while (e < Z.nc - 1 && !Z.fpb[e] && !Z.fpb[e + 1] && Z.fj[e + 1] == Z.fj[e] + 1 && Z.w[e] == h) ++e;
-          b = e;
-        }
-      } else {
-        a = -1;
-      }
-    }
-    if (b < 0) continue;
+    int a, b;
+    if (!zone_interior_run(Z, h, a, b)) continue;
     int slot = -1;
     for (int y = 0; y < I.zone_cap; ++y)
       if (!zones[y].alive) {
@@ -1547,6 +1553,7 @@ __device__ __noinline__ void post_inst(const Dev& d, int ii) {
     Z.B = Z.fj[a];
     Z.changed = 1;
     Zn.changed = 1;
+    work[nw++] = I.zone_off + slot;
   }
   double smax = __longlong_as_double((long long)I.smax_bits);
   // creation events -> new zones
@@ -1596,6 +1603,7 @@ __device__ __noinline__ void post_inst(const Dev& d, int ii) {
     for (int k = 0; k <= ZC; ++k) Z.pwl[k] = Z.pwr[k] = 0.0;
     Z.changed = 1;
     smax = fmax(smax, fabs(E.mC / E.rhoC) + c_fluid.ph[E.phC].a);
+    work[nw++] = I.zone_off + slot;
     creations++;
   }
   I.n_ev = 0;
@@ -1603,7 +1611,8 @@ __device__ __noinline__ void post_inst(const Dev& d, int ii) {
   // checked against their neighbours (O(changed x zones))
   for (bool again = true; again;) {
     again = false;
-    for (int a = 0; a < I.zone_cap && !again; ++a) {
+    for (int w = 0; w < nw && !again; ++w) {
+      const int a = work[w] - I.zone_off;
       if (!zones[a].alive || !zones[a].changed) continue;
       // nearest zone to the left (largest B <= A_a) and to the right (smallest A >= B_a)
       int left = -1, right = -1;
@@ -1653,14 +1662,14 @@ __device__ __noinline__ void post_inst(const Dev& d, int ii) {
         Za.fpb[Za.nc] = 0;
         Za.fj[Za.nc] = Zb.B;
         Za.B = Zb.B;
-        Za.changed = 1;
         Zb.alive = 0;
+        if (!Za.changed) work[nw++] = I.zone_off + ia;  // a zone that changes only now joins the list
+        Za.changed = 1;
         again = true;
       }
     }
   }
-  for (int z = 0; z < I.zone_cap; ++z) zones[z].changed = 0;
-  if (splits) I.stats[5] += splits;
+  for (int w = 0; w < nw; ++w) d.zones[work[w]].changed = 0;
   if (creations) I.stats[6] += creations;
   // time and next step
   const Ctrl& C = *d.ctrl;
@@ -1712,9 +1721,20 @@ __global__ void k_dts(Dev d, int n) {
   int zi = blockIdx.x * blockDim.x + threadIdx.x;
   if (zi < n && zone_active(d, zi)) dts_zone<NEWTON>(d, zi);
 }
+__global__ void k_post_zones(Dev d, int n) {
+  int zi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (zi < n) post_zone(d, zi);
+}
 __global__ void k_post(Dev d, int n) {
   int ii = blockIdx.x * blockDim.x + threadIdx.x;
   if (ii < n && d.inst[ii].active) post_inst(d, ii);
+}
+
+// the whole grid management of one instance by one thread (the group kernels' warp 0)
+__device__ inline void post_all(const Dev& d, int ii) {
+  const Inst& I = d.inst[ii];
+  for (int z = I.zone_off; z < I.zone_off + I.zone_cap; ++z) post_zone(d, z);
+  post_inst(d, ii);
 }
 
 // Group-resident schedule: one CTA advances a group of instances (similar sizes) step after step
@@ -1780,7 +1800,7 @@ __global__ void __launch_bounds__(NT, (NT <= 128 ? 2 : 1)) k_group(Dev d, const 
     long long c2 = clock64();
     cyc[0] += c1 - c0;
     cyc[4] += c2 - c1;
-    if (warp == 0 && ii >= 0 && d.inst[ii].active) post_inst(d, ii);
+    if (warp == 0 && ii >= 0 && d.inst[ii].active) post_all(d, ii);
     if (threadIdx.x == 0) s_more = 0;
     __syncthreads();
     if (warp == 0 && ii >= 0 && d.inst[ii].active && !d.inst[ii].status) atomicOr(&s_more, 1);
@@ -1882,7 +1902,7 @@ __global__ void __launch_bounds__(128, 2) k_group_async(Dev d, const int* ginst,
         set_status(I, IMEXDS_ERR_TIMEOUT);
         break;
       }
-      post_inst(d, ii);
+      post_all(d, ii);
       long long c4 = clock64();
       cp += c1 - c0;
       cd += c2 - c1;
@@ -2310,6 +2330,7 @@ void free_dev(imexds_ctx* c) {
   cudaFree(d.inst);
   cudaFree(d.ev);
   cudaFree(d.tiles);
+  cudaFree(d.work);
   cudaFree(d.ctrl);
   cudaFree(c->d_ginst);
   cudaFree(c->d_grange);
@@ -2366,8 +2387,9 @@ void launch_step_forked(imexds_ctx* c) {
   else
     k_sweep<false><<<sb, 256, 0, c->stream>>>(c->d, c->n_tiles);
   cudaStreamWaitEvent(c->stream, c->join_ev, 0);
+  k_post_zones<<<zb, zt, 0, c->stream>>>(c->d, c->n_zone_slots);
   k_post<<<ib, zt, 0, c->stream>>>(c->d, c->n_inst);
-  c->launches += 5;
+  c->launches += 6;
 }
 
 void launch_step(imexds_ctx* c, cudaEvent_t* ev = nullptr) {
@@ -2390,9 +2412,10 @@ void launch_step(imexds_ctx* c, cudaEvent_t* ev = nullptr) {
   else
     k_dts<false><<<zb, zt, 0, c->stream>>>(c->d, c->n_zone_slots);
   if (ev) cudaEventRecord(ev[4], c->stream);
+  k_post_zones<<<zb, zt, 0, c->stream>>>(c->d, c->n_zone_slots);
   k_post<<<ib, zt, 0, c->stream>>>(c->d, c->n_inst);
   if (ev) cudaEventRecord(ev[5], c->stream);
-  c->launches += 5;
+  c->launches += 6;
 }
 
 void accumulate_times(imexds_ctx* c, int steps) {
@@ -2823,6 +2846,7 @@ imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double*
   CK(cudaMalloc(&d.inst, sizeof(Inst) * n));
   CK(cudaMemcpyAsync(d.inst, hi.data(), sizeof(Inst) * n, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMalloc(&d.ev, sizeof(Event) * EV_CAP * n));
+  CK(cudaMalloc(&d.work, sizeof(int) * std::max(1, n_zone)));
   CK(cudaMalloc(&d.tiles, sizeof(int2) * tiles.size()));
   CK(cudaMemcpyAsync(d.tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMalloc(&d.ctrl, sizeof(Ctrl)));

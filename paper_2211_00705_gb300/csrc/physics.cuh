@@ -755,4 +755,97 @@ __device__ __noinline__ CreateOut creation_solve(const Fluid& F, const Opts& o, 
   return R;
 }
 
+// A Newton correction d below 1e-14 max(|W|, 1) in every component cannot move the iterate any further than its
+// own rounding: the iteration has reached the floor that rounding puts under the residual (for a tiny cell the
+// update T amplifies rounding by 1/alpha, which can exceed a tight stop tolerance). The block then stops as
+// though it had reached l_max (the last iterate is used and counted as such).
+constexpr double kNewtonFloor = 1e-14;
+__device__ inline bool newton_at_floor(int nb, const double* W0, const double* W1, const double* d0, const double* d1) {
+  bool floor = true;
+  for (int q = 0; q < nb; ++q)
+    floor = floor && fabs(d0[q]) <= kNewtonFloor * fmax(fabs(W0[q]), 1.0) &&
+            fabs(d1[q]) <= kNewtonFloor * fmax(fabs(W1[q]), 1.0);
+  return floor;
+}
+
+// One Newton step on a block's implicit system R(W) = W - T(W) = 0 (Algorithm 2 Part 1's update T with fluxes and
+// widths at W; the option block_solver = 1): dR/dW = I - dT/dW assembled from the face Jacobians,
+//   dT_q/dW = -(dt / h_q) [(dF_{q+1/2} - dF_{q-1/2}) + T_q (dw_{q+1/2} - dw_{q-1/2})],
+// rows and columns (cell q, component c) = 2q + c, then the solve of dR/dW d = T - W. Cells 0..nb-1 of the block;
+// ih[q] = 1 / h_q(W); fj[g] the Jacobian of interior face g = 1..nb-1 (between cells g-1 and g). Blocks of three
+// cells (the common one) use the dense 6 x 6 solve, larger blocks the banded one, so that every kernel that solves
+// a block of a given size (the forward kernels and the adjoint's replay) produces the same bits. False if the
+// system is singular.
+__device__ inline bool newton_block_step(int nb, double dt, const double* ih, const double* T0, const double* T1,
+                                         const double* W0, const double* W1, const FaceJac* fj, double* d0,
+                                         double* d1) {
+  if (nb == 3) {
+    double A[6][7];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) A[r][c] = (r == c) ? 1.0 : 0.0;
+      A[r][6] = (r & 1) ? T1[r >> 1] - W1[r >> 1] : T0[r >> 1] - W0[r >> 1];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const double coef = dt * ih[q];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const double Tq = c ? T1[q] : T0[q];
+        if (q + 1 <= 2) {  // right face q+1: + coef (dF + T dw), columns of cells q, q+1
+          const FaceJac& J = fj[q + 1];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) A[2 * q + c][2 * q + k] += coef * ((c ? J.dF1[k] : J.dF0[k]) + Tq * J.dw[k]);
+        }
+        if (q >= 1) {  // left face q: - coef (dF + T dw), columns of cells q-1, q
+          const FaceJac& J = fj[q];
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            A[2 * q + c][2 * (q - 1) + k] -= coef * ((c ? J.dF1[k] : J.dF0[k]) + Tq * J.dw[k]);
+        }
+      }
+    }
+    if (!solve_dense<6>(A)) return false;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      d0[q] = A[2 * q][6];
+      d1[q] = A[2 * q + 1][6];
+    }
+    return true;
+  }
+  constexpr int NMAX = 2 * 18;
+  const int n2 = 2 * nb;
+  if (n2 > NMAX) return false;
+  double A[NMAX][BAND_W], rhs[NMAX];
+  for (int r = 0; r < n2; ++r) {
+    for (int k = 0; k < BAND_W; ++k) A[r][k] = 0.0;
+    A[r][3] = 1.0;  // the identity (column r)
+  }
+  for (int q = 0; q < nb; ++q) {
+    const double coef = dt * ih[q];
+    rhs[2 * q] = T0[q] - W0[q];
+    rhs[2 * q + 1] = T1[q] - W1[q];
+    for (int c = 0; c < 2; ++c) {
+      const int row = 2 * q + c;
+      const double Tq = c ? T1[q] : T0[q];
+      if (q + 1 < nb) {
+        const FaceJac& J = fj[q + 1];
+        for (int k = 0; k < 4; ++k) A[row][2 * q + k - row + 3] += coef * ((c ? J.dF1[k] : J.dF0[k]) + Tq * J.dw[k]);
+      }
+      if (q >= 1) {
+        const FaceJac& J = fj[q];
+        for (int k = 0; k < 4; ++k)
+          A[row][2 * (q - 1) + k - row + 3] -= coef * ((c ? J.dF1[k] : J.dF0[k]) + Tq * J.dw[k]);
+      }
+    }
+  }
+  if (!solve_band(A, rhs, n2)) return false;
+  for (int q = 0; q < nb; ++q) {
+    d0[q] = rhs[2 * q];
+    d1[q] = rhs[2 * q + 1];
+  }
+  return true;
+}
+
 }  // namespace imexds
