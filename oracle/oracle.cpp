@@ -20,6 +20,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <limits>
 #include <thread>
 #include <type_traits>
 #include <vector>
@@ -921,6 +922,7 @@ void step_instance(const Fluid& F, const orc_opts& o, Inst<T>& I, double t_end) 
       }
       const double FLv[2] = {val(FL[0]), val(FL[1])}, FRv[2] = {val(FR[0]), val(FR[1])};
       std::vector<std::vector<double>> dT(n2, std::vector<double>(n2, 0.0));
+      double corr_prev = std::numeric_limits<double>::infinity();
       for (l = 0; l < o.l_max; ++l) {
         if (!target(Wr, Wm, Tv)) {
           I.status = ORC_ERR_VANISH;
@@ -959,13 +961,17 @@ void step_instance(const Fluid& F, const orc_opts& o, Inst<T>& I, double t_end) 
           I.status = ORC_ERR_PB_NOCONV;
           return;
         }
-        // a correction below 1e-14 max(|W|, 1) in every component cannot move the iterate further than its own
-        // rounding (the residual has reached the floor rounding puts under it): stop as at l_max
-        bool at_floor = true;
+        // the floor rounding puts under the residual (a tiny cell's update amplifies a one-ulp change of W by
+        // about 1/alpha): with c = max |correction| / max(|W|, 1), stop as at l_max when c <= 1e-14 (the
+        // correction is below the iterate's own rounding) or when 1e-10 >= c > c_prev / 2 (the corrections no
+        // longer contract, which quadratic convergence rules out; c_prev of the first step is infinite)
+        double corr = 0.0;
         for (int r = 0; r < n2; ++r) {
           const double w = std::fabs(val((r % 2 == 0) ? Wr[lo + r / 2] : Wm[lo + r / 2]));
-          at_floor = at_floor && std::fabs(val(A[r][n2])) <= 1e-14 * std::max(w, 1.0);
+          corr = std::max(corr, std::fabs(val(A[r][n2])) / std::max(w, 1.0));
         }
+        const bool at_floor = corr <= 1e-14 || (corr <= 1e-10 && corr > 0.5 * corr_prev);
+        corr_prev = corr;
         for (int r = 0; r < n2; ++r) {
           if (r % 2 == 0)
             Wr[lo + r / 2] = Wr[lo + r / 2] + A[r][n2];

@@ -373,6 +373,7 @@ __device__ bool dts_block(const ADev& A, AInst& I, const SharedStep& S, int lo, 
     // Newton on the block's system R(W) = W - T(W) with the stop test of Sec. 4 (the forward kernels'
     // newton_simple / newton_general): fluxes at W, T(W), the test, then (I - dT/dW) dW = T(W) - W
     const double dtr = (c_opts.res_mode == 1) ? 1.0 : dt;
+    double corr_prev = INFINITY;
     for (int l = 0; l < c_opts.l_max; ++l) {
       int e = fluxes();
       if (e) {
@@ -397,7 +398,9 @@ __device__ bool dts_block(const ADev& A, AInst& I, const SharedStep& S, int lo, 
         afail(I, IMEXDS_ERR_PB_NOCONV);
         return false;
       }
-      const bool at_floor = newton_at_floor(nb, Wr, Wm, dr, dmv);
+      const double corr = newton_corr(nb, Wr, Wm, dr, dmv);
+      const bool at_floor = newton_at_floor(corr, corr_prev);
+      corr_prev = corr;
       for (int q = 0; q < nb; ++q) {
         Wr[q] += dr[q];
         Wm[q] += dmv[q];

@@ -729,6 +729,7 @@ __device__ __noinline__ bool newton_general(const Dev& d, Zone& Z, Inst& I, int 
     };
     bool stop = false;
     int l, fail = 0;
+    double corr_prev = INFINITY;
     for (l = 0; l < c_opts.l_max; ++l) {
       fail = fluxes();
       if (fail) break;
@@ -748,7 +749,9 @@ __device__ __noinline__ bool newton_general(const Dev& d, Zone& Z, Inst& I, int 
         fail = 3;
         break;
       }
-      const bool at_floor = newton_at_floor(hi - lo + 1, Wr + lo, Wm + lo, dr, dm);
+      const double corr = newton_corr(hi - lo + 1, Wr + lo, Wm + lo, dr, dm);
+      const bool at_floor = newton_at_floor(corr, corr_prev);
+      corr_prev = corr;
       for (int q = lo; q <= hi; ++q) {
         Wr[q] += dr[q - lo];
         Wm[q] += dm[q - lo];
@@ -1056,6 +1059,7 @@ __device__ __noinline__ void newton_simple(const Dev& d, int zi) {
   bool stop = false;
   int l, fail = 0;
   double T0[3], T1[3], ih[3];
+  double corr_prev = INFINITY;
   for (l = 0; l < c_opts.l_max; ++l) {
     fail = fluxes();
     if (fail) break;
@@ -1083,7 +1087,9 @@ __device__ __noinline__ void newton_simple(const Dev& d, int zi) {
       fail = 3;
       break;
     }
-    const bool at_floor = newton_at_floor(3, W0, W1, d0, d1);
+    const double corr = newton_corr(3, W0, W1, d0, d1);
+    const bool at_floor = newton_at_floor(corr, corr_prev);
+    corr_prev = corr;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       W0[q] += d0[q];

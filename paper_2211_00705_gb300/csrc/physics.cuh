@@ -755,17 +755,28 @@ __device__ __noinline__ CreateOut creation_solve(const Fluid& F, const Opts& o, 
   return R;
 }
 
-// A Newton correction d below 1e-14 max(|W|, 1) in every component cannot move the iterate any further than its
-// own rounding: the iteration has reached the floor that rounding puts under the residual (for a tiny cell the
-// update T amplifies rounding by 1/alpha, which can exceed a tight stop tolerance). The block then stops as
-// though it had reached l_max (the last iterate is used and counted as such).
+// Two ways the block Newton iteration reaches the floor that rounding puts under the residual before the Sec. 4
+// test holds (for a tiny cell of fraction alpha the update T amplifies a one-ulp change of W by about 1/alpha, which
+// can exceed a tight stop tolerance; the iterate then cycles among a few points ulps apart). With the correction
+// measured as c = max over components |d| / max(|W|, 1):
+//   (a) c <= 1e-14: the correction cannot move the iterate further than its own rounding;
+//   (b) c <= 1e-10 and c > c_prev / 2: the corrections stopped contracting; Newton's quadratic convergence
+//       takes small corrections to much smaller ones, so only rounding (or a kink of the flux exactly at the
+//       root) can keep them from shrinking.
+// Either ends the iteration as l_max would: the corrected iterate is used and counted among the blocks that did
+// not meet the test. c_prev of the first step is +infinity, so (b) needs two corrections.
 constexpr double kNewtonFloor = 1e-14;
-__device__ inline bool newton_at_floor(int nb, const double* W0, const double* W1, const double* d0, const double* d1) {
-  bool floor = true;
-  for (int q = 0; q < nb; ++q)
-    floor = floor && fabs(d0[q]) <= kNewtonFloor * fmax(fabs(W0[q]), 1.0) &&
-            fabs(d1[q]) <= kNewtonFloor * fmax(fabs(W1[q]), 1.0);
-  return floor;
+constexpr double kNewtonStallBelow = 1e-10;
+__device__ inline double newton_corr(int nb, const double* W0, const double* W1, const double* d0, const double* d1) {
+  double c = 0.0;
+  for (int q = 0; q < nb; ++q) {
+    c = fmax(c, fabs(d0[q]) / fmax(fabs(W0[q]), 1.0));
+    c = fmax(c, fabs(d1[q]) / fmax(fabs(W1[q]), 1.0));
+  }
+  return c;
+}
+__device__ inline bool newton_at_floor(double c, double c_prev) {
+  return c <= kNewtonFloor || (c <= kNewtonStallBelow && c > 0.5 * c_prev);
 }
 
 // One Newton step on a block's implicit system R(W) = W - T(W) = 0 (Algorithm 2 Part 1's update T with fluxes and

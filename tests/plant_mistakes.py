@@ -7,7 +7,7 @@ oracle tests run against that library (ORACLE_LIB, stopping at the first failure
 never written. Run from anywhere:
 
     python tests/plant_mistakes.py            # every batch (a few minutes)
-    python tests/plant_mistakes.py dual        # one batch: scheme, batch2, batch3, batch4, dual, residual
+    python tests/plant_mistakes.py dual        # one batch: scheme, batch2, batch3, batch4, dual, residual, newton
 """
 import os
 import subprocess
@@ -22,7 +22,7 @@ ORACLE = os.path.join(ROOT, "oracle")
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 TESTS = ["tests/test_oracle_pins.py", "tests/test_oracle_residual.py", "tests/test_oracle_scheme.py",
-         "tests/test_oracle_tangent.py"]
+         "tests/test_oracle_tangent.py", "tests/test_oracle_newton_floor.py"]
 
 SCHEME = [
  ("kinetic relation: sign of the kinetic-energy jump", "T Q = (R.g - L.g) - 0.5 * jp * (L.v + R.v);", "T Q = (R.g - L.g) + 0.5 * jp * (L.v + R.v);"),
@@ -84,8 +84,15 @@ RESIDUAL = [
  ("dual-time stop: tiny and other cells' residuals exchanged", "          if (tiny[i])\n            res_k = std::max(res_k, res);\n          else\n            res_nb = std::max(res_nb, res);\n        }\n        Wr = Nr;", "          if (!tiny[i])\n            res_k = std::max(res_k, res);\n          else\n            res_nb = std::max(res_nb, res);\n        }\n        Wr = Nr;"),
 ]
 
+NEWTON = [
+ ("block Newton: the stall rule dropped", "const bool at_floor = corr <= 1e-14 || (corr <= 1e-10 && corr > 0.5 * corr_prev);", "const bool at_floor = corr <= 1e-14;"),
+ ("block Newton: the stall rule's contraction test reversed", "(corr <= 1e-10 && corr > 0.5 * corr_prev)", "(corr <= 1e-10 && corr < 0.5 * corr_prev)"),
+ ("block Newton: the correction's sign", "Wr[lo + r / 2] = Wr[lo + r / 2] + A[r][n2];", "Wr[lo + r / 2] = Wr[lo + r / 2] - A[r][n2];"),
+]
+
 BATCHES = {"scheme": ("oracle.cpp", SCHEME), "batch2": ("oracle.cpp", BATCH2), "batch3": ("oracle.cpp", BATCH3),
-           "batch4": ("oracle.cpp", BATCH4), "dual": ("dual.h", DUAL), "residual": ("oracle.cpp", RESIDUAL)}
+           "batch4": ("oracle.cpp", BATCH4), "dual": ("dual.h", DUAL), "residual": ("oracle.cpp", RESIDUAL),
+           "newton": ("oracle.cpp", NEWTON)}
 
 
 def run_batch(fname, mutations):
