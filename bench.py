@@ -76,11 +76,13 @@ def cell_steps(stats, counts):
     return float(np.sum(stats["steps"].astype(np.float64) * counts.astype(np.float64)))
 
 
-def measure_adjoint(dev, steps, warmup, scale=1.0, n_steps=2000, block_solver=0):
-    """The adjoint on its workload (Riemann instances, N=500, 2000 steps, checkpoints every 64): forward run
-    (also a target run with tau x 1.1 for the misfit), then imexds_adjoint timed. Cell-steps of the adjoint
-    = initial cells x steps of every instance (the replay, the recompute and the reverse sweep all count as
-    one reverse cell-step). Returns the JSON object of the adjoint line."""
+def measure_adjoint(dev, steps, warmup, scale=1.0, n_steps=2000, block_solver=0, checkpoint_every=None):
+    """The adjoint on its workload (Riemann instances, N=500, 2000 steps): forward run (also a target run with
+    tau x 1.1 for the misfit), then imexds_adjoint timed. Checkpoints every `checkpoint_every` steps (default:
+    the whole run, i.e. one taped replay and one reverse sweep, its tape ~34 GB of HBM at full size; with 64,
+    a replay writing checkpoints, a taped recompute of every segment but the last, and the reverse sweep).
+    Cell-steps of the adjoint = initial cells x steps of every instance (replay, recompute and reverse sweep
+    together count as one reverse cell-step). Returns the JSON object of the adjoint line."""
     import dataclasses
     import torch
     from paper_2211_00705_gb300 import inputs as I
@@ -96,7 +98,8 @@ def measure_adjoint(dev, steps, warmup, scale=1.0, n_steps=2000, block_solver=0)
     tctx.close()
     rs_t, _ = I.sample_density(ts, ts["offsets"], b.n_lattice, b.x_left, b.x_right)
     ctx = Imexds.from_batch(b)
-    ctx.set_adjoint_checkpoint(64)
+    k = int(checkpoint_every or prog_steps)
+    ctx.set_adjoint_checkpoint(k)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -110,8 +113,10 @@ def measure_adjoint(dev, steps, warmup, scale=1.0, n_steps=2000, block_solver=0)
     g_rho = np.zeros(int(s["offsets"][-1]))
     np.add.at(g_rho, idx, h * (rs - rs_t))
     g_m = np.zeros_like(g_rho)
+    free0 = torch.cuda.mem_get_info(dev)[0]
     for _ in range(max(1, warmup)):
         g = ctx.adjoint(g_rho, g_m)
+    adj_bytes = max(0, free0 - torch.cuda.mem_get_info(dev)[0])
     kern, wall = [], []
     for _ in range(steps):
         torch.cuda.synchronize()
@@ -124,7 +129,8 @@ def measure_adjoint(dev, steps, warmup, scale=1.0, n_steps=2000, block_solver=0)
     fwd_cs = float(np.sum(st["steps"] * np.diff(b.cell_offsets)))
     ctx.close()
     cs = float(info["cell_steps"])
-    return {"value": cs / float(np.mean(kern)), "unit": UNIT, "workload": b.name, "checkpoint_every": 64,
+    return {"value": cs / float(np.mean(kern)), "unit": UNIT, "workload": b.name, "checkpoint_every": k,
+            "adjoint_device_gb": round(adj_bytes / 1e9, 2),
             "seconds_per_call": float(np.mean(kern)), "calls": steps,
             "e2e": {"value": cs / float(np.mean(wall)), "unit": UNIT,
                     "note": "imexds_adjoint call with host seed/gradient arrays, layout and copies included"},
@@ -631,6 +637,10 @@ def main():
     ap.add_argument("--only", choices=["adjoint", "hbm", "cavitation"], default=None,
                     help="run one auxiliary measurement alone and print its JSON (profiling)")
     ap.add_argument("--adjoint-steps", type=int, default=2000, help="steps of the adjoint workload")
+    ap.add_argument("--adjoint-checkpoint", type=int, default=0,
+                    help="checkpoint interval of the adjoint (0: the whole run taped at once)")
+    ap.add_argument("--adjoint-solver", type=int, default=0, choices=[0, 1],
+                    help="block solver of the --only adjoint run: 0 dual time stepping, 1 Newton")
     ap.add_argument("--table", action="store_true", help="per-workload rates (GPU, plain GPU, oracle) as JSON")
     ap.add_argument("--group-threads", type=int, default=0,
                     help="CTA width of the group schedules when --schedule is 2 or 3 (0: the library's default)")
@@ -654,7 +664,9 @@ def main():
     if args.table:
         return table(args)
     if args.only == "adjoint":
-        print(json.dumps(measure_adjoint(dev, args.steps, args.warmup, scale=args.scale, n_steps=args.adjoint_steps)))
+        print(json.dumps(measure_adjoint(dev, args.steps, args.warmup, scale=args.scale, n_steps=args.adjoint_steps,
+                                         block_solver=args.adjoint_solver,
+                                         checkpoint_every=args.adjoint_checkpoint or None)))
         return 0
     if args.only == "hbm":
         print(json.dumps(measure_large_domain_sweep()))
@@ -768,11 +780,13 @@ def main():
         if not args.no_adjoint:
             # at most two timed calls (~13 s each at full size): the adjoint is reported beside the headline
             line["adjoint"] = measure_adjoint(dev, max(1, min(2, args.steps // 2)), 1, scale=args.scale,
-                                              n_steps=args.adjoint_steps)
+                                              n_steps=args.adjoint_steps,
+                                              checkpoint_every=args.adjoint_checkpoint or None)
             # the same adjoint of a Newton run (forward and replay with Newton on the blocks; the reverse step
             # differentiates the converged block systems either way)
             line["adjoint"]["newton"] = measure_adjoint(dev, 1, 1, scale=args.scale, n_steps=args.adjoint_steps,
-                                                        block_solver=1)
+                                                        block_solver=1,
+                                                        checkpoint_every=args.adjoint_checkpoint or None)
         if not args.no_hbm:
             line["large_domain_sweep"] = measure_large_domain_sweep()
         if ws == 1 and not args.no_cpu_baseline:

@@ -54,7 +54,8 @@ struct AInst {
   long long off;  // first slot of this instance in every per-cell / per-face array (stride cap + 1)
   long long done; // steps done inside the current program call
   int M, cap, status, pc;
-  int nsteps, M_seed, site, pad1;  // site: where an instance was stopped (1..5, see k_adjoint)
+  int nsteps, M_seed, site, nexp;  // site: where an instance was stopped (1..5, see k_adjoint); nexp: steps
+                                  // of the forward run, which the replay is expected to repeat
   double h, xL, tau, t;
   double lam_t, lam_tau;
 };
@@ -1382,7 +1383,11 @@ __global__ void __launch_bounds__(ATHREADS, 8) k_adjoint(ADev A) {
   __shared__ SharedStep S;
   __shared__ int s_go;
   __shared__ double s_tend;
-  // phase A: replay from the initial states, a checkpoint every k steps
+  // phase A: replay from the initial states, a checkpoint every k steps. The steps of the last segment (as the
+  // forward run's step count places it) are taped on the way, so that segment needs no recompute; with k at
+  // least the run's length the whole adjoint is one taped replay and one reverse sweep.
+  const int tape_from = (I.nexp > 0) ? ((I.nexp - 1) / A.k) * A.k : 0;
+  int taped = 0;
   int n = 0;
   for (;;) {
     if (n % A.k == 0) {
@@ -1410,7 +1415,9 @@ __global__ void __launch_bounds__(ATHREADS, 8) k_adjoint(ADev A) {
     }
     __syncthreads();
     if (!s_go) break;
-    fwd_step(A, I, S, s_tend, nullptr, 0);
+    const bool tape = n >= tape_from && n - tape_from < A.k;
+    fwd_step(A, I, S, s_tend, tape ? A.rec + (long long)(n - tape_from) * A.n_inst + ii : nullptr, n - tape_from);
+    if (tape) ++taped;
     ++n;
   }
   __syncthreads();
@@ -1429,29 +1436,33 @@ __global__ void __launch_bounds__(ATHREADS, 8) k_adjoint(ADev A) {
     const int first = sg * A.k, last = min(n, first + A.k) - 1;
     const ACk& h = A.ck_h[(long long)sg * A.n_inst + ii];
     const int Mlam = I.M;  // the adjoint list length (cells of the state after step last)
+    // the last segment, taped whole during the replay, which left the list at the state after its last step
+    const bool taped_whole = sg == n_seg - 1 && first == tape_from && taped == last - first + 1;
     __syncthreads();
-    load_list(A, I, (long long)sg * A.stride + I.off, h.M);
-    if (threadIdx.x == 0) {
-      I.M = h.M;
-      I.t = h.t;
-      I.pc = h.pc;
-      I.done = h.done;
-    }
-    __syncthreads();
-    for (int s = first; s <= last; ++s) {
+    if (!taped_whole) {
+      load_list(A, I, (long long)sg * A.stride + I.off, h.M);
       if (threadIdx.x == 0) {
-        double te = -1.0;
-        s_go = prog_next(A, I, te) ? 1 : 0;
-        s_tend = te;
+        I.M = h.M;
+        I.t = h.t;
+        I.pc = h.pc;
+        I.done = h.done;
       }
       __syncthreads();
-      if (!s_go) {
-        if (threadIdx.x == 0) afail(I, IMEXDS_ERR_STATE, 1);
+      for (int s = first; s <= last; ++s) {
+        if (threadIdx.x == 0) {
+          double te = -1.0;
+          s_go = prog_next(A, I, te) ? 1 : 0;
+          s_tend = te;
+        }
         __syncthreads();
-        return;
+        if (!s_go) {
+          if (threadIdx.x == 0) afail(I, IMEXDS_ERR_STATE, 1);
+          __syncthreads();
+          return;
+        }
+        fwd_step(A, I, S, s_tend, A.rec + (long long)(s - first) * A.n_inst + ii, s - first);
+        if (I.status) return;
       }
-      fwd_step(A, I, S, s_tend, A.rec + (long long)(s - first) * A.n_inst + ii, s - first);
-      if (I.status) return;
     }
     __syncthreads();
     if (threadIdx.x == 0) I.M = Mlam;

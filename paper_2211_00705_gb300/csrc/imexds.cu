@@ -3467,6 +3467,7 @@ static imexds_status adjoint_launch(imexds_ctx* c, AdjRun& R, const double* dJ_d
     I.cap = caps[i];
     I.M = M0;
     I.M_seed = R.MT[i];
+    I.nexp = (int)R.stats[10 * i];
     I.h = h;
     I.xL = c->xL[i];
     I.tau = c->tau[i];

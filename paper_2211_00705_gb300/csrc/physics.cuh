@@ -93,8 +93,12 @@ __device__ inline double gibbs(const Phase& e, double rho) { return e.a2 * log(r
 
 // HLL flux at a same-phase face (Toro), Davis wave speeds S_L = min(u_l, u_r) - a, S_R = max + a, physical
 // flux (rho u, rho u^2 + p) (Eq. eeq:isoT both), arranged for the sweep: the physical fluxes come in
-// precomputed (u = m/rho once per cell) and one reciprocal of S_R - S_L serves both components; every
-// product-sum is an explicit fused multiply-add so that every kernel computing a face flux gets the same bits.
+// precomputed (u = m/rho once per cell) and one reciprocal of S_R - S_L serves both components. With
+// w = S_R / (S_R - S_L) (so -S_L / (S_R - S_L) = 1 - w) the HLL average
+//   (S_R F_l - S_L F_r + S_L S_R (U_r - U_l)) / (S_R - S_L)  =  F_r + w ((F_l - F_r) + S_L (U_r - U_l)),
+// two fused multiply-adds per component; for the mass component F_l - F_r = m_l - m_r = -(U_r - U_l)_m.
+// Every product-sum is an explicit fused multiply-add so that every kernel computing a face flux gets the
+// same bits.
 __device__ inline double pressure_fma(const Phase& e, double rho) {
   return e.kind == 0 ? e.a2 * rho : __fma_rn(e.a2, rho - e.rho0, e.p0);
 }
@@ -106,10 +110,10 @@ __device__ inline void hll_pre(double a, double rl, double ml, double ul, double
   const double SL = umin - a, SR = umax + a;
   // branch-free: the HLL average is formed for every face (S_R - S_L >= 2a > 0) and the upwind cases
   // select the one-sided physical flux, the same values the three-way branch gives
-  const double inv = rcp_nr(SR - SL);
-  const double slsr = SL * SR;
-  const double H0 = __fma_rn(-SL, mr, __fma_rn(slsr, rr - rl, SR * ml)) * inv;
-  const double H1 = __fma_rn(-SL, fr1, __fma_rn(slsr, mr - ml, SR * fl1)) * inv;
+  const double w = SR * rcp_nr(SR - SL);
+  const double d0 = rr - rl, d1 = mr - ml;
+  const double H0 = __fma_rn(w, __fma_rn(SL, d0, -d1), mr);
+  const double H1 = __fma_rn(w, __fma_rn(SL, d1, fl1 - fr1), fr1);
   const bool up_l = ge0_bits(SL), up_r = le0_bits(SR);
   F0 = up_l ? ml : (up_r ? mr : H0);
   F1 = up_l ? fl1 : (up_r ? fr1 : H1);
