@@ -2,7 +2,13 @@
 // the final cell states with respect to the initial states, the initial boundary positions (through the
 // widths) and the kinetic coefficient tau of every instance.
 //
-// Design (one CTA per instance, all instances in one launch):
+// Design (up to AWARPS instances per CTA, one warp each, all instances in one launch):
+//   * Warp w advances instance base + w through the data-parallel parts of a step (fluxes, updates, list copies,
+//     reductions); lane l of warp 0 runs the one-thread parts of instance base + l (boundary solves and grid
+//     management, Algorithm 2 on the blocks, created cells and splits; in reverse the transposed block solves),
+//     so that the serial chains of the CTA's instances issue their FP64 instructions together (GB300 issues a
+//     one-lane FP64 warp instruction at the cost of a full one). The instances of a CTA step in lockstep; an
+//     instance that has finished or failed sits out the remaining steps.
 //   * Replay: the step of Algorithm 1 / Algorithm 2 runs again on a plain cell list of the instance
 //     (the paper's moving grid: one entry per cell, faces with their kind), from the initial states of
 //     the last forward call, with the same device physics as the forward kernels. Every k steps the
@@ -27,7 +33,8 @@
 namespace imexds {
 namespace adj {
 
-constexpr int ATHREADS = 64;   // one CTA per instance; 8 resident CTAs per SM
+constexpr int AWARPS = 8;      // instances per CTA at most, one warp each
+constexpr int ATHREADS = 32 * AWARPS;
 constexpr int AMAXPB = 16;   // phase boundaries per instance
 constexpr int AMAXBLK = 8;   // blocks per step
 constexpr int AMAXB = 8;     // cells per block
@@ -108,18 +115,18 @@ __device__ inline void afail(AInst& I, int code, int site = 0) {
 }
 
 // ------------------------------------------------------------------------------ list helpers
-// copy n cells (and n + 1 faces when faces) between two lists of the same layout, whole CTA
+// copy n cells (and n + 1 faces when faces) between two lists of the same layout, whole warp
 __device__ inline void cta_copy_d(double* dst, const double* src, int n) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+  for (int i = threadIdx.x & 31; i < n; i += 32) dst[i] = src[i];
 }
 __device__ inline void cta_copy_b(unsigned char* dst, const unsigned char* src, int n) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+  for (int i = threadIdx.x & 31; i < n; i += 32) dst[i] = src[i];
 }
 __device__ inline void cta_copy_i(int* dst, const int* src, int n) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+  for (int i = threadIdx.x & 31; i < n; i += 32) dst[i] = src[i];
 }
 __device__ inline void cta_zero(double* dst, int n) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = 0.0;
+  for (int i = threadIdx.x & 31; i < n; i += 32) dst[i] = 0.0;
 }
 
 // one thread: erase cell b (and face b) of a list
@@ -174,15 +181,20 @@ __device__ void lam_open(double* lw, double* lr, double* lm, double* lx, int M, 
   for (int g = M; g >= p; --g) lx[g + 1] = lx[g];
 }
 
+// Per-instance state of the current step, in shared memory (one entry per warp of the CTA).
 struct SharedStep {
-  double dt, lam, red_v[ATHREADS / 32], lam_dt;
-  int red_i[ATHREADS / 32];
-  int M, kmax, clipped, done, bad;
+  double dt, lam, lam_dt;  // lam_dt: d(dt) contributions of a reverse step (lane 0 of the instance's warp and
+                           // the instance's lane of warp 0 add to it in turn)
+  int M, kmax, clipped, done, bad, act;  // act: the instance takes part in this step
   int n_pb, pb[AMAXPB];
   int n_blk, blo[AMAXBLK], bhi[AMAXBLK];
   int n_cr, cr_g[AMAXCR], cr_P[AMAXCR];
   double cr_o[AMAXCR][7];
   double t_end;
+  double hp[AMAXBC];  // predicted widths of the block cells (block after block)
+  int tiny[AMAXBC];   // tiny flags of the block cells
+  StepRec* rec;       // where this step's decisions are taped (nullptr: not taped)
+  int slot;           // tape slot of the pre-step list
 };
 
 // creation event at face g of this step, or -1
@@ -236,56 +248,36 @@ __device__ inline bool face_in_block(const SharedStep& S, int g) {
   return false;
 }
 
-// CTA max of s (first index among equal maxima); result in S.red_v[0] / S.red_i[0]
-__device__ void cta_argmax(SharedStep& S, double v, int idx) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+// warp max of v (first index among equal maxima); every lane gets the result
+__device__ inline void warp_argmax(double& v, int& idx) {
   for (int o = 16; o > 0; o >>= 1) {
-    double v2 = __shfl_down_sync(0xffffffffu, v, o);
-    int i2 = __shfl_down_sync(0xffffffffu, idx, o);
+    const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+    const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
     if (v2 > v || (v2 == v && i2 < idx)) {
       v = v2;
       idx = i2;
     }
   }
-  if (lane == 0) {
-    S.red_v[wid] = v;
-    S.red_i[wid] = idx;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
-      if (S.red_v[q] > S.red_v[0] || (S.red_v[q] == S.red_v[0] && S.red_i[q] < S.red_i[0])) {
-        S.red_v[0] = S.red_v[q];
-        S.red_i[0] = S.red_i[q];
-      }
-  }
-  __syncthreads();
 }
-__device__ double cta_sum(SharedStep& S, double v) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if (lane == 0) S.red_v[wid] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += S.red_v[q];
-  return s;  // valid in thread 0
+// warp sum in a fixed order (the same bits on every lane)
+__device__ inline double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
-// collect the phase-boundary faces of a list (ascending) into S.pb; false if there are too many
+// collect the phase-boundary faces of a list (ascending) into S.pb, whole warp; false if there are too many
 __device__ bool collect_pbs(SharedStep& S, const unsigned char* fpb, int M) {
-  if (threadIdx.x == 0) S.n_pb = 0;
-  __syncthreads();
-  for (int g = 1 + threadIdx.x; g < M; g += blockDim.x)
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) S.n_pb = 0;
+  __syncwarp();
+  for (int g = 1 + lane; g < M; g += 32)
     if (fpb[g]) {
       int q = atomicAdd(&S.n_pb, 1);
       if (q < AMAXPB) S.pb[q] = g;
     }
-  __syncthreads();
-  bool ok = S.n_pb <= AMAXPB;
-  __syncthreads();
-  if (threadIdx.x == 0 && ok) {
+  __syncwarp();
+  const bool ok = S.n_pb <= AMAXPB;
+  if (lane == 0 && ok) {
     for (int a = 1; a < S.n_pb; ++a) {  // insertion sort of a handful of faces
       int v = S.pb[a], b = a - 1;
       while (b >= 0 && S.pb[b] > v) {
@@ -295,7 +287,7 @@ __device__ bool collect_pbs(SharedStep& S, const unsigned char* fpb, int M) {
       S.pb[b + 1] = v;
     }
   }
-  __syncthreads();
+  __syncwarp();
   return ok;
 }
 
@@ -479,438 +471,469 @@ __device__ bool dts_block(const ADev& A, AInst& I, const SharedStep& S, int lo, 
   return true;
 }
 
-// One time step of the replay (whole CTA). Tapes the pre-step list into tape slot `slot` and the
-// decisions into *rec when rec != nullptr.
-__device__ void fwd_step(const ADev& A, AInst& I, SharedStep& S, double t_end, StepRec* rec, int slot) {
+// Grid management of one instance at the start of a step (one thread: the instance's lane of warp 0).
+__device__ __noinline__ void serial_grid(const ADev& A, AInst& I, SharedStep& S) {
   const long long o = I.off;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    S.M = I.M;
-    S.bad = 0;
-  }
-  __syncthreads();
-  int M = S.M;
-  if (rec) {
-    const long long to = (long long)slot * A.stride + o;
-    cta_copy_d(A.tp_w + to, A.w + o, M);
-    cta_copy_d(A.tp_r + to, A.r + o, M);
-    cta_copy_d(A.tp_m + to, A.m + o, M);
-    cta_copy_b(A.tp_ph + to, A.ph + o, M);
-    cta_copy_b(A.tp_fpb + to, A.fpb + o, M + 1);
-    if (tid == 0) A.tp_M[(long long)slot * A.n_inst + (int)(&I - A.I)] = M;
-  }
-  // (1) CFL time step (Eq. cfl_cond:unif) over all cells, with the argmax cell
-  {
-    double v = -1.0;
-    int idx = 0x7fffffff;
-    for (int i = tid; i < M; i += blockDim.x) {
-      double s = fabs(A.m[o + i] / A.r[o + i]) + c_fluid.ph[A.ph[o + i]].a;
-      if (s > v) {
-        v = s;
-        idx = i;
-      }
-    }
-    cta_argmax(S, v, idx);
-    if (tid == 0) {
-      double dt = c_opts.cfl * I.h / S.red_v[0];
-      int clipped = 0;
-      if (t_end > 0.0 && t_end - I.t <= dt) {
-        dt = t_end - I.t;
-        clipped = 1;
-      }
-      S.dt = dt;
-      S.lam = dt / I.h;
-      S.kmax = S.red_i[0];
-      S.clipped = clipped;
-      if (rec) {
-        rec->dt = dt;
-        rec->clipped = clipped;
-        rec->kmax = S.red_i[0];
-        rec->n_merge = rec->n_blk = rec->n_split = rec->n_pbf = 0;
-      }
-    }
-  }
-  if (!collect_pbs(S, A.fpb + o, M)) {
-    if (tid == 0) afail(I, IMEXDS_ERR_CAPACITY);
-    __syncthreads();
-    return;
-  }
+  StepRec* rec = S.rec;
   // (2) grid management: boundary solves at U^n, marks, merges (thread 0; the list is short-edited)
-  __shared__ double s_hp[AMAXBC];
-  __shared__ int s_tiny[AMAXBC];
-  if (tid == 0) {
-    const double dt = S.dt;
-    double wf[AMAXPB];
-    int nmk = 0, mk[2 * AMAXPB];
-    bool ok = true;
+  const double dt = S.dt;
+  double wf[AMAXPB];
+  int nmk = 0, mk[2 * AMAXPB];
+  bool ok = true;
+  for (int q = 0; q < S.n_pb && ok; ++q) {
+    int g = S.pb[q];
+    PBOut R = pb_solve_warm(c_fluid, c_opts, I.tau, A.ph[o + g - 1], A.r[o + g - 1], A.m[o + g - 1], A.ph[o + g],
+                            A.r[o + g], A.m[o + g], A.pwl[o + g], A.pwr[o + g]);
+    if (!R.ok) {
+      afail(I, IMEXDS_ERR_PB_NOCONV);
+      ok = false;
+    }
+    wf[q] = R.w;
+  }
+  // candidate cells: both neighbours of every boundary, ascending, without repeats
+  for (int q = 0; q < S.n_pb && ok; ++q)
+    for (int s = 0; s < 2; ++s) {
+      int i = S.pb[q] - 1 + s;
+      if (nmk > 0 && mk[nmk - 1] >= i) continue;
+      int ql = -1, qr = -1;  // boundary indices on the left / right face of i
+      for (int p = 0; p < S.n_pb; ++p) {
+        if (S.pb[p] == i) ql = p;
+        if (S.pb[p] == i + 1) qr = p;
+      }
+      double wl = ql >= 0 ? wf[ql] : 0.0, wr = qr >= 0 ? wf[qr] : 0.0;
+      double hp = A.w[o + i] + (wr - wl) * dt;
+      if (hp < fmax(c_opts.alpha_min * I.h, 0.5 * A.w[o + i])) mk[nmk++] = i;
+    }
+  // merges in ascending order with the index shifts of earlier merges
+  int nmerge = 0, shift = 0;
+  bool any = false;
+  for (int q = 0; q < nmk && ok; ++q) {
+    if (mk[q] < 0) continue;  // consumed by the merge before it
+    int i = mk[q] - shift;
+    int Mi = S.M;
+    bool left_fixed = (i > 0) && !A.fpb[o + i];
+    bool right_fixed = (i + 1 < Mi) && !A.fpb[o + i + 1];
+    int a, b;
+    if (left_fixed) {
+      a = i - 1;
+      b = i;
+    } else if (right_fixed) {
+      a = i;
+      b = i + 1;
+      // the right neighbour is consumed: a later mark on it is dropped
+      if (q + 1 < nmk && mk[q + 1] - shift == i + 1) mk[q + 1] = -1000000;
+    } else {
+      afail(I, IMEXDS_ERR_VANISH);
+      ok = false;
+      break;
+    }
+    if (nmerge >= AMAXEV) {
+      afail(I, IMEXDS_ERR_CAPACITY);
+      ok = false;
+      break;
+    }
+    double wa = A.w[o + a], ra = A.r[o + a], ma = A.m[o + a];
+    double wb = A.w[o + b], rb = A.r[o + b], mb = A.m[o + b];
+    double wm = wa + wb;
+    A.r[o + a] = (wa * ra + wb * rb) / wm;
+    A.m[o + a] = (wa * ma + wb * mb) / wm;
+    A.w[o + a] = wm;
+    list_erase(A.w + o, A.r + o, A.m + o, A.ph + o, A.fpb + o, A.fj + o, A.fx + o, A.pwl + o, A.pwr + o, Mi, b);
+    S.M = Mi - 1;
+    if (rec) {
+      rec->mg_a[nmerge] = a;
+      rec->mg_b[nmerge] = b;
+      double* v = rec->mg_v[nmerge];
+      v[0] = wa, v[1] = ra, v[2] = ma, v[3] = wb, v[4] = rb, v[5] = mb;
+    }
+    nmerge++;
+    shift++;
+    any = true;
+    for (int p = 0; p < S.n_pb; ++p)
+      if (S.pb[p] > b) S.pb[p]--;
+  }
+  if (rec) rec->n_merge = nmerge;
+  // predicted widths on the merged grid (boundary speeds at U^n of the merged cells)
+  if (ok && any)
     for (int q = 0; q < S.n_pb && ok; ++q) {
       int g = S.pb[q];
-      PBOut R = pb_solve_warm(c_fluid, c_opts, I.tau, A.ph[o + g - 1], A.r[o + g - 1], A.m[o + g - 1], A.ph[o + g],
-                              A.r[o + g], A.m[o + g], A.pwl[o + g], A.pwr[o + g]);
+      PBOut R = pb_solve_warm(c_fluid, c_opts, I.tau, A.ph[o + g - 1], A.r[o + g - 1], A.m[o + g - 1],
+                              A.ph[o + g], A.r[o + g], A.m[o + g], A.pwl[o + g], A.pwr[o + g]);
       if (!R.ok) {
         afail(I, IMEXDS_ERR_PB_NOCONV);
         ok = false;
       }
       wf[q] = R.w;
     }
-    // candidate cells: both neighbours of every boundary, ascending, without repeats
-    for (int q = 0; q < S.n_pb && ok; ++q)
-      for (int s = 0; s < 2; ++s) {
-        int i = S.pb[q] - 1 + s;
-        if (nmk > 0 && mk[nmk - 1] >= i) continue;
-        int ql = -1, qr = -1;  // boundary indices on the left / right face of i
-        for (int p = 0; p < S.n_pb; ++p) {
-          if (S.pb[p] == i) ql = p;
-          if (S.pb[p] == i + 1) qr = p;
-        }
-        double wl = ql >= 0 ? wf[ql] : 0.0, wr = qr >= 0 ? wf[qr] : 0.0;
-        double hp = A.w[o + i] + (wr - wl) * dt;
-        if (hp < fmax(c_opts.alpha_min * I.h, 0.5 * A.w[o + i])) mk[nmk++] = i;
-      }
-    // merges in ascending order with the index shifts of earlier merges
-    int nmerge = 0, shift = 0;
-    bool any = false;
-    for (int q = 0; q < nmk && ok; ++q) {
-      if (mk[q] < 0) continue;  // consumed by the merge before it
-      int i = mk[q] - shift;
-      int Mi = S.M;
-      bool left_fixed = (i > 0) && !A.fpb[o + i];
-      bool right_fixed = (i + 1 < Mi) && !A.fpb[o + i + 1];
-      int a, b;
-      if (left_fixed) {
-        a = i - 1;
-        b = i;
-      } else if (right_fixed) {
-        a = i;
-        b = i + 1;
-        // the right neighbour is consumed: a later mark on it is dropped
-        if (q + 1 < nmk && mk[q + 1] - shift == i + 1) mk[q + 1] = -1000000;
-      } else {
-        afail(I, IMEXDS_ERR_VANISH);
-        ok = false;
-        break;
-      }
-      if (nmerge >= AMAXEV) {
+  // (3) blocks {k-1, k, k+1} around the tiny cell of every boundary, joined where they overlap
+  int nbk = 0;
+  const int Mm = S.M;
+  for (int q = 0; q < S.n_pb && ok; ++q) {
+    int g = S.pb[q];
+    int k = (A.w[o + g - 1] < A.w[o + g]) ? g - 1 : g;
+    int lo = max(k - 1, 0), hi = min(k + 1, Mm - 1);
+    if (nbk > 0 && lo <= S.bhi[nbk - 1]) {
+      S.bhi[nbk - 1] = max(S.bhi[nbk - 1], hi);
+    } else {
+      if (nbk >= AMAXBLK) {
         afail(I, IMEXDS_ERR_CAPACITY);
         ok = false;
         break;
       }
-      double wa = A.w[o + a], ra = A.r[o + a], ma = A.m[o + a];
-      double wb = A.w[o + b], rb = A.r[o + b], mb = A.m[o + b];
-      double wm = wa + wb;
-      A.r[o + a] = (wa * ra + wb * rb) / wm;
-      A.m[o + a] = (wa * ma + wb * mb) / wm;
-      A.w[o + a] = wm;
-      list_erase(A.w + o, A.r + o, A.m + o, A.ph + o, A.fpb + o, A.fj + o, A.fx + o, A.pwl + o, A.pwr + o, Mi, b);
-      S.M = Mi - 1;
-      if (rec) {
-        rec->mg_a[nmerge] = a;
-        rec->mg_b[nmerge] = b;
-        double* v = rec->mg_v[nmerge];
-        v[0] = wa, v[1] = ra, v[2] = ma, v[3] = wb, v[4] = rb, v[5] = mb;
-      }
-      nmerge++;
-      shift++;
-      any = true;
-      for (int p = 0; p < S.n_pb; ++p)
-        if (S.pb[p] > b) S.pb[p]--;
+      S.blo[nbk] = lo;
+      S.bhi[nbk] = hi;
+      nbk++;
     }
-    if (rec) rec->n_merge = nmerge;
-    // predicted widths on the merged grid (boundary speeds at U^n of the merged cells)
-    if (ok && any)
-      for (int q = 0; q < S.n_pb && ok; ++q) {
+  }
+  S.n_blk = ok ? nbk : 0;
+  // per block cell: predicted width and tiny flag (block cells numbered block after block)
+  int c = 0;
+  for (int b = 0; b < S.n_blk && ok; ++b) {
+    if (S.bhi[b] - S.blo[b] + 1 > AMAXB || c + S.bhi[b] - S.blo[b] + 1 > AMAXBC) {
+      afail(I, IMEXDS_ERR_CAPACITY);
+      ok = false;
+      break;
+    }
+    for (int i = S.blo[b]; i <= S.bhi[b]; ++i, ++c) {
+      double wl = 0.0, wr = 0.0;
+      int tiny = 0;
+      for (int q = 0; q < S.n_pb; ++q) {
         int g = S.pb[q];
-        PBOut R = pb_solve_warm(c_fluid, c_opts, I.tau, A.ph[o + g - 1], A.r[o + g - 1], A.m[o + g - 1],
-                                A.ph[o + g], A.r[o + g], A.m[o + g], A.pwl[o + g], A.pwr[o + g]);
-        if (!R.ok) {
-          afail(I, IMEXDS_ERR_PB_NOCONV);
-          ok = false;
-        }
-        wf[q] = R.w;
+        if (g == i) wl = wf[q];
+        if (g == i + 1) wr = wf[q];
+        int k = (A.w[o + g - 1] < A.w[o + g]) ? g - 1 : g;
+        if (k == i) tiny = 1;
       }
-    // (3) blocks {k-1, k, k+1} around the tiny cell of every boundary, joined where they overlap
-    int nbk = 0;
-    const int Mm = S.M;
-    for (int q = 0; q < S.n_pb && ok; ++q) {
-      int g = S.pb[q];
-      int k = (A.w[o + g - 1] < A.w[o + g]) ? g - 1 : g;
-      int lo = max(k - 1, 0), hi = min(k + 1, Mm - 1);
-      if (nbk > 0 && lo <= S.bhi[nbk - 1]) {
-        S.bhi[nbk - 1] = max(S.bhi[nbk - 1], hi);
-      } else {
-        if (nbk >= AMAXBLK) {
+      S.hp[c] = A.w[o + i] + (wr - wl) * S.dt;
+      S.tiny[c] = tiny;
+    }
+  }
+  if (rec && ok) {
+    rec->n_blk = S.n_blk;
+    for (int b = 0; b < S.n_blk; ++b) {
+      rec->blo[b] = S.blo[b];
+      rec->bhi[b] = S.bhi[b];
+    }
+  }
+  if (!ok) S.bad = 1;
+}
+
+// Algorithm 2 on every block of one instance, Part 2 and the boundary positions, created cells, splits and
+// the instance's new time (one thread: the instance's lane of warp 0).
+__device__ __noinline__ void serial_blocks(const ADev& A, AInst& I, SharedStep& S) {
+  const long long o = I.off;
+  StepRec* rec = S.rec;
+  const double t_end = S.t_end;
+  // (6) Algorithm 2 on every block, Part 2, boundary positions; (8) splits
+  bool ok = true;
+  int rc = 0, rp = 0, c = 0;
+  for (int b = 0; b < S.n_blk && ok; ++b) {
+    const int lo = S.blo[b], hi = S.bhi[b], nb = hi - lo + 1;
+    double orr[AMAXB], om[AMAXB], ow[AMAXB], wc[AMAXB + 1];
+    ok = dts_block(A, I, S, lo, hi, S.hp + c, S.tiny + c, A.F0[o + lo], A.F1[o + lo], A.F0[o + hi + 1],
+                   A.F1[o + hi + 1], rec, rc, rp, orr, om, ow, wc);
+    c += nb;
+    if (!ok) break;
+    for (int q = 0; q < nb; ++q) {
+      A.r[o + lo + q] = orr[q];
+      A.m[o + lo + q] = om[q];
+      A.w[o + lo + q] = ow[q];
+    }
+    for (int q = 1; q < nb; ++q)
+      if (A.fpb[o + lo + q]) A.fx[o + lo + q] += wc[q] * S.dt;
+  }
+  if (rec) rec->n_pbf = rp;
+  // (7) created cells (App. B), highest face first: width (w2 - w1) dt between two new boundaries at
+  //     x_g + w1 dt and x_g + w2 dt, state (rho_C, rho_C u_C), the other phase
+  for (int k = S.n_cr - 1; k >= 0 && ok; --k) {
+    const int g = S.cr_g[k];
+    const double* e = S.cr_o[k];
+    const int Mi = S.M;
+    if (Mi + 1 > I.cap || S.n_pb + 2 > AMAXPB) {
+      afail(I, IMEXDS_ERR_CAPACITY);
+      ok = false;
+      break;
+    }
+    const double xg = I.xL + (double)A.fj[o + g] * I.h;
+    list_open(A.w + o, A.r + o, A.m + o, A.ph + o, A.fpb + o, A.fj + o, A.fx + o, A.pwl + o, A.pwr + o, Mi, g);
+    S.M = Mi + 1;
+    A.w[o + g] = (e[6] - e[5]) * S.dt;
+    A.r[o + g] = e[4];
+    A.m[o + g] = e[4] * e[2];
+    A.ph[o + g] = (unsigned char)(1 - S.cr_P[k]);
+    A.fpb[o + g] = 1;
+    A.fx[o + g] = xg + e[5] * S.dt;
+    A.fpb[o + g + 1] = 1;
+    A.fx[o + g + 1] = xg + e[6] * S.dt;
+    A.pwl[o + g] = A.pwr[o + g] = A.pwl[o + g + 1] = A.pwr[o + g + 1] = 0.0;
+    // boundary list: faces at or after g move one up; the two new boundaries join it (kept sorted)
+    int np = 0, tmp[AMAXPB];
+    bool put = false;
+    for (int p = 0; p < S.n_pb; ++p) {
+      int f = S.pb[p] >= g ? S.pb[p] + 1 : S.pb[p];
+      if (!put && f > g) {
+        tmp[np++] = g;
+        tmp[np++] = g + 1;
+        put = true;
+      }
+      tmp[np++] = f;
+    }
+    if (!put) {
+      tmp[np++] = g;
+      tmp[np++] = g + 1;
+    }
+    for (int p = 0; p < np; ++p) S.pb[p] = tmp[p];
+    S.n_pb = np;
+  }
+  // splits of boundary cells wider than split_ratio h (Sec. 3.4), keeping fixed faces on the lattice
+  int nsp = 0;
+  if (ok) {
+    int Mi = S.M;
+    int last = -1;
+    for (int q = 0; q < S.n_pb && ok; ++q)
+      for (int s = 0; s < 2; ++s) {
+        int i = S.pb[q] - 1 + s + nsp;  // boundary faces shift by the cells inserted so far
+        if (i <= last) continue;
+        last = i;
+        bool lpb = A.fpb[o + i], rpb = A.fpb[o + i + 1];
+        if (!(lpb || rpb) || !(A.w[o + i] > c_opts.split_ratio * I.h)) continue;
+        double w1, w2;
+        int jc, cs;
+        if (!lpb) {
+          jc = A.fj[o + i] + 1;
+          w1 = I.h;
+          w2 = A.w[o + i] - I.h;
+          cs = 1;
+        } else if (!rpb) {
+          jc = A.fj[o + i + 1] - 1;
+          w2 = I.h;
+          w1 = A.w[o + i] - I.h;
+          cs = 2;
+        } else {
+          double xm = 0.5 * (A.fx[o + i] + A.fx[o + i + 1]);
+          jc = (int)llround((xm - I.xL) / I.h);
+          w1 = (I.xL + (double)jc * I.h) - A.fx[o + i];
+          w2 = A.w[o + i] - w1;
+          cs = 3;
+          if (!(w1 > 0.0) || !(w2 > 0.0)) continue;
+        }
+        if (Mi + 1 > I.cap || nsp >= AMAXEV) {
           afail(I, IMEXDS_ERR_CAPACITY);
           ok = false;
           break;
         }
-        S.blo[nbk] = lo;
-        S.bhi[nbk] = hi;
-        nbk++;
-      }
-    }
-    S.n_blk = ok ? nbk : 0;
-    // per block cell: predicted width and tiny flag (block cells numbered block after block)
-    int c = 0;
-    for (int b = 0; b < S.n_blk && ok; ++b) {
-      if (S.bhi[b] - S.blo[b] + 1 > AMAXB || c + S.bhi[b] - S.blo[b] + 1 > AMAXBC) {
-        afail(I, IMEXDS_ERR_CAPACITY);
-        ok = false;
-        break;
-      }
-      for (int i = S.blo[b]; i <= S.bhi[b]; ++i, ++c) {
-        double wl = 0.0, wr = 0.0;
-        int tiny = 0;
-        for (int q = 0; q < S.n_pb; ++q) {
-          int g = S.pb[q];
-          if (g == i) wl = wf[q];
-          if (g == i + 1) wr = wf[q];
-          int k = (A.w[o + g - 1] < A.w[o + g]) ? g - 1 : g;
-          if (k == i) tiny = 1;
-        }
-        s_hp[c] = A.w[o + i] + (wr - wl) * S.dt;
-        s_tiny[c] = tiny;
-      }
-    }
-    if (rec && ok) {
-      rec->n_blk = S.n_blk;
-      for (int b = 0; b < S.n_blk; ++b) {
-        rec->blo[b] = S.blo[b];
-        rec->bhi[b] = S.bhi[b];
-      }
-    }
-    if (!ok) S.bad = 1;
-  }
-  __syncthreads();
-  if (S.bad) return;
-  M = S.M;
-  // (4) phase creation (App. B) at same-phase faces between two explicit cells: detection by the
-  //     no-transition star pressure, a face whose left neighbour face is also detected is not used
-  if (tid == 0) S.n_cr = 0;
-  __syncthreads();
-  if (c_opts.creation) {
-    for (int g = tid; g <= M; g += blockDim.x) {
-      unsigned char det = 0;
-      if (g >= 1 && g < M && !A.fpb[o + g] && !in_block(S, g - 1) && !in_block(S, g)) {
-        det = creation_detect(c_fluid, A.ph[o + g], A.r[o + g - 1], div_nr(A.m[o + g - 1], A.r[o + g - 1]),
-                              A.r[o + g], div_nr(A.m[o + g], A.r[o + g]));
-      }
-      A.cdet[o + g] = det;
-    }
-    __syncthreads();
-    for (int g = 1 + tid; g < M; g += blockDim.x)
-      if (A.cdet[o + g] && !A.cdet[o + g - 1]) {
-        const int q = atomicAdd(&S.n_cr, 1);
-        if (q < AMAXCR) S.cr_g[q] = g;
-      }
-    __syncthreads();
-    if (tid == 0) {
-      if (S.n_cr > AMAXCR) {
-        afail(I, IMEXDS_ERR_CAPACITY);
-        S.bad = 1;
-        S.n_cr = 0;
-      }
-      for (int a = 1; a < S.n_cr; ++a) {
-        int v = S.cr_g[a], b = a - 1;
-        while (b >= 0 && S.cr_g[b] > v) {
-          S.cr_g[b + 1] = S.cr_g[b];
-          --b;
-        }
-        S.cr_g[b + 1] = v;
-      }
-      for (int k = 0; k < S.n_cr && !S.bad; ++k) {
-        const int g = S.cr_g[k];
-        const int P = A.ph[o + g];
-        CreateOut R = creation_solve(c_fluid, c_opts, I.tau, P, A.r[o + g - 1], A.m[o + g - 1], A.r[o + g], A.m[o + g]);
-        if (!R.ok) {
-          afail(I, IMEXDS_ERR_PB_NOCONV);
-          S.bad = 1;
-          break;
-        }
-        S.cr_P[k] = P;
-        const double out[7] = {R.z1, R.z2, R.uC, R.pC, R.rhoC, R.w1, R.w2};
-        for (int q = 0; q < 7; ++q) S.cr_o[k][q] = out[q];
+        list_open(A.w + o, A.r + o, A.m + o, A.ph + o, A.fpb + o, A.fj + o, A.fx + o, A.pwl + o, A.pwr + o, Mi,
+                  i + 1);
+        Mi++;
+        A.fpb[o + i + 1] = 0;
+        A.fj[o + i + 1] = jc;
+        A.fx[o + i + 1] = 0.0;
+        A.pwl[o + i + 1] = A.pwr[o + i + 1] = 0.0;
+        A.w[o + i] = w1;
+        A.w[o + i + 1] = w2;
+        A.r[o + i + 1] = A.r[o + i];  // both parts keep the state of the split cell
+        A.m[o + i + 1] = A.m[o + i];
+        A.ph[o + i + 1] = A.ph[o + i];
         if (rec) {
-          rec->cr_g[k] = g;
-          rec->cr_P[k] = P;
-          rec->cr_x[k][0] = R.pPl;
-          rec->cr_x[k][1] = R.pC;
-          rec->cr_x[k][2] = R.pPr;
-          for (int q = 0; q < 7; ++q) rec->cr_o[k][q] = out[q];
+          rec->sp_i[nsp] = i;
+          rec->sp_case[nsp] = cs;
+        }
+        nsp++;
+        last = i + 1;  // the new cell is not examined in this step
+      }
+    S.M = Mi;
+  }
+  if (rec) rec->n_split = nsp;
+  if (!ok) S.bad = 1;
+  I.M = S.M;
+  I.t = S.clipped ? t_end : I.t + S.dt;
+  I.done++;
+}
+
+// One time step of the replay for the instances of this CTA that take part (S.act). Warp w advances instance
+// base + w through the data-parallel parts; lane l of warp 0 runs the one-thread parts of instance base + l
+// (serial_grid, serial_blocks). Tapes the pre-step list into tape slot S.slot and the decisions into *S.rec
+// when S.rec != nullptr. Every thread of the CTA calls it.
+__device__ void fwd_step_grp(const ADev& A, SharedStep* SS, int base, int G) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = lane;
+  SharedStep& S = SS[w];
+  const bool mine = S.act != 0;
+  if (mine) {
+    AInst& I = A.I[base + w];
+    const long long o = I.off;
+    StepRec* rec = S.rec;
+    const int slot = S.slot;
+    const double t_end = S.t_end;
+    if (lane == 0) {
+      S.M = I.M;
+      S.bad = 0;
+    }
+    __syncwarp();
+    int M = S.M;
+    if (rec) {
+      const long long to = (long long)slot * A.stride + o;
+      cta_copy_d(A.tp_w + to, A.w + o, M);
+      cta_copy_d(A.tp_r + to, A.r + o, M);
+      cta_copy_d(A.tp_m + to, A.m + o, M);
+      cta_copy_b(A.tp_ph + to, A.ph + o, M);
+      cta_copy_b(A.tp_fpb + to, A.fpb + o, M + 1);
+      if (lane == 0) A.tp_M[(long long)slot * A.n_inst + (int)(&I - A.I)] = M;
+    }
+    // (1) CFL time step (Eq. cfl_cond:unif) over all cells, with the argmax cell
+    {
+      double v = -1.0;
+      int idx = 0x7fffffff;
+      for (int i = tid; i < M; i += 32) {
+        double s = fabs(A.m[o + i] / A.r[o + i]) + c_fluid.ph[A.ph[o + i]].a;
+        if (s > v) {
+          v = s;
+          idx = i;
+        }
+      }
+      warp_argmax(v, idx);
+      if (lane == 0) {
+        double dt = c_opts.cfl * I.h / v;
+        int clipped = 0;
+        if (t_end > 0.0 && t_end - I.t <= dt) {
+          dt = t_end - I.t;
+          clipped = 1;
+        }
+        S.dt = dt;
+        S.lam = dt / I.h;
+        S.kmax = idx;
+        S.clipped = clipped;
+        if (rec) {
+          rec->dt = dt;
+          rec->clipped = clipped;
+          rec->kmax = idx;
+          rec->n_merge = rec->n_blk = rec->n_split = rec->n_pbf = 0;
         }
       }
     }
-    __syncthreads();
-    if (S.bad) return;
-  }
-  if (rec && tid == 0) rec->n_cr = S.n_cr;
-  // (5) explicit fluxes from U^n at every face outside the blocks, then the explicit update
-  for (int g = tid; g <= M; g += blockDim.x) {
-    if (face_in_block(S, g)) continue;
-    if (S.n_cr && cr_at(S, g) >= 0) continue;  // creation faces: the per-side fluxes of the event
-    double f0, f1;
-    if (g == 0)
-      phys_flux_fast(c_fluid.ph[A.ph[o]], A.r[o], A.m[o], f0, f1);
-    else if (g == M)
-      phys_flux_fast(c_fluid.ph[A.ph[o + M - 1]], A.r[o + M - 1], A.m[o + M - 1], f0, f1);
-    else
-      hll_fast(c_fluid.ph[A.ph[o + g]], A.r[o + g - 1], A.m[o + g - 1], A.r[o + g], A.m[o + g], f0, f1);
-    A.F0[o + g] = f0;
-    A.F1[o + g] = f1;
+    if (!collect_pbs(S, A.fpb + o, M) && lane == 0) {
+      afail(I, IMEXDS_ERR_CAPACITY);
+      S.bad = 1;
+    }
+    __syncwarp();
   }
   __syncthreads();
-  for (int i = tid; i < M; i += blockDim.x) {
-    if (in_block(S, i)) continue;
-    const double wi = A.w[o + i];
-    if (S.n_cr && (cr_at(S, i) >= 0 || cr_at(S, i + 1) >= 0)) {
-      const CellUpd c = cell_upd(A.F0 + o, A.F1 + o, S, i, wi, S.dt);
-      A.r[o + i] = (wi * A.r[o + i] - S.dt * (c.fr0 - c.fl0)) / c.h1;
-      A.m[o + i] = (wi * A.m[o + i] - S.dt * (c.fr1 - c.fl1)) / c.h1;
-      A.w[o + i] = c.h1;
-    } else if (wi == I.h) {
-      A.r[o + i] = __fma_rn(-S.lam, A.F0[o + i + 1] - A.F0[o + i], A.r[o + i]);
-      A.m[o + i] = __fma_rn(-S.lam, A.F1[o + i + 1] - A.F1[o + i], A.m[o + i]);
-    } else {
-      A.r[o + i] = (wi * A.r[o + i] - S.dt * (A.F0[o + i + 1] - A.F0[o + i])) / wi;
-      A.m[o + i] = (wi * A.m[o + i] - S.dt * (A.F1[o + i + 1] - A.F1[o + i])) / wi;
-    }
-  }
+  if (w == 0 && lane < G && SS[lane].act && !SS[lane].bad) serial_grid(A, A.I[base + lane], SS[lane]);
   __syncthreads();
-  // (6) Algorithm 2 on every block, Part 2, boundary positions; (8) splits
-  if (tid == 0) {
-    bool ok = true;
-    int rc = 0, rp = 0, c = 0;
-    for (int b = 0; b < S.n_blk && ok; ++b) {
-      const int lo = S.blo[b], hi = S.bhi[b], nb = hi - lo + 1;
-      double orr[AMAXB], om[AMAXB], ow[AMAXB], wc[AMAXB + 1];
-      ok = dts_block(A, I, S, lo, hi, s_hp + c, s_tiny + c, A.F0[o + lo], A.F1[o + lo], A.F0[o + hi + 1],
-                     A.F1[o + hi + 1], rec, rc, rp, orr, om, ow, wc);
-      c += nb;
-      if (!ok) break;
-      for (int q = 0; q < nb; ++q) {
-        A.r[o + lo + q] = orr[q];
-        A.m[o + lo + q] = om[q];
-        A.w[o + lo + q] = ow[q];
-      }
-      for (int q = 1; q < nb; ++q)
-        if (A.fpb[o + lo + q]) A.fx[o + lo + q] += wc[q] * S.dt;
-    }
-    if (rec) rec->n_pbf = rp;
-    // (7) created cells (App. B), highest face first: width (w2 - w1) dt between two new boundaries at
-    //     x_g + w1 dt and x_g + w2 dt, state (rho_C, rho_C u_C), the other phase
-    for (int k = S.n_cr - 1; k >= 0 && ok; --k) {
-      const int g = S.cr_g[k];
-      const double* e = S.cr_o[k];
-      const int Mi = S.M;
-      if (Mi + 1 > I.cap || S.n_pb + 2 > AMAXPB) {
-        afail(I, IMEXDS_ERR_CAPACITY);
-        ok = false;
-        break;
-      }
-      const double xg = I.xL + (double)A.fj[o + g] * I.h;
-      list_open(A.w + o, A.r + o, A.m + o, A.ph + o, A.fpb + o, A.fj + o, A.fx + o, A.pwl + o, A.pwr + o, Mi, g);
-      S.M = Mi + 1;
-      A.w[o + g] = (e[6] - e[5]) * S.dt;
-      A.r[o + g] = e[4];
-      A.m[o + g] = e[4] * e[2];
-      A.ph[o + g] = (unsigned char)(1 - S.cr_P[k]);
-      A.fpb[o + g] = 1;
-      A.fx[o + g] = xg + e[5] * S.dt;
-      A.fpb[o + g + 1] = 1;
-      A.fx[o + g + 1] = xg + e[6] * S.dt;
-      A.pwl[o + g] = A.pwr[o + g] = A.pwl[o + g + 1] = A.pwr[o + g + 1] = 0.0;
-      // boundary list: faces at or after g move one up; the two new boundaries join it (kept sorted)
-      int np = 0, tmp[AMAXPB];
-      bool put = false;
-      for (int p = 0; p < S.n_pb; ++p) {
-        int f = S.pb[p] >= g ? S.pb[p] + 1 : S.pb[p];
-        if (!put && f > g) {
-          tmp[np++] = g;
-          tmp[np++] = g + 1;
-          put = true;
+  if (mine && !S.bad) {
+    AInst& I = A.I[base + w];
+    const long long o = I.off;
+    StepRec* rec = S.rec;
+    int M = S.M;
+    // (4) phase creation (App. B) at same-phase faces between two explicit cells: detection by the
+    //     no-transition star pressure, a face whose left neighbour face is also detected is not used
+    if (lane == 0) S.n_cr = 0;
+    __syncwarp();
+    if (c_opts.creation) {
+      for (int g = tid; g <= M; g += 32) {
+        unsigned char det = 0;
+        if (g >= 1 && g < M && !A.fpb[o + g] && !in_block(S, g - 1) && !in_block(S, g)) {
+          det = creation_detect(c_fluid, A.ph[o + g], A.r[o + g - 1], div_nr(A.m[o + g - 1], A.r[o + g - 1]),
+                                A.r[o + g], div_nr(A.m[o + g], A.r[o + g]));
         }
-        tmp[np++] = f;
+        A.cdet[o + g] = det;
       }
-      if (!put) {
-        tmp[np++] = g;
-        tmp[np++] = g + 1;
-      }
-      for (int p = 0; p < np; ++p) S.pb[p] = tmp[p];
-      S.n_pb = np;
-    }
-    // splits of boundary cells wider than split_ratio h (Sec. 3.4), keeping fixed faces on the lattice
-    int nsp = 0;
-    if (ok) {
-      int Mi = S.M;
-      int last = -1;
-      for (int q = 0; q < S.n_pb && ok; ++q)
-        for (int s = 0; s < 2; ++s) {
-          int i = S.pb[q] - 1 + s + nsp;  // boundary faces shift by the cells inserted so far
-          if (i <= last) continue;
-          last = i;
-          bool lpb = A.fpb[o + i], rpb = A.fpb[o + i + 1];
-          if (!(lpb || rpb) || !(A.w[o + i] > c_opts.split_ratio * I.h)) continue;
-          double w1, w2;
-          int jc, cs;
-          if (!lpb) {
-            jc = A.fj[o + i] + 1;
-            w1 = I.h;
-            w2 = A.w[o + i] - I.h;
-            cs = 1;
-          } else if (!rpb) {
-            jc = A.fj[o + i + 1] - 1;
-            w2 = I.h;
-            w1 = A.w[o + i] - I.h;
-            cs = 2;
-          } else {
-            double xm = 0.5 * (A.fx[o + i] + A.fx[o + i + 1]);
-            jc = (int)llround((xm - I.xL) / I.h);
-            w1 = (I.xL + (double)jc * I.h) - A.fx[o + i];
-            w2 = A.w[o + i] - w1;
-            cs = 3;
-            if (!(w1 > 0.0) || !(w2 > 0.0)) continue;
+      __syncwarp();
+      for (int g = 1 + tid; g < M; g += 32)
+        if (A.cdet[o + g] && !A.cdet[o + g - 1]) {
+          const int q = atomicAdd(&S.n_cr, 1);
+          if (q < AMAXCR) S.cr_g[q] = g;
+        }
+      __syncwarp();
+      if (lane == 0) {
+        if (S.n_cr > AMAXCR) {
+          afail(I, IMEXDS_ERR_CAPACITY);
+          S.bad = 1;
+          S.n_cr = 0;
+        }
+        for (int a = 1; a < S.n_cr; ++a) {
+          int v = S.cr_g[a], b = a - 1;
+          while (b >= 0 && S.cr_g[b] > v) {
+            S.cr_g[b + 1] = S.cr_g[b];
+            --b;
           }
-          if (Mi + 1 > I.cap || nsp >= AMAXEV) {
-            afail(I, IMEXDS_ERR_CAPACITY);
-            ok = false;
+          S.cr_g[b + 1] = v;
+        }
+        for (int k = 0; k < S.n_cr && !S.bad; ++k) {
+          const int g = S.cr_g[k];
+          const int P = A.ph[o + g];
+          CreateOut R = creation_solve(c_fluid, c_opts, I.tau, P, A.r[o + g - 1], A.m[o + g - 1], A.r[o + g], A.m[o + g]);
+          if (!R.ok) {
+            afail(I, IMEXDS_ERR_PB_NOCONV);
+            S.bad = 1;
             break;
           }
-          list_open(A.w + o, A.r + o, A.m + o, A.ph + o, A.fpb + o, A.fj + o, A.fx + o, A.pwl + o, A.pwr + o, Mi,
-                    i + 1);
-          Mi++;
-          A.fpb[o + i + 1] = 0;
-          A.fj[o + i + 1] = jc;
-          A.fx[o + i + 1] = 0.0;
-          A.pwl[o + i + 1] = A.pwr[o + i + 1] = 0.0;
-          A.w[o + i] = w1;
-          A.w[o + i + 1] = w2;
-          A.r[o + i + 1] = A.r[o + i];  // both parts keep the state of the split cell
-          A.m[o + i + 1] = A.m[o + i];
-          A.ph[o + i + 1] = A.ph[o + i];
+          S.cr_P[k] = P;
+          const double out[7] = {R.z1, R.z2, R.uC, R.pC, R.rhoC, R.w1, R.w2};
+          for (int q = 0; q < 7; ++q) S.cr_o[k][q] = out[q];
           if (rec) {
-            rec->sp_i[nsp] = i;
-            rec->sp_case[nsp] = cs;
+            rec->cr_g[k] = g;
+            rec->cr_P[k] = P;
+            rec->cr_x[k][0] = R.pPl;
+            rec->cr_x[k][1] = R.pC;
+            rec->cr_x[k][2] = R.pPr;
+            for (int q = 0; q < 7; ++q) rec->cr_o[k][q] = out[q];
           }
-          nsp++;
-          last = i + 1;  // the new cell is not examined in this step
         }
-      S.M = Mi;
+      }
+      __syncwarp();
     }
-    if (rec) rec->n_split = nsp;
-    if (!ok) S.bad = 1;
-    I.M = S.M;
-    I.t = S.clipped ? t_end : I.t + S.dt;
-    I.done++;
+    if (!S.bad) {
+      if (rec && lane == 0) rec->n_cr = S.n_cr;
+      // (5) explicit fluxes from U^n at every face outside the blocks, then the explicit update
+      for (int g = tid; g <= M; g += 32) {
+        if (face_in_block(S, g)) continue;
+        if (S.n_cr && cr_at(S, g) >= 0) continue;  // creation faces: the per-side fluxes of the event
+        double f0, f1;
+        if (g == 0)
+          phys_flux_fast(c_fluid.ph[A.ph[o]], A.r[o], A.m[o], f0, f1);
+        else if (g == M)
+          phys_flux_fast(c_fluid.ph[A.ph[o + M - 1]], A.r[o + M - 1], A.m[o + M - 1], f0, f1);
+        else
+          hll_fast(c_fluid.ph[A.ph[o + g]], A.r[o + g - 1], A.m[o + g - 1], A.r[o + g], A.m[o + g], f0, f1);
+        A.F0[o + g] = f0;
+        A.F1[o + g] = f1;
+      }
+      __syncwarp();
+      for (int i = tid; i < M; i += 32) {
+        if (in_block(S, i)) continue;
+        const double wi = A.w[o + i];
+        if (S.n_cr && (cr_at(S, i) >= 0 || cr_at(S, i + 1) >= 0)) {
+          const CellUpd c = cell_upd(A.F0 + o, A.F1 + o, S, i, wi, S.dt);
+          A.r[o + i] = (wi * A.r[o + i] - S.dt * (c.fr0 - c.fl0)) / c.h1;
+          A.m[o + i] = (wi * A.m[o + i] - S.dt * (c.fr1 - c.fl1)) / c.h1;
+          A.w[o + i] = c.h1;
+        } else if (wi == I.h) {
+          A.r[o + i] = __fma_rn(-S.lam, A.F0[o + i + 1] - A.F0[o + i], A.r[o + i]);
+          A.m[o + i] = __fma_rn(-S.lam, A.F1[o + i + 1] - A.F1[o + i], A.m[o + i]);
+        } else {
+          A.r[o + i] = (wi * A.r[o + i] - S.dt * (A.F0[o + i + 1] - A.F0[o + i])) / wi;
+          A.m[o + i] = (wi * A.m[o + i] - S.dt * (A.F1[o + i + 1] - A.F1[o + i])) / wi;
+        }
+      }
+      __syncwarp();
+    }
   }
   __syncthreads();
-  M = S.M;
-  int badc = 0;
-  for (int i = tid; i < M; i += blockDim.x) {
-    double ri = A.r[o + i], mi = A.m[o + i], wi = A.w[o + i];
-    if (!(ri > 0.0) || !isfinite(ri) || !isfinite(mi) || !(wi > 0.0)) badc = 1;
-  }
-  badc = __syncthreads_or(badc);
-  if (tid == 0 && badc) afail(I, IMEXDS_ERR_NONPHYSICAL);
+  if (w == 0 && lane < G && SS[lane].act && !SS[lane].bad) serial_blocks(A, A.I[base + lane], SS[lane]);
   __syncthreads();
+  if (mine && A.I[base + w].status == 0) {
+    AInst& I = A.I[base + w];
+    const long long o = I.off;
+    const int M = S.M;
+    int badc = 0;
+    for (int i = lane; i < M; i += 32) {
+      double ri = A.r[o + i], mi = A.m[o + i], wi = A.w[o + i];
+      if (!(ri > 0.0) || !isfinite(ri) || !isfinite(mi) || !(wi > 0.0)) badc = 1;
+    }
+    badc = __any_sync(0xffffffffu, badc);
+    if (lane == 0 && badc) afail(I, IMEXDS_ERR_NONPHYSICAL);
+  }
+  __syncwarp();
 }
 
 // ------------------------------------------------------------------------------ reverse step
@@ -1057,296 +1080,315 @@ __device__ __noinline__ bool block_adjoint(const ADev& A, AInst& I, const StepRe
   return true;
 }
 
-__device__ void rev_step(const ADev& A, AInst& I, SharedStep& S, int slot, const StepRec& R) {
-  const long long o = I.off;
-  const int tid = threadIdx.x;
-  const long long to = (long long)slot * A.stride + o;
-  const int Mn = A.tp_M[(long long)slot * A.n_inst + (int)(&I - A.I)];
+// The blocks of one reverse step (one thread: the instance's lane of warp 0): block_adjoint on each, in the
+// order the forward step solved them.
+__device__ __noinline__ void serial_rev_blocks(const ADev& A, AInst& I, SharedStep& S) {
+  const StepRec& R = *S.rec;
   const double dt = R.dt;
-  double lam_dt = 0.0;        // thread 0 accumulates d(dt) contributions here
-  double lcr[AMAXCR][7];      // thread 0: adjoints of the creation outputs z1, z2, u_C, p_C, rho_C, w1, w2
-  // (a) splits^T on the adjoint list, then the created cells leave it (insertion^T)
-  if (tid == 0) {
-    int Mc = I.M;
-    for (int q = R.n_split - 1; q >= 0; --q) {
-      const int i = R.sp_i[q];
-      A.lr[o + i] += A.lr[o + i + 1];
-      A.lm[o + i] += A.lm[o + i + 1];
-      if (R.sp_case[q] == 1) {
-        A.lw[o + i] = A.lw[o + i + 1];
-      } else if (R.sp_case[q] == 3) {
-        A.lx[o + i] += -A.lw[o + i] + A.lw[o + i + 1];
-        A.lw[o + i] = A.lw[o + i + 1];
+  int cell0 = 0, pbf = 0;
+  double ltau = 0.0;
+  for (int b = 0; b < S.n_blk; ++b) {
+    if (!block_adjoint(A, I, R, S.blo[b], S.bhi[b], cell0, pbf, dt, S.lam_dt, ltau)) {
+      S.bad = 1;
+      afail(I, IMEXDS_ERR_STATE, 3);
+      break;
+    }
+    cell0 += S.bhi[b] - S.blo[b] + 1;
+  }
+  I.lam_tau += ltau;
+}
+
+// One reverse step for the instances of this CTA that take part (S.act), the step taped in slot S.slot with the
+// record *S.rec. Warp w runs the data-parallel parts of instance base + w; lane l of warp 0 the transposed block
+// solves of instance base + l (serial_rev_blocks). Every thread of the CTA calls it.
+__device__ void rev_step_grp(const ADev& A, SharedStep* SS, int base, int G) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = lane;
+  SharedStep& S = SS[w];
+  const bool mine = S.act != 0;
+  double lcr[AMAXCR][7];  // lane 0: adjoints of the creation outputs z1, z2, u_C, p_C, rho_C, w1, w2
+  if (mine) {
+    AInst& I = A.I[base + w];
+    const StepRec& R = *S.rec;
+    const long long o = I.off;
+    const long long to = (long long)S.slot * A.stride + o;
+    const int Mn = A.tp_M[(long long)S.slot * A.n_inst + base + w];
+    const double dt = R.dt;
+    // (a) splits^T on the adjoint list, then the created cells leave it (insertion^T)
+    if (lane == 0) {
+      S.lam_dt = 0.0;
+      int Mc = I.M;
+      for (int q = R.n_split - 1; q >= 0; --q) {
+        const int i = R.sp_i[q];
+        A.lr[o + i] += A.lr[o + i + 1];
+        A.lm[o + i] += A.lm[o + i + 1];
+        if (R.sp_case[q] == 1) {
+          A.lw[o + i] = A.lw[o + i + 1];
+        } else if (R.sp_case[q] == 3) {
+          A.lx[o + i] += -A.lw[o + i] + A.lw[o + i + 1];
+          A.lw[o + i] = A.lw[o + i + 1];
+        }
+        lam_erase(A.lw + o, A.lr + o, A.lm + o, A.lx + o, Mc, i + 1);
+        Mc--;
       }
-      lam_erase(A.lw + o, A.lr + o, A.lm + o, A.lx + o, Mc, i + 1);
-      Mc--;
-    }
-    S.n_cr = R.n_cr;
-    for (int k = 0; k < R.n_cr; ++k) {
-      S.cr_g[k] = R.cr_g[k];
-      S.cr_P[k] = R.cr_P[k];
-      for (int q = 0; q < 7; ++q) {
-        S.cr_o[k][q] = R.cr_o[k][q];
-        lcr[k][q] = 0.0;
+      S.n_cr = R.n_cr;
+      for (int k = 0; k < R.n_cr; ++k) {
+        S.cr_g[k] = R.cr_g[k];
+        S.cr_P[k] = R.cr_P[k];
+        for (int q = 0; q < 7; ++q) {
+          S.cr_o[k][q] = R.cr_o[k][q];
+          lcr[k][q] = 0.0;
+        }
       }
-    }
-    // the created cell of event k sits at g_k + k (each earlier event shifted it by one): highest first.
-    // w_C = (w2 - w1) dt, rho_C, m_C = rho_C u_C, boundaries at x_g + w1 dt and x_g + w2 dt
-    for (int k = R.n_cr - 1; k >= 0; --k) {
-      const int p = R.cr_g[k] + k;
-      const double* e = R.cr_o[k];
-      const double lwC = A.lw[o + p], lrC = A.lr[o + p], lmC = A.lm[o + p];
-      const double lxl = A.lx[o + p], lxr = A.lx[o + p + 1];
-      lcr[k][5] += (-lwC + lxl) * dt;
-      lcr[k][6] += (lwC + lxr) * dt;
-      lcr[k][4] += lrC + lmC * e[2];
-      lcr[k][2] += lmC * e[4];
-      lam_dt += lwC * (e[6] - e[5]) + lxl * e[5] + lxr * e[6];
-      lam_erase(A.lw + o, A.lr + o, A.lm + o, A.lx + o, Mc, p);
-      Mc--;
-      A.lx[o + p] = 0.0;  // the fixed face the boundaries were created at
-    }
-    S.M = Mc;  // post-merge count
-    S.n_blk = R.n_blk;
-    for (int b = 0; b < R.n_blk; ++b) {
-      S.blo[b] = R.blo[b];
-      S.bhi[b] = R.bhi[b];
-    }
-    S.bad = 0;
-  }
-  __syncthreads();
-  // (b) the post-merge list: the taped pre-step list with the recorded merges applied
-  cta_copy_d(A.pw + o, A.tp_w + to, Mn);
-  cta_copy_d(A.pr + o, A.tp_r + to, Mn);
-  cta_copy_d(A.pm + o, A.tp_m + to, Mn);
-  cta_copy_b(A.pph + o, A.tp_ph + to, Mn);
-  cta_copy_b(A.pfpb + o, A.tp_fpb + to, Mn + 1);
-  __syncthreads();
-  if (tid == 0) {
-    int Mc = Mn;
-    for (int q = 0; q < R.n_merge; ++q) {
-      const int a = R.mg_a[q], b = R.mg_b[q];
-      const double* v = R.mg_v[q];
-      double wm = v[0] + v[3];
-      A.pr[o + a] = (v[0] * v[1] + v[3] * v[4]) / wm;
-      A.pm[o + a] = (v[0] * v[2] + v[3] * v[5]) / wm;
-      A.pw[o + a] = wm;
-      list_erase(A.pw + o, A.pr + o, A.pm + o, A.pph + o, A.pfpb + o, nullptr, nullptr, nullptr, nullptr, Mc, b);
-      Mc--;
-    }
-    if (Mc != S.M) S.bad = 1;
-  }
-  __syncthreads();
-  if (S.bad) {
-    if (tid == 0) afail(I, IMEXDS_ERR_STATE, 2);
-    __syncthreads();
-    return;
-  }
-  const int M = S.M;
-  // (c) zero the accumulators; explicit fluxes at U^n (post-merge)
-  cta_zero(A.nw + o, M);
-  cta_zero(A.nr + o, M);
-  cta_zero(A.nm + o, M);
-  cta_zero(A.nx + o, M + 1);
-  cta_zero(A.LF0 + o, M + 1);
-  cta_zero(A.LF1 + o, M + 1);
-  for (int g = tid; g <= M; g += blockDim.x) {
-    if (face_in_block(S, g)) continue;
-    if (S.n_cr && cr_at(S, g) >= 0) continue;
-    double f0, f1;
-    if (g == 0)
-      phys_flux_fast(c_fluid.ph[A.pph[o]], A.pr[o], A.pm[o], f0, f1);
-    else if (g == M)
-      phys_flux_fast(c_fluid.ph[A.pph[o + M - 1]], A.pr[o + M - 1], A.pm[o + M - 1], f0, f1);
-    else
-      hll_fast(c_fluid.ph[A.pph[o + g]], A.pr[o + g - 1], A.pm[o + g - 1], A.pr[o + g], A.pm[o + g], f0, f1);
-    A.F0[o + g] = f0;
-    A.F1[o + g] = f1;
-  }
-  __syncthreads();
-  // (d) blocks (thread 0)
-  if (tid == 0) {
-    int cell0 = 0, pbf = 0;
-    double ltau = 0.0;
-    for (int b = 0; b < S.n_blk; ++b) {
-      if (!block_adjoint(A, I, R, S.blo[b], S.bhi[b], cell0, pbf, dt, lam_dt, ltau)) {
-        S.bad = 1;
-        break;
+      // the created cell of event k sits at g_k + k (each earlier event shifted it by one): highest first.
+      // w_C = (w2 - w1) dt, rho_C, m_C = rho_C u_C, boundaries at x_g + w1 dt and x_g + w2 dt
+      for (int k = R.n_cr - 1; k >= 0; --k) {
+        const int p = R.cr_g[k] + k;
+        const double* e = R.cr_o[k];
+        const double lwC = A.lw[o + p], lrC = A.lr[o + p], lmC = A.lm[o + p];
+        const double lxl = A.lx[o + p], lxr = A.lx[o + p + 1];
+        lcr[k][5] += (-lwC + lxl) * dt;
+        lcr[k][6] += (lwC + lxr) * dt;
+        lcr[k][4] += lrC + lmC * e[2];
+        lcr[k][2] += lmC * e[4];
+        S.lam_dt += lwC * (e[6] - e[5]) + lxl * e[5] + lxr * e[6];
+        lam_erase(A.lw + o, A.lr + o, A.lm + o, A.lx + o, Mc, p);
+        Mc--;
+        A.lx[o + p] = 0.0;  // the fixed face the boundaries were created at
       }
-      cell0 += S.bhi[b] - S.blo[b] + 1;
-    }
-    I.lam_tau += ltau;
-  }
-  __syncthreads();
-  if (S.bad) {
-    if (tid == 0) afail(I, IMEXDS_ERR_STATE, 3);
-    __syncthreads();
-    return;
-  }
-  // (e) explicit sweep^T: face adjoints from the explicit cells, then the face Jacobians at U^n
-  for (int g = tid; g <= M; g += blockDim.x) {
-    if (face_in_block(S, g)) continue;
-    if (S.n_cr && cr_at(S, g) >= 0) {  // a creation face: its adjoint goes to the event (thread 0, below)
-      A.CL0[o + g] = A.CL1[o + g] = A.CR0[o + g] = A.CR1[o + g] = 0.0;
-      continue;
-    }
-    double l0 = A.LF0[o + g], l1 = A.LF1[o + g];
-    if (g > 0 && !in_block(S, g - 1)) {
-      const double c = dt / cell_upd(A.F0 + o, A.F1 + o, S, g - 1, A.pw[o + g - 1], dt).h1;
-      l0 -= c * A.lr[o + g - 1];
-      l1 -= c * A.lm[o + g - 1];
-    }
-    if (g < M && !in_block(S, g)) {
-      const double c = dt / cell_upd(A.F0 + o, A.F1 + o, S, g, A.pw[o + g], dt).h1;
-      l0 += c * A.lr[o + g];
-      l1 += c * A.lm[o + g];
-    }
-    double cl0 = 0.0, cl1 = 0.0, cr0 = 0.0, cr1 = 0.0;
-    if (g == 0 || g == M) {
-      const int i = (g == 0) ? 0 : M - 1;
-      Dual<2> rr = dvar<2>(A.pr[o + i], 0), mm = dvar<2>(A.pm[o + i], 1), f0, f1;
-      phys_flux_d<2>(c_fluid.ph[A.pph[o + i]], rr, mm, f0, f1);
-      const double a0 = l0 * f0.d[0] + l1 * f1.d[0], a1 = l0 * f0.d[1] + l1 * f1.d[1];
-      if (g == 0) {
-        cr0 = a0;
-        cr1 = a1;
-      } else {
-        cl0 = a0;
-        cl1 = a1;
+      S.M = Mc;  // post-merge count
+      S.n_blk = R.n_blk;
+      for (int b = 0; b < R.n_blk; ++b) {
+        S.blo[b] = R.blo[b];
+        S.bhi[b] = R.bhi[b];
       }
+      S.bad = 0;
+    }
+    __syncwarp();
+    // (b) the post-merge list: the taped pre-step list with the recorded merges applied
+    cta_copy_d(A.pw + o, A.tp_w + to, Mn);
+    cta_copy_d(A.pr + o, A.tp_r + to, Mn);
+    cta_copy_d(A.pm + o, A.tp_m + to, Mn);
+    cta_copy_b(A.pph + o, A.tp_ph + to, Mn);
+    cta_copy_b(A.pfpb + o, A.tp_fpb + to, Mn + 1);
+    __syncwarp();
+    if (lane == 0) {
+      int Mc = Mn;
+      for (int q = 0; q < R.n_merge; ++q) {
+        const int a = R.mg_a[q], b = R.mg_b[q];
+        const double* v = R.mg_v[q];
+        double wm = v[0] + v[3];
+        A.pr[o + a] = (v[0] * v[1] + v[3] * v[4]) / wm;
+        A.pm[o + a] = (v[0] * v[2] + v[3] * v[5]) / wm;
+        A.pw[o + a] = wm;
+        list_erase(A.pw + o, A.pr + o, A.pm + o, A.pph + o, A.pfpb + o, nullptr, nullptr, nullptr, nullptr, Mc, b);
+        Mc--;
+      }
+      if (Mc != S.M) S.bad = 1;
+    }
+    __syncwarp();
+    if (S.bad) {
+      if (lane == 0) afail(I, IMEXDS_ERR_STATE, 2);
     } else {
-      Dual<4> rl = dvar<4>(A.pr[o + g - 1], 0), ml = dvar<4>(A.pm[o + g - 1], 1);
-      Dual<4> rr = dvar<4>(A.pr[o + g], 2), mr = dvar<4>(A.pm[o + g], 3), f0, f1;
-      hll_d<4>(c_fluid.ph[A.pph[o + g]], rl, ml, rr, mr, f0, f1);
-      cl0 = l0 * f0.d[0] + l1 * f1.d[0];
-      cl1 = l0 * f0.d[1] + l1 * f1.d[1];
-      cr0 = l0 * f0.d[2] + l1 * f1.d[2];
-      cr1 = l0 * f0.d[3] + l1 * f1.d[3];
+      const int M = S.M;
+      // (c) zero the accumulators; explicit fluxes at U^n (post-merge)
+      cta_zero(A.nw + o, M);
+      cta_zero(A.nr + o, M);
+      cta_zero(A.nm + o, M);
+      cta_zero(A.nx + o, M + 1);
+      cta_zero(A.LF0 + o, M + 1);
+      cta_zero(A.LF1 + o, M + 1);
+      for (int g = tid; g <= M; g += 32) {
+        if (face_in_block(S, g)) continue;
+        if (S.n_cr && cr_at(S, g) >= 0) continue;
+        double f0, f1;
+        if (g == 0)
+          phys_flux_fast(c_fluid.ph[A.pph[o]], A.pr[o], A.pm[o], f0, f1);
+        else if (g == M)
+          phys_flux_fast(c_fluid.ph[A.pph[o + M - 1]], A.pr[o + M - 1], A.pm[o + M - 1], f0, f1);
+        else
+          hll_fast(c_fluid.ph[A.pph[o + g]], A.pr[o + g - 1], A.pm[o + g - 1], A.pr[o + g], A.pm[o + g], f0, f1);
+        A.F0[o + g] = f0;
+        A.F1[o + g] = f1;
+      }
     }
-    A.CL0[o + g] = cl0;
-    A.CL1[o + g] = cl1;
-    A.CR0[o + g] = cr0;
-    A.CR1[o + g] = cr1;
-  }
-  double ldt_part = 0.0;
-  for (int i = tid; i < M; i += blockDim.x) {
-    if (in_block(S, i)) continue;
-    const double wi = A.pw[o + i], lr = A.lr[o + i], lm = A.lm[o + i];
-    const CellUpd c = cell_upd(A.F0 + o, A.F1 + o, S, i, wi, dt);
-    const double dF = (c.fr0 - c.fl0) * lr + (c.fr1 - c.fl1) * lm;
-    if (c.wl == 0.0 && c.wr == 0.0) {
-      A.nr[o + i] += lr;
-      A.nm[o + i] += lm;
-      A.nw[o + i] += A.lw[o + i] + dt * dF / (wi * wi);
-      ldt_part -= dF / wi;
-    } else {  // next to a creation face: the width moves with w1 / w2
-      const double r1 = (wi * A.pr[o + i] - dt * (c.fr0 - c.fl0)) / c.h1;
-      const double m1 = (wi * A.pm[o + i] - dt * (c.fr1 - c.fl1)) / c.h1;
-      const double sc = wi / c.h1, dw = c.wl - c.wr;
-      A.nr[o + i] += lr * sc;
-      A.nm[o + i] += lm * sc;
-      A.nw[o + i] += A.lw[o + i] + (lr * (A.pr[o + i] - r1) + lm * (A.pm[o + i] - m1)) / c.h1;
-      ldt_part += (-dF - (lr * r1 + lm * m1) * dw) / c.h1 + A.lw[o + i] * dw;
-    }
+    __syncwarp();
   }
   __syncthreads();
-  // (f) gather the face contributions into the cells (faces inside a block contribute nothing here)
-  for (int i = tid; i < M; i += blockDim.x) {
-    double a0 = 0.0, a1 = 0.0;
-    if (!face_in_block(S, i)) {
-      a0 += A.CR0[o + i];
-      a1 += A.CR1[o + i];
-    }
-    if (!face_in_block(S, i + 1)) {
-      a0 += A.CL0[o + i + 1];
-      a1 += A.CL1[o + i + 1];
-    }
-    A.nr[o + i] += a0;
-    A.nm[o + i] += a1;
-  }
-  double tot = cta_sum(S, ldt_part);
+  if (w == 0 && lane < G && SS[lane].act && !SS[lane].bad) serial_rev_blocks(A, A.I[base + lane], SS[lane]);
   __syncthreads();
-  // (g') creation faces^T (thread 0): the two cells beside each creation face see its per-side fluxes and
-  //      move its faces; the event's outputs go back to the adjacent states and tau through the implicit
-  //      function theorem on the creation system
-  if (tid == 0) {
-    for (int k = 0; k < S.n_cr; ++k) {
-      const int g = S.cr_g[k];
-      const double* e = S.cr_o[k];
-      double* L = lcr[k];
-      for (int side = 0; side < 2; ++side) {
-        const int i = g - 1 + side;
-        const double wi = A.pw[o + i], lr = A.lr[o + i], lm = A.lm[o + i], lw = A.lw[o + i];
-        const CellUpd c = cell_upd(A.F0 + o, A.F1 + o, S, i, wi, dt);
+  if (mine && !S.bad) {
+    AInst& I = A.I[base + w];
+    const StepRec& R = *S.rec;
+    const long long o = I.off;
+    const long long to = (long long)S.slot * A.stride + o;
+    const int Mn = A.tp_M[(long long)S.slot * A.n_inst + base + w];
+    const double dt = R.dt;
+    const int M = S.M;
+    // (e) explicit sweep^T: face adjoints from the explicit cells, then the face Jacobians at U^n
+    for (int g = tid; g <= M; g += 32) {
+      if (face_in_block(S, g)) continue;
+      if (S.n_cr && cr_at(S, g) >= 0) {  // a creation face: its adjoint goes to the event (thread 0, below)
+        A.CL0[o + g] = A.CL1[o + g] = A.CR0[o + g] = A.CR1[o + g] = 0.0;
+        continue;
+      }
+      double l0 = A.LF0[o + g], l1 = A.LF1[o + g];
+      if (g > 0 && !in_block(S, g - 1)) {
+        const double c = dt / cell_upd(A.F0 + o, A.F1 + o, S, g - 1, A.pw[o + g - 1], dt).h1;
+        l0 -= c * A.lr[o + g - 1];
+        l1 -= c * A.lm[o + g - 1];
+      }
+      if (g < M && !in_block(S, g)) {
+        const double c = dt / cell_upd(A.F0 + o, A.F1 + o, S, g, A.pw[o + g], dt).h1;
+        l0 += c * A.lr[o + g];
+        l1 += c * A.lm[o + g];
+      }
+      double cl0 = 0.0, cl1 = 0.0, cr0 = 0.0, cr1 = 0.0;
+      if (g == 0 || g == M) {
+        const int i = (g == 0) ? 0 : M - 1;
+        Dual<2> rr = dvar<2>(A.pr[o + i], 0), mm = dvar<2>(A.pm[o + i], 1), f0, f1;
+        phys_flux_d<2>(c_fluid.ph[A.pph[o + i]], rr, mm, f0, f1);
+        const double a0 = l0 * f0.d[0] + l1 * f1.d[0], a1 = l0 * f0.d[1] + l1 * f1.d[1];
+        if (g == 0) {
+          cr0 = a0;
+          cr1 = a1;
+        } else {
+          cl0 = a0;
+          cl1 = a1;
+        }
+      } else {
+        Dual<4> rl = dvar<4>(A.pr[o + g - 1], 0), ml = dvar<4>(A.pm[o + g - 1], 1);
+        Dual<4> rr = dvar<4>(A.pr[o + g], 2), mr = dvar<4>(A.pm[o + g], 3), f0, f1;
+        hll_d<4>(c_fluid.ph[A.pph[o + g]], rl, ml, rr, mr, f0, f1);
+        cl0 = l0 * f0.d[0] + l1 * f1.d[0];
+        cl1 = l0 * f0.d[1] + l1 * f1.d[1];
+        cr0 = l0 * f0.d[2] + l1 * f1.d[2];
+        cr1 = l0 * f0.d[3] + l1 * f1.d[3];
+      }
+      A.CL0[o + g] = cl0;
+      A.CL1[o + g] = cl1;
+      A.CR0[o + g] = cr0;
+      A.CR1[o + g] = cr1;
+    }
+    double ldt_part = 0.0;
+    for (int i = tid; i < M; i += 32) {
+      if (in_block(S, i)) continue;
+      const double wi = A.pw[o + i], lr = A.lr[o + i], lm = A.lm[o + i];
+      const CellUpd c = cell_upd(A.F0 + o, A.F1 + o, S, i, wi, dt);
+      const double dF = (c.fr0 - c.fl0) * lr + (c.fr1 - c.fl1) * lm;
+      if (c.wl == 0.0 && c.wr == 0.0) {
+        A.nr[o + i] += lr;
+        A.nm[o + i] += lm;
+        A.nw[o + i] += A.lw[o + i] + dt * dF / (wi * wi);
+        ldt_part -= dF / wi;
+      } else {  // next to a creation face: the width moves with w1 / w2
         const double r1 = (wi * A.pr[o + i] - dt * (c.fr0 - c.fl0)) / c.h1;
         const double m1 = (wi * A.pm[o + i] - dt * (c.fr1 - c.fl1)) / c.h1;
-        const double sgn = side ? 1.0 : -1.0;  // the flux enters the right face of cell g-1, the left of cell g
-        const double a0 = sgn * dt / c.h1 * lr, a1 = sgn * dt / c.h1 * lm;
-        const double zs = side ? e[1] : e[0];
-        L[side] += -a0 - a1 * e[2];  // (-z, -z u_C + p_C)
-        L[2] += -a1 * zs;
-        L[3] += a1;
-        L[5 + side] += -sgn * dt * (lw - (lr * r1 + lm * m1) / c.h1);  // h1 = w + (w_l - w_r) dt
+        const double sc = wi / c.h1, dw = c.wl - c.wr;
+        A.nr[o + i] += lr * sc;
+        A.nm[o + i] += lm * sc;
+        A.nw[o + i] += A.lw[o + i] + (lr * (A.pr[o + i] - r1) + lm * (A.pm[o + i] - m1)) / c.h1;
+        ldt_part += (-dF - (lr * r1 + lm * m1) * dw) / c.h1 + A.lw[o + i] * dw;
       }
-      Dual<5> rl = dvar<5>(A.pr[o + g - 1], 0), ml = dvar<5>(A.pm[o + g - 1], 1);
-      Dual<5> rr = dvar<5>(A.pr[o + g], 2), mr = dvar<5>(A.pm[o + g], 3), ta = dvar<5>(I.tau, 4);
-      Dual<5> out[7];
-      if (!creation_d<5>(c_fluid, S.cr_P[k], rl, ml, rr, mr, ta, R.cr_x[k], out)) {
-        afail(I, IMEXDS_ERR_STATE, 3);
-        break;
+    }
+    __syncwarp();
+    // (f) gather the face contributions into the cells (faces inside a block contribute nothing here)
+    for (int i = tid; i < M; i += 32) {
+      double a0 = 0.0, a1 = 0.0;
+      if (!face_in_block(S, i)) {
+        a0 += A.CR0[o + i];
+        a1 += A.CR1[o + i];
       }
-      double lt[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-      for (int q = 0; q < 7; ++q)
-        for (int kk = 0; kk < 5; ++kk) lt[kk] += L[q] * out[q].d[kk];
-      A.nr[o + g - 1] += lt[0];
-      A.nm[o + g - 1] += lt[1];
-      A.nr[o + g] += lt[2];
-      A.nm[o + g] += lt[3];
-      I.lam_tau += lt[4];
+      if (!face_in_block(S, i + 1)) {
+        a0 += A.CL0[o + i + 1];
+        a1 += A.CL1[o + i + 1];
+      }
+      A.nr[o + i] += a0;
+      A.nm[o + i] += a1;
     }
+    const double tot = warp_sum(ldt_part);
+    __syncwarp();
+    // (g') creation faces^T (thread 0): the two cells beside each creation face see its per-side fluxes and
+    //      move its faces; the event's outputs go back to the adjacent states and tau through the implicit
+    //      function theorem on the creation system
+    if (lane == 0) {
+      for (int k = 0; k < S.n_cr; ++k) {
+        const int g = S.cr_g[k];
+        const double* e = S.cr_o[k];
+        double* L = lcr[k];
+        for (int side = 0; side < 2; ++side) {
+          const int i = g - 1 + side;
+          const double wi = A.pw[o + i], lr = A.lr[o + i], lm = A.lm[o + i], lw = A.lw[o + i];
+          const CellUpd c = cell_upd(A.F0 + o, A.F1 + o, S, i, wi, dt);
+          const double r1 = (wi * A.pr[o + i] - dt * (c.fr0 - c.fl0)) / c.h1;
+          const double m1 = (wi * A.pm[o + i] - dt * (c.fr1 - c.fl1)) / c.h1;
+          const double sgn = side ? 1.0 : -1.0;  // the flux enters the right face of cell g-1, the left of cell g
+          const double a0 = sgn * dt / c.h1 * lr, a1 = sgn * dt / c.h1 * lm;
+          const double zs = side ? e[1] : e[0];
+          L[side] += -a0 - a1 * e[2];  // (-z, -z u_C + p_C)
+          L[2] += -a1 * zs;
+          L[3] += a1;
+          L[5 + side] += -sgn * dt * (lw - (lr * r1 + lm * m1) / c.h1);  // h1 = w + (w_l - w_r) dt
+        }
+        Dual<5> rl = dvar<5>(A.pr[o + g - 1], 0), ml = dvar<5>(A.pm[o + g - 1], 1);
+        Dual<5> rr = dvar<5>(A.pr[o + g], 2), mr = dvar<5>(A.pm[o + g], 3), ta = dvar<5>(I.tau, 4);
+        Dual<5> out[7];
+        if (!creation_d<5>(c_fluid, S.cr_P[k], rl, ml, rr, mr, ta, R.cr_x[k], out)) {
+          afail(I, IMEXDS_ERR_STATE, 3);
+          break;
+        }
+        double lt[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int q = 0; q < 7; ++q)
+          for (int kk = 0; kk < 5; ++kk) lt[kk] += L[q] * out[q].d[kk];
+        A.nr[o + g - 1] += lt[0];
+        A.nm[o + g - 1] += lt[1];
+        A.nr[o + g] += lt[2];
+        A.nm[o + g] += lt[3];
+        I.lam_tau += lt[4];
+      }
+    }
+    // (g) merges^T and (h) dt^T (thread 0)
+    if (lane == 0) {
+      double lam_dt = S.lam_dt + tot;
+      int Mc = M;
+      for (int q = R.n_merge - 1; q >= 0; --q) {
+        const int a = R.mg_a[q], b = R.mg_b[q];
+        const double* v = R.mg_v[q];
+        const double wm = v[0] + v[3];
+        const double rm = (v[0] * v[1] + v[3] * v[4]) / wm, mm = (v[0] * v[2] + v[3] * v[5]) / wm;
+        const double Lw = A.nw[o + a], Lr = A.nr[o + a], Lm = A.nm[o + a];
+        lam_open(A.nw + o, A.nr + o, A.nm + o, A.nx + o, Mc, b);
+        Mc++;
+        A.nx[o + b] = 0.0;
+        A.nr[o + a] = Lr * v[0] / wm;
+        A.nm[o + a] = Lm * v[0] / wm;
+        A.nw[o + a] = Lw + (Lr * (v[1] - rm) + Lm * (v[2] - mm)) / wm;
+        A.nr[o + b] = Lr * v[3] / wm;
+        A.nm[o + b] = Lm * v[3] / wm;
+        A.nw[o + b] = Lw + (Lr * (v[4] - rm) + Lm * (v[5] - mm)) / wm;
+      }
+      if (R.clipped) {
+        I.lam_t = -lam_dt;
+      } else {
+        lam_dt += I.lam_t;
+        const int k = R.kmax;
+        const double rk = A.tp_r[to + k], mk = A.tp_m[to + k];
+        const double S_ = fabs(mk / rk) + c_fluid.ph[A.tp_ph[to + k]].a;
+        const double lS = -lam_dt * dt / S_;
+        const double sg = (mk > 0.0) ? 1.0 : ((mk < 0.0) ? -1.0 : 0.0);
+        A.nm[o + k] += lS * sg / rk;
+        A.nr[o + k] += -lS * sg * mk / (rk * rk);
+      }
+      I.M = Mc;
+      if (Mc != Mn) afail(I, IMEXDS_ERR_STATE, 4);
+    }
+    __syncwarp();
+    // lambda^n <- accumulators
+    cta_copy_d(A.lw + o, A.nw + o, Mn);
+    cta_copy_d(A.lr + o, A.nr + o, Mn);
+    cta_copy_d(A.lm + o, A.nm + o, Mn);
+    cta_copy_d(A.lx + o, A.nx + o, Mn + 1);
   }
-  // (g) merges^T and (h) dt^T (thread 0)
-  if (tid == 0) {
-    lam_dt += tot;
-    int Mc = M;
-    for (int q = R.n_merge - 1; q >= 0; --q) {
-      const int a = R.mg_a[q], b = R.mg_b[q];
-      const double* v = R.mg_v[q];
-      const double wm = v[0] + v[3];
-      const double rm = (v[0] * v[1] + v[3] * v[4]) / wm, mm = (v[0] * v[2] + v[3] * v[5]) / wm;
-      const double Lw = A.nw[o + a], Lr = A.nr[o + a], Lm = A.nm[o + a];
-      lam_open(A.nw + o, A.nr + o, A.nm + o, A.nx + o, Mc, b);
-      Mc++;
-      A.nx[o + b] = 0.0;
-      A.nr[o + a] = Lr * v[0] / wm;
-      A.nm[o + a] = Lm * v[0] / wm;
-      A.nw[o + a] = Lw + (Lr * (v[1] - rm) + Lm * (v[2] - mm)) / wm;
-      A.nr[o + b] = Lr * v[3] / wm;
-      A.nm[o + b] = Lm * v[3] / wm;
-      A.nw[o + b] = Lw + (Lr * (v[4] - rm) + Lm * (v[5] - mm)) / wm;
-    }
-    if (R.clipped) {
-      I.lam_t = -lam_dt;
-    } else {
-      lam_dt += I.lam_t;
-      const int k = R.kmax;
-      const double rk = A.tp_r[to + k], mk = A.tp_m[to + k];
-      const double S_ = fabs(mk / rk) + c_fluid.ph[A.tp_ph[to + k]].a;
-      const double lS = -lam_dt * dt / S_;
-      const double sg = (mk > 0.0) ? 1.0 : ((mk < 0.0) ? -1.0 : 0.0);
-      A.nm[o + k] += lS * sg / rk;
-      A.nr[o + k] += -lS * sg * mk / (rk * rk);
-    }
-    I.M = Mc;
-    if (Mc != Mn) afail(I, IMEXDS_ERR_STATE, 4);
-  }
-  __syncthreads();
-  // lambda^n <- accumulators
-  cta_copy_d(A.lw + o, A.nw + o, Mn);
-  cta_copy_d(A.lr + o, A.nr + o, Mn);
-  cta_copy_d(A.lm + o, A.nm + o, Mn);
-  cta_copy_d(A.lx + o, A.nx + o, Mn + 1);
-  __syncthreads();
+  __syncwarp();
 }
 
 __device__ void save_list(const ADev& A, AInst& I, long long dst_off, double* w, double* r, double* m,
@@ -1375,101 +1417,154 @@ __device__ void load_list(const ADev& A, AInst& I, long long src_off, int M) {
   cta_copy_d(A.pwr + o, A.ck_pwr + src_off, M + 1);
 }
 
-// The whole adjoint of one instance: replay with checkpoints, then the segments in reverse.
-__global__ void __launch_bounds__(ATHREADS, 8) k_adjoint(ADev A) {
-  const int ii = blockIdx.x;
-  if (ii >= A.n_inst) return;
-  AInst& I = A.I[ii];
-  __shared__ SharedStep S;
-  __shared__ int s_go;
-  __shared__ double s_tend;
+// The whole adjoint of the CTA's instances, base + w for warp w < G (G = blockDim.x / 32): replay with
+// checkpoints, then the segments from last to first, recomputed (all but the last, taped during the replay) and
+// reversed. The instances step in lockstep; one that has finished its program, or failed, sits out.
+__global__ void __launch_bounds__(ATHREADS, 2) k_adjoint(ADev A) {
+  const int G = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int base = blockIdx.x * G, ii = base + w;
+  __shared__ SharedStep SS[AWARPS];
+  __shared__ int s_max[AWARPS];
+  SharedStep& S = SS[w];
+  const bool valid = ii < A.n_inst;
+  // CTA-wide maximum of a value that is uniform within each warp; every thread calls it
+  auto cta_max = [&](int v) -> int {
+    __syncthreads();
+    if (lane == 0) s_max[w] = v;
+    __syncthreads();
+    int m = s_max[0];
+    for (int q = 1; q < G; ++q) m = max(m, s_max[q]);
+    return m;
+  };
   // phase A: replay from the initial states, a checkpoint every k steps. The steps of the last segment (as the
   // forward run's step count places it) are taped on the way, so that segment needs no recompute; with k at
   // least the run's length the whole adjoint is one taped replay and one reverse sweep.
-  const int tape_from = (I.nexp > 0) ? ((I.nexp - 1) / A.k) * A.k : 0;
-  int taped = 0;
-  int n = 0;
+  int n = 0, taped = 0, tape_from = 0;
+  bool run = valid;
+  if (valid) {
+    const int ne = A.I[ii].nexp;
+    tape_from = (ne > 0) ? ((ne - 1) / A.k) * A.k : 0;
+  }
   for (;;) {
-    if (n % A.k == 0) {
+    if (run && n % A.k == 0) {
+      AInst& I = A.I[ii];
       const int c = n / A.k;
       if (c >= A.n_ck) {
-        if (threadIdx.x == 0) afail(I, IMEXDS_ERR_CAPACITY);
-        __syncthreads();
-        break;
+        if (lane == 0) afail(I, IMEXDS_ERR_CAPACITY);
+        run = false;
+      } else {
+        save_list(A, I, (long long)c * A.stride + I.off, A.ck_w, A.ck_r, A.ck_m, A.ck_ph, A.ck_fpb, A.ck_fj, A.ck_fx,
+                  A.ck_pwl, A.ck_pwr);
+        if (lane == 0) {
+          ACk& h = A.ck_h[(long long)c * A.n_inst + ii];
+          h.done = I.done;
+          h.M = I.M;
+          h.status = I.status;
+          h.pc = I.pc;
+          h.t = I.t;
+        }
       }
-      save_list(A, I, (long long)c * A.stride + I.off, A.ck_w, A.ck_r, A.ck_m, A.ck_ph, A.ck_fpb, A.ck_fj, A.ck_fx,
-                A.ck_pwl, A.ck_pwr);
-      if (threadIdx.x == 0) {
-        ACk& h = A.ck_h[(long long)c * A.n_inst + ii];
-        h.done = I.done;
-        h.M = I.M;
-        h.status = I.status;
-        h.pc = I.pc;
-        h.t = I.t;
-      }
+      __syncwarp();
     }
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
+      int go = 0;
       double te = -1.0;
-      s_go = prog_next(A, I, te) ? 1 : 0;
-      s_tend = te;
+      if (run) go = prog_next(A, A.I[ii], te) ? 1 : 0;
+      const bool tape = go && n >= tape_from && n - tape_from < A.k;
+      S.act = go;
+      S.t_end = te;
+      S.rec = tape ? A.rec + (long long)(n - tape_from) * A.n_inst + ii : nullptr;
+      S.slot = n - tape_from;
     }
-    __syncthreads();
-    if (!s_go) break;
-    const bool tape = n >= tape_from && n - tape_from < A.k;
-    fwd_step(A, I, S, s_tend, tape ? A.rec + (long long)(n - tape_from) * A.n_inst + ii : nullptr, n - tape_from);
-    if (tape) ++taped;
-    ++n;
+    __syncwarp();
+    run = S.act != 0;
+    if (!__syncthreads_or(run ? 1 : 0)) break;
+    fwd_step_grp(A, SS, base, G);
+    if (run) {
+      if (S.rec) ++taped;
+      ++n;
+    }
   }
-  __syncthreads();
-  if (threadIdx.x == 0) I.nsteps = n;
-  save_list(A, I, I.off, A.fin_w, A.fin_r, A.fin_m, A.fin_ph, nullptr, nullptr, nullptr, nullptr, nullptr);
-  if (threadIdx.x == 0) A.fin_M[ii] = I.M;
-  __syncthreads();
-  if (I.status) return;
-  if (I.M != I.M_seed) {
-    if (threadIdx.x == 0) afail(I, IMEXDS_ERR_STATE, 5);
-    return;
+  bool alive = false;
+  if (valid) {
+    AInst& I = A.I[ii];
+    if (lane == 0) I.nsteps = n;
+    save_list(A, I, I.off, A.fin_w, A.fin_r, A.fin_m, A.fin_ph, nullptr, nullptr, nullptr, nullptr, nullptr);
+    if (lane == 0) A.fin_M[ii] = I.M;
+    __syncwarp();
+    alive = I.status == 0;
+    if (alive && I.M != I.M_seed) {
+      if (lane == 0) afail(I, IMEXDS_ERR_STATE, 5);
+      alive = false;
+    }
+    __syncwarp();
   }
   // phase B: segments from last to first
-  const int n_seg = (n + A.k - 1) / A.k;
-  for (int sg = n_seg - 1; sg >= 0; --sg) {
-    const int first = sg * A.k, last = min(n, first + A.k) - 1;
-    const ACk& h = A.ck_h[(long long)sg * A.n_inst + ii];
-    const int Mlam = I.M;  // the adjoint list length (cells of the state after step last)
+  const int n_seg = alive ? (n + A.k - 1) / A.k : 0;
+  const int max_seg = cta_max(n_seg);
+  for (int sg = max_seg - 1; sg >= 0; --sg) {
+    const int first = sg * A.k;
+    const bool part = alive && sg < n_seg;
+    const int last = part ? min(n, first + A.k) - 1 : -1;
     // the last segment, taped whole during the replay, which left the list at the state after its last step
-    const bool taped_whole = sg == n_seg - 1 && first == tape_from && taped == last - first + 1;
-    __syncthreads();
-    if (!taped_whole) {
+    const bool taped_whole = part && sg == n_seg - 1 && first == tape_from && taped == last - first + 1;
+    bool rerun = part && !taped_whole;
+    const int Mlam = part ? A.I[ii].M : 0;  // the adjoint list length (cells of the state after step last)
+    if (rerun) {
+      AInst& I = A.I[ii];
+      const ACk& h = A.ck_h[(long long)sg * A.n_inst + ii];
       load_list(A, I, (long long)sg * A.stride + I.off, h.M);
-      if (threadIdx.x == 0) {
+      if (lane == 0) {
         I.M = h.M;
         I.t = h.t;
         I.pc = h.pc;
         I.done = h.done;
       }
+      __syncwarp();
+    }
+    const int last_rerun = cta_max(rerun ? last : -1);
+    for (int s = first; s <= last_rerun; ++s) {
+      const bool go = rerun && s <= last;
+      if (lane == 0) {
+        int ok = 0;
+        double te = -1.0;
+        if (go) {
+          ok = prog_next(A, A.I[ii], te) ? 1 : 0;
+          if (!ok) afail(A.I[ii], IMEXDS_ERR_STATE, 1);
+          S.rec = A.rec + (long long)(s - first) * A.n_inst + ii;
+          S.slot = s - first;
+        }
+        S.act = ok;
+        S.t_end = te;
+      }
+      __syncwarp();
+      if (go && !S.act) {  // the program ended early in a recomputed segment
+        alive = false;
+        rerun = false;
+      }
       __syncthreads();
-      for (int s = first; s <= last; ++s) {
-        if (threadIdx.x == 0) {
-          double te = -1.0;
-          s_go = prog_next(A, I, te) ? 1 : 0;
-          s_tend = te;
-        }
-        __syncthreads();
-        if (!s_go) {
-          if (threadIdx.x == 0) afail(I, IMEXDS_ERR_STATE, 1);
-          __syncthreads();
-          return;
-        }
-        fwd_step(A, I, S, s_tend, A.rec + (long long)(s - first) * A.n_inst + ii, s - first);
-        if (I.status) return;
+      fwd_step_grp(A, SS, base, G);
+      if (go && alive && A.I[ii].status) {
+        alive = false;
+        rerun = false;
       }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) I.M = Mlam;
-    __syncthreads();
-    for (int s = last; s >= first; --s) {
-      rev_step(A, I, S, s - first, A.rec[(long long)(s - first) * A.n_inst + ii]);
-      if (I.status) return;
+    const bool rpart = part && alive;
+    if (rpart && lane == 0) A.I[ii].M = Mlam;
+    __syncwarp();
+    const int last_rev = cta_max(rpart ? last : -1);
+    for (int s = last_rev; s >= first; --s) {
+      const bool go = rpart && alive && s <= last;
+      if (lane == 0) {
+        S.act = go ? 1 : 0;
+        if (go) {
+          S.rec = A.rec + (long long)(s - first) * A.n_inst + ii;
+          S.slot = s - first;
+        }
+      }
+      __syncthreads();
+      rev_step_grp(A, SS, base, G);
+      if (go && A.I[ii].status) alive = false;
     }
   }
 }

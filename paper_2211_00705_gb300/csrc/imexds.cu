@@ -21,7 +21,7 @@
 // k_sweep and k_dts read U^n only and write disjoint cells of U^{n+1}. Group schedule: k_group, one
 // resident CTA per group of instances for the whole call, runs the same device functions (warp 0 one
 // instance per lane: solves, plan, dual time, grid management; the other warps the sweep tiles).
-// Adjoint: k_adjoint (adjoint.cuh), one CTA per instance.
+// Adjoint: k_adjoint (adjoint.cuh), up to eight instances per CTA, one warp each.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -3521,7 +3521,12 @@ static imexds_status adjoint_launch(imexds_ctx* c, AdjRun& R, const double* dJ_d
   CK(cudaEventCreate(&R.e0));
   CK(cudaEventCreate(&R.e1));
   CK(cudaEventRecord(R.e0, sm));
-  k_adjoint<<<n, ATHREADS, 0, sm>>>(A);
+  // instances per CTA (one warp each): as many as give about two CTAs per SM, at most AWARPS
+  int dev = 0, n_sm = 1;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  const int G = std::max(1, std::min(AWARPS, (n + 2 * n_sm - 1) / (2 * n_sm)));
+  k_adjoint<<<(n + G - 1) / G, 32 * G, 0, sm>>>(A);
   CK(cudaGetLastError());
   CK(cudaEventRecord(R.e1, sm));
   // the host staging of the initial lists must outlive the copies
