@@ -36,11 +36,11 @@ SWEEP_FLOP_PER_CELL = 33
 FP64_PEAK_TFLOPS = 1.25   # GB300 dense FP64 (nominal; no FP64 figure in MEASURED_PEAKS.json)
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture each; profiles/) of the kernels as
 # committed, for the traffic entry of the roofline objects: the per-step sweep per lattice cell it updates (a
-# launch with every instance active: 198.4 MB for 4.48 M cells), the resident group kernel per explicit
-# cell-step of a whole run of this workload (dual time, 96 threads: 185.3 GB for 3.69e9; Newton, 256 threads:
-# 177.1 GB). Scaled by the cells or cell-steps of the launch being reported.
-SWEEP_TRAFFIC_BYTES_PER_CELL = 44.31
-GROUP_TRAFFIC_BYTES_PER_CELL_STEP = {0: 50.24, 1: 48.03}
+# launch with every instance active: 198.1 MB for 4.48 M cells), the resident group kernel per explicit
+# cell-step of a whole run of this workload (dual time, 96 threads: 185.8 GB for 3.69e9; Newton, 256 threads:
+# 175.9 GB). Scaled by the cells or cell-steps of the launch being reported.
+SWEEP_TRAFFIC_BYTES_PER_CELL = 44.25
+GROUP_TRAFFIC_BYTES_PER_CELL_STEP = {0: 50.38, 1: 47.70}
 
 
 def dist_env():
