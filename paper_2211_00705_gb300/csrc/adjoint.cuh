@@ -401,35 +401,34 @@ __device__ bool dts_block(const ADev& A, AInst& I, const SharedStep& S, int lo, 
       if (at_floor) break;
     }
   }
+  // Algorithm 2 Part 1 in the forward kernels' arithmetic (dts_simple, dts_zone_general), so that the replay
+  // takes the same stop decisions: the Sec. 4 test of a component, (1 + theta)|W^{l+1} - W^l| / (theta dt
+  // max(|W^l|, 1)) (x dt in the res dt mode) below tol, as |W^{l+1} - W^l| < lim max(|W^l|, 1)
+  double ith[AMAXB], lim[AMAXB];
+  {
+    const double dtr = (c_opts.res_mode == 1) ? 1.0 : dt;
+    for (int q = 0; q < nb; ++q) {
+      ith[q] = 1.0 / (1.0 + th[q]);
+      lim[q] = (tiny[q] ? c_opts.tol_k : c_opts.tol_nb) * th[q] * dtr * ith[q];
+    }
+  }
   for (int l = 0; !newton_solver && l < c_opts.l_max && !stop; ++l) {
     int e = fluxes();
     if (e) {
       afail(I, e == 1 ? IMEXDS_ERR_PB_NOCONV : IMEXDS_ERR_VANISH);
       return false;
     }
-    double res_nb = 0.0, res_k = 0.0;
-    double Nr[AMAXB], Nm[AMAXB];
+    stop = true;
     for (int q = 0; q < nb; ++q) {
-      double t = th[q];
-      double tr = Uw[q] / hl[q] * Ur[q] - dt / hl[q] * (F0[q + 1] - F0[q]);
-      double tm = Uw[q] / hl[q] * Um[q] - dt / hl[q] * (F1[q + 1] - F1[q]);
-      Nr[q] = (Wr[q] + t * tr) / (1.0 + t);
-      Nm[q] = (Wm[q] + t * tm) / (1.0 + t);
-      double dtau = t * dt;
-      double e0 = (1.0 + t) * fabs(Nr[q] - Wr[q]) / (dtau * fmax(fabs(Wr[q]), 1.0));
-      double e1 = (1.0 + t) * fabs(Nm[q] - Wm[q]) / (dtau * fmax(fabs(Wm[q]), 1.0));
-      double res = fmax(e0, e1);
-      if (c_opts.res_mode == 1) res *= dt;
-      if (tiny[q])
-        res_k = fmax(res_k, res);
-      else
-        res_nb = fmax(res_nb, res);
+      const double t = th[q], ih = rcp_nr(hl[q]);
+      const double tr = (Uw[q] * Ur[q] - dt * (F0[q + 1] - F0[q])) * ih;
+      const double tm = (Uw[q] * Um[q] - dt * (F1[q + 1] - F1[q])) * ih;
+      const double nr = (Wr[q] + t * tr) * ith[q];
+      const double nm = (Wm[q] + t * tm) * ith[q];
+      stop = stop && below_tol(nr - Wr[q], Wr[q], lim[q]) && below_tol(nm - Wm[q], Wm[q], lim[q]);
+      Wr[q] = nr;
+      Wm[q] = nm;
     }
-    for (int q = 0; q < nb; ++q) {
-      Wr[q] = Nr[q];
-      Wm[q] = Nm[q];
-    }
-    if (res_nb < c_opts.tol_nb && res_k < c_opts.tol_k) stop = true;
   }
   int e = fluxes();  // Part 2 at the last iterate
   if (e) {

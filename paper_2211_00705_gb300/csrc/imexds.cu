@@ -602,10 +602,16 @@ __device__ __noinline__ bool dts_general(const Dev& d, Zone& Z, Inst& I, int e0,
       Wr[q] = B.r[q];
       Wm[q] = B.m[q];
     }
+    // the Sec. 4 test of a component, |W^{l+1} - W^l| (1 + theta) / (theta dt max(|W^l|, 1)) (x dt in the
+    // res dt mode) below tol, as |W^{l+1} - W^l| < lim max(|W^l|, 1), lim = tol theta dt' / (1 + theta)
+    const double dtr = (c_opts.res_mode == 1) ? 1.0 : dt;
+    double ith[ZB], lim[ZB];
     for (int q = lo; q <= hi; ++q) {
       int e = q + e0;
       double hp = (e < 0 || e >= Z.nc) ? h : Z.hp[e];
       theta[q] = fmin(c_opts.theta_nb, hp / h);
+      ith[q] = 1.0 / (1.0 + theta[q]);
+      lim[q] = (((Z.tiny_mask >> (q + e0 + 1)) & 1u) ? c_opts.tol_k : c_opts.tol_nb) * theta[q] * dtr * ith[q];
     }
     bool stop = false, nonconv = false;
     double gl[ZB + 1], gr[ZB + 1];  // Newton starts per face: the zone's last solution, then the previous iterate
@@ -622,28 +628,19 @@ __device__ __noinline__ bool dts_general(const Dev& d, Zone& Z, Inst& I, int e0,
         set_status(I, nonconv ? IMEXDS_ERR_PB_NOCONV : IMEXDS_ERR_VANISH);
         return false;
       }
-      double res_nb = 0.0, res_k = 0.0;
+      stop = true;
       for (int q = lo; q <= hi; ++q) {
-        double th = theta[q];
-        double tr = B.w[q] / hl[q] * B.r[q] - dt / hl[q] * (F0[q + 1] - F0[q]);
-        double tm = B.w[q] / hl[q] * B.m[q] - dt / hl[q] * (F1[q + 1] - F1[q]);
-        Nr[q] = (Wr[q] + th * tr) / (1.0 + th);
-        Nm[q] = (Wm[q] + th * tm) / (1.0 + th);
-        double dtau = th * dt;
-        double e0r = (1.0 + th) * fabs(Nr[q] - Wr[q]) / (dtau * fmax(fabs(Wr[q]), 1.0));
-        double e1m = (1.0 + th) * fabs(Nm[q] - Wm[q]) / (dtau * fmax(fabs(Wm[q]), 1.0));
-        double res = fmax(e0r, e1m);
-        if (c_opts.res_mode == 1) res *= dt;
-        if ((Z.tiny_mask >> (q + e0 + 1)) & 1u)
-          res_k = fmax(res_k, res);
-        else
-          res_nb = fmax(res_nb, res);
+        const double th = theta[q], ih = rcp_nr(hl[q]);
+        const double tr = (B.w[q] * B.r[q] - dt * (F0[q + 1] - F0[q])) * ih;
+        const double tm = (B.w[q] * B.m[q] - dt * (F1[q + 1] - F1[q])) * ih;
+        Nr[q] = (Wr[q] + th * tr) * ith[q];
+        Nm[q] = (Wm[q] + th * tm) * ith[q];
+        stop = stop && below_tol(Nr[q] - Wr[q], Wr[q], lim[q]) && below_tol(Nm[q] - Wm[q], Wm[q], lim[q]);
       }
       for (int q = lo; q <= hi; ++q) {
         Wr[q] = Nr[q];
         Wm[q] = Nm[q];
       }
-      if (res_nb < c_opts.tol_nb && res_k < c_opts.tol_k) stop = true;
     }
     if (!stop) maxiter++;
     iters_sum += l;
@@ -849,7 +846,7 @@ __device__ void dts_simple(const Dev& d, int zi) {
   }
   constexpr int a = PBF - 1;               // boundary between cells a and a+1
   constexpr int b = (PBF == 1) ? 2 : 1;    // fixed interior face between cells b-1 and b
-  const double ih_fixed = 1.0 / Uw[PBF == 1 ? 2 : 0];  // the cell away from the boundary keeps its width
+  const double ih_fixed = rcp_nr(Uw[PBF == 1 ? 2 : 0]);  // the cell away from the boundary keeps its width
   double gl = Z.pwl[1], gr = Z.pwr[1];
   double W0[3] = {Ur[0], Ur[1], Ur[2]}, W1[3] = {Um[0], Um[1], Um[2]};
   long long newton = 0, solves = 0;
@@ -895,7 +892,7 @@ __device__ void dts_simple(const Dev& d, int zi) {
       set_status(I, IMEXDS_ERR_VANISH);
       return;
     }
-    const double iha = 1.0 / ha, ihb = 1.0 / hb;
+    const double iha = rcp_nr(ha), ihb = rcp_nr(hb);
     stop = true;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -905,8 +902,7 @@ __device__ void dts_simple(const Dev& d, int zi) {
       const double ih = (q == a) ? iha : ((q == a + 1) ? ihb : ih_fixed);
       const double n0 = (W0[q] + th[q] * ((hU0[q] - dt * (f0r - f0l)) * ih)) * ith[q];
       const double n1 = (W1[q] + th[q] * ((hU1[q] - dt * (f1r - f1l)) * ih)) * ith[q];
-      stop = stop && (fabs(n0 - W0[q]) < lim[q] * fmax(fabs(W0[q]), 1.0)) &&
-             (fabs(n1 - W1[q]) < lim[q] * fmax(fabs(W1[q]), 1.0));
+      stop = stop && below_tol(n0 - W0[q], W0[q], lim[q]) && below_tol(n1 - W1[q], W1[q], lim[q]);
       W0[q] = n0;
       W1[q] = n1;
     }
@@ -2320,6 +2316,7 @@ Phase make_phase(const imexds_eos& e, double p_sat) {
   P.ia2 = 1.0 / e.a2;
   P.ia = 1.0 / P.a;
   P.ln_rho_sat = std::log(P.rho_sat);
+  P.irho_sat = 1.0 / P.rho_sat;
   return P;
 }
 

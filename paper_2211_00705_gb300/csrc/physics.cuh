@@ -55,6 +55,14 @@ __device__ __forceinline__ bool finite_bits(double x) {
 // x != 0 (+0 and -0 are zero; true for NaN, as the FP64 comparison)
 __device__ __forceinline__ bool nonzero_bits(double x) { return (__double_as_longlong(x) << 1) != 0; }
 
+// |d| < lim * max(|w|, 1) for lim >= 0, the Sec. 4 stop test of one component, with the maximum and the
+// comparison decided on the bit patterns (non-negative doubles order as their bits); one FP64 multiply.
+__device__ __forceinline__ bool below_tol(double d, double w, double lim) {
+  const double aw = fabs(w);
+  const double m = (__double_as_longlong(aw) > 0x3FF0000000000000ll) ? aw : 1.0;
+  return __double_as_longlong(fabs(d)) < __double_as_longlong(lim * m);
+}
+
 constexpr int VAP = 0;
 constexpr int LIQ = 1;
 
@@ -63,7 +71,7 @@ struct Phase {
   double a2, a;   // squared sound speed, sound speed
   double p0, rho0;
   double rho_sat; // density at the saturation pressure (zero of g)
-  double ia2, ia, ln_rho_sat;  // 1/a2, 1/a, ln(rho_sat) (set on the host)
+  double ia2, ia, ln_rho_sat, irho_sat;  // 1/a2, 1/a, ln(rho_sat), 1/rho_sat (set on the host)
 };
 
 struct Fluid {
@@ -220,8 +228,8 @@ __device__ inline SideData side_data(const Phase& e, double rK) {
   s.E = &e;
   s.rK = rK;
   s.pK = pressure(e, rK);
-  s.invK = 1.0 / rK;
-  s.isat = 1.0 / e.rho_sat;
+  s.invK = rcp_nr(rK);
+  s.isat = e.irho_sat;
   s.CK = e.ln_rho_sat - fast_log(rK);  // ln(rho_sat / rho_K), independent of 1/rho_K
   s.ia2 = e.ia2;
   s.ia = e.ia;
@@ -237,7 +245,7 @@ struct SideEval {
 __device__ inline bool side_eval(const SideData& s, double p, SideEval& o) {
   const Phase& e = *s.E;
   double rs = e.kind == 0 ? p * s.ia2 : __fma_rn(p - e.p0, s.ia2, e.rho0);
-  double v = 1.0 / rs;
+  double v = rcp_nr(rs);
   double Ls = fast_log(rs * s.isat);
   o.p = p;
   o.v = v;
@@ -290,7 +298,7 @@ __device__ inline bool pbf_eval(const SideData& sl, const SideData& sr, bool lef
 __device__ inline int pbf_newton(const Fluid& F, const Opts& o, const SideData& sl, const SideData& sr, bool left_vap,
                                  double tau, double du, double imp, double& x0, double& x1, PBFast& S, int& iters) {
   if (!pbf_eval(sl, sr, left_vap, tau, du, x0, x1, S)) return 0;
-  const double iimp = 1.0 / imp;
+  const double iimp = rcp_nr(imp);
   // the Armijo test on squared norms: |G_t|^2 <= (1 - 1e-4 lam)^2 |G|^2
   double g0 = S.G0 * iimp;
   double nrm2 = __fma_rn(g0, g0, S.G1 * S.G1);
@@ -300,7 +308,7 @@ __device__ inline int pbf_newton(const Fluid& F, const Opts& o, const SideData& 
     ++it;
     double det = S.J00 * S.J11 - S.J01 * S.J10;
     if (!isfinite(det) || det == 0.0) break;
-    double idet = 1.0 / det;
+    double idet = rcp_nr(det);
     double d0 = -(S.J11 * S.G0 - S.J01 * S.G1) * idet;
     double d1 = -(-S.J10 * S.G0 + S.J00 * S.G1) * idet;
     {
@@ -379,7 +387,7 @@ __device__ inline PBOut pb_solve_core(const Fluid& F, const Opts& o, double tau,
   R.ok = 0;
   R.iters = 0;
   R.F0 = R.F1 = R.w = R.z = R.pl = R.pr = 0.0;
-  double ul = ml / rl, ur = mr / rr;
+  double ul = div_nr(ml, rl), ur = div_nr(mr, rr);
   const SideData sl = side_data(F.ph[phl], rl), sr = side_data(F.ph[phr], rr);
   const bool left_vap = (phl == VAP);
   const double imp = rl * F.ph[phl].a + rr * F.ph[phr].a, du = ur - ul;
