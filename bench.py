@@ -37,10 +37,10 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 dense FP64 (nominal; no FP64 figure in MEASURE
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture each; profiles/) of the kernels as
 # committed, for the traffic entry of the roofline objects: the per-step sweep per lattice cell it updates (a
 # launch with every instance active: 198.1 MB for 4.48 M cells), the resident group kernel per explicit
-# cell-step of a whole run of this workload (dual time, 96 threads: 185.8 GB for 3.69e9; Newton, 256 threads:
-# 175.9 GB). Scaled by the cells or cell-steps of the launch being reported.
+# cell-step of a whole run of this workload (dual time, 96 threads: 186.3 GB for 3.69e9; Newton, 256 threads:
+# 174.1 GB). Scaled by the cells or cell-steps of the launch being reported.
 SWEEP_TRAFFIC_BYTES_PER_CELL = 44.25
-GROUP_TRAFFIC_BYTES_PER_CELL_STEP = {0: 50.38, 1: 47.70}
+GROUP_TRAFFIC_BYTES_PER_CELL_STEP = {0: 50.53, 1: 47.21}
 
 
 def dist_env():

@@ -376,7 +376,7 @@ __device__ bool dts_block(const ADev& A, AInst& I, const SharedStep& S, int lo, 
       double Tr[AMAXB], Tm[AMAXB], ih[AMAXB];
       stop = true;
       for (int q = 0; q < nb; ++q) {
-        ih[q] = 1.0 / hl[q];
+        ih[q] = rcp_nr(hl[q]);
         Tr[q] = (Uw[q] * Ur[q] - dt * (F0[q + 1] - F0[q])) * ih[q];
         Tm[q] = (Uw[q] * Um[q] - dt * (F1[q + 1] - F1[q])) * ih[q];
         const double lim = (tiny[q] ? c_opts.tol_k : c_opts.tol_nb) * dtr;

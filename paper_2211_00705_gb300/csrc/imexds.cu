@@ -732,7 +732,7 @@ __device__ __noinline__ bool newton_general(const Dev& d, Zone& Z, Inst& I, int 
       if (fail) break;
       stop = true;
       for (int q = lo; q <= hi; ++q) {
-        ih[q] = 1.0 / hl[q];
+        ih[q] = rcp_nr(hl[q]);
         Tr[q] = (B.w[q] * B.r[q] - dt * (F0[q + 1] - F0[q])) * ih[q];
         Tm[q] = (B.w[q] * B.m[q] - dt * (F1[q + 1] - F1[q])) * ih[q];
         const double lim = (((Z.tiny_mask >> (q + e0 + 1)) & 1u) ? c_opts.tol_k : c_opts.tol_nb) * dtr;
@@ -1059,9 +1059,9 @@ __device__ __noinline__ void newton_simple(const Dev& d, int zi) {
   for (l = 0; l < c_opts.l_max; ++l) {
     fail = fluxes();
     if (fail) break;
-    ih[a] = 1.0 / ha;
-    ih[a + 1] = 1.0 / hb;
-    ih[(PBF == 1) ? 2 : 0] = 1.0 / Uw[(PBF == 1) ? 2 : 0];
+    ih[a] = rcp_nr(ha);
+    ih[a + 1] = rcp_nr(hb);
+    ih[(PBF == 1) ? 2 : 0] = rcp_nr(Uw[(PBF == 1) ? 2 : 0]);
     stop = true;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {

@@ -414,7 +414,7 @@ __device__ inline PBOut pb_solve_core(const Fluid& F, const Opts& o, double tau,
   gl = x0;
   gr = x1;
   if (JAC) {
-    const double irl = 1.0 / rl, irr = 1.0 / rr;
+    const double irl = rcp_nr(rl), irr = rcp_nr(rr);
     const double fKl = dwave_drhoK(F.ph[phl], sl, x0, S.L.v, S.L.f);
     const double fKr = dwave_drhoK(F.ph[phr], sr, x1, S.R.v, S.R.f);
     // dG_2 / d(rho_l, m_l, rho_r, m_r): f_l(p_l; rho_l) + f_r(p_r; rho_r) + z [[v]] + u_r - u_l
@@ -424,7 +424,7 @@ __device__ inline PBOut pb_solve_core(const Fluid& F, const Opts& o, double tau,
       R.ok = 0;
       return R;
     }
-    const double idet = 1.0 / det;
+    const double idet = rcp_nr(det);
     const double cl = S.J01 * idet, cr = -S.J00 * idet;  // dp_l = cl g2, dp_r = cr g2
     const double dul[4] = {-ul * irl, irl, 0.0, 0.0};
     const double dur[4] = {0.0, 0.0, -ur * irr, irr};
@@ -458,7 +458,7 @@ __device__ inline PBOut pb_solve_warm(const Fluid& F, const Opts& o, double tau,
 // Jacobian of the HLL flux of hll_pre / hll_fast (Davis speeds, the same branch and the same min/max choice)
 // with respect to (rho_l, m_l, rho_r, m_r); the face does not move (dw = 0).
 __device__ inline void hll_jac(const Phase& e, double rl, double ml, double rr, double mr, FaceJac& J) {
-  const double irl = 1.0 / rl, irr = 1.0 / rr;
+  const double irl = rcp_nr(rl), irr = rcp_nr(rr);
   const double ul = ml * irl, ur = mr * irr;
   const double a2 = e.a2, a = e.a;
   const double dul[4] = {-ul * irl, irl, 0.0, 0.0};
@@ -489,7 +489,7 @@ __device__ inline void hll_jac(const Phase& e, double rl, double ml, double rr, 
     return;
   }
   // H = (S_R F_l - S_L F_r + S_L S_R (U_r - U_l)) / (S_R - S_L): dH = (dN - H (dS_R - dS_L)) / (S_R - S_L)
-  const double iw = 1.0 / (SR - SL);
+  const double iw = rcp_nr(SR - SL);
   const double H0 = (SR * ml - SL * mr + SL * SR * (rr - rl)) * iw;
   const double H1 = (SR * fl1 - SL * fr1 + SL * SR * (mr - ml)) * iw;
 #pragma unroll
@@ -530,7 +530,7 @@ __device__ inline bool solve_dense(double (&A)[N][N + 1]) {
       }
     }
     if (!nonzero_bits(A[c][c]) || !finite_bits(A[c][c])) return false;
-    const double ip = 1.0 / A[c][c];
+    const double ip = rcp_nr(A[c][c]);
 #pragma unroll
     for (int r = c + 1; r < N; ++r) {
       const double f = A[r][c] * ip;
@@ -572,7 +572,7 @@ __device__ inline bool solve_band(double (*A)[BAND_W], double* b, int n) {
       b[c] = b[p];
       b[p] = t;
     }
-    const double ip = 1.0 / A[c][3];
+    const double ip = rcp_nr(A[c][3]);
     for (int r = c + 1; r <= rmax; ++r) {
       const double f = A[r][c - r + 3] * ip;
       for (int j = c + 1; j <= jmax; ++j) A[r][j - r + 3] = __fma_rn(-f, A[c][j - c + 3], A[r][j - r + 3]);
@@ -782,8 +782,8 @@ constexpr double kNewtonStallBelow = 1e-10;
 __device__ inline double newton_corr(int nb, const double* W0, const double* W1, const double* d0, const double* d1) {
   double c = 0.0;
   for (int q = 0; q < nb; ++q) {
-    c = fmax(c, fabs(d0[q]) / fmax(fabs(W0[q]), 1.0));
-    c = fmax(c, fabs(d1[q]) / fmax(fabs(W1[q]), 1.0));
+    c = fmax(c, fabs(d0[q]) * rcp_nr(fmax(fabs(W0[q]), 1.0)));
+    c = fmax(c, fabs(d1[q]) * rcp_nr(fmax(fabs(W1[q]), 1.0)));
   }
   return c;
 }

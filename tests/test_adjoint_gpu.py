@@ -90,6 +90,60 @@ def test_adjoint_matches_oracle_tangent(program):
         assert np.max(err) <= TOL_TANGENT, (q, got, ref[q])
 
 
+def test_adjoint_through_the_split_of_a_cell_between_two_boundaries():
+    """Split of a cell between two phase boundaries (Sec. 3.4: cut at the lattice face nearest its midpoint): a
+    vapour cell of 2.4h between boundaries at 7.1h and 9.5h, perturbed states, split in the first of 3 steps.
+    Random seeds on the final densities, momenta and widths; the adjoint's directional derivatives (tau,
+    density and momentum fields, each boundary position on its own) against the oracle's forward-mode
+    derivative of the same run."""
+    from paper_2211_00705_gb300.imexds import Imexds
+    N = 20
+    h = 1.0 / N
+    fl = I.workload_fluid()
+    rv = fl.p_sat / fl.a2_vap
+    widths = np.array([h] * 7 + [0.1 * h, 2.4 * h, 0.5 * h] + [h] * 10)
+    phase = np.array([1] * 8 + [0] + [1] * 11, np.uint8)
+    rng = np.random.default_rng(4)
+    M = len(widths)
+    rho = np.where(phase == 1, fl.rho0_liq * (1 + 1e-4 * rng.uniform(-1, 1, M)), rv * (1 + 1e-2 * rng.uniform(-1, 1, M)))
+    m = rho * rng.uniform(-2, 2, M)
+    b = I.Batch(n_lattice=np.array([N], np.int32), x_left=np.zeros(1), x_right=np.ones(1),
+                tau=np.array([I.tau_paper()]), cell_offsets=np.array([0, M], np.int32), widths=widths, rho=rho, m=m,
+                phase=phase, fluid=fl, options=I.scaled_options(tol_nb=3e-13, tol_k=3e-11), t_end=0.0, n_steps=3,
+                name="vapour cell between two boundaries")
+    ctx = Imexds.from_batch(b)
+    ctx.set_adjoint_checkpoint(2)
+    ctx.step(3)
+    s, st = ctx.get_states(), ctx.stats()
+    assert s["status"][0] == 0 and st["splits"][0] == 1
+    n = int(s["offsets"][-1])
+    sr, sm, sw = rng.standard_normal(n), rng.standard_normal(n) * 1e-2, rng.standard_normal(n) * 1e3
+    g = ctx.adjoint(sr, sm, sw)
+    ctx.close()
+    assert (g["status"] == 0).all(), g["status"]
+    zero, z1 = np.zeros(M), np.zeros(1)
+    dirs = [{"tau": b.tau.copy(), "rho": zero, "m": zero, "widths": zero}]
+    for _ in range(2):
+        dirs.append({"tau": z1, "rho": rng.standard_normal(M) * rho, "m": zero, "widths": zero})
+        dirs.append({"tau": z1, "rho": zero, "m": rng.standard_normal(M) * np.maximum(np.abs(m), rho), "widths": zero})
+    for f in (7, 8):  # the boundaries at faces 8 and 9: cells f | f+1, moved by 1e-3 of the smaller width
+        dw = np.zeros(M)
+        d = 1e-3 * min(widths[f], widths[f + 1])
+        dw[f], dw[f + 1] = d, -d
+        dirs.append({"tau": z1, "rho": zero, "m": zero, "widths": dw})
+    so, d = P.Oracle(b).tangent([("step", 3)], seed_w=np.stack([x["widths"] for x in dirs]),
+                                 seed_rho=np.stack([x["rho"] for x in dirs]), seed_m=np.stack([x["m"] for x in dirs]),
+                                 seed_tau=np.stack([x["tau"] for x in dirs]))
+    assert int(so["offsets"][-1]) == n
+    np.testing.assert_array_equal(so["phase"], s["phase"])
+    for q, x in enumerate(dirs):
+        terms = np.concatenate([sr * d["rho"][q], sm * d["m"][q], sw * d["widths"][q]])
+        ref, scale = float(terms.sum()), float(np.abs(terms).sum())
+        got = float(grad_dot(b, g, x)[0])
+        print(q, got, ref, scale)
+        assert abs(got - ref) <= TOL_TANGENT * scale, (q, got, ref, scale)
+
+
 # central-difference steps (relative) and bars per parameter kind. The oracle's own central differences
 # against its own exact tangent (same code, same run) show the floor of the measurement on this loss:
 # momentum derivatives at step 1e-6 are off by up to 2e-4 (round-off of the final states, ~1e-16 rho,
