@@ -221,6 +221,13 @@ imexds_status imexds_step_uniform_noalloc(const imexds_fluid* fluid, double cfl,
  * the lattice velocity and the HLL weights) and CUDA's division on n host pairs; results in fast and ref. */
 imexds_status imexds_check_div(int32_t n, const double* a, const double* b, double* fast, double* ref);
 
+/* Diagnostic: the library's dual-time stop test of one component, |d| < lim max(|w|, 1) (Sec. 4's residual
+ * test with the tolerance folded into lim > 0), decided on IEEE bit patterns in integer instructions, and the
+ * same test in FP64 comparisons, on n host triples (d, w, lim); 0/1 results in fast and ref. The two agree
+ * for every non-NaN d and w and finite lim > 0. */
+imexds_status imexds_check_tol(int32_t n, const double* d, const double* w, const double* lim, uint8_t* fast,
+                               uint8_t* ref);
+
 /* Diagnostic: evaluate the library's table-driven logarithm (Tang's method, used in the boundary
  * solves) and CUDA's log on n host values x > 0; results in the host arrays fast and ref. */
 imexds_status imexds_check_log(int32_t n, const double* x, double* fast, double* ref);
@@ -261,7 +268,11 @@ imexds_status imexds_adjoint(imexds_ctx* ctx, const double* dJ_dw_T, const doubl
 imexds_status imexds_adjoint_device(imexds_ctx* ctx, const double* dJ_dw_T, const double* dJ_drho_T,
                                     const double* dJ_dm_T, double* dJ_dw0, double* dJ_drho0, double* dJ_dm0,
                                     double* dJ_dtau, int32_t* inst_status);
-/* Checkpoint interval k of the adjoint (default 64). */
+/* Checkpoint interval k of the adjoint (default 64). The adjoint replays the forward run, keeping a copy of the
+ * cell lists every k steps, and recomputes each k-step segment with a tape before reversing it; the last segment
+ * is taped during the replay. Device memory grows with k (per instance and taped step about 26 B per cell slot
+ * plus a 1.7 KB step record; per checkpoint about 54 B per slot); with k at least the run's step count the run
+ * is taped once and nothing is recomputed (1024 instances x 565 slots x 2000 steps: 35 GB). */
 imexds_status imexds_set_adjoint_checkpoint(imexds_ctx* ctx, int32_t every);
 /* The last imexds_adjoint: device time of its kernel (ms), the largest relative deviation of its
  * replayed final states from the forward run's (rho and m relative to max|rho|, widths relative to h),

@@ -308,9 +308,9 @@ __device__ bool prog_next(const ADev& A, AInst& I, double& t_end) {
   return true;
 }
 
-// Algorithm 2 on one block of the list (thread 0). U^n of the block cells is still in the list (the
-// sweep does not touch them); FL/FR are the explicit fluxes at faces lo and hi+1. Writes the last
-// iterate and converged boundary pressures to the step record (when rec != nullptr) and the Part 2
+// Algorithm 2 on one block of the list (one thread: the instance's lane of warp 0). U^n of the block cells is
+// still in the list (the sweep does not touch them); FL/FR are the explicit fluxes at faces lo and hi+1. Writes
+// the last iterate and converged boundary pressures to the step record (when rec != nullptr) and the Part 2
 // result to out_*.
 __device__ bool dts_block(const ADev& A, AInst& I, const SharedStep& S, int lo, int hi, const double* hp,
                           const int* tiny, double FL0, double FL1, double FR0, double FR1, StepRec* rec,
@@ -474,7 +474,7 @@ __device__ bool dts_block(const ADev& A, AInst& I, const SharedStep& S, int lo, 
 __device__ __noinline__ void serial_grid(const ADev& A, AInst& I, SharedStep& S) {
   const long long o = I.off;
   StepRec* rec = S.rec;
-  // (2) grid management: boundary solves at U^n, marks, merges (thread 0; the list is short-edited)
+  // (2) grid management: boundary solves at U^n, marks, merges (the list is short-edited)
   const double dt = S.dt;
   double wf[AMAXPB];
   int nmk = 0, mk[2 * AMAXPB];
@@ -968,9 +968,9 @@ __device__ bool solve_T(int n, double (*Aw)[2 * AMAXB], const double* b, double*
   return true;
 }
 
-// Adjoint of one block (thread 0): reads lambda of the outputs (lw, lr, lm, lx in post-merge numbering),
-// writes the accumulators of the block cells' U^n and widths, the face adjoints of F_left/F_right and
-// the boundary faces' positions, and returns the dt and tau contributions.
+// Adjoint of one block (one thread: the instance's lane of warp 0): reads lambda of the outputs (lw, lr, lm, lx
+// in post-merge numbering), writes the accumulators of the block cells' U^n and widths, the face adjoints of
+// F_left/F_right and the boundary faces' positions, and returns the dt and tau contributions.
 __device__ __noinline__ bool block_adjoint(const ADev& A, AInst& I, const StepRec& R, int lo, int hi, int cell0,
                                            int& pbf, double dt, double& lam_dt, double& lam_tau) {
   const long long o = I.off;
@@ -1226,7 +1226,7 @@ __device__ void rev_step_grp(const ADev& A, SharedStep* SS, int base, int G) {
     // (e) explicit sweep^T: face adjoints from the explicit cells, then the face Jacobians at U^n
     for (int g = tid; g <= M; g += 32) {
       if (face_in_block(S, g)) continue;
-      if (S.n_cr && cr_at(S, g) >= 0) {  // a creation face: its adjoint goes to the event (thread 0, below)
+      if (S.n_cr && cr_at(S, g) >= 0) {  // a creation face: its adjoint goes to the event (lane 0, below)
         A.CL0[o + g] = A.CL1[o + g] = A.CR0[o + g] = A.CR1[o + g] = 0.0;
         continue;
       }
@@ -1306,7 +1306,7 @@ __device__ void rev_step_grp(const ADev& A, SharedStep* SS, int base, int G) {
     }
     const double tot = warp_sum(ldt_part);
     __syncwarp();
-    // (g') creation faces^T (thread 0): the two cells beside each creation face see its per-side fluxes and
+    // (g') creation faces^T (lane 0): the two cells beside each creation face see its per-side fluxes and
     //      move its faces; the event's outputs go back to the adjacent states and tau through the implicit
     //      function theorem on the creation system
     if (lane == 0) {
@@ -1345,7 +1345,7 @@ __device__ void rev_step_grp(const ADev& A, SharedStep* SS, int base, int G) {
         I.lam_tau += lt[4];
       }
     }
-    // (g) merges^T and (h) dt^T (thread 0)
+    // (g) merges^T and (h) dt^T (lane 0)
     if (lane == 0) {
       double lam_dt = S.lam_dt + tot;
       int Mc = M;

@@ -3169,6 +3169,35 @@ imexds_status imexds_check_div(int32_t n, const double* a, const double* b, doub
   return IMEXDS_OK;
 }
 
+__global__ void k_check_tol(const double* d, const double* w, const double* lim, uint8_t* fast, uint8_t* ref,
+                            int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    fast[i] = below_tol(d[i], w[i], lim[i]) ? 1 : 0;
+    ref[i] = (fabs(d[i]) < lim[i] * fmax(fabs(w[i]), 1.0)) ? 1 : 0;
+  }
+}
+
+imexds_status imexds_check_tol(int32_t n, const double* d, const double* w, const double* lim, uint8_t* fast,
+                               uint8_t* ref) {
+  if (n <= 0 || !d || !w || !lim || !fast || !ref) return IMEXDS_ERR_ARG;
+  double* g = nullptr;
+  CK(cudaMalloc(&g, sizeof(double) * 3 * (size_t)n + 2 * (size_t)n));
+  uint8_t* gb = (uint8_t*)(g + 3 * (size_t)n);
+  cudaError_t e = cudaMemcpy(g, d, sizeof(double) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g + n, w, sizeof(double) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g + 2 * (size_t)n, lim, sizeof(double) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_check_tol<<<(n + 255) / 256, 256>>>(g, g + n, g + 2 * (size_t)n, gb, gb + n, n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(fast, gb, n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(ref, gb + n, n, cudaMemcpyDeviceToHost);
+  cudaFree(g);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return IMEXDS_OK;
+}
+
 imexds_status imexds_check_log(int32_t n, const double* x, double* fast, double* ref) {
   if (n <= 0 || !x || !fast || !ref) return IMEXDS_ERR_ARG;
   static LogTable host_tab = make_log_table();

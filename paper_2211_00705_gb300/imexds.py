@@ -21,8 +21,8 @@ EXPORTED = ["imexds_create", "imexds_set_states", "imexds_set_states_device", "i
             "imexds_status_string", "imexds_last_error_string", "imexds_reset", "imexds_set_kernel_timing",
             "imexds_get_kernel_times", "imexds_set_schedule", "imexds_check_log", "imexds_step_uniform_noalloc",
             "imexds_get_group_phase_cycles", "imexds_adjoint", "imexds_set_adjoint_checkpoint",
-            "imexds_adjoint_info", "imexds_adjoint_replay", "imexds_check_div", "imexds_get_states_device",
-            "imexds_adjoint_device"]
+            "imexds_adjoint_info", "imexds_adjoint_replay", "imexds_check_div", "imexds_check_tol",
+            "imexds_get_states_device", "imexds_adjoint_device"]
 
 
 class ImexdsError(RuntimeError):
@@ -79,6 +79,7 @@ def load():
         L.imexds_get_group_phase_cycles.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.imexds_check_log.argtypes = [C.c_int32, dp, dp, dp]
         L.imexds_check_div.argtypes = [C.c_int32, dp, dp, dp, dp]
+        L.imexds_check_tol.argtypes = [C.c_int32, dp, dp, dp, C.POINTER(C.c_uint8), C.POINTER(C.c_uint8)]
         L.imexds_step_uniform_noalloc.argtypes = [C.POINTER(FluidS), C.c_double, C.c_int32, ip, dp, dp, vp, vp, vp,
                                                   vp, vp, vp, vp]
         L.imexds_adjoint.argtypes = [vp, dp, dp, dp, dp, dp, dp, dp, ip]
@@ -149,6 +150,17 @@ def check_div(a, b):
     fast = np.zeros_like(a)
     ref = np.zeros_like(a)
     _check(load().imexds_check_div(int(a.shape[0]), _dp(a), _dp(b), _dp(fast), _dp(ref)))
+    return fast, ref
+
+
+def check_tol(d, w, lim):
+    """The library's bit-pattern stop test |d| < lim max(|w|, 1) and the FP64 comparison (diagnostic)."""
+    d, w, lim = (np.ascontiguousarray(v, dtype=np.float64) for v in (d, w, lim))
+    fast = np.zeros(d.shape[0], dtype=np.uint8)
+    ref = np.zeros(d.shape[0], dtype=np.uint8)
+    u8 = C.POINTER(C.c_uint8)
+    _check(load().imexds_check_tol(int(d.shape[0]), _dp(d), _dp(w), _dp(lim), fast.ctypes.data_as(u8),
+                                   ref.ctypes.data_as(u8)))
     return fast, ref
 
 

@@ -51,3 +51,23 @@ def test_refined_reciprocal_against_division():
     b = np.ldexp(mant, rng.integers(-12, 40, mant.shape[0]))
     fast, ref = check_div(np.ones_like(b), b)
     assert np.max(np.abs(fast - ref) / np.spacing(np.abs(ref))) <= 1.0
+
+
+def test_bit_pattern_stop_test_against_the_fp64_comparison():
+    """The dual-time stop test |d| < lim max(|w|, 1), decided on bit patterns in integer instructions, gives
+    the FP64 comparison's answer: random magnitudes over 600 decades, either sign, the boundary values
+    (products rounded onto the limit, w = +-1, zeros of either sign, subnormals, infinities)."""
+    from paper_2211_00705_gb300.imexds import check_tol
+    rng = np.random.default_rng(11)
+    n = 1 << 20
+    w = rng.choice([-1.0, 1.0], n) * 10.0 ** rng.uniform(-300, 300, n)
+    lim = 10.0 ** rng.uniform(-300, 0, n)
+    m = np.maximum(np.abs(w), 1.0)
+    d = rng.choice([-1.0, 1.0], n) * lim * m * rng.choice([0.5, 1.0, 2.0, 1.0 - 2.0 ** -52, 1.0 + 2.0 ** -52], n)
+    tiny = np.array([0.0, -0.0, 5e-324, -5e-324, 2.2250738585072014e-308, np.inf, -np.inf, 1.0, -1.0])
+    dd = np.concatenate([d, np.repeat(tiny, len(tiny)), tiny, np.full(len(tiny), 3e-9)])
+    ww = np.concatenate([w, np.tile(tiny, len(tiny)), np.ones(len(tiny)), tiny])
+    ll = np.concatenate([lim, np.full(len(tiny) ** 2, 3e-13), np.full(len(tiny), 5e-324), np.full(len(tiny), 3e-9)])
+    fast, ref = check_tol(dd, ww, ll)
+    assert 0.2 < ref.mean() < 0.8  # both outcomes are well represented
+    np.testing.assert_array_equal(fast, ref)
