@@ -41,6 +41,12 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 dense FP64 (nominal; no FP64 figure in MEASURE
 # 174.1 GB). Scaled by the cells or cell-steps of the launch being reported.
 SWEEP_TRAFFIC_BYTES_PER_CELL = 44.25
 GROUP_TRAFFIC_BYTES_PER_CELL_STEP = {0: 50.53, 1: 47.21}
+# FP64 issue of the same captures (sm__inst_executed_pipe_fp64.sum, sm__pipe_fp64_cycles_active): the sweep issues
+# one warp instruction for the 30 cells of a tile; the group kernel's count is per explicit cell-step of the run
+# (sweep warps and block solves together).
+SWEEP_FP64_ISSUE = {"warp_instructions_per_30_cell_tile": 27.8, "fp64_pipe_busy_pct": 87.2}
+GROUP_FP64_ISSUE = {0: {"warp_instructions_per_cell_step": 2.19, "fp64_pipe_busy_pct": 55.0},
+                    1: {"warp_instructions_per_cell_step": 1.19, "fp64_pipe_busy_pct": 63.7}}
 
 
 def dist_env():
@@ -612,6 +618,9 @@ def measure_run(batch, steps, warmup, schedule, flush, barrier, sampler=None, ws
             "timed_in": "the timed region (library events around the resident kernel)" if group else
                         "one instrumented run after the timed region",
             "phase_cycles": phase}
+    if dominant == "k_group":
+        roof["fp64_issue"] = dict(GROUP_FP64_ISSUE[batch.options.block_solver],
+                                  source="ncu, one full launch (profiles/k_group_riemann4096.md)")
     return {"ctx": ctx, "tuned": tuned, "stats": st, "value": job_value(cs_run, steps, ws, t_max),
             "ms_per_step": 1e3 * t_max / steps, "cell_steps_run": cs_run, "launches": launches, "clocks": clocks,
             "block_iters_per_step": float(st["dts_iters"].sum() / max(1, st["steps"].sum())),
@@ -744,6 +753,7 @@ def main():
         "traffic_source": "ncu DRAM bytes of one launch with every instance active (profiles/k_sweep_riemann4096.md) "
                           "per lattice cell, times this run's average cells per launch",
         "algorithmic_bytes": 32.0 * sweep_cells / n_sw, "ms_per_launch": per_launch_s * 1e3,
+        "fp64_issue": dict(SWEEP_FP64_ISSUE, source="ncu, one launch at step 101 (profiles/k_sweep_riemann4096.md)"),
         "share": {k: round(v[0] / tot, 4) if tot else None for k, v in kt_steps.items()},
         "ms_per_launch_by_kernel": {k: (v[0] / v[1] if v[1] else None) for k, v in kt_steps.items()}}
 

@@ -121,7 +121,8 @@ imexds_status imexds_cell_counts(imexds_ctx* ctx, int32_t* counts);
  * entries). t and inst_status have n_inst entries; inst_status holds an imexds_status per instance: an
  * instance that met an error (IMEXDS_ERR_NONPHYSICAL, _PB_NOCONV, _VANISH, _CAPACITY) stopped in the
  * step where it occurred; its states are then not meaningful. IMEXDS_ERR_STATE before
- * imexds_set_states. */
+ * imexds_set_states. The lists are packed on the device into a staging buffer the context keeps (allocated on
+ * the first call, 25 B per cell) and copied once; pinned host arrays copy fastest. */
 imexds_status imexds_get_states(imexds_ctx* ctx, int32_t* cell_offsets, double* widths, double* rho,
                                 double* m, uint8_t* phase, double* t, int32_t* inst_status);
 

@@ -14,7 +14,8 @@ DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in sorted(os.listdir(os.pa
 # -split-compile=0: the optimizer works on the translation unit's functions in parallel on every host core (the
 # one translation unit holds ~30 kernels; serial compilation takes minutes)
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-              "-fmad=false", "-split-compile=0", "-Xcompiler", "-fPIC", "-shared", "-Xptxas", "-v"]
+              "-fmad=false", "-split-compile=0", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "-shared",
+              "-Xptxas", "-v"]
 
 
 def nvcc() -> str:

@@ -29,6 +29,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/imexds.h"
@@ -2268,6 +2269,9 @@ struct imexds_ctx {
   int *g_delta = nullptr, *g_zstart = nullptr, *g_counts = nullptr, *g_off = nullptr, *g_st = nullptr;
   unsigned char* g_cov = nullptr;
   double* g_t = nullptr;
+  // device staging of the packed cell lists of imexds_get_states (w, rho, m then phase), grown on demand
+  void* g_pack = nullptr;
+  size_t g_pack_cells = 0;
 };
 
 namespace {
@@ -2320,7 +2324,23 @@ Phase make_phase(const imexds_eos& e, double p_sat) {
   return P;
 }
 
+// The arrays that depend on the instance groups (rebuilt at every imexds_set_states), the timing counters and
+// the step graph.
+void free_groups(imexds_ctx* c) {
+  cudaFree(c->d_ginst);
+  cudaFree(c->d_grange);
+  cudaFree(c->d_phase);
+  c->d_ginst = nullptr;
+  c->d_grange = nullptr;
+  c->d_phase = nullptr;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  for (auto e : c->tev) cudaEventDestroy(e);
+  c->tev.clear();
+}
+
 void free_dev(imexds_ctx* c) {
+  free_groups(c);
   Dev& d = c->d;
   for (int k = 0; k < 2; ++k) {
     cudaFree(d.rho[k]);
@@ -2335,10 +2355,6 @@ void free_dev(imexds_ctx* c) {
   cudaFree(d.tiles);
   cudaFree(d.work);
   cudaFree(d.ctrl);
-  cudaFree(c->d_ginst);
-  cudaFree(c->d_grange);
-  cudaFree(c->d_phase);
-  c->d_phase = nullptr;
   cudaFree(c->g_delta);
   cudaFree(c->g_zstart);
   cudaFree(c->g_cov);
@@ -2349,8 +2365,9 @@ void free_dev(imexds_ctx* c) {
   c->g_delta = c->g_zstart = c->g_counts = c->g_off = c->g_st = nullptr;
   c->g_cov = nullptr;
   c->g_t = nullptr;
-  c->d_ginst = nullptr;
-  c->d_grange = nullptr;
+  cudaFree(c->g_pack);
+  c->g_pack = nullptr;
+  c->g_pack_cells = 0;
   d = Dev{};
   Dev& sv = c->saved;
   for (int k = 0; k < 2; ++k) {
@@ -2362,10 +2379,6 @@ void free_dev(imexds_ctx* c) {
   cudaFree(sv.zones);
   cudaFree(sv.inst);
   sv = Dev{};
-  if (c->graph) cudaGraphExecDestroy(c->graph);
-  c->graph = nullptr;
-  for (auto e : c->tev) cudaEventDestroy(e);
-  c->tev.clear();
 }
 
 // one time step: five kernel launches on the context stream
@@ -2702,7 +2715,8 @@ imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double*
   std::vector<unsigned char> hph(n_lat, 1);
   std::vector<std::vector<Zone>> inst_zones(n);
   std::vector<int> status(n, 0);
-  for (int i = 0; i < n; ++i) {
+  // instances are parsed independently (each writes its own lattice range and zone list), on the host's cores
+  auto parse = [&](int i) -> imexds_status {
     const int a = off[i], b = off[i + 1], M = b - a, N = c->N[i];
     const double xL = c->xL[i], h = (c->xR[i] - c->xL[i]) / (double)N;
     if (M < 1) return IMEXDS_ERR_ARG;
@@ -2795,6 +2809,22 @@ imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double*
     // lattice phase under zones: the phase of the zone cell covering it (kept for released cells)
     for (auto& Z : inst_zones[i])
       for (int j = Z.A; j < Z.B; ++j) hph[lat_off[i] + j] = (unsigned char)Z.ph[0];
+    return IMEXDS_OK;
+  };
+  {
+    for (int i = 0; i < n; ++i)
+      if (off[i + 1] - off[i] < 1) return IMEXDS_ERR_ARG;
+    std::vector<imexds_status> perr(n, IMEXDS_OK);
+    const int nth = std::max(1, std::min({(int)std::thread::hardware_concurrency(), 16, n}));
+    auto work = [&](int t) {
+      for (int i = t; i < n; i += nth) perr[i] = parse(i);
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nth; ++t) pool.emplace_back(work, t);
+    work(0);
+    for (auto& th : pool) th.join();
+    for (int i = 0; i < n; ++i)  // the first failing instance decides, as a sequential parse would
+      if (perr[i] != IMEXDS_OK) return perr[i];
   }
   std::vector<int> zone_off(n + 1, 0), zone_cap(n, 0);
   for (int i = 0; i < n; ++i) {
@@ -2829,53 +2859,62 @@ imexds_status imexds_set_states(imexds_ctx* c, const int32_t* off, const double*
   std::vector<int2> tiles;
   for (int i = 0; i < n; ++i)
     for (int j0 = 0; j0 < c->N[i]; j0 += TILE) tiles.push_back(make_int2(i, j0));
-  free_dev(c);
+  // the lattice is fixed by the context (n_lat), the zone slots by the boundaries per instance: a call with the
+  // layout of the loaded states keeps every device buffer and only uploads the states
+  const bool reuse = c->loaded && c->n_lat == n_lat && c->n_zone_slots == n_zone && c->n_tiles == (int)tiles.size();
+  if (reuse)
+    free_groups(c);
+  else
+    free_dev(c);
   Dev& d = c->d;
-  for (int k = 0; k < 2; ++k) {
-    CK(cudaMalloc(&d.rho[k], sizeof(double) * n_lat));
-    CK(cudaMalloc(&d.m[k], sizeof(double) * n_lat));
-    CK(cudaMalloc(&d.u[k], sizeof(double) * n_lat));
-    CK(cudaMemcpyAsync(d.rho[k], hr.data(), sizeof(double) * n_lat, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(d.m[k], hm.data(), sizeof(double) * n_lat, cudaMemcpyHostToDevice, c->stream));
-    k_init_u<<<(n_lat + 255) / 256, 256, 0, c->stream>>>(d.rho[k], d.m[k], d.u[k], n_lat);
-    CK(cudaGetLastError());
+  Dev& sv = c->saved;
+  if (!reuse) {
+    for (int k = 0; k < 2; ++k) {
+      CK(cudaMalloc(&d.rho[k], sizeof(double) * n_lat));
+      CK(cudaMalloc(&d.m[k], sizeof(double) * n_lat));
+      CK(cudaMalloc(&d.u[k], sizeof(double) * n_lat));
+      CK(cudaMalloc(&sv.rho[k], sizeof(double) * n_lat));
+      CK(cudaMalloc(&sv.m[k], sizeof(double) * n_lat));
+      CK(cudaMalloc(&sv.u[k], sizeof(double) * n_lat));
+    }
+    CK(cudaMalloc(&d.phase, n_lat));
+    CK(cudaMalloc(&d.own, sizeof(int) * n_lat));
+    CK(cudaMalloc(&d.zones, sizeof(Zone) * std::max(1, n_zone)));
+    CK(cudaMalloc(&d.inst, sizeof(Inst) * n));
+    CK(cudaMalloc(&d.ev, sizeof(Event) * EV_CAP * n));
+    CK(cudaMalloc(&d.work, sizeof(int) * std::max(1, n_zone)));
+    CK(cudaMalloc(&d.tiles, sizeof(int2) * tiles.size()));
+    CK(cudaMalloc(&d.ctrl, sizeof(Ctrl)));
+    CK(cudaMalloc(&sv.phase, n_lat));
+    CK(cudaMalloc(&sv.zones, sizeof(Zone) * std::max(1, n_zone)));
+    CK(cudaMalloc(&sv.inst, sizeof(Inst) * n));
+    CK(cudaMemcpyAsync(d.tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, c->stream));
   }
-  CK(cudaMalloc(&d.phase, n_lat));
+  // both parity buffers start from the same states: one upload, the second buffer filled on the device
+  CK(cudaMemcpyAsync(d.rho[0], hr.data(), sizeof(double) * n_lat, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(d.m[0], hm.data(), sizeof(double) * n_lat, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(d.rho[1], d.rho[0], sizeof(double) * n_lat, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(d.m[1], d.m[0], sizeof(double) * n_lat, cudaMemcpyDeviceToDevice, c->stream));
+  for (int k = 0; k < 2; ++k) k_init_u<<<(n_lat + 255) / 256, 256, 0, c->stream>>>(d.rho[k], d.m[k], d.u[k], n_lat);
+  CK(cudaGetLastError());
   CK(cudaMemcpyAsync(d.phase, hph.data(), n_lat, cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMalloc(&d.own, sizeof(int) * n_lat));
   CK(cudaMemsetAsync(d.own, 0xff, sizeof(int) * n_lat, c->stream));
-  CK(cudaMalloc(&d.zones, sizeof(Zone) * std::max(1, n_zone)));
   CK(cudaMemcpyAsync(d.zones, hz.data(), sizeof(Zone) * n_zone, cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMalloc(&d.inst, sizeof(Inst) * n));
   CK(cudaMemcpyAsync(d.inst, hi.data(), sizeof(Inst) * n, cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMalloc(&d.ev, sizeof(Event) * EV_CAP * n));
-  CK(cudaMalloc(&d.work, sizeof(int) * std::max(1, n_zone)));
-  CK(cudaMalloc(&d.tiles, sizeof(int2) * tiles.size()));
-  CK(cudaMemcpyAsync(d.tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMalloc(&d.ctrl, sizeof(Ctrl)));
   {
     static LogTable host_tab = make_log_table();
     CK(cudaMemcpyToSymbolAsync(g_logtab, &host_tab, sizeof(LogTable), 0, cudaMemcpyHostToDevice, c->stream));
   }
   CK(cudaMemcpyToSymbolAsync(c_fluid, &c->fluid, sizeof(Fluid), 0, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyToSymbolAsync(c_opts, &c->opts, sizeof(Opts), 0, cudaMemcpyHostToDevice, c->stream));
-  {
-    Dev& sv = c->saved;
-    for (int k = 0; k < 2; ++k) {
-      CK(cudaMalloc(&sv.rho[k], sizeof(double) * n_lat));
-      CK(cudaMalloc(&sv.m[k], sizeof(double) * n_lat));
-      CK(cudaMalloc(&sv.u[k], sizeof(double) * n_lat));
-      CK(cudaMemcpyAsync(sv.rho[k], d.rho[k], sizeof(double) * n_lat, cudaMemcpyDeviceToDevice, c->stream));
-      CK(cudaMemcpyAsync(sv.m[k], d.m[k], sizeof(double) * n_lat, cudaMemcpyDeviceToDevice, c->stream));
-      CK(cudaMemcpyAsync(sv.u[k], d.u[k], sizeof(double) * n_lat, cudaMemcpyDeviceToDevice, c->stream));
-    }
-    CK(cudaMalloc(&sv.phase, n_lat));
-    CK(cudaMemcpyAsync(sv.phase, d.phase, n_lat, cudaMemcpyDeviceToDevice, c->stream));
-    CK(cudaMalloc(&sv.zones, sizeof(Zone) * std::max(1, n_zone)));
-    CK(cudaMemcpyAsync(sv.zones, d.zones, sizeof(Zone) * n_zone, cudaMemcpyDeviceToDevice, c->stream));
-    CK(cudaMalloc(&sv.inst, sizeof(Inst) * n));
-    CK(cudaMemcpyAsync(sv.inst, d.inst, sizeof(Inst) * n, cudaMemcpyDeviceToDevice, c->stream));
+  for (int k = 0; k < 2; ++k) {
+    CK(cudaMemcpyAsync(sv.rho[k], d.rho[k], sizeof(double) * n_lat, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(sv.m[k], d.m[k], sizeof(double) * n_lat, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(sv.u[k], d.u[k], sizeof(double) * n_lat, cudaMemcpyDeviceToDevice, c->stream));
   }
+  CK(cudaMemcpyAsync(sv.phase, d.phase, n_lat, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(sv.zones, d.zones, sizeof(Zone) * n_zone, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(sv.inst, d.inst, sizeof(Inst) * n, cudaMemcpyDeviceToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   {
     // instance groups: instances sorted by size (largest first), at most GROUP_MAX per group and
@@ -3054,60 +3093,41 @@ imexds_status imexds_get_states_device(imexds_ctx* c, int32_t* off, double* w_d,
   return IMEXDS_OK;
 }
 
+// The cell lists gathered on the device (the kernels of imexds_get_states_device) into a packed staging buffer the
+// context keeps, then one copy per array into the caller's host memory: only the cells themselves cross the bus.
 imexds_status imexds_get_states(imexds_ctx* c, int32_t* off, double* widths, double* rho, double* m,
                                 uint8_t* phase, double* t, int32_t* inst_status) {
   if (!c || !off || !widths || !rho || !m || !phase || !t || !inst_status) return IMEXDS_ERR_ARG;
   if (!c->loaded) return IMEXDS_ERR_STATE;
   const int n = c->n_inst;
-  std::vector<double> r[2], mm[2];
-  for (int k = 0; k < 2; ++k) {
-    r[k].resize(c->n_lat);
-    mm[k].resize(c->n_lat);
-    CK(cudaMemcpyAsync(r[k].data(), c->d.rho[k], sizeof(double) * c->n_lat, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(mm[k].data(), c->d.m[k], sizeof(double) * c->n_lat, cudaMemcpyDeviceToHost, c->stream));
+  std::vector<int32_t> counts(n);
+  imexds_status st = imexds_cell_counts(c, counts.data());
+  if (st) return st;
+  off[0] = 0;
+  for (int i = 0; i < n; ++i) off[i + 1] = off[i] + counts[i];
+  const size_t tot = (size_t)off[n];
+  if (tot > c->g_pack_cells) {
+    cudaFree(c->g_pack);
+    c->g_pack = nullptr;
+    c->g_pack_cells = 0;
+    CK(cudaMalloc(&c->g_pack, tot * (3 * sizeof(double) + 1)));
+    c->g_pack_cells = tot;
   }
-  std::vector<unsigned char> ph(c->n_lat);
-  CK(cudaMemcpyAsync(ph.data(), c->d.phase, c->n_lat, cudaMemcpyDeviceToHost, c->stream));
-  std::vector<Zone> hz(c->n_zone_slots);
-  CK(cudaMemcpyAsync(hz.data(), c->d.zones, sizeof(Zone) * hz.size(), cudaMemcpyDeviceToHost, c->stream));
-  std::vector<Inst> hi(n);
-  CK(cudaMemcpyAsync(hi.data(), c->d.inst, sizeof(Inst) * n, cudaMemcpyDeviceToHost, c->stream));
+  double* gw = (double*)c->g_pack;
+  double* gr = gw + tot;
+  double* gm = gr + tot;
+  uint8_t* gph = (uint8_t*)(gm + tot);
+  st = gather_states(c, off, gw, gr, gm, gph);
+  if (st) return st;
+  k_inst_ts<<<(n + 127) / 128, 128, 0, c->stream>>>(c->d, n, c->g_t, c->g_st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(widths, gw, sizeof(double) * tot, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(rho, gr, sizeof(double) * tot, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(m, gm, sizeof(double) * tot, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(phase, gph, tot, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(t, c->g_t, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(inst_status, c->g_st, sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  int o = 0;
-  for (int i = 0; i < n; ++i) {
-    off[i] = o;
-    const Inst& I = hi[i];
-    const int p = I.parity;
-    std::vector<const Zone*> zs;
-    for (int z = 0; z < c->zone_cap[i]; ++z)
-      if (hz[c->zone_off[i] + z].alive) zs.push_back(&hz[c->zone_off[i] + z]);
-    std::sort(zs.begin(), zs.end(), [](const Zone* a, const Zone* b) { return a->A < b->A; });
-    size_t zk = 0;
-    for (int j = 0; j < c->N[i];) {
-      if (zk < zs.size() && zs[zk]->A == j) {
-        const Zone& Z = *zs[zk];
-        for (int q = 0; q < Z.nc; ++q, ++o) {
-          widths[o] = Z.w[q];
-          rho[o] = Z.r[q];
-          m[o] = Z.m[q];
-          phase[o] = (uint8_t)Z.ph[q];
-        }
-        j = Z.B;
-        ++zk;
-        continue;
-      }
-      int g = c->lat_off[i] + j;
-      widths[o] = I.h;
-      rho[o] = r[p][g];
-      m[o] = mm[p][g];
-      phase[o] = ph[g];
-      ++o;
-      ++j;
-    }
-    t[i] = I.t;
-    inst_status[i] = I.status;
-  }
-  off[n] = o;
   return IMEXDS_OK;
 }
 
