@@ -358,7 +358,7 @@ __device__ bool dts_block(const ADev& A, AInst& I, const SharedStep& S, int lo, 
     }
     for (int q = 0; q < nb; ++q) hl[q] = Uw[q] + (wc[q + 1] - wc[q]) * dt;
     for (int q = 0; q < nb; ++q)
-      if (!(hl[q] > 0.0)) return 2;
+      if (!pos_finite_bits(hl[q])) return 2;
     return 0;
   };
   bool stop = false;

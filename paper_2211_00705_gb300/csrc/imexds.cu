@@ -722,7 +722,7 @@ __device__ __noinline__ bool newton_general(const Dev& d, Zone& Z, Inst& I, int 
       }
       for (int q = lo; q <= hi; ++q) hl[q] = B.w[q] + (wc[q + 1] - wc[q]) * dt;
       for (int q = lo; q <= hi; ++q)
-        if (!(hl[q] > 0.0)) return 2;
+        if (!pos_finite_bits(hl[q])) return 2;
       return 0;
     };
     bool stop = false;
@@ -889,7 +889,7 @@ __device__ void dts_simple(const Dev& d, int zi) {
       break;
     }
     const double ha = Uw[a] + (wpb - 0.0) * dt, hb = Uw[a + 1] + (0.0 - wpb) * dt;
-    if (!(ha > 0.0) || !(hb > 0.0)) {
+    if (!pos_finite_bits(ha) || !pos_finite_bits(hb)) {
       set_status(I, IMEXDS_ERR_VANISH);
       return;
     }
@@ -913,7 +913,7 @@ __device__ void dts_simple(const Dev& d, int zi) {
     return;
   }
   const double ha = Uw[a] + (wpb - 0.0) * dt, hb = Uw[a + 1] + (0.0 - wpb) * dt;
-  if (!(ha > 0.0) || !(hb > 0.0)) {
+  if (!pos_finite_bits(ha) || !pos_finite_bits(hb)) {
     set_status(I, IMEXDS_ERR_VANISH);
     return;
   }
@@ -1050,7 +1050,7 @@ __device__ __noinline__ void newton_simple(const Dev& d, int zi) {
     wpb = R.w;
     ha = Uw[a] + (wpb - 0.0) * dt;
     hb = Uw[a + 1] + (0.0 - wpb) * dt;
-    if (!(ha > 0.0) || !(hb > 0.0)) return 2;
+    if (!pos_finite_bits(ha) || !pos_finite_bits(hb)) return 2;
     return 0;
   };
   bool stop = false;

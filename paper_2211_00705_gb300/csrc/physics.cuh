@@ -256,11 +256,12 @@ __device__ inline bool side_eval(const SideData& s, double p, SideEval& o) {
   double dp = p - s.pK;
   double q = dp * dvk;
   double dq = __fma_rn(dp * v * v, s.ia2, dvk);
-  double rq = rsqrt(fmax(q, 1e-300));
-  bool shock = (dp > 0.0) && (q > 0.0);
+  const bool qpos = pos_finite_bits(q);  // q > 0 (finite), decided on the bit pattern
+  double rq = rsqrt(qpos ? q : 1.0);
+  bool shock = pos_finite_bits(dp) && qpos;
   o.f = shock ? q * rq : e.a * (Ls + s.CK);
   o.df = shock ? 0.5 * dq * rq : v * s.ia;
-  return (rs > 0.0) && isfinite(p);
+  return pos_finite_bits(rs) && finite_bits(p);
 }
 
 struct PBFast {
@@ -289,7 +290,15 @@ __device__ inline bool pbf_eval(const SideData& sl, const SideData& sr, bool lef
   S.J01 = 1.0 + 2.0 * z * dzr * jv + z * z * R.dv;
   S.J10 = L.df + dzl * jv - z * L.dv;
   S.J11 = R.df + dzr * jv + z * R.dv;
-  return isfinite(S.G0) && isfinite(S.G1);
+  return finite_bits(S.G0) && finite_bits(S.G1);
+}
+
+// |d| <= 1e-8 max(|x|, p_sat) for finite x and p_sat > 0, the maximum and the comparison decided on bit patterns
+// (non-negative doubles order as their bits; false for a NaN d, as the FP64 comparison).
+__device__ __forceinline__ bool small_step(double d, double x, double p_sat) {
+  const double ax = fabs(x);
+  const double m = (__double_as_longlong(ax) > __double_as_longlong(p_sat)) ? ax : p_sat;
+  return __double_as_longlong(fabs(d)) <= __double_as_longlong(1e-8 * m);
 }
 
 // Newton-Armijo from (x0, x1); returns 1 on convergence with S evaluated at the returned point. One
@@ -307,7 +316,7 @@ __device__ inline int pbf_newton(const Fluid& F, const Opts& o, const SideData& 
   while (!conv && it < o.newton_itmax) {
     ++it;
     double det = S.J00 * S.J11 - S.J01 * S.J10;
-    if (!isfinite(det) || det == 0.0) break;
+    if (!finite_bits(det) || !nonzero_bits(det)) break;
     double idet = rcp_nr(det);
     double d0 = -(S.J11 * S.G0 - S.J01 * S.G1) * idet;
     double d1 = -(-S.J10 * S.G0 + S.J00 * S.G1) * idet;
@@ -317,7 +326,7 @@ __device__ inline int pbf_newton(const Fluid& F, const Opts& o, const SideData& 
       // and carry the recovery quantities (f, v, z) to it to first order (their second-order terms are
       // O(1e-16) relative as well).
       // (tested without dividing: |d| <= 1e-8 max(|x|, p_sat) for both unknowns)
-      if (fabs(d0) <= 1e-8 * fmax(fabs(x0), F.p_sat) && fabs(d1) <= 1e-8 * fmax(fabs(x1), F.p_sat)) {
+      if (small_step(d0, x0, F.p_sat) && small_step(d1, x1, F.p_sat)) {
         S.L.f = __fma_rn(S.L.df, d0, S.L.f);
         S.R.f = __fma_rn(S.R.df, d1, S.R.f);
         S.L.v = __fma_rn(S.L.dv, d0, S.L.v);
