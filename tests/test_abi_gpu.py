@@ -150,3 +150,38 @@ def test_forced_caps_report_through_status_and_counters():
     c.close()
     assert (s["status"] == 0).all() and (st["steps"] == 10).all()
     assert (st["maxiter"] >= st["steps"]).all() and (st["dts_iters"] == st["steps"]).all()
+
+
+def test_set_states_again_with_the_same_or_another_layout():
+    """imexds_set_states on a loaded context: with the layout of the loaded states it keeps the device buffers,
+    with another number of boundaries (other zone slots) it allocates anew. Either way the run that follows is
+    bit for bit the run of a fresh context on the same states."""
+    from paper_2211_00705_gb300.imexds import Imexds
+    b = I.workload(1, scale=16 / 4096)
+    N = b.n_lattice
+    h = (b.x_right - b.x_left) / N
+    off_u = np.concatenate([[0], np.cumsum(N)]).astype(np.int32)   # every instance one liquid phase, at rest
+    w_u = np.repeat(h, N)
+    uniform = dict(offsets=off_u, widths=w_u, rho=np.full(w_u.shape, 998.0), m=np.zeros(w_u.shape),
+                   phase=np.ones(w_u.shape, np.uint8))
+    riemann = dict(offsets=b.cell_offsets, widths=b.widths, rho=b.rho, m=b.m, phase=b.phase)
+
+    def run(ctx, st):
+        ctx.set_states(st["offsets"], st["widths"], st["rho"], st["m"], st["phase"])
+        ctx.step(50)
+        return ctx.get_states()
+
+    def fresh(st):  # a context whose only imexds_set_states is this one
+        ctx = Imexds(b.n_lattice, b.x_left, b.x_right, b.tau, b.fluid, b.options)
+        s = run(ctx, st)
+        ctx.close()
+        return s
+
+    ref_r, ref_u = fresh(riemann), fresh(uniform)
+    ctx = Imexds.from_batch(b)   # loaded with the same layout: the first call below keeps the buffers
+    got = [run(ctx, riemann), run(ctx, uniform), run(ctx, riemann), run(ctx, riemann)]
+    ctx.close()
+    for s, ref in zip(got, (ref_r, ref_u, ref_r, ref_r)):
+        for key in ("offsets", "widths", "rho", "m", "phase", "t", "status"):
+            np.testing.assert_array_equal(s[key], ref[key], err_msg=key)
+    assert (ref_r["status"] == 0).all() and (ref_u["status"] == 0).all()
