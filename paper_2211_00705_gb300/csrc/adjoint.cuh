@@ -421,10 +421,10 @@ __device__ bool dts_block(const ADev& A, AInst& I, const SharedStep& S, int lo, 
     stop = true;
     for (int q = 0; q < nb; ++q) {
       const double t = th[q], ih = rcp_nr(hl[q]);
-      const double tr = (Uw[q] * Ur[q] - dt * (F0[q + 1] - F0[q])) * ih;
-      const double tm = (Uw[q] * Um[q] - dt * (F1[q + 1] - F1[q])) * ih;
-      const double nr = (Wr[q] + t * tr) * ith[q];
-      const double nm = (Wm[q] + t * tm) * ith[q];
+      const double tr = __fma_rn(-dt, F0[q + 1] - F0[q], Uw[q] * Ur[q]) * ih;
+      const double tm = __fma_rn(-dt, F1[q + 1] - F1[q], Uw[q] * Um[q]) * ih;
+      const double nr = __fma_rn(t, tr, Wr[q]) * ith[q];
+      const double nm = __fma_rn(t, tm, Wm[q]) * ith[q];
       stop = stop && below_tol(nr - Wr[q], Wr[q], lim[q]) && below_tol(nm - Wm[q], Wm[q], lim[q]);
       Wr[q] = nr;
       Wm[q] = nm;

@@ -632,10 +632,10 @@ __device__ __noinline__ bool dts_general(const Dev& d, Zone& Z, Inst& I, int e0,
       stop = true;
       for (int q = lo; q <= hi; ++q) {
         const double th = theta[q], ih = rcp_nr(hl[q]);
-        const double tr = (B.w[q] * B.r[q] - dt * (F0[q + 1] - F0[q])) * ih;
-        const double tm = (B.w[q] * B.m[q] - dt * (F1[q + 1] - F1[q])) * ih;
-        Nr[q] = (Wr[q] + th * tr) * ith[q];
-        Nm[q] = (Wm[q] + th * tm) * ith[q];
+        const double tr = __fma_rn(-dt, F0[q + 1] - F0[q], B.w[q] * B.r[q]) * ih;
+        const double tm = __fma_rn(-dt, F1[q + 1] - F1[q], B.w[q] * B.m[q]) * ih;
+        Nr[q] = __fma_rn(th, tr, Wr[q]) * ith[q];
+        Nm[q] = __fma_rn(th, tm, Wm[q]) * ith[q];
         stop = stop && below_tol(Nr[q] - Wr[q], Wr[q], lim[q]) && below_tol(Nm[q] - Wm[q], Wm[q], lim[q]);
       }
       for (int q = lo; q <= hi; ++q) {
@@ -901,8 +901,8 @@ __device__ void dts_simple(const Dev& d, int zi) {
       face(q, f0l, f1l);
       face(q + 1, f0r, f1r);
       const double ih = (q == a) ? iha : ((q == a + 1) ? ihb : ih_fixed);
-      const double n0 = (W0[q] + th[q] * ((hU0[q] - dt * (f0r - f0l)) * ih)) * ith[q];
-      const double n1 = (W1[q] + th[q] * ((hU1[q] - dt * (f1r - f1l)) * ih)) * ith[q];
+      const double n0 = __fma_rn(th[q], __fma_rn(-dt, f0r - f0l, hU0[q]) * ih, W0[q]) * ith[q];
+      const double n1 = __fma_rn(th[q], __fma_rn(-dt, f1r - f1l, hU1[q]) * ih, W1[q]) * ith[q];
       stop = stop && below_tol(n0 - W0[q], W0[q], lim[q]) && below_tol(n1 - W1[q], W1[q], lim[q]);
       W0[q] = n0;
       W1[q] = n1;

@@ -250,12 +250,13 @@ __device__ inline bool side_eval(const SideData& s, double p, SideEval& o) {
   o.p = p;
   o.v = v;
   o.g = e.a2 * Ls;
-  o.dv = -v * v * s.ia2;
+  const double vv = v * v;
+  o.dv = -vv * s.ia2;
   // shock (p > p_K): f = sqrt(q), q = (p - p_K)(v_K - v); rarefaction: f = a ln(rho*/rho_K)
   double dvk = s.invK - v;
   double dp = p - s.pK;
   double q = dp * dvk;
-  double dq = __fma_rn(dp * v * v, s.ia2, dvk);
+  double dq = __fma_rn(dp * vv, s.ia2, dvk);
   const bool qpos = pos_finite_bits(q);  // q > 0 (finite), decided on the bit pattern
   double rq = rsqrt(qpos ? q : 1.0);
   bool shock = pos_finite_bits(dp) && qpos;
@@ -273,23 +274,28 @@ __device__ inline bool pbf_eval(const SideData& sl, const SideData& sr, bool lef
                                 double pl, double pr, PBFast& S) {
   if (!side_eval(sl, pl, S.L) || !side_eval(sr, pr, S.R)) return false;
   const SideEval &L = S.L, &R = S.R;
-  double pV = left_vap ? pl : pr;
-  double jp = pr - pl, jv = R.v - L.v, vs = L.v + R.v;
-  double Q = (R.g - L.g) - 0.5 * jp * vs;
-  double dQl = -L.v + 0.5 * vs - 0.5 * jp * L.dv;
-  double dQr = R.v - 0.5 * vs - 0.5 * jp * R.dv;
-  double dzl = tau * ((left_vap ? Q : 0.0) + pV * dQl);
-  double dzr = tau * ((left_vap ? 0.0 : Q) + pV * dQr);
-  double z = tau * pV * Q;
+  // G and its Jacobian with every product-sum fused (the same values to rounding; this is the dual-time
+  // chain's inner loop): Q = (g_R - g_L) - jp vs / 2, z = tau p_V Q, G0 = jp + z^2 jv, G1 = f_L + f_R + z jv + du
+  const double pV = left_vap ? pl : pr;
+  const double jp = pr - pl, jv = R.v - L.v, vs = L.v + R.v;
+  const double hj = 0.5 * jp, hv = 0.5 * vs;
+  const double Q = __fma_rn(-hj, vs, R.g - L.g);
+  const double dQl = __fma_rn(-hj, L.dv, hv - L.v);
+  const double dQr = __fma_rn(-hj, R.dv, R.v - hv);
+  const double tpV = tau * pV, tQ = tau * Q;
+  const double dzl = __fma_rn(tpV, dQl, left_vap ? tQ : 0.0);
+  const double dzr = __fma_rn(tpV, dQr, left_vap ? 0.0 : tQ);
+  const double z = tpV * Q;
+  const double zz = z * z, zj2 = 2.0 * z * jv;
   S.z = z;
   S.dzl = dzl;
   S.dzr = dzr;
-  S.G0 = jp + z * z * jv;
-  S.G1 = L.f + R.f + z * jv + du;
-  S.J00 = -1.0 + 2.0 * z * dzl * jv - z * z * L.dv;
-  S.J01 = 1.0 + 2.0 * z * dzr * jv + z * z * R.dv;
-  S.J10 = L.df + dzl * jv - z * L.dv;
-  S.J11 = R.df + dzr * jv + z * R.dv;
+  S.G0 = __fma_rn(zz, jv, jp);
+  S.G1 = __fma_rn(z, jv, (L.f + R.f) + du);
+  S.J00 = __fma_rn(-zz, L.dv, __fma_rn(zj2, dzl, -1.0));
+  S.J01 = __fma_rn(zz, R.dv, __fma_rn(zj2, dzr, 1.0));
+  S.J10 = __fma_rn(-z, L.dv, __fma_rn(dzl, jv, L.df));
+  S.J11 = __fma_rn(z, R.dv, __fma_rn(dzr, jv, R.df));
   return finite_bits(S.G0) && finite_bits(S.G1);
 }
 
@@ -315,11 +321,11 @@ __device__ inline int pbf_newton(const Fluid& F, const Opts& o, const SideData& 
   int it = 0;
   while (!conv && it < o.newton_itmax) {
     ++it;
-    double det = S.J00 * S.J11 - S.J01 * S.J10;
+    double det = __fma_rn(S.J00, S.J11, -(S.J01 * S.J10));
     if (!finite_bits(det) || !nonzero_bits(det)) break;
     double idet = rcp_nr(det);
-    double d0 = -(S.J11 * S.G0 - S.J01 * S.G1) * idet;
-    double d1 = -(-S.J10 * S.G0 + S.J00 * S.G1) * idet;
+    double d0 = -__fma_rn(S.J11, S.G0, -(S.J01 * S.G1)) * idet;
+    double d1 = -__fma_rn(S.J00, S.G1, -(S.J10 * S.G0)) * idet;
     {
       // A full Newton step below 1e-8 (relative) lands within O(1e-16) of the root (quadratic
       // convergence), the point the newton_tol test reaches: take it without the line-search evaluation
@@ -399,7 +405,7 @@ __device__ inline PBOut pb_solve_core(const Fluid& F, const Opts& o, double tau,
   double ul = div_nr(ml, rl), ur = div_nr(mr, rr);
   const SideData sl = side_data(F.ph[phl], rl), sr = side_data(F.ph[phr], rr);
   const bool left_vap = (phl == VAP);
-  const double imp = rl * F.ph[phl].a + rr * F.ph[phr].a, du = ur - ul;
+  const double imp = __fma_rn(rl, F.ph[phl].a, rr * F.ph[phr].a), du = ur - ul;
   PBFast S;
   double x0 = gl, x1 = gr;
   int ok = 0;
@@ -414,9 +420,9 @@ __device__ inline PBOut pb_solve_core(const Fluid& F, const Opts& o, double tau,
   double vV = left_vap ? S.L.v : S.R.v;
   double pV = left_vap ? x0 : x1;
   R.z = S.z;
-  R.w = uV + R.z * vV;
+  R.w = __fma_rn(R.z, vV, uV);
   R.F0 = -R.z;
-  R.F1 = -R.z * uV + pV;
+  R.F1 = __fma_rn(-R.z, uV, pV);
   R.pl = x0;
   R.pr = x1;
   R.ok = 1;
