@@ -356,7 +356,7 @@ __device__ bool dts_block(const ADev& A, AInst& I, const SharedStep& S, int lo, 
         wc[q] = 0.0;
       }
     }
-    for (int q = 0; q < nb; ++q) hl[q] = Uw[q] + (wc[q + 1] - wc[q]) * dt;
+    for (int q = 0; q < nb; ++q) hl[q] = __fma_rn(wc[q + 1] - wc[q], dt, Uw[q]);
     for (int q = 0; q < nb; ++q)
       if (!pos_finite_bits(hl[q])) return 2;
     return 0;
@@ -377,11 +377,10 @@ __device__ bool dts_block(const ADev& A, AInst& I, const SharedStep& S, int lo, 
       stop = true;
       for (int q = 0; q < nb; ++q) {
         ih[q] = rcp_nr(hl[q]);
-        Tr[q] = (Uw[q] * Ur[q] - dt * (F0[q + 1] - F0[q])) * ih[q];
-        Tm[q] = (Uw[q] * Um[q] - dt * (F1[q + 1] - F1[q])) * ih[q];
+        Tr[q] = __fma_rn(-dt, F0[q + 1] - F0[q], Uw[q] * Ur[q]) * ih[q];
+        Tm[q] = __fma_rn(-dt, F1[q + 1] - F1[q], Uw[q] * Um[q]) * ih[q];
         const double lim = (tiny[q] ? c_opts.tol_k : c_opts.tol_nb) * dtr;
-        stop = stop && (fabs(Tr[q] - Wr[q]) < lim * fmax(fabs(Wr[q]), 1.0)) &&
-               (fabs(Tm[q] - Wm[q]) < lim * fmax(fabs(Wm[q]), 1.0));
+        stop = stop && below_tol(Tr[q] - Wr[q], Wr[q], lim) && below_tol(Tm[q] - Wm[q], Wm[q], lim);
       }
       if (stop) break;
       for (int q = 1; q < nb; ++q)
@@ -1014,7 +1013,7 @@ __device__ __noinline__ bool block_adjoint(const ADev& A, AInst& I, const StepRe
     }
   }
   for (int q = 0; q < nb; ++q) {
-    hl[q] = Uw[q] + (wcv[q + 1] - wcv[q]) * dt;
+    hl[q] = __fma_rn(wcv[q + 1] - wcv[q], dt, Uw[q]);
     gv[q][0] = (Uw[q] * Ur[q] - dt * (Fv[q + 1][0] - Fv[q][0])) / hl[q];
     gv[q][1] = (Uw[q] * Um[q] - dt * (Fv[q + 1][1] - Fv[q][1])) / hl[q];
   }

@@ -582,9 +582,9 @@ __device__ inline bool block_fluxes(const BlockCtx& B, int lo, int hi, const dou
       wc[g] = 0.0;
     }
   }
-  for (int i = lo; i <= hi; ++i) hl[i] = B.w[i] + (wc[i + 1] - wc[i]) * dt;
+  for (int i = lo; i <= hi; ++i) hl[i] = __fma_rn(wc[i + 1] - wc[i], dt, B.w[i]);
   for (int i = lo; i <= hi; ++i)
-    if (!(hl[i] > 0.0)) return false;
+    if (!pos_finite_bits(hl[i])) return false;
   return true;
 }
 
@@ -720,7 +720,7 @@ __device__ __noinline__ bool newton_general(const Dev& d, Zone& Z, Inst& I, int 
           wc[g] = 0.0;
         }
       }
-      for (int q = lo; q <= hi; ++q) hl[q] = B.w[q] + (wc[q + 1] - wc[q]) * dt;
+      for (int q = lo; q <= hi; ++q) hl[q] = __fma_rn(wc[q + 1] - wc[q], dt, B.w[q]);
       for (int q = lo; q <= hi; ++q)
         if (!pos_finite_bits(hl[q])) return 2;
       return 0;
@@ -734,11 +734,10 @@ __device__ __noinline__ bool newton_general(const Dev& d, Zone& Z, Inst& I, int 
       stop = true;
       for (int q = lo; q <= hi; ++q) {
         ih[q] = rcp_nr(hl[q]);
-        Tr[q] = (B.w[q] * B.r[q] - dt * (F0[q + 1] - F0[q])) * ih[q];
-        Tm[q] = (B.w[q] * B.m[q] - dt * (F1[q + 1] - F1[q])) * ih[q];
+        Tr[q] = __fma_rn(-dt, F0[q + 1] - F0[q], B.w[q] * B.r[q]) * ih[q];
+        Tm[q] = __fma_rn(-dt, F1[q + 1] - F1[q], B.w[q] * B.m[q]) * ih[q];
         const double lim = (((Z.tiny_mask >> (q + e0 + 1)) & 1u) ? c_opts.tol_k : c_opts.tol_nb) * dtr;
-        stop = stop && (fabs(Tr[q] - Wr[q]) < lim * fmax(fabs(Wr[q]), 1.0)) &&
-               (fabs(Tm[q] - Wm[q]) < lim * fmax(fabs(Wm[q]), 1.0));
+        stop = stop && below_tol(Tr[q] - Wr[q], Wr[q], lim) && below_tol(Tm[q] - Wm[q], Wm[q], lim);
       }
       if (stop) break;
       for (int g = lo + 1; g <= hi; ++g)
@@ -888,7 +887,7 @@ __device__ void dts_simple(const Dev& d, int zi) {
       fail = true;
       break;
     }
-    const double ha = Uw[a] + (wpb - 0.0) * dt, hb = Uw[a + 1] + (0.0 - wpb) * dt;
+    const double ha = __fma_rn(wpb - 0.0, dt, Uw[a]), hb = __fma_rn(0.0 - wpb, dt, Uw[a + 1]);
     if (!pos_finite_bits(ha) || !pos_finite_bits(hb)) {
       set_status(I, IMEXDS_ERR_VANISH);
       return;
@@ -912,7 +911,7 @@ __device__ void dts_simple(const Dev& d, int zi) {
     set_status(I, IMEXDS_ERR_PB_NOCONV);
     return;
   }
-  const double ha = Uw[a] + (wpb - 0.0) * dt, hb = Uw[a + 1] + (0.0 - wpb) * dt;
+  const double ha = __fma_rn(wpb - 0.0, dt, Uw[a]), hb = __fma_rn(0.0 - wpb, dt, Uw[a + 1]);
   if (!pos_finite_bits(ha) || !pos_finite_bits(hb)) {
     set_status(I, IMEXDS_ERR_VANISH);
     return;
@@ -1048,8 +1047,8 @@ __device__ __noinline__ void newton_simple(const Dev& d, int zi) {
     Fp0 = R.F0;
     Fp1 = R.F1;
     wpb = R.w;
-    ha = Uw[a] + (wpb - 0.0) * dt;
-    hb = Uw[a + 1] + (0.0 - wpb) * dt;
+    ha = __fma_rn(wpb - 0.0, dt, Uw[a]);
+    hb = __fma_rn(0.0 - wpb, dt, Uw[a + 1]);
     if (!pos_finite_bits(ha) || !pos_finite_bits(hb)) return 2;
     return 0;
   };
@@ -1069,10 +1068,9 @@ __device__ __noinline__ void newton_simple(const Dev& d, int zi) {
       double f0l, f1l, f0r, f1r;
       face(q, f0l, f1l);
       face(q + 1, f0r, f1r);
-      T0[q] = (hU0[q] - dt * (f0r - f0l)) * ih[q];
-      T1[q] = (hU1[q] - dt * (f1r - f1l)) * ih[q];
-      stop = stop && (fabs(T0[q] - W0[q]) < lim[q] * fmax(fabs(W0[q]), 1.0)) &&
-             (fabs(T1[q] - W1[q]) < lim[q] * fmax(fabs(W1[q]), 1.0));
+      T0[q] = __fma_rn(-dt, f0r - f0l, hU0[q]) * ih[q];
+      T1[q] = __fma_rn(-dt, f1r - f1l, hU1[q]) * ih[q];
+      stop = stop && below_tol(T0[q] - W0[q], W0[q], lim[q]) && below_tol(T1[q] - W1[q], W1[q], lim[q]);
     }
     if (stop) break;
     // Newton step: (I - dT/dW) d = T - W

@@ -220,17 +220,18 @@ __device__ inline void pb_initial_guess(const Fluid& F, int phl, double rl, doub
 // the HLLC start of App. A as fallback.
 struct SideData {
   const Phase* E;
-  double rK, pK, invK, CK, ia2, ia, isat;
+  double rK, pK, invK, CK, aCK, ia2, ia, isat;
 };
 
 __device__ inline SideData side_data(const Phase& e, double rK) {
   SideData s;
   s.E = &e;
   s.rK = rK;
-  s.pK = pressure(e, rK);
+  s.pK = pressure_fma(e, rK);
   s.invK = rcp_nr(rK);
   s.isat = e.irho_sat;
   s.CK = e.ln_rho_sat - fast_log(rK);  // ln(rho_sat / rho_K), independent of 1/rho_K
+  s.aCK = e.a * s.CK;
   s.ia2 = e.ia2;
   s.ia = e.ia;
   return s;
@@ -260,7 +261,7 @@ __device__ inline bool side_eval(const SideData& s, double p, SideEval& o) {
   const bool qpos = pos_finite_bits(q);  // q > 0 (finite), decided on the bit pattern
   double rq = rsqrt(qpos ? q : 1.0);
   bool shock = pos_finite_bits(dp) && qpos;
-  o.f = shock ? q * rq : e.a * (Ls + s.CK);
+  o.f = shock ? q * rq : __fma_rn(e.a, Ls, s.aCK);
   o.df = shock ? 0.5 * dq * rq : v * s.ia;
   return pos_finite_bits(rs) && finite_bits(p);
 }
@@ -409,7 +410,7 @@ __device__ inline PBOut pb_solve_core(const Fluid& F, const Opts& o, double tau,
   PBFast S;
   double x0 = gl, x1 = gr;
   int ok = 0;
-  if (gl != 0.0 || gr != 0.0) ok = pbf_newton(F, o, sl, sr, left_vap, tau, du, imp, x0, x1, S, R.iters);
+  if (nonzero_bits(gl) || nonzero_bits(gr)) ok = pbf_newton(F, o, sl, sr, left_vap, tau, du, imp, x0, x1, S, R.iters);
   if (!ok) {
     pb_initial_guess(F, phl, rl, ul, phr, rr, ur, x0, x1);
     ok = pbf_newton(F, o, sl, sr, left_vap, tau, du, imp, x0, x1, S, R.iters);
@@ -434,8 +435,8 @@ __device__ inline PBOut pb_solve_core(const Fluid& F, const Opts& o, double tau,
     const double fKr = dwave_drhoK(F.ph[phr], sr, x1, S.R.v, S.R.f);
     // dG_2 / d(rho_l, m_l, rho_r, m_r): f_l(p_l; rho_l) + f_r(p_r; rho_r) + z [[v]] + u_r - u_l
     const double g2[4] = {fKl + ul * irl, -irl, fKr - ur * irr, irr};
-    const double det = S.J00 * S.J11 - S.J01 * S.J10;
-    if (!(det != 0.0) || !isfinite(det)) {
+    const double det = __fma_rn(S.J00, S.J11, -(S.J01 * S.J10));
+    if (!nonzero_bits(det) || !finite_bits(det)) {
       R.ok = 0;
       return R;
     }
@@ -446,20 +447,20 @@ __device__ inline PBOut pb_solve_core(const Fluid& F, const Opts& o, double tau,
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const double dpl = cl * g2[k], dpr = cr * g2[k];
-      const double dz = S.dzl * dpl + S.dzr * dpr;
+      const double dz = __fma_rn(S.dzl, dpl, S.dzr * dpr);
       double duV, dpV, dvV;
       if (left_vap) {
-        duV = dul[k] - (S.L.df * dpl + (k == 0 ? fKl : 0.0));
+        duV = dul[k] - __fma_rn(S.L.df, dpl, k == 0 ? fKl : 0.0);
         dpV = dpl;
         dvV = S.L.dv * dpl;
       } else {
-        duV = dur[k] + (S.R.df * dpr + (k == 2 ? fKr : 0.0));
+        duV = dur[k] + __fma_rn(S.R.df, dpr, k == 2 ? fKr : 0.0);
         dpV = dpr;
         dvV = S.R.dv * dpr;
       }
       J->dF0[k] = -dz;
-      J->dF1[k] = dpV - dz * uV - R.z * duV;
-      J->dw[k] = duV + dz * vV + R.z * dvV;
+      J->dF1[k] = __fma_rn(-R.z, duV, __fma_rn(-dz, uV, dpV));
+      J->dw[k] = __fma_rn(R.z, dvV, __fma_rn(dz, vV, duV));
     }
   }
   return R;
@@ -511,13 +512,17 @@ __device__ inline void hll_jac(const Phase& e, double rl, double ml, double rr, 
   for (int k = 0; k < 4; ++k) {
     const double dSL = lt ? dul[k] : dur[k];
     const double dSR = lt ? dur[k] : dul[k];
-    const double dss = dSL * SR + SL * dSR;
+    const double dss = __fma_rn(dSL, SR, SL * dSR);
     const double dU0 = (k == 2 ? 1.0 : 0.0) - (k == 0 ? 1.0 : 0.0);
     const double dU1 = (k == 3 ? 1.0 : 0.0) - (k == 1 ? 1.0 : 0.0);
-    const double dN0 = dSR * ml + SR * dFl0[k] - dSL * mr - SL * dFr0[k] + dss * (rr - rl) + SL * SR * dU0;
-    const double dN1 = dSR * fl1 + SR * dFl1[k] - dSL * fr1 - SL * dFr1[k] + dss * (mr - ml) + SL * SR * dU1;
-    J.dF0[k] = (dN0 - H0 * (dSR - dSL)) * iw;
-    J.dF1[k] = (dN1 - H1 * (dSR - dSL)) * iw;
+    // dN = dS_R F_l + S_R dF_l - dS_L F_r - S_L dF_r + d(S_L S_R) (U_r - U_l) + S_L S_R dU, fused
+    const double dN0 = __fma_rn(dSR, ml, __fma_rn(SR, dFl0[k], __fma_rn(-dSL, mr, __fma_rn(-SL, dFr0[k],
+                                          __fma_rn(dss, rr - rl, SL * SR * dU0)))));
+    const double dN1 = __fma_rn(dSR, fl1, __fma_rn(SR, dFl1[k], __fma_rn(-dSL, fr1, __fma_rn(-SL, dFr1[k],
+                                          __fma_rn(dss, mr - ml, SL * SR * dU1)))));
+    const double dsd = dSR - dSL;
+    J.dF0[k] = __fma_rn(-H0, dsd, dN0) * iw;
+    J.dF1[k] = __fma_rn(-H1, dsd, dN1) * iw;
   }
 }
 
@@ -834,13 +839,15 @@ __device__ inline bool newton_block_step(int nb, double dt, const double* ih, co
         if (q + 1 <= 2) {  // right face q+1: + coef (dF + T dw), columns of cells q, q+1
           const FaceJac& J = fj[q + 1];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) A[2 * q + c][2 * q + k] += coef * ((c ? J.dF1[k] : J.dF0[k]) + Tq * J.dw[k]);
+          for (int k = 0; k < 4; ++k)
+            A[2 * q + c][2 * q + k] = __fma_rn(coef, __fma_rn(Tq, J.dw[k], c ? J.dF1[k] : J.dF0[k]), A[2 * q + c][2 * q + k]);
         }
         if (q >= 1) {  // left face q: - coef (dF + T dw), columns of cells q-1, q
           const FaceJac& J = fj[q];
 #pragma unroll
           for (int k = 0; k < 4; ++k)
-            A[2 * q + c][2 * (q - 1) + k] -= coef * ((c ? J.dF1[k] : J.dF0[k]) + Tq * J.dw[k]);
+            A[2 * q + c][2 * (q - 1) + k] =
+                __fma_rn(-coef, __fma_rn(Tq, J.dw[k], c ? J.dF1[k] : J.dF0[k]), A[2 * q + c][2 * (q - 1) + k]);
         }
       }
     }
@@ -869,12 +876,15 @@ __device__ inline bool newton_block_step(int nb, double dt, const double* ih, co
       const double Tq = c ? T1[q] : T0[q];
       if (q + 1 < nb) {
         const FaceJac& J = fj[q + 1];
-        for (int k = 0; k < 4; ++k) A[row][2 * q + k - row + 3] += coef * ((c ? J.dF1[k] : J.dF0[k]) + Tq * J.dw[k]);
+        for (int k = 0; k < 4; ++k)
+          A[row][2 * q + k - row + 3] =
+              __fma_rn(coef, __fma_rn(Tq, J.dw[k], c ? J.dF1[k] : J.dF0[k]), A[row][2 * q + k - row + 3]);
       }
       if (q >= 1) {
         const FaceJac& J = fj[q];
         for (int k = 0; k < 4; ++k)
-          A[row][2 * (q - 1) + k - row + 3] -= coef * ((c ? J.dF1[k] : J.dF0[k]) + Tq * J.dw[k]);
+          A[row][2 * (q - 1) + k - row + 3] =
+              __fma_rn(-coef, __fma_rn(Tq, J.dw[k], c ? J.dF1[k] : J.dF0[k]), A[row][2 * (q - 1) + k - row + 3]);
       }
     }
   }
