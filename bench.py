@@ -37,16 +37,16 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 dense FP64 (nominal; no FP64 figure in MEASURE
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture each; profiles/) of the kernels as
 # committed, for the traffic entry of the roofline objects: the per-step sweep per lattice cell it updates (a
 # launch with every instance active: 198.1 MB for 4.48 M cells), the resident group kernel per explicit
-# cell-step of a whole run of this workload (dual time, 96 threads: 186.9 GB for 3.69e9; Newton, 256 threads:
-# 173.9 GB). Scaled by the cells or cell-steps of the launch being reported.
+# cell-step of a whole run of this workload (dual time, 96 threads: 187.5 GB for 3.69e9; Newton, 256 threads:
+# 174.7 GB). Scaled by the cells or cell-steps of the launch being reported.
 SWEEP_TRAFFIC_BYTES_PER_CELL = 44.25
-GROUP_TRAFFIC_BYTES_PER_CELL_STEP = {0: 50.67, 1: 47.16}
+GROUP_TRAFFIC_BYTES_PER_CELL_STEP = {0: 50.84, 1: 47.36}
 # FP64 issue of the same captures (sm__inst_executed_pipe_fp64.sum, sm__pipe_fp64_cycles_active): the sweep issues
 # one warp instruction for the 30 cells of a tile; the group kernel's count is per explicit cell-step of the run
 # (sweep warps and block solves together).
 SWEEP_FP64_ISSUE = {"warp_instructions_per_30_cell_tile": 27.8, "fp64_pipe_busy_pct": 87.2}
-GROUP_FP64_ISSUE = {0: {"warp_instructions_per_cell_step": 2.14, "fp64_pipe_busy_pct": 55.1},
-                    1: {"warp_instructions_per_cell_step": 1.18, "fp64_pipe_busy_pct": 63.7}}
+GROUP_FP64_ISSUE = {0: {"warp_instructions_per_cell_step": 1.98, "fp64_pipe_busy_pct": 54.5},
+                    1: {"warp_instructions_per_cell_step": 1.14, "fp64_pipe_busy_pct": 62.9}}
 
 
 def dist_env():
