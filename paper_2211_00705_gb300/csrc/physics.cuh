@@ -223,12 +223,13 @@ struct SideData {
   double rK, pK, invK, CK, aCK, ia2, ia, isat;
 };
 
-__device__ inline SideData side_data(const Phase& e, double rK) {
+// invK: 1 / rho_K, the reciprocal the caller also forms the side's velocity with
+__device__ inline SideData side_data(const Phase& e, double rK, double invK) {
   SideData s;
   s.E = &e;
   s.rK = rK;
   s.pK = pressure_fma(e, rK);
-  s.invK = rcp_nr(rK);
+  s.invK = invK;
   s.isat = e.irho_sat;
   s.CK = e.ln_rho_sat - fast_log(rK);  // ln(rho_sat / rho_K), independent of 1/rho_K
   s.aCK = e.a * s.CK;
@@ -403,8 +404,9 @@ __device__ inline PBOut pb_solve_core(const Fluid& F, const Opts& o, double tau,
   R.ok = 0;
   R.iters = 0;
   R.F0 = R.F1 = R.w = R.z = R.pl = R.pr = 0.0;
-  double ul = div_nr(ml, rl), ur = div_nr(mr, rr);
-  const SideData sl = side_data(F.ph[phl], rl), sr = side_data(F.ph[phr], rr);
+  const double irl0 = rcp_nr(rl), irr0 = rcp_nr(rr);  // one reciprocal per side: velocity and 1/rho_K
+  double ul = ml * irl0, ur = mr * irr0;
+  const SideData sl = side_data(F.ph[phl], rl, irl0), sr = side_data(F.ph[phr], rr, irr0);
   const bool left_vap = (phl == VAP);
   const double imp = __fma_rn(rl, F.ph[phl].a, rr * F.ph[phr].a), du = ur - ul;
   PBFast S;
@@ -430,7 +432,7 @@ __device__ inline PBOut pb_solve_core(const Fluid& F, const Opts& o, double tau,
   gl = x0;
   gr = x1;
   if (JAC) {
-    const double irl = rcp_nr(rl), irr = rcp_nr(rr);
+    const double irl = irl0, irr = irr0;
     const double fKl = dwave_drhoK(F.ph[phl], sl, x0, S.L.v, S.L.f);
     const double fKr = dwave_drhoK(F.ph[phr], sr, x1, S.R.v, S.R.f);
     // dG_2 / d(rho_l, m_l, rho_r, m_r): f_l(p_l; rho_l) + f_r(p_r; rho_r) + z [[v]] + u_r - u_l
