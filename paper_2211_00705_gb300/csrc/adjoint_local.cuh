@@ -58,16 +58,16 @@ __device__ __forceinline__ Dual<K> operator*(const Dual<K>& a, const Dual<K>& b)
   Dual<K> r;
   r.v = a.v * b.v;
 #pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+  for (int k = 0; k < K; ++k) r.d[k] = __fma_rn(a.d[k], b.v, a.v * b.d[k]);
   return r;
 }
 template <int K>
 __device__ __forceinline__ Dual<K> operator/(const Dual<K>& a, const Dual<K>& b) {
   Dual<K> r;
-  r.v = a.v / b.v;
-  const double ib = 1.0 / b.v;
+  const double ib = rcp_nr(b.v);  // within 1 ulp of 1 / b
+  r.v = a.v * ib;
 #pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
+  for (int k = 0; k < K; ++k) r.d[k] = __fma_rn(-r.v, b.d[k], a.d[k]) * ib;
   return r;
 }
 template <int K>
@@ -97,9 +97,10 @@ __device__ __forceinline__ Dual<K> operator-(double a, const Dual<K>& b) {
 template <int K>
 __device__ __forceinline__ Dual<K> operator/(const Dual<K>& a, double b) {
   Dual<K> r;
-  r.v = a.v / b;
+  const double ib = rcp_nr(b);
+  r.v = a.v * ib;
 #pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] / b;
+  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * ib;
   return r;
 }
 template <int K>
@@ -110,7 +111,7 @@ template <int K>
 __device__ __forceinline__ Dual<K> dsqrt(const Dual<K>& a) {
   Dual<K> r;
   r.v = sqrt(a.v);
-  const double s = 0.5 / r.v;
+  const double s = 0.5 * rcp_nr(r.v);
 #pragma unroll
   for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * s;
   return r;
@@ -119,7 +120,7 @@ template <int K>
 __device__ __forceinline__ Dual<K> dlog(const Dual<K>& a) {
   Dual<K> r;
   r.v = log(a.v);
-  const double s = 1.0 / a.v;
+  const double s = rcp_nr(a.v);
 #pragma unroll
   for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * s;
   return r;
