@@ -29,10 +29,12 @@ if ROOT not in sys.path:
 
 METRIC = "batched FP64 cell-steps/s (fwd, adjoint) vs plain GPU step at ≤1e-9 rel err; %HBM"
 UNIT = "cell-steps/s"
-# algorithmic FP64 flops of one explicit cell-step (a multiply and an add count separately, a division as
-# one): per cell u, p, momentum flux, |u|+a and the max (7); per face S_L, S_R (4), S_R - S_L, S_L S_R, two
-# flux components with the division (2 x 7); update (6)
-SWEEP_FLOP_PER_CELL = 33
+# algorithmic FP64 flops of one explicit cell-step (a multiply and an add count separately, so a fused
+# multiply-add counts two, a division one), in the smallest arrangement of the scheme's arithmetic: per cell u,
+# p, the momentum flux m u + p, |u| + a and the max (7); per face the two Davis speeds (4), S_R - S_L (1), the
+# weight w = S_R / (S_R - S_L) (1), the differences of rho and m (2), the HLL average of each component as
+# F_r + w ((F_l - F_r) + S_L (U_r - U_l)) (4 for mass, 5 for momentum); the update of rho and m (6)
+SWEEP_FLOP_PER_CELL = 30
 FP64_PEAK_TFLOPS = 1.25   # GB300 dense FP64 (nominal; no FP64 figure in MEASURED_PEAKS.json)
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture each; profiles/) of the kernels as
 # committed, for the traffic entry of the roofline objects: the per-step sweep per lattice cell it updates (a
@@ -598,7 +600,7 @@ def measure_run(batch, steps, warmup, schedule, flush, barrier, sampler=None, ws
     kms, kn = kt[dominant]
     per_launch_s = kms / 1e3 / max(kn, 1)
     launches_per_run = kn / (steps if group else 1)
-    # algorithmic work per launch of the dominant kernel: 33 FP64 flops and 32 bytes per explicit cell-step
+    # algorithmic work per launch of the dominant kernel: 30 FP64 flops and 32 bytes per explicit cell-step
     cs_launch = cs_run / max(launches_per_run, 1)
     ach = SWEEP_FLOP_PER_CELL * cs_launch / per_launch_s / 1e12 if per_launch_s > 0 else None
     hbm_peak = load_peak("hbm_gbs")

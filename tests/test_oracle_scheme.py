@@ -318,8 +318,9 @@ def test_operation_count_of_the_explicit_step():
     """The counting scalar (oracle/counted.h) runs the oracle's own templated scheme: its run is bit-identical
     to the plain one and leaves the oracle's states as they were. On single-phase data (every cell explicit)
     it gives the oracle's operation mix per explicit cell-step (about 54 flops in the liquid, 50 in the
-    vapour, with u formed at both faces of a cell and one division per flux component), above the 33 flops
-    per cell-step the roofline counts for the minimal arrangement (u once per cell, one reciprocal per face)."""
+    vapour, with u formed at both faces of a cell and one division per flux component), above the 30 flops
+    per cell-step the roofline counts for the smallest arrangement (u once per cell, one reciprocal per face,
+    the HLL average in its weighted form)."""
     fl = I.workload_fluid()
     N = 64
     rng = np.random.default_rng(1)
@@ -339,7 +340,7 @@ def test_operation_count_of_the_explicit_step():
         plain.step(10)
         np.testing.assert_array_equal(o.states()["rho"], plain.states()["rho"])
         flops = (c["add"] + c["mul"] + c["div"]) / c["cell_steps"]
-        assert 33 <= flops <= 60 and c["sqrt"] == c["log"] == c["exp"] == 0
+        assert 30 <= flops <= 60 and c["sqrt"] == c["log"] == c["exp"] == 0
 
 
 def test_block_newton_option_agrees_with_dual_time():
