@@ -1,0 +1,56 @@
+"""The pseudo-time step study of Sec. 4.1 (table of dual-time iterations for theta_{k+-1} in {0.9, 0.1, alpha},
+theta_k = alpha) in its isothermal analogue, on the CUDA path through the C-ABI: liquid | vapour Riemann data
+(rho_L = 972, u_L = -6, rho_V = 0.40, u_V = 4, the boundary at the lattice midpoint, tau = 1e-2 tau_paper) at
+N = 100, 200, 400 (one batch of three instances per theta_{k+-1} and alpha) with the dimensionless residual.
+The CUDA run and the oracle agree cell by cell (<= 1e-9) and in their iteration counts, and the counts show
+the paper's findings: theta_{k+-1} = 0.9 needs the fewest pseudo steps per time step, fewer as N grows; 0.1
+several times more; theta_{k+-1} = alpha orders of magnitude more, every step ending at l_max for
+alpha <= 1e-4 (those runs take 5 time steps)."""
+import dataclasses as dc
+
+import numpy as np
+import pytest
+
+from paper_2211_00705_gb300 import inputs as I
+from tests.parity import compare, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+NS = (100, 200, 400)
+ALPHAS = (1e-2, 1e-4, 1e-6)
+
+
+def _batch(theta, alpha):
+    opts = dc.replace(I.scaled_options(), theta_nb=alpha if theta == "alpha" else float(theta))
+    cells = [I._riemann_cells(N, N // 2, alpha, 972.0, -6.0, 1, 0.40, 4.0, 0) for N in NS]
+    capped = theta == "alpha" and alpha <= 1e-4
+    return I._assemble(cells, np.array(NS), np.full(len(NS), 1e-2 * I.tau_paper()), I.workload_fluid(), opts,
+                       t_end=0.0 if capped else 2e-4, n_steps=5 if capped else 0,
+                       name=f"theta study, theta_nb={theta}, alpha={alpha:g}")
+
+
+def test_theta_study_on_the_cuda_path():
+    per = {}
+    for theta in ("0.9", "0.1", "alpha"):
+        for alpha in ALPHAS:
+            b = _batch(theta, alpha)
+            a, sa = run_oracle(b)
+            g, sg = run_gpu(b)
+            compare(a, g)
+            assert (sg["maxiter"] <= sg["steps"]).all()
+            np.testing.assert_array_equal(sa["steps"], sg["steps"])
+            np.testing.assert_array_equal(sa["maxiter"], sg["maxiter"])
+            d = np.abs(sa["dts_iters"] - sg["dts_iters"])
+            assert (d <= np.maximum(2, sa["dts_iters"] // 1000)).all(), (theta, alpha, sa["dts_iters"], sg["dts_iters"])
+            for k, N in enumerate(NS):
+                per[theta, alpha, N] = (sg["dts_iters"][k] / sg["steps"][k], sg["maxiter"][k], sg["steps"][k])
+    for alpha in ALPHAS:
+        c = [per["0.9", alpha, N][0] for N in NS]
+        assert c[0] > c[1] > c[2] and c[0] < 30
+        for N in NS:
+            assert per["0.1", alpha, N][0] > 3 * per["0.9", alpha, N][0]
+    for N in NS:
+        assert per["alpha", 1e-2, N][0] > 5 * per["0.1", 1e-2, N][0]
+        for alpha in (1e-4, 1e-6):
+            it, maxiter, steps = per["alpha", alpha, N]
+            assert steps == 5 and maxiter == steps and it == 10000
