@@ -36,24 +36,19 @@ UNIT = "cell-steps/s"
 # F_r + w ((F_l - F_r) + S_L (U_r - U_l)) (4 for mass, 5 for momentum); the update of rho and m (6)
 SWEEP_FLOP_PER_CELL = 30
 FP64_PEAK_TFLOPS = 1.25   # GB300 dense FP64 (nominal; no FP64 figure in MEASURED_PEAKS.json)
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture each; profiles/) for the traffic entry
-# of the roofline objects, per lattice cell of a per-step sweep launch with every instance active (198.1 MB for
-# 4.48 M cells; the sweep's code is unchanged since), scaled by the cells of the launch being reported.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture each; profiles/) of the kernels as
+# committed, for the traffic entry of the roofline objects: the per-step sweep per lattice cell it updates (a
+# launch with every instance active: 198.1 MB for 4.48 M cells), the resident group kernel per explicit
+# cell-step of a whole run of this workload (dual time, 96 threads: 187.5 GB for 3.69e9; Newton, 256 threads:
+# 173.6 GB). Scaled by the cells or cell-steps of the launch being reported.
 SWEEP_TRAFFIC_BYTES_PER_CELL = 44.25
-# The resident group kernel's last capture (dual time, 96 threads: 187.5 GB for 3.69e9 explicit cell-steps, 50.84 B
-# each; Newton, 256 threads: 174.7 GB, 47.36 B) was taken before its boundary solve came to share one reciprocal
-# per side between the velocity and 1/rho_K. The kernel has changed since, so its traffic entry is null; the
-# earlier figures are given as a note only.
-GROUP_TRAFFIC_NOTE = {0: "50.84 B per explicit cell-step in the last ncu capture, taken on the group kernel before "
-                         "its boundary solve shared one reciprocal per side (profiles/k_group_riemann4096.md)",
-                      1: "47.36 B per explicit cell-step in the last ncu capture, taken on the group kernel before "
-                         "its boundary solve shared one reciprocal per side (profiles/k_group_riemann4096.md)"}
+GROUP_TRAFFIC_BYTES_PER_CELL_STEP = {0: 50.85, 1: 47.06}
 # FP64 issue of the same captures (sm__inst_executed_pipe_fp64.sum, sm__pipe_fp64_cycles_active): the sweep issues
 # one warp instruction for the 30 cells of a tile; the group kernel's count is per explicit cell-step of the run
-# (sweep warps and block solves together), from the capture before the shared reciprocal.
+# (sweep warps and block solves together).
 SWEEP_FP64_ISSUE = {"warp_instructions_per_30_cell_tile": 27.8, "fp64_pipe_busy_pct": 87.2}
-GROUP_FP64_ISSUE = {0: {"warp_instructions_per_cell_step": 1.98, "fp64_pipe_busy_pct": 54.5},
-                    1: {"warp_instructions_per_cell_step": 1.14, "fp64_pipe_busy_pct": 62.9}}
+GROUP_FP64_ISSUE = {0: {"warp_instructions_per_cell_step": 1.98, "fp64_pipe_busy_pct": 54.4},
+                    1: {"warp_instructions_per_cell_step": 1.14, "fp64_pipe_busy_pct": 62.6}}
 
 
 def dist_env():
@@ -612,9 +607,10 @@ def measure_run(batch, steps, warmup, schedule, flush, barrier, sampler=None, ws
     gbs = 32.0 * cs_launch / per_launch_s / 1e9 if per_launch_s > 0 else None
     roof = {"bound": "alu", "kernel": dominant, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": (ach / FP64_PEAK_TFLOPS) if ach else None,
-            "traffic": None,
-            "traffic_note": (GROUP_TRAFFIC_NOTE[batch.options.block_solver] if dominant == "k_group" else
-                             "no ncu capture of this kernel in this schedule"),
+            "traffic": (GROUP_TRAFFIC_BYTES_PER_CELL_STEP[batch.options.block_solver] * cs_launch
+                        if dominant == "k_group" else None),
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one full launch (profiles/"
+                              "k_group_riemann4096.md), per explicit cell-step, times this launch's cell-steps",
             "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table; no FP64 entry in MEASURED_PEAKS.json)",
             "ms_per_launch": per_launch_s * 1e3, "launches_per_run": launches_per_run,
             "algorithmic_flops_per_launch": SWEEP_FLOP_PER_CELL * cs_launch,
@@ -626,8 +622,7 @@ def measure_run(batch, steps, warmup, schedule, flush, barrier, sampler=None, ws
             "phase_cycles": phase}
     if dominant == "k_group":
         roof["fp64_issue"] = dict(GROUP_FP64_ISSUE[batch.options.block_solver],
-                                  source="ncu, one full launch of the group kernel before its boundary solve shared "
-                                         "one reciprocal per side (profiles/k_group_riemann4096.md)")
+                                  source="ncu, one full launch (profiles/k_group_riemann4096.md)")
     return {"ctx": ctx, "tuned": tuned, "stats": st, "value": job_value(cs_run, steps, ws, t_max),
             "ms_per_step": 1e3 * t_max / steps, "cell_steps_run": cs_run, "launches": launches, "clocks": clocks,
             "block_iters_per_step": float(st["dts_iters"].sum() / max(1, st["steps"].sum())),
