@@ -226,6 +226,20 @@ def riemann_batch(workload_id: int, n_inst: int, n_range=(100, 100), alpha_range
     return _assemble(cells, N, tau, fluid, options, t_end=t_end, n_steps=n_steps, name=name)
 
 
+def riemann_set(n_lattice, alpha: float, rho_liq: float, u_liq: float, rho_vap: float, u_vap: float, tau: float,
+                options: Options | None = None, fluid: Fluid | None = None, t_end: float = 2e-4, n_steps: int = 0,
+                name: str = "") -> Batch:
+    """Fixed liquid | vapour Riemann data at several lattice sizes, one instance per entry of n_lattice: the
+    boundary in background cell N // 2 with the tiny vapour piece alpha h (the layout of riemann_batch), the
+    same states and kinetic coefficient tau in every instance (the pseudo-time-step study of Sec. 4.1)."""
+    fluid = fluid or workload_fluid()
+    options = options or Options()
+    ns = [int(N) for N in n_lattice]
+    cells = [_riemann_cells(N, N // 2, alpha, rho_liq, u_liq, 1, rho_vap, u_vap, 0) for N in ns]
+    return _assemble(cells, np.array(ns), np.full(len(ns), float(tau)), fluid, options, t_end=t_end,
+                     n_steps=n_steps, name=name)
+
+
 def jitter_states(batch: Batch, workload_id: int, eps: float = 1e-3) -> Batch:
     """Per-cell jitter of the states: rho (1 + eps U[-1,1]), m + eps rho U[-1,1] (1 m/s). The discrete
     scheme is not differentiable where the CFL maximum is attained by several cells at once (piecewise

@@ -122,3 +122,24 @@ def test_slab_creation_layout():
         inner = w[flips[0] + 2:flips[1]]
         assert len(inner) >= 2 and np.allclose(inner, 1.0 / b.n_lattice[i])
         assert np.count_nonzero(np.abs(np.diff(u)) > 1e-9) == 1
+
+
+def test_riemann_set_matches_single_riemann_instances():
+    """riemann_set (fixed states at several N, the pseudo-time-step study's data) is the concatenation of the
+    one-instance riemann_batch draws with those states, the boundary at the lattice midpoint and tau fixed."""
+    Ns, alpha, tau = (100, 200, 400), 1e-4, 1e-2 * I.tau_paper()
+    s = I.riemann_set(Ns, alpha, 972.0, -6.0, 0.40, 4.0, tau, t_end=2e-4)
+    parts = []
+    for N in Ns:
+        b = I.riemann_batch(0, 1, n_range=(N, N), alpha_range=(alpha, alpha), coef_range=(1, 1),
+                            rho_liq=(972.0, 972.0), rho_vap=(0.40, 0.40), u_range=(0, 0), pb_range=(0.5, 0.5))
+        b.m[:] = np.where(b.phase == 1, b.rho * -6.0, b.rho * 4.0)
+        parts.append(b)
+    np.testing.assert_array_equal(s.n_lattice, Ns)
+    np.testing.assert_array_equal(s.tau, np.full(3, tau))
+    for f in ("rho", "m", "phase"):
+        np.testing.assert_array_equal(getattr(s, f), np.concatenate([getattr(b, f) for b in parts]))
+    # riemann_batch draws alpha log-uniformly, exp(log alpha) here: the tiny widths agree to rounding
+    np.testing.assert_allclose(s.widths, np.concatenate([b.widths for b in parts]), rtol=1e-14, atol=0)
+    np.testing.assert_array_equal(np.diff(s.cell_offsets), [N + 1 for N in Ns])
+    assert s.t_end == 2e-4

@@ -22,11 +22,10 @@ ALPHAS = (1e-2, 1e-4, 1e-6)
 
 def _batch(theta, alpha):
     opts = dc.replace(I.scaled_options(), theta_nb=alpha if theta == "alpha" else float(theta))
-    cells = [I._riemann_cells(N, N // 2, alpha, 972.0, -6.0, 1, 0.40, 4.0, 0) for N in NS]
     capped = theta == "alpha" and alpha <= 1e-4
-    return I._assemble(cells, np.array(NS), np.full(len(NS), 1e-2 * I.tau_paper()), I.workload_fluid(), opts,
-                       t_end=0.0 if capped else 2e-4, n_steps=5 if capped else 0,
-                       name=f"theta study, theta_nb={theta}, alpha={alpha:g}")
+    return I.riemann_set(NS, alpha, 972.0, -6.0, 0.40, 4.0, 1e-2 * I.tau_paper(), options=opts,
+                         t_end=0.0 if capped else 2e-4, n_steps=5 if capped else 0,
+                         name=f"theta study, theta_nb={theta}, alpha={alpha:g}")
 
 
 def test_theta_study_on_the_cuda_path():
