@@ -167,7 +167,9 @@ imexds_status imexds_reset(imexds_ctx* ctx);
  * the group whose launch took the most cycles (slowest6) and summed over all groups (sum6). Arrays of 6:
  * 0 boundary solves + plan, 1 sweep (first sweep warp), 2 dual time or Newton (warp 0), 3 grid management,
  * 4 the concurrent phase of 1 and 2 (barrier to barrier), 5 the whole launch. With the lockstep groups,
- * 0 + 4 + 3 equals 5 up to the loop's own instructions and 1, 2 <= 4; with the independent groups (schedule
+ * 0 + 4 + 3 equals 5 up to the loop's own instructions and, by design, 1, 2 <= 4; with Newton on the blocks
+ * at full size 1 has been measured above 4 by about 3 (the wait for the longer sweep appears to be counted in 3), so
+ * there the split between 4 and 3 is not reliable, while 5 is; with the independent groups (schedule
  * 3) each entry is the maximum over the group's instances, 4 being dual time plus the wait for the sweep.
  * The counters accumulate over the timing-mode calls since the last imexds_set_kernel_timing. */
 imexds_status imexds_get_group_phase_cycles(imexds_ctx* ctx, int64_t* slowest6, int64_t* sum6);
